@@ -1,0 +1,304 @@
+// FP64 oracle -- TEST INFRASTRUCTURE ONLY.  C API of the oracle (loaded with ctypes by the
+// tests, by the package's smoke() check and by bench.py's CPU-baseline leg).
+//
+// Arrays are environment-major ([env][coord]) doubles.  Every function returns 0 on success
+// and a negative value on a bad argument.
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "orc_model.hpp"
+#include "orc_step.hpp"
+
+using orc::Model;
+
+extern "C" {
+
+void* orc_model_new(const orc::Desc* d, char* err, int errlen) {
+  Model* m = new Model();
+  std::string e = orc::compile_model(*d, *m);
+  if (!e.empty()) {
+    if (err && errlen > 0) { std::strncpy(err, e.c_str(), errlen - 1); err[errlen - 1] = 0; }
+    delete m;
+    return nullptr;
+  }
+  return m;
+}
+
+void orc_model_free(void* h) { delete static_cast<Model*>(h); }
+
+// nq nv nu nbody ngeom nslot nrow_max njnt npair nlimited max_contacts
+int orc_model_sizes(void* h, int* out) {
+  const Model& m = *static_cast<Model*>(h);
+  int v[11] = {m.nq, m.nv, m.nu, m.nbody, m.ngeom, m.nslot, m.nrow_max, m.njnt, m.npair, m.nlimited, m.max_contacts};
+  std::memcpy(out, v, sizeof(v));
+  return 0;
+}
+
+int orc_model_massprops(void* h, double* mass, double* ipos, double* inertia, double* armature) {
+  const Model& m = *static_cast<Model*>(h);
+  std::memcpy(mass, m.mass.data(), sizeof(double) * m.nbody);
+  std::memcpy(ipos, m.ipos.data(), sizeof(double) * 3 * m.nbody);
+  std::memcpy(inertia, m.inertia.data(), sizeof(double) * 6 * m.nbody);
+  std::memcpy(armature, m.dof_armature.data(), sizeof(double) * m.nv);
+  return 0;
+}
+
+// Advance n_envs independent environments by n_steps control steps of n_substeps substeps
+// each (controls held over a control step).  solver_cap >= 1: capped Newton; < 0: converged.
+int orc_rollout(void* h, int n_envs, int n_steps, int n_substeps, double* qpos, double* qvel, double* qacc_warm,
+                const double* ctrl, uint32_t* status, int solver_cap, int nthreads, double* traj_qpos,
+                double* traj_qvel) {
+  const Model& m = *static_cast<Model*>(h);
+  if (n_envs < 0 || n_steps < 0 || n_substeps < 1) return -1;
+  if (nthreads < 1) nthreads = 1;
+  auto work = [&](int lo, int hi) {
+    for (int e = lo; e < hi; e++) {
+      double* q = qpos + (size_t)e * m.nq;
+      double* v = qvel + (size_t)e * m.nv;
+      double* w = qacc_warm + (size_t)e * m.nv;
+      for (int t = 0; t < n_steps; t++) {
+        const double* u = ctrl + ((size_t)t * n_envs + e) * m.nu;
+        for (int s = 0; s < n_substeps; s++) status[e] |= orc::substep(m, q, v, w, u, solver_cap);
+        if (traj_qpos) std::memcpy(traj_qpos + ((size_t)t * n_envs + e) * m.nq, q, sizeof(double) * m.nq);
+        if (traj_qvel) std::memcpy(traj_qvel + ((size_t)t * n_envs + e) * m.nv, v, sizeof(double) * m.nv);
+      }
+    }
+  };
+  if (nthreads == 1 || n_envs <= 1) {
+    work(0, n_envs);
+  } else {
+    std::vector<std::thread> pool;
+    int per = (n_envs + nthreads - 1) / nthreads;
+    for (int t = 0; t < nthreads; t++) {
+      int lo = t * per, hi = std::min(n_envs, lo + per);
+      if (lo < hi) pool.emplace_back(work, lo, hi);
+    }
+    for (auto& th : pool) th.join();
+  }
+  return 0;
+}
+
+// Offsets (in doubles) of the per-substep diagnostic record written by orc_forward:
+// 0 xpos[nbody][3]  1 xmat[nbody][9]  2 xcom[nbody][3]  3 M[nv][nv]  4 bias[nv]  5 passive[nv]
+// 6 actuator[nv]  7 a0[nv]  8 contacts[nslot][14] (active, dist, pos3, n3, t1 3, t2 3)
+// 9 nrow  10 rows[nrow_max][nv + 7] (J[nv], r, v, aref, D, Ahat, imp, force)  11 qacc[nv]
+// 12 iterations  13 status  14 qpos_next[nq]  15 qvel_next[nv]  16 total
+int orc_forward_layout(void* h, int* off) {
+  const Model& m = *static_cast<Model*>(h);
+  int sz[16] = {3 * m.nbody, 9 * m.nbody, 3 * m.nbody, m.nv * m.nv, m.nv, m.nv, m.nv, m.nv, 14 * m.nslot, 1,
+                m.nrow_max * (m.nv + 7), m.nv, 1, 1, m.nq, m.nv};
+  off[0] = 0;
+  for (int i = 0; i < 16; i++) off[i + 1] = off[i] + sz[i];
+  return 0;
+}
+
+int orc_forward(void* h, const double* qpos, const double* qvel, const double* qacc_warm, const double* ctrl,
+                int solver_cap, double* out) {
+  const Model& m = *static_cast<Model*>(h);
+  int off[17];
+  orc_forward_layout(h, off);
+  std::memset(out, 0, sizeof(double) * off[16]);
+  std::vector<double> q(qpos, qpos + m.nq), v(qvel, qvel + m.nv), w(qacc_warm, qacc_warm + m.nv);
+  orc::Forward<double> F;
+  uint32_t st = orc::substep(m, q.data(), v.data(), w.data(), ctrl, solver_cap, &F);
+  for (int b = 0; b < m.nbody; b++) {
+    for (int k = 0; k < 3; k++) out[off[0] + 3 * b + k] = F.kin.xbody[b].p[k];
+    for (int k = 0; k < 9; k++) out[off[1] + 9 * b + k] = F.kin.xbody[b].R[k];
+    for (int k = 0; k < 3; k++) out[off[2] + 3 * b + k] = F.kin.xcom[b][k];
+  }
+  std::memcpy(out + off[3], F.M.data(), sizeof(double) * m.nv * m.nv);
+  std::memcpy(out + off[4], F.bias.data(), sizeof(double) * m.nv);
+  std::memcpy(out + off[5], F.passive.data(), sizeof(double) * m.nv);
+  std::memcpy(out + off[6], F.actuator.data(), sizeof(double) * m.nv);
+  std::memcpy(out + off[7], F.a0.data(), sizeof(double) * m.nv);
+  for (int s = 0; s < m.nslot; s++) {
+    double* c = out + off[8] + 14 * s;
+    const orc::Contact<double>& k = F.con[s];
+    c[0] = k.active ? 1 : 0;
+    c[1] = k.dist;
+    for (int i = 0; i < 3; i++) { c[2 + i] = k.pos[i]; c[5 + i] = k.n[i]; c[8 + i] = k.t1[i]; c[11 + i] = k.t2[i]; }
+  }
+  out[off[9]] = F.rows.n;
+  for (int r = 0; r < F.rows.n && r < m.nrow_max; r++) {
+    double* o = out + off[10] + r * (m.nv + 7);
+    for (int j = 0; j < m.nv; j++) o[j] = F.rows.J[r * m.nv + j];
+    o[m.nv] = F.rows.r[r];
+    o[m.nv + 1] = F.rows.v[r];
+    o[m.nv + 2] = F.rows.aref[r];
+    o[m.nv + 3] = F.rows.D[r];
+    o[m.nv + 4] = F.rows.Ahat[r];
+    o[m.nv + 5] = F.rows.imp[r];
+    o[m.nv + 6] = F.sol.force.empty() ? 0.0 : F.sol.force[r];
+  }
+  std::memcpy(out + off[11], F.sol.qacc.data(), sizeof(double) * m.nv);
+  out[off[12]] = F.sol.iterations;
+  out[off[13]] = st;
+  std::memcpy(out + off[14], q.data(), sizeof(double) * m.nq);
+  std::memcpy(out + off[15], v.data(), sizeof(double) * m.nv);
+  return 0;
+}
+
+int orc_inverse_dynamics(void* h, const double* qpos, const double* qvel, const double* qacc, double* tau) {
+  const Model& m = *static_cast<Model*>(h);
+  orc::Kin<double> k;
+  orc::kinematics(m, qpos, k);
+  std::vector<double> t;
+  orc::inverse_dynamics(m, k, qvel, qacc, t);
+  std::memcpy(tau, t.data(), sizeof(double) * m.nv);
+  return 0;
+}
+
+int orc_mass_matrix(void* h, const double* qpos, double* M) {
+  const Model& m = *static_cast<Model*>(h);
+  orc::Kin<double> k;
+  orc::kinematics(m, qpos, k);
+  std::vector<double> Mm;
+  orc::mass_matrix(m, k, Mm);
+  std::memcpy(M, Mm.data(), sizeof(double) * m.nv * m.nv);
+  return 0;
+}
+
+// per body: R (9, row-major), x (3), com (3)
+int orc_body_frames(void* h, const double* qpos, double* out) {
+  const Model& m = *static_cast<Model*>(h);
+  orc::Kin<double> k;
+  orc::kinematics(m, qpos, k);
+  for (int b = 0; b < m.nbody; b++) {
+    for (int i = 0; i < 9; i++) out[15 * b + i] = k.xbody[b].R[i];
+    for (int i = 0; i < 3; i++) out[15 * b + 9 + i] = k.xbody[b].p[i];
+    for (int i = 0; i < 3; i++) out[15 * b + 12 + i] = k.xcom[b][i];
+  }
+  return 0;
+}
+
+// per geom: R (9), x (3)
+int orc_geom_frames(void* h, const double* qpos, double* out) {
+  const Model& m = *static_cast<Model*>(h);
+  orc::Kin<double> k;
+  orc::kinematics(m, qpos, k);
+  for (int g = 0; g < m.ngeom; g++) {
+    for (int i = 0; i < 9; i++) out[12 * g + i] = k.xgeom[g].R[i];
+    for (int i = 0; i < 3; i++) out[12 * g + 9 + i] = k.xgeom[g].p[i];
+  }
+  return 0;
+}
+
+// kinetic energy from per-body velocities (sum 1/2 m |v_com|^2 + 1/2 w^T Iw w, plus
+// 1/2 armature qdot^2) and potential energy -sum m g . com
+int orc_energy(void* h, const double* qpos, const double* qvel, double* out) {
+  const Model& m = *static_cast<Model*>(h);
+  orc::Kin<double> k;
+  orc::kinematics(m, qpos, k);
+  std::vector<double> zero(m.nv, 0.0);
+  std::vector<orc::Motion<double>> mo;
+  orc::body_motion(m, k, qvel, zero.data(), mo);
+  double T = 0, U = 0;
+  for (int b = 1; b < m.nbody; b++) {
+    orc::V3<double> vc = orc::point_vel(mo[b], k.xcom[b]);
+    orc::V3<double> Iw = orc::mv(k.Iw[b], mo[b].w);
+    T += 0.5 * m.mass[b] * orc::dot(vc, vc) + 0.5 * orc::dot(mo[b].w, Iw);
+    U -= m.mass[b] * (m.gravity[0] * k.xcom[b][0] + m.gravity[1] * k.xcom[b][1] + m.gravity[2] * k.xcom[b][2]);
+  }
+  for (int i = 0; i < m.nv; i++) T += 0.5 * m.dof_armature[i] * qvel[i] * qvel[i];
+  out[0] = T;
+  out[1] = U;
+  return 0;
+}
+
+// linear momentum P, angular momentum about the system COM, and the COM
+int orc_momentum(void* h, const double* qpos, const double* qvel, double* out) {
+  const Model& m = *static_cast<Model*>(h);
+  orc::Kin<double> k;
+  orc::kinematics(m, qpos, k);
+  std::vector<double> zero(m.nv, 0.0);
+  std::vector<orc::Motion<double>> mo;
+  orc::body_motion(m, k, qvel, zero.data(), mo);
+  orc::V3<double> P{0, 0, 0}, C{0, 0, 0}, L{0, 0, 0};
+  double Mt = 0;
+  for (int b = 1; b < m.nbody; b++) {
+    Mt += m.mass[b];
+    C = orc::add(C, orc::scl(k.xcom[b], m.mass[b]));
+  }
+  C = orc::scl(C, 1.0 / Mt);
+  for (int b = 1; b < m.nbody; b++) {
+    orc::V3<double> vc = orc::point_vel(mo[b], k.xcom[b]);
+    P = orc::add(P, orc::scl(vc, m.mass[b]));
+    L = orc::add(L, orc::add(orc::mv(k.Iw[b], mo[b].w), orc::scl(orc::cross(orc::sub(k.xcom[b], C), vc), m.mass[b])));
+  }
+  for (int i = 0; i < 3; i++) { out[i] = P[i]; out[3 + i] = L[i]; out[6 + i] = C[i]; }
+  return 0;
+}
+
+int orc_point_jacobian(void* h, const double* qpos, int body, const double* point, double* Jv, double* Jw) {
+  const Model& m = *static_cast<Model*>(h);
+  if (body < 0 || body >= m.nbody) return -1;
+  orc::Kin<double> k;
+  orc::kinematics(m, qpos, k);
+  std::vector<double> a, b;
+  orc::point_jacobian(m, k, body, orc::V3<double>{point[0], point[1], point[2]}, a, b);
+  std::memcpy(Jv, a.data(), sizeof(double) * 3 * m.nv);
+  std::memcpy(Jw, b.data(), sizeof(double) * 3 * m.nv);
+  return 0;
+}
+
+int orc_integrate_pos(void* h, double* qpos, const double* qvel, double dt) {
+  orc::integrate_pos(*static_cast<Model*>(h), qpos, qvel, dt);
+  return 0;
+}
+
+// Model-free collision of one primitive pair; frames given as R (row-major 3x3) and p.
+// Writes pair_max_points records of 13 doubles: dist, pos3, n3, t1 3, t2 3.  Returns the count.
+int orc_collide(int t1, const double* R1, const double* p1, const double* s1, int t2, const double* R2,
+                const double* p2, const double* s2, double* out) {
+  int n = orc::pair_max_points(t1, t2);
+  if (n < 0) return -1;
+  orc::Xf<double> X1, X2;
+  for (int i = 0; i < 9; i++) { X1.R[i] = R1[i]; X2.R[i] = R2[i]; }
+  for (int i = 0; i < 3; i++) { X1.p[i] = p1[i]; X2.p[i] = p2[i]; }
+  orc::Contact<double> c[4];
+  orc::collide_pair(t1, X1, s1, t2, X2, s2, c);
+  for (int i = 0; i < n; i++) {
+    double* o = out + 13 * i;
+    o[0] = c[i].dist;
+    for (int k = 0; k < 3; k++) { o[1 + k] = c[i].pos[k]; o[4 + k] = c[i].n[k]; o[7 + k] = c[i].t1[k]; o[10 + k] = c[i].t2[k]; }
+  }
+  return n;
+}
+
+// The Newton solver on raw data (M, a0, rows J/aref/D); cap < 0 selects the converged mode.
+int orc_solve(int nv, const double* M, const double* a0, int nr, const double* J, const double* aref, const double* D,
+              const double* warm, int cap, double* qacc, double* force, int* iters) {
+  std::vector<double> Mm(M, M + nv * nv), a(a0, a0 + nv);
+  orc::Rows<double> R;
+  R.n = nr;
+  R.J.assign(J, J + nr * nv);
+  R.aref.assign(aref, aref + nr);
+  R.D.assign(D, D + nr);
+  orc::SolveResult<double> s = orc::newton_solve(nv, Mm, a, R, warm, cap < 0 ? 200 : cap);
+  std::memcpy(qacc, s.qacc.data(), sizeof(double) * nv);
+  if (nr > 0) std::memcpy(force, s.force.data(), sizeof(double) * nr);
+  *iters = s.iterations;
+  return s.converged ? 1 : 0;
+}
+
+double orc_cost(int nv, const double* M, const double* a0, int nr, const double* J, const double* aref, const double* D,
+                const double* a) {
+  std::vector<double> Mm(M, M + nv * nv), aa(a0, a0 + nv), x(a, a + nv);
+  orc::Rows<double> R;
+  R.n = nr;
+  R.J.assign(J, J + nr * nv);
+  R.aref.assign(aref, aref + nr);
+  R.D.assign(D, D + nr);
+  return orc::cost(nv, Mm, aa, R, x);
+}
+
+double orc_impedance(double r, const double* solimp) { return orc::impedance(r, solimp); }
+
+void orc_solid_inertia(int type, const double* size, double m, double* out) { orc::solid_inertia(type, size, m, out); }
+
+double orc_rotor_armature(double kg, double mr, double rr) { return orc::rotor_armature(kg, mr, rr); }
+
+}  // extern "C"

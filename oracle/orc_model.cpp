@@ -1,0 +1,192 @@
+// FP64 oracle -- TEST INFRASTRUCTURE ONLY.  Derived model tables.
+#include "orc_model.hpp"
+
+#include <algorithm>
+#include <cmath>
+
+namespace orc {
+
+static M3<double> quat_rot(const double* q) {
+  double n = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  double u[4] = {q[0] / n, q[1] / n, q[2] / n, q[3] / n};
+  return quat2mat(u);
+}
+
+std::string compile_model(const Desc& d, Model& m) {
+  if (d.nbody < 1) return "nbody must be >= 1 (body 0 is the world)";
+  m.nbody = d.nbody; m.njnt = d.njnt; m.ngeom = d.ngeom; m.npair = d.npair; m.nu = d.nu;
+  m.parent.assign(d.body_parent, d.body_parent + d.nbody);
+  m.parent[0] = -1;
+  for (int b = 1; b < m.nbody; b++)
+    if (m.parent[b] < 0 || m.parent[b] >= b) return "body_parent must satisfy 0 <= parent[i] < i (level order)";
+  m.body_pos.assign(d.body_pos, d.body_pos + 3 * d.nbody);
+  m.body_quat.assign(d.body_quat, d.body_quat + 4 * d.nbody);
+  for (int b = 0; b < m.nbody; b++) {   // normalise the offset quaternions
+    double* q = &m.body_quat[4 * b];
+    double n = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    if (!(n > 0)) return "body_quat must be non-zero";
+    for (int k = 0; k < 4; k++) q[k] /= n;
+  }
+  // joints
+  m.jnt_type.assign(d.jnt_type, d.jnt_type + d.njnt);
+  m.jnt_body.assign(d.jnt_body, d.jnt_body + d.njnt);
+  m.jnt_pos.assign(d.jnt_pos, d.jnt_pos + 3 * d.njnt);
+  m.jnt_axis.assign(d.jnt_axis, d.jnt_axis + 3 * d.njnt);
+  m.jnt_limited.assign(d.jnt_limited, d.jnt_limited + d.njnt);
+  m.jnt_range.assign(d.jnt_range, d.jnt_range + 2 * d.njnt);
+  m.body_jntadr.assign(m.nbody, 0);
+  m.body_jntnum.assign(m.nbody, 0);
+  m.nq = m.nv = 0;
+  for (int j = 0; j < m.njnt; j++) {
+    int b = m.jnt_body[j], t = m.jnt_type[j];
+    if (b < 1 || b >= m.nbody) return "jnt_body out of range";
+    if (j > 0 && m.jnt_body[j - 1] > b) return "joints must be grouped by body in body order";
+    if (t != FREE && t != HINGE && t != SLIDE) return "unknown joint type";
+    if (m.body_jntnum[b] == 0) m.body_jntadr[b] = j;
+    m.body_jntnum[b]++;
+    m.jnt_qposadr.push_back(m.nq);
+    m.jnt_dofadr.push_back(m.nv);
+    m.nq += t == FREE ? 7 : 1;
+    m.nv += t == FREE ? 6 : 1;
+    if (t != FREE) {
+      double* a = &m.jnt_axis[3 * j];
+      double n = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+      if (!(n > 0)) return "joint axis must be non-zero";
+      for (int k = 0; k < 3; k++) a[k] /= n;
+      if (m.jnt_limited[j] && !(m.jnt_range[2 * j] < m.jnt_range[2 * j + 1])) return "limited joint needs range lo < hi";
+    }
+  }
+  for (int j = 0; j < m.njnt; j++)
+    if (m.jnt_type[j] == FREE && (m.parent[m.jnt_body[j]] != 0 || m.body_jntnum[m.jnt_body[j]] != 1))
+      return "a free joint must be the only joint of a child of the world";
+  // dofs and the dof tree (parent = previous dof of the body, else the last dof of the nearest
+  // ancestor body that has dofs)
+  m.dof_body.assign(m.nv, 0);
+  m.dof_jnt.assign(m.nv, 0);
+  m.dof_parent.assign(m.nv, -1);
+  std::vector<int> body_lastdof(m.nbody, -1);
+  for (int b = 1; b < m.nbody; b++) {
+    int last = body_lastdof[m.parent[b]];
+    for (int j = m.body_jntadr[b]; j < m.body_jntadr[b] + m.body_jntnum[b]; j++) {
+      int n = m.jnt_type[j] == FREE ? 6 : 1;
+      for (int k = 0; k < n; k++) {
+        int dof = m.jnt_dofadr[j] + k;
+        m.dof_body[dof] = b;
+        m.dof_jnt[dof] = j;
+        m.dof_parent[dof] = last;
+        last = dof;
+      }
+    }
+    body_lastdof[b] = last;
+  }
+  m.body_root.assign(m.nbody, 0);
+  for (int b = 1; b < m.nbody; b++) m.body_root[b] = m.parent[b] == 0 ? b : m.body_root[m.parent[b]];
+  m.dof_damping.assign(d.dof_damping, d.dof_damping + m.nv);
+  m.dof_armature.assign(m.nv, 0.0);
+  for (int i = 0; i < m.nv; i++)
+    m.dof_armature[i] = d.dof_armature[i] + rotor_armature(d.dof_rotor[3 * i], d.dof_rotor[3 * i + 1], d.dof_rotor[3 * i + 2]);
+  // geoms
+  m.geom_type.assign(d.geom_type, d.geom_type + d.ngeom);
+  m.geom_body.assign(d.geom_body, d.geom_body + d.ngeom);
+  m.geom_pos.assign(d.geom_pos, d.geom_pos + 3 * d.ngeom);
+  m.geom_quat.assign(d.geom_quat, d.geom_quat + 4 * d.ngeom);
+  m.geom_size.assign(d.geom_size, d.geom_size + 3 * d.ngeom);
+  m.geom_mass.assign(d.geom_mass, d.geom_mass + d.ngeom);
+  for (int g = 0; g < m.ngeom; g++) {
+    if (m.geom_type[g] < PLANE || m.geom_type[g] > BOX) return "unknown geom type";
+    if (m.geom_body[g] < 0 || m.geom_body[g] >= m.nbody) return "geom_body out of range";
+    double* q = &m.geom_quat[4 * g];
+    double n = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    if (!(n > 0)) return "geom_quat must be non-zero";
+    for (int k = 0; k < 4; k++) q[k] /= n;
+  }
+  // mass properties: given, or the union of the body's geoms as uniform solids
+  m.mass.assign(m.nbody, 0.0);
+  m.ipos.assign(3 * m.nbody, 0.0);
+  m.inertia.assign(6 * m.nbody, 0.0);
+  for (int b = 1; b < m.nbody; b++) {
+    if (!d.body_geom_inertia[b]) {
+      m.mass[b] = d.body_mass[b];
+      for (int k = 0; k < 3; k++) m.ipos[3 * b + k] = d.body_ipos[3 * b + k];
+      for (int k = 0; k < 6; k++) m.inertia[6 * b + k] = d.body_inertia[6 * b + k];
+      continue;
+    }
+    double M = 0, c[3] = {0, 0, 0};
+    for (int g = 0; g < m.ngeom; g++) {
+      if (m.geom_body[g] != b || m.geom_mass[g] <= 0) continue;
+      M += m.geom_mass[g];
+      for (int k = 0; k < 3; k++) c[k] += m.geom_mass[g] * m.geom_pos[3 * g + k];
+    }
+    if (M <= 0) continue;
+    for (int k = 0; k < 3; k++) c[k] /= M;
+    double I[9] = {0};
+    for (int g = 0; g < m.ngeom; g++) {
+      if (m.geom_body[g] != b || m.geom_mass[g] <= 0) continue;
+      if (m.geom_type[g] == PLANE) return "a plane cannot carry mass";
+      double Id[3];
+      solid_inertia(m.geom_type[g], &m.geom_size[3 * g], m.geom_mass[g], Id);
+      M3<double> R = quat_rot(&m.geom_quat[4 * g]);
+      double dv[3] = {m.geom_pos[3 * g] - c[0], m.geom_pos[3 * g + 1] - c[1], m.geom_pos[3 * g + 2] - c[2]};
+      double dd = dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2];
+      for (int r = 0; r < 3; r++)
+        for (int s = 0; s < 3; s++) {
+          double rot = 0;
+          for (int k = 0; k < 3; k++) rot += R[3 * r + k] * Id[k] * R[3 * s + k];
+          I[3 * r + s] += rot + m.geom_mass[g] * ((r == s ? dd : 0.0) - dv[r] * dv[s]);
+        }
+    }
+    m.mass[b] = M;
+    for (int k = 0; k < 3; k++) m.ipos[3 * b + k] = c[k];
+    double six[6] = {I[0], I[4], I[8], I[1], I[2], I[5]};
+    for (int k = 0; k < 6; k++) m.inertia[6 * b + k] = six[k];
+  }
+  // contact pairs and their static slots
+  m.nslot = 0;
+  for (int p = 0; p < m.npair; p++) {
+    int g1 = d.pair_geom[2 * p], g2 = d.pair_geom[2 * p + 1];
+    if (g1 < 0 || g1 >= m.ngeom || g2 < 0 || g2 >= m.ngeom) return "pair geom out of range";
+    int n = pair_max_points(m.geom_type[g1], m.geom_type[g2]);
+    if (n < 0) return "unsupported pair (geom1's type must not exceed geom2's: plane < sphere < capsule < box)";
+    if (d.pair_condim[p] != 1 && d.pair_condim[p] != 3) return "pair_condim must be 1 or 3";
+    m.pair_g1.push_back(g1);
+    m.pair_g2.push_back(g2);
+    m.pair_condim.push_back(d.pair_condim[p]);
+    m.pair_friction.push_back(d.pair_friction[p]);
+    m.pair_slotadr.push_back(m.nslot);
+    m.pair_nslot.push_back(n);
+    m.nslot += n;
+  }
+  // actuators
+  for (int a = 0; a < m.nu; a++) {
+    int j = d.act_jnt[a];
+    if (j < 0 || j >= m.njnt || m.jnt_type[j] == FREE) return "actuators act on hinge or slide joints";
+    if (d.act_type[a] != MOTOR && d.act_type[a] != POSITION) return "unknown actuator type";
+  }
+  m.act_type.assign(d.act_type, d.act_type + d.nu);
+  m.act_jnt.assign(d.act_jnt, d.act_jnt + d.nu);
+  m.act_gear.assign(d.act_gear, d.act_gear + d.nu);
+  m.act_kp.assign(d.act_kp, d.act_kp + d.nu);
+  m.act_kd.assign(d.act_kd, d.act_kd + d.nu);
+  m.act_ctrllimited.assign(d.act_ctrllimited, d.act_ctrllimited + d.nu);
+  m.act_ctrlrange.assign(d.act_ctrlrange, d.act_ctrlrange + 2 * d.nu);
+  // options
+  if (!(d.timestep > 0)) return "timestep must be > 0";
+  m.timestep = d.timestep;
+  for (int k = 0; k < 3; k++) m.gravity[k] = d.gravity[k];
+  m.iterations = d.iterations;
+  m.cone = d.cone;
+  if (m.cone != PYRAMIDAL) return "only the pyramidal cone is implemented";
+  m.impratio = d.impratio;
+  for (int k = 0; k < 2; k++) m.solref[k] = d.solref[k];
+  for (int k = 0; k < 5; k++) m.solimp[k] = d.solimp[k];
+  m.margin = d.margin;
+  m.max_contacts = d.max_contacts < 0 ? m.nslot : std::min(d.max_contacts, m.nslot);
+  m.nlimited = 0;
+  for (int j = 0; j < m.njnt; j++)
+    if (m.jnt_limited[j] && m.jnt_type[j] != FREE) m.nlimited++;
+  m.rows_per_contact = 4;
+  m.nrow_max = m.max_contacts * m.rows_per_contact + m.nlimited;
+  return "";
+}
+
+}  // namespace orc

@@ -1,0 +1,912 @@
+// FP64 oracle -- TEST INFRASTRUCTURE ONLY.
+//
+// One physics substep of one environment, written as plainly as possible:
+//   kinematics with rigid transforms, the mass matrix from its kinetic-energy definition
+//   (sum over bodies of m Jv^T Jv + Jw^T I Jw), bias forces by Newton-Euler on per-body
+//   velocities/accelerations projected through the Jacobians, dense Cholesky solves,
+//   primitive collision by direct geometry, constraint rows, the capped (or converged)
+//   Newton solve with an exact line search on sorted breakpoints, PD/motor actuation and
+//   semi-implicit Euler.
+//
+// The paper (MuJoCo Playground, Sec. 1 and Limitations) runs its environments on MJX and
+// does not print the step's mathematics; the formulation below is the textbook rigid-body
+// method in generalised coordinates, with these choices fixed (identically on the GPU):
+//   * PD law tau = kp (q_des - q) - kd qdot, eq. (pd_mapping), App. B.2.1, held over substeps;
+//   * armature I_a = k_g^2 m_r r_r^2 / 2, App. C.2.2;
+//   * static candidate pair lists with fixed per-pair slots (Limitations; App. B.2.3);
+//   * a Newton solver with a fixed iteration cap (Table dm_control_envs, iterations=1..4);
+//   * soft constraints: aref = -b v - k d(r) r, R = (1-d)/d * Ahat with the exact diagonal
+//     Ahat = (J M^-1 J^T)_ii, D = 1/R; impedance d(r) from solimp (d0, dwidth, width, mid, p).
+#pragma once
+#include <algorithm>
+#include <cstdint>
+#include <vector>
+
+#include "orc_math.hpp"
+#include "orc_model.hpp"
+
+namespace orc {
+
+using std::sqrt;
+
+// ------------------------------------------------------------------------------------
+// kinematics
+// ------------------------------------------------------------------------------------
+template <class T> struct Kin {
+  std::vector<Xf<T>> xbody;    // body frames in the world
+  std::vector<V3<T>> xcom;     // body centres of mass
+  std::vector<M3<T>> Iw;       // body inertia about the COM, world axes
+  std::vector<V3<T>> janchor;  // joint anchor (world), taken before the joint moves
+  std::vector<V3<T>> jaxis;    // joint axis (world)
+  std::vector<Xf<T>> xgeom;    // geom frames
+};
+
+template <class T> inline Xf<T> body_offset(const Model& m, int b) {
+  T q[4] = {T(m.body_quat[4 * b]), T(m.body_quat[4 * b + 1]), T(m.body_quat[4 * b + 2]), T(m.body_quat[4 * b + 3])};
+  return Xf<T>{quat2mat(q), V3<T>{T(m.body_pos[3 * b]), T(m.body_pos[3 * b + 1]), T(m.body_pos[3 * b + 2])}};
+}
+
+template <class T> inline V3<T> cv3(const double* p) { return V3<T>{T(p[0]), T(p[1]), T(p[2])}; }
+
+// World frame of every body: X(b) = X(parent) * X_offset(b) * prod_j X_joint(j, q_j).
+// Hinge: rotation by q about the axis through the anchor; slide: translation q along the axis;
+// free: position qpos[0:3] and the normalised quaternion qpos[3:7] (the parent is the world).
+template <class T> void kinematics(const Model& m, const T* qpos, Kin<T>& k) {
+  k.xbody.assign(m.nbody, xf_identity<T>());
+  k.xcom.assign(m.nbody, V3<T>{T(0), T(0), T(0)});
+  k.Iw.assign(m.nbody, M3<T>{});
+  k.janchor.assign(m.njnt, V3<T>{});
+  k.jaxis.assign(m.njnt, V3<T>{});
+  for (int b = 1; b < m.nbody; b++) {
+    Xf<T> X = compose(k.xbody[m.parent[b]], body_offset<T>(m, b));
+    for (int j = m.body_jntadr[b]; j < m.body_jntadr[b] + m.body_jntnum[b]; j++) {
+      const T* q = qpos + m.jnt_qposadr[j];
+      V3<T> p = cv3<T>(&m.jnt_pos[3 * j]), a = cv3<T>(&m.jnt_axis[3 * j]);
+      if (m.jnt_type[j] == FREE) {
+        T n = sqrt(q[3] * q[3] + q[4] * q[4] + q[5] * q[5] + q[6] * q[6]);
+        T qu[4] = {q[3] / n, q[4] / n, q[5] / n, q[6] / n};
+        X = Xf<T>{quat2mat(qu), V3<T>{q[0], q[1], q[2]}};
+        k.janchor[j] = X.p;
+        k.jaxis[j] = V3<T>{T(0), T(0), T(0)};
+      } else {
+        k.janchor[j] = xform(X, p);
+        k.jaxis[j] = mv(X.R, a);
+        if (m.jnt_type[j] == HINGE) {
+          Xf<T> to{eye3<T>(), p}, back{eye3<T>(), scl(p, T(-1))}, rot{axis_angle(a, q[0]), V3<T>{T(0), T(0), T(0)}};
+          X = compose(X, compose(to, compose(rot, back)));
+        } else {
+          X = compose(X, Xf<T>{eye3<T>(), scl(a, q[0])});
+        }
+      }
+    }
+    k.xbody[b] = X;
+    k.xcom[b] = xform(X, cv3<T>(&m.ipos[3 * b]));
+    const double* I = &m.inertia[6 * b];
+    M3<T> Ib{T(I[0]), T(I[3]), T(I[4]), T(I[3]), T(I[1]), T(I[5]), T(I[4]), T(I[5]), T(I[2])};
+    k.Iw[b] = mm(X.R, mm(Ib, mT(X.R)));
+  }
+  k.xgeom.resize(m.ngeom);
+  for (int g = 0; g < m.ngeom; g++) {
+    T q[4] = {T(m.geom_quat[4 * g]), T(m.geom_quat[4 * g + 1]), T(m.geom_quat[4 * g + 2]), T(m.geom_quat[4 * g + 3])};
+    k.xgeom[g] = compose(k.xbody[m.geom_body[g]], Xf<T>{quat2mat(q), cv3<T>(&m.geom_pos[3 * g])});
+  }
+}
+
+// Linear (Jv) and angular (Jw) velocity Jacobians, 3 x nv row-major, of the world point P
+// moving with body b.  Columns: hinge (a, a x (P - anchor)); slide (0, a); free translation
+// (0, e_k) in world axes; free rotation (R e_k, R e_k x (P - x_body)) for the body-local
+// angular velocity.
+template <class T> void point_jacobian(const Model& m, const Kin<T>& k, int b, const V3<T>& P, std::vector<T>& Jv,
+                                       std::vector<T>& Jw) {
+  const int nv = m.nv;
+  Jv.assign(3 * nv, T(0));
+  Jw.assign(3 * nv, T(0));
+  for (int bb = b; bb > 0; bb = m.parent[bb]) {
+    for (int j = m.body_jntadr[bb]; j < m.body_jntadr[bb] + m.body_jntnum[bb]; j++) {
+      int d = m.jnt_dofadr[j];
+      if (m.jnt_type[j] == FREE) {
+        const M3<T>& R = k.xbody[bb].R;
+        for (int c = 0; c < 3; c++) {
+          Jv[c * nv + d + c] = T(1);
+          V3<T> e = col(R, c);
+          V3<T> lin = cross(e, sub(P, k.xbody[bb].p));
+          for (int r = 0; r < 3; r++) {
+            Jw[r * nv + d + 3 + c] = e[r];
+            Jv[r * nv + d + 3 + c] = lin[r];
+          }
+        }
+      } else if (m.jnt_type[j] == HINGE) {
+        V3<T> a = k.jaxis[j], lin = cross(a, sub(P, k.janchor[j]));
+        for (int r = 0; r < 3; r++) {
+          Jw[r * nv + d] = a[r];
+          Jv[r * nv + d] = lin[r];
+        }
+      } else {
+        for (int r = 0; r < 3; r++) Jv[r * nv + d] = k.jaxis[j][r];
+      }
+    }
+  }
+}
+
+// M = sum_b ( m_b Jv(com_b)^T Jv(com_b) + Jw_b^T Iw_b Jw_b ) + diag(armature):
+// the matrix of the kinetic energy 1/2 qdot^T M qdot (rotor inertia on the diagonal).
+template <class T> void mass_matrix(const Model& m, const Kin<T>& k, std::vector<T>& M) {
+  const int nv = m.nv;
+  M.assign(nv * nv, T(0));
+  std::vector<T> Jv, Jw;
+  for (int b = 1; b < m.nbody; b++) {
+    point_jacobian(m, k, b, k.xcom[b], Jv, Jw);
+    for (int i = 0; i < nv; i++)
+      for (int j = 0; j < nv; j++) {
+        T s = T(0);
+        for (int r = 0; r < 3; r++) s = s + T(m.mass[b]) * Jv[r * nv + i] * Jv[r * nv + j];
+        for (int r = 0; r < 3; r++)
+          for (int c = 0; c < 3; c++) s = s + Jw[r * nv + i] * k.Iw[b][3 * r + c] * Jw[c * nv + j];
+        M[i * nv + j] = M[i * nv + j] + s;
+      }
+  }
+  for (int i = 0; i < nv; i++) M[i * nv + i] = M[i * nv + i] + T(m.dof_armature[i]);
+}
+
+// Per-body angular velocity w and acceleration al, and a reference point r fixed in the body
+// with its velocity vr and acceleration ar, propagated from the world along each joint:
+//   hinge (axis a through p): move the reference to p (rigid-body formulas), then
+//         w += a qd,  al += a qdd + w_before x (a qd);
+//   slide (axis a): vr += a qd, ar += a qdd + 2 w x (a qd)   (relative + Coriolis terms);
+//   free: w = R qd[3:6], al = R qdd[3:6], r = x_body, vr = qd[0:3], ar = qdd[0:3].
+template <class T> struct Motion {
+  V3<T> w, al, r, vr, ar;
+};
+
+template <class T> void body_motion(const Model& m, const Kin<T>& k, const T* qvel, const T* qacc,
+                                    std::vector<Motion<T>>& out) {
+  V3<T> z{T(0), T(0), T(0)};
+  out.assign(m.nbody, Motion<T>{z, z, z, z, z});
+  for (int b = 1; b < m.nbody; b++) {
+    Motion<T> s = out[m.parent[b]];
+    for (int j = m.body_jntadr[b]; j < m.body_jntadr[b] + m.body_jntnum[b]; j++) {
+      int d = m.jnt_dofadr[j];
+      if (m.jnt_type[j] == FREE) {
+        const M3<T>& R = k.xbody[b].R;
+        s.w = mv(R, V3<T>{qvel[d + 3], qvel[d + 4], qvel[d + 5]});
+        s.al = mv(R, V3<T>{qacc[d + 3], qacc[d + 4], qacc[d + 5]});
+        s.r = k.xbody[b].p;
+        s.vr = V3<T>{qvel[d], qvel[d + 1], qvel[d + 2]};
+        s.ar = V3<T>{qacc[d], qacc[d + 1], qacc[d + 2]};
+      } else if (m.jnt_type[j] == HINGE) {
+        V3<T> p = k.janchor[j], a = k.jaxis[j], rp = sub(p, s.r);
+        s.vr = add(s.vr, cross(s.w, rp));
+        s.ar = add(add(s.ar, cross(s.al, rp)), cross(s.w, cross(s.w, rp)));
+        s.r = p;
+        s.al = add(add(s.al, scl(a, qacc[d])), cross(s.w, scl(a, qvel[d])));
+        s.w = add(s.w, scl(a, qvel[d]));
+      } else {
+        V3<T> a = k.jaxis[j];
+        s.vr = add(s.vr, scl(a, qvel[d]));
+        s.ar = add(add(s.ar, scl(a, qacc[d])), scl(cross(s.w, scl(a, qvel[d])), T(2)));
+      }
+    }
+    out[b] = s;
+  }
+}
+
+template <class T> inline V3<T> point_vel(const Motion<T>& s, const V3<T>& P) { return add(s.vr, cross(s.w, sub(P, s.r))); }
+template <class T> inline V3<T> point_acc(const Motion<T>& s, const V3<T>& P) {
+  V3<T> d = sub(P, s.r);
+  return add(add(s.ar, cross(s.al, d)), cross(s.w, cross(s.w, d)));
+}
+
+// Inverse dynamics tau = M(q) qdd + c(q, qd) by Newton-Euler: per body the force
+// m (a_com - g) and the torque about the COM Iw al + w x Iw w, mapped to generalised forces
+// with the body's Jacobians (virtual work); plus armature * qdd.
+template <class T> void inverse_dynamics(const Model& m, const Kin<T>& k, const T* qvel, const T* qacc, std::vector<T>& tau) {
+  const int nv = m.nv;
+  std::vector<Motion<T>> mo;
+  body_motion(m, k, qvel, qacc, mo);
+  tau.assign(nv, T(0));
+  V3<T> g{T(m.gravity[0]), T(m.gravity[1]), T(m.gravity[2])};
+  std::vector<T> Jv, Jw;
+  for (int b = 1; b < m.nbody; b++) {
+    V3<T> ac = point_acc(mo[b], k.xcom[b]);
+    V3<T> F = scl(sub(ac, g), T(m.mass[b]));
+    V3<T> Iwv = mv(k.Iw[b], mo[b].w);
+    V3<T> N = add(mv(k.Iw[b], mo[b].al), cross(mo[b].w, Iwv));
+    point_jacobian(m, k, b, k.xcom[b], Jv, Jw);
+    for (int i = 0; i < nv; i++) {
+      T s = T(0);
+      for (int r = 0; r < 3; r++) s = s + Jv[r * nv + i] * F[r] + Jw[r * nv + i] * N[r];
+      tau[i] = tau[i] + s;
+    }
+  }
+  for (int i = 0; i < nv; i++) tau[i] = tau[i] + T(m.dof_armature[i]) * qacc[i];
+}
+
+// ------------------------------------------------------------------------------------
+// collision
+// ------------------------------------------------------------------------------------
+template <class T> struct Contact {
+  bool active = false;
+  T dist = T(0);
+  V3<T> pos{}, n{}, t1{}, t2{};
+};
+
+// Tangent frame: t1 = normalise(n x e_k), e_k the world axis with the smallest |n_k|
+// (ties to the lowest k); t2 = n x t1.
+template <class T> void contact_frame(Contact<T>& c) {
+  double a0 = std::fabs(val(c.n[0])), a1 = std::fabs(val(c.n[1])), a2 = std::fabs(val(c.n[2]));
+  int kmin = 0;
+  if (a1 < a0) kmin = 1;
+  if (a2 < (kmin == 0 ? a0 : a1)) kmin = 2;
+  V3<T> e{T(0), T(0), T(0)};
+  e[kmin] = T(1);
+  V3<T> t = cross(c.n, e);
+  c.t1 = scl(t, T(1) / norm(t));
+  c.t2 = cross(c.n, c.t1);
+}
+
+// Two spheres (c1, r1) -> (c2, r2); normal from the first to the second; the contact point is
+// the midpoint of the two surface points.  Coincident centres use the normal +z.
+template <class T> Contact<T> sphere_sphere(const V3<T>& c1, T r1, const V3<T>& c2, T r2) {
+  Contact<T> c;
+  V3<T> d = sub(c2, c1);
+  T L = norm(d);
+  if (val(L) > 1e-12) c.n = scl(d, T(1) / L);
+  else c.n = V3<T>{T(0), T(0), T(1)};
+  c.dist = L - r1 - r2;
+  V3<T> s1 = add(c1, scl(c.n, r1)), s2 = sub(c2, scl(c.n, r2));
+  c.pos = scl(add(s1, s2), T(0.5));
+  return c;
+}
+
+// Sphere (c, r) against a plane through p0 with unit normal nz (the plane is geom1).
+template <class T> Contact<T> plane_sphere(const V3<T>& p0, const V3<T>& nz, const V3<T>& c, T r) {
+  Contact<T> out;
+  T h = dot(nz, sub(c, p0));
+  out.n = nz;
+  out.dist = h - r;
+  V3<T> s_sphere = sub(c, scl(nz, r)), s_plane = sub(c, scl(nz, h));
+  out.pos = scl(add(s_sphere, s_plane), T(0.5));
+  return out;
+}
+
+// Sphere (c, r) (geom1) against a box (frame X, half-sizes h) (geom2).  Outside: the closest
+// box point by clamping; inside: the face of least penetration (ties to the lowest axis).
+template <class T> Contact<T> sphere_box(const V3<T>& c, T r, const Xf<T>& X, const double* h) {
+  Contact<T> out;
+  V3<T> p = mtv(X.R, sub(c, X.p));
+  V3<T> q;
+  bool inside = true;
+  for (int k = 0; k < 3; k++) {
+    T hk = T(h[k]);
+    if (val(p[k]) > h[k]) { q[k] = hk; inside = false; }
+    else if (val(p[k]) < -h[k]) { q[k] = -hk; inside = false; }
+    else q[k] = p[k];
+  }
+  V3<T> out_dir;   // unit direction from the box towards the sphere (world)
+  V3<T> surf;      // box surface point (box frame)
+  if (!inside) {
+    V3<T> d = sub(p, q);
+    T L = norm(d);
+    out_dir = mv(X.R, scl(d, T(1) / L));
+    surf = q;
+    out.dist = L - r;
+  } else {
+    int kb = 0;
+    double best = h[0] - std::fabs(val(p[0]));
+    for (int k = 1; k < 3; k++) {
+      double s = h[k] - std::fabs(val(p[k]));
+      if (s < best) { best = s; kb = k; }
+    }
+    T sg = val(p[kb]) >= 0 ? T(1) : T(-1);
+    V3<T> e{T(0), T(0), T(0)};
+    e[kb] = sg;
+    out_dir = mv(X.R, e);
+    surf = p;
+    surf[kb] = sg * T(h[kb]);
+    T pen = T(h[kb]) - sg * p[kb];
+    out.dist = -pen - r;
+  }
+  out.n = scl(out_dir, T(-1));
+  V3<T> s_box = xform(X, surf), s_sph = add(c, scl(out.n, r));
+  out.pos = scl(add(s_box, s_sph), T(0.5));
+  return out;
+}
+
+// Closest points of the segments c1 + u a1 (|u| <= h1) and c2 + v a2 (|v| <= h2), unit axes:
+// u from the unconstrained solution (u = 0 when the axes are parallel, 1 - (a1.a2)^2 <= 1e-10),
+// clamped; then v optimal for u, clamped; then u optimal for v, clamped.
+template <class T> void segment_segment(const V3<T>& c1, const V3<T>& a1, T h1, const V3<T>& c2, const V3<T>& a2, T h2,
+                                        T& u, T& v) {
+  V3<T> r = sub(c1, c2);
+  T b = dot(a1, a2), c = dot(a1, r), f = dot(a2, r);
+  T den = T(1) - b * b;
+  auto clamp = [](T x, T lo, T hi) { return val(x) < val(lo) ? lo : (val(x) > val(hi) ? hi : x); };
+  if (val(den) > 1e-10) u = clamp((b * f - c) / den, -h1, h1);
+  else u = T(0);
+  v = clamp(b * u + f, -h2, h2);
+  u = clamp(b * v - c, -h1, h1);
+}
+
+template <class T> inline V3<T> seg_axis(const Xf<T>& X) { return col(X.R, 2); }
+
+// Box-box by the separating-axis test over the 15 candidate axes (3 face normals of each box and
+// the 9 edge-edge cross products).  Overlap along a unit axis L: sum_k hA_k |L.A_k| +
+// sum_k hB_k |L.B_k| - |L.(cB - cA)|.  If any axis separates, every slot stays inactive.
+// Axis choice: the best face axis of box 1, replaced by box 2's best face axis only if that is
+// smaller by more than tol = 1e-5 (1 + overlap), then by the best edge axis only if smaller
+// again by more than tol (ties to the lower index throughout).
+//   Face case: the owning box is the reference; the incident face is the other box's face whose
+//   outward normal is most opposed to the reference normal; it is clipped (Sutherland-Hodgman)
+//   against the four side planes of the reference face; clipped points below the reference face
+//   (depth >= 0) are contacts, at the midpoint between the point and its projection on the
+//   reference face.  More than 4: the deepest, the farthest from it, the one of largest triangle
+//   area with those two, then the one farthest outside that triangle; kept in polygon order.
+//   Edge case: the closest points of the two supporting edges; one contact.
+// The normal points from box 1 to box 2.
+template <class T> void box_box(const Xf<T>& XA, const double* hA, const Xf<T>& XB, const double* hB, Contact<T>* out) {
+  for (int i = 0; i < 4; i++) { out[i].dist = T(1); out[i].n = V3<T>{T(0), T(0), T(1)}; out[i].pos = XA.p; }
+  V3<T> A[3] = {col(XA.R, 0), col(XA.R, 1), col(XA.R, 2)};
+  V3<T> B[3] = {col(XB.R, 0), col(XB.R, 1), col(XB.R, 2)};
+  V3<T> dc = sub(XB.p, XA.p);
+  auto overlap = [&](const V3<T>& L) {
+    T rA = T(0), rB = T(0);
+    for (int k = 0; k < 3; k++) {
+      T a = dot(L, A[k]), b = dot(L, B[k]);
+      rA = rA + T(hA[k]) * (val(a) < 0 ? -a : a);
+      rB = rB + T(hB[k]) * (val(b) < 0 ? -b : b);
+    }
+    T s = dot(L, dc);
+    return rA + rB - (val(s) < 0 ? -s : s);
+  };
+  V3<T> axes[15];
+  bool valid[15];
+  T ov[15];
+  for (int k = 0; k < 3; k++) { axes[k] = A[k]; axes[3 + k] = B[k]; valid[k] = valid[3 + k] = true; }
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) {
+      V3<T> c = cross(A[i], B[j]);
+      T n = norm(c);
+      valid[6 + 3 * i + j] = val(n) > 1e-6;
+      axes[6 + 3 * i + j] = valid[6 + 3 * i + j] ? scl(c, T(1) / n) : c;
+    }
+  for (int k = 0; k < 15; k++) {
+    if (!valid[k]) continue;
+    ov[k] = overlap(axes[k]);
+    if (val(ov[k]) < 0) return;   // separated
+  }
+  auto best_in = [&](int lo, int hi) {
+    int b = -1;
+    for (int k = lo; k < hi; k++)
+      if (valid[k] && (b < 0 || val(ov[k]) < val(ov[b]))) b = k;
+    return b;
+  };
+  int best = best_in(0, 3);
+  int bB = best_in(3, 6);
+  if (val(ov[bB]) < val(ov[best]) - 1e-5 * (1 + val(ov[best]))) best = bB;
+  int bE = best_in(6, 15);
+  if (bE >= 0 && val(ov[bE]) < val(ov[best]) - 1e-5 * (1 + val(ov[best]))) best = bE;
+  V3<T> L = axes[best];
+  T depth = ov[best];
+  V3<T> n = val(dot(L, dc)) < 0 ? scl(L, T(-1)) : L;   // from box 1 to box 2
+  if (best >= 6) {
+    int i = (best - 6) / 3, j = (best - 6) % 3;
+    V3<T> pa = XA.p, pb = XB.p;
+    for (int k = 0; k < 3; k++) {
+      if (k != i) pa = add(pa, scl(A[k], T(val(dot(n, A[k])) >= 0 ? hA[k] : -hA[k])));
+      if (k != j) pb = add(pb, scl(B[k], T(val(dot(n, B[k])) >= 0 ? -hB[k] : hB[k])));
+    }
+    T u, v;
+    segment_segment(pa, A[i], T(hA[i]), pb, B[j], T(hB[j]), u, v);
+    V3<T> qa = add(pa, scl(A[i], u)), qb = add(pb, scl(B[j], v));
+    out[0].n = n;
+    out[0].dist = -depth;
+    out[0].pos = scl(add(qa, qb), T(0.5));
+    return;
+  }
+  // face case
+  bool refA = best < 3;
+  const Xf<T>& XR = refA ? XA : XB;
+  const Xf<T>& XI = refA ? XB : XA;
+  const double* hR = refA ? hA : hB;
+  const double* hI = refA ? hB : hA;
+  int kr = refA ? best : best - 3;
+  V3<T> nref = refA ? n : scl(n, T(-1));   // reference normal, towards the incident box
+  // incident face: outward normal most opposed to nref
+  int fk = 0;
+  double fs = 1, bestd = 2;
+  for (int k = 0; k < 3; k++) {
+    double d = val(dot(col(XI.R, k), nref));
+    if (d < bestd) { bestd = d; fk = k; fs = 1; }
+    if (-d < bestd) { bestd = -d; fk = k; fs = -1; }
+  }
+  int ku = (fk + 1) % 3, kv = (fk + 2) % 3;
+  static const int su[4] = {-1, 1, 1, -1}, sv[4] = {-1, -1, 1, 1};
+  std::vector<V3<T>> poly;
+  for (int c = 0; c < 4; c++) {
+    V3<T> l{T(0), T(0), T(0)};
+    l[fk] = T(fs * hI[fk]);
+    l[ku] = T(su[c] * hI[ku]);
+    l[kv] = T(sv[c] * hI[kv]);
+    poly.push_back(xform(XI, l));
+  }
+  int ru = (kr + 1) % 3, rv = (kr + 2) % 3;
+  V3<T> planes_n[4] = {col(XR.R, ru), scl(col(XR.R, ru), T(-1)), col(XR.R, rv), scl(col(XR.R, rv), T(-1))};
+  double planes_h[4] = {hR[ru], hR[ru], hR[rv], hR[rv]};
+  for (int pl = 0; pl < 4 && !poly.empty(); pl++) {
+    auto side = [&](const V3<T>& p) { return T(planes_h[pl]) - dot(sub(p, XR.p), planes_n[pl]); };
+    std::vector<V3<T>> outp;
+    V3<T> S = poly.back();
+    for (size_t e = 0; e < poly.size(); e++) {
+      V3<T> E = poly[e];
+      T sS = side(S), sE = side(E);
+      if (val(sE) >= 0) {
+        if (val(sS) < 0) outp.push_back(add(S, scl(sub(E, S), sS / (sS - sE))));
+        outp.push_back(E);
+      } else if (val(sS) >= 0) {
+        outp.push_back(add(S, scl(sub(E, S), sS / (sS - sE))));
+      }
+      S = E;
+    }
+    poly = outp;
+  }
+  std::vector<int> idx;
+  std::vector<T> dep;
+  for (size_t i = 0; i < poly.size(); i++) {
+    T d = T(hR[kr]) - dot(sub(poly[i], XR.p), nref);
+    dep.push_back(d);
+    if (val(d) >= 0) idx.push_back((int)i);
+  }
+  if (idx.size() > 4) {
+    std::vector<int> keep;
+    int p0 = idx[0];
+    for (int i : idx) if (val(dep[i]) > val(dep[p0])) p0 = i;
+    keep.push_back(p0);
+    int p1 = -1;
+    double bd = -1;
+    for (int i : idx) {
+      if (i == p0) continue;
+      double d = val(norm(sub(poly[i], poly[p0])));
+      if (d > bd) { bd = d; p1 = i; }
+    }
+    keep.push_back(p1);
+    int p2 = -1;
+    bd = -1;
+    for (int i : idx) {
+      if (i == p0 || i == p1) continue;
+      double d = val(norm(cross(sub(poly[p1], poly[p0]), sub(poly[i], poly[p0]))));
+      if (d > bd) { bd = d; p2 = i; }
+    }
+    keep.push_back(p2);
+    int p3 = -1;
+    bd = -1;
+    for (int i : idx) {
+      if (i == p0 || i == p1 || i == p2) continue;
+      double d = val(norm(cross(sub(poly[p1], poly[p0]), sub(poly[i], poly[p0])))) +
+                 val(norm(cross(sub(poly[p2], poly[p1]), sub(poly[i], poly[p1])))) +
+                 val(norm(cross(sub(poly[p0], poly[p2]), sub(poly[i], poly[p2]))));
+      if (d > bd) { bd = d; p3 = i; }
+    }
+    keep.push_back(p3);
+    std::sort(keep.begin(), keep.end());
+    idx = keep;
+  }
+  for (size_t c = 0; c < idx.size(); c++) {
+    int i = idx[c];
+    out[c].n = n;
+    out[c].dist = -dep[i];
+    out[c].pos = add(poly[i], scl(nref, dep[i] * T(0.5)));
+  }
+}
+
+// All candidate contacts of one pair, written to out[0 .. pair_max_points).
+template <class T> void collide_pair(int t1, const Xf<T>& X1, const double* s1, int t2, const Xf<T>& X2, const double* s2,
+                                     Contact<T>* out) {
+  if (t1 == PLANE) {
+    V3<T> nz = col(X1.R, 2), p0 = X1.p;
+    if (t2 == SPHERE) {
+      out[0] = plane_sphere(p0, nz, X2.p, T(s2[0]));
+    } else if (t2 == CAPSULE) {
+      V3<T> a = seg_axis(X2);
+      for (int e = 0; e < 2; e++) {
+        T sgn = e == 0 ? T(-1) : T(1);
+        out[e] = plane_sphere(p0, nz, add(X2.p, scl(a, sgn * T(s2[1]))), T(s2[0]));
+      }
+    } else if (t2 == BOX) {
+      // the 4 deepest of the 8 corners (ties to the lower corner index), kept in corner order
+      T d[8];
+      V3<T> cp[8];
+      for (int v = 0; v < 8; v++) {
+        V3<T> l{T((v & 1) ? s2[0] : -s2[0]), T((v & 2) ? s2[1] : -s2[1]), T((v & 4) ? s2[2] : -s2[2])};
+        cp[v] = xform(X2, l);
+        d[v] = dot(nz, sub(cp[v], p0));
+      }
+      int order[8] = {0, 1, 2, 3, 4, 5, 6, 7};
+      std::stable_sort(order, order + 8, [&](int a, int b) { return val(d[a]) < val(d[b]); });
+      int keep[4] = {order[0], order[1], order[2], order[3]};
+      std::sort(keep, keep + 4);
+      for (int i = 0; i < 4; i++) {
+        int v = keep[i];
+        out[i].n = nz;
+        out[i].dist = d[v];
+        out[i].pos = sub(cp[v], scl(nz, d[v] * T(0.5)));
+      }
+    }
+  } else if (t1 == SPHERE) {
+    if (t2 == SPHERE) {
+      out[0] = sphere_sphere(X1.p, T(s1[0]), X2.p, T(s2[0]));
+    } else if (t2 == CAPSULE) {
+      V3<T> a = seg_axis(X2);
+      T t = dot(sub(X1.p, X2.p), a);
+      T h = T(s2[1]);
+      if (val(t) > val(h)) t = h;
+      if (val(t) < -val(h)) t = -h;
+      out[0] = sphere_sphere(X1.p, T(s1[0]), add(X2.p, scl(a, t)), T(s2[0]));
+    } else if (t2 == BOX) {
+      out[0] = sphere_box(X1.p, T(s1[0]), X2, s2);
+    }
+  } else if (t1 == CAPSULE) {
+    if (t2 == CAPSULE) {
+      V3<T> a1 = seg_axis(X1), a2 = seg_axis(X2);
+      T u, v;
+      segment_segment(X1.p, a1, T(s1[1]), X2.p, a2, T(s2[1]), u, v);
+      out[0] = sphere_sphere(add(X1.p, scl(a1, u)), T(s1[0]), add(X2.p, scl(a2, v)), T(s2[0]));
+    } else if (t2 == BOX) {
+      V3<T> a = seg_axis(X1);
+      for (int e = 0; e < 2; e++) {
+        T sgn = e == 0 ? T(-1) : T(1);
+        out[e] = sphere_box(add(X1.p, scl(a, sgn * T(s1[1]))), T(s1[0]), X2, s2);
+      }
+    }
+  } else if (t1 == BOX && t2 == BOX) {
+    box_box(X1, s1, X2, s2, out);
+  }
+  for (int i = 0; i < pair_max_points(t1, t2); i++) contact_frame(out[i]);
+}
+
+// ------------------------------------------------------------------------------------
+// constraint rows
+// ------------------------------------------------------------------------------------
+template <class T> struct Rows {
+  int n = 0;
+  std::vector<T> J;                          // n x nv
+  std::vector<T> r, v, aref, D, Ahat, imp;   // per row
+  std::vector<int> slot;                     // contact slot (or -1 - joint for a limit)
+};
+
+// Impedance d(r) from solimp = (d0, dwidth, width, mid, power): x = min(|r| / width, 1),
+// y = x^p / mid^(p-1) for x <= mid, else 1 - (1-x)^p / (1-mid)^(p-1); d = d0 + y (dwidth - d0).
+template <class T> T impedance(const T& r, const double* solimp) {
+  using std::pow;
+  double d0 = solimp[0], d1 = solimp[1], width = solimp[2], mid = solimp[3], p = solimp[4];
+  T x = (val(r) < 0 ? -r : r) / T(width);
+  if (val(x) >= 1.0) return T(d1);
+  T y;
+  if (val(x) <= mid) y = pow(x, p) / std::pow(mid, p - 1);
+  else y = T(1) - pow(T(1) - x, p) / std::pow(1 - mid, p - 1);
+  return T(d0) + y * T(d1 - d0);
+}
+
+// ------------------------------------------------------------------------------------
+// the convex soft-constraint problem and its Newton solver
+// ------------------------------------------------------------------------------------
+// f(a) = 1/2 (a - a0)^T M (a - a0) + sum_i 1/2 D_i min(0, J_i a - aref_i)^2
+template <class T> T cost(int nv, const std::vector<T>& M, const std::vector<T>& a0, const Rows<T>& R,
+                          const std::vector<T>& a) {
+  T f = T(0);
+  for (int i = 0; i < nv; i++) {
+    T s = T(0);
+    for (int j = 0; j < nv; j++) s = s + M[i * nv + j] * (a[j] - a0[j]);
+    f = f + T(0.5) * (a[i] - a0[i]) * s;
+  }
+  for (int i = 0; i < R.n; i++) {
+    T jar = -R.aref[i];
+    for (int j = 0; j < nv; j++) jar = jar + R.J[i * nv + j] * a[j];
+    if (val(jar) < 0) f = f + T(0.5) * R.D[i] * jar * jar;
+  }
+  return f;
+}
+
+template <class T> struct SolveResult {
+  std::vector<T> qacc, force;
+  int iterations = 0;
+  bool converged = false;
+  bool warm_used = false;
+};
+
+// Exact minimiser over alpha of f(a + alpha p) (piecewise quadratic, convex): sort the
+// breakpoints alpha_i = -jar_i / Jp_i > 0 (ties by row index) and walk the segments until the
+// derivative phi'(alpha) = alpha (p^T M p + sum_act D Jp^2) + (p^T M (a-a0) + sum_act D Jp jar)
+// changes sign.
+template <class T> T exact_line_search(int nv, const std::vector<T>& M, const std::vector<T>& a0, const Rows<T>& R,
+                                       const std::vector<T>& a, const std::vector<T>& p) {
+  std::vector<T> jar(R.n), Jp(R.n);
+  for (int i = 0; i < R.n; i++) {
+    T s = -R.aref[i], t = T(0);
+    for (int j = 0; j < nv; j++) {
+      s = s + R.J[i * nv + j] * a[j];
+      t = t + R.J[i * nv + j] * p[j];
+    }
+    jar[i] = s;
+    Jp[i] = t;
+  }
+  T quad = T(0), lin = T(0);
+  for (int i = 0; i < nv; i++) {
+    T Mp = T(0), Md = T(0);
+    for (int j = 0; j < nv; j++) {
+      Mp = Mp + M[i * nv + j] * p[j];
+      Md = Md + M[i * nv + j] * (a[j] - a0[j]);
+    }
+    quad = quad + p[i] * Mp;
+    lin = lin + p[i] * Md;
+  }
+  std::vector<char> act(R.n, 0);
+  std::vector<int> bp;
+  for (int i = 0; i < R.n; i++) {
+    bool on = val(jar[i]) < 0 || (val(jar[i]) == 0 && val(Jp[i]) < 0);
+    act[i] = on;
+    if (on) { quad = quad + R.D[i] * Jp[i] * Jp[i]; lin = lin + R.D[i] * Jp[i] * jar[i]; }
+    if (val(Jp[i]) != 0 && -val(jar[i]) / val(Jp[i]) > 0) bp.push_back(i);
+  }
+  std::stable_sort(bp.begin(), bp.end(), [&](int x, int y) {
+    return -val(jar[x]) / val(Jp[x]) < -val(jar[y]) / val(Jp[y]);
+  });
+  for (size_t k = 0; k <= bp.size(); k++) {
+    T root = -lin / quad;
+    if (k == bp.size() || val(root) <= -val(jar[bp[k]]) / val(Jp[bp[k]])) return root;
+    int i = bp[k];   // crossing this breakpoint toggles row i
+    if (act[i]) { quad = quad - R.D[i] * Jp[i] * Jp[i]; lin = lin - R.D[i] * Jp[i] * jar[i]; act[i] = 0; }
+    else { quad = quad + R.D[i] * Jp[i] * Jp[i]; lin = lin + R.D[i] * Jp[i] * jar[i]; act[i] = 1; }
+  }
+  return -lin / quad;
+}
+
+// Newton's method on f: g = M(a - a0) + J_A^T D_A (J_A a - aref_A), H = M + J_A^T D_A J_A,
+// p = -H^-1 g (dense Cholesky), exact line search, a += alpha p.  It stops at the iteration cap
+// or as soon as the active set after the step equals the one used to build H (then the step
+// was exact and a is the minimiser).  Warm start: qacc_warm if f(qacc_warm) < f(a0), else a0.
+template <class T> SolveResult<T> newton_solve(int nv, const std::vector<T>& M, const std::vector<T>& a0,
+                                               const Rows<T>& R, const T* warm, int cap) {
+  SolveResult<T> out;
+  std::vector<T> a = a0;
+  if (R.n == 0) {
+    out.qacc = a0;
+    out.converged = true;
+    return out;
+  }
+  if (warm) {
+    std::vector<T> w(warm, warm + nv);
+    if (val(cost(nv, M, a0, R, w)) < val(cost(nv, M, a0, R, a0))) { a = w; out.warm_used = true; }
+  }
+  auto active_set = [&](const std::vector<T>& x) {
+    std::vector<char> s(R.n);
+    for (int i = 0; i < R.n; i++) {
+      T jar = -R.aref[i];
+      for (int j = 0; j < nv; j++) jar = jar + R.J[i * nv + j] * x[j];
+      s[i] = val(jar) < 0;
+    }
+    return s;
+  };
+  for (int it = 0; it < cap; it++) {
+    std::vector<char> A = active_set(a);
+    std::vector<T> g(nv), H(M);
+    for (int i = 0; i < nv; i++) {
+      T s = T(0);
+      for (int j = 0; j < nv; j++) s = s + M[i * nv + j] * (a[j] - a0[j]);
+      g[i] = s;
+    }
+    for (int r = 0; r < R.n; r++) {
+      if (!A[r]) continue;
+      T jar = -R.aref[r];
+      for (int j = 0; j < nv; j++) jar = jar + R.J[r * nv + j] * a[j];
+      for (int i = 0; i < nv; i++) {
+        g[i] = g[i] + R.D[r] * jar * R.J[r * nv + i];
+        for (int j = 0; j < nv; j++) H[i * nv + j] = H[i * nv + j] + R.D[r] * R.J[r * nv + i] * R.J[r * nv + j];
+      }
+    }
+    out.iterations = it + 1;
+    bool zero = true;
+    for (int i = 0; i < nv; i++) zero = zero && val(g[i]) == 0;
+    if (zero) { out.converged = true; break; }
+    if (!cholesky(H, nv)) break;
+    std::vector<T> p(g);
+    chol_solve(H, nv, p);
+    for (int i = 0; i < nv; i++) p[i] = -p[i];
+    T alpha = exact_line_search(nv, M, a0, R, a, p);
+    for (int i = 0; i < nv; i++) a[i] = a[i] + alpha * p[i];
+    if (active_set(a) == A) { out.converged = true; break; }
+  }
+  out.qacc = a;
+  out.force.assign(R.n, T(0));
+  for (int i = 0; i < R.n; i++) {
+    T jar = -R.aref[i];
+    for (int j = 0; j < nv; j++) jar = jar + R.J[i * nv + j] * a[j];
+    if (val(jar) < 0) out.force[i] = -R.D[i] * jar;
+  }
+  return out;
+}
+
+// ------------------------------------------------------------------------------------
+// one substep
+// ------------------------------------------------------------------------------------
+template <class T> struct Forward {
+  Kin<T> kin;
+  std::vector<T> M, bias, passive, actuator, a0;
+  std::vector<Contact<T>> con;
+  Rows<T> rows;
+  SolveResult<T> sol;
+  uint32_t status = 0;
+};
+
+// Actuation: motor tau += gear * u (u clamped to ctrlrange when ctrllimited);
+// position (PD, eq. pd_mapping) tau += kp (u - q) - kd qdot on the actuated joint.
+template <class T> void actuation(const Model& m, const T* qpos, const T* qvel, const T* ctrl, std::vector<T>& tau) {
+  tau.assign(m.nv, T(0));
+  for (int a = 0; a < m.nu; a++) {
+    int j = m.act_jnt[a], d = m.jnt_dofadr[j], qa = m.jnt_qposadr[j];
+    T u = ctrl[a];
+    if (m.act_ctrllimited[a]) {
+      if (val(u) < m.act_ctrlrange[2 * a]) u = T(m.act_ctrlrange[2 * a]);
+      if (val(u) > m.act_ctrlrange[2 * a + 1]) u = T(m.act_ctrlrange[2 * a + 1]);
+    }
+    if (m.act_type[a] == MOTOR) tau[d] = tau[d] + T(m.act_gear[a]) * u;
+    else tau[d] = tau[d] + T(m.act_kp[a]) * (u - qpos[qa]) - T(m.act_kd[a]) * qvel[d];
+  }
+}
+
+template <class T> void build_rows(const Model& m, const Forward<T>& F, const T* qpos, const T* qvel, Rows<T>& R,
+                                   const std::vector<T>& Mchol) {
+  const int nv = m.nv;
+  R = Rows<T>();
+  std::vector<T> Jv1, Jw1, Jv2, Jw2;
+  auto push = [&](const std::vector<T>& Jrow, T r, int slot) {
+    R.J.insert(R.J.end(), Jrow.begin(), Jrow.end());
+    R.r.push_back(r);
+    R.slot.push_back(slot);
+    R.n++;
+  };
+  for (int p = 0; p < m.npair; p++) {
+    int g1 = m.pair_g1[p], g2 = m.pair_g2[p];
+    int b1 = m.geom_body[g1], b2 = m.geom_body[g2];
+    for (int s = m.pair_slotadr[p]; s < m.pair_slotadr[p] + m.pair_nslot[p]; s++) {
+      const Contact<T>& c = F.con[s];
+      if (!c.active) continue;
+      point_jacobian(m, F.kin, b1, c.pos, Jv1, Jw1);
+      point_jacobian(m, F.kin, b2, c.pos, Jv2, Jw2);
+      std::vector<T> Jn(nv), Jt1(nv), Jt2(nv);
+      for (int i = 0; i < nv; i++) {
+        V3<T> dj{Jv2[i] - Jv1[i], Jv2[nv + i] - Jv1[nv + i], Jv2[2 * nv + i] - Jv1[2 * nv + i]};
+        Jn[i] = dot(c.n, dj);
+        Jt1[i] = dot(c.t1, dj);
+        Jt2[i] = dot(c.t2, dj);
+      }
+      if (m.pair_condim[p] == 1) {
+        push(Jn, c.dist, s);
+      } else {
+        T mu = T(m.pair_friction[p]);
+        std::vector<T> e(nv);
+        for (int k = 0; k < 4; k++) {
+          const std::vector<T>& Jt = k < 2 ? Jt1 : Jt2;
+          T sg = (k % 2 == 0) ? mu : -mu;
+          for (int i = 0; i < nv; i++) e[i] = Jn[i] + sg * Jt[i];
+          push(e, c.dist, s);
+        }
+      }
+    }
+  }
+  for (int j = 0; j < m.njnt; j++) {
+    if (!m.jnt_limited[j] || m.jnt_type[j] == FREE) continue;
+    T q = qpos[m.jnt_qposadr[j]];
+    int d = m.jnt_dofadr[j];
+    std::vector<T> e(nv, T(0));
+    if (val(q) - m.jnt_range[2 * j] < m.margin) {
+      e[d] = T(1);
+      push(e, q - T(m.jnt_range[2 * j]), -1 - j);
+    } else if (m.jnt_range[2 * j + 1] - val(q) < m.margin) {
+      e[d] = T(-1);
+      push(e, T(m.jnt_range[2 * j + 1]) - q, -1 - j);
+    }
+  }
+  // reference acceleration and regularisation per row
+  double h = m.timestep;
+  double tc = std::max(m.solref[0], 2 * h), zeta = m.solref[1], dmax = m.solimp[1];
+  double kk = 1.0 / (dmax * dmax * tc * tc * zeta * zeta), bb = 2.0 / (dmax * tc);
+  R.v.resize(R.n); R.aref.resize(R.n); R.D.resize(R.n); R.Ahat.resize(R.n); R.imp.resize(R.n);
+  for (int i = 0; i < R.n; i++) {
+    T v = T(0);
+    for (int j = 0; j < nv; j++) v = v + R.J[i * nv + j] * qvel[j];
+    std::vector<T> x(R.J.begin() + i * nv, R.J.begin() + (i + 1) * nv);
+    chol_solve(Mchol, nv, x);
+    T A = T(0);
+    for (int j = 0; j < nv; j++) A = A + R.J[i * nv + j] * x[j];
+    T d = impedance(R.r[i], m.solimp);
+    R.v[i] = v;
+    R.Ahat[i] = A;
+    R.imp[i] = d;
+    R.aref[i] = -T(bb) * v - T(kk) * d * R.r[i];
+    R.D[i] = d / ((T(1) - d) * A);
+  }
+}
+
+// solver_cap < 0 selects the converged mode (cap 200, exact termination only)
+template <class T> void forward(const Model& m, const T* qpos, const T* qvel, const T* qacc_warm, const T* ctrl,
+                                int solver_cap, Forward<T>& F) {
+  const int nv = m.nv;
+  kinematics(m, qpos, F.kin);
+  mass_matrix(m, F.kin, F.M);
+  std::vector<T> zero(nv, T(0));
+  inverse_dynamics(m, F.kin, qvel, zero.data(), F.bias);
+  F.passive.assign(nv, T(0));
+  for (int i = 0; i < nv; i++) F.passive[i] = -T(m.dof_damping[i]) * qvel[i];
+  actuation(m, qpos, qvel, ctrl, F.actuator);
+  std::vector<T> Mchol(F.M);
+  if (!cholesky(Mchol, nv)) F.status |= ST_NAN;
+  F.a0.assign(nv, T(0));
+  for (int i = 0; i < nv; i++) F.a0[i] = F.actuator[i] + F.passive[i] - F.bias[i];
+  chol_solve(Mchol, nv, F.a0);
+  // collision over the static pair list; then the active-contact cap in slot order
+  F.con.assign(m.nslot, Contact<T>());
+  for (int p = 0; p < m.npair; p++) {
+    int g1 = m.pair_g1[p], g2 = m.pair_g2[p];
+    collide_pair(m.geom_type[g1], F.kin.xgeom[g1], &m.geom_size[3 * g1], m.geom_type[g2], F.kin.xgeom[g2],
+                 &m.geom_size[3 * g2], &F.con[m.pair_slotadr[p]]);
+  }
+  int nact = 0;
+  for (int s = 0; s < m.nslot; s++) {
+    F.con[s].active = val(F.con[s].dist) < m.margin;
+    if (F.con[s].active) {
+      if (nact >= m.max_contacts) { F.con[s].active = false; F.status |= ST_CAPACITY; }
+      else nact++;
+    }
+  }
+  build_rows(m, F, qpos, qvel, F.rows, Mchol);
+  bool warm_ok = true;
+  for (int i = 0; i < nv; i++) warm_ok = warm_ok && std::isfinite(val(qacc_warm[i]));
+  if (!warm_ok) F.status |= ST_WARM_RESET;
+  int cap = solver_cap < 0 ? 200 : solver_cap;
+  F.sol = newton_solve(nv, F.M, F.a0, F.rows, warm_ok ? qacc_warm : nullptr, cap);
+  if (!F.sol.converged) F.status |= ST_NOT_CONVERGED;
+}
+
+// Semi-implicit Euler: qvel += h qacc, then positions with the new velocity; the free joint's
+// quaternion is multiplied by the rotation of angle h |w| about w (body-local w) and normalised.
+template <class T> void integrate_pos(const Model& m, T* qpos, const T* qvel, double h) {
+  for (int j = 0; j < m.njnt; j++) {
+    T* q = qpos + m.jnt_qposadr[j];
+    const T* v = qvel + m.jnt_dofadr[j];
+    if (m.jnt_type[j] == FREE) {
+      for (int k = 0; k < 3; k++) q[k] = q[k] + T(h) * v[k];
+      T wn = sqrt(v[3] * v[3] + v[4] * v[4] + v[5] * v[5]);
+      std::array<T, 4> qq{q[3], q[4], q[5], q[6]};
+      if (val(wn) > 0) {
+        using std::cos; using std::sin;
+        T ang = T(h) * wn, s = sin(ang * T(0.5)) / wn;
+        std::array<T, 4> dq{cos(ang * T(0.5)), v[3] * s, v[4] * s, v[5] * s};
+        qq = qmul(qq, dq);
+      }
+      T n = sqrt(qq[0] * qq[0] + qq[1] * qq[1] + qq[2] * qq[2] + qq[3] * qq[3]);
+      for (int k = 0; k < 4; k++) q[3 + k] = qq[k] / n;
+    } else {
+      q[0] = q[0] + T(h) * v[0];
+    }
+  }
+}
+
+template <class T> uint32_t substep(const Model& m, T* qpos, T* qvel, T* qacc_warm, const T* ctrl, int solver_cap,
+                                    Forward<T>* keep = nullptr) {
+  Forward<T> local;
+  Forward<T>& F = keep ? *keep : local;
+  F = Forward<T>();
+  forward(m, qpos, qvel, qacc_warm, ctrl, solver_cap, F);
+  const int nv = m.nv;
+  for (int i = 0; i < nv; i++) qvel[i] = qvel[i] + T(m.timestep) * F.sol.qacc[i];
+  integrate_pos(m, qpos, qvel, m.timestep);
+  for (int i = 0; i < nv; i++) qacc_warm[i] = F.sol.qacc[i];
+  uint32_t st = F.status;
+  for (int i = 0; i < nv; i++)
+    if (!std::isfinite(val(qvel[i])) || !std::isfinite(val(F.sol.qacc[i]))) st |= ST_NAN;
+  for (int i = 0; i < m.nq; i++)
+    if (!std::isfinite(val(qpos[i]))) st |= ST_NAN;
+  return st;
+}
+
+}  // namespace orc

@@ -1,0 +1,380 @@
+"""Synthetic robot models and seeded inputs for the batched physics step.
+
+This module only *describes* inputs: flat kinematic-tree arrays in level order
+(the model format the library's compiler and the oracle both read) and the
+seeded initial states and action sequences.  It contains none of the step's
+arithmetic (no kinematics, dynamics, collision or solver code); both the CUDA
+path and the FP64 oracle consume what it produces.
+
+The paper's own workloads are MJCF robots from MuJoCo Menagerie and the DM
+Control Suite (Sec. 2), which are not available here.  The models below stand
+in for them at matching scale: a DM-Control-style cartpole, a Go1-like 12-DoF
+quadruped with feet-only contacts (Sec. 4.2.1, App. B.2.3), a LEAP-like
+16-DoF hand with a 7 cm cube (Sec. 4.3.1, App. C.2.2) and a G1-like 29-DoF
+humanoid (Sec. 4.2.2).
+
+Random numbers: SplitMix64 (Steele, Lea & Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014) with seed = config * 2**40 + env.
+The k-th draw of a stream is mix(seed + (k + 1) * gamma), so any draw can be
+generated independently; a draw becomes a double in [0, 1) from its top 53
+bits, and every value handed to either path is first rounded to float32.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+
+# joint, geom, actuator and cone type codes (shared numbering of the model format)
+FREE, HINGE, SLIDE = 0, 1, 2
+PLANE, SPHERE, CAPSULE, BOX = 0, 1, 2, 3
+MOTOR, POSITION = 0, 1
+PYRAMIDAL, ELLIPTIC = 0, 1
+
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: np.ndarray, k: np.ndarray) -> np.ndarray:
+    """k-th output (k >= 0) of the SplitMix64 stream started at `seed` (uint64, broadcast)."""
+    with np.errstate(over="ignore"):
+        z = np.asarray(seed, np.uint64) + (np.asarray(k, np.uint64) + np.uint64(1)) * _GAMMA
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        return z ^ (z >> np.uint64(31))
+
+
+def uniform01(seed: np.ndarray, k: np.ndarray) -> np.ndarray:
+    """Doubles in [0, 1) from the top 53 bits of the k-th draw."""
+    return (splitmix64(seed, k) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def env_seeds(config: int, n_envs: int, env0: int = 0) -> np.ndarray:
+    return np.uint64(config) * np.uint64(1 << 40) + np.arange(env0, env0 + n_envs, dtype=np.uint64)
+
+
+def _f32(x) -> np.ndarray:
+    return np.asarray(x, dtype=np.float64).astype(np.float32)
+
+
+# --------------------------------------------------------------------------------------
+# model description
+# --------------------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Model:
+    """Flat kinematic-tree arrays (body 0 is the world; parent[i] < i)."""
+
+    name: str
+    body_parent: np.ndarray      # [nbody] int32
+    body_pos: np.ndarray         # [nbody,3] frame offset in the parent frame at q = 0
+    body_quat: np.ndarray        # [nbody,4] (w,x,y,z)
+    body_mass: np.ndarray        # [nbody]
+    body_ipos: np.ndarray        # [nbody,3] centre of mass in the body frame
+    body_inertia: np.ndarray     # [nbody,6] (xx,yy,zz,xy,xz,yz) about the COM, body axes
+    body_geom_inertia: np.ndarray  # [nbody] int32: 1 = derive mass/COM/inertia from the body's geoms
+    jnt_type: np.ndarray         # [njnt] int32 FREE/HINGE/SLIDE
+    jnt_body: np.ndarray         # [njnt] int32 (joints grouped by body, in body order)
+    jnt_pos: np.ndarray          # [njnt,3] anchor in the body frame
+    jnt_axis: np.ndarray         # [njnt,3] axis in the body frame
+    jnt_limited: np.ndarray      # [njnt] int32
+    jnt_range: np.ndarray        # [njnt,2]
+    dof_damping: np.ndarray      # [nv]
+    dof_armature: np.ndarray     # [nv]
+    dof_rotor: np.ndarray        # [nv,3] (gear ratio k_g, rotor mass m_r, rotor radius r_r); k_g = 0: none
+    geom_type: np.ndarray        # [ngeom] int32
+    geom_body: np.ndarray        # [ngeom] int32
+    geom_pos: np.ndarray         # [ngeom,3]
+    geom_quat: np.ndarray        # [ngeom,4]
+    geom_size: np.ndarray        # [ngeom,3] sphere (r), capsule (r, half-length), box (half-sizes)
+    geom_mass: np.ndarray        # [ngeom]
+    pair_geom: np.ndarray        # [npair,2] int32 candidate contact pairs (geom1, geom2)
+    pair_friction: np.ndarray    # [npair]
+    pair_condim: np.ndarray      # [npair] int32: 1 (frictionless) or 3
+    act_type: np.ndarray         # [nu] int32 MOTOR/POSITION
+    act_jnt: np.ndarray          # [nu] int32 (hinge or slide joint)
+    act_gear: np.ndarray         # [nu]
+    act_kp: np.ndarray           # [nu]
+    act_kd: np.ndarray           # [nu]
+    act_ctrllimited: np.ndarray  # [nu] int32
+    act_ctrlrange: np.ndarray    # [nu,2]
+    timestep: float
+    gravity: np.ndarray          # [3]
+    iterations: int              # Newton iteration cap
+    cone: int                    # PYRAMIDAL / ELLIPTIC
+    impratio: float
+    solref: np.ndarray           # [2] (timeconst, dampratio)
+    solimp: np.ndarray           # [5] (d0, dwidth, width, mid, power)
+    margin: float
+    max_contacts: int            # cap on simultaneously active contacts
+    n_substeps: int = 1          # physics substeps per control step for this workload
+    default_ctrl: Optional[np.ndarray] = None  # [nu] e.g. the standing pose targets
+    qpos_init: Optional[np.ndarray] = None     # [nq] reference initial configuration
+
+    @property
+    def nbody(self) -> int:
+        return int(self.body_parent.shape[0])
+
+    @property
+    def njnt(self) -> int:
+        return int(self.jnt_type.shape[0])
+
+    @property
+    def nq(self) -> int:
+        return int(sum(7 if t == FREE else 1 for t in self.jnt_type))
+
+    @property
+    def nv(self) -> int:
+        return int(sum(6 if t == FREE else 1 for t in self.jnt_type))
+
+    @property
+    def nu(self) -> int:
+        return int(self.act_type.shape[0])
+
+    @property
+    def ngeom(self) -> int:
+        return int(self.geom_type.shape[0])
+
+    @property
+    def npair(self) -> int:
+        return int(self.pair_geom.shape[0])
+
+    def jnt_qposadr(self) -> np.ndarray:
+        adr, out = 0, []
+        for t in self.jnt_type:
+            out.append(adr)
+            adr += 7 if t == FREE else 1
+        return np.asarray(out, np.int32)
+
+    def jnt_dofadr(self) -> np.ndarray:
+        adr, out = 0, []
+        for t in self.jnt_type:
+            out.append(adr)
+            adr += 6 if t == FREE else 1
+        return np.asarray(out, np.int32)
+
+
+class ModelBuilder:
+    """Appends bodies, joints, geoms, pairs and actuators in level order."""
+
+    def __init__(self, name: str):
+        self.name = name
+        self.bodies: List[dict] = [dict(parent=-1, pos=(0, 0, 0), quat=(1, 0, 0, 0), mass=0.0,
+                                        ipos=(0, 0, 0), inertia=(0,) * 6, geom_inertia=0)]
+        self.joints: List[dict] = []
+        self.geoms: List[dict] = []
+        self.pairs: List[dict] = []
+        self.acts: List[dict] = []
+
+    def body(self, parent: int, pos, quat=(1, 0, 0, 0), mass: float = 0.0, ipos=(0, 0, 0),
+             inertia=(0,) * 6, geom_inertia: bool = True) -> int:
+        assert 0 <= parent < len(self.bodies)
+        self.bodies.append(dict(parent=parent, pos=pos, quat=quat, mass=mass, ipos=ipos,
+                                inertia=inertia, geom_inertia=int(geom_inertia)))
+        return len(self.bodies) - 1
+
+    def joint(self, body: int, jtype: int, pos=(0, 0, 0), axis=(0, 0, 1), limited=False,
+              range=(0.0, 0.0), damping=0.0, armature=0.0, rotor=(0.0, 0.0, 0.0)) -> int:
+        assert not self.joints or self.joints[-1]["body"] <= body, "joints must follow body order"
+        self.joints.append(dict(body=body, type=jtype, pos=pos, axis=axis, limited=int(limited),
+                                range=range, damping=damping, armature=armature, rotor=rotor))
+        return len(self.joints) - 1
+
+    def geom(self, body: int, gtype: int, size, pos=(0, 0, 0), quat=(1, 0, 0, 0), mass=0.0) -> int:
+        s = list(size) + [0.0] * (3 - len(size))
+        self.geoms.append(dict(body=body, type=gtype, size=s, pos=pos, quat=quat, mass=mass))
+        return len(self.geoms) - 1
+
+    def pair(self, g1: int, g2: int, friction=1.0, condim=3) -> int:
+        self.pairs.append(dict(g=(g1, g2), friction=friction, condim=condim))
+        return len(self.pairs) - 1
+
+    def actuator(self, jnt: int, atype: int, gear=1.0, kp=0.0, kd=0.0, ctrllimited=False,
+                 ctrlrange=(0.0, 0.0)) -> int:
+        self.acts.append(dict(jnt=jnt, type=atype, gear=gear, kp=kp, kd=kd,
+                              ctrllimited=int(ctrllimited), ctrlrange=ctrlrange))
+        return len(self.acts) - 1
+
+    def build(self, *, timestep, gravity=(0, 0, -9.81), iterations=4, cone=PYRAMIDAL, impratio=1.0,
+              solref=(0.02, 1.0), solimp=(0.9, 0.95, 0.001, 0.5, 2.0), margin=0.0,
+              max_contacts=None, n_substeps=1, default_ctrl=None, qpos_init=None) -> Model:
+        B, J, G = self.bodies, self.joints, self.geoms
+        dof = []
+        for j in J:
+            n = 6 if j["type"] == FREE else 1
+            dof += [j] * n
+        maxpts = {(PLANE, SPHERE): 1, (PLANE, CAPSULE): 2, (PLANE, BOX): 4, (SPHERE, SPHERE): 1,
+                  (SPHERE, CAPSULE): 1, (CAPSULE, CAPSULE): 1, (SPHERE, BOX): 1, (CAPSULE, BOX): 2,
+                  (BOX, BOX): 4}
+        slots = sum(maxpts[(G[p["g"][0]]["type"], G[p["g"][1]]["type"])] for p in self.pairs)
+        i32 = lambda x: np.asarray(x, np.int32)
+        m = Model(
+            name=self.name,
+            body_parent=i32([b["parent"] for b in B]),
+            body_pos=_f32([b["pos"] for b in B]).reshape(-1, 3),
+            body_quat=_f32([b["quat"] for b in B]).reshape(-1, 4),
+            body_mass=_f32([b["mass"] for b in B]),
+            body_ipos=_f32([b["ipos"] for b in B]).reshape(-1, 3),
+            body_inertia=_f32([b["inertia"] for b in B]).reshape(-1, 6),
+            body_geom_inertia=i32([b["geom_inertia"] for b in B]),
+            jnt_type=i32([j["type"] for j in J]),
+            jnt_body=i32([j["body"] for j in J]),
+            jnt_pos=_f32([j["pos"] for j in J]).reshape(-1, 3),
+            jnt_axis=_f32([j["axis"] for j in J]).reshape(-1, 3),
+            jnt_limited=i32([j["limited"] for j in J]),
+            jnt_range=_f32([j["range"] for j in J]).reshape(-1, 2),
+            dof_damping=_f32([j["damping"] for j in dof]),
+            dof_armature=_f32([j["armature"] for j in dof]),
+            dof_rotor=_f32([j["rotor"] for j in dof]).reshape(-1, 3),
+            geom_type=i32([g["type"] for g in G]),
+            geom_body=i32([g["body"] for g in G]),
+            geom_pos=_f32([g["pos"] for g in G]).reshape(-1, 3),
+            geom_quat=_f32([g["quat"] for g in G]).reshape(-1, 4),
+            geom_size=_f32([g["size"] for g in G]).reshape(-1, 3),
+            geom_mass=_f32([g["mass"] for g in G]),
+            pair_geom=i32([p["g"] for p in self.pairs]).reshape(-1, 2),
+            pair_friction=_f32([p["friction"] for p in self.pairs]),
+            pair_condim=i32([p["condim"] for p in self.pairs]),
+            act_type=i32([a["type"] for a in self.acts]),
+            act_jnt=i32([a["jnt"] for a in self.acts]),
+            act_gear=_f32([a["gear"] for a in self.acts]),
+            act_kp=_f32([a["kp"] for a in self.acts]),
+            act_kd=_f32([a["kd"] for a in self.acts]),
+            act_ctrllimited=i32([a["ctrllimited"] for a in self.acts]),
+            act_ctrlrange=_f32([a["ctrlrange"] for a in self.acts]).reshape(-1, 2),
+            timestep=float(np.float32(timestep)),
+            gravity=_f32(gravity),
+            iterations=int(iterations),
+            cone=int(cone),
+            impratio=float(np.float32(impratio)),
+            solref=_f32(solref),
+            solimp=_f32(solimp),
+            margin=float(np.float32(margin)),
+            max_contacts=int(slots if max_contacts is None else max_contacts),
+            n_substeps=int(n_substeps),
+            default_ctrl=None if default_ctrl is None else _f32(default_ctrl),
+            qpos_init=None if qpos_init is None else _f32(qpos_init),
+        )
+        return m
+
+
+def _axis_quat(axis, angle):
+    a = np.asarray(axis, np.float64)
+    a = a / np.linalg.norm(a)
+    return (math.cos(angle / 2),) + tuple(a * math.sin(angle / 2))
+
+
+# --------------------------------------------------------------------------------------
+# the synthetic models
+# --------------------------------------------------------------------------------------
+
+def cartpole() -> Model:
+    """Cart on a slider (box 0.4x0.2x0.1 m, 1 kg, damping 0.1) carrying a hinged pole
+    (capsule 1.0 m, radius 0.05 m, 0.1 kg); motor with gear 10 on the slider; dt 0.01 s.
+    q = 0 is the pole upright.  No contacts and no limits."""
+    b = ModelBuilder("cartpole")
+    cart = b.body(0, (0, 0, 0))
+    b.joint(cart, SLIDE, axis=(1, 0, 0), damping=0.1)
+    b.geom(cart, BOX, (0.2, 0.1, 0.05), mass=1.0)
+    pole = b.body(cart, (0, 0, 0))
+    b.joint(pole, HINGE, axis=(0, 1, 0))
+    b.geom(pole, CAPSULE, (0.05, 0.5), pos=(0, 0, 0.5), mass=0.1)
+    b.actuator(0, MOTOR, gear=10.0, ctrllimited=True, ctrlrange=(-1.0, 1.0))
+    return b.build(timestep=0.01, iterations=1, n_substeps=1, qpos_init=(0.0, 0.0))
+
+
+QUAD_HIP = ((0.19, 0.05), (0.19, -0.05), (-0.19, 0.05), (-0.19, -0.05))
+QUAD_STAND = (0.0, 0.9, -1.8)       # (abduction, flexion, knee) per leg
+QUAD_LINK = 0.2
+QUAD_FOOT_R = 0.02
+
+
+def quadruped_standing_height() -> float:
+    """Torso height with every foot 1 mm above the plane in the standing pose: the hip is
+    at the torso origin height and thigh + calf make a closed 'V' (0.9 rad and -1.8 rad)."""
+    th, kn = QUAD_STAND[1], QUAD_STAND[2]
+    drop = QUAD_LINK * math.cos(th) + QUAD_LINK * math.cos(th + kn)
+    return drop + QUAD_FOOT_R + 0.001
+
+
+def quadruped() -> Model:
+    """Floating-base quadruped: torso box 0.38x0.1x0.1 m, 5 kg; per leg an abduction (x) and a
+    flexion (y) hinge at the hip, thigh capsule 0.2 m r 0.02 0.6 kg, knee (y) hinge, calf capsule
+    0.2 m r 0.02 0.15 kg and a massless r 0.02 foot sphere.  Feet-only foot/plane contacts,
+    friction 1, pyramidal cone; PD kp 35 kd 0.5; dt 0.004 s, 5 substeps, Newton cap 4."""
+    b = ModelBuilder("quadruped")
+    floor = b.geom(0, PLANE, (0, 0, 0))
+    z0 = quadruped_standing_height()
+    torso = b.body(0, (0, 0, z0))
+    b.joint(torso, FREE)
+    b.geom(torso, BOX, (0.19, 0.05, 0.05), mass=5.0)
+    thighs, calves, feet = [], [], []
+    for hx, hy in QUAD_HIP:
+        t = b.body(torso, (hx, hy, 0.0))
+        b.joint(t, HINGE, axis=(1, 0, 0), limited=True, range=(-1.0, 1.0))
+        b.joint(t, HINGE, axis=(0, 1, 0), limited=True, range=(-1.5, 1.5))
+        b.geom(t, CAPSULE, (QUAD_FOOT_R, QUAD_LINK / 2), pos=(0, 0, -QUAD_LINK / 2), mass=0.6)
+        thighs.append(t)
+    for t in thighs:
+        c = b.body(t, (0, 0, -QUAD_LINK))
+        b.joint(c, HINGE, axis=(0, 1, 0), limited=True, range=(-2.7, -0.9))
+        b.geom(c, CAPSULE, (QUAD_FOOT_R, QUAD_LINK / 2), pos=(0, 0, -QUAD_LINK / 2), mass=0.15)
+        feet.append(b.geom(c, SPHERE, (QUAD_FOOT_R,), pos=(0, 0, -QUAD_LINK), mass=0.0))
+        calves.append(c)
+    for f in feet:
+        b.pair(floor, f, friction=1.0, condim=3)
+    # actuators in joint order: 4 x (abduction, flexion) then 4 x knee
+    for j in range(1, 13):
+        b.actuator(j, POSITION, kp=35.0, kd=0.5)
+    stand = [QUAD_STAND[0], QUAD_STAND[1]] * 4 + [QUAD_STAND[2]] * 4
+    qpos = [0.0, 0.0, z0, 1.0, 0.0, 0.0, 0.0] + stand
+    return b.build(timestep=0.004, iterations=4, cone=PYRAMIDAL, n_substeps=5,
+                   default_ctrl=stand, qpos_init=qpos)
+
+
+MODELS = {"cartpole": cartpole, "quadruped": quadruped}
+
+
+def model(name: str) -> Model:
+    return MODELS[name]()
+
+
+# --------------------------------------------------------------------------------------
+# seeded initial states and actions
+# --------------------------------------------------------------------------------------
+
+def initial_state(m: Model, config: int, n_envs: int, env0: int = 0, noise: Optional[float] = None):
+    """qpos [N, nq], qvel [N, nv] float32.  Draws 0 .. nq+nv-1 of each env's stream.
+    noise=None uses the workload's recipe: cartpole U(+-0.1) on qpos and qvel, the others
+    start at rest in the reference configuration."""
+    seeds = env_seeds(config, n_envs, env0)[:, None]
+    nq, nv = m.nq, m.nv
+    q0 = np.zeros(nq) if m.qpos_init is None else m.qpos_init.astype(np.float64)
+    if noise is None:
+        noise = 0.1 if m.name == "cartpole" else 0.0
+    u = uniform01(seeds, np.arange(nq + nv, dtype=np.uint64)[None, :])
+    qpos = q0[None, :] + noise * (2.0 * u[:, :nq] - 1.0)
+    qvel = noise * (2.0 * u[:, nq:] - 1.0)
+    return _f32(qpos), _f32(qvel)
+
+
+def actions(m: Model, config: int, n_envs: int, t0: int, n_steps: int, env0: int = 0,
+            amplitude: float = 0.3) -> np.ndarray:
+    """Controls [n_steps, N, nu] float32 for control steps t0 .. t0+n_steps-1.
+    Draw index of (t, j) is nq + nv + t*nu + j.  Cartpole: U[-1, 1].  Position-actuated
+    models: default_ctrl + U(+-amplitude) when default_ctrl is set, else U(ctrlrange)."""
+    seeds = env_seeds(config, n_envs, env0)[None, :, None]
+    nu, base = m.nu, m.nq + m.nv
+    t = np.arange(t0, t0 + n_steps, dtype=np.uint64)[:, None, None]
+    j = np.arange(nu, dtype=np.uint64)[None, None, :]
+    u = uniform01(seeds, np.uint64(base) + t * np.uint64(nu) + j)
+    if m.default_ctrl is not None:
+        out = m.default_ctrl.astype(np.float64)[None, None, :] + amplitude * (2.0 * u - 1.0)
+    else:
+        lo = m.act_ctrlrange[:, 0].astype(np.float64)
+        hi = m.act_ctrlrange[:, 1].astype(np.float64)
+        out = lo + (hi - lo) * u
+    return _f32(out)

@@ -1,0 +1,87 @@
+"""Small hand-built models used only by the tests (inputs; no physics arithmetic)."""
+from __future__ import annotations
+
+import math
+
+from paper_2502_08844_b300 import workloads as W
+
+
+def planar_chain(n_links=3, length=0.5, mass=1.0, radius=0.02, gravity=(0, 0, -9.81), damping=0.0,
+                 timestep=0.001, limited=False):
+    """n hinge links about y, each a capsule of `length` hanging along -z from its hinge."""
+    b = W.ModelBuilder("chain%d" % n_links)
+    parent, pos = 0, (0, 0, 0)
+    for i in range(n_links):
+        body = b.body(parent, pos)
+        b.joint(body, W.HINGE, axis=(0, 1, 0), damping=damping, limited=limited, range=(-1.0, 1.0))
+        b.geom(body, W.CAPSULE, (radius, length / 2), pos=(0, 0, -length / 2), mass=mass)
+        parent, pos = body, (0, 0, -length)
+    return b.build(timestep=timestep, gravity=gravity)
+
+
+def free_body(gravity=(0, 0, -9.81), timestep=0.01, inertia=None, mass=2.0, z0=1.0, geom=True):
+    """One free body; with inertia=(xx,yy,zz,xy,xz,yz) the mass properties are explicit (COM at the origin)."""
+    b = W.ModelBuilder("free_body")
+    if inertia is None:
+        body = b.body(0, (0, 0, z0))
+        b.geom(body, W.BOX, (0.1, 0.2, 0.3), mass=mass)
+    else:
+        body = b.body(0, (0, 0, z0), mass=mass, inertia=inertia, geom_inertia=False)
+    b.joint(body, W.FREE)
+    return b.build(timestep=timestep, gravity=gravity)
+
+
+def sphere_on_plane(mass=1.0, radius=0.1, friction=0.0, condim=1, timestep=0.002, z0=None, iterations=50):
+    b = W.ModelBuilder("sphere_on_plane")
+    floor = b.geom(0, W.PLANE, (0, 0, 0))
+    body = b.body(0, (0, 0, radius if z0 is None else z0))
+    b.joint(body, W.FREE)
+    s = b.geom(body, W.SPHERE, (radius,), mass=mass)
+    b.pair(floor, s, friction=friction, condim=condim)
+    return b.build(timestep=timestep, iterations=iterations)
+
+
+def pendulum(length=1.0, mass=1.0, radius=0.02, timestep=0.001):
+    """A single capsule on a hinge about y (compound pendulum)."""
+    b = W.ModelBuilder("pendulum")
+    body = b.body(0, (0, 0, 0))
+    b.joint(body, W.HINGE, axis=(0, 1, 0))
+    b.geom(body, W.CAPSULE, (radius, length / 2), pos=(0, 0, -length / 2), mass=mass)
+    return b.build(timestep=timestep)
+
+
+def quadruped_zero_gravity(timestep=0.004):
+    m = W.quadruped()
+    m.gravity[:] = 0.0
+    m.pair_geom = m.pair_geom[:0]
+    m.pair_friction = m.pair_friction[:0]
+    m.pair_condim = m.pair_condim[:0]
+    m.jnt_limited[:] = 0
+    m.timestep = timestep
+    m.max_contacts = 0
+    return m
+
+
+def arm_with_slider(gravity=(0, 0, 0), timestep=0.001):
+    """Hinge (y) arm carrying a slider along the arm's x axis and a second hinge at the slider:
+    exercises slide joints on rotating frames."""
+    b = W.ModelBuilder("arm_slider")
+    arm = b.body(0, (0, 0, 0))
+    b.joint(arm, W.HINGE, axis=(0, 1, 0))
+    b.geom(arm, W.CAPSULE, (0.02, 0.2), pos=(0.2, 0, 0), quat=(0.7071068, 0, 0.7071068, 0), mass=0.5)
+    slider = b.body(arm, (0.1, 0, 0))
+    b.joint(slider, W.SLIDE, axis=(1, 0, 0))
+    b.geom(slider, W.BOX, (0.05, 0.04, 0.03), pos=(0.02, 0.01, 0.0), mass=0.8)
+    tip = b.body(slider, (0.05, 0, 0.02))
+    b.joint(tip, W.HINGE, axis=(0, 0.6, 0.8))
+    b.geom(tip, W.CAPSULE, (0.02, 0.1), pos=(0, 0, -0.1), mass=0.3)
+    return b.build(timestep=timestep, gravity=gravity)
+
+
+def quadruped_passive(timestep=0.004, gravity=(0, 0, 0)):
+    """The quadruped without actuation, limits or contacts (a free-floating passive tree)."""
+    m = quadruped_zero_gravity(timestep)
+    m.gravity[:] = gravity
+    m.act_kp[:] = 0.0
+    m.act_kd[:] = 0.0
+    return m
