@@ -1,0 +1,305 @@
+"""Benchmark of the batched physics step on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload quadruped|cartpole]
+
+One bench step = one control step (n_substeps physics substeps: FK, CRBA, LDL^T, RNEA,
+collision, Jacobians, Newton solve, PD actuation, semi-implicit Euler) of every environment.
+Default workload: 8192 synthetic quadrupeds, 5 substeps of 4 ms, Newton cap 4, control
+targets standing pose + U(+-0.3) rad per step, K = 1000 control steps.  Prints one JSON line.
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on the launching
+stream; L2 is flushed (a 256 MB write) between timed steps outside the events; barrier +
+synchronize around the timed region; max over ranks.  Under torchrun every rank runs its own
+independent replica (envs are independent: weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2502_08844_b300 import workloads as W  # noqa: E402
+from paper_2502_08844_b300 import flops as FL  # noqa: E402
+
+METRIC = "env-steps/s on 1 B300 (quadruped, 8192 envs), % roofline; adjoint/forward time"
+CONFIG_OF = {"quadruped": (1, 8192), "cartpole": (0, 256)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % index)
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_traffic(workload: str):
+    """DRAM bytes per launch from a committed ncu summary, valid only for the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    src = os.path.join(ROOT, "paper_2502_08844_b300", "csrc", "step.cu")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    ent = d.get(workload)
+    if not ent or ent.get("step_cu_sha256_16") != h:
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def cpu_baseline(model: W.Model, cfg: int, n_envs: int, budget_s: float = 10.0, chunk: int = 10):
+    """The FP64 oracle on the host cores, on a bounded sample of the workload."""
+    from oracle import oracle as O
+    cores = os.cpu_count() or 1
+    om = O.OracleModel(model)
+    n = min(n_envs, max(cores * 16, 64))
+    q, v = W.initial_state(model, cfg, n)
+    warm = None
+    steps, t0 = 0, time.time()
+    q = q.astype(np.float64); v = v.astype(np.float64)
+    while True:
+        U = W.actions(model, cfg, n, steps, chunk)
+        q, v, warm, _ = om.rollout(q, v, U, model.n_substeps, qacc_warm=warm, nthreads=cores)
+        steps += chunk
+        if time.time() - t0 >= budget_s:
+            break
+    dt = time.time() - t0
+    return {"value": n * steps / dt, "unit": "env-steps/s", "cores": cores, "kind": "oracle",
+            "sample": "%d envs x %d control steps (%d substeps each) of the %s workload, FP64, %d threads" % (
+                n, steps, model.n_substeps, model.name, cores)}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle as it stands, timed on the host cores."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    cfg, n_total = CONFIG_OF[args.workload]
+    m = W.model(args.workload)
+    from oracle import oracle as O
+    cores = os.cpu_count() or 1
+    om = O.OracleModel(m)
+    n = min(n_total, max(cores * 4, 32))
+    q, v = W.initial_state(m, cfg, n)
+    q = q.astype(np.float64); v = v.astype(np.float64)
+    warm = None
+    for t in range(args.warmup):
+        q, v, warm, _ = om.rollout(q, v, W.actions(m, cfg, n, t, 1), m.n_substeps, qacc_warm=warm, nthreads=cores)
+    t0 = time.time()
+    for t in range(args.steps):
+        q, v, warm, _ = om.rollout(q, v, W.actions(m, cfg, n, args.warmup + t, 1), m.n_substeps, qacc_warm=warm,
+                                   nthreads=cores)
+    dt = time.time() - t0
+    val = n * args.steps / dt
+    line = {"metric": METRIC, "value": val, "unit": "env-steps/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "%s-%d" % (args.workload, n_total), "sample_envs_per_step": n,
+                       "substeps": m.n_substeps, "newton_cap": m.iterations},
+            "impl": "reference",
+            "cpu_baseline": {"value": val, "unit": "env-steps/s", "cores": cores, "kind": "oracle",
+                             "sample": "%d envs per step, FP64 oracle, %d threads" % (n, cores)},
+            "e2e": {"value": val, "unit": "env-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2502_08844_b300 import core
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg, n = CONFIG_OF[args.workload]
+    m = W.model(args.workload)
+    cm = core.CompiledModel(m)
+    batch = core.Batch([(cm, n)], envs_per_cta=args.envs_per_cta)
+    state = core.State(batch, dev)
+    env0 = rank * n
+    q0, v0 = W.initial_state(m, cfg, n, env0)
+    ld = state.ld
+    state.qpos.copy_(torch.from_numpy(core.to_soa(q0, ld, batch.nq_max)))
+    state.qvel.copy_(torch.from_numpy(core.to_soa(v0, ld, batch.nv_max)))
+    T = args.warmup + args.steps
+    U = W.actions(m, cfg, n, 0, T, env0)                                # [T, n, nu]
+    Usoa = np.zeros((T, max(batch.nu_max, 1), ld), np.float32)
+    Usoa[:, :m.nu, :n] = U.transpose(0, 2, 1)
+    ctrl = torch.from_numpy(Usoa).to(dev)
+    stream = torch.cuda.current_stream()
+    for t in range(args.warmup):
+        core.step(batch, state, ctrl[t], m.n_substeps)
+    torch.cuda.synchronize()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stats = state.enable_stats()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.time()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        core.step(batch, state, ctrl[args.warmup + k], m.n_substeps)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    wall = time.time() - wall0
+    ck = clocks.stop()
+    times = [a.elapsed_time(b) for a, b in ev]          # ms per launch
+    dev_s = sum(times) / 1e3
+    st = stats[:, :n].to(torch.int64).sum(dim=1).cpu().numpy()
+    status = state.status.cpu().numpy().view(np.uint32)
+    if ws > 1:
+        t = torch.tensor([dev_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_s = float(t.item())
+    value = ws * n * args.steps / dev_s
+    # roofline: algorithmic FP32 flops per launch / mean launch time, against the CUDA-core peak
+    fm = FL.flop_model(m)
+    flops_total = fm.substeps(n * m.n_substeps * args.steps, st[1], st[0], st[2])
+    flops_launch = flops_total / args.steps
+    mean_launch = statistics.mean(times) / 1e3
+    peaks, src = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
+    peak = FL.fp32_peak_tflops(props.multi_processor_count, sm_mhz)
+    achieved = flops_launch / mean_launch / 1e12
+    bytes_launch = n * 4 * (2 * (m.nq + 2 * m.nv) + m.nu)
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": kernel_traffic(args.workload),
+            "peak_source": "%d SMs x 128 FP32 lanes x 2 x sm_max_mhz %.0f (%s)" % (props.multi_processor_count, sm_mhz, src),
+            "flops_per_launch": flops_launch, "algorithmic_bytes_per_launch": bytes_launch,
+            "hbm_frac": bytes_launch / mean_launch / 1e9 / float(peaks.get("hbm_gbs", 6400.0)),
+            "newton_iters_per_substep": float(st[0]) / (n * m.n_substeps * args.steps),
+            "rows_per_substep": float(st[1]) / (n * m.n_substeps * args.steps)}
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        Ke = min(args.steps, 200)
+        ctrl_h = torch.from_numpy(Usoa[args.warmup:args.warmup + Ke]).pin_memory()
+        qh = torch.empty((batch.nq_max, ld), dtype=torch.float32).pin_memory()
+        vh = torch.empty((batch.nv_max, ld), dtype=torch.float32).pin_memory()
+        state.stats = None
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(Ke):
+            core.step_host(batch, state, ctrl_h[k], qh, vh, m.n_substeps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_e2e = e0.elapsed_time(e1) / 1e3
+        e2e = {"value": ws * n * Ke / t_e2e, "unit": "env-steps/s", "steps": Ke,
+               "h2d_bytes_per_step": int(batch.nu_max * ld * 4),
+               "d2h_bytes_per_step": int((batch.nq_max + batch.nv_max) * ld * 4)}
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "%s-%d" % (args.workload, n), "n_envs_per_gpu": n, "substeps": m.n_substeps,
+                       "dt": m.timestep, "newton_cap": m.iterations, "cone": "pyramidal",
+                       "envs_per_cta": args.envs_per_cta or "default",
+                       "l2": "flushed between timed steps (256 MB write outside the events)",
+                       "wall_s_timed_region": wall},
+            "roofline": roof, "e2e": e2e, "gpu_launches": args.steps,
+            "clocks": ck, "status_bits_seen": int(np.bitwise_or.reduce(status)) if status.size else 0,
+            "adjoint_forward_ratio": None}
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(m, cfg, n)
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(CONFIG_OF), default="quadruped")
+    ap.add_argument("--envs-per-cta", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

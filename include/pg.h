@@ -1,0 +1,169 @@
+/*
+ * pg.h -- C ABI of the B300-native batched physics step.
+ *
+ * The library advances thousands of independent copies of articulated rigid-body models
+ * ("environments") by one control step per call, entirely on the GPU: forward kinematics,
+ * composite-rigid-body mass matrix with a tree-sparse LDL^T factorisation, recursive
+ * Newton-Euler bias forces, primitive-geom collision, contact/limit Jacobians, a per-env
+ * convex soft-contact Newton solve with an exact line search and a fixed iteration cap,
+ * PD / motor actuation and semi-implicit Euler.  This is the physics step under the
+ * training loop of MuJoCo Playground (arXiv 2502.08844): its environments run the MJX
+ * physics step on thousands of envs on one device (Sec. 1), with static pair lists whose
+ * cost follows the number of possible contacts (Limitations), per-task solver caps
+ * ("iterations", Table dm_control_envs), PD position control (eq. pd_mapping, App. B.2.1),
+ * reflected rotor inertia (App. C.2.2) and physics substeps per control decision
+ * (App. "Bottlenecks in Pixels-based Training": 10 substeps of 5 ms per 20 Hz decision).
+ *
+ * Conventions
+ *   - Every function returns PG_OK (0) or a negative status; pg_last_error() then gives a
+ *     human-readable reason (thread-local, valid until the next call on the same thread).
+ *   - Argument errors are detected synchronously, before any work is queued.  Numerical
+ *     trouble inside an environment never traps: it sets bits of that env's status word.
+ *   - Device work is queued on the caller's stream and is asynchronous.
+ *   - Ownership: the caller owns every state, control, output and gradient buffer (for
+ *     example torch tensors); the library owns models, batches and their device copies,
+ *     all allocated at compile time.  pg_step allocates nothing.
+ *   - Batch state is structure-of-arrays: coordinate-major [coord][ld] float32 device
+ *     arrays, env e of coordinate c at c*ld + e, with n <= ld (ld is the row pitch in
+ *     elements).  In a mixed batch every array has max-over-models rows.
+ */
+#ifndef PG_H_
+#define PG_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ----------------------------------------------------------------- */
+#define PG_OK 0
+#define PG_EINVAL (-1)        /* bad argument, bad array, level order violated          */
+#define PG_ENOMEM (-2)        /* device or host allocation failed                       */
+#define PG_ECUDA (-3)         /* a CUDA runtime call failed                             */
+#define PG_EUNSUPPORTED (-4)  /* pair type, cone type or size beyond the kernel limits   */
+#define PG_ECAPACITY (-5)     /* too many bodies/dofs/rows for the compiled kernels      */
+
+/* ---- per-environment status bits (OR-accumulated until pg_reset) ------------------ */
+#define PG_STATUS_NAN 1u            /* non-finite qacc / qvel / qpos                     */
+#define PG_STATUS_NOT_CONVERGED 2u  /* Newton reached its cap before exact termination   */
+#define PG_STATUS_CAPACITY 4u       /* more active contacts than max_contacts (extra     */
+                                    /* contacts dropped in slot order)                   */
+#define PG_STATUS_WARM_RESET 8u     /* non-finite warm start replaced by the smooth acc. */
+
+/* ---- type codes ------------------------------------------------------------------- */
+enum { PG_JNT_FREE = 0, PG_JNT_HINGE = 1, PG_JNT_SLIDE = 2 };
+enum { PG_GEOM_PLANE = 0, PG_GEOM_SPHERE = 1, PG_GEOM_CAPSULE = 2, PG_GEOM_BOX = 3 };
+enum { PG_ACT_MOTOR = 0, PG_ACT_POSITION = 1 };
+enum { PG_CONE_PYRAMIDAL = 0, PG_CONE_ELLIPTIC = 1 };
+
+/*
+ * Model description: flat kinematic-tree arrays in level order (host memory, caller-owned,
+ * read only during pg_model_compile).  Body 0 is the world; parent[i] < i.  Joints are
+ * grouped by body in body order; a free joint is the only joint of a child of the world.
+ * Lengths: nbody, njnt, ngeom, npair, nu, and nv = sum of dofs (free 6, hinge/slide 1).
+ *   body_pos[3], body_quat[4]     frame of the body in its parent at q = 0, quat (w,x,y,z)
+ *   body_mass, body_ipos[3], body_inertia[6] (xx,yy,zz,xy,xz,yz about the COM, body axes),
+ *   body_geom_inertia              1: derive mass, COM and inertia from the body's geoms as
+ *                                  uniform solids of geom_mass (box: 2*size edges; capsule:
+ *                                  radius size[0], cylinder half-length size[1] along z)
+ *   jnt_pos[3], jnt_axis[3]        anchor and axis in the body frame; jnt_range[2] (lo < hi)
+ *   dof_rotor[3]                   (gear ratio k_g, rotor mass m_r, radius r_r): armature
+ *                                  k_g^2 m_r r_r^2 / 2 is added to dof_armature (App. C.2.2)
+ *   pair_geom[2]                   candidate pair (geom1, geom2), type(geom1) <= type(geom2)
+ *                                  in plane < sphere < capsule < box; the normal points from
+ *                                  geom1 to geom2.  Static list: no broadphase.
+ *   pair_condim                    1 (frictionless) or 3 (pyramidal cone, 4 edge rows)
+ *   act_jnt                        hinge or slide joint driven by the actuator
+ *   solref = (timeconst, dampratio); solimp = (d0, dwidth, width, mid, power)
+ *   iterations                     Newton iteration cap (>= 1); max_contacts: cap on active
+ *                                  contacts per env (< 0: number of candidate slots)
+ */
+typedef struct pg_model_desc {
+  int nbody, njnt, ngeom, npair, nu;
+  const int* body_parent; const float* body_pos; const float* body_quat; const float* body_mass;
+  const float* body_ipos; const float* body_inertia; const int* body_geom_inertia;
+  const int* jnt_type; const int* jnt_body; const float* jnt_pos; const float* jnt_axis;
+  const int* jnt_limited; const float* jnt_range;
+  const float* dof_damping; const float* dof_armature; const float* dof_rotor;
+  const int* geom_type; const int* geom_body; const float* geom_pos; const float* geom_quat;
+  const float* geom_size; const float* geom_mass;
+  const int* pair_geom; const float* pair_friction; const int* pair_condim;
+  const int* act_type; const int* act_jnt; const float* act_gear; const float* act_kp; const float* act_kd;
+  const int* act_ctrllimited; const float* act_ctrlrange;
+  float timestep; const float* gravity; int iterations; int cone; float impratio;
+  const float* solref; const float* solimp; float margin; int max_contacts;
+} pg_model_desc;
+
+typedef struct pg_model pg_model;   /* opaque, library-owned */
+typedef struct pg_batch pg_batch;   /* opaque, library-owned */
+
+typedef struct pg_model_sizes {
+  int nq, nv, nu, nbody, njnt, ngeom, npair;
+  int nslot;          /* candidate contact slots (sum over pairs of the pair's max points) */
+  int nrow_max;       /* max constraint rows per env (4 per contact + 1 per limited joint) */
+  int max_contacts;
+  int workspace_bytes;  /* per-env shared-memory workspace of the step kernel            */
+  int debug_floats;     /* length of the record written by pg_debug_substep              */
+} pg_model_sizes;
+
+/* Caller-owned batch state (device pointers, [coord][ld] float32; status [n] uint32). */
+typedef struct pg_state {
+  float* qpos;        /* [nq_max][ld] */
+  float* qvel;        /* [nv_max][ld] */
+  float* qacc_warm;   /* [nv_max][ld]; warm start of the Newton solve, zeroed by pg_reset */
+  uint32_t* status;   /* [n] status bits                                                   */
+  int64_t n;          /* number of environments                                            */
+  int64_t ld;         /* row pitch in elements (>= n)                                      */
+  uint32_t* stats;    /* optional [3][ld] solver counters, NULL = off: per env and substep
+                         += Newton iterations, += constraint rows, += rows * iterations      */
+} pg_state;
+
+/* Validate a description and build the library's model (host tables and a device copy).
+ * Errors: PG_EINVAL (malformed tree or arrays), PG_EUNSUPPORTED (pair/cone type),
+ * PG_ECAPACITY (beyond the kernel's compiled limits: nv <= 64, nbody <= 64, slots <= 64,
+ * rows <= 128), PG_ECUDA / PG_ENOMEM. */
+int pg_model_compile(const pg_model_desc* desc, pg_model** out);
+int pg_model_info(const pg_model* model, pg_model_sizes* out);
+void pg_model_free(pg_model* model);
+
+/* Batch of environments: counts[k] consecutive envs of models[k], in that order.  The
+ * models must outlive the batch.  envs_per_cta (>= 1, or 0 for the default) sets how many
+ * environments (one warp each) share a thread block. */
+int pg_batch_compile(const pg_model* const* models, const int64_t* counts, int nmodels, int envs_per_cta,
+                     pg_batch** out);
+int pg_batch_info(const pg_batch* batch, int64_t* n_envs, int* nq_max, int* nv_max, int* nu_max);
+void pg_batch_free(pg_batch* batch);
+
+/* Reset the envs whose env_mask_dev[e] != 0 (all envs when env_mask_dev is NULL): copy
+ * qpos0/qvel0 ([coord][ld], same layout as the state), zero qacc_warm and status. */
+int pg_reset(const pg_batch* batch, pg_state* state, const uint8_t* env_mask_dev, const float* qpos0_dev,
+             const float* qvel0_dev, void* stream);
+
+/* One control step: n_substeps physics substeps with the controls ctrl_dev ([nu_max][ld])
+ * held (zero-order hold).  Advances qpos, qvel, qacc_warm and ORs status bits in place. */
+int pg_step(const pg_batch* batch, pg_state* state, const float* ctrl_dev, int n_substeps, void* stream);
+
+/* Diagnostics: one substep of environment `env` only (the others are untouched), writing
+ * every intermediate to out_dev (debug_floats floats, device memory) in this order:
+ * xpos[nbody][3] xmat[nbody][9] xcom[nbody][3] M[nv][nv] bias[nv] passive[nv] actuator[nv]
+ * a0[nv] contacts[nslot][14] (active, dist, pos3, n3, t1 3, t2 3) nrow rows[nrow_max][nv+7]
+ * (J[nv], r, v, aref, D, Ahat, imp, force) qacc[nv] iterations status qpos_next[nq]
+ * qvel_next[nv].  The env's state is advanced as by one substep of pg_step. */
+int pg_debug_substep(const pg_batch* batch, pg_state* state, const float* ctrl_dev, int64_t env, float* out_dev,
+                     void* stream);
+
+/* Host-buffer convenience path: copy ctrl_host ([nu_max][ld] floats, pinned recommended)
+ * to a library-owned device buffer, run pg_step, copy qpos/qvel back to qpos_host/qvel_host
+ * ([coord][ld]).  Returns after queuing; synchronise the stream before reading the host
+ * outputs. */
+int pg_step_host(pg_batch* batch, pg_state* state, const float* ctrl_host, float* qpos_host, float* qvel_host,
+                 int n_substeps, void* stream);
+
+const char* pg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PG_H_ */

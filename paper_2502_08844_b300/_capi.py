@@ -1,0 +1,143 @@
+"""ctypes binding of the C ABI in include/pg.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls.  The shared library is the
+in-tree `libpg.so`; importing this module fails loudly when it is missing (there is no
+fallback implementation of the step).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpg.so")
+
+PG_OK, PG_EINVAL, PG_ENOMEM, PG_ECUDA, PG_EUNSUPPORTED, PG_ECAPACITY = 0, -1, -2, -3, -4, -5
+PG_STATUS_NAN, PG_STATUS_NOT_CONVERGED, PG_STATUS_CAPACITY, PG_STATUS_WARM_RESET = 1, 2, 4, 8
+
+_fp = C.POINTER(C.c_float)
+_ip = C.POINTER(C.c_int)
+
+
+class pg_model_desc(C.Structure):
+    _fields_ = [
+        ("nbody", C.c_int), ("njnt", C.c_int), ("ngeom", C.c_int), ("npair", C.c_int), ("nu", C.c_int),
+        ("body_parent", _ip), ("body_pos", _fp), ("body_quat", _fp), ("body_mass", _fp),
+        ("body_ipos", _fp), ("body_inertia", _fp), ("body_geom_inertia", _ip),
+        ("jnt_type", _ip), ("jnt_body", _ip), ("jnt_pos", _fp), ("jnt_axis", _fp),
+        ("jnt_limited", _ip), ("jnt_range", _fp),
+        ("dof_damping", _fp), ("dof_armature", _fp), ("dof_rotor", _fp),
+        ("geom_type", _ip), ("geom_body", _ip), ("geom_pos", _fp), ("geom_quat", _fp),
+        ("geom_size", _fp), ("geom_mass", _fp),
+        ("pair_geom", _ip), ("pair_friction", _fp), ("pair_condim", _ip),
+        ("act_type", _ip), ("act_jnt", _ip), ("act_gear", _fp), ("act_kp", _fp), ("act_kd", _fp),
+        ("act_ctrllimited", _ip), ("act_ctrlrange", _fp),
+        ("timestep", C.c_float), ("gravity", _fp), ("iterations", C.c_int), ("cone", C.c_int),
+        ("impratio", C.c_float), ("solref", _fp), ("solimp", _fp), ("margin", C.c_float),
+        ("max_contacts", C.c_int),
+    ]
+
+
+class pg_model_sizes(C.Structure):
+    _fields_ = [(n, C.c_int) for n in ("nq", "nv", "nu", "nbody", "njnt", "ngeom", "npair", "nslot", "nrow_max",
+                                        "max_contacts", "workspace_bytes", "debug_floats")]
+
+
+class pg_state(C.Structure):
+    _fields_ = [("qpos", C.c_void_p), ("qvel", C.c_void_p), ("qacc_warm", C.c_void_p), ("status", C.c_void_p),
+                ("n", C.c_int64), ("ld", C.c_int64), ("stats", C.c_void_p)]
+
+
+EXPORTS = ["pg_model_compile", "pg_model_info", "pg_model_free", "pg_batch_compile", "pg_batch_info",
+           "pg_batch_free", "pg_reset", "pg_step", "pg_debug_substep", "pg_step_host", "pg_last_error"]
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libpg.so is not built (run `python -m paper_2502_08844_b300.build` or "
+                      "__graft_entry__.build()); there is no fallback implementation of the step")
+
+_lib = C.CDLL(LIB_PATH)
+
+_lib.pg_last_error.restype = C.c_char_p
+_lib.pg_last_error.argtypes = []
+_lib.pg_model_compile.argtypes = [C.POINTER(pg_model_desc), C.POINTER(C.c_void_p)]
+_lib.pg_model_info.argtypes = [C.c_void_p, C.POINTER(pg_model_sizes)]
+_lib.pg_model_free.argtypes = [C.c_void_p]
+_lib.pg_model_free.restype = None
+_lib.pg_batch_compile.argtypes = [C.POINTER(C.c_void_p), C.POINTER(C.c_int64), C.c_int, C.c_int, C.POINTER(C.c_void_p)]
+_lib.pg_batch_info.argtypes = [C.c_void_p, C.POINTER(C.c_int64), _ip, _ip, _ip]
+_lib.pg_batch_free.argtypes = [C.c_void_p]
+_lib.pg_batch_free.restype = None
+_lib.pg_reset.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+_lib.pg_step.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_int, C.c_void_p]
+_lib.pg_debug_substep.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
+_lib.pg_step_host.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
+for _n in EXPORTS:
+    if _n not in ("pg_last_error", "pg_model_free", "pg_batch_free"):
+        getattr(_lib, _n).restype = C.c_int
+
+
+class PgError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__("%s failed (%d): %s" % (where, code, pg_last_error()))
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != PG_OK:
+        raise PgError(rc, where)
+
+
+def pg_last_error() -> str:
+    s = _lib.pg_last_error()
+    return s.decode() if s else ""
+
+
+def pg_model_compile(desc: pg_model_desc) -> C.c_void_p:
+    out = C.c_void_p()
+    _check(_lib.pg_model_compile(C.byref(desc), C.byref(out)), "pg_model_compile")
+    return out
+
+
+def pg_model_info(model) -> pg_model_sizes:
+    s = pg_model_sizes()
+    _check(_lib.pg_model_info(model, C.byref(s)), "pg_model_info")
+    return s
+
+
+def pg_model_free(model) -> None:
+    _lib.pg_model_free(model)
+
+
+def pg_batch_compile(models, counts, envs_per_cta: int = 0) -> C.c_void_p:
+    arr = (C.c_void_p * len(models))(*[m.value for m in models])
+    cnt = (C.c_int64 * len(counts))(*counts)
+    out = C.c_void_p()
+    _check(_lib.pg_batch_compile(arr, cnt, len(models), int(envs_per_cta), C.byref(out)), "pg_batch_compile")
+    return out
+
+
+def pg_batch_info(batch):
+    n = C.c_int64(); nq = C.c_int(); nv = C.c_int(); nu = C.c_int()
+    _check(_lib.pg_batch_info(batch, C.byref(n), C.byref(nq), C.byref(nv), C.byref(nu)), "pg_batch_info")
+    return n.value, nq.value, nv.value, nu.value
+
+
+def pg_batch_free(batch) -> None:
+    _lib.pg_batch_free(batch)
+
+
+def pg_reset(batch, state: pg_state, env_mask_ptr, qpos0_ptr, qvel0_ptr, stream) -> None:
+    _check(_lib.pg_reset(batch, C.byref(state), env_mask_ptr, qpos0_ptr, qvel0_ptr, stream), "pg_reset")
+
+
+def pg_step(batch, state: pg_state, ctrl_ptr, n_substeps: int, stream) -> None:
+    _check(_lib.pg_step(batch, C.byref(state), ctrl_ptr, int(n_substeps), stream), "pg_step")
+
+
+def pg_debug_substep(batch, state: pg_state, ctrl_ptr, env: int, out_ptr, stream) -> None:
+    _check(_lib.pg_debug_substep(batch, C.byref(state), ctrl_ptr, int(env), out_ptr, stream), "pg_debug_substep")
+
+
+def pg_step_host(batch, state: pg_state, ctrl_host_ptr, qpos_host_ptr, qvel_host_ptr, n_substeps: int, stream) -> None:
+    _check(_lib.pg_step_host(batch, C.byref(state), ctrl_host_ptr, qpos_host_ptr, qvel_host_ptr, int(n_substeps), stream),
+           "pg_step_host")

@@ -1,0 +1,174 @@
+"""Torch-facing wrapper of the C ABI: compiled models, batches, batch state and the step.
+
+PyTorch only provides device memory and streams here; every step of the physics runs in
+the CUDA library (`libpg.so`) behind `_capi`.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+import torch
+
+from . import _capi
+from . import workloads as W
+
+_fp = C.POINTER(C.c_float)
+_ip = C.POINTER(C.c_int)
+
+
+def _stream_ptr(stream: Optional[torch.cuda.Stream]):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+class CompiledModel:
+    """A model compiled by pg_model_compile from a workloads.Model description."""
+
+    def __init__(self, m: W.Model):
+        self.src = m
+        keep = []
+
+        def f(a):
+            a = np.ascontiguousarray(np.asarray(a, np.float32))
+            keep.append(a)
+            return a.ctypes.data_as(_fp)
+
+        def i(a):
+            a = np.ascontiguousarray(np.asarray(a, np.int32))
+            keep.append(a)
+            return a.ctypes.data_as(_ip)
+
+        pair_geom = m.pair_geom if m.npair else np.zeros((0, 2), np.int32)
+        d = _capi.pg_model_desc(
+            m.nbody, m.njnt, m.ngeom, m.npair, m.nu,
+            i(m.body_parent), f(m.body_pos), f(m.body_quat), f(m.body_mass), f(m.body_ipos), f(m.body_inertia),
+            i(m.body_geom_inertia), i(m.jnt_type), i(m.jnt_body), f(m.jnt_pos), f(m.jnt_axis), i(m.jnt_limited),
+            f(m.jnt_range), f(m.dof_damping), f(m.dof_armature), f(m.dof_rotor), i(m.geom_type), i(m.geom_body),
+            f(m.geom_pos), f(m.geom_quat), f(m.geom_size), f(m.geom_mass), i(pair_geom), f(m.pair_friction),
+            i(m.pair_condim), i(m.act_type), i(m.act_jnt), f(m.act_gear), f(m.act_kp), f(m.act_kd),
+            i(m.act_ctrllimited), f(m.act_ctrlrange), float(m.timestep), f(m.gravity), int(m.iterations),
+            int(m.cone), float(m.impratio), f(m.solref), f(m.solimp), float(m.margin), int(m.max_contacts))
+        self.handle = _capi.pg_model_compile(d)
+        self.sizes = _capi.pg_model_info(self.handle)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            _capi.pg_model_free(h)
+            self.handle = None
+
+    @property
+    def nq(self):
+        return self.sizes.nq
+
+    @property
+    def nv(self):
+        return self.sizes.nv
+
+    @property
+    def nu(self):
+        return self.sizes.nu
+
+
+class Batch:
+    """counts[k] consecutive environments of models[k], stepped in one launch."""
+
+    def __init__(self, parts: Sequence[Tuple[CompiledModel, int]], envs_per_cta: int = 0):
+        self.models = [m for m, _ in parts]
+        self.counts = [int(c) for _, c in parts]
+        self.handle = _capi.pg_batch_compile([m.handle for m in self.models], self.counts, envs_per_cta)
+        self.n, self.nq_max, self.nv_max, self.nu_max = _capi.pg_batch_info(self.handle)
+        self.env_off = list(np.cumsum([0] + self.counts[:-1]))
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            _capi.pg_batch_free(h)
+            self.handle = None
+
+
+class State:
+    """Batch state in device memory: [coord][ld] float32 arrays, status [n] (uint32 bits)."""
+
+    def __init__(self, batch: Batch, device="cuda"):
+        self.n = batch.n
+        self.ld = max(4, (batch.n + 3) // 4 * 4)
+        self.qpos = torch.zeros((batch.nq_max, self.ld), dtype=torch.float32, device=device)
+        self.qvel = torch.zeros((batch.nv_max, self.ld), dtype=torch.float32, device=device)
+        self.qacc_warm = torch.zeros((batch.nv_max, self.ld), dtype=torch.float32, device=device)
+        self.status = torch.zeros((self.n,), dtype=torch.int32, device=device)
+        self.stats = None   # optional [3, ld] int32 solver counters (enable_stats)
+
+    def enable_stats(self):
+        self.stats = torch.zeros((3, self.ld), dtype=torch.int32, device=self.qpos.device)
+        return self.stats
+
+    def c(self) -> _capi.pg_state:
+        return _capi.pg_state(self.qpos.data_ptr(), self.qvel.data_ptr(), self.qacc_warm.data_ptr(),
+                              self.status.data_ptr(), self.n, self.ld,
+                              None if self.stats is None else self.stats.data_ptr())
+
+
+def reset(batch: Batch, state: State, qpos0: torch.Tensor, qvel0: torch.Tensor, mask: Optional[torch.Tensor] = None,
+          stream=None) -> None:
+    assert qpos0.shape == state.qpos.shape and qvel0.shape == state.qvel.shape
+    _capi.pg_reset(batch.handle, state.c(), _ptr(mask), _ptr(qpos0.contiguous()), _ptr(qvel0.contiguous()),
+                   _stream_ptr(stream))
+
+
+def step(batch: Batch, state: State, ctrl: torch.Tensor, n_substeps: int, stream=None) -> None:
+    assert ctrl.dtype == torch.float32 and ctrl.is_contiguous() and ctrl.shape[-1] == state.ld
+    _capi.pg_step(batch.handle, state.c(), _ptr(ctrl), int(n_substeps), _stream_ptr(stream))
+
+
+def step_host(batch: Batch, state: State, ctrl_host: torch.Tensor, qpos_host: torch.Tensor, qvel_host: torch.Tensor,
+              n_substeps: int, stream=None) -> None:
+    _capi.pg_step_host(batch.handle, state.c(), _ptr(ctrl_host), _ptr(qpos_host), _ptr(qvel_host), int(n_substeps),
+                       _stream_ptr(stream))
+
+
+DEBUG_FIELDS = ["xpos", "xmat", "xcom", "M", "bias", "passive", "actuator", "a0", "contacts", "nrow", "rows", "qacc",
+                "iterations", "status", "qpos_next", "qvel_next"]
+
+
+def debug_layout(sizes) -> List[int]:
+    nb, nv, nq, ns, nr = sizes.nbody, sizes.nv, sizes.nq, sizes.nslot, sizes.nrow_max
+    lens = [3 * nb, 9 * nb, 3 * nb, nv * nv, nv, nv, nv, nv, 14 * ns, 1, nr * (nv + 7), nv, 1, 1, nq, nv]
+    return list(np.cumsum([0] + lens))
+
+
+def debug_substep(batch: Batch, state: State, ctrl: torch.Tensor, env: int, stream=None) -> dict:
+    """Run one substep of env `env` and return its intermediates (numpy)."""
+    k = max(i for i in range(len(batch.models)) if batch.env_off[i] <= env)
+    sz = batch.models[k].sizes
+    off = debug_layout(sz)
+    out = torch.zeros(off[-1], dtype=torch.float32, device=state.qpos.device)
+    _capi.pg_debug_substep(batch.handle, state.c(), _ptr(ctrl), int(env), _ptr(out), _stream_ptr(stream))
+    torch.cuda.synchronize()
+    o = out.cpu().numpy().astype(np.float64)
+    r = {name: o[off[i]:off[i + 1]] for i, name in enumerate(DEBUG_FIELDS)}
+    nv, nb = sz.nv, sz.nbody
+    r["xpos"] = r["xpos"].reshape(nb, 3)
+    r["xmat"] = r["xmat"].reshape(nb, 3, 3)
+    r["xcom"] = r["xcom"].reshape(nb, 3)
+    r["M"] = r["M"].reshape(nv, nv)
+    r["contacts"] = r["contacts"].reshape(sz.nslot, 14)
+    r["nrow"] = int(r["nrow"][0])
+    r["rows"] = r["rows"].reshape(sz.nrow_max, nv + 7)[: r["nrow"]]
+    r["iterations"] = int(r["iterations"][0])
+    r["status"] = int(r["status"][0])
+    return r
+
+
+def to_soa(x: np.ndarray, ld: int, rows: Optional[int] = None) -> np.ndarray:
+    """[N, k] env-major -> [rows, ld] coordinate-major (zero padded)."""
+    n, k = x.shape
+    out = np.zeros((rows if rows is not None else k, ld), np.float32)
+    out[:k, :n] = x.T
+    return out

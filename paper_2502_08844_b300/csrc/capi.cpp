@@ -1,0 +1,212 @@
+// C ABI entry points (declared in include/pg.h): argument checks, batch / tile construction,
+// device copies of the model blobs, kernel launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pg.h"
+#include "pg_host.h"
+#include "pg_internal.h"
+
+namespace pg {
+
+static thread_local std::string g_error;
+
+int set_error(int code, const std::string& msg) {
+  g_error = msg;
+  return code;
+}
+
+static int cuda_error(cudaError_t e, const char* what) {
+  return set_error(e == cudaErrorMemoryAllocation ? PG_ENOMEM : PG_ECUDA,
+                   std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+constexpr size_t kMaxSmem = 232448;   // 227 KB opt-in shared memory per block on sm_103a
+
+}  // namespace pg
+
+using namespace pg;
+
+extern "C" {
+
+const char* pg_last_error(void) { return g_error.c_str(); }
+
+int pg_model_compile(const pg_model_desc* desc, pg_model** out) {
+  if (!out) return set_error(PG_EINVAL, "out is NULL");
+  *out = nullptr;
+  pg_model* m = new (std::nothrow) pg_model();
+  if (!m) return set_error(PG_ENOMEM, "host allocation failed");
+  int rc = compile_model(desc, m);
+  if (rc != PG_OK) {
+    delete m;
+    return rc;
+  }
+  *out = m;
+  g_error.clear();
+  return PG_OK;
+}
+
+int pg_model_info(const pg_model* m, pg_model_sizes* out) {
+  if (!m || !out) return set_error(PG_EINVAL, "NULL argument");
+  const ModelHdr& h = m->hdr;
+  out->nq = h.nq; out->nv = h.nv; out->nu = h.nu; out->nbody = h.nbody; out->njnt = h.njnt; out->ngeom = h.ngeom;
+  out->npair = h.npair; out->nslot = h.nslot; out->nrow_max = h.nrow_max; out->max_contacts = h.max_contacts;
+  out->workspace_bytes = 4 * h.ws_floats;
+  out->debug_floats = h.debug_floats;
+  return PG_OK;
+}
+
+void pg_model_free(pg_model* m) {
+  if (!m) return;
+  if (m->d_blob) cudaFree(m->d_blob);
+  delete m;
+}
+
+void pg_batch_free(pg_batch* b) {
+  if (!b) return;
+  if (b->d_blobs) cudaFree(b->d_blobs);
+  if (b->d_blob_off) cudaFree(b->d_blob_off);
+  if (b->d_tiles) cudaFree(b->d_tiles);
+  if (b->d_ctrl_stage) cudaFree(b->d_ctrl_stage);
+  delete b;
+}
+
+int pg_batch_compile(const pg_model* const* models, const int64_t* counts, int nmodels, int envs_per_cta, pg_batch** out) {
+  if (!out) return set_error(PG_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!models || !counts || nmodels < 1) return set_error(PG_EINVAL, "need at least one model");
+  if (envs_per_cta < 0 || envs_per_cta > 8) return set_error(PG_EINVAL, "envs_per_cta must be 0 (default) or 1..8");
+  pg_batch* b = new (std::nothrow) pg_batch();
+  if (!b) return set_error(PG_ENOMEM, "host allocation failed");
+  for (int k = 0; k < nmodels; k++) {
+    if (!models[k]) { delete b; return set_error(PG_EINVAL, "NULL model in batch"); }
+    if (counts[k] < 0) { delete b; return set_error(PG_EINVAL, "negative env count"); }
+    b->models.push_back(models[k]);
+    b->counts.push_back(counts[k]);
+    b->env_off.push_back(b->n);
+    b->n += counts[k];
+    const ModelHdr& h = models[k]->hdr;
+    b->nq_max = std::max(b->nq_max, h.nq);
+    b->nv_max = std::max(b->nv_max, h.nv);
+    b->nu_max = std::max(b->nu_max, h.nu);
+    b->max_ws_floats = std::max(b->max_ws_floats, h.ws_floats);
+    b->max_blob_words = std::max(b->max_blob_words, h.words);
+    b->max_debug = std::max(b->max_debug, h.debug_floats);
+    b->blob_off.push_back(0);
+  }
+  if (b->n > (int64_t)1 << 31) { delete b; return set_error(PG_EINVAL, "too many environments"); }
+  int warps = envs_per_cta ? envs_per_cta : 4;
+  auto smem_for = [&](int w) { return 4 * ((size_t)b->max_blob_words + (size_t)w * b->max_ws_floats); };
+  while (warps > 1 && smem_for(warps) > kMaxSmem) {
+    if (envs_per_cta) { delete b; return set_error(PG_ECAPACITY, "envs_per_cta exceeds shared memory for these models"); }
+    warps--;
+  }
+  if (smem_for(warps) > kMaxSmem) { delete b; return set_error(PG_ECAPACITY, "one environment's workspace exceeds shared memory"); }
+  b->warps = warps;
+  b->smem_bytes = smem_for(warps);
+  std::vector<uint32_t> all;
+  for (int k = 0; k < nmodels; k++) {
+    b->blob_off[k] = (int)all.size();
+    all.insert(all.end(), models[k]->blob.begin(), models[k]->blob.end());
+  }
+  for (int k = 0; k < nmodels; k++)
+    for (int64_t e0 = 0; e0 < counts[k]; e0 += warps)
+      b->tiles.push_back(Tile{k, (int)(b->env_off[k] + e0), (int)std::min<int64_t>(warps, counts[k] - e0), 0});
+  b->ntiles = (int)b->tiles.size();
+  cudaError_t e;
+  if ((e = cudaMalloc(&b->d_blobs, all.size() * 4)) != cudaSuccess) { pg_batch_free(b); return cuda_error(e, "cudaMalloc"); }
+  if ((e = cudaMalloc(&b->d_blob_off, nmodels * sizeof(int))) != cudaSuccess) { pg_batch_free(b); return cuda_error(e, "cudaMalloc"); }
+  if (b->ntiles && (e = cudaMalloc(&b->d_tiles, b->tiles.size() * sizeof(Tile))) != cudaSuccess) { pg_batch_free(b); return cuda_error(e, "cudaMalloc"); }
+  if ((e = cudaMemcpy(b->d_blobs, all.data(), all.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(b->d_blob_off, b->blob_off.data(), nmodels * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (b->ntiles && (e = cudaMemcpy(b->d_tiles, b->tiles.data(), b->tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice)) != cudaSuccess)) {
+    pg_batch_free(b);
+    return cuda_error(e, "cudaMemcpy");
+  }
+  if ((e = configure_step_kernels(b->smem_bytes)) != cudaSuccess) { pg_batch_free(b); return cuda_error(e, "cudaFuncSetAttribute"); }
+  *out = b;
+  g_error.clear();
+  return PG_OK;
+}
+
+int pg_batch_info(const pg_batch* b, int64_t* n_envs, int* nq_max, int* nv_max, int* nu_max) {
+  if (!b) return set_error(PG_EINVAL, "batch is NULL");
+  if (n_envs) *n_envs = b->n;
+  if (nq_max) *nq_max = b->nq_max;
+  if (nv_max) *nv_max = b->nv_max;
+  if (nu_max) *nu_max = b->nu_max;
+  return PG_OK;
+}
+
+static int check_state(const pg_batch* b, const pg_state* s) {
+  if (!b || !s) return set_error(PG_EINVAL, "NULL batch or state");
+  if (s->n != b->n) return set_error(PG_EINVAL, "state.n differs from the batch's environment count");
+  if (s->ld < s->n) return set_error(PG_EINVAL, "state.ld must be >= state.n");
+  if (b->n > 0 && (!s->qpos || !s->qvel || !s->qacc_warm || !s->status)) return set_error(PG_EINVAL, "NULL state array");
+  return PG_OK;
+}
+
+int pg_reset(const pg_batch* b, pg_state* s, const uint8_t* mask, const float* qpos0, const float* qvel0, void* stream) {
+  int rc = check_state(b, s);
+  if (rc) return rc;
+  if (b->n > 0 && (!qpos0 || !qvel0)) return set_error(PG_EINVAL, "NULL qpos0 / qvel0");
+  cudaError_t e = launch_reset(b, s, mask, qpos0, qvel0, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_error(e, "reset launch");
+  return PG_OK;
+}
+
+int pg_step(const pg_batch* b, pg_state* s, const float* ctrl, int n_substeps, void* stream) {
+  int rc = check_state(b, s);
+  if (rc) return rc;
+  if (n_substeps < 1) return set_error(PG_EINVAL, "n_substeps must be >= 1");
+  if (b->n > 0 && b->nu_max > 0 && !ctrl) return set_error(PG_EINVAL, "NULL ctrl");
+  cudaError_t e = launch_step(b, s, ctrl, n_substeps, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_error(e, "step launch");
+  return PG_OK;
+}
+
+int pg_debug_substep(const pg_batch* b, pg_state* s, const float* ctrl, int64_t env, float* out, void* stream) {
+  int rc = check_state(b, s);
+  if (rc) return rc;
+  if (env < 0 || env >= b->n) return set_error(PG_EINVAL, "env out of range");
+  if (!out) return set_error(PG_EINVAL, "NULL out");
+  if (b->nu_max > 0 && !ctrl) return set_error(PG_EINVAL, "NULL ctrl");
+  cudaError_t e = launch_debug(b, s, ctrl, env, out, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_error(e, "debug launch");
+  return PG_OK;
+}
+
+int pg_step_host(pg_batch* b, pg_state* s, const float* ctrl_host, float* qpos_host, float* qvel_host, int n_substeps,
+                 void* stream) {
+  int rc = check_state(b, s);
+  if (rc) return rc;
+  if (n_substeps < 1) return set_error(PG_EINVAL, "n_substeps must be >= 1");
+  if ((b->nu_max > 0 && !ctrl_host) || !qpos_host || !qvel_host) return set_error(PG_EINVAL, "NULL host buffer");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t need = (size_t)std::max(b->nu_max, 1) * (size_t)s->ld;
+  if (b->ctrl_stage_floats < need) {
+    if (b->d_ctrl_stage) cudaFree(b->d_ctrl_stage);
+    b->d_ctrl_stage = nullptr;
+    b->ctrl_stage_floats = 0;
+    cudaError_t e = cudaMalloc(&b->d_ctrl_stage, need * sizeof(float));
+    if (e != cudaSuccess) return cuda_error(e, "cudaMalloc (control staging)");
+    b->ctrl_stage_floats = need;
+  }
+  cudaError_t e;
+  if (b->nu_max > 0 &&
+      (e = cudaMemcpyAsync(b->d_ctrl_stage, ctrl_host, (size_t)b->nu_max * s->ld * sizeof(float), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return cuda_error(e, "control upload");
+  if ((e = launch_step(b, s, b->d_ctrl_stage, n_substeps, st)) != cudaSuccess) return cuda_error(e, "step launch");
+  if ((e = cudaMemcpyAsync(qpos_host, s->qpos, (size_t)b->nq_max * s->ld * sizeof(float), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return cuda_error(e, "qpos download");
+  if ((e = cudaMemcpyAsync(qvel_host, s->qvel, (size_t)b->nv_max * s->ld * sizeof(float), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return cuda_error(e, "qvel download");
+  return PG_OK;
+}
+
+}  // extern "C"

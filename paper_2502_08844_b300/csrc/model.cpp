@@ -1,0 +1,373 @@
+// Host-side model compiler: validates a pg_model_desc, derives the tables the step kernel
+// needs (levels, child lists, dof tree, packed LDL pattern, contact slots, mass properties,
+// options) and packs them into one blob of 32-bit words (layout in pg_internal.h).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pg.h"
+#include "pg_host.h"
+#include "pg_internal.h"
+
+namespace pg {
+
+namespace {
+
+struct Blob {
+  std::vector<uint32_t> w;
+  int ints(const std::vector<int>& v) {
+    int o = (int)w.size();
+    for (int x : v) w.push_back((uint32_t)x);
+    return o;
+  }
+  int floats(const std::vector<float>& v) {
+    int o = (int)w.size();
+    for (float x : v) {
+      uint32_t u;
+      std::memcpy(&u, &x, 4);
+      w.push_back(u);
+    }
+    return o;
+  }
+};
+
+// points a primitive pair type can produce (its static slot count); -1: unsupported
+int slots_for(int t1, int t2) {
+  static const int table[4][4] = {
+      //            plane sphere capsule box
+      /* plane   */ {-1, 1, 2, 4},
+      /* sphere  */ {-1, 1, 1, 1},
+      /* capsule */ {-1, -1, 1, 2},
+      /* box     */ {-1, -1, -1, 4},
+  };
+  if (t1 < 0 || t1 > 3 || t2 < 0 || t2 > 3) return -1;
+  return table[t1][t2];
+}
+
+// rotation matrix (row-major) of a quaternion, normalised here
+void quat_matrix(const float* qin, double R[9]) {
+  double w = qin[0], x = qin[1], y = qin[2], z = qin[3];
+  double n = std::sqrt(w * w + x * x + y * y + z * z);
+  w /= n; x /= n; y /= n; z /= n;
+  double xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z, wx = w * x, wy = w * y, wz = w * z;
+  R[0] = 1 - 2 * (yy + zz); R[1] = 2 * (xy - wz); R[2] = 2 * (xz + wy);
+  R[3] = 2 * (xy + wz); R[4] = 1 - 2 * (xx + zz); R[5] = 2 * (yz - wx);
+  R[6] = 2 * (xz - wy); R[7] = 2 * (yz + wx); R[8] = 1 - 2 * (xx + yy);
+}
+
+// principal moments of a uniform solid about its centre (geom axes)
+void principal_moments(int type, const float* size, double m, double I[3]) {
+  const double pi = 3.14159265358979323846;
+  I[0] = I[1] = I[2] = 0.0;
+  if (type == PG_GEOM_SPHERE) {
+    double r = size[0];
+    I[0] = I[1] = I[2] = 2.0 / 5.0 * m * r * r;
+  } else if (type == PG_GEOM_BOX) {
+    double X = 2.0 * size[0], Y = 2.0 * size[1], Z = 2.0 * size[2];
+    I[0] = m / 12.0 * (Y * Y + Z * Z);
+    I[1] = m / 12.0 * (X * X + Z * Z);
+    I[2] = m / 12.0 * (X * X + Y * Y);
+  } else if (type == PG_GEOM_CAPSULE) {
+    // cylinder of length L plus two hemispherical caps, mass shared by volume
+    double r = size[0], L = 2.0 * size[1];
+    double v_cyl = pi * r * r * L, v_caps = 4.0 / 3.0 * pi * r * r * r;
+    double m_cyl = m * v_cyl / (v_cyl + v_caps), m_cap = 0.5 * m * v_caps / (v_cyl + v_caps);   // per cap
+    double cyl_axial = 0.5 * m_cyl * r * r, cyl_trans = m_cyl * (3.0 * r * r + L * L) / 12.0;
+    double d = 0.5 * L + 3.0 * r / 8.0;   // cap centroid from the capsule centre
+    double cap_axial = 0.4 * m_cap * r * r;
+    double cap_trans = m_cap * (83.0 / 320.0) * r * r + m_cap * d * d;
+    I[0] = I[1] = cyl_trans + 2.0 * cap_trans;
+    I[2] = cyl_axial + 2.0 * cap_axial;
+  }
+}
+
+int align4(int x) { return (x + 3) & ~3; }
+
+}  // namespace
+
+int compile_model(const pg_model_desc* d, pg_model* out) {
+  if (!d) return set_error(PG_EINVAL, "desc is NULL");
+  const int nbody = d->nbody, njnt = d->njnt, ngeom = d->ngeom, npair = d->npair, nu = d->nu;
+  if (nbody < 1 || njnt < 0 || ngeom < 0 || npair < 0 || nu < 0) return set_error(PG_EINVAL, "negative counts");
+  if (nbody > kMaxBody) return set_error(PG_ECAPACITY, "nbody exceeds the kernel limit (64)");
+  if (!d->body_parent || !d->body_pos || !d->body_quat) return set_error(PG_EINVAL, "body arrays missing");
+  // ---- tree ----
+  std::vector<int> parent(d->body_parent, d->body_parent + nbody);
+  parent[0] = -1;
+  for (int b = 1; b < nbody; b++)
+    if (parent[b] < 0 || parent[b] >= b) return set_error(PG_EINVAL, "body_parent violates level order (parent[i] < i)");
+  std::vector<int> level(nbody, 0), root(nbody, 0);
+  int nlevel = 1;
+  for (int b = 1; b < nbody; b++) {
+    level[b] = level[parent[b]] + 1;
+    root[b] = parent[b] == 0 ? b : root[parent[b]];
+    nlevel = std::max(nlevel, level[b] + 1);
+  }
+  std::vector<int> level_start(nlevel + 1, 0), level_body;
+  for (int L = 0; L < nlevel; L++) {
+    level_start[L] = (int)level_body.size();
+    for (int b = 0; b < nbody; b++)
+      if (level[b] == L) level_body.push_back(b);
+  }
+  level_start[nlevel] = nbody;
+  std::vector<int> child_start(nbody + 1, 0), child;
+  for (int b = 0; b < nbody; b++) {
+    child_start[b] = (int)child.size();
+    for (int c = b + 1; c < nbody; c++)
+      if (parent[c] == b) child.push_back(c);
+  }
+  child_start[nbody] = (int)child.size();
+  // ---- joints ----
+  std::vector<int> jnt_type(njnt), jnt_body(njnt), qposadr(njnt), dofadr(njnt);
+  std::vector<int> body_jntadr(nbody, 0), body_jntnum(nbody, 0);
+  std::vector<float> jpos(3 * njnt), jaxis(3 * njnt), jrange(2 * njnt);
+  int nq = 0, nv = 0;
+  for (int j = 0; j < njnt; j++) {
+    int t = d->jnt_type[j], b = d->jnt_body[j];
+    if (t != PG_JNT_FREE && t != PG_JNT_HINGE && t != PG_JNT_SLIDE) return set_error(PG_EINVAL, "bad joint type");
+    if (b < 1 || b >= nbody) return set_error(PG_EINVAL, "jnt_body out of range");
+    if (j > 0 && d->jnt_body[j - 1] > b) return set_error(PG_EINVAL, "joints must be grouped by body, in body order");
+    jnt_type[j] = t;
+    jnt_body[j] = b;
+    if (body_jntnum[b]++ == 0) body_jntadr[b] = j;
+    qposadr[j] = nq;
+    dofadr[j] = nv;
+    nq += t == PG_JNT_FREE ? 7 : 1;
+    nv += t == PG_JNT_FREE ? 6 : 1;
+    double ax = d->jnt_axis[3 * j], ay = d->jnt_axis[3 * j + 1], az = d->jnt_axis[3 * j + 2];
+    double an = std::sqrt(ax * ax + ay * ay + az * az);
+    if (t != PG_JNT_FREE && !(an > 0)) return set_error(PG_EINVAL, "zero joint axis");
+    if (t == PG_JNT_FREE) an = 1.0;
+    jaxis[3 * j] = (float)(ax / an); jaxis[3 * j + 1] = (float)(ay / an); jaxis[3 * j + 2] = (float)(az / an);
+    for (int k = 0; k < 3; k++) jpos[3 * j + k] = d->jnt_pos[3 * j + k];
+    jrange[2 * j] = d->jnt_range[2 * j];
+    jrange[2 * j + 1] = d->jnt_range[2 * j + 1];
+    if (d->jnt_limited[j] && t != PG_JNT_FREE && !(jrange[2 * j] < jrange[2 * j + 1]))
+      return set_error(PG_EINVAL, "limited joint needs range lo < hi");
+  }
+  for (int j = 0; j < njnt; j++)
+    if (jnt_type[j] == PG_JNT_FREE && (parent[jnt_body[j]] != 0 || body_jntnum[jnt_body[j]] != 1))
+      return set_error(PG_EINVAL, "a free joint must be the only joint of a child of the world");
+  if (nv > kMaxNv) return set_error(PG_ECAPACITY, "nv exceeds the kernel limit (64)");
+  // ---- dof tree: each dof's parent is the previous dof on its body, else the last dof of the
+  // nearest ancestor body with dofs ----
+  std::vector<int> dof_body(nv), dof_parent(nv, -1), depth(nv, 0);
+  std::vector<int> last_dof(nbody, -1);
+  std::vector<uint64_t> mask(nbody, 0);
+  for (int b = 1; b < nbody; b++) {
+    int prev = last_dof[parent[b]];
+    mask[b] = mask[parent[b]];
+    for (int j = body_jntadr[b]; j < body_jntadr[b] + body_jntnum[b]; j++) {
+      int n = jnt_type[j] == PG_JNT_FREE ? 6 : 1;
+      for (int k = 0; k < n; k++) {
+        int dof = dofadr[j] + k;
+        dof_body[dof] = b;
+        dof_parent[dof] = prev;
+        depth[dof] = prev < 0 ? 0 : depth[prev] + 1;
+        mask[b] |= (uint64_t)1 << dof;
+        prev = dof;
+      }
+    }
+    last_dof[b] = prev;
+  }
+  std::vector<int> rowadr(nv), Lcol;
+  for (int i = 0; i < nv; i++) {
+    rowadr[i] = (int)Lcol.size();
+    for (int a = i; a >= 0; a = dof_parent[a]) Lcol.push_back(a);
+  }
+  const int nL = (int)Lcol.size();
+  // ---- mass properties ----
+  std::vector<float> mass(nbody, 0.f), ipos(3 * nbody, 0.f), inertia(6 * nbody, 0.f);
+  for (int b = 1; b < nbody; b++) {
+    if (!(d->body_geom_inertia && d->body_geom_inertia[b])) {
+      mass[b] = d->body_mass[b];
+      for (int k = 0; k < 3; k++) ipos[3 * b + k] = d->body_ipos[3 * b + k];
+      for (int k = 0; k < 6; k++) inertia[6 * b + k] = d->body_inertia[6 * b + k];
+      continue;
+    }
+    double M = 0, com[3] = {0, 0, 0};
+    for (int g = 0; g < ngeom; g++)
+      if (d->geom_body[g] == b && d->geom_mass[g] > 0) {
+        M += d->geom_mass[g];
+        for (int k = 0; k < 3; k++) com[k] += d->geom_mass[g] * (double)d->geom_pos[3 * g + k];
+      }
+    if (!(M > 0)) continue;
+    for (int k = 0; k < 3; k++) com[k] /= M;
+    double I[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int g = 0; g < ngeom; g++) {
+      if (d->geom_body[g] != b || !(d->geom_mass[g] > 0)) continue;
+      if (d->geom_type[g] == PG_GEOM_PLANE) return set_error(PG_EINVAL, "a plane geom cannot carry mass");
+      double Ip[3], R[9];
+      principal_moments(d->geom_type[g], d->geom_size + 3 * g, d->geom_mass[g], Ip);
+      quat_matrix(d->geom_quat + 4 * g, R);
+      double r[3];
+      for (int k = 0; k < 3; k++) r[k] = d->geom_pos[3 * g + k] - com[k];
+      double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+      for (int a = 0; a < 3; a++)
+        for (int c = 0; c < 3; c++) {
+          double rot = R[3 * a] * Ip[0] * R[3 * c] + R[3 * a + 1] * Ip[1] * R[3 * c + 1] + R[3 * a + 2] * Ip[2] * R[3 * c + 2];
+          double shift = d->geom_mass[g] * ((a == c ? r2 : 0.0) - r[a] * r[c]);
+          I[a][c] += rot + shift;
+        }
+    }
+    mass[b] = (float)M;
+    for (int k = 0; k < 3; k++) ipos[3 * b + k] = (float)com[k];
+    inertia[6 * b + 0] = (float)I[0][0]; inertia[6 * b + 1] = (float)I[1][1]; inertia[6 * b + 2] = (float)I[2][2];
+    inertia[6 * b + 3] = (float)I[0][1]; inertia[6 * b + 4] = (float)I[0][2]; inertia[6 * b + 5] = (float)I[1][2];
+  }
+  // ---- dofs ----
+  std::vector<float> damping(nv), armature(nv);
+  for (int i = 0; i < nv; i++) {
+    damping[i] = d->dof_damping ? d->dof_damping[i] : 0.f;
+    double arm = d->dof_armature ? d->dof_armature[i] : 0.0;
+    if (d->dof_rotor) {
+      double kg = d->dof_rotor[3 * i], mr = d->dof_rotor[3 * i + 1], rr = d->dof_rotor[3 * i + 2];
+      double Ir = 0.5 * mr * rr * rr;   // uniform rotor disc
+      arm += kg * kg * Ir;               // reflected through the gearbox
+    }
+    armature[i] = (float)arm;
+  }
+  // ---- geoms and pairs ----
+  std::vector<int> gtype(d->geom_type, d->geom_type + ngeom), gbody(d->geom_body, d->geom_body + ngeom);
+  std::vector<float> gpos(d->geom_pos, d->geom_pos + 3 * ngeom), gquat(4 * ngeom), gsize(d->geom_size, d->geom_size + 3 * ngeom);
+  for (int g = 0; g < ngeom; g++) {
+    if (gtype[g] < PG_GEOM_PLANE || gtype[g] > PG_GEOM_BOX) return set_error(PG_EINVAL, "bad geom type");
+    if (gbody[g] < 0 || gbody[g] >= nbody) return set_error(PG_EINVAL, "geom_body out of range");
+    double q[4], n = 0;
+    for (int k = 0; k < 4; k++) { q[k] = d->geom_quat[4 * g + k]; n += q[k] * q[k]; }
+    n = std::sqrt(n);
+    if (!(n > 0)) return set_error(PG_EINVAL, "zero geom quaternion");
+    for (int k = 0; k < 4; k++) gquat[4 * g + k] = (float)(q[k] / n);
+  }
+  std::vector<int> pg1(npair), pg2(npair), pcondim(npair), pslotadr(npair), pnslot(npair);
+  std::vector<float> pfric(npair);
+  int nslot = 0;
+  for (int p = 0; p < npair; p++) {
+    int a = d->pair_geom[2 * p], b = d->pair_geom[2 * p + 1];
+    if (a < 0 || a >= ngeom || b < 0 || b >= ngeom) return set_error(PG_EINVAL, "pair geom out of range");
+    int n = slots_for(gtype[a], gtype[b]);
+    if (n < 0) return set_error(PG_EUNSUPPORTED, "unsupported pair: type(geom1) must not exceed type(geom2) (plane<sphere<capsule<box), plane-plane unsupported");
+    if (d->pair_condim[p] != 1 && d->pair_condim[p] != 3) return set_error(PG_EUNSUPPORTED, "pair_condim must be 1 or 3");
+    pg1[p] = a; pg2[p] = b; pcondim[p] = d->pair_condim[p]; pfric[p] = d->pair_friction[p];
+    pslotadr[p] = nslot; pnslot[p] = n;
+    nslot += n;
+  }
+  if (nslot > kMaxSlot) return set_error(PG_ECAPACITY, "candidate contact slots exceed the kernel limit (64)");
+  // ---- actuators ----
+  std::vector<int> atype(nu), adof(nu), aqadr(nu), aclim(nu);
+  std::vector<float> agear(nu), akp(nu), akd(nu), arange(2 * nu);
+  for (int a = 0; a < nu; a++) {
+    int j = d->act_jnt[a];
+    if (j < 0 || j >= njnt || jnt_type[j] == PG_JNT_FREE) return set_error(PG_EINVAL, "actuators drive hinge or slide joints");
+    if (d->act_type[a] != PG_ACT_MOTOR && d->act_type[a] != PG_ACT_POSITION) return set_error(PG_EINVAL, "bad actuator type");
+    atype[a] = d->act_type[a]; adof[a] = dofadr[j]; aqadr[a] = qposadr[j]; aclim[a] = d->act_ctrllimited[a];
+    agear[a] = d->act_gear[a]; akp[a] = d->act_kp[a]; akd[a] = d->act_kd[a];
+    arange[2 * a] = d->act_ctrlrange[2 * a]; arange[2 * a + 1] = d->act_ctrlrange[2 * a + 1];
+  }
+  std::vector<int> limit_jnt;
+  for (int j = 0; j < njnt; j++)
+    if (d->jnt_limited[j] && jnt_type[j] != PG_JNT_FREE) limit_jnt.push_back(j);
+  // ---- options ----
+  if (!(d->timestep > 0)) return set_error(PG_EINVAL, "timestep must be > 0");
+  if (d->iterations < 1) return set_error(PG_EINVAL, "iterations must be >= 1");
+  if (d->cone != PG_CONE_PYRAMIDAL) return set_error(PG_EUNSUPPORTED, "only the pyramidal cone is implemented");
+  int max_contacts = d->max_contacts < 0 ? nslot : std::min(d->max_contacts, nslot);
+  int nrow_max = 4 * max_contacts + (int)limit_jnt.size();
+  if (nrow_max > kMaxRow) return set_error(PG_ECAPACITY, "constraint rows exceed the kernel limit (128)");
+
+  ModelHdr h;
+  std::memset(&h, 0, sizeof(h));
+  h.nbody = nbody; h.njnt = njnt; h.nq = nq; h.nv = nv; h.nu = nu; h.ngeom = ngeom; h.npair = npair;
+  h.nslot = nslot; h.nrow_max = nrow_max; h.max_contacts = max_contacts; h.nlimited = (int)limit_jnt.size();
+  h.nlevel = nlevel; h.nL = nL; h.cap = d->iterations; h.cone = d->cone;
+  h.h = d->timestep;
+  for (int k = 0; k < 3; k++) h.grav[k] = d->gravity[k];
+  {
+    double tc = std::max((double)d->solref[0], 2.0 * (double)d->timestep), zeta = d->solref[1], dmax = d->solimp[1];
+    h.kref = (float)(1.0 / (dmax * dmax * tc * tc * zeta * zeta));
+    h.bref = (float)(2.0 / (dmax * tc));
+  }
+  for (int k = 0; k < 5; k++) h.solimp[k] = d->solimp[k];
+  h.margin = d->margin;
+
+  Blob B;
+  B.w.assign(kHdrWords, 0u);
+  std::vector<int> body_dofmask(2 * nbody);
+  for (int b = 0; b < nbody; b++) {
+    body_dofmask[2 * b] = (int)(uint32_t)(mask[b] & 0xffffffffu);
+    body_dofmask[2 * b + 1] = (int)(uint32_t)(mask[b] >> 32);
+  }
+  std::vector<float> bpos(d->body_pos, d->body_pos + 3 * nbody), bquat(4 * nbody);
+  for (int b = 0; b < nbody; b++) {
+    double n = 0;
+    for (int k = 0; k < 4; k++) n += (double)d->body_quat[4 * b + k] * d->body_quat[4 * b + k];
+    n = std::sqrt(n);
+    if (!(n > 0)) return set_error(PG_EINVAL, "zero body quaternion");
+    for (int k = 0; k < 4; k++) bquat[4 * b + k] = (float)(d->body_quat[4 * b + k] / n);
+  }
+  h.o_body_parent = B.ints(parent); h.o_body_root = B.ints(root);
+  h.o_body_jntadr = B.ints(body_jntadr); h.o_body_jntnum = B.ints(body_jntnum);
+  h.o_body_pos = B.floats(bpos); h.o_body_quat = B.floats(bquat); h.o_body_mass = B.floats(mass);
+  h.o_body_ipos = B.floats(ipos); h.o_body_inertia = B.floats(inertia); h.o_body_dofmask = B.ints(body_dofmask);
+  h.o_level_start = B.ints(level_start); h.o_level_body = B.ints(level_body);
+  h.o_child_start = B.ints(child_start); h.o_child = B.ints(child);
+  h.o_jnt_type = B.ints(jnt_type); h.o_jnt_qposadr = B.ints(qposadr); h.o_jnt_dofadr = B.ints(dofadr);
+  h.o_jnt_pos = B.floats(jpos); h.o_jnt_axis = B.floats(jaxis); h.o_jnt_range = B.floats(jrange);
+  h.o_dof_body = B.ints(dof_body); h.o_dof_depth = B.ints(depth); h.o_dof_rowadr = B.ints(rowadr);
+  h.o_dof_damping = B.floats(damping); h.o_dof_armature = B.floats(armature); h.o_Lcol = B.ints(Lcol);
+  h.o_geom_type = B.ints(gtype); h.o_geom_body = B.ints(gbody); h.o_geom_pos = B.floats(gpos);
+  h.o_geom_quat = B.floats(gquat); h.o_geom_size = B.floats(gsize);
+  h.o_pair_g1 = B.ints(pg1); h.o_pair_g2 = B.ints(pg2); h.o_pair_friction = B.floats(pfric);
+  h.o_pair_condim = B.ints(pcondim); h.o_pair_slotadr = B.ints(pslotadr); h.o_pair_nslot = B.ints(pnslot);
+  h.o_act_type = B.ints(atype); h.o_act_dof = B.ints(adof); h.o_act_qposadr = B.ints(aqadr);
+  h.o_act_gear = B.floats(agear); h.o_act_kp = B.floats(akp); h.o_act_kd = B.floats(akd);
+  h.o_act_ctrllimited = B.ints(aclim); h.o_act_range = B.floats(arange);
+  h.o_limit_jnt = B.ints(limit_jnt);
+  while (B.w.size() % 4) B.w.push_back(0u);
+  h.words = (int)B.w.size();
+
+  // ---- per-env workspace layout (floats) ----
+  int o = 0;
+  auto take = [&](int n) { int r = o; o = align4(o + n); return r; };
+  h.w_qpos = take(nq); h.w_qvel = take(nv); h.w_warm = take(nv); h.w_ctrl = take(std::max(nu, 1));
+  h.w_M = take(nv * nv); h.w_L = take(nL); h.w_D = take(nv); h.w_bias = take(nv); h.w_passive = take(nv);
+  h.w_act = take(nv); h.w_a0 = take(nv); h.w_vtmp = take(nv); h.w_con = take(14 * std::max(nslot, 1));
+  const int u1 = o;
+  h.w_xpos = take(3 * nbody); h.w_xquat = take(4 * nbody); h.w_xmat = take(9 * nbody); h.w_xipos = take(3 * nbody);
+  h.w_janchor = take(3 * std::max(njnt, 1)); h.w_jaxis = take(3 * std::max(njnt, 1));
+  h.w_gpos = take(3 * std::max(ngeom, 1)); h.w_gmat = take(9 * std::max(ngeom, 1));
+  h.w_cdof = take(6 * nv); h.w_cinert = take(10 * nbody);
+  const int end_kin = o;
+  o = u1;
+  h.w_H = take(nv * nv); h.w_a = take(nv); h.w_g = take(nv); h.w_p = take(nv); h.w_Mp = take(nv);
+  h.w_Z = take(std::max(nrow_max, 1) * nv);
+  const int end_newton = o;
+  const int u2 = std::max(end_kin, end_newton);
+  o = u2;
+  h.w_crb = take(10 * nbody); h.w_cvel = take(6 * nbody); h.w_cacc = take(6 * nbody); h.w_cfrc = take(6 * nbody);
+  h.w_F = take(6 * nv);
+  const int end_dyn = o;
+  o = u2;
+  const int R = std::max(nrow_max, 1);
+  h.w_J = take(R * nv); h.w_rr = take(R); h.w_rv = take(R); h.w_aref = take(R); h.w_rD = take(R); h.w_Ahat = take(R);
+  h.w_imp = take(R); h.w_jar = take(R); h.w_Jp = take(R); h.w_force = take(R); h.w_rowslot = take(R);
+  const int end_rows = o;
+  h.ws_floats = std::max(end_dyn, end_rows);
+  // ---- debug record layout ----
+  int q = 0;
+  auto dbg = [&](int n) { int r = q; q += n; return r; };
+  h.dbg_xpos = dbg(3 * nbody); h.dbg_xmat = dbg(9 * nbody); h.dbg_xcom = dbg(3 * nbody); h.dbg_M = dbg(nv * nv);
+  h.dbg_bias = dbg(nv); h.dbg_passive = dbg(nv); h.dbg_act = dbg(nv); h.dbg_a0 = dbg(nv); h.dbg_con = dbg(14 * nslot);
+  h.dbg_nrow = dbg(1); h.dbg_rows = dbg(nrow_max * (nv + 7)); h.dbg_qacc = dbg(nv); h.dbg_iter = dbg(1);
+  h.dbg_status = dbg(1); h.dbg_qpos = dbg(nq); h.dbg_qvel = dbg(nv);
+  h.debug_floats = q;
+
+  std::memcpy(B.w.data(), &h, sizeof(h));
+  out->hdr = h;
+  out->blob = std::move(B.w);
+  return PG_OK;
+}
+
+}  // namespace pg

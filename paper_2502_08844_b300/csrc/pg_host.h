@@ -1,0 +1,49 @@
+// Host-side internals of the library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "pg.h"
+#include "pg_internal.h"
+
+struct pg_model {
+  pg::ModelHdr hdr;
+  std::vector<uint32_t> blob;
+  uint32_t* d_blob = nullptr;   // device copy of the blob
+};
+
+struct pg_batch {
+  std::vector<const pg_model*> models;
+  std::vector<int64_t> counts, env_off;
+  int64_t n = 0;
+  int nq_max = 0, nv_max = 0, nu_max = 0;
+  int warps = 4;                   // environments (one warp each) per thread block
+  int max_ws_floats = 0, max_blob_words = 0, max_debug = 0;
+  size_t smem_bytes = 0;
+  uint32_t* d_blobs = nullptr;     // all models' blobs, concatenated
+  int* d_blob_off = nullptr;       // word offset of each model's blob
+  pg::Tile* d_tiles = nullptr;
+  int ntiles = 0;
+  std::vector<int> blob_off;
+  std::vector<pg::Tile> tiles;
+  // staging buffer of the host-buffer path (allocated on its first use)
+  float* d_ctrl_stage = nullptr;
+  size_t ctrl_stage_floats = 0;
+};
+
+namespace pg {
+
+int set_error(int code, const std::string& msg);
+int compile_model(const pg_model_desc* d, pg_model* out);
+
+// kernel launchers (step.cu)
+cudaError_t launch_step(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st);
+cudaError_t launch_debug(const pg_batch* b, const pg_state* s, const float* ctrl, int64_t env, float* out,
+                         cudaStream_t st);
+cudaError_t launch_reset(const pg_batch* b, const pg_state* s, const uint8_t* mask, const float* qpos0,
+                         const float* qvel0, cudaStream_t st);
+cudaError_t configure_step_kernels(size_t smem_bytes);
+
+}  // namespace pg

@@ -1,0 +1,71 @@
+"""CPU-only checks of the C ABI library: it loads, exports every function include/pg.h
+declares, and the host-side model compiler validates descriptions (no GPU work)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2502_08844_b300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "pg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(pg_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_library_exports_every_declared_function():
+    from paper_2502_08844_b300 import _capi
+    names = header_functions()
+    assert len(names) >= 11
+    lib = C.CDLL(_capi.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(_capi.EXPORTS)
+
+
+def test_model_compile_sizes():
+    from paper_2502_08844_b300 import core
+    q = core.CompiledModel(W.quadruped())
+    s = q.sizes
+    assert (s.nq, s.nv, s.nu, s.nbody, s.nslot) == (19, 18, 12, 10, 4)
+    assert s.nrow_max == 4 * 4 + 12
+    c = core.CompiledModel(W.cartpole())
+    assert (c.sizes.nq, c.sizes.nv, c.sizes.nu, c.sizes.nslot, c.sizes.nrow_max) == (2, 2, 1, 0, 0)
+
+
+def _broken(mutate):
+    m = W.quadruped()
+    mutate(m)
+    return m
+
+
+@pytest.mark.parametrize("mutate,code", [
+    (lambda m: m.body_parent.__setitem__(2, 5), -1),                     # parent after child
+    (lambda m: m.jnt_type.__setitem__(3, 7), -1),                        # bad joint type
+    (lambda m: m.jnt_axis.__setitem__(slice(3, 4), 0.0), -1),           # zero hinge axis
+    (lambda m: m.pair_geom.__setitem__((0, 0), m.pair_geom[0, 1]) or m.pair_geom.__setitem__((0, 1), 0), -4),  # sphere-plane order
+    (lambda m: m.pair_condim.__setitem__(0, 6), -4),                     # condim 6
+    (lambda m: setattr(m, "cone", W.ELLIPTIC), -4),
+    (lambda m: setattr(m, "timestep", 0.0), -1),
+    (lambda m: m.act_jnt.__setitem__(0, 0), -1),                         # actuator on the free joint
+])
+def test_model_compile_rejects_bad_descriptions(mutate, code):
+    from paper_2502_08844_b300 import core, _capi
+    with pytest.raises(_capi.PgError) as ei:
+        core.CompiledModel(_broken(mutate))
+    assert ei.value.code == code
+    assert len(_capi.pg_last_error()) > 0
+
+
+def test_null_arguments_are_errors():
+    from paper_2502_08844_b300 import _capi
+    lib = _capi._lib
+    assert lib.pg_model_compile(None, None) == _capi.PG_EINVAL
+    assert lib.pg_step(None, None, None, 1, None) == _capi.PG_EINVAL
+    assert lib.pg_model_info(None, None) == _capi.PG_EINVAL
+    assert lib.pg_batch_compile(None, None, 0, 0, None) == _capi.PG_EINVAL

@@ -1,0 +1,260 @@
+"""GPU parity of the CUDA step (through the C ABI) against the FP64 oracle on identical seeded
+float32 inputs.
+
+Tolerance form (FP32 kernel vs FP64 oracle), per environment and per compared vector x:
+    max_i |x_i - ref_i| <= rtol * max_i |ref_i| + atol
+i.e. relative to the scale of the vector.  The FP32 state and arithmetic cannot resolve
+smaller components more finely than the largest terms that produce them (accelerations of
+the PD-driven quadruped reach 1e4 m/s^2, so one substep carries ~1e-5 m/s of rounding into
+every velocity component).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2502_08844_b300 import workloads as W
+from tests.gpu_helpers import GpuRun, canon_qpos
+
+pytestmark = pytest.mark.gpu
+
+ONE_STEP_RTOL, ONE_STEP_ATOL = 1e-5, 1e-6
+ROLLOUT_RTOL = 1e-3
+FORCE_RTOL = 1e-3
+
+
+def scaled_err(x, ref):
+    """smallest rtol with max|x - ref| <= rtol * max|ref| + 1e-6"""
+    x = np.asarray(x, np.float64); ref = np.asarray(ref, np.float64)
+    d = np.abs(x - ref).max() - ONE_STEP_ATOL
+    return max(d, 0.0) / max(np.abs(ref).max(), 1e-30)
+
+
+def assert_close_scaled(name, x, ref, rtol):
+    e = scaled_err(x, ref)
+    assert e <= rtol, "%s: scaled error %.3e > %.1e" % (name, e, rtol)
+
+
+def _contact_states(n_states=6):
+    m = W.quadruped()
+    om = O.OracleModel(m)
+    q0, v0 = W.initial_state(m, 1, 3)
+    U = W.actions(m, 1, 3, 0, 60)
+    _, _, w, _, tq, tv = om.rollout(q0, v0, U, 5, trajectory=True)
+    out = []
+    for t in (0, 4, 19, 39, 59, 30)[:n_states]:
+        e = t % 3
+        out.append((tq[t, e].astype(np.float32).astype(np.float64), tv[t, e].astype(np.float32).astype(np.float64),
+                    U[min(t + 1, 59), e].astype(np.float64)))
+    return m, om, out
+
+
+PHASE_FIELDS = ["xpos", "xmat", "xcom", "M", "bias", "passive", "actuator", "a0", "qacc", "qvel_next"]
+
+
+def _phase_compare(m, om, q, v, u, warm=None, env=5, n=8):
+    run = GpuRun(m, n)
+    w = np.zeros(m.nv) if warm is None else warm
+    run.set_state(np.repeat(q[None], n, 0), np.repeat(v[None], n, 0), np.repeat(w[None], n, 0))
+    g = run.debug(np.repeat(u[None], n, 0), env)
+    o = om.forward(q, v, w, u)
+    for k in PHASE_FIELDS:
+        assert_close_scaled(k, g[k], o[k], ONE_STEP_RTOL)
+    assert_close_scaled("qpos_next", canon_qpos(m, g["qpos_next"]), canon_qpos(m, o["qpos_next"]), ONE_STEP_RTOL)
+    # contacts: same active set (no slot within 1e-6 of the margin here), same geometry
+    if m.npair:
+        near = np.abs(o["contacts"][:, 1]) < 1e-6
+        assert np.array_equal(g["contacts"][~near, 0], o["contacts"][~near, 0])
+        for a, b, name in [(1, 2, "dist"), (2, 5, "pos"), (5, 14, "frame")]:
+            assert_close_scaled("contact " + name, g["contacts"][:, a:b], o["contacts"][:, a:b], ONE_STEP_RTOL)
+    assert g["nrow"] == o["nrow"]
+    if g["nrow"]:
+        nv = m.nv
+        assert_close_scaled("J", g["rows"][:, :nv], o["rows"][:, :nv], ONE_STEP_RTOL)
+        for i, k in enumerate(["r", "v", "aref", "D", "Ahat", "imp", "force"]):
+            assert_close_scaled(k, g["rows"][:, nv + i], o["rows"][:, nv + i], ONE_STEP_RTOL)
+    assert g["iterations"] == o["iterations"]
+    return g, o
+
+
+def test_phase_parity_quadruped_contact_states():
+    m, om, states = _contact_states()
+    nrows = []
+    for q, v, u in states:
+        g, o = _phase_compare(m, om, q, v, u)
+        nrows.append(g["nrow"])
+    assert max(nrows) >= 8   # contact-rich states were exercised
+
+
+def test_phase_parity_quadruped_with_warm_start_and_limits():
+    m, om, states = _contact_states(2)
+    q, v, u = states[1]
+    q = q.copy()
+    q[7 + 8] = -2.75   # a knee beyond its lower limit: one limit row
+    warm = np.random.default_rng(0).normal(size=18) * 5
+    g, o = _phase_compare(m, om, q, v, u, warm=warm)
+    assert np.any(np.all(o["rows"][:, :18] == np.eye(18)[14], axis=1))   # the knee's lower-limit row
+
+
+def test_phase_parity_cartpole():
+    m = W.cartpole()
+    om = O.OracleModel(m)
+    q, v = W.initial_state(m, 0, 4)
+    u = W.actions(m, 0, 4, 0, 1)[0]
+    for i in range(4):
+        _phase_compare(m, om, q[i].astype(np.float64), v[i].astype(np.float64), u[i].astype(np.float64), env=i, n=4)
+
+
+def _trajectory_parity(mname, cfg, n, T, envs_per_cta=0):
+    m = W.model(mname)
+    om = O.OracleModel(m)
+    q0, v0 = W.initial_state(m, cfg, n)
+    U = W.actions(m, cfg, n, 0, T)
+    run = GpuRun(m, n, envs_per_cta=envs_per_cta)
+    run.set_state(q0, v0)
+    tqg, tvg = run.rollout(U, m.n_substeps, keep=True)
+    _, _, _, sto, tqo, tvo = om.rollout(q0, v0, U, m.n_substeps, trajectory=True, nthreads=8)
+    return m, tqg, tvg, tqo, tvo, run.status(), sto
+
+
+@pytest.mark.parametrize("mname,cfg,n", [("quadruped", 1, 37), ("cartpole", 0, 256)])
+def test_one_control_step(mname, cfg, n):
+    m, tqg, tvg, tqo, tvo, stg, sto = _trajectory_parity(mname, cfg, n, 1)
+    for e in range(n):
+        assert_close_scaled("qpos env %d" % e, canon_qpos(m, tqg[0, e]), canon_qpos(m, tqo[0, e]), ONE_STEP_RTOL)
+        assert_close_scaled("qvel env %d" % e, tvg[0, e], tvo[0, e], ONE_STEP_RTOL)
+    assert np.array_equal(stg & 1, sto & 1)
+
+
+@pytest.mark.parametrize("mname,cfg,n", [("quadruped", 1, 33), ("cartpole", 0, 64)])
+def test_rollout_50_steps(mname, cfg, n):
+    m, tqg, tvg, tqo, tvo, stg, sto = _trajectory_parity(mname, cfg, n, 50)
+    for e in range(n):
+        assert_close_scaled("qpos env %d" % e, canon_qpos(m, tqg[-1, e]), canon_qpos(m, tqo[-1, e]), ROLLOUT_RTOL)
+        assert_close_scaled("qvel env %d" % e, tvg[-1, e], tvo[-1, e], ROLLOUT_RTOL)
+
+
+def _frame_forces(rows, nv, contacts, m):
+    """per active contact: (f_n, f_t1, f_t2) from the 4 pyramid edge forces"""
+    f = rows[:, nv + 6]
+    out, r = [], 0
+    for s in range(contacts.shape[0]):
+        if contacts[s, 0] == 0:
+            continue
+        e = f[r:r + 4]
+        mu = 1.0
+        out.append([e.sum(), mu * (e[0] - e[1]), mu * (e[2] - e[3])])
+        r += 4
+    return np.array(out)
+
+
+def test_contact_forces_match_converged_oracle():
+    m, om, states = _contact_states()
+    mc = W.quadruped()
+    mc.iterations = 100   # run the GPU Newton to its exact termination
+    checked = 0
+    for q, v, u in states:
+        run = GpuRun(mc, 4)
+        run.set_state(np.repeat(q[None], 4, 0), np.repeat(v[None], 4, 0))
+        g = run.debug(np.repeat(u[None], 4, 0), 2)
+        o = om.forward(q, v, np.zeros(18), u, solver_cap=-1)
+        if g["nrow"] == 0 or g["nrow"] != o["nrow"]:
+            continue
+        fg = _frame_forces(g["rows"], 18, g["contacts"], m)
+        fo = _frame_forces(o["rows"], 18, o["contacts"], m)
+        assert fg.shape == fo.shape
+        err = np.abs(fg - fo).max() / max(np.abs(fo).max(), 1e-9)
+        assert err <= FORCE_RTOL, err
+        checked += 1
+    assert checked >= 3
+
+
+def test_full_size_launch_sampled_envs():
+    """8192 quadrupeds in the benchmark's launch configuration; 16 sampled envs against the oracle."""
+    m = W.quadruped()
+    om = O.OracleModel(m)
+    n = 8192
+    q0, v0 = W.initial_state(m, 1, n)
+    U = W.actions(m, 1, n, 0, 3)
+    run = GpuRun(m, n)
+    run.set_state(q0, v0)
+    run.rollout(U, 5)
+    qg, vg, _ = run.get()
+    idx = np.random.default_rng(1).choice(n, 16, replace=False)
+    idx[0], idx[1] = 0, n - 1
+    qo, vo, _, _ = om.rollout(q0[idx], v0[idx], U[:, idx], 5, nthreads=8)
+    for k, e in enumerate(idx):
+        assert_close_scaled("qpos env %d" % e, canon_qpos(m, qg[e]), canon_qpos(m, qo[k]), 1e-4)
+        assert_close_scaled("qvel env %d" % e, vg[e], vo[k], 1e-4)
+    assert np.all(np.isfinite(qg)) and np.all(np.isfinite(vg))
+
+
+@pytest.mark.parametrize("n,epc", [(1, 0), (33, 0), (33, 1), (35, 3), (64, 8)])
+def test_ragged_and_tile_shapes(n, epc):
+    m, tqg, tvg, tqo, tvo, _, _ = _trajectory_parity("quadruped", 1, n, 2, envs_per_cta=epc)
+    for e in range(n):
+        assert_close_scaled("qpos", canon_qpos(m, tqg[-1, e]), canon_qpos(m, tqo[-1, e]), 1e-4)
+        assert_close_scaled("qvel", tvg[-1, e], tvo[-1, e], 1e-4)
+
+
+def test_status_bits_nan_and_warm_reset():
+    m = W.quadruped()
+    n = 8
+    q0, v0 = W.initial_state(m, 1, n)
+    q0[3, 2] = np.nan          # env 3: non-finite position
+    warm = np.zeros((n, 18), np.float32)
+    warm[5, 4] = np.inf        # env 5: non-finite warm start
+    run = GpuRun(m, n)
+    run.set_state(q0, v0, warm)
+    run.step(W.actions(m, 1, n, 0, 1)[0], 5)
+    st = run.status()
+    assert st[3] & 1
+    assert st[5] & 8 and not st[5] & 1
+    assert all(st[e] & 1 == 0 for e in range(n) if e != 3)
+
+
+def test_reset_with_mask_and_host_path():
+    import torch
+    from paper_2502_08844_b300 import core
+    m = W.quadruped()
+    n = 12
+    q0, v0 = W.initial_state(m, 1, n)
+    run = GpuRun(m, n)
+    run.set_state(q0, v0)
+    U = W.actions(m, 1, n, 0, 2)
+    run.step(U[0], 5)
+    qpos0 = run.state.qpos.clone() * 0 + torch.from_numpy(core.to_soa(q0, run.state.ld, run.batch.nq_max)).cuda()
+    qvel0 = torch.zeros_like(run.state.qvel)
+    mask = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    mask[[2, 7]] = 1
+    core.reset(run.batch, run.state, qpos0, qvel0, mask)
+    q, v, w = run.get()
+    assert np.allclose(q[2], q0[2]) and np.allclose(q[7], q0[7]) and np.all(w[[2, 7]] == 0)
+    assert not np.allclose(q[3], q0[3])
+    # host-buffer path equals the device path
+    run2 = GpuRun(m, n)
+    run2.set_state(q0, v0)
+    ctrl_h = torch.from_numpy(core.to_soa(U[0], run2.state.ld, 12)).pin_memory()
+    qh = torch.zeros((run2.batch.nq_max, run2.state.ld)).pin_memory()
+    vh = torch.zeros((run2.batch.nv_max, run2.state.ld)).pin_memory()
+    core.step_host(run2.batch, run2.state, ctrl_h, qh, vh, 5)
+    torch.cuda.synchronize()
+    run3 = GpuRun(m, n)
+    run3.set_state(q0, v0)
+    run3.step(U[0], 5)
+    q3, v3, _ = run3.get()
+    assert np.array_equal(qh.numpy()[:19, :n].T, q3.astype(np.float32))
+    assert np.array_equal(vh.numpy()[:18, :n].T, v3.astype(np.float32))
+
+
+def test_debug_substep_matches_step():
+    m = W.quadruped()
+    n = 8
+    q0, v0 = W.initial_state(m, 1, n)
+    u = W.actions(m, 1, n, 0, 1)[0]
+    r1 = GpuRun(m, n); r1.set_state(q0, v0)
+    d = r1.debug(u, 6)
+    r2 = GpuRun(m, n); r2.set_state(q0, v0)
+    r2.step(u, 1)
+    q2, v2, _ = r2.get()
+    assert np.array_equal(d["qpos_next"].astype(np.float32), q2[6].astype(np.float32))
+    assert np.array_equal(d["qvel_next"].astype(np.float32), v2[6].astype(np.float32))
