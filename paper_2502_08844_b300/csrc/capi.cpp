@@ -80,7 +80,6 @@ int pg_batch_compile(const pg_model* const* models, const int64_t* counts, int n
   if (!out) return set_error(PG_EINVAL, "out is NULL");
   *out = nullptr;
   if (!models || !counts || nmodels < 1) return set_error(PG_EINVAL, "need at least one model");
-  if (envs_per_cta < 0 || envs_per_cta > 8) return set_error(PG_EINVAL, "envs_per_cta must be 0 (default) or 1..8");
   pg_batch* b = new (std::nothrow) pg_batch();
   if (!b) return set_error(PG_ENOMEM, "host allocation failed");
   for (int k = 0; k < nmodels; k++) {
@@ -100,23 +99,38 @@ int pg_batch_compile(const pg_model* const* models, const int64_t* counts, int n
     b->blob_off.push_back(0);
   }
   if (b->n > (int64_t)1 << 31) { delete b; return set_error(PG_EINVAL, "too many environments"); }
-  int warps = envs_per_cta ? envs_per_cta : 4;
-  auto smem_for = [&](int w) { return 4 * ((size_t)b->max_blob_words + (size_t)w * b->max_ws_floats); };
-  while (warps > 1 && smem_for(warps) > kMaxSmem) {
-    if (envs_per_cta) { delete b; return set_error(PG_ECAPACITY, "envs_per_cta exceeds shared memory for these models"); }
-    warps--;
+  if (envs_per_cta < 0 || envs_per_cta > kMaxEnvsPerCta) { delete b; return set_error(PG_EINVAL, "envs_per_cta must be 0 (auto) or 1..256"); }
+  // environments per block: enough blocks to give every SM work in one wave, as many envs per
+  // block as shared memory allows (the workspace is reserved per warp of 32 environments)
+  int sms = 148, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (nmodels > kMaxModels) { delete b; return set_error(PG_ECAPACITY, "more than 8 models in one batch"); }
+  const size_t per_warp = (size_t)128 * b->max_ws_floats;
+  const size_t blob_bytes = 0;   // the model blobs travel as a kernel parameter
+  if (blob_bytes + per_warp > kMaxSmem) { delete b; return set_error(PG_ECAPACITY, "one warp's workspace exceeds shared memory"); }
+  const int warps_fit = (int)std::min<size_t>((kMaxSmem - blob_bytes) / per_warp, kMaxEnvsPerCta / 32);
+  int threads = 32;
+  for (int k = 0; k < nmodels; k++) {
+    int e = envs_per_cta ? envs_per_cta : (int)std::max<int64_t>(1, (counts[k] + sms - 1) / sms);
+    if (envs_per_cta && (e + 31) / 32 > warps_fit) { delete b; return set_error(PG_ECAPACITY, "envs_per_cta exceeds shared memory for these models"); }
+    e = std::min(e, 32 * warps_fit);
+    b->envs_per_cta.push_back(e);
+    threads = std::max(threads, (e + 31) / 32 * 32);
   }
-  if (smem_for(warps) > kMaxSmem) { delete b; return set_error(PG_ECAPACITY, "one environment's workspace exceeds shared memory"); }
-  b->warps = warps;
-  b->smem_bytes = smem_for(warps);
+  b->threads = threads;
+  b->smem_bytes = blob_bytes + (size_t)(threads / 32) * per_warp;
   std::vector<uint32_t> all;
   for (int k = 0; k < nmodels; k++) {
     b->blob_off[k] = (int)all.size();
     all.insert(all.end(), models[k]->blob.begin(), models[k]->blob.end());
   }
-  for (int k = 0; k < nmodels; k++)
-    for (int64_t e0 = 0; e0 < counts[k]; e0 += warps)
-      b->tiles.push_back(Tile{k, (int)(b->env_off[k] + e0), (int)std::min<int64_t>(warps, counts[k] - e0), 0});
+  if ((int)all.size() > kMaxParamWords) { delete b; return set_error(PG_ECAPACITY, "the batch's model tables exceed the 28 KB kernel-parameter budget"); }
+  b->blob_host = all;
+  for (int k = 0; k < nmodels; k++) {
+    const int e = b->envs_per_cta[k];
+    for (int64_t e0 = 0; e0 < counts[k]; e0 += e)
+      b->tiles.push_back(Tile{k, (int)(b->env_off[k] + e0), (int)std::min<int64_t>(e, counts[k] - e0), 0});
+  }
   b->ntiles = (int)b->tiles.size();
   cudaError_t e;
   if ((e = cudaMalloc(&b->d_blobs, all.size() * 4)) != cudaSuccess) { pg_batch_free(b); return cuda_error(e, "cudaMalloc"); }

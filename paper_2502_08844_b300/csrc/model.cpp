@@ -2,6 +2,7 @@
 // needs (levels, child lists, dof tree, packed LDL pattern, contact slots, mass properties,
 // options) and packs them into one blob of 32-bit words (layout in pg_internal.h).
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -98,27 +99,8 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
   parent[0] = -1;
   for (int b = 1; b < nbody; b++)
     if (parent[b] < 0 || parent[b] >= b) return set_error(PG_EINVAL, "body_parent violates level order (parent[i] < i)");
-  std::vector<int> level(nbody, 0), root(nbody, 0);
-  int nlevel = 1;
-  for (int b = 1; b < nbody; b++) {
-    level[b] = level[parent[b]] + 1;
-    root[b] = parent[b] == 0 ? b : root[parent[b]];
-    nlevel = std::max(nlevel, level[b] + 1);
-  }
-  std::vector<int> level_start(nlevel + 1, 0), level_body;
-  for (int L = 0; L < nlevel; L++) {
-    level_start[L] = (int)level_body.size();
-    for (int b = 0; b < nbody; b++)
-      if (level[b] == L) level_body.push_back(b);
-  }
-  level_start[nlevel] = nbody;
-  std::vector<int> child_start(nbody + 1, 0), child;
-  for (int b = 0; b < nbody; b++) {
-    child_start[b] = (int)child.size();
-    for (int c = b + 1; c < nbody; c++)
-      if (parent[c] == b) child.push_back(c);
-  }
-  child_start[nbody] = (int)child.size();
+  std::vector<int> root(nbody, 0);
+  for (int b = 1; b < nbody; b++) root[b] = parent[b] == 0 ? b : root[parent[b]];
   // ---- joints ----
   std::vector<int> jnt_type(njnt), jnt_body(njnt), qposadr(njnt), dofadr(njnt);
   std::vector<int> body_jntadr(nbody, 0), body_jntnum(nbody, 0);
@@ -269,6 +251,34 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
   std::vector<int> limit_jnt;
   for (int j = 0; j < njnt; j++)
     if (d->jnt_limited[j] && jnt_type[j] != PG_JNT_FREE) limit_jnt.push_back(j);
+  // ---- pair columns: the dofs whose contact-Jacobian column can be non-zero, i.e. the dofs on
+  // exactly one of the two bodies' chains (shared ancestors cancel), sorted deepest first, with
+  // sign +1 for geom2's side and -1 for geom1's.  When every pair's columns form one chain the
+  // Newton Hessian keeps M's ancestor pattern and is factorised like M. ----
+  std::vector<int> pcoladr(npair), pncol(npair), col_dof, col_sign, slot_pair(std::max(nslot, 1), 0);
+  int tree_hessian = 1, ncol_max = 1;
+  for (int p = 0; p < npair; p++) {
+    const int b1 = gbody[pg1[p]], b2 = gbody[pg2[p]];
+    pcoladr[p] = (int)col_dof.size();
+    for (int dof = nv - 1; dof >= 0; dof--) {
+      const bool in1 = (mask[b1] >> dof) & 1u, in2 = (mask[b2] >> dof) & 1u;
+      if (in1 == in2) continue;
+      col_dof.push_back(dof);
+      col_sign.push_back(in2 ? 1 : -1);
+    }
+    pncol[p] = (int)col_dof.size() - pcoladr[p];
+    ncol_max = std::max(ncol_max, pncol[p]);
+    for (int a = pcoladr[p] + 1; a < (int)col_dof.size(); a++) {
+      // each column must be an ancestor of the previous one
+      int x = col_dof[a - 1];
+      while (x >= 0 && x != col_dof[a]) x = dof_parent[x];
+      if (x < 0) tree_hessian = 0;
+    }
+    for (int s = pslotadr[p]; s < pslotadr[p] + pnslot[p]; s++) slot_pair[s] = p;
+  }
+  std::vector<int> root_freeadr(nbody, -1);
+  for (int j = 0; j < njnt; j++)
+    if (jnt_type[j] == PG_JNT_FREE) root_freeadr[jnt_body[j]] = qposadr[j];
   // ---- options ----
   if (!(d->timestep > 0)) return set_error(PG_EINVAL, "timestep must be > 0");
   if (d->iterations < 1) return set_error(PG_EINVAL, "iterations must be >= 1");
@@ -281,7 +291,7 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
   std::memset(&h, 0, sizeof(h));
   h.nbody = nbody; h.njnt = njnt; h.nq = nq; h.nv = nv; h.nu = nu; h.ngeom = ngeom; h.npair = npair;
   h.nslot = nslot; h.nrow_max = nrow_max; h.max_contacts = max_contacts; h.nlimited = (int)limit_jnt.size();
-  h.nlevel = nlevel; h.nL = nL; h.cap = d->iterations; h.cone = d->cone;
+  h.nL = nL; h.cap = d->iterations; h.cone = d->cone; h.tree_hessian = tree_hessian; h.ncol_max = ncol_max;
   h.h = d->timestep;
   for (int k = 0; k < 3; k++) h.grav[k] = d->gravity[k];
   {
@@ -294,11 +304,6 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
 
   Blob B;
   B.w.assign(kHdrWords, 0u);
-  std::vector<int> body_dofmask(2 * nbody);
-  for (int b = 0; b < nbody; b++) {
-    body_dofmask[2 * b] = (int)(uint32_t)(mask[b] & 0xffffffffu);
-    body_dofmask[2 * b + 1] = (int)(uint32_t)(mask[b] >> 32);
-  }
   std::vector<float> bpos(d->body_pos, d->body_pos + 3 * nbody), bquat(4 * nbody);
   for (int b = 0; b < nbody; b++) {
     double n = 0;
@@ -310,9 +315,7 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
   h.o_body_parent = B.ints(parent); h.o_body_root = B.ints(root);
   h.o_body_jntadr = B.ints(body_jntadr); h.o_body_jntnum = B.ints(body_jntnum);
   h.o_body_pos = B.floats(bpos); h.o_body_quat = B.floats(bquat); h.o_body_mass = B.floats(mass);
-  h.o_body_ipos = B.floats(ipos); h.o_body_inertia = B.floats(inertia); h.o_body_dofmask = B.ints(body_dofmask);
-  h.o_level_start = B.ints(level_start); h.o_level_body = B.ints(level_body);
-  h.o_child_start = B.ints(child_start); h.o_child = B.ints(child);
+  h.o_body_ipos = B.floats(ipos); h.o_body_inertia = B.floats(inertia); h.o_root_freeadr = B.ints(root_freeadr);
   h.o_jnt_type = B.ints(jnt_type); h.o_jnt_qposadr = B.ints(qposadr); h.o_jnt_dofadr = B.ints(dofadr);
   h.o_jnt_pos = B.floats(jpos); h.o_jnt_axis = B.floats(jaxis); h.o_jnt_range = B.floats(jrange);
   h.o_dof_body = B.ints(dof_body); h.o_dof_depth = B.ints(depth); h.o_dof_rowadr = B.ints(rowadr);
@@ -321,6 +324,8 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
   h.o_geom_quat = B.floats(gquat); h.o_geom_size = B.floats(gsize);
   h.o_pair_g1 = B.ints(pg1); h.o_pair_g2 = B.ints(pg2); h.o_pair_friction = B.floats(pfric);
   h.o_pair_condim = B.ints(pcondim); h.o_pair_slotadr = B.ints(pslotadr); h.o_pair_nslot = B.ints(pnslot);
+  h.o_pair_coladr = B.ints(pcoladr); h.o_pair_ncol = B.ints(pncol); h.o_col_dof = B.ints(col_dof);
+  h.o_col_sign = B.ints(col_sign); h.o_slot_pair = B.ints(slot_pair);
   h.o_act_type = B.ints(atype); h.o_act_dof = B.ints(adof); h.o_act_qposadr = B.ints(aqadr);
   h.o_act_gear = B.floats(agear); h.o_act_kp = B.floats(akp); h.o_act_kd = B.floats(akd);
   h.o_act_ctrllimited = B.ints(aclim); h.o_act_range = B.floats(arange);
@@ -328,33 +333,42 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
   while (B.w.size() % 4) B.w.push_back(0u);
   h.words = (int)B.w.size();
 
-  // ---- per-env workspace layout (floats) ----
-  int o = 0;
-  auto take = [&](int n) { int r = o; o = align4(o + n); return r; };
-  h.w_qpos = take(nq); h.w_qvel = take(nv); h.w_warm = take(nv); h.w_ctrl = take(std::max(nu, 1));
-  h.w_M = take(nv * nv); h.w_L = take(nL); h.w_D = take(nv); h.w_bias = take(nv); h.w_passive = take(nv);
-  h.w_act = take(nv); h.w_a0 = take(nv); h.w_vtmp = take(nv); h.w_con = take(14 * std::max(nslot, 1));
-  const int u1 = o;
-  h.w_xpos = take(3 * nbody); h.w_xquat = take(4 * nbody); h.w_xmat = take(9 * nbody); h.w_xipos = take(3 * nbody);
-  h.w_janchor = take(3 * std::max(njnt, 1)); h.w_jaxis = take(3 * std::max(njnt, 1));
-  h.w_gpos = take(3 * std::max(ngeom, 1)); h.w_gmat = take(9 * std::max(ngeom, 1));
-  h.w_cdof = take(6 * nv); h.w_cinert = take(10 * nbody);
-  const int end_kin = o;
-  o = u1;
-  h.w_H = take(nv * nv); h.w_a = take(nv); h.w_g = take(nv); h.w_p = take(nv); h.w_Mp = take(nv);
-  h.w_Z = take(std::max(nrow_max, 1) * nv);
-  const int end_newton = o;
-  const int u2 = std::max(end_kin, end_newton);
-  o = u2;
-  h.w_crb = take(10 * nbody); h.w_cvel = take(6 * nbody); h.w_cacc = take(6 * nbody); h.w_cfrc = take(6 * nbody);
-  h.w_F = take(6 * nv);
-  const int end_dyn = o;
-  o = u2;
-  const int R = std::max(nrow_max, 1);
-  h.w_J = take(R * nv); h.w_rr = take(R); h.w_rv = take(R); h.w_aref = take(R); h.w_rD = take(R); h.w_Ahat = take(R);
-  h.w_imp = take(R); h.w_jar = take(R); h.w_Jp = take(R); h.w_force = take(R); h.w_rowslot = take(R);
-  const int end_rows = o;
-  h.ws_floats = std::max(end_dyn, end_rows);
+  // ---- per-env workspace: buffers with the phase interval in which they are live, packed
+  // first-fit.  Phases: 0 state, 1 kinematics, 2 RNEA, 3 CRBA, 4 LDL, 5 smooth acceleration,
+  // 6 collision, 7 Jacobians, 8 row parameters, 9 Newton, 10 integration / diagnostics. ----
+  struct Buf { int* off; int size; int birth, death; };
+  const int R = std::max(nrow_max, 1), C = std::max(max_contacts, 1);
+  const int Hsize = tree_hessian ? 0 : nv * nv;
+  std::vector<Buf> bufs = {
+      {&h.w_qpos, nq, 0, 10}, {&h.w_qvel, nv, 0, 10}, {&h.w_warm, nv, 0, 10},
+      {&h.w_xpos, 3 * nbody, 1, 7}, {&h.w_xquat, 4 * nbody, 1, 7}, {&h.w_cdof, 6 * nv, 1, 7},
+      {&h.w_cinert, 10 * nbody, 1, 3}, {&h.w_cvel, 6 * nbody, 2, 2}, {&h.w_cacc, 6 * nbody, 2, 2},
+      {&h.w_cfrc, 6 * nbody, 2, 2}, {&h.w_bias, nv, 2, 5}, {&h.w_M, nL, 3, 9}, {&h.w_L, nL, 4, 9},
+      {&h.w_a0, nv, 5, 9}, {&h.w_con, kConFloats * C, 6, 10}, {&h.w_J, 3 * ncol_max * C, 7, 10},
+      {&h.w_gcol, ncol_max * C, 7, 10}, {&h.w_lsgn, std::max((int)limit_jnt.size(), 1), 7, 10},
+      {&h.w_gmu, C, 8, 10}, {&h.w_gcond, C, 8, 10},
+      {&h.w_z, 3 * nv, 8, 8}, {&h.w_rr, R, 8, 10}, {&h.w_rv, R, 8, 10},
+      {&h.w_Ahat, R, 8, 10}, {&h.w_imp, R, 8, 10}, {&h.w_aref, R, 8, 10}, {&h.w_rD, R, 8, 10},
+      {&h.w_jar, R, 9, 10}, {&h.w_Jp, R, 9, 9}, {&h.w_a, nv, 9, 10}, {&h.w_g, nv, 9, 9}, {&h.w_p, nv, 9, 9},
+      {&h.w_t, nv, 9, 9}, {&h.w_H, Hsize, 9, 9}};
+  std::vector<std::array<int, 4>> placed;   // offset, size, birth, death
+  int ws = 0;
+  for (Buf& b : bufs) {
+    int off = 0;
+    bool moved = true;
+    while (moved) {
+      moved = false;
+      for (auto& q : placed) {
+        const bool overlap_t = !(b.death < q[2] || q[3] < b.birth);
+        const bool overlap_s = off < q[0] + q[1] && q[0] < off + b.size;
+        if (overlap_t && overlap_s) { off = q[0] + q[1]; moved = true; }
+      }
+    }
+    *b.off = off;
+    placed.push_back({off, b.size, b.birth, b.death});
+    ws = std::max(ws, off + b.size);
+  }
+  h.ws_floats = std::max(ws, 1);
   // ---- debug record layout ----
   int q = 0;
   auto dbg = [&](int n) { int r = q; q += n; return r; };

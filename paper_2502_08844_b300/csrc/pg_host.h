@@ -19,7 +19,8 @@ struct pg_batch {
   std::vector<int64_t> counts, env_off;
   int64_t n = 0;
   int nq_max = 0, nv_max = 0, nu_max = 0;
-  int warps = 4;                   // environments (one warp each) per thread block
+  int threads = 32;                // threads per block (one environment per thread)
+  std::vector<int> envs_per_cta;   // per model
   int max_ws_floats = 0, max_blob_words = 0, max_debug = 0;
   size_t smem_bytes = 0;
   uint32_t* d_blobs = nullptr;     // all models' blobs, concatenated
@@ -27,6 +28,7 @@ struct pg_batch {
   pg::Tile* d_tiles = nullptr;
   int ntiles = 0;
   std::vector<int> blob_off;
+  std::vector<uint32_t> blob_host;   // all models' blobs, concatenated (passed as a kernel parameter)
   std::vector<pg::Tile> tiles;
   // staging buffer of the host-buffer path (allocated on its first use)
   float* d_ctrl_stage = nullptr;

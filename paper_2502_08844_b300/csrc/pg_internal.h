@@ -1,46 +1,53 @@
 // Internal layout shared by the host model compiler and the step kernel.
 //
-// A compiled model is one flat blob of 32-bit words: a fixed header (counts, options and the
-// word offsets of every table) followed by the tables.  Each thread block copies its model's
-// blob into shared memory once and reads every table from there.  The blob also records the
-// per-environment shared-memory workspace layout (float offsets), computed on the host.
+// A compiled model is one flat blob of 32-bit words: a fixed header (counts, options, the word
+// offsets of every table and the per-environment workspace layout) followed by the tables.
+// The blobs of a batch's models travel to the step kernel as a read-only kernel parameter; all
+// threads of a warp step different environments of the same model, so every table read is a
+// uniform (broadcast) read that never aliases the workspace.
+//
+// Per-environment workspaces are structure-of-arrays across the 32 lanes of a warp: element i
+// of lane l lives at [i * 32 + l], so lanes never conflict on a shared-memory bank whatever
+// element each of them touches.  The host assigns every buffer an interval of the substep's
+// phases and packs buffers whose intervals do not overlap into the same space.
 #pragma once
 #include <stdint.h>
 
 namespace pg {
 
 // compiled kernel limits
-constexpr int kMaxNv = 64;       // ancestor-dof masks are 64-bit
+constexpr int kMaxNv = 64;
 constexpr int kMaxBody = 64;
 constexpr int kMaxSlot = 64;
-constexpr int kMaxRow = 128;     // active-set masks are 4 x 32 bits
+constexpr int kMaxRow = 128;     // active-set masks are 4 x 32 bits per environment
+constexpr int kMaxEnvsPerCta = 256;
+constexpr int kMaxModels = 8;          // models per batch (their blobs travel as a kernel parameter)
+constexpr int kMaxParamWords = 7168;   // 28 KB of blob words in the kernel's parameter space
 
 struct ModelHdr {
   // counts
-  int nbody, njnt, nq, nv, nu, ngeom, npair, nslot, nrow_max, max_contacts, nlimited, nlevel, nL;
-  int cap, cone;
+  int nbody, njnt, nq, nv, nu, ngeom, npair, nslot, nrow_max, max_contacts, nlimited, nL;
+  int cap, cone, tree_hessian, ncol_max;
   // options (float32)
   float h, grav[3], kref, bref, solimp[5], margin;
   // table offsets (words from the blob start)
   int o_body_parent, o_body_root, o_body_jntadr, o_body_jntnum, o_body_pos, o_body_quat, o_body_mass,
-      o_body_ipos, o_body_inertia, o_body_dofmask, o_level_start, o_level_body, o_child_start, o_child;
+      o_body_ipos, o_body_inertia, o_root_freeadr;
   int o_jnt_type, o_jnt_qposadr, o_jnt_dofadr, o_jnt_pos, o_jnt_axis, o_jnt_range;
   int o_dof_body, o_dof_depth, o_dof_rowadr, o_dof_damping, o_dof_armature, o_Lcol;
   int o_geom_type, o_geom_body, o_geom_pos, o_geom_quat, o_geom_size;
-  int o_pair_g1, o_pair_g2, o_pair_friction, o_pair_condim, o_pair_slotadr, o_pair_nslot;
+  int o_pair_g1, o_pair_g2, o_pair_friction, o_pair_condim, o_pair_slotadr, o_pair_nslot, o_pair_coladr,
+      o_pair_ncol, o_col_dof, o_col_sign, o_slot_pair;
   int o_act_type, o_act_dof, o_act_qposadr, o_act_gear, o_act_kp, o_act_kd, o_act_ctrllimited, o_act_range;
   int o_limit_jnt;
   int words;   // total blob size
-  // per-env workspace layout (float offsets from the env's workspace base)
+  // per-environment workspace layout (element offsets, see above)
   int ws_floats;
-  int w_qpos, w_qvel, w_warm, w_ctrl;
-  int w_M, w_L, w_D, w_bias, w_passive, w_act, w_a0, w_vtmp, w_con;
-  // union 1: kinematics (until the rows are built) / Newton + row solves (afterwards)
-  int w_xpos, w_xquat, w_xmat, w_xipos, w_janchor, w_jaxis, w_gpos, w_gmat, w_cdof, w_cinert;
-  int w_H, w_a, w_g, w_p, w_Mp, w_Z;
-  // union 2: dynamics temporaries (CRBA / RNEA) / constraint rows
-  int w_crb, w_cvel, w_cacc, w_cfrc, w_F;
-  int w_J, w_rr, w_rv, w_aref, w_rD, w_Ahat, w_imp, w_jar, w_Jp, w_force, w_rowslot;
+  int w_qpos, w_qvel, w_warm;
+  int w_xpos, w_xquat, w_cdof, w_cinert, w_cvel, w_cacc, w_cfrc, w_bias;
+  int w_M, w_L, w_a0, w_con, w_J, w_z;
+  int w_gcol, w_gmu, w_gcond, w_lsgn, w_rr, w_rv, w_Ahat, w_imp, w_aref, w_rD, w_jar, w_Jp;
+  int w_a, w_g, w_p, w_t, w_H;
   int debug_floats;
   int dbg_xpos, dbg_xmat, dbg_xcom, dbg_M, dbg_bias, dbg_passive, dbg_act, dbg_a0, dbg_con, dbg_nrow, dbg_rows,
       dbg_qacc, dbg_iter, dbg_status, dbg_qpos, dbg_qvel;
@@ -48,6 +55,9 @@ struct ModelHdr {
 
 constexpr int kHdrWords = (int)(sizeof(ModelHdr) / 4);
 static_assert(sizeof(ModelHdr) % 4 == 0, "header must be whole words");
+
+// per active contact in the workspace: slot, dist, pos[3], n[3]
+constexpr int kConFloats = 8;
 
 // one thread block's work: `count` consecutive envs starting at `env0` of model `model`
 struct Tile {

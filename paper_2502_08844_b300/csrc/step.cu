@@ -1,29 +1,31 @@
-// Fused batched physics step for sm_103a: one warp per environment, one thread block per tile
-// of consecutive environments of one model.  The block copies its model blob into shared
-// memory, stages its environments' state in a per-warp shared-memory workspace, runs all
-// substeps on chip, and writes the state back.  FP32 CUDA-core arithmetic throughout (the
-// per-environment matrices are small and not a dense contraction, so no tensor cores).
+// Fused batched physics step for sm_103a: one thread per environment.
 //
-// Per substep (all 32 lanes of a warp cooperate; level-parallel tree sweeps):
-//   FK -> body COM / spatial inertia / geom frames / motion subspaces (cdof)
-//   -> CRBA (composite inertias, dense symmetric M) -> tree-sparse LDL^T of M
-//   -> RNEA bias forces -> passive + actuator forces -> a0 = M^-1 (tau - c)
-//   -> collision over the static pair list -> contact / limit rows, Ahat = (J M^-1 J^T)_ii
-//   -> Newton on the convex soft-constraint cost (dense H, Cholesky, exact line search)
-//   -> semi-implicit Euler.
-// Spatial vectors are (angular; linear) in world axes about each tree's reference point
-// o = position of the tree's root body (a body whose parent is the world).
+// A thread block holds up to 256 environments of one model (a tile); each warp steps 32 of them
+// in lockstep through the same generic loops over the model's tables, which sit in shared
+// memory and are read as broadcasts.  Every environment's working set (state, kinematics,
+// packed mass matrix and its LDL^T factor, contacts, constraint rows, Newton vectors) lives in
+// a structure-of-arrays shared-memory workspace, element i of lane l at [32 i + l], so no two
+// lanes ever hit the same bank.  All substeps of a control step run on chip; state is read
+// once and written once, coalesced across environments.  FP32 CUDA-core arithmetic throughout
+// (the per-environment matrices are small and not a dense contraction, so no tensor cores).
+//
+// Per substep: kinematics (frames, motion subspaces cdof and spatial inertias about each tree's
+// reference point o) -> RNEA bias forces -> CRBA mass matrix (packed on the ancestor pattern)
+// -> tree-sparse LDL^T and a0 = M^-1 (tau - c) -> collision over the static pair list ->
+// contact / joint-limit rows with exact Ahat = (J M^-1 J^T)_rr -> Newton on the convex
+// soft-constraint cost (Hessian on M's pattern when every pair lies on one kinematic chain,
+// dense otherwise; exact line search) -> semi-implicit Euler.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+
+#include <cstring>
 
 #include "pg_host.h"
 #include "pg_internal.h"
 
 namespace pg {
 namespace {
-
-constexpr unsigned kFull = 0xffffffffu;
 
 // ---------------------------------------------------------------------------------------
 // small vector algebra
@@ -75,378 +77,8 @@ __device__ __forceinline__ float3 mat_tmul(const float* R, float3 v) {   // R^T 
                      R[2] * v.x + R[5] * v.y + R[8] * v.z);
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-  return v;
-}
-__device__ __forceinline__ float warp_max(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
-  return v;
-}
-__device__ __forceinline__ float warp_min(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, o));
-  return v;
-}
-
-// spatial inertia (about o, world axes) times a motion vector: ci = (Ixx Iyy Izz Ixy Ixz Iyz, h, m)
-__device__ __forceinline__ void inert_mul(const float* ci, float3 w, float3 v, float3& fa, float3& fl) {
-  float3 h = make_float3(ci[6], ci[7], ci[8]);
-  fa = make_float3(ci[0] * w.x + ci[3] * w.y + ci[4] * w.z, ci[3] * w.x + ci[1] * w.y + ci[5] * w.z,
-                   ci[4] * w.x + ci[5] * w.y + ci[2] * w.z) + cross3(h, v);
-  fl = v * ci[9] - cross3(h, w);
-}
-
 // ---------------------------------------------------------------------------------------
-// environment context
-// ---------------------------------------------------------------------------------------
-struct Env {
-  const ModelHdr* h;
-  const int* I;
-  const float* F;
-  float* w;
-  int lane;
-};
-
-#define MI(name, i) (e.I[e.h->o_##name + (i)])
-#define MF(name, i) (e.F[e.h->o_##name + (i)])
-#define WS(name) (e.w + e.h->w_##name)
-
-// ---------------------------------------------------------------------------------------
-// kinematics
-// ---------------------------------------------------------------------------------------
-__device__ void fk(const Env& e) {
-  const ModelHdr& h = *e.h;
-  float *xpos = WS(xpos), *xquat = WS(xquat), *xmat = WS(xmat), *janc = WS(janchor), *jax = WS(jaxis);
-  const float* qpos = WS(qpos);
-  if (e.lane == 0) {
-    st3(xpos, make_float3(0.f, 0.f, 0.f));
-    stq(xquat, Quat{1.f, 0.f, 0.f, 0.f});
-    float* R = xmat;
-    R[0] = 1; R[1] = 0; R[2] = 0; R[3] = 0; R[4] = 1; R[5] = 0; R[6] = 0; R[7] = 0; R[8] = 1;
-  }
-  __syncwarp();
-  for (int L = 1; L < h.nlevel; L++) {
-    const int s = MI(level_start, L), t = MI(level_start, L + 1);
-    for (int k = s + e.lane; k < t; k += 32) {
-      const int b = MI(level_body, k), p = MI(body_parent, b);
-      Quat qp = ldq(xquat + 4 * p);
-      float3 x = ld3(xpos + 3 * p) + qrot(qp, ld3(&MF(body_pos, 3 * b)));
-      Quat q = qmul(qp, ldq(&MF(body_quat, 4 * b)));
-      const int j0 = MI(body_jntadr, b), nj = MI(body_jntnum, b);
-      for (int j = j0; j < j0 + nj; j++) {
-        const int type = MI(jnt_type, j), qa = MI(jnt_qposadr, j);
-        if (type == PG_JNT_FREE) {
-          x = ld3(qpos + qa);
-          q = qnormalize(Quat{qpos[qa + 3], qpos[qa + 4], qpos[qa + 5], qpos[qa + 6]});
-          st3(janc + 3 * j, x);
-          st3(jax + 3 * j, make_float3(0.f, 0.f, 0.f));
-        } else {
-          const float3 lp = ld3(&MF(jnt_pos, 3 * j)), la = ld3(&MF(jnt_axis, 3 * j));
-          const float3 anchor = x + qrot(q, lp), axis = qrot(q, la);
-          st3(janc + 3 * j, anchor);
-          st3(jax + 3 * j, axis);
-          if (type == PG_JNT_HINGE) {
-            float sn, cs;
-            sincosf(0.5f * qpos[qa], &sn, &cs);
-            q = qmul(q, Quat{cs, la.x * sn, la.y * sn, la.z * sn});
-            x = anchor - qrot(q, lp);
-          } else {
-            x = x + axis * qpos[qa];
-          }
-        }
-      }
-      q = qnormalize(q);
-      st3(xpos + 3 * b, x);
-      stq(xquat + 4 * b, q);
-      qmat(q, xmat + 9 * b);
-    }
-    __syncwarp();
-  }
-}
-
-// COM, spatial inertia about the tree reference point, geom frames and motion subspaces
-__device__ void derived(const Env& e) {
-  const ModelHdr& h = *e.h;
-  const float *xpos = WS(xpos), *xmat = WS(xmat), *xquat = WS(xquat);
-  float *xipos = WS(xipos), *cinert = WS(cinert), *gpos = WS(gpos), *gmat = WS(gmat), *cdof = WS(cdof);
-  for (int b = 1 + e.lane; b < h.nbody; b += 32) {
-    const float* R = xmat + 9 * b;
-    const float3 o = ld3(xpos + 3 * MI(body_root, b));
-    const float3 com = ld3(xpos + 3 * b) + mat_mul(R, ld3(&MF(body_ipos, 3 * b)));
-    st3(xipos + 3 * b, com);
-    const float m = MF(body_mass, b);
-    const float* In = &MF(body_inertia, 6 * b);
-    // I_world = R I_body R^T
-    float Ib[9] = {In[0], In[3], In[4], In[3], In[1], In[5], In[4], In[5], In[2]};
-    float T[9];
-#pragma unroll
-    for (int r = 0; r < 3; r++)
-#pragma unroll
-      for (int c = 0; c < 3; c++) T[3 * r + c] = R[3 * r] * Ib[c] + R[3 * r + 1] * Ib[3 + c] + R[3 * r + 2] * Ib[6 + c];
-    float Iw[6];
-    Iw[0] = T[0] * R[0] + T[1] * R[1] + T[2] * R[2];
-    Iw[1] = T[3] * R[3] + T[4] * R[4] + T[5] * R[5];
-    Iw[2] = T[6] * R[6] + T[7] * R[7] + T[8] * R[8];
-    Iw[3] = T[0] * R[3] + T[1] * R[4] + T[2] * R[5];
-    Iw[4] = T[0] * R[6] + T[1] * R[7] + T[2] * R[8];
-    Iw[5] = T[3] * R[6] + T[4] * R[7] + T[5] * R[8];
-    const float3 c = com - o;
-    const float c2 = dot3(c, c);
-    float* ci = cinert + 10 * b;
-    ci[0] = Iw[0] + m * (c2 - c.x * c.x);
-    ci[1] = Iw[1] + m * (c2 - c.y * c.y);
-    ci[2] = Iw[2] + m * (c2 - c.z * c.z);
-    ci[3] = Iw[3] - m * c.x * c.y;
-    ci[4] = Iw[4] - m * c.x * c.z;
-    ci[5] = Iw[5] - m * c.y * c.z;
-    ci[6] = m * c.x; ci[7] = m * c.y; ci[8] = m * c.z;
-    ci[9] = m;
-  }
-  for (int g = e.lane; g < h.ngeom; g += 32) {
-    const int b = MI(geom_body, g);
-    Quat qb = ldq(xquat + 4 * b);
-    st3(gpos + 3 * g, ld3(xpos + 3 * b) + qrot(qb, ld3(&MF(geom_pos, 3 * g))));
-    qmat(qnormalize(qmul(qb, ldq(&MF(geom_quat, 4 * g)))), gmat + 9 * g);
-  }
-  for (int d = e.lane; d < h.nv; d += 32) {
-    const int b = MI(dof_body, d);
-    const float3 o = ld3(xpos + 3 * MI(body_root, b));
-    // the joint owning this dof: the last joint of b whose dofadr <= d
-    const int j0 = MI(body_jntadr, b), nj = MI(body_jntnum, b);
-    int j = j0;
-    for (int jj = j0; jj < j0 + nj; jj++)
-      if (MI(jnt_dofadr, jj) <= d) j = jj;
-    const int type = MI(jnt_type, j);
-    float3 ang, lin;
-    if (type == PG_JNT_FREE) {
-      const int k = d - MI(jnt_dofadr, j);
-      if (k < 3) {
-        ang = make_float3(0.f, 0.f, 0.f);
-        lin = make_float3(k == 0 ? 1.f : 0.f, k == 1 ? 1.f : 0.f, k == 2 ? 1.f : 0.f);
-      } else {
-        ang = mat_col(xmat + 9 * b, k - 3);
-        lin = cross3(ang, o - ld3(xpos + 3 * b));
-      }
-    } else if (type == PG_JNT_HINGE) {
-      ang = ld3(WS(jaxis) + 3 * j);
-      lin = cross3(ang, o - ld3(WS(janchor) + 3 * j));
-    } else {
-      ang = make_float3(0.f, 0.f, 0.f);
-      lin = ld3(WS(jaxis) + 3 * j);
-    }
-    st3(cdof + 6 * d, ang);
-    st3(cdof + 6 * d + 3, lin);
-  }
-  __syncwarp();
-}
-
-// ---------------------------------------------------------------------------------------
-// CRBA: composite inertias (backward level sweep), M_ji = cdof_i . (Ic(body j) cdof_j) for i on
-// j's dof chain; armature on the diagonal.  Dense symmetric M plus the packed copy that the
-// LDL factorisation works on (row j: j, parent(j), grandparent(j), ...).
-// ---------------------------------------------------------------------------------------
-__device__ void crba(const Env& e) {
-  const ModelHdr& h = *e.h;
-  float *crb = WS(crb), *Fv = WS(F), *M = WS(M), *Lp = WS(L);
-  const float *cinert = WS(cinert), *cdof = WS(cdof);
-  for (int i = e.lane; i < 10 * h.nbody; i += 32) crb[i] = cinert[i];
-  for (int i = e.lane; i < h.nv * h.nv; i += 32) M[i] = 0.f;
-  __syncwarp();
-  for (int L = h.nlevel - 2; L >= 1; L--) {
-    const int s = MI(level_start, L), t = MI(level_start, L + 1);
-    for (int k = s + e.lane; k < t; k += 32) {
-      const int p = MI(level_body, k);
-      float acc[10];
-#pragma unroll
-      for (int i = 0; i < 10; i++) acc[i] = crb[10 * p + i];
-      for (int c = MI(child_start, p); c < MI(child_start, p + 1); c++) {
-        const int ch = MI(child, c);
-#pragma unroll
-        for (int i = 0; i < 10; i++) acc[i] += crb[10 * ch + i];
-      }
-#pragma unroll
-      for (int i = 0; i < 10; i++) crb[10 * p + i] = acc[i];
-    }
-    __syncwarp();
-  }
-  for (int d = e.lane; d < h.nv; d += 32) {
-    float3 fa, fl;
-    inert_mul(crb + 10 * MI(dof_body, d), ld3(cdof + 6 * d), ld3(cdof + 6 * d + 3), fa, fl);
-    st3(Fv + 6 * d, fa);
-    st3(Fv + 6 * d + 3, fl);
-  }
-  __syncwarp();
-  const int nv = h.nv;
-  for (int j = e.lane; j < nv; j += 32) {
-    const float3 fa = ld3(Fv + 6 * j), fl = ld3(Fv + 6 * j + 3);
-    const int r0 = MI(dof_rowadr, j), n = MI(dof_depth, j) + 1;
-    for (int t = 0; t < n; t++) {
-      const int i = MI(Lcol, r0 + t);
-      float v = dot3(ld3(cdof + 6 * i), fa) + dot3(ld3(cdof + 6 * i + 3), fl);
-      if (t == 0) v += MF(dof_armature, j);
-      M[j * nv + i] = v;
-      M[i * nv + j] = v;
-      Lp[r0 + t] = v;
-    }
-  }
-  __syncwarp();
-}
-
-// In-place tree-sparse factorisation M = L^T D L (L unit lower triangular on the ancestor
-// pattern, no fill-in): for k = nv-1 .. 0, with d = D_k = M_kk, the entries of row k become
-// L_ki = M_ki / d and every ancestor pair (i, j) of k (j on i's chain) is updated
-// M_ij -= L_ki M_kj.  Lane t handles the t-th ancestor row of k.
-__device__ void ldl_factor(const Env& e) {
-  const ModelHdr& h = *e.h;
-  float *Lp = WS(L), *D = WS(D), *tmp = WS(vtmp);
-  for (int k = h.nv - 1; k >= 0; k--) {
-    const int r0 = MI(dof_rowadr, k), dk = MI(dof_depth, k);
-    const float diag = Lp[r0];
-    for (int t = e.lane + 1; t <= dk; t += 32) {
-      const float lkt = Lp[r0 + t] / diag;
-      tmp[t] = lkt;
-      const int i = MI(Lcol, r0 + t), ri = MI(dof_rowadr, i);
-      for (int s = t; s <= dk; s++) Lp[ri + (s - t)] -= lkt * Lp[r0 + s];
-    }
-    __syncwarp();
-    for (int t = e.lane + 1; t <= dk; t += 32) Lp[r0 + t] = tmp[t];
-    if (e.lane == 0) D[k] = diag;
-    __syncwarp();
-  }
-}
-
-// x <- M^-1 x with the packed factor (one lane; x in shared memory)
-__device__ void ldl_solve_lane(const Env& e, float* x) {
-  const ModelHdr& h = *e.h;
-  const float *Lp = WS(L), *D = WS(D);
-  for (int k = h.nv - 1; k >= 0; k--) {
-    const int r0 = MI(dof_rowadr, k), dk = MI(dof_depth, k);
-    const float xk = x[k];
-    for (int t = 1; t <= dk; t++) x[MI(Lcol, r0 + t)] -= Lp[r0 + t] * xk;
-  }
-  for (int k = 0; k < h.nv; k++) x[k] /= D[k];
-  for (int k = 0; k < h.nv; k++) {
-    const int r0 = MI(dof_rowadr, k), dk = MI(dof_depth, k);
-    float s = x[k];
-    for (int t = 1; t <= dk; t++) s -= Lp[r0 + t] * x[MI(Lcol, r0 + t)];
-    x[k] = s;
-  }
-}
-
-// ---------------------------------------------------------------------------------------
-// RNEA bias forces c(q, qdot): velocities and bias accelerations outward (the world
-// accelerates by -gravity), body forces I a + v x* I v, accumulated inward, projected on cdof.
-// Serial joints on one body are a chain of massless frames; a free joint's three rotational
-// dofs all use the velocity after its translation (their axes move with the body).
-// ---------------------------------------------------------------------------------------
-__device__ __forceinline__ void cross_motion(float3 w, float3 v, float3 a, float3 b, float3& ra, float3& rl) {
-  ra = cross3(w, a);
-  rl = cross3(w, b) + cross3(v, a);
-}
-
-__device__ void rnea(const Env& e) {
-  const ModelHdr& h = *e.h;
-  float *cvel = WS(cvel), *cacc = WS(cacc), *cfrc = WS(cfrc), *bias = WS(bias);
-  const float *cdof = WS(cdof), *cinert = WS(cinert), *qvel = WS(qvel);
-  if (e.lane == 0) {
-    for (int i = 0; i < 6; i++) cvel[i] = 0.f;
-    cacc[0] = cacc[1] = cacc[2] = 0.f;
-    cacc[3] = -h.grav[0]; cacc[4] = -h.grav[1]; cacc[5] = -h.grav[2];
-  }
-  __syncwarp();
-  for (int L = 1; L < h.nlevel; L++) {
-    const int s = MI(level_start, L), t = MI(level_start, L + 1);
-    for (int k = s + e.lane; k < t; k += 32) {
-      const int b = MI(level_body, k), p = MI(body_parent, b);
-      float3 w = ld3(cvel + 6 * p), v = ld3(cvel + 6 * p + 3), aw = ld3(cacc + 6 * p), av = ld3(cacc + 6 * p + 3);
-      const int j0 = MI(body_jntadr, b), nj = MI(body_jntnum, b);
-      for (int j = j0; j < j0 + nj; j++) {
-        const int d0 = MI(jnt_dofadr, j);
-        if (MI(jnt_type, j) == PG_JNT_FREE) {
-          v = v + make_float3(qvel[d0], qvel[d0 + 1], qvel[d0 + 2]);   // world-axis translation
-          float3 dw = make_float3(0.f, 0.f, 0.f), dv = dw;
-          for (int k3 = 3; k3 < 6; k3++) {
-            dw = dw + ld3(cdof + 6 * (d0 + k3)) * qvel[d0 + k3];
-            dv = dv + ld3(cdof + 6 * (d0 + k3) + 3) * qvel[d0 + k3];
-          }
-          float3 ra, rl;
-          cross_motion(w, v, dw, dv, ra, rl);
-          aw = aw + ra; av = av + rl;
-          w = w + dw; v = v + dv;
-        } else {
-          const float qd = qvel[d0];
-          const float3 dw = ld3(cdof + 6 * d0) * qd, dv = ld3(cdof + 6 * d0 + 3) * qd;
-          float3 ra, rl;
-          cross_motion(w, v, dw, dv, ra, rl);
-          aw = aw + ra; av = av + rl;
-          w = w + dw; v = v + dv;
-        }
-      }
-      st3(cvel + 6 * b, w); st3(cvel + 6 * b + 3, v);
-      st3(cacc + 6 * b, aw); st3(cacc + 6 * b + 3, av);
-      // f = I a + v x* (I v)
-      float3 fa, fl, ia, il;
-      inert_mul(cinert + 10 * b, aw, av, fa, fl);
-      inert_mul(cinert + 10 * b, w, v, ia, il);
-      fa = fa + cross3(w, ia) + cross3(v, il);
-      fl = fl + cross3(w, il);
-      st3(cfrc + 6 * b, fa); st3(cfrc + 6 * b + 3, fl);
-    }
-    __syncwarp();
-  }
-  for (int L = h.nlevel - 2; L >= 1; L--) {
-    const int s = MI(level_start, L), t = MI(level_start, L + 1);
-    for (int k = s + e.lane; k < t; k += 32) {
-      const int p = MI(level_body, k);
-      float acc[6];
-#pragma unroll
-      for (int i = 0; i < 6; i++) acc[i] = cfrc[6 * p + i];
-      for (int c = MI(child_start, p); c < MI(child_start, p + 1); c++) {
-        const int ch = MI(child, c);
-#pragma unroll
-        for (int i = 0; i < 6; i++) acc[i] += cfrc[6 * ch + i];
-      }
-#pragma unroll
-      for (int i = 0; i < 6; i++) cfrc[6 * p + i] = acc[i];
-    }
-    __syncwarp();
-  }
-  for (int d = e.lane; d < h.nv; d += 32) {
-    const float* f = cfrc + 6 * MI(dof_body, d);
-    bias[d] = dot3(ld3(cdof + 6 * d), ld3(f)) + dot3(ld3(cdof + 6 * d + 3), ld3(f + 3));
-  }
-  __syncwarp();
-}
-
-// passive (joint damping) and actuator forces (motor: gear * clamp(u); position / PD:
-// kp (u - q) - kd qdot), then the unconstrained acceleration a0 = M^-1 (tau - c)
-__device__ void smooth_acc(const Env& e) {
-  const ModelHdr& h = *e.h;
-  float *passive = WS(passive), *act = WS(act), *a0 = WS(a0);
-  const float *qvel = WS(qvel), *qpos = WS(qpos), *ctrl = WS(ctrl), *bias = WS(bias);
-  for (int d = e.lane; d < h.nv; d += 32) {
-    passive[d] = -MF(dof_damping, d) * qvel[d];
-    float tau = 0.f;
-    for (int a = 0; a < h.nu; a++) {
-      if (MI(act_dof, a) != d) continue;
-      float u = ctrl[a];
-      if (MI(act_ctrllimited, a)) u = fminf(fmaxf(u, MF(act_range, 2 * a)), MF(act_range, 2 * a + 1));
-      if (MI(act_type, a) == PG_ACT_MOTOR) tau += MF(act_gear, a) * u;
-      else tau += MF(act_kp, a) * (u - qpos[MI(act_qposadr, a)]) - MF(act_kd, a) * qvel[d];
-    }
-    act[d] = tau;
-    a0[d] = tau + passive[d] - bias[d];
-  }
-  __syncwarp();
-  if (e.lane == 0) ldl_solve_lane(e, a0);
-  __syncwarp();
-}
-
-// ---------------------------------------------------------------------------------------
-// collision
+// collision primitives (per thread)
 // ---------------------------------------------------------------------------------------
 struct Con {
   float dist;
@@ -688,62 +320,377 @@ __device__ __forceinline__ void contact_frame(float3 n, float3& t1, float3& t2) 
   t2 = cross3(n, t1);
 }
 
-__device__ void collide(const Env& e, uint32_t& status) {
-  const ModelHdr& h = *e.h;
-  float* con = WS(con);
-  const float *gpos = WS(gpos), *gmat = WS(gmat);
-  for (int p = e.lane; p < h.npair; p += 32) {
+// ---------------------------------------------------------------------------------------
+// per-environment context: model tables in shared memory (broadcast reads), the thread's
+// structure-of-arrays workspace (element i at w[32 i]) and its controls in global memory
+// ---------------------------------------------------------------------------------------
+struct Ctx {
+  const ModelHdr& h;
+  const int* __restrict__ I;
+  const float* __restrict__ F;
+  float* __restrict__ w;
+  const float* __restrict__ ctrl;
+  int64_t ld;
+  int64_t env;
+};
+
+#define MI(name, i) (c.I[c.h.o_##name + (i)])
+#define MF(name, i) (c.F[c.h.o_##name + (i)])
+#define W(name, i) (c.w[(c.h.w_##name + (i)) * 32])
+
+__device__ __forceinline__ float3 W3(const Ctx& c, int off) {
+  return make_float3(c.w[off * 32], c.w[(off + 1) * 32], c.w[(off + 2) * 32]);
+}
+__device__ __forceinline__ void S3(const Ctx& c, int off, float3 v) {
+  c.w[off * 32] = v.x; c.w[(off + 1) * 32] = v.y; c.w[(off + 2) * 32] = v.z;
+}
+__device__ __forceinline__ float3 T3(const float* t) { return make_float3(t[0], t[1], t[2]); }
+
+// reference point of body b's tree: the free root's position, else the root's fixed frame origin
+__device__ __forceinline__ float3 tree_origin(const Ctx& c, int b) {
+  const int r = MI(body_root, b), fa = MI(root_freeadr, r);
+  if (fa >= 0) return W3(c, c.h.w_qpos + fa);
+  return T3(&MF(body_pos, 3 * r));
+}
+
+__device__ __forceinline__ void body_frame(const Ctx& c, int b, float3& x, Quat& q) {
+  if (b == 0) {
+    x = make_float3(0.f, 0.f, 0.f);
+    q = Quat{1.f, 0.f, 0.f, 0.f};
+  } else {
+    x = W3(c, c.h.w_xpos + 3 * b);
+    const int o = c.h.w_xquat + 4 * b;
+    q = Quat{c.w[o * 32], c.w[(o + 1) * 32], c.w[(o + 2) * 32], c.w[(o + 3) * 32]};
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// kinematics: bodies in level order (parent before child), each from its parent's frame, the
+// body offset and its joints (hinge: rotation about the axis through the anchor; slide:
+// translation; free: qpos position and normalised quaternion).  On the way: the motion
+// subspace of every dof (cdof, angular;linear about the tree's reference point o) and the
+// body's spatial inertia about o (Ixx Iyy Izz Ixy Ixz Iyz, m c, m).
+// ---------------------------------------------------------------------------------------
+__device__ void kinematics(const Ctx& c) {
+  const ModelHdr& h = c.h;
+  for (int b = 1; b < h.nbody; b++) {
+    float3 x;
+    Quat q;
+    body_frame(c, MI(body_parent, b), x, q);
+    x = x + qrot(q, T3(&MF(body_pos, 3 * b)));
+    q = qmul(q, Quat{MF(body_quat, 4 * b), MF(body_quat, 4 * b + 1), MF(body_quat, 4 * b + 2), MF(body_quat, 4 * b + 3)});
+    const float3 o = tree_origin(c, b);
+    const int j0 = MI(body_jntadr, b), nj = MI(body_jntnum, b);
+    for (int j = j0; j < j0 + nj; j++) {
+      const int type = MI(jnt_type, j), qa = MI(jnt_qposadr, j), d0 = MI(jnt_dofadr, j);
+      if (type == PG_JNT_FREE) {
+        x = W3(c, h.w_qpos + qa);
+        q = qnormalize(Quat{W(qpos, qa + 3), W(qpos, qa + 4), W(qpos, qa + 5), W(qpos, qa + 6)});
+        float R[9];
+        qmat(q, R);
+        for (int k = 0; k < 3; k++) {
+          S3(c, h.w_cdof + 6 * (d0 + k), make_float3(0.f, 0.f, 0.f));
+          S3(c, h.w_cdof + 6 * (d0 + k) + 3, make_float3(k == 0 ? 1.f : 0.f, k == 1 ? 1.f : 0.f, k == 2 ? 1.f : 0.f));
+          const float3 ax = mat_col(R, k);
+          S3(c, h.w_cdof + 6 * (d0 + 3 + k), ax);
+          S3(c, h.w_cdof + 6 * (d0 + 3 + k) + 3, cross3(ax, o - x));
+        }
+      } else {
+        const float3 lp = T3(&MF(jnt_pos, 3 * j)), la = T3(&MF(jnt_axis, 3 * j));
+        const float3 anchor = x + qrot(q, lp), axis = qrot(q, la);
+        if (type == PG_JNT_HINGE) {
+          S3(c, h.w_cdof + 6 * d0, axis);
+          S3(c, h.w_cdof + 6 * d0 + 3, cross3(axis, o - anchor));
+          float sn, cs;
+          sincosf(0.5f * W(qpos, qa), &sn, &cs);
+          q = qmul(q, Quat{cs, la.x * sn, la.y * sn, la.z * sn});
+          x = anchor - qrot(q, lp);
+        } else {
+          S3(c, h.w_cdof + 6 * d0, make_float3(0.f, 0.f, 0.f));
+          S3(c, h.w_cdof + 6 * d0 + 3, axis);
+          x = x + axis * W(qpos, qa);
+        }
+      }
+    }
+    q = qnormalize(q);
+    S3(c, h.w_xpos + 3 * b, x);
+    const int qo = h.w_xquat + 4 * b;
+    c.w[qo * 32] = q.w; c.w[(qo + 1) * 32] = q.x; c.w[(qo + 2) * 32] = q.y; c.w[(qo + 3) * 32] = q.z;
+    // spatial inertia about o: I_com(world) + m (|c|^2 1 - c c^T), h = m c
+    float R[9];
+    qmat(q, R);
+    const float3 com = x + mat_mul(R, T3(&MF(body_ipos, 3 * b)));
+    const float m = MF(body_mass, b);
+    const float* In = &MF(body_inertia, 6 * b);
+    const float Ib[9] = {In[0], In[3], In[4], In[3], In[1], In[5], In[4], In[5], In[2]};
+    float T[9];
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+      for (int k = 0; k < 3; k++) T[3 * r + k] = R[3 * r] * Ib[k] + R[3 * r + 1] * Ib[3 + k] + R[3 * r + 2] * Ib[6 + k];
+    const float3 cc = com - o;
+    const float c2 = dot3(cc, cc);
+    const int ci = h.w_cinert + 10 * b;
+    c.w[(ci + 0) * 32] = T[0] * R[0] + T[1] * R[1] + T[2] * R[2] + m * (c2 - cc.x * cc.x);
+    c.w[(ci + 1) * 32] = T[3] * R[3] + T[4] * R[4] + T[5] * R[5] + m * (c2 - cc.y * cc.y);
+    c.w[(ci + 2) * 32] = T[6] * R[6] + T[7] * R[7] + T[8] * R[8] + m * (c2 - cc.z * cc.z);
+    c.w[(ci + 3) * 32] = T[0] * R[3] + T[1] * R[4] + T[2] * R[5] - m * cc.x * cc.y;
+    c.w[(ci + 4) * 32] = T[0] * R[6] + T[1] * R[7] + T[2] * R[8] - m * cc.x * cc.z;
+    c.w[(ci + 5) * 32] = T[3] * R[6] + T[4] * R[7] + T[5] * R[8] - m * cc.y * cc.z;
+    c.w[(ci + 6) * 32] = m * cc.x;
+    c.w[(ci + 7) * 32] = m * cc.y;
+    c.w[(ci + 8) * 32] = m * cc.z;
+    c.w[(ci + 9) * 32] = m;
+  }
+}
+
+// spatial inertia (about o) times a motion vector (w; v)
+__device__ __forceinline__ void inert_mul(const Ctx& c, int ci, float3 w, float3 v, float3& fa, float3& fl) {
+  const float* q = c.w + ci * 32;
+  const float i0 = q[0], i1 = q[32], i2 = q[64], i3 = q[96], i4 = q[128], i5 = q[160];
+  const float3 hc = make_float3(q[192], q[224], q[256]);
+  const float m = q[288];
+  fa = make_float3(i0 * w.x + i3 * w.y + i4 * w.z, i3 * w.x + i1 * w.y + i5 * w.z, i4 * w.x + i5 * w.y + i2 * w.z) +
+       cross3(hc, v);
+  fl = v * m - cross3(hc, w);
+}
+
+// ---------------------------------------------------------------------------------------
+// RNEA bias forces c(q, qdot): velocities and bias accelerations outward (the world
+// accelerates by -gravity), body forces I a + v x* I v accumulated inward, projected on cdof.
+// Serial joints of one body act as massless intermediate frames; the free joint's three
+// rotations all take the velocity after its translation (their axes move with the body).
+// ---------------------------------------------------------------------------------------
+__device__ void rnea(const Ctx& c) {
+  const ModelHdr& h = c.h;
+  for (int b = 1; b < h.nbody; b++) {
+    const int p = MI(body_parent, b);
+    float3 w, v, aw, av;
+    if (p == 0) {
+      w = v = aw = make_float3(0.f, 0.f, 0.f);
+      av = make_float3(-h.grav[0], -h.grav[1], -h.grav[2]);
+    } else {
+      w = W3(c, h.w_cvel + 6 * p); v = W3(c, h.w_cvel + 6 * p + 3);
+      aw = W3(c, h.w_cacc + 6 * p); av = W3(c, h.w_cacc + 6 * p + 3);
+    }
+    const int j0 = MI(body_jntadr, b), nj = MI(body_jntnum, b);
+    for (int j = j0; j < j0 + nj; j++) {
+      const int d0 = MI(jnt_dofadr, j);
+      float3 dw, dv;
+      if (MI(jnt_type, j) == PG_JNT_FREE) {
+        v = v + make_float3(W(qvel, d0), W(qvel, d0 + 1), W(qvel, d0 + 2));
+        dw = dv = make_float3(0.f, 0.f, 0.f);
+        for (int k = 3; k < 6; k++) {
+          const float qd = W(qvel, d0 + k);
+          dw = dw + W3(c, h.w_cdof + 6 * (d0 + k)) * qd;
+          dv = dv + W3(c, h.w_cdof + 6 * (d0 + k) + 3) * qd;
+        }
+      } else {
+        const float qd = W(qvel, d0);
+        dw = W3(c, h.w_cdof + 6 * d0) * qd;
+        dv = W3(c, h.w_cdof + 6 * d0 + 3) * qd;
+      }
+      aw = aw + cross3(w, dw);
+      av = av + cross3(w, dv) + cross3(v, dw);
+      w = w + dw;
+      v = v + dv;
+    }
+    S3(c, h.w_cvel + 6 * b, w); S3(c, h.w_cvel + 6 * b + 3, v);
+    S3(c, h.w_cacc + 6 * b, aw); S3(c, h.w_cacc + 6 * b + 3, av);
+    float3 fa, fl, ia, il;
+    inert_mul(c, h.w_cinert + 10 * b, aw, av, fa, fl);
+    inert_mul(c, h.w_cinert + 10 * b, w, v, ia, il);
+    S3(c, h.w_cfrc + 6 * b, fa + cross3(w, ia) + cross3(v, il));
+    S3(c, h.w_cfrc + 6 * b + 3, fl + cross3(w, il));
+  }
+  for (int b = h.nbody - 1; b >= 1; b--) {
+    const int p = MI(body_parent, b);
+    if (p == 0) continue;
+    for (int k = 0; k < 6; k++) W(cfrc, 6 * p + k) += W(cfrc, 6 * b + k);
+  }
+  for (int d = 0; d < h.nv; d++) {
+    const int f = h.w_cfrc + 6 * MI(dof_body, d);
+    W(bias, d) = dot3(W3(c, h.w_cdof + 6 * d), W3(c, f)) + dot3(W3(c, h.w_cdof + 6 * d + 3), W3(c, f + 3));
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// CRBA: composite inertias (inward sum, in place), M_ji = cdof_i . (Ic(body j) cdof_j) for i on
+// j's dof chain, armature on the diagonal, stored packed (row j: j, parent(j), ...)
+// ---------------------------------------------------------------------------------------
+__device__ void crba(const Ctx& c) {
+  const ModelHdr& h = c.h;
+  for (int b = h.nbody - 1; b >= 1; b--) {
+    const int p = MI(body_parent, b);
+    if (p == 0) continue;
+    for (int k = 0; k < 10; k++) W(cinert, 10 * p + k) += W(cinert, 10 * b + k);
+  }
+  for (int j = 0; j < h.nv; j++) {
+    float3 fa, fl;
+    inert_mul(c, h.w_cinert + 10 * MI(dof_body, j), W3(c, h.w_cdof + 6 * j), W3(c, h.w_cdof + 6 * j + 3), fa, fl);
+    const int r0 = MI(dof_rowadr, j), n = MI(dof_depth, j) + 1;
+    for (int t = 0; t < n; t++) {
+      const int i = MI(Lcol, r0 + t);
+      float v = dot3(W3(c, h.w_cdof + 6 * i), fa) + dot3(W3(c, h.w_cdof + 6 * i + 3), fl);
+      if (t == 0) v += MF(dof_armature, j);
+      W(M, r0 + t) = v;
+    }
+  }
+}
+
+// packed tree-sparse factorisation in place: A = L^T D L, L unit lower triangular on the
+// ancestor pattern (no fill-in); row k ends as (D_k, L_k,parent(k), ...)
+__device__ void ldl_factor(const Ctx& c, int A) {
+  const ModelHdr& h = c.h;
+  float* a = c.w + A * 32;
+  for (int k = h.nv - 1; k >= 0; k--) {
+    const int r0 = MI(dof_rowadr, k), dk = MI(dof_depth, k);
+    const float dinv = 1.f / a[r0 * 32];
+    for (int t = 1; t <= dk; t++) {
+      const int ri = MI(dof_rowadr, MI(Lcol, r0 + t));
+      const float lt = a[(r0 + t) * 32] * dinv;
+      for (int s = t; s <= dk; s++) a[(ri + s - t) * 32] -= lt * a[(r0 + s) * 32];
+    }
+    for (int t = 1; t <= dk; t++) a[(r0 + t) * 32] *= dinv;
+  }
+}
+
+// x <- A^-1 x with the packed factor of A (x: element offset of an nv-vector)
+__device__ void ldl_solve(const Ctx& c, int A, int X) {
+  const ModelHdr& h = c.h;
+  const float* a = c.w + A * 32;
+  float* x = c.w + X * 32;
+  for (int k = h.nv - 1; k >= 0; k--) {
+    const int r0 = MI(dof_rowadr, k), dk = MI(dof_depth, k);
+    const float xk = x[k * 32];
+    for (int t = 1; t <= dk; t++) x[MI(Lcol, r0 + t) * 32] -= a[(r0 + t) * 32] * xk;
+  }
+  for (int k = 0; k < h.nv; k++) x[k * 32] /= a[MI(dof_rowadr, k) * 32];
+  for (int k = 0; k < h.nv; k++) {
+    const int r0 = MI(dof_rowadr, k), dk = MI(dof_depth, k);
+    float s = x[k * 32];
+    for (int t = 1; t <= dk; t++) s -= a[(r0 + t) * 32] * x[MI(Lcol, r0 + t) * 32];
+    x[k * 32] = s;
+  }
+}
+
+// y = M x with M stored packed symmetric (x, y: element offsets of nv-vectors)
+__device__ void sym_mul(const Ctx& c, int Mo, int X, int Y) {
+  const ModelHdr& h = c.h;
+  const float* m = c.w + Mo * 32;
+  const float* x = c.w + X * 32;
+  float* y = c.w + Y * 32;
+  for (int j = 0; j < h.nv; j++) y[j * 32] = 0.f;
+  for (int j = 0; j < h.nv; j++) {
+    const int r0 = MI(dof_rowadr, j), dj = MI(dof_depth, j);
+    const float xj = x[j * 32];
+    float yj = m[r0 * 32] * xj;
+    for (int t = 1; t <= dj; t++) {
+      const int i = MI(Lcol, r0 + t);
+      const float mji = m[(r0 + t) * 32];
+      yj = fmaf(mji, x[i * 32], yj);
+      y[i * 32] = fmaf(mji, xj, y[i * 32]);
+    }
+    y[j * 32] += yj;
+  }
+}
+
+// passive (joint damping) and actuator forces (motor: gear * clamp(u); PD: kp (u - q) - kd qd),
+// then a0 = M^-1 (tau - c)
+template <bool DEBUG>
+__device__ void smooth_acc(const Ctx& c, float* dbg) {
+  const ModelHdr& h = c.h;
+  for (int d = 0; d < h.nv; d++) {
+    const float pas = -MF(dof_damping, d) * W(qvel, d);
+    W(a0, d) = pas - W(bias, d);
+    if (DEBUG) { dbg[h.dbg_passive + d] = pas; dbg[h.dbg_act + d] = 0.f; dbg[h.dbg_bias + d] = W(bias, d); }
+  }
+  for (int a = 0; a < h.nu; a++) {
+    const int d = MI(act_dof, a);
+    float u = c.ctrl[a * c.ld + c.env];
+    if (MI(act_ctrllimited, a)) u = fminf(fmaxf(u, MF(act_range, 2 * a)), MF(act_range, 2 * a + 1));
+    const float tau = MI(act_type, a) == PG_ACT_MOTOR
+                          ? MF(act_gear, a) * u
+                          : MF(act_kp, a) * (u - W(qpos, MI(act_qposadr, a))) - MF(act_kd, a) * W(qvel, d);
+    W(a0, d) += tau;
+    if (DEBUG) dbg[h.dbg_act + d] += tau;
+  }
+  for (int k = 0; k < h.nL; k++) W(L, k) = W(M, k);
+  ldl_factor(c, h.w_L);
+  ldl_solve(c, h.w_L, h.w_a0);
+}
+// ---------------------------------------------------------------------------------------
+// collision over the static pair list; active contacts (dist < margin) are kept in slot order
+// up to max_contacts as (slot, dist, pos, n)
+// ---------------------------------------------------------------------------------------
+template <bool DEBUG>
+__device__ int collide(const Ctx& c, uint32_t& status, float* dbg) {
+  const ModelHdr& h = c.h;
+  int nc = 0;
+  for (int p = 0; p < h.npair; p++) {
     const int g1 = MI(pair_g1, p), g2 = MI(pair_g2, p);
     const int t1 = MI(geom_type, g1), t2 = MI(geom_type, g2);
-    const float3 x1 = ld3(gpos + 3 * g1), x2 = ld3(gpos + 3 * g2);
-    const float *R1 = gmat + 9 * g1, *R2 = gmat + 9 * g2;
+    float3 x1, x2;
+    float R1[9], R2[9];
+    {
+      float3 bx;
+      Quat bq;
+      body_frame(c, MI(geom_body, g1), bx, bq);
+      x1 = bx + qrot(bq, T3(&MF(geom_pos, 3 * g1)));
+      qmat(qnormalize(qmul(bq, Quat{MF(geom_quat, 4 * g1), MF(geom_quat, 4 * g1 + 1), MF(geom_quat, 4 * g1 + 2),
+                                    MF(geom_quat, 4 * g1 + 3)})), R1);
+      body_frame(c, MI(geom_body, g2), bx, bq);
+      x2 = bx + qrot(bq, T3(&MF(geom_pos, 3 * g2)));
+      qmat(qnormalize(qmul(bq, Quat{MF(geom_quat, 4 * g2), MF(geom_quat, 4 * g2 + 1), MF(geom_quat, 4 * g2 + 2),
+                                    MF(geom_quat, 4 * g2 + 3)})), R2);
+    }
     const float *s1 = &MF(geom_size, 3 * g1), *s2 = &MF(geom_size, 3 * g2);
     const int s0 = MI(pair_slotadr, p), ns = MI(pair_nslot, p);
-    Con c[4];
-    int valid = ns;   // candidates produced (others stay inactive)
-    for (int i = 0; i < 4; i++) { c[i].dist = 1.f; c[i].pos = x1; c[i].n = make_float3(0.f, 0.f, 1.f); }
+    Con k[4];
+    int valid = ns;
+    for (int i = 0; i < 4; i++) { k[i].dist = 1.f; k[i].pos = x1; k[i].n = make_float3(0.f, 0.f, 1.f); }
     if (t1 == PG_GEOM_PLANE) {
       const float3 nz = mat_col(R1, 2);
       if (t2 == PG_GEOM_SPHERE) {
-        c[0] = plane_sphere(x1, nz, x2, s2[0]);
+        k[0] = plane_sphere(x1, nz, x2, s2[0]);
       } else if (t2 == PG_GEOM_CAPSULE) {
         const float3 a = mat_col(R2, 2);
-        c[0] = plane_sphere(x1, nz, x2 - a * s2[1], s2[0]);
-        c[1] = plane_sphere(x1, nz, x2 + a * s2[1], s2[0]);
-      } else if (t2 == PG_GEOM_BOX) {
-        float d[8];
+        k[0] = plane_sphere(x1, nz, x2 - a * s2[1], s2[0]);
+        k[1] = plane_sphere(x1, nz, x2 + a * s2[1], s2[0]);
+      } else {
+        float dd[8];
         float3 cp[8];
         for (int v = 0; v < 8; v++) {
           const float3 l = make_float3((v & 1) ? s2[0] : -s2[0], (v & 2) ? s2[1] : -s2[1], (v & 4) ? s2[2] : -s2[2]);
           cp[v] = x2 + mat_mul(R2, l);
-          d[v] = dot3(nz, cp[v] - x1);
+          dd[v] = dot3(nz, cp[v] - x1);
         }
         // the 4 deepest corners (ties: lower index), kept in corner order
         unsigned chosen = 0;
         for (int r = 0; r < 4; r++) {
           int bi = -1;
           for (int v = 0; v < 8; v++)
-            if (!((chosen >> v) & 1u) && (bi < 0 || d[v] < d[bi])) bi = v;
+            if (!((chosen >> v) & 1u) && (bi < 0 || dd[v] < dd[bi])) bi = v;
           chosen |= 1u << bi;
         }
         int i = 0;
         for (int v = 0; v < 8; v++)
           if ((chosen >> v) & 1u) {
-            c[i].n = nz;
-            c[i].dist = d[v];
-            c[i].pos = cp[v] - nz * (0.5f * d[v]);
+            k[i].n = nz;
+            k[i].dist = dd[v];
+            k[i].pos = cp[v] - nz * (0.5f * dd[v]);
             i++;
           }
       }
     } else if (t1 == PG_GEOM_SPHERE) {
       if (t2 == PG_GEOM_SPHERE) {
-        c[0] = sphere_sphere(x1, s1[0], x2, s2[0]);
+        k[0] = sphere_sphere(x1, s1[0], x2, s2[0]);
       } else if (t2 == PG_GEOM_CAPSULE) {
         const float3 a = mat_col(R2, 2);
         const float t = fminf(fmaxf(dot3(x1 - x2, a), -s2[1]), s2[1]);
-        c[0] = sphere_sphere(x1, s1[0], x2 + a * t, s2[0]);
+        k[0] = sphere_sphere(x1, s1[0], x2 + a * t, s2[0]);
       } else {
-        c[0] = sphere_box(x1, s1[0], x2, R2, make_float3(s2[0], s2[1], s2[2]));
+        k[0] = sphere_box(x1, s1[0], x2, R2, make_float3(s2[0], s2[1], s2[2]));
       }
     } else if (t1 == PG_GEOM_CAPSULE) {
       const float3 a1 = mat_col(R1, 2);
@@ -751,343 +698,440 @@ __device__ void collide(const Env& e, uint32_t& status) {
         const float3 a2 = mat_col(R2, 2);
         float u, v;
         seg_seg(x1, a1, s1[1], x2, a2, s2[1], u, v);
-        c[0] = sphere_sphere(x1 + a1 * u, s1[0], x2 + a2 * v, s2[0]);
+        k[0] = sphere_sphere(x1 + a1 * u, s1[0], x2 + a2 * v, s2[0]);
       } else {
         const float3 hb = make_float3(s2[0], s2[1], s2[2]);
-        c[0] = sphere_box(x1 - a1 * s1[1], s1[0], x2, R2, hb);
-        c[1] = sphere_box(x1 + a1 * s1[1], s1[0], x2, R2, hb);
+        k[0] = sphere_box(x1 - a1 * s1[1], s1[0], x2, R2, hb);
+        k[1] = sphere_box(x1 + a1 * s1[1], s1[0], x2, R2, hb);
       }
     } else {
-      valid = box_box(x1, R1, make_float3(s1[0], s1[1], s1[2]), x2, R2, make_float3(s2[0], s2[1], s2[2]), c);
+      valid = box_box(x1, R1, make_float3(s1[0], s1[1], s1[2]), x2, R2, make_float3(s2[0], s2[1], s2[2]), k);
     }
     for (int i = 0; i < ns; i++) {
-      float* k = con + 14 * (s0 + i);
-      const bool act = i < valid && c[i].dist < h.margin;
-      float3 t1v, t2v;
-      contact_frame(c[i].n, t1v, t2v);
-      k[0] = act ? 1.f : 0.f;
-      k[1] = i < valid ? c[i].dist : 1.f;
-      st3(k + 2, c[i].pos);
-      st3(k + 5, c[i].n);
-      st3(k + 8, t1v);
-      st3(k + 11, t2v);
-    }
-  }
-  __syncwarp();
-  // at most max_contacts active contacts, kept in slot order
-  if (e.lane == 0) {
-    int na = 0;
-    for (int s = 0; s < h.nslot; s++) {
-      if (con[14 * s] != 0.f) {
-        if (na >= h.max_contacts) { con[14 * s] = 0.f; status |= PG_STATUS_CAPACITY; }
-        else na++;
+      const bool act = i < valid && k[i].dist < h.margin;
+      if (DEBUG) {
+        float3 tv1, tv2;
+        contact_frame(k[i].n, tv1, tv2);
+        float* o = dbg + h.dbg_con + 14 * (s0 + i);
+        o[0] = 0.f;
+        o[1] = i < valid ? k[i].dist : 1.f;
+        o[2] = k[i].pos.x; o[3] = k[i].pos.y; o[4] = k[i].pos.z;
+        o[5] = k[i].n.x; o[6] = k[i].n.y; o[7] = k[i].n.z;
+        o[8] = tv1.x; o[9] = tv1.y; o[10] = tv1.z;
+        o[11] = tv2.x; o[12] = tv2.y; o[13] = tv2.z;
+        if (act && nc < h.max_contacts) o[0] = 1.f;
       }
+      if (!act) continue;
+      if (nc >= h.max_contacts) { status |= PG_STATUS_CAPACITY; continue; }
+      const int o = h.w_con + kConFloats * nc;
+      c.w[o * 32] = (float)(s0 + i);
+      c.w[(o + 1) * 32] = k[i].dist;
+      S3(c, o + 2, k[i].pos);
+      S3(c, o + 5, k[i].n);
+      nc++;
     }
   }
-  __syncwarp();
+  return nc;
 }
 
 // ---------------------------------------------------------------------------------------
-// constraint rows
+// constraint rows, laid out identically in every environment (static shapes):
+//   rows 4k .. 4k+3 belong to the k-th active contact (k < max_contacts): edges n+mu t1,
+//   n-mu t1, n+mu t2, n-mu t2 of the pyramid (a condim-1 contact uses edge 0 = n only);
+//   rows 4 max_contacts + l belong to the l-th limited joint.
+// A row that does not exist in this environment has D = 0 and is never active.  The k-th
+// contact's Jacobian rows (n, t1, t2) are stored over its pair's columns, padded to ncol_max
+// (padding columns are zero and point at the first column).
 // ---------------------------------------------------------------------------------------
-// row ids: contact rows encode 4 * slot + edge (edge 0..3; condim 1 uses edge 0);
-// limit rows encode -1 - (2 * limit_index + side) with side 0 = lower, 1 = upper.
-__device__ int assign_rows(const Env& e) {
-  const ModelHdr& h = *e.h;
-  int* rowslot = reinterpret_cast<int*>(WS(rowslot));
-  int nrow = 0;
-  if (e.lane == 0) {
-    const float* con = WS(con);
-    for (int p = 0; p < h.npair; p++) {
-      const int s0 = MI(pair_slotadr, p), ns = MI(pair_nslot, p), ne = MI(pair_condim, p) == 3 ? 4 : 1;
-      for (int s = s0; s < s0 + ns; s++)
-        if (con[14 * s] != 0.f)
-          for (int k = 0; k < ne; k++) rowslot[nrow++] = 4 * s + k;
-    }
-    const float* qpos = WS(qpos);
-    for (int li = 0; li < h.nlimited; li++) {
-      const int j = MI(limit_jnt, li);
-      const float q = qpos[MI(jnt_qposadr, j)];
-      if (q - MF(jnt_range, 2 * j) < h.margin) rowslot[nrow++] = -1 - 2 * li;
-      else if (MF(jnt_range, 2 * j + 1) - q < h.margin) rowslot[nrow++] = -1 - (2 * li + 1);
-    }
-  }
-  nrow = __shfl_sync(kFull, nrow, 0);
-  __syncwarp();
-  return nrow;
+__device__ __forceinline__ int con_pair(const Ctx& c, int k) {
+  return MI(slot_pair, (int)c.w[(c.h.w_con + kConFloats * k) * 32]);
 }
 
-__device__ __forceinline__ int slot_pair(const Env& e, int s) {
-  int p = 0;
-  while (p + 1 < e.h->npair && MI(pair_slotadr, p + 1) <= s) p++;
-  return p;
-}
-
-// J rows (dense over nv), row position r, velocity J qdot, Ahat, impedance, aref, D
-__device__ void build_rows(const Env& e, int nrow) {
-  const ModelHdr& h = *e.h;
-  const int nv = h.nv;
-  float* J = WS(J);
-  const int* rowslot = reinterpret_cast<const int*>(WS(rowslot));
-  const float *con = WS(con), *cdof = WS(cdof), *xpos = WS(xpos);
-  for (int i = e.lane; i < nrow * nv; i += 32) J[i] = 0.f;
-  __syncwarp();
-  // contact rows: lane = dof, loop over the contacts (first row of each)
-  for (int d = e.lane; d < nv; d += 32) {
-    const float3 cw = ld3(cdof + 6 * d), cl = ld3(cdof + 6 * d + 3);
-    const int db = MI(dof_body, d);
-    (void)db;
-    for (int r = 0; r < nrow; r++) {
-      const int id = rowslot[r];
-      if (id < 0 || (id & 3) != 0) continue;
-      const int s = id >> 2, p = slot_pair(e, s);
-      const int b1 = MI(geom_body, MI(pair_g1, p)), b2 = MI(geom_body, MI(pair_g2, p));
-      const float* k = con + 14 * s;
-      const float3 pos = ld3(k + 2);
-      float3 jac = make_float3(0.f, 0.f, 0.f);
-      const uint64_t m2 = (uint64_t)(uint32_t)MI(body_dofmask, 2 * b2) | ((uint64_t)(uint32_t)MI(body_dofmask, 2 * b2 + 1) << 32);
-      const uint64_t m1 = (uint64_t)(uint32_t)MI(body_dofmask, 2 * b1) | ((uint64_t)(uint32_t)MI(body_dofmask, 2 * b1 + 1) << 32);
-      if ((m2 >> d) & 1ull) jac = jac + cl + cross3(cw, pos - ld3(xpos + 3 * MI(body_root, b2)));
-      if ((m1 >> d) & 1ull) jac = jac - (cl + cross3(cw, pos - ld3(xpos + 3 * MI(body_root, b1))));
-      const float jn = dot3(ld3(k + 5), jac);
-      if (MI(pair_condim, p) == 3) {
-        const float mu = MF(pair_friction, p);
-        const float jt1 = dot3(ld3(k + 8), jac), jt2 = dot3(ld3(k + 11), jac);
-        J[(r + 0) * nv + d] = jn + mu * jt1;
-        J[(r + 1) * nv + d] = jn - mu * jt1;
-        J[(r + 2) * nv + d] = jn + mu * jt2;
-        J[(r + 3) * nv + d] = jn - mu * jt2;
+__device__ void build_rows(const Ctx& c, int nc) {
+  const ModelHdr& h = c.h;
+  const int NC = h.ncol_max;
+  for (int k = 0; k < h.max_contacts; k++) {
+    float* J = c.w + (h.w_J + 3 * NC * k) * 32;
+    float* gc = c.w + (h.w_gcol + NC * k) * 32;
+    if (k >= nc) {
+      for (int a = 0; a < NC; a++) { J[a * 32] = 0.f; J[(NC + a) * 32] = 0.f; J[(2 * NC + a) * 32] = 0.f; gc[a * 32] = 0.f; }
+      continue;
+    }
+    const int p = con_pair(c, k);
+    const int co = h.w_con + kConFloats * k;
+    const float3 pos = W3(c, co + 2), n = W3(c, co + 5);
+    float3 t1, t2;
+    contact_frame(n, t1, t2);
+    const int b1 = MI(geom_body, MI(pair_g1, p)), b2 = MI(geom_body, MI(pair_g2, p));
+    const float3 o1 = tree_origin(c, b1), o2 = tree_origin(c, b2);
+    const int ca = MI(pair_coladr, p), ncol = MI(pair_ncol, p);
+    for (int a = 0; a < NC; a++) {
+      if (a < ncol) {
+        const int d = MI(col_dof, ca + a), sg = MI(col_sign, ca + a);
+        const float3 cw = W3(c, h.w_cdof + 6 * d), cl = W3(c, h.w_cdof + 6 * d + 3);
+        const float3 jac = (cl + cross3(cw, pos - (sg > 0 ? o2 : o1))) * (float)sg;
+        J[a * 32] = dot3(n, jac);
+        J[(NC + a) * 32] = dot3(t1, jac);
+        J[(2 * NC + a) * 32] = dot3(t2, jac);
+        gc[a * 32] = __int_as_float(d);
       } else {
-        J[r * nv + d] = jn;
+        J[a * 32] = 0.f; J[(NC + a) * 32] = 0.f; J[(2 * NC + a) * 32] = 0.f;
+        gc[a * 32] = __int_as_float(ncol > 0 ? MI(col_dof, ca) : 0);
       }
     }
   }
-  // limit rows
-  for (int r = e.lane; r < nrow; r += 32) {
-    const int id = rowslot[r];
-    if (id >= 0) continue;
-    const int code = -1 - id, li = code >> 1, side = code & 1;
+  for (int li = 0; li < h.nlimited; li++) {
     const int j = MI(limit_jnt, li);
-    J[r * nv + MI(jnt_dofadr, j)] = side == 0 ? 1.f : -1.f;
+    const float q = W(qpos, MI(jnt_qposadr, j));
+    float sgn = 0.f;
+    if (q - MF(jnt_range, 2 * j) < h.margin) sgn = 1.f;
+    else if (MF(jnt_range, 2 * j + 1) - q < h.margin) sgn = -1.f;
+    W(lsgn, li) = sgn;
   }
-  __syncwarp();
 }
 
-// per-row position, velocity, exact Ahat = (J M^-1 J^T)_rr = sum_k z_k^2 / D_k with
-// z = L^-T J_r^T (one lane per row), impedance, reference acceleration and D = 1 / R
-__device__ void row_params(const Env& e, int nrow) {
-  const ModelHdr& h = *e.h;
-  const int nv = h.nv;
-  const float *J = WS(J), *con = WS(con), *qvel = WS(qvel), *qpos = WS(qpos), *Lp = WS(L), *Dd = WS(D);
-  const int* rowslot = reinterpret_cast<const int*>(WS(rowslot));
-  float *rr = WS(rr), *rv = WS(rv), *aref = WS(aref), *rD = WS(rD), *Ahat = WS(Ahat), *imp = WS(imp), *Z = WS(Z);
-  for (int r = e.lane; r < nrow; r += 32) {
-    const int id = rowslot[r];
-    float pos;
-    if (id >= 0) {
-      pos = con[14 * (id >> 2) + 1];
-    } else {
-      const int code = -1 - id, li = code >> 1, side = code & 1, j = MI(limit_jnt, li);
-      const float q = qpos[MI(jnt_qposadr, j)];
-      pos = side == 0 ? q - MF(jnt_range, 2 * j) : MF(jnt_range, 2 * j + 1) - q;
+__device__ __forceinline__ float edge_value(float mu, int e, float dn, float d1, float d2) {
+  const float dt = e < 2 ? d1 : d2;
+  return (e & 1) ? dn - mu * dt : dn + mu * dt;
+}
+
+// J_r . x for every row into the element buffer OUT (rows of absent contacts give 0)
+__device__ void rows_dot(const Ctx& c, int X, int OUT) {
+  const ModelHdr& h = c.h;
+  const int NC = h.ncol_max, MC = h.max_contacts;
+  const float* x = c.w + X * 32;
+  for (int k = 0; k < MC; k++) {
+    const float* J = c.w + (h.w_J + 3 * NC * k) * 32;
+    const float* gc = c.w + (h.w_gcol + NC * k) * 32;
+    float dn = 0.f, d1 = 0.f, d2 = 0.f;
+    for (int a = 0; a < NC; a++) {
+      const float xa = x[__float_as_int(gc[a * 32]) * 32];
+      dn = fmaf(J[a * 32], xa, dn);
+      d1 = fmaf(J[(NC + a) * 32], xa, d1);
+      d2 = fmaf(J[(2 * NC + a) * 32], xa, d2);
     }
-    const float* Jr = J + r * nv;
-    float* z = Z + r * nv;
-    float vel = 0.f;
-    for (int k = 0; k < nv; k++) { z[k] = Jr[k]; vel = fmaf(Jr[k], qvel[k], vel); }
-    float A = 0.f;
-    for (int k = nv - 1; k >= 0; k--) {
-      const float zk = z[k];
-      if (zk != 0.f) {
-        const int r0 = MI(dof_rowadr, k), dk = MI(dof_depth, k);
-        for (int t = 1; t <= dk; t++) z[MI(Lcol, r0 + t)] -= Lp[r0 + t] * zk;
+    const float mu = W(gmu, k);
+    for (int e = 0; e < 4; e++) c.w[(OUT + 4 * k + e) * 32] = edge_value(mu, e, dn, d1, d2);
+  }
+  for (int li = 0; li < h.nlimited; li++) {
+    const int d = MI(jnt_dofadr, MI(limit_jnt, li));
+    c.w[(OUT + 4 * MC + li) * 32] = W(lsgn, li) * x[d * 32];
+  }
+}
+
+// impedance d(r) from solimp = (d0, dwidth, width, mid, power)
+__device__ __forceinline__ float impedance(const ModelHdr& h, float pos) {
+  const float d0 = h.solimp[0], d1 = h.solimp[1], width = h.solimp[2], mid = h.solimp[3], pw = h.solimp[4];
+  const float x = fminf(fabsf(pos) / width, 1.f);
+  float y;
+  if (x >= 1.f) y = 1.f;
+  else if (x <= mid) y = powf(x, pw) / powf(mid, pw - 1.f);
+  else y = 1.f - powf(1.f - x, pw) / powf(1.f - mid, pw - 1.f);
+  return d0 + y * (d1 - d0);
+}
+
+__device__ __forceinline__ void set_row(const Ctx& c, int r, bool valid, float pos, float A) {
+  const ModelHdr& h = c.h;
+  const float d = impedance(h, pos), vel = W(rv, r);
+  W(rr, r) = pos;
+  W(Ahat, r) = A;
+  W(imp, r) = d;
+  W(aref, r) = -h.bref * vel - h.kref * d * pos;
+  W(rD, r) = valid ? d / ((1.f - d) * A) : 0.f;
+}
+
+// z <- L^-T z along the chain that starts at dof c0 (z is zero off that chain), or over all dofs
+// when the model's pairs do not lie on single chains
+__device__ __forceinline__ void ltsolve_chain(const Ctx& c, float* z, int c0) {
+  const ModelHdr& h = c.h;
+  const float* L = c.w + h.w_L * 32;
+  if (h.tree_hessian) {
+    const int rc = MI(dof_rowadr, c0), n = MI(dof_depth, c0);
+    for (int t = 0; t <= n; t++) {
+      const int k = MI(Lcol, rc + t);
+      const float zk = z[k * 32];
+      const int r0 = MI(dof_rowadr, k), dk = MI(dof_depth, k);
+      for (int s = 1; s <= dk; s++) z[MI(Lcol, r0 + s) * 32] -= L[(r0 + s) * 32] * zk;
+    }
+  } else {
+    for (int k = h.nv - 1; k >= 0; k--) {
+      const float zk = z[k * 32];
+      const int r0 = MI(dof_rowadr, k), dk = MI(dof_depth, k);
+      for (int s = 1; s <= dk; s++) z[MI(Lcol, r0 + s) * 32] -= L[(r0 + s) * 32] * zk;
+    }
+  }
+}
+
+// per row: position, velocity, exact Ahat = (J M^-1 J^T)_rr = sum_k z_k z_k / D_k with
+// z = L^-T J_r^T (for a pyramid from the n / t1 / t2 solves: Ahat = A_nn +- 2 mu A_nk + mu^2 A_kk),
+// impedance, aref = -b v - k d r, D = d / ((1 - d) Ahat) (0 for absent rows)
+__device__ void row_params(const Ctx& c, int nc) {
+  const ModelHdr& h = c.h;
+  const int nv = h.nv, NC = h.ncol_max, MC = h.max_contacts;
+  const float* L = c.w + h.w_L * 32;
+  for (int k = 0; k < MC; k++) {
+    const bool valid = k < nc;
+    const int p = valid ? con_pair(c, k) : 0;
+    W(gmu, k) = valid ? MF(pair_friction, p) : 0.f;
+    W(gcond, k) = valid ? (float)MI(pair_condim, p) : 0.f;
+  }
+  rows_dot(c, h.w_qvel, h.w_rv);
+  for (int k = 0; k < MC; k++) {
+    const bool valid = k < nc;
+    const float mu = W(gmu, k), dist = valid ? W(con, kConFloats * k + 1) : 0.f;
+    const bool pyr = W(gcond, k) == 3.f;
+    const float* J = c.w + (h.w_J + 3 * NC * k) * 32;
+    const float* gc = c.w + (h.w_gcol + NC * k) * 32;
+    float Ann = 1.f, An1 = 0.f, An2 = 0.f, A11 = 1.f, A22 = 1.f;
+    if (valid) {
+      const int c0 = __float_as_int(gc[0]);
+      for (int s = 0; s < 3; s++) {
+        float* z = c.w + (h.w_z + s * nv) * 32;
+        for (int i = 0; i < nv; i++) z[i * 32] = 0.f;
+        for (int a = 0; a < NC; a++) z[__float_as_int(gc[a * 32]) * 32] += J[(s * NC + a) * 32];
+        ltsolve_chain(c, z, c0);
       }
-      A = fmaf(zk * zk, 1.f / Dd[k], A);
+      Ann = An1 = An2 = A11 = A22 = 0.f;
+      for (int i = 0; i < nv; i++) {
+        const float dinv = 1.f / L[MI(dof_rowadr, i) * 32];
+        const float zn = W(z, i), z1 = W(z, nv + i), z2 = W(z, 2 * nv + i);
+        Ann = fmaf(zn * zn, dinv, Ann);
+        An1 = fmaf(zn * z1, dinv, An1);
+        An2 = fmaf(zn * z2, dinv, An2);
+        A11 = fmaf(z1 * z1, dinv, A11);
+        A22 = fmaf(z2 * z2, dinv, A22);
+      }
     }
-    // impedance d(r) from solimp = (d0, dwidth, width, mid, power)
-    const float d0 = h.solimp[0], d1 = h.solimp[1], width = h.solimp[2], mid = h.solimp[3], pw = h.solimp[4];
-    const float x = fminf(fabsf(pos) / width, 1.f);
-    float y;
-    if (x >= 1.f) y = 1.f;
-    else if (x <= mid) y = powf(x, pw) / powf(mid, pw - 1.f);
-    else y = 1.f - powf(1.f - x, pw) / powf(1.f - mid, pw - 1.f);
-    const float dimp = d0 + y * (d1 - d0);
-    rr[r] = pos;
-    rv[r] = vel;
-    Ahat[r] = A;
-    imp[r] = dimp;
-    aref[r] = -h.bref * vel - h.kref * dimp * pos;
-    rD[r] = dimp / ((1.f - dimp) * A);
+    if (pyr) {
+      set_row(c, 4 * k + 0, valid, dist, Ann + 2.f * mu * An1 + mu * mu * A11);
+      set_row(c, 4 * k + 1, valid, dist, Ann - 2.f * mu * An1 + mu * mu * A11);
+      set_row(c, 4 * k + 2, valid, dist, Ann + 2.f * mu * An2 + mu * mu * A22);
+      set_row(c, 4 * k + 3, valid, dist, Ann - 2.f * mu * An2 + mu * mu * A22);
+    } else {
+      set_row(c, 4 * k + 0, valid, dist, Ann);
+      for (int e = 1; e < 4; e++) set_row(c, 4 * k + e, false, dist, 1.f);
+    }
   }
-  __syncwarp();
+  for (int li = 0; li < h.nlimited; li++) {
+    const int j = MI(limit_jnt, li), d = MI(jnt_dofadr, j);
+    const float sgn = W(lsgn, li);
+    const float q = W(qpos, MI(jnt_qposadr, j));
+    const float pos = sgn < 0.f ? MF(jnt_range, 2 * j + 1) - q : q - MF(jnt_range, 2 * j);
+    float A = 1.f;
+    if (sgn != 0.f) {
+      // (M^-1)_dd = sum_k z_k^2 / D_k with z = L^-T e_d, supported on d's chain
+      float* z = c.w + h.w_z * 32;
+      for (int i = 0; i < nv; i++) z[i * 32] = 0.f;
+      z[d * 32] = 1.f;
+      const int rc = MI(dof_rowadr, d), n = MI(dof_depth, d);
+      A = 0.f;
+      for (int t = 0; t <= n; t++) {
+        const int k = MI(Lcol, rc + t);
+        const float zk = z[k * 32];
+        const int r0 = MI(dof_rowadr, k), dk = MI(dof_depth, k);
+        for (int s = 1; s <= dk; s++) z[MI(Lcol, r0 + s) * 32] -= L[(r0 + s) * 32] * zk;
+        A = fmaf(zk * zk, 1.f / L[r0 * 32], A);
+      }
+    }
+    set_row(c, 4 * MC + li, sgn != 0.f, pos, A);
+  }
 }
 
 // ---------------------------------------------------------------------------------------
-// Newton solve of  min_a 1/2 (a-a0)^T M (a-a0) + sum_r 1/2 D_r min(0, J_r a - aref_r)^2
+// Newton solve of  min_a f(a) = 1/2 (a-a0)^T M (a-a0) + sum_r 1/2 D_r min(0, J_r a - aref_r)^2
 // ---------------------------------------------------------------------------------------
-// f(x) with x in shared memory (all lanes get the value)
-__device__ float cost_of(const Env& e, const float* x, int nrow) {
-  const ModelHdr& h = *e.h;
-  const int nv = h.nv;
-  const float *M = WS(M), *a0 = WS(a0), *J = WS(J), *aref = WS(aref), *rD = WS(rD);
-  float part = 0.f;
-  for (int j = e.lane; j < nv; j += 32) {
-    float s = 0.f;
-    for (int k = 0; k < nv; k++) s = fmaf(M[j * nv + k], x[k] - a0[k], s);
-    part = fmaf(0.5f * (x[j] - a0[j]), s, part);
+__device__ float cost_of(const Ctx& c, int X) {
+  const ModelHdr& h = c.h;
+  for (int k = 0; k < h.nv; k++) W(t, k) = c.w[(X + k) * 32] - W(a0, k);
+  sym_mul(c, h.w_M, h.w_t, h.w_g);
+  float f = 0.f;
+  for (int k = 0; k < h.nv; k++) f = fmaf(0.5f * W(t, k), W(g, k), f);
+  rows_dot(c, X, h.w_jar);
+  for (int r = 0; r < h.nrow_max; r++) {
+    const float jar = W(jar, r) - W(aref, r);
+    if (jar < 0.f) f = fmaf(0.5f * W(rD, r) * jar, jar, f);
   }
-  for (int r = e.lane; r < nrow; r += 32) {
-    float jar = -aref[r];
-    for (int k = 0; k < nv; k++) jar = fmaf(J[r * nv + k], x[k], jar);
-    if (jar < 0.f) part = fmaf(0.5f * rD[r] * jar, jar, part);
-  }
-  return warp_sum(part);
-}
-
-// active set of x: bit r of word r/32, with jar stored (all lanes get the 4 words)
-__device__ void active_set(const Env& e, const float* x, int nrow, unsigned act[4]) {
-  const int nv = e.h->nv;
-  const float *J = WS(J), *aref = WS(aref);
-  float* jar = WS(jar);
-#pragma unroll
-  for (int w = 0; w < 4; w++) {
-    const int r = 32 * w + e.lane;
-    bool on = false;
-    if (r < nrow) {
-      float s = -aref[r];
-      for (int k = 0; k < nv; k++) s = fmaf(J[r * nv + k], x[k], s);
-      jar[r] = s;
-      on = s < 0.f;
-    }
-    act[w] = __ballot_sync(kFull, on);
-  }
-  __syncwarp();
+  return f;
 }
 
 __device__ __forceinline__ bool bit(const unsigned act[4], int r) { return (act[r >> 5] >> (r & 31)) & 1u; }
 
-// returns iterations used; sets converged
-__device__ int newton(const Env& e, int nrow, bool& converged) {
-  const ModelHdr& h = *e.h;
+// jar = J a - aref for every row; the active set holds the existing rows with jar < 0
+__device__ void residuals(const Ctx& c, unsigned act[4]) {
+  const ModelHdr& h = c.h;
+  rows_dot(c, h.w_a, h.w_jar);
+  act[0] = act[1] = act[2] = act[3] = 0u;
+  for (int r = 0; r < h.nrow_max; r++) {
+    const float jar = W(jar, r) - W(aref, r);
+    W(jar, r) = jar;
+    if (jar < 0.f && W(rD, r) > 0.f) act[r >> 5] |= 1u << (r & 31);
+  }
+}
+
+// g = M (a - a0) + J_A^T D_A jar_A, H = M + J_A^T D_A J_A (packed on the tree pattern in the
+// L buffer, or dense lower triangle), factorised; p = -H^-1 g.  `zero`: g is exactly zero.
+__device__ bool newton_direction(const Ctx& c, const unsigned act[4], bool& zero) {
+  const ModelHdr& h = c.h;
+  const int nv = h.nv, nL = h.nL, NC = h.ncol_max, MC = h.max_contacts;
+  const bool tree = h.tree_hessian != 0;
+  for (int k = 0; k < nv; k++) W(t, k) = W(a, k) - W(a0, k);
+  sym_mul(c, h.w_M, h.w_t, h.w_g);
+  if (tree) {
+    for (int k = 0; k < nL; k++) W(L, k) = W(M, k);
+  } else {
+    for (int i = 0; i < nv * nv; i++) W(H, i) = 0.f;
+    for (int j = 0; j < nv; j++) {
+      const int r0 = MI(dof_rowadr, j), dj = MI(dof_depth, j);
+      for (int t = 0; t <= dj; t++) W(H, j * nv + MI(Lcol, r0 + t)) = W(M, r0 + t);
+    }
+  }
+  for (int k = 0; k < MC; k++) {
+    const float mu = W(gmu, k);
+    // the active edges summed in the (n, t1, t2) basis
+    float Sn = 0.f, c1 = 0.f, c2 = 0.f, s1 = 0.f, s2 = 0.f, gn = 0.f, g1 = 0.f, g2 = 0.f;
+    for (int e = 0; e < 4; e++) {
+      const int r = 4 * k + e;
+      const float D = bit(act, r) ? W(rD, r) : 0.f, DJ = D * W(jar, r);
+      const float sg = (e & 1) ? -mu : mu;
+      Sn += D;
+      gn += DJ;
+      if (e < 2) { c1 += sg * D; s1 += mu * mu * D; g1 += sg * DJ; }
+      else { c2 += sg * D; s2 += mu * mu * D; g2 += sg * DJ; }
+    }
+    if (Sn == 0.f) continue;
+    const float* J = c.w + (h.w_J + 3 * NC * k) * 32;
+    const float* gc = c.w + (h.w_gcol + NC * k) * 32;
+    for (int a = 0; a < NC; a++) {
+      const int da = __float_as_int(gc[a * 32]);
+      const float na = J[a * 32], ta = J[(NC + a) * 32], ua = J[(2 * NC + a) * 32];
+      W(g, da) += gn * na + g1 * ta + g2 * ua;
+      const float hn = Sn * na + c1 * ta + c2 * ua;
+      const float ht = c1 * na + s1 * ta;
+      const float hu = c2 * na + s2 * ua;
+      const int ra = MI(dof_rowadr, da), depa = MI(dof_depth, da);
+      for (int b = a; b < NC; b++) {
+        const int db = __float_as_int(gc[b * 32]);
+        const float v = hn * J[b * 32] + ht * J[(NC + b) * 32] + hu * J[(2 * NC + b) * 32];
+        if (tree) W(L, ra + depa - MI(dof_depth, db)) += v;
+        else W(H, (da > db ? da * nv + db : db * nv + da)) += v;
+      }
+    }
+  }
+  for (int li = 0; li < h.nlimited; li++) {
+    const int r = 4 * MC + li, d = MI(jnt_dofadr, MI(limit_jnt, li));
+    const float D = bit(act, r) ? W(rD, r) : 0.f;
+    W(g, d) += W(lsgn, li) * D * W(jar, r);
+    if (tree) W(L, MI(dof_rowadr, d)) += D;
+    else W(H, d * nv + d) += D;
+  }
+  bool nz = false;
+  for (int k = 0; k < nv; k++) { W(p, k) = -W(g, k); nz = nz || W(g, k) != 0.f; }
+  zero = !nz;
+  if (zero) return false;
+  if (tree) {
+    ldl_factor(c, h.w_L);
+    for (int k = 0; k < nv; k++)
+      if (!(W(L, MI(dof_rowadr, k)) > 0.f)) return false;
+    ldl_solve(c, h.w_L, h.w_p);
+    return true;
+  }
+  for (int j = 0; j < nv; j++) {
+    float s = W(H, j * nv + j);
+    for (int k = 0; k < j; k++) s -= W(H, j * nv + k) * W(H, j * nv + k);
+    if (!(s > 0.f)) return false;
+    const float djj = sqrtf(s), inv = 1.f / djj;
+    W(H, j * nv + j) = djj;
+    for (int i = j + 1; i < nv; i++) {
+      float t = W(H, i * nv + j);
+      for (int k = 0; k < j; k++) t -= W(H, i * nv + k) * W(H, j * nv + k);
+      W(H, i * nv + j) = t * inv;
+    }
+  }
+  for (int i = 0; i < nv; i++) {
+    float s = W(p, i);
+    for (int k = 0; k < i; k++) s -= W(H, i * nv + k) * W(p, k);
+    W(p, i) = s / W(H, i * nv + i);
+  }
+  for (int i = nv - 1; i >= 0; i--) {
+    float s = W(p, i);
+    for (int k = i + 1; k < nv; k++) s -= W(H, k * nv + i) * W(p, k);
+    W(p, i) = s / W(H, i * nv + i);
+  }
+  return true;
+}
+
+// Exact minimiser of phi(alpha) = f(a + alpha p) (convex, piecewise quadratic): start from the
+// active set just after alpha = 0 and walk the breakpoints alpha_r = -jar_r / Jp_r in increasing
+// order (each next one found by a scan), toggling the rows that cross, until the root of the
+// current linear piece of phi' lies before the next breakpoint.
+__device__ float line_search(const Ctx& c) {
+  const ModelHdr& h = c.h;
+  const int nv = h.nv, R = h.nrow_max;
+  sym_mul(c, h.w_M, h.w_p, h.w_g);   // g <- M p
+  float qt = 0.f, lt = 0.f;
+  for (int k = 0; k < nv; k++) {
+    qt = fmaf(W(p, k), W(g, k), qt);
+    lt = fmaf(W(t, k), W(g, k), lt);   // t = a - a0
+  }
+  rows_dot(c, h.w_p, h.w_Jp);
+  unsigned on[4] = {0u, 0u, 0u, 0u};
+  for (int r = 0; r < R; r++) {
+    const float D = W(rD, r), jp = W(Jp, r), jr = W(jar, r);
+    if (D > 0.f && (jr < 0.f || (jr == 0.f && jp < 0.f))) {
+      on[r >> 5] |= 1u << (r & 31);
+      qt = fmaf(D * jp, jp, qt);
+      lt = fmaf(D * jp, jr, lt);
+    }
+  }
+  float alpha = 0.f;
+  for (int step = 0; step <= R; step++) {
+    const float root = qt > 0.f ? -lt / qt : alpha;
+    float next = INFINITY;
+    for (int r = 0; r < R; r++) {
+      const float jp = W(Jp, r);
+      if (!(W(rD, r) > 0.f) || jp == 0.f) continue;
+      const float br = -W(jar, r) / jp;
+      if (br > alpha && br < next) next = br;
+    }
+    if (root <= next) return root;
+    alpha = next;
+    for (int r = 0; r < R; r++) {
+      const float D = W(rD, r), jp = W(Jp, r);
+      if (!(D > 0.f) || jp == 0.f || -W(jar, r) / jp != next) continue;
+      const float sg = bit(on, r) ? -1.f : 1.f;
+      on[r >> 5] ^= 1u << (r & 31);
+      qt = fmaf(sg * D * jp, jp, qt);
+      lt = fmaf(sg * D * jp, W(jar, r), lt);
+    }
+  }
+  return qt > 0.f ? -lt / qt : alpha;
+}
+
+// Newton's method with exact termination: stop at the cap or when the active set after the
+// step equals the one the Hessian was built from.  Warm start: qacc_warm if f(warm) < f(a0).
+__device__ int newton(const Ctx& c, bool& converged) {
+  const ModelHdr& h = c.h;
   const int nv = h.nv;
-  float *a = WS(a), *g = WS(g), *p = WS(p), *Mp = WS(Mp), *H = WS(H), *jar = WS(jar), *Jp = WS(Jp);
-  const float *M = WS(M), *a0 = WS(a0), *J = WS(J), *rD = WS(rD), *warm = WS(warm);
   converged = false;
-  // warm start: qacc_warm if f(qacc_warm) < f(a0), else a0
-  const float fw = cost_of(e, warm, nrow), f0 = cost_of(e, a0, nrow);
+  const float fw = cost_of(c, h.w_warm), f0 = cost_of(c, h.w_a0);
   const bool use_warm = fw < f0;
-  for (int j = e.lane; j < nv; j += 32) a[j] = use_warm ? warm[j] : a0[j];
-  __syncwarp();
+  for (int k = 0; k < nv; k++) W(a, k) = use_warm ? W(warm, k) : W(a0, k);
+  unsigned act[4];
+  residuals(c, act);
   int it = 0;
-  for (; it < h.cap;) {
-    unsigned act[4];
-    active_set(e, a, nrow, act);
-    // gradient and Hessian rows (lane = row j of H)
-    bool nz = false;
-    for (int j = e.lane; j < nv; j += 32) {
-      float gj = 0.f;
-      for (int k = 0; k < nv; k++) gj = fmaf(M[j * nv + k], a[k] - a0[k], gj);
-      for (int k = 0; k < nv; k++) H[j * nv + k] = M[j * nv + k];
-      for (int r = 0; r < nrow; r++) {
-        if (!bit(act, r)) continue;
-        const float Dj = rD[r] * J[r * nv + j];
-        gj = fmaf(Dj, jar[r], gj);
-        if (Dj != 0.f)
-          for (int k = 0; k < nv; k++) H[j * nv + k] = fmaf(Dj, J[r * nv + k], H[j * nv + k]);
-      }
-      g[j] = gj;
-      nz = nz || gj != 0.f;
-    }
+  while (it < h.cap) {
+    bool zero = false;
+    const bool ok = newton_direction(c, act, zero);
     it++;
-    if (!__any_sync(kFull, nz)) { converged = true; break; }
-    __syncwarp();
-    // Cholesky H = L L^T in place (lower triangle), row i owned by a lane
-    bool ok = true;
-    for (int k = 0; k < nv; k++) {
-      const float dkk = H[k * nv + k];
-      ok = ok && dkk > 0.f;
-      const float dk = sqrtf(fmaxf(dkk, 1e-30f));
-      const float inv = 1.f / dk;
-      for (int i = k + 1 + e.lane; i < nv; i += 32) H[i * nv + k] *= inv;
-      __syncwarp();
-      for (int i = k + 1 + e.lane; i < nv; i += 32) {
-        const float lik = H[i * nv + k];
-        for (int j = k + 1; j <= i; j++) H[i * nv + j] = fmaf(-lik, H[j * nv + k], H[i * nv + j]);
-      }
-      if (e.lane == 0) H[k * nv + k] = dk;
-      __syncwarp();
-    }
+    if (zero) { converged = true; break; }
     if (!ok) break;
-    // p = -H^-1 g: forward (L y = -g) then backward (L^T p = y), column-oriented updates
-    for (int j = e.lane; j < nv; j += 32) p[j] = -g[j];
-    __syncwarp();
-    for (int k = 0; k < nv; k++) {
-      const float pk = p[k] / H[k * nv + k];
-      for (int i = k + 1 + e.lane; i < nv; i += 32) p[i] = fmaf(-H[i * nv + k], pk, p[i]);
-      __syncwarp();
-      if (e.lane == 0) p[k] = pk;
-      __syncwarp();
-    }
-    for (int k = nv - 1; k >= 0; k--) {
-      const float pk = p[k] / H[k * nv + k];
-      for (int i = e.lane; i < k; i += 32) p[i] = fmaf(-H[k * nv + i], pk, p[i]);
-      __syncwarp();
-      if (e.lane == 0) p[k] = pk;
-      __syncwarp();
-    }
-    // exact line search on phi(alpha) = f(a + alpha p)
-    float qp = 0.f, lp = 0.f;
-    for (int j = e.lane; j < nv; j += 32) {
-      float s = 0.f;
-      for (int k = 0; k < nv; k++) s = fmaf(M[j * nv + k], p[k], s);
-      Mp[j] = s;
-      qp = fmaf(p[j], s, qp);
-      lp = fmaf(s, a[j] - a0[j], lp);
-    }
-    const float quad0 = warp_sum(qp), lin0 = warp_sum(lp);
-    for (int r = e.lane; r < nrow; r += 32) {
-      float s = 0.f;
-      for (int k = 0; k < nv; k++) s = fmaf(J[r * nv + k], p[k], s);
-      Jp[r] = s;
-    }
-    __syncwarp();
-    // phi' at each row's breakpoint (lane = row); bracket the root between the largest
-    // breakpoint with phi' < 0 and the smallest with phi' >= 0
-    float lo = 0.f, hi = INFINITY;
-    for (int r = e.lane; r < ((nrow + 31) & ~31); r += 32) {
-      float ar = -1.f;
-      if (r < nrow && Jp[r] != 0.f) ar = -jar[r] / Jp[r];
-      if (r < nrow && ar > 0.f) {
-        float dphi = fmaf(ar, quad0, lin0);
-        for (int q = 0; q < nrow; q++) {
-          const float v = fmaf(ar, Jp[q], jar[q]);
-          if (v < 0.f) dphi = fmaf(rD[q] * Jp[q], v, dphi);
-        }
-        if (dphi < 0.f) lo = fmaxf(lo, ar);
-        else hi = fminf(hi, ar);
-      }
-    }
-    lo = warp_max(lo);
-    hi = warp_min(hi);
-    const float amid = isinf(hi) ? lo + 1.f : 0.5f * (lo + hi);
-    float qa = 0.f, la = 0.f;
-    for (int r = e.lane; r < nrow; r += 32) {
-      if (fmaf(amid, Jp[r], jar[r]) < 0.f) {
-        const float dj = rD[r] * Jp[r];
-        qa = fmaf(dj, Jp[r], qa);
-        la = fmaf(dj, jar[r], la);
-      }
-    }
-    const float qt = quad0 + warp_sum(qa), lt = lin0 + warp_sum(la);
-    const float alpha = qt > 0.f ? -lt / qt : 0.f;
-    for (int j = e.lane; j < nv; j += 32) a[j] = fmaf(alpha, p[j], a[j]);
-    __syncwarp();
+    const float alpha = line_search(c);
+    for (int k = 0; k < nv; k++) W(a, k) = fmaf(alpha, W(p, k), W(a, k));
     unsigned act2[4];
-    active_set(e, a, nrow, act2);
-    if (act2[0] == act[0] && act2[1] == act[1] && act2[2] == act[2] && act2[3] == act[3]) {
-      converged = true;
-      break;
-    }
+    residuals(c, act2);
+    const bool same = act2[0] == act[0] && act2[1] == act[1] && act2[2] == act[2] && act2[3] == act[3];
+    act[0] = act2[0]; act[1] = act2[1]; act[2] = act2[2]; act[3] = act2[3];
+    if (same) { converged = true; break; }
   }
   return it;
 }
@@ -1096,56 +1140,100 @@ __device__ int newton(const Env& e, int nrow, bool& converged) {
 // one substep
 // ---------------------------------------------------------------------------------------
 template <bool DEBUG>
-__device__ void substep(const Env& e, uint32_t& status, float* dbg, uint32_t cnt[3]) {
-  const ModelHdr& h = *e.h;
+__device__ void substep(const Ctx& c, uint32_t& status, float* dbg, uint32_t cnt[3]) {
+  const ModelHdr& h = c.h;
   const int nv = h.nv;
-  fk(e);
-  derived(e);
+  kinematics(c);
   if (DEBUG) {
-    for (int i = e.lane; i < 3 * h.nbody; i += 32) { dbg[h.dbg_xpos + i] = WS(xpos)[i]; dbg[h.dbg_xcom + i] = WS(xipos)[i]; }
-    for (int i = e.lane; i < 9 * h.nbody; i += 32) dbg[h.dbg_xmat + i] = WS(xmat)[i];
-    if (e.lane < 3) dbg[h.dbg_xcom + e.lane] = 0.f;   // world body
+    for (int b = 0; b < h.nbody; b++) {
+      float3 x;
+      Quat q;
+      body_frame(c, b, x, q);
+      float R[9];
+      qmat(q, R);
+      const float3 com = b ? x + mat_mul(R, T3(&MF(body_ipos, 3 * b))) : make_float3(0.f, 0.f, 0.f);
+      dbg[h.dbg_xpos + 3 * b] = x.x; dbg[h.dbg_xpos + 3 * b + 1] = x.y; dbg[h.dbg_xpos + 3 * b + 2] = x.z;
+      dbg[h.dbg_xcom + 3 * b] = com.x; dbg[h.dbg_xcom + 3 * b + 1] = com.y; dbg[h.dbg_xcom + 3 * b + 2] = com.z;
+      for (int k = 0; k < 9; k++) dbg[h.dbg_xmat + 9 * b + k] = R[k];
+    }
   }
-  crba(e);
-  ldl_factor(e);
-  rnea(e);
-  smooth_acc(e);
-  collide(e, status);
-  const int nrow = assign_rows(e);
-  build_rows(e, nrow);
-  // kinematic buffers are dead from here on (the Newton / row-solve union reuses them)
-  __syncwarp();
-  row_params(e, nrow);
-  float* a = WS(a);
+  rnea(c);
+  crba(c);
+  if (DEBUG) {
+    for (int i = 0; i < nv * nv; i++) dbg[h.dbg_M + i] = 0.f;
+    for (int j = 0; j < nv; j++) {
+      const int r0 = MI(dof_rowadr, j), dj = MI(dof_depth, j);
+      for (int t = 0; t <= dj; t++) {
+        const int i = MI(Lcol, r0 + t);
+        dbg[h.dbg_M + j * nv + i] = W(M, r0 + t);
+        dbg[h.dbg_M + i * nv + j] = W(M, r0 + t);
+      }
+    }
+  }
+  smooth_acc<DEBUG>(c, dbg);
+  if (DEBUG)
+    for (int k = 0; k < nv; k++) dbg[h.dbg_a0 + k] = W(a0, k);
+  const int nc = collide<DEBUG>(c, status, dbg);
+  build_rows(c, nc);
+  row_params(c, nc);
+  int nrow = 0;   // rows that exist in this environment
+  for (int r = 0; r < h.nrow_max; r++) nrow += W(rD, r) > 0.f ? 1 : 0;
   int iters = 0;
   bool conv = true;
   if (nrow == 0) {
-    for (int j = e.lane; j < nv; j += 32) a[j] = WS(a0)[j];
-    __syncwarp();
+    for (int k = 0; k < nv; k++) W(a, k) = W(a0, k);
   } else {
-    iters = newton(e, nrow, conv);
+    iters = newton(c, conv);
     if (!conv) status |= PG_STATUS_NOT_CONVERGED;
   }
   cnt[0] += (uint32_t)iters;
   cnt[1] += (uint32_t)nrow;
   cnt[2] += (uint32_t)(nrow * iters);
-  // semi-implicit Euler
-  float *qvel = WS(qvel), *qpos = WS(qpos), *warm = WS(warm);
-  bool bad = false;
-  for (int d = e.lane; d < nv; d += 32) {
-    const float acc = a[d];
-    qvel[d] = fmaf(h.h, acc, qvel[d]);
-    warm[d] = acc;
-    bad = bad || !isfinite(acc) || !isfinite(qvel[d]);
+  if (DEBUG) {
+    // rows in the oracle's order: existing contact rows, then existing limit rows
+    rows_dot(c, h.w_a, h.w_jar);
+    int o_r = 0;
+    for (int r = 0; r < h.nrow_max; r++) {
+      if (!(W(rD, r) > 0.f)) continue;
+      float* o = dbg + h.dbg_rows + (o_r++) * (nv + 7);
+      for (int k = 0; k < nv; k++) o[k] = 0.f;
+      if (r < 4 * h.max_contacts) {
+        const int k = r >> 2, e = r & 3;
+        const float mu = W(gmu, k);
+        const float* J = c.w + (h.w_J + 3 * h.ncol_max * k) * 32;
+        const float* gc = c.w + (h.w_gcol + h.ncol_max * k) * 32;
+        for (int a = 0; a < h.ncol_max; a++)
+          o[__float_as_int(gc[a * 32])] += W(gcond, k) == 3.f
+              ? edge_value(mu, e, J[a * 32], J[(h.ncol_max + a) * 32], J[(2 * h.ncol_max + a) * 32])
+              : J[a * 32];
+      } else {
+        const int li = r - 4 * h.max_contacts, d = MI(jnt_dofadr, MI(limit_jnt, li));
+        o[d] = W(lsgn, li);
+      }
+      o[nv] = W(rr, r); o[nv + 1] = W(rv, r); o[nv + 2] = W(aref, r); o[nv + 3] = W(rD, r);
+      o[nv + 4] = W(Ahat, r); o[nv + 5] = W(imp, r);
+      const float jar = W(jar, r) - W(aref, r);
+      o[nv + 6] = jar < 0.f ? -W(rD, r) * jar : 0.f;
+    }
+    dbg[h.dbg_nrow] = (float)nrow;
+    dbg[h.dbg_iter] = (float)iters;
   }
-  __syncwarp();
-  for (int j = e.lane; j < h.njnt; j += 32) {
+  // semi-implicit Euler
+  bool bad = false;
+  for (int d = 0; d < nv; d++) {
+    const float acc = W(a, d);
+    W(qvel, d) = fmaf(h.h, acc, W(qvel, d));
+    W(warm, d) = acc;
+    bad = bad || !isfinite(acc) || !isfinite(W(qvel, d));
+    if (DEBUG) dbg[h.dbg_qacc + d] = acc;
+  }
+  for (int j = 0; j < h.njnt; j++) {
     const int qa = MI(jnt_qposadr, j), da = MI(jnt_dofadr, j);
     if (MI(jnt_type, j) == PG_JNT_FREE) {
-      for (int k = 0; k < 3; k++) qpos[qa + k] = fmaf(h.h, qvel[da + k], qpos[qa + k]);
-      const float3 w = make_float3(qvel[da + 3], qvel[da + 4], qvel[da + 5]);
+      for (int k = 0; k < 3; k++) W(qpos, qa + k) = fmaf(h.h, W(qvel, da + k), W(qpos, qa + k));
+      const float3 w = make_float3(W(qvel, da + 3), W(qvel, da + 4), W(qvel, da + 5));
       const float wn = sqrtf(dot3(w, w));
-      Quat q{qpos[qa + 3], qpos[qa + 4], qpos[qa + 5], qpos[qa + 6]};
+      Quat q{W(qpos, qa + 3), W(qpos, qa + 4), W(qpos, qa + 5), W(qpos, qa + 6)};
       if (wn > 0.f) {
         float sn, cs;
         sincosf(0.5f * h.h * wn, &sn, &cs);
@@ -1153,48 +1241,18 @@ __device__ void substep(const Env& e, uint32_t& status, float* dbg, uint32_t cnt
         q = qmul(q, Quat{cs, w.x * s, w.y * s, w.z * s});
       }
       q = qnormalize(q);
-      qpos[qa + 3] = q.w; qpos[qa + 4] = q.x; qpos[qa + 5] = q.y; qpos[qa + 6] = q.z;
-      for (int k = 0; k < 7; k++) bad = bad || !isfinite(qpos[qa + k]);
+      W(qpos, qa + 3) = q.w; W(qpos, qa + 4) = q.x; W(qpos, qa + 5) = q.y; W(qpos, qa + 6) = q.z;
+      for (int k = 0; k < 7; k++) bad = bad || !isfinite(W(qpos, qa + k));
     } else {
-      qpos[qa] = fmaf(h.h, qvel[da], qpos[qa]);
-      bad = bad || !isfinite(qpos[qa]);
+      W(qpos, qa) = fmaf(h.h, W(qvel, da), W(qpos, qa));
+      bad = bad || !isfinite(W(qpos, qa));
     }
   }
-  if (__any_sync(kFull, bad)) status |= PG_STATUS_NAN;
-  __syncwarp();
+  if (bad) status |= PG_STATUS_NAN;
   if (DEBUG) {
-    for (int i = e.lane; i < nv * nv; i += 32) dbg[h.dbg_M + i] = WS(M)[i];
-    for (int i = e.lane; i < nv; i += 32) {
-      dbg[h.dbg_bias + i] = WS(bias)[i];
-      dbg[h.dbg_passive + i] = WS(passive)[i];
-      dbg[h.dbg_act + i] = WS(act)[i];
-      dbg[h.dbg_a0 + i] = WS(a0)[i];
-      dbg[h.dbg_qacc + i] = a[i];
-      dbg[h.dbg_qvel + i] = qvel[i];
-    }
-    for (int i = e.lane; i < h.nq; i += 32) dbg[h.dbg_qpos + i] = qpos[i];
-    for (int i = e.lane; i < 14 * h.nslot; i += 32) dbg[h.dbg_con + i] = WS(con)[i];
-    const float *J = WS(J), *jar = WS(jar), *rD = WS(rD);
-    for (int r = e.lane; r < nrow; r += 32) {
-      float* o = dbg + h.dbg_rows + r * (nv + 7);
-      for (int k = 0; k < nv; k++) o[k] = J[r * nv + k];
-      o[nv] = WS(rr)[r];
-      o[nv + 1] = WS(rv)[r];
-      o[nv + 2] = WS(aref)[r];
-      o[nv + 3] = rD[r];
-      o[nv + 4] = WS(Ahat)[r];
-      o[nv + 5] = WS(imp)[r];
-      // force at the final acceleration
-      float s = -WS(aref)[r];
-      for (int k = 0; k < nv; k++) s = fmaf(J[r * nv + k], a[k], s);
-      o[nv + 6] = s < 0.f ? -rD[r] * s : 0.f;
-      (void)jar;
-    }
-    if (e.lane == 0) {
-      dbg[h.dbg_nrow] = (float)nrow;
-      dbg[h.dbg_iter] = (float)iters;
-      dbg[h.dbg_status] = (float)status;
-    }
+    for (int k = 0; k < h.nq; k++) dbg[h.dbg_qpos + k] = W(qpos, k);
+    for (int k = 0; k < nv; k++) dbg[h.dbg_qvel + k] = W(qvel, k);
+    dbg[h.dbg_status] = (float)status;
   }
 }
 
@@ -1202,8 +1260,6 @@ __device__ void substep(const Env& e, uint32_t& status, float* dbg, uint32_t cnt
 // kernels
 // ---------------------------------------------------------------------------------------
 struct StepArgs {
-  const uint32_t* blobs;
-  const int* blob_off;
   const Tile* tiles;
   float* qpos;
   float* qvel;
@@ -1212,82 +1268,53 @@ struct StepArgs {
   uint32_t* stats;
   const float* ctrl;
   int64_t ld;
-  int blob_words;   // max over models (shared-memory slot size)
   int n_substeps;
   float* dbg;
   Tile dbg_tile;
+  int model_off[kMaxModels];          // word offset of each model's blob in `blob`
+  uint32_t blob[kMaxParamWords];      // the batch's model blobs (header + tables)
 };
 
+// One thread per environment; a block steps the `count` consecutive environments of its tile.
 template <bool DEBUG>
-__global__ void __launch_bounds__(256) step_kernel(StepArgs A) {
+__global__ void __launch_bounds__(kMaxEnvsPerCta) step_kernel(const __grid_constant__ StepArgs A) {
   extern __shared__ __align__(16) float smem[];
   const Tile tile = DEBUG ? A.dbg_tile : A.tiles[blockIdx.x];
-  // model blob -> shared memory
-  {
-    const uint4* src = reinterpret_cast<const uint4*>(A.blobs + A.blob_off[tile.model]);
-    const int nw = reinterpret_cast<const ModelHdr*>(A.blobs + A.blob_off[tile.model])->words;
-    uint4* dst = reinterpret_cast<uint4*>(smem);
-    for (int i = threadIdx.x; i < nw / 4; i += blockDim.x) dst[i] = src[i];
+  const int t = threadIdx.x;
+  if (t >= tile.count) return;
+  const uint32_t* blob = A.blob + A.model_off[tile.model];
+  const ModelHdr& h = *reinterpret_cast<const ModelHdr*>(blob);
+  const int64_t env = tile.env0 + t;
+  float* w = smem + (t >> 5) * (32 * h.ws_floats) + (t & 31);
+  Ctx c{h, reinterpret_cast<const int*>(blob), reinterpret_cast<const float*>(blob), w, A.ctrl, A.ld, env};
+  for (int k = 0; k < h.nq; k++) W(qpos, k) = A.qpos[k * A.ld + env];
+  uint32_t status = 0;
+  bool warm_bad = false;
+  for (int k = 0; k < h.nv; k++) {
+    W(qvel, k) = A.qvel[k * A.ld + env];
+    const float wv = A.warm[k * A.ld + env];
+    warm_bad = warm_bad || !isfinite(wv);
+    W(warm, k) = wv;
   }
-  __syncthreads();
-  const ModelHdr* hdr = reinterpret_cast<const ModelHdr*>(smem);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ws = hdr->ws_floats;
-  float* wsbase = smem + A.blob_words;
-  const int count = tile.count;
-  // stage the tile's state: [coord][env] runs of `count` consecutive envs (coalesced)
-  {
-    const int nq = hdr->nq, nv = hdr->nv, nu = hdr->nu;
-    const int tot = count * (nq + 2 * nv + nu);
-    for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-      const int c = i / count, k = i - c * count;
-      const int64_t env = tile.env0 + k;
-      float* w = wsbase + k * ws;
-      if (c < nq) w[hdr->w_qpos + c] = A.qpos[c * A.ld + env];
-      else if (c < nq + nv) w[hdr->w_qvel + (c - nq)] = A.qvel[(c - nq) * A.ld + env];
-      else if (c < nq + 2 * nv) w[hdr->w_warm + (c - nq - nv)] = A.warm[(c - nq - nv) * A.ld + env];
-      else w[hdr->w_ctrl + (c - nq - 2 * nv)] = A.ctrl[(c - nq - 2 * nv) * A.ld + env];
-    }
+  if (warm_bad) {   // a non-finite warm start is replaced by zeros (flagged)
+    status |= PG_STATUS_WARM_RESET;
+    for (int k = 0; k < h.nv; k++) W(warm, k) = 0.f;
   }
-  __syncthreads();
-  if (warp < count) {
-    Env e{hdr, reinterpret_cast<const int*>(smem), smem, wsbase + warp * ws, lane};
-    uint32_t status = 0;
-    // a non-finite warm start is replaced by zeros (flagged)
-    {
-      bool bad = false;
-      for (int d = lane; d < hdr->nv; d += 32) bad = bad || !isfinite(e.w[hdr->w_warm + d]);
-      if (__any_sync(kFull, bad)) {
-        status |= PG_STATUS_WARM_RESET;
-        for (int d = lane; d < hdr->nv; d += 32) e.w[hdr->w_warm + d] = 0.f;
-      }
-      __syncwarp();
-    }
-    const int nsub = DEBUG ? 1 : A.n_substeps;
-    uint32_t cnt[3] = {0u, 0u, 0u};
-    for (int s = 0; s < nsub; s++) substep<DEBUG>(e, status, A.dbg, cnt);
-    if (lane == 0 && status) atomicOr(A.status + tile.env0 + warp, status);
-    if (lane == 0 && A.stats)
-      for (int c = 0; c < 3; c++) A.stats[c * A.ld + tile.env0 + warp] += cnt[c];
+  uint32_t cnt[3] = {0u, 0u, 0u};
+  const int nsub = DEBUG ? 1 : A.n_substeps;
+  for (int s = 0; s < nsub; s++) substep<DEBUG>(c, status, A.dbg, cnt);
+  for (int k = 0; k < h.nq; k++) A.qpos[k * A.ld + env] = W(qpos, k);
+  for (int k = 0; k < h.nv; k++) {
+    A.qvel[k * A.ld + env] = W(qvel, k);
+    A.warm[k * A.ld + env] = W(warm, k);
   }
-  __syncthreads();
-  {
-    const int nq = hdr->nq, nv = hdr->nv;
-    const int tot = count * (nq + 2 * nv);
-    for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-      const int c = i / count, k = i - c * count;
-      const int64_t env = tile.env0 + k;
-      const float* w = wsbase + k * ws;
-      if (c < nq) A.qpos[c * A.ld + env] = w[hdr->w_qpos + c];
-      else if (c < nq + nv) A.qvel[(c - nq) * A.ld + env] = w[hdr->w_qvel + (c - nq)];
-      else A.warm[(c - nq - nv) * A.ld + env] = w[hdr->w_warm + (c - nq - nv)];
-    }
-  }
+  if (status) A.status[env] |= status;
+  if (A.stats)
+    for (int k = 0; k < 3; k++) A.stats[k * A.ld + env] += cnt[k];
 }
 
-__global__ void reset_kernel(const int* env_model, const uint32_t* blobs, const int* blob_off, float* qpos, float* qvel,
-                             float* warm, uint32_t* status, int64_t ld, int64_t n, const uint8_t* mask, const float* qpos0,
-                             const float* qvel0, int nq_max, int nv_max) {
+__global__ void reset_kernel(float* qpos, float* qvel, float* warm, uint32_t* status, int64_t ld, int64_t n,
+                             const uint8_t* mask, const float* qpos0, const float* qvel0, int nq_max, int nv_max) {
   const int64_t env = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (env >= n) return;
   if (mask && !mask[env]) return;
@@ -1297,7 +1324,6 @@ __global__ void reset_kernel(const int* env_model, const uint32_t* blobs, const 
     warm[c * ld + env] = 0.f;
   }
   status[env] = 0u;
-  (void)env_model; (void)blobs; (void)blob_off;
 }
 
 }  // namespace
@@ -1308,10 +1334,7 @@ cudaError_t configure_step_kernels(size_t smem_bytes) {
   return cudaFuncSetAttribute(step_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
 }
 
-static StepArgs make_args(const pg_batch* b, const pg_state* s, const float* ctrl) {
-  StepArgs A;
-  A.blobs = b->d_blobs;
-  A.blob_off = b->d_blob_off;
+static void make_args(StepArgs& A, const pg_batch* b, const pg_state* s, const float* ctrl) {
   A.tiles = b->d_tiles;
   A.qpos = s->qpos;
   A.qvel = s->qvel;
@@ -1320,29 +1343,31 @@ static StepArgs make_args(const pg_batch* b, const pg_state* s, const float* ctr
   A.stats = s->stats;
   A.ctrl = ctrl;
   A.ld = s->ld;
-  A.blob_words = b->max_blob_words;
   A.n_substeps = 1;
   A.dbg = nullptr;
   A.dbg_tile = Tile{0, 0, 0, 0};
-  return A;
+  for (int k = 0; k < kMaxModels; k++) A.model_off[k] = k < (int)b->blob_off.size() ? b->blob_off[k] : 0;
+  std::memcpy(A.blob, b->blob_host.data(), b->blob_host.size() * sizeof(uint32_t));
 }
 
 cudaError_t launch_step(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st) {
   if (b->ntiles == 0) return cudaSuccess;
-  StepArgs A = make_args(b, s, ctrl);
+  static thread_local StepArgs A;
+  make_args(A, b, s, ctrl);
   A.n_substeps = n_substeps;
-  step_kernel<false><<<b->ntiles, 32 * b->warps, b->smem_bytes, st>>>(A);
+  step_kernel<false><<<b->ntiles, b->threads, b->smem_bytes, st>>>(A);
   return cudaGetLastError();
 }
 
 cudaError_t launch_debug(const pg_batch* b, const pg_state* s, const float* ctrl, int64_t env, float* out, cudaStream_t st) {
-  StepArgs A = make_args(b, s, ctrl);
+  static thread_local StepArgs A;
+  make_args(A, b, s, ctrl);
   int model = 0;
   for (size_t k = 0; k < b->models.size(); k++)
     if (env >= b->env_off[k] && env < b->env_off[k] + b->counts[k]) model = (int)k;
   A.dbg = out;
   A.dbg_tile = Tile{model, (int)env, 1, 0};
-  step_kernel<true><<<1, 32 * b->warps, b->smem_bytes, st>>>(A);
+  step_kernel<true><<<1, 32, b->smem_bytes, st>>>(A);
   return cudaGetLastError();
 }
 
@@ -1351,8 +1376,8 @@ cudaError_t launch_reset(const pg_batch* b, const pg_state* s, const uint8_t* ma
   if (s->n == 0) return cudaSuccess;
   const int threads = 256;
   const int blocks = (int)((s->n + threads - 1) / threads);
-  reset_kernel<<<blocks, threads, 0, st>>>(nullptr, b->d_blobs, b->d_blob_off, s->qpos, s->qvel, s->qacc_warm, s->status,
-                                           s->ld, s->n, mask, qpos0, qvel0, b->nq_max, b->nv_max);
+  reset_kernel<<<blocks, threads, 0, st>>>(s->qpos, s->qvel, s->qacc_warm, s->status, s->ld, s->n, mask, qpos0, qvel0,
+                                           b->nq_max, b->nv_max);
   return cudaGetLastError();
 }
 
