@@ -136,6 +136,50 @@ def cpu_baseline(model: W.Model, cfg: int, n_envs: int, budget_s: float = 10.0, 
                 n, steps, model.n_substeps, model.name, cores)}
 
 
+def measure_mixed(dev, steps: int = 200):
+    """Mixed-model batch: 4096 cartpoles + 4096 quadrupeds + 2048 humanoids in one launch per
+    control step (each env with its own model's timestep and substeps), a 200-step rollout
+    captured in a CUDA graph, launch shape from the autotuner."""
+    import torch
+    from paper_2502_08844_b300 import core, rollout
+    comp = [("cartpole", 0, 4096), ("quadruped", 1, 4096), ("humanoid", 3, 2048)]
+    models = [(core.CompiledModel(W.model(nm)), n) for nm, _, n in comp]
+    epc = rollout.autotune(models)
+    batch = core.Batch(models, envs_per_cta=epc)
+    st = core.State(batch, dev)
+    ld = st.ld
+    Q = np.zeros((batch.nq_max, ld), np.float32)
+    V = np.zeros((batch.nv_max, ld), np.float32)
+    U = np.zeros((steps, max(batch.nu_max, 1), ld), np.float32)
+    o = 0
+    for (nm, cfg, n), (cm, _) in zip(comp, models):
+        m = cm.src
+        q0, v0 = W.initial_state(m, cfg, n)
+        Q[:m.nq, o:o + n] = q0.T
+        V[:m.nv, o:o + n] = v0.T
+        U[:, :m.nu, o:o + n] = W.actions(m, cfg, n, 0, steps).transpose(0, 2, 1)
+        o += n
+    st.qpos.copy_(torch.from_numpy(Q)); st.qvel.copy_(torch.from_numpy(V))
+    ctrl = torch.from_numpy(U).to(dev)
+    g = rollout.GraphRollout(batch, st, ctrl, 0)
+    g.capture()
+    st.qpos.copy_(torch.from_numpy(Q)); st.qvel.copy_(torch.from_numpy(V)); st.qacc_warm.zero_()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(); g.replay(); b.record()
+    torch.cuda.synchronize()
+    t_graph = a.elapsed_time(b) / 1e3
+    st.qpos.copy_(torch.from_numpy(Q)); st.qvel.copy_(torch.from_numpy(V)); st.qacc_warm.zero_()
+    torch.cuda.synchronize()
+    a.record(); g.run_eager(); b.record()
+    torch.cuda.synchronize()
+    t_eager = a.elapsed_time(b) / 1e3
+    n_tot = sum(n for _, _, n in comp)
+    return {"value": n_tot * steps / t_graph, "unit": "env-steps/s", "eager_value": n_tot * steps / t_eager,
+            "composition": {nm: n for nm, _, n in comp}, "steps": steps, "cuda_graph": True,
+            "envs_per_cta": epc or "default (one wave)", "launches": steps}
+
+
 def run_reference(args):
     """Reference arm: the FP64 oracle as it stands, timed on the host cores."""
     ws, rank, _ = dist_env()
@@ -277,6 +321,8 @@ def run_ours(args):
             "roofline": roof, "e2e": e2e, "gpu_launches": args.steps,
             "clocks": ck, "status_bits_seen": int(np.bitwise_or.reduce(status)) if status.size else 0,
             "adjoint_forward_ratio": None}
+    if not args.no_mixed:
+        line["mixed_batch"] = measure_mixed(dev)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(m, cfg, n)
     print(json.dumps(line))
@@ -292,6 +338,7 @@ def main():
     ap.add_argument("--envs-per-cta", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

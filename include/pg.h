@@ -94,6 +94,8 @@ typedef struct pg_model_desc {
   const int* act_ctrllimited; const float* act_ctrlrange;
   float timestep; const float* gravity; int iterations; int cone; float impratio;
   const float* solref; const float* solimp; float margin; int max_contacts;
+  int substeps;   /* the model's own physics substeps per control step (used by pg_step when
+                     n_substeps == 0, e.g. in a mixed batch); values < 1 mean 1 */
 } pg_model_desc;
 
 typedef struct pg_model pg_model;   /* opaque, library-owned */
@@ -142,7 +144,9 @@ int pg_reset(const pg_batch* batch, pg_state* state, const uint8_t* env_mask_dev
              const float* qvel0_dev, void* stream);
 
 /* One control step: n_substeps physics substeps with the controls ctrl_dev ([nu_max][ld])
- * held (zero-order hold).  Advances qpos, qvel, qacc_warm and ORs status bits in place. */
+ * held (zero-order hold); n_substeps == 0 runs each model's own `substeps` (a mixed batch
+ * whose models run different rates).  Every environment integrates with its own model's
+ * timestep.  Advances qpos, qvel, qacc_warm and ORs status bits in place. */
 int pg_step(const pg_batch* batch, pg_state* state, const float* ctrl_dev, int n_substeps, void* stream);
 
 /* Diagnostics: one substep of environment `env` only (the others are untouched), writing

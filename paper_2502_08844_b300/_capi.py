@@ -34,7 +34,7 @@ class pg_model_desc(C.Structure):
         ("act_ctrllimited", _ip), ("act_ctrlrange", _fp),
         ("timestep", C.c_float), ("gravity", _fp), ("iterations", C.c_int), ("cone", C.c_int),
         ("impratio", C.c_float), ("solref", _fp), ("solimp", _fp), ("margin", C.c_float),
-        ("max_contacts", C.c_int),
+        ("max_contacts", C.c_int), ("substeps", C.c_int),
     ]
 
 

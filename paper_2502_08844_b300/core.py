@@ -53,7 +53,8 @@ class CompiledModel:
             f(m.geom_pos), f(m.geom_quat), f(m.geom_size), f(m.geom_mass), i(pair_geom), f(m.pair_friction),
             i(m.pair_condim), i(m.act_type), i(m.act_jnt), f(m.act_gear), f(m.act_kp), f(m.act_kd),
             i(m.act_ctrllimited), f(m.act_ctrlrange), float(m.timestep), f(m.gravity), int(m.iterations),
-            int(m.cone), float(m.impratio), f(m.solref), f(m.solimp), float(m.margin), int(m.max_contacts))
+            int(m.cone), float(m.impratio), f(m.solref), f(m.solimp), float(m.margin), int(m.max_contacts),
+            int(m.n_substeps))
         self.handle = _capi.pg_model_compile(d)
         self.sizes = _capi.pg_model_info(self.handle)
 

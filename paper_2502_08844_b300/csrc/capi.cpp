@@ -26,7 +26,6 @@ static int cuda_error(cudaError_t e, const char* what) {
                    std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-constexpr size_t kMaxSmem = 232448;   // 227 KB opt-in shared memory per block on sm_103a
 
 }  // namespace pg
 
@@ -101,24 +100,28 @@ int pg_batch_compile(const pg_model* const* models, const int64_t* counts, int n
   if (b->n > (int64_t)1 << 31) { delete b; return set_error(PG_EINVAL, "too many environments"); }
   if (envs_per_cta < 0 || envs_per_cta > kMaxEnvsPerCta) { delete b; return set_error(PG_EINVAL, "envs_per_cta must be 0 (auto) or 1..256"); }
   // environments per block: enough blocks to give every SM work in one wave, as many envs per
-  // block as shared memory allows (the workspace is reserved per warp of 32 environments)
+  // block as shared memory allows.  Each warp holds `soa` environments of its model.
   int sms = 148, dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (nmodels > kMaxModels) { delete b; return set_error(PG_ECAPACITY, "more than 8 models in one batch"); }
-  const size_t per_warp = (size_t)128 * b->max_ws_floats;
-  const size_t blob_bytes = 0;   // the model blobs travel as a kernel parameter
-  if (blob_bytes + per_warp > kMaxSmem) { delete b; return set_error(PG_ECAPACITY, "one warp's workspace exceeds shared memory"); }
-  const int warps_fit = (int)std::min<size_t>((kMaxSmem - blob_bytes) / per_warp, kMaxEnvsPerCta / 32);
-  int threads = 32;
+  // each model's blocks use as many warps as fit its own per-warp workspace; the launch
+  // reserves the largest block footprint
+  size_t smem = 0;
+  int nwarps_max = 1;
   for (int k = 0; k < nmodels; k++) {
+    const int soa = models[k]->hdr.soa;
+    const size_t per_warp = (size_t)4 * soa * models[k]->hdr.ws_floats;
+    const int warps_fit = (int)std::min<size_t>((size_t)kMaxSmem / per_warp, kMaxEnvsPerCta / 32);
+    const int cap = warps_fit * soa;
+    if (envs_per_cta && envs_per_cta > cap) { delete b; return set_error(PG_ECAPACITY, "envs_per_cta exceeds shared memory for these models"); }
     int e = envs_per_cta ? envs_per_cta : (int)std::max<int64_t>(1, (counts[k] + sms - 1) / sms);
-    if (envs_per_cta && (e + 31) / 32 > warps_fit) { delete b; return set_error(PG_ECAPACITY, "envs_per_cta exceeds shared memory for these models"); }
-    e = std::min(e, 32 * warps_fit);
+    e = std::min(e, cap);
     b->envs_per_cta.push_back(e);
-    threads = std::max(threads, (e + 31) / 32 * 32);
+    const int nw = (e + soa - 1) / soa;
+    nwarps_max = std::max(nwarps_max, nw);
+    smem = std::max(smem, (size_t)nw * per_warp);
   }
-  b->threads = threads;
-  b->smem_bytes = blob_bytes + (size_t)(threads / 32) * per_warp;
+  b->threads = 32 * nwarps_max;
+  b->smem_bytes = smem;
   std::vector<uint32_t> all;
   for (int k = 0; k < nmodels; k++) {
     b->blob_off[k] = (int)all.size();
@@ -131,6 +134,11 @@ int pg_batch_compile(const pg_model* const* models, const int64_t* counts, int n
     for (int64_t e0 = 0; e0 < counts[k]; e0 += e)
       b->tiles.push_back(Tile{k, (int)(b->env_off[k] + e0), (int)std::min<int64_t>(e, counts[k] - e0), 0});
   }
+  // heaviest models' tiles first (blocks start roughly in index order): a per-environment cost
+  // proxy of the model's workspace size
+  std::stable_sort(b->tiles.begin(), b->tiles.end(), [&](const Tile& x, const Tile& y) {
+    return models[x.model]->hdr.ws_floats > models[y.model]->hdr.ws_floats;
+  });
   b->ntiles = (int)b->tiles.size();
   cudaError_t e;
   if ((e = cudaMalloc(&b->d_blobs, all.size() * 4)) != cudaSuccess) { pg_batch_free(b); return cuda_error(e, "cudaMalloc"); }
@@ -177,7 +185,7 @@ int pg_reset(const pg_batch* b, pg_state* s, const uint8_t* mask, const float* q
 int pg_step(const pg_batch* b, pg_state* s, const float* ctrl, int n_substeps, void* stream) {
   int rc = check_state(b, s);
   if (rc) return rc;
-  if (n_substeps < 1) return set_error(PG_EINVAL, "n_substeps must be >= 1");
+  if (n_substeps < 0) return set_error(PG_EINVAL, "n_substeps must be >= 0 (0: each model's own)");
   if (b->n > 0 && b->nu_max > 0 && !ctrl) return set_error(PG_EINVAL, "NULL ctrl");
   cudaError_t e = launch_step(b, s, ctrl, n_substeps, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_error(e, "step launch");
@@ -199,7 +207,7 @@ int pg_step_host(pg_batch* b, pg_state* s, const float* ctrl_host, float* qpos_h
                  void* stream) {
   int rc = check_state(b, s);
   if (rc) return rc;
-  if (n_substeps < 1) return set_error(PG_EINVAL, "n_substeps must be >= 1");
+  if (n_substeps < 0) return set_error(PG_EINVAL, "n_substeps must be >= 0 (0: each model's own)");
   if ((b->nu_max > 0 && !ctrl_host) || !qpos_host || !qvel_host) return set_error(PG_EINVAL, "NULL host buffer");
   cudaStream_t st = (cudaStream_t)stream;
   const size_t need = (size_t)std::max(b->nu_max, 1) * (size_t)s->ld;

@@ -293,6 +293,7 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
   h.nslot = nslot; h.nrow_max = nrow_max; h.max_contacts = max_contacts; h.nlimited = (int)limit_jnt.size();
   h.nL = nL; h.cap = d->iterations; h.cone = d->cone; h.tree_hessian = tree_hessian; h.ncol_max = ncol_max;
   h.h = d->timestep;
+  h.substeps = std::max(d->substeps, 1);
   for (int k = 0; k < 3; k++) h.grav[k] = d->gravity[k];
   {
     double tc = std::max((double)d->solref[0], 2.0 * (double)d->timestep), zeta = d->solref[1], dmax = d->solimp[1];
@@ -369,6 +370,10 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
     ws = std::max(ws, off + b.size);
   }
   h.ws_floats = std::max(ws, 1);
+  // environments per warp block: the largest power of two <= 32 whose workspaces fit in shared memory
+  h.soa = 32;
+  while (h.soa > 1 && (size_t)4 * h.soa * h.ws_floats > (size_t)kMaxSmem) h.soa /= 2;
+  if ((size_t)4 * h.ws_floats > (size_t)kMaxSmem) return set_error(PG_ECAPACITY, "one environment's workspace exceeds shared memory");
   // ---- debug record layout ----
   int q = 0;
   auto dbg = [&](int n) { int r = q; q += n; return r; };

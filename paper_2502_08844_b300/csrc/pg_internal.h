@@ -21,13 +21,14 @@ constexpr int kMaxBody = 64;
 constexpr int kMaxSlot = 64;
 constexpr int kMaxRow = 128;     // active-set masks are 4 x 32 bits per environment
 constexpr int kMaxEnvsPerCta = 256;
+constexpr int kMaxSmem = 232448;       // 227 KB opt-in shared memory per block
 constexpr int kMaxModels = 8;          // models per batch (their blobs travel as a kernel parameter)
 constexpr int kMaxParamWords = 7168;   // 28 KB of blob words in the kernel's parameter space
 
 struct ModelHdr {
   // counts
   int nbody, njnt, nq, nv, nu, ngeom, npair, nslot, nrow_max, max_contacts, nlimited, nL;
-  int cap, cone, tree_hessian, ncol_max;
+  int cap, cone, tree_hessian, ncol_max, soa, substeps;
   // options (float32)
   float h, grav[3], kref, bref, solimp[5], margin;
   // table offsets (words from the blob start)

@@ -326,6 +326,7 @@ __device__ __forceinline__ void contact_frame(float3 n, float3& t1, float3& t2) 
 // ---------------------------------------------------------------------------------------
 struct Ctx {
   const ModelHdr& h;
+  int S;   // element stride of the structure-of-arrays workspace (environments per warp block)
   const int* __restrict__ I;
   const float* __restrict__ F;
   float* __restrict__ w;
@@ -336,13 +337,13 @@ struct Ctx {
 
 #define MI(name, i) (c.I[c.h.o_##name + (i)])
 #define MF(name, i) (c.F[c.h.o_##name + (i)])
-#define W(name, i) (c.w[(c.h.w_##name + (i)) * 32])
+#define W(name, i) (c.w[(c.h.w_##name + (i)) * c.S])
 
 __device__ __forceinline__ float3 W3(const Ctx& c, int off) {
-  return make_float3(c.w[off * 32], c.w[(off + 1) * 32], c.w[(off + 2) * 32]);
+  return make_float3(c.w[off * c.S], c.w[(off + 1) * c.S], c.w[(off + 2) * c.S]);
 }
 __device__ __forceinline__ void S3(const Ctx& c, int off, float3 v) {
-  c.w[off * 32] = v.x; c.w[(off + 1) * 32] = v.y; c.w[(off + 2) * 32] = v.z;
+  c.w[off * c.S] = v.x; c.w[(off + 1) * c.S] = v.y; c.w[(off + 2) * c.S] = v.z;
 }
 __device__ __forceinline__ float3 T3(const float* t) { return make_float3(t[0], t[1], t[2]); }
 
@@ -360,7 +361,7 @@ __device__ __forceinline__ void body_frame(const Ctx& c, int b, float3& x, Quat&
   } else {
     x = W3(c, c.h.w_xpos + 3 * b);
     const int o = c.h.w_xquat + 4 * b;
-    q = Quat{c.w[o * 32], c.w[(o + 1) * 32], c.w[(o + 2) * 32], c.w[(o + 3) * 32]};
+    q = Quat{c.w[o * c.S], c.w[(o + 1) * c.S], c.w[(o + 2) * c.S], c.w[(o + 3) * c.S]};
   }
 }
 
@@ -415,7 +416,7 @@ __device__ void kinematics(const Ctx& c) {
     q = qnormalize(q);
     S3(c, h.w_xpos + 3 * b, x);
     const int qo = h.w_xquat + 4 * b;
-    c.w[qo * 32] = q.w; c.w[(qo + 1) * 32] = q.x; c.w[(qo + 2) * 32] = q.y; c.w[(qo + 3) * 32] = q.z;
+    c.w[qo * c.S] = q.w; c.w[(qo + 1) * c.S] = q.x; c.w[(qo + 2) * c.S] = q.y; c.w[(qo + 3) * c.S] = q.z;
     // spatial inertia about o: I_com(world) + m (|c|^2 1 - c c^T), h = m c
     float R[9];
     qmat(q, R);
@@ -431,25 +432,26 @@ __device__ void kinematics(const Ctx& c) {
     const float3 cc = com - o;
     const float c2 = dot3(cc, cc);
     const int ci = h.w_cinert + 10 * b;
-    c.w[(ci + 0) * 32] = T[0] * R[0] + T[1] * R[1] + T[2] * R[2] + m * (c2 - cc.x * cc.x);
-    c.w[(ci + 1) * 32] = T[3] * R[3] + T[4] * R[4] + T[5] * R[5] + m * (c2 - cc.y * cc.y);
-    c.w[(ci + 2) * 32] = T[6] * R[6] + T[7] * R[7] + T[8] * R[8] + m * (c2 - cc.z * cc.z);
-    c.w[(ci + 3) * 32] = T[0] * R[3] + T[1] * R[4] + T[2] * R[5] - m * cc.x * cc.y;
-    c.w[(ci + 4) * 32] = T[0] * R[6] + T[1] * R[7] + T[2] * R[8] - m * cc.x * cc.z;
-    c.w[(ci + 5) * 32] = T[3] * R[6] + T[4] * R[7] + T[5] * R[8] - m * cc.y * cc.z;
-    c.w[(ci + 6) * 32] = m * cc.x;
-    c.w[(ci + 7) * 32] = m * cc.y;
-    c.w[(ci + 8) * 32] = m * cc.z;
-    c.w[(ci + 9) * 32] = m;
+    c.w[(ci + 0) * c.S] = T[0] * R[0] + T[1] * R[1] + T[2] * R[2] + m * (c2 - cc.x * cc.x);
+    c.w[(ci + 1) * c.S] = T[3] * R[3] + T[4] * R[4] + T[5] * R[5] + m * (c2 - cc.y * cc.y);
+    c.w[(ci + 2) * c.S] = T[6] * R[6] + T[7] * R[7] + T[8] * R[8] + m * (c2 - cc.z * cc.z);
+    c.w[(ci + 3) * c.S] = T[0] * R[3] + T[1] * R[4] + T[2] * R[5] - m * cc.x * cc.y;
+    c.w[(ci + 4) * c.S] = T[0] * R[6] + T[1] * R[7] + T[2] * R[8] - m * cc.x * cc.z;
+    c.w[(ci + 5) * c.S] = T[3] * R[6] + T[4] * R[7] + T[5] * R[8] - m * cc.y * cc.z;
+    c.w[(ci + 6) * c.S] = m * cc.x;
+    c.w[(ci + 7) * c.S] = m * cc.y;
+    c.w[(ci + 8) * c.S] = m * cc.z;
+    c.w[(ci + 9) * c.S] = m;
   }
 }
 
 // spatial inertia (about o) times a motion vector (w; v)
 __device__ __forceinline__ void inert_mul(const Ctx& c, int ci, float3 w, float3 v, float3& fa, float3& fl) {
-  const float* q = c.w + ci * 32;
-  const float i0 = q[0], i1 = q[32], i2 = q[64], i3 = q[96], i4 = q[128], i5 = q[160];
-  const float3 hc = make_float3(q[192], q[224], q[256]);
-  const float m = q[288];
+  const float* q = c.w + ci * c.S;
+  const int S = c.S;
+  const float i0 = q[0], i1 = q[S], i2 = q[2 * S], i3 = q[3 * S], i4 = q[4 * S], i5 = q[5 * S];
+  const float3 hc = make_float3(q[6 * S], q[7 * S], q[8 * S]);
+  const float m = q[9 * S];
   fa = make_float3(i0 * w.x + i3 * w.y + i4 * w.z, i3 * w.x + i1 * w.y + i5 * w.z, i4 * w.x + i5 * w.y + i2 * w.z) +
        cross3(hc, v);
   fl = v * m - cross3(hc, w);
@@ -542,56 +544,56 @@ __device__ void crba(const Ctx& c) {
 // ancestor pattern (no fill-in); row k ends as (D_k, L_k,parent(k), ...)
 __device__ void ldl_factor(const Ctx& c, int A) {
   const ModelHdr& h = c.h;
-  float* a = c.w + A * 32;
+  float* a = c.w + A * c.S;
   for (int k = h.nv - 1; k >= 0; k--) {
     const int r0 = MI(dof_rowadr, k), dk = MI(dof_depth, k);
-    const float dinv = 1.f / a[r0 * 32];
+    const float dinv = 1.f / a[r0 * c.S];
     for (int t = 1; t <= dk; t++) {
       const int ri = MI(dof_rowadr, MI(Lcol, r0 + t));
-      const float lt = a[(r0 + t) * 32] * dinv;
-      for (int s = t; s <= dk; s++) a[(ri + s - t) * 32] -= lt * a[(r0 + s) * 32];
+      const float lt = a[(r0 + t) * c.S] * dinv;
+      for (int s = t; s <= dk; s++) a[(ri + s - t) * c.S] -= lt * a[(r0 + s) * c.S];
     }
-    for (int t = 1; t <= dk; t++) a[(r0 + t) * 32] *= dinv;
+    for (int t = 1; t <= dk; t++) a[(r0 + t) * c.S] *= dinv;
   }
 }
 
 // x <- A^-1 x with the packed factor of A (x: element offset of an nv-vector)
 __device__ void ldl_solve(const Ctx& c, int A, int X) {
   const ModelHdr& h = c.h;
-  const float* a = c.w + A * 32;
-  float* x = c.w + X * 32;
+  const float* a = c.w + A * c.S;
+  float* x = c.w + X * c.S;
   for (int k = h.nv - 1; k >= 0; k--) {
     const int r0 = MI(dof_rowadr, k), dk = MI(dof_depth, k);
-    const float xk = x[k * 32];
-    for (int t = 1; t <= dk; t++) x[MI(Lcol, r0 + t) * 32] -= a[(r0 + t) * 32] * xk;
+    const float xk = x[k * c.S];
+    for (int t = 1; t <= dk; t++) x[MI(Lcol, r0 + t) * c.S] -= a[(r0 + t) * c.S] * xk;
   }
-  for (int k = 0; k < h.nv; k++) x[k * 32] /= a[MI(dof_rowadr, k) * 32];
+  for (int k = 0; k < h.nv; k++) x[k * c.S] /= a[MI(dof_rowadr, k) * c.S];
   for (int k = 0; k < h.nv; k++) {
     const int r0 = MI(dof_rowadr, k), dk = MI(dof_depth, k);
-    float s = x[k * 32];
-    for (int t = 1; t <= dk; t++) s -= a[(r0 + t) * 32] * x[MI(Lcol, r0 + t) * 32];
-    x[k * 32] = s;
+    float s = x[k * c.S];
+    for (int t = 1; t <= dk; t++) s -= a[(r0 + t) * c.S] * x[MI(Lcol, r0 + t) * c.S];
+    x[k * c.S] = s;
   }
 }
 
 // y = M x with M stored packed symmetric (x, y: element offsets of nv-vectors)
 __device__ void sym_mul(const Ctx& c, int Mo, int X, int Y) {
   const ModelHdr& h = c.h;
-  const float* m = c.w + Mo * 32;
-  const float* x = c.w + X * 32;
-  float* y = c.w + Y * 32;
-  for (int j = 0; j < h.nv; j++) y[j * 32] = 0.f;
+  const float* m = c.w + Mo * c.S;
+  const float* x = c.w + X * c.S;
+  float* y = c.w + Y * c.S;
+  for (int j = 0; j < h.nv; j++) y[j * c.S] = 0.f;
   for (int j = 0; j < h.nv; j++) {
     const int r0 = MI(dof_rowadr, j), dj = MI(dof_depth, j);
-    const float xj = x[j * 32];
-    float yj = m[r0 * 32] * xj;
+    const float xj = x[j * c.S];
+    float yj = m[r0 * c.S] * xj;
     for (int t = 1; t <= dj; t++) {
       const int i = MI(Lcol, r0 + t);
-      const float mji = m[(r0 + t) * 32];
-      yj = fmaf(mji, x[i * 32], yj);
-      y[i * 32] = fmaf(mji, xj, y[i * 32]);
+      const float mji = m[(r0 + t) * c.S];
+      yj = fmaf(mji, x[i * c.S], yj);
+      y[i * c.S] = fmaf(mji, xj, y[i * c.S]);
     }
-    y[j * 32] += yj;
+    y[j * c.S] += yj;
   }
 }
 
@@ -724,8 +726,8 @@ __device__ int collide(const Ctx& c, uint32_t& status, float* dbg) {
       if (!act) continue;
       if (nc >= h.max_contacts) { status |= PG_STATUS_CAPACITY; continue; }
       const int o = h.w_con + kConFloats * nc;
-      c.w[o * 32] = (float)(s0 + i);
-      c.w[(o + 1) * 32] = k[i].dist;
+      c.w[o * c.S] = (float)(s0 + i);
+      c.w[(o + 1) * c.S] = k[i].dist;
       S3(c, o + 2, k[i].pos);
       S3(c, o + 5, k[i].n);
       nc++;
@@ -744,17 +746,17 @@ __device__ int collide(const Ctx& c, uint32_t& status, float* dbg) {
 // (padding columns are zero and point at the first column).
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ int con_pair(const Ctx& c, int k) {
-  return MI(slot_pair, (int)c.w[(c.h.w_con + kConFloats * k) * 32]);
+  return MI(slot_pair, (int)c.w[(c.h.w_con + kConFloats * k) * c.S]);
 }
 
 __device__ void build_rows(const Ctx& c, int nc) {
   const ModelHdr& h = c.h;
   const int NC = h.ncol_max;
   for (int k = 0; k < h.max_contacts; k++) {
-    float* J = c.w + (h.w_J + 3 * NC * k) * 32;
-    float* gc = c.w + (h.w_gcol + NC * k) * 32;
+    float* J = c.w + (h.w_J + 3 * NC * k) * c.S;
+    float* gc = c.w + (h.w_gcol + NC * k) * c.S;
     if (k >= nc) {
-      for (int a = 0; a < NC; a++) { J[a * 32] = 0.f; J[(NC + a) * 32] = 0.f; J[(2 * NC + a) * 32] = 0.f; gc[a * 32] = 0.f; }
+      for (int a = 0; a < NC; a++) { J[a * c.S] = 0.f; J[(NC + a) * c.S] = 0.f; J[(2 * NC + a) * c.S] = 0.f; gc[a * c.S] = 0.f; }
       continue;
     }
     const int p = con_pair(c, k);
@@ -770,13 +772,13 @@ __device__ void build_rows(const Ctx& c, int nc) {
         const int d = MI(col_dof, ca + a), sg = MI(col_sign, ca + a);
         const float3 cw = W3(c, h.w_cdof + 6 * d), cl = W3(c, h.w_cdof + 6 * d + 3);
         const float3 jac = (cl + cross3(cw, pos - (sg > 0 ? o2 : o1))) * (float)sg;
-        J[a * 32] = dot3(n, jac);
-        J[(NC + a) * 32] = dot3(t1, jac);
-        J[(2 * NC + a) * 32] = dot3(t2, jac);
-        gc[a * 32] = __int_as_float(d);
+        J[a * c.S] = dot3(n, jac);
+        J[(NC + a) * c.S] = dot3(t1, jac);
+        J[(2 * NC + a) * c.S] = dot3(t2, jac);
+        gc[a * c.S] = __int_as_float(d);
       } else {
-        J[a * 32] = 0.f; J[(NC + a) * 32] = 0.f; J[(2 * NC + a) * 32] = 0.f;
-        gc[a * 32] = __int_as_float(ncol > 0 ? MI(col_dof, ca) : 0);
+        J[a * c.S] = 0.f; J[(NC + a) * c.S] = 0.f; J[(2 * NC + a) * c.S] = 0.f;
+        gc[a * c.S] = __int_as_float(ncol > 0 ? MI(col_dof, ca) : 0);
       }
     }
   }
@@ -799,23 +801,23 @@ __device__ __forceinline__ float edge_value(float mu, int e, float dn, float d1,
 __device__ void rows_dot(const Ctx& c, int X, int OUT) {
   const ModelHdr& h = c.h;
   const int NC = h.ncol_max, MC = h.max_contacts;
-  const float* x = c.w + X * 32;
+  const float* x = c.w + X * c.S;
   for (int k = 0; k < MC; k++) {
-    const float* J = c.w + (h.w_J + 3 * NC * k) * 32;
-    const float* gc = c.w + (h.w_gcol + NC * k) * 32;
+    const float* J = c.w + (h.w_J + 3 * NC * k) * c.S;
+    const float* gc = c.w + (h.w_gcol + NC * k) * c.S;
     float dn = 0.f, d1 = 0.f, d2 = 0.f;
     for (int a = 0; a < NC; a++) {
-      const float xa = x[__float_as_int(gc[a * 32]) * 32];
-      dn = fmaf(J[a * 32], xa, dn);
-      d1 = fmaf(J[(NC + a) * 32], xa, d1);
-      d2 = fmaf(J[(2 * NC + a) * 32], xa, d2);
+      const float xa = x[__float_as_int(gc[a * c.S]) * c.S];
+      dn = fmaf(J[a * c.S], xa, dn);
+      d1 = fmaf(J[(NC + a) * c.S], xa, d1);
+      d2 = fmaf(J[(2 * NC + a) * c.S], xa, d2);
     }
     const float mu = W(gmu, k);
-    for (int e = 0; e < 4; e++) c.w[(OUT + 4 * k + e) * 32] = edge_value(mu, e, dn, d1, d2);
+    for (int e = 0; e < 4; e++) c.w[(OUT + 4 * k + e) * c.S] = edge_value(mu, e, dn, d1, d2);
   }
   for (int li = 0; li < h.nlimited; li++) {
     const int d = MI(jnt_dofadr, MI(limit_jnt, li));
-    c.w[(OUT + 4 * MC + li) * 32] = W(lsgn, li) * x[d * 32];
+    c.w[(OUT + 4 * MC + li) * c.S] = W(lsgn, li) * x[d * c.S];
   }
 }
 
@@ -844,20 +846,20 @@ __device__ __forceinline__ void set_row(const Ctx& c, int r, bool valid, float p
 // when the model's pairs do not lie on single chains
 __device__ __forceinline__ void ltsolve_chain(const Ctx& c, float* z, int c0) {
   const ModelHdr& h = c.h;
-  const float* L = c.w + h.w_L * 32;
+  const float* L = c.w + h.w_L * c.S;
   if (h.tree_hessian) {
     const int rc = MI(dof_rowadr, c0), n = MI(dof_depth, c0);
     for (int t = 0; t <= n; t++) {
       const int k = MI(Lcol, rc + t);
-      const float zk = z[k * 32];
+      const float zk = z[k * c.S];
       const int r0 = MI(dof_rowadr, k), dk = MI(dof_depth, k);
-      for (int s = 1; s <= dk; s++) z[MI(Lcol, r0 + s) * 32] -= L[(r0 + s) * 32] * zk;
+      for (int s = 1; s <= dk; s++) z[MI(Lcol, r0 + s) * c.S] -= L[(r0 + s) * c.S] * zk;
     }
   } else {
     for (int k = h.nv - 1; k >= 0; k--) {
-      const float zk = z[k * 32];
+      const float zk = z[k * c.S];
       const int r0 = MI(dof_rowadr, k), dk = MI(dof_depth, k);
-      for (int s = 1; s <= dk; s++) z[MI(Lcol, r0 + s) * 32] -= L[(r0 + s) * 32] * zk;
+      for (int s = 1; s <= dk; s++) z[MI(Lcol, r0 + s) * c.S] -= L[(r0 + s) * c.S] * zk;
     }
   }
 }
@@ -868,7 +870,7 @@ __device__ __forceinline__ void ltsolve_chain(const Ctx& c, float* z, int c0) {
 __device__ void row_params(const Ctx& c, int nc) {
   const ModelHdr& h = c.h;
   const int nv = h.nv, NC = h.ncol_max, MC = h.max_contacts;
-  const float* L = c.w + h.w_L * 32;
+  const float* L = c.w + h.w_L * c.S;
   for (int k = 0; k < MC; k++) {
     const bool valid = k < nc;
     const int p = valid ? con_pair(c, k) : 0;
@@ -880,20 +882,20 @@ __device__ void row_params(const Ctx& c, int nc) {
     const bool valid = k < nc;
     const float mu = W(gmu, k), dist = valid ? W(con, kConFloats * k + 1) : 0.f;
     const bool pyr = W(gcond, k) == 3.f;
-    const float* J = c.w + (h.w_J + 3 * NC * k) * 32;
-    const float* gc = c.w + (h.w_gcol + NC * k) * 32;
+    const float* J = c.w + (h.w_J + 3 * NC * k) * c.S;
+    const float* gc = c.w + (h.w_gcol + NC * k) * c.S;
     float Ann = 1.f, An1 = 0.f, An2 = 0.f, A11 = 1.f, A22 = 1.f;
     if (valid) {
       const int c0 = __float_as_int(gc[0]);
       for (int s = 0; s < 3; s++) {
-        float* z = c.w + (h.w_z + s * nv) * 32;
-        for (int i = 0; i < nv; i++) z[i * 32] = 0.f;
-        for (int a = 0; a < NC; a++) z[__float_as_int(gc[a * 32]) * 32] += J[(s * NC + a) * 32];
+        float* z = c.w + (h.w_z + s * nv) * c.S;
+        for (int i = 0; i < nv; i++) z[i * c.S] = 0.f;
+        for (int a = 0; a < NC; a++) z[__float_as_int(gc[a * c.S]) * c.S] += J[(s * NC + a) * c.S];
         ltsolve_chain(c, z, c0);
       }
       Ann = An1 = An2 = A11 = A22 = 0.f;
       for (int i = 0; i < nv; i++) {
-        const float dinv = 1.f / L[MI(dof_rowadr, i) * 32];
+        const float dinv = 1.f / L[MI(dof_rowadr, i) * c.S];
         const float zn = W(z, i), z1 = W(z, nv + i), z2 = W(z, 2 * nv + i);
         Ann = fmaf(zn * zn, dinv, Ann);
         An1 = fmaf(zn * z1, dinv, An1);
@@ -920,17 +922,17 @@ __device__ void row_params(const Ctx& c, int nc) {
     float A = 1.f;
     if (sgn != 0.f) {
       // (M^-1)_dd = sum_k z_k^2 / D_k with z = L^-T e_d, supported on d's chain
-      float* z = c.w + h.w_z * 32;
-      for (int i = 0; i < nv; i++) z[i * 32] = 0.f;
-      z[d * 32] = 1.f;
+      float* z = c.w + h.w_z * c.S;
+      for (int i = 0; i < nv; i++) z[i * c.S] = 0.f;
+      z[d * c.S] = 1.f;
       const int rc = MI(dof_rowadr, d), n = MI(dof_depth, d);
       A = 0.f;
       for (int t = 0; t <= n; t++) {
         const int k = MI(Lcol, rc + t);
-        const float zk = z[k * 32];
+        const float zk = z[k * c.S];
         const int r0 = MI(dof_rowadr, k), dk = MI(dof_depth, k);
-        for (int s = 1; s <= dk; s++) z[MI(Lcol, r0 + s) * 32] -= L[(r0 + s) * 32] * zk;
-        A = fmaf(zk * zk, 1.f / L[r0 * 32], A);
+        for (int s = 1; s <= dk; s++) z[MI(Lcol, r0 + s) * c.S] -= L[(r0 + s) * c.S] * zk;
+        A = fmaf(zk * zk, 1.f / L[r0 * c.S], A);
       }
     }
     set_row(c, 4 * MC + li, sgn != 0.f, pos, A);
@@ -942,7 +944,7 @@ __device__ void row_params(const Ctx& c, int nc) {
 // ---------------------------------------------------------------------------------------
 __device__ float cost_of(const Ctx& c, int X) {
   const ModelHdr& h = c.h;
-  for (int k = 0; k < h.nv; k++) W(t, k) = c.w[(X + k) * 32] - W(a0, k);
+  for (int k = 0; k < h.nv; k++) W(t, k) = c.w[(X + k) * c.S] - W(a0, k);
   sym_mul(c, h.w_M, h.w_t, h.w_g);
   float f = 0.f;
   for (int k = 0; k < h.nv; k++) f = fmaf(0.5f * W(t, k), W(g, k), f);
@@ -999,19 +1001,19 @@ __device__ bool newton_direction(const Ctx& c, const unsigned act[4], bool& zero
       else { c2 += sg * D; s2 += mu * mu * D; g2 += sg * DJ; }
     }
     if (Sn == 0.f) continue;
-    const float* J = c.w + (h.w_J + 3 * NC * k) * 32;
-    const float* gc = c.w + (h.w_gcol + NC * k) * 32;
+    const float* J = c.w + (h.w_J + 3 * NC * k) * c.S;
+    const float* gc = c.w + (h.w_gcol + NC * k) * c.S;
     for (int a = 0; a < NC; a++) {
-      const int da = __float_as_int(gc[a * 32]);
-      const float na = J[a * 32], ta = J[(NC + a) * 32], ua = J[(2 * NC + a) * 32];
+      const int da = __float_as_int(gc[a * c.S]);
+      const float na = J[a * c.S], ta = J[(NC + a) * c.S], ua = J[(2 * NC + a) * c.S];
       W(g, da) += gn * na + g1 * ta + g2 * ua;
       const float hn = Sn * na + c1 * ta + c2 * ua;
       const float ht = c1 * na + s1 * ta;
       const float hu = c2 * na + s2 * ua;
       const int ra = MI(dof_rowadr, da), depa = MI(dof_depth, da);
       for (int b = a; b < NC; b++) {
-        const int db = __float_as_int(gc[b * 32]);
-        const float v = hn * J[b * 32] + ht * J[(NC + b) * 32] + hu * J[(2 * NC + b) * 32];
+        const int db = __float_as_int(gc[b * c.S]);
+        const float v = hn * J[b * c.S] + ht * J[(NC + b) * c.S] + hu * J[(2 * NC + b) * c.S];
         if (tree) W(L, ra + depa - MI(dof_depth, db)) += v;
         else W(H, (da > db ? da * nv + db : db * nv + da)) += v;
       }
@@ -1200,12 +1202,12 @@ __device__ void substep(const Ctx& c, uint32_t& status, float* dbg, uint32_t cnt
       if (r < 4 * h.max_contacts) {
         const int k = r >> 2, e = r & 3;
         const float mu = W(gmu, k);
-        const float* J = c.w + (h.w_J + 3 * h.ncol_max * k) * 32;
-        const float* gc = c.w + (h.w_gcol + h.ncol_max * k) * 32;
+        const float* J = c.w + (h.w_J + 3 * h.ncol_max * k) * c.S;
+        const float* gc = c.w + (h.w_gcol + h.ncol_max * k) * c.S;
         for (int a = 0; a < h.ncol_max; a++)
-          o[__float_as_int(gc[a * 32])] += W(gcond, k) == 3.f
-              ? edge_value(mu, e, J[a * 32], J[(h.ncol_max + a) * 32], J[(2 * h.ncol_max + a) * 32])
-              : J[a * 32];
+          o[__float_as_int(gc[a * c.S])] += W(gcond, k) == 3.f
+              ? edge_value(mu, e, J[a * c.S], J[(h.ncol_max + a) * c.S], J[(2 * h.ncol_max + a) * c.S])
+              : J[a * c.S];
       } else {
         const int li = r - 4 * h.max_contacts, d = MI(jnt_dofadr, MI(limit_jnt, li));
         o[d] = W(lsgn, li);
@@ -1280,13 +1282,15 @@ template <bool DEBUG>
 __global__ void __launch_bounds__(kMaxEnvsPerCta) step_kernel(const __grid_constant__ StepArgs A) {
   extern __shared__ __align__(16) float smem[];
   const Tile tile = DEBUG ? A.dbg_tile : A.tiles[blockIdx.x];
-  const int t = threadIdx.x;
-  if (t >= tile.count) return;
   const uint32_t* blob = A.blob + A.model_off[tile.model];
   const ModelHdr& h = *reinterpret_cast<const ModelHdr*>(blob);
+  const int S = h.soa, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane >= S) return;
+  const int t = warp * S + lane;   // environment within the tile
+  if (t >= tile.count) return;
   const int64_t env = tile.env0 + t;
-  float* w = smem + (t >> 5) * (32 * h.ws_floats) + (t & 31);
-  Ctx c{h, reinterpret_cast<const int*>(blob), reinterpret_cast<const float*>(blob), w, A.ctrl, A.ld, env};
+  float* w = smem + warp * (S * h.ws_floats) + lane;
+  Ctx c{h, S, reinterpret_cast<const int*>(blob), reinterpret_cast<const float*>(blob), w, A.ctrl, A.ld, env};
   for (int k = 0; k < h.nq; k++) W(qpos, k) = A.qpos[k * A.ld + env];
   uint32_t status = 0;
   bool warm_bad = false;
@@ -1301,7 +1305,7 @@ __global__ void __launch_bounds__(kMaxEnvsPerCta) step_kernel(const __grid_const
     for (int k = 0; k < h.nv; k++) W(warm, k) = 0.f;
   }
   uint32_t cnt[3] = {0u, 0u, 0u};
-  const int nsub = DEBUG ? 1 : A.n_substeps;
+  const int nsub = DEBUG ? 1 : (A.n_substeps > 0 ? A.n_substeps : h.substeps);
   for (int s = 0; s < nsub; s++) substep<DEBUG>(c, status, A.dbg, cnt);
   for (int k = 0; k < h.nq; k++) A.qpos[k * A.ld + env] = W(qpos, k);
   for (int k = 0; k < h.nv; k++) {

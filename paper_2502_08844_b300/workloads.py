@@ -335,7 +335,147 @@ def quadruped() -> Model:
                    default_ctrl=stand, qpos_init=qpos)
 
 
-MODELS = {"cartpole": cartpole, "quadruped": quadruped}
+_ROT_Z_TO_Y = (math.cos(-math.pi / 4), math.sin(-math.pi / 4), 0.0, 0.0)   # capsule axis along +y
+_ROT_Z_TO_X = (math.cos(math.pi / 4), 0.0, math.sin(math.pi / 4), 0.0)     # capsule axis along +x
+
+# LEAP-hand style rotor (App. C.2.2): gear ratio 288.35, rotor 2.0 g, radius 4.12 mm
+HAND_ROTOR = (288.35, 2.0e-3, 4.12e-3)
+HAND_PHALANX = ((0.05, 0.05), (0.04, 0.04), (0.035, 0.03), (0.03, 0.02))   # (length, mass)
+HAND_CUBE = 0.07
+HAND_CUBE_Y = 0.025   # cube centre towards the finger roots: curled fingers reach its +y face
+
+
+def hand(max_contacts: int = 20) -> Model:
+    """Fixed-base 16-hinge hand with a free 7 cm cube (LEAP-like, App. C.2).  World-fixed palm box
+    0.12x0.10x0.02 m with its top face at z = 0; 4 fingers rooted on the palm's +y edge, each a
+    chain of 4 capsule phalanges (r 0.01; 0.05/0.04/0.035/0.03 m, 0.05/0.04/0.03/0.02 kg) with
+    joints abduction (z) then 3 flexions (x), and a fingertip sphere r 0.012.  Reflected rotor
+    inertia on every dof from the paper's servo numbers.  The cube rests on the palm near the
+    finger roots (centre y = 0.025).  Contacts: fingertip spheres and the
+    capsules of the last three phalanges against the cube, cube against palm; at most 20 active,
+    friction 1, pyramidal cone.  PD kp 3 kd 0.1; dt 5 ms, 10 substeps, Newton cap 6."""
+    b = ModelBuilder("hand")
+    palm = b.geom(0, BOX, (0.06, 0.05, 0.01), pos=(0, 0, -0.01))
+    tips, caps = [], []
+    for i in range(4):
+        parent, pos = 0, (-0.045 + 0.03 * i, 0.05, 0.0)
+        for s, (L, m) in enumerate(HAND_PHALANX):
+            link = b.body(parent, pos)
+            if s == 0:
+                b.joint(link, HINGE, axis=(0, 0, 1), limited=True, range=(-0.5, 0.5), rotor=HAND_ROTOR)
+            else:
+                b.joint(link, HINGE, axis=(1, 0, 0), limited=True, range=(-0.3, 1.6), rotor=HAND_ROTOR)
+            g = b.geom(link, CAPSULE, (0.01, L / 2), pos=(0, L / 2, 0), quat=_ROT_Z_TO_Y, mass=m)
+            if s > 0:
+                caps.append(g)
+            if s == 3:
+                tips.append(b.geom(link, SPHERE, (0.012,), pos=(0, L, 0), mass=0.0))
+            parent, pos = link, (0, L, 0)
+    cube = b.body(0, (0, HAND_CUBE_Y, HAND_CUBE / 2))
+    b.joint(cube, FREE)
+    cg = b.geom(cube, BOX, (HAND_CUBE / 2,) * 3, mass=0.1)
+    for t in tips:
+        b.pair(t, cg, friction=1.0, condim=3)
+    for g in caps:
+        b.pair(g, cg, friction=1.0, condim=3)
+    b.pair(palm, cg, friction=1.0, condim=3)
+    for j in range(16):   # targets are drawn within the joint's range
+        b.actuator(j, POSITION, kp=3.0, kd=0.1, ctrlrange=(-0.5, 0.5) if j % 4 == 0 else (-0.3, 1.6))
+    qpos = [0.0] * 16 + [0.0, HAND_CUBE_Y, HAND_CUBE / 2, 1.0, 0.0, 0.0, 0.0]
+    return b.build(timestep=0.005, iterations=6, cone=PYRAMIDAL, n_substeps=10, max_contacts=max_contacts,
+                   qpos_init=qpos)
+
+
+def humanoid() -> Model:
+    """Floating-base 29-hinge humanoid (G1-like, Sec. 4.2.2): pelvis with a free joint; waist
+    (3 hinges) carrying the torso and two 7-hinge arms (shoulder 3, elbow, wrist 3); two 6-hinge
+    legs (hip 3, knee, ankle 2) with box feet 0.2x0.08x0.03 m.  Capsule links 0.08-0.36 m, masses
+    scaled to 35 kg.  Contacts: each foot box against the plane (<= 4 points), each hand capsule
+    against the torso capsule; friction 1, pyramidal.  PD on every hinge (legs/waist kp 60 kd 2,
+    arms kp 20 kd 0.5), armature 0.01; dt 4 ms, 5 substeps, Newton cap 4."""
+    raw = {"pelvis": 6.0, "torso": 12.0, "thigh": 4.5, "shin": 2.5, "foot": 0.8, "upper": 1.5, "fore": 1.0,
+           "hand": 0.4}
+    total = raw["pelvis"] + raw["torso"] + 2 * (raw["thigh"] + raw["shin"] + raw["foot"] + raw["upper"] + raw["fore"]
+                                                 + raw["hand"])
+    s = 35.0 / total
+    ms = {k: v * s for k, v in raw.items()}
+    b = ModelBuilder("humanoid")
+    floor = b.geom(0, PLANE, (0, 0, 0))
+    z0 = 0.05 + 0.4 + 0.4 + 0.05 + 0.015 + 0.001
+    pelvis = b.body(0, (0, 0, z0))
+    b.joint(pelvis, FREE)
+    b.geom(pelvis, CAPSULE, (0.07, 0.08), quat=_ROT_Z_TO_Y, mass=ms["pelvis"])
+    torso = b.body(pelvis, (0, 0, 0.1))
+    arm = dict(armature=0.01, limited=True)
+    for ax in ((0, 0, 1), (1, 0, 0), (0, 1, 0)):
+        b.joint(torso, HINGE, axis=ax, range=(-0.5, 0.5), **arm)
+    torso_g = b.geom(torso, CAPSULE, (0.1, 0.12), pos=(0, 0, 0.2), mass=ms["torso"])
+    hips, shoulders = [], []
+    for side in (1, -1):
+        hips.append(b.body(pelvis, (0, 0.1 * side, -0.05)))
+    for side in (1, -1):
+        shoulders.append(b.body(torso, (0, 0.22 * side, 0.3)))
+    knees, ankles, feet = [], [], []
+    for h_ in hips:
+        b.joint(h_, HINGE, axis=(1, 0, 0), range=(-0.5, 0.5), **arm)
+        b.joint(h_, HINGE, axis=(0, 0, 1), range=(-0.5, 0.5), **arm)
+        b.joint(h_, HINGE, axis=(0, 1, 0), range=(-1.5, 1.0), **arm)
+        b.geom(h_, CAPSULE, (0.06, 0.18), pos=(0, 0, -0.2), mass=ms["thigh"])
+    elbows, wrists, hands = [], [], []
+    for sh in shoulders:
+        b.joint(sh, HINGE, axis=(0, 1, 0), range=(-1.5, 1.5), **arm)
+        b.joint(sh, HINGE, axis=(1, 0, 0), range=(-1.5, 1.5), **arm)
+        b.joint(sh, HINGE, axis=(0, 0, 1), range=(-1.5, 1.5), **arm)
+        b.geom(sh, CAPSULE, (0.04, 0.12), pos=(0, 0, -0.14), mass=ms["upper"])
+    for h_ in hips:
+        k = b.body(h_, (0, 0, -0.4))
+        b.joint(k, HINGE, axis=(0, 1, 0), range=(-0.1, 2.3), **arm)
+        b.geom(k, CAPSULE, (0.05, 0.18), pos=(0, 0, -0.2), mass=ms["shin"])
+        knees.append(k)
+    for sh in shoulders:
+        e = b.body(sh, (0, 0, -0.28))
+        b.joint(e, HINGE, axis=(0, 1, 0), range=(-2.5, 0.0), **arm)
+        b.geom(e, CAPSULE, (0.035, 0.1), pos=(0, 0, -0.12), mass=ms["fore"])
+        elbows.append(e)
+    for k in knees:
+        a = b.body(k, (0, 0, -0.4))
+        b.joint(a, HINGE, axis=(0, 1, 0), range=(-0.8, 0.8), **arm)
+        b.joint(a, HINGE, axis=(1, 0, 0), range=(-0.4, 0.4), **arm)
+        feet.append(b.geom(a, BOX, (0.1, 0.04, 0.015), pos=(0.03, 0, -0.05), mass=ms["foot"]))
+        ankles.append(a)
+    for e in elbows:
+        w = b.body(e, (0, 0, -0.25))
+        b.joint(w, HINGE, axis=(0, 0, 1), range=(-0.8, 0.8), **arm)
+        b.joint(w, HINGE, axis=(0, 1, 0), range=(-0.8, 0.8), **arm)
+        b.joint(w, HINGE, axis=(1, 0, 0), range=(-0.8, 0.8), **arm)
+        hands.append(b.geom(w, CAPSULE, (0.04, 0.04), pos=(0, 0, -0.06), mass=ms["hand"]))
+        wrists.append(w)
+    for f in feet:
+        b.pair(floor, f, friction=1.0, condim=3)
+    for hg in hands:
+        b.pair(torso_g, hg, friction=1.0, condim=3)
+    # PD on every hinge, in joint order; the first 3 hinges (waist) and the legs are stiffer
+    legs = set()
+    for j in range(1, b_njnt(b)):
+        body = b.joints[j]["body"]
+        if body in hips or body in knees or body in ankles or body == torso:
+            legs.add(j)
+    for j in range(1, b_njnt(b)):
+        if j in legs:
+            b.actuator(j, POSITION, kp=60.0, kd=2.0)
+        else:
+            b.actuator(j, POSITION, kp=20.0, kd=0.5)
+    nh = b_njnt(b) - 1
+    qpos = [0.0, 0.0, z0, 1.0, 0.0, 0.0, 0.0] + [0.0] * nh
+    return b.build(timestep=0.004, iterations=4, cone=PYRAMIDAL, n_substeps=5, max_contacts=16,
+                   default_ctrl=[0.0] * nh, qpos_init=qpos)
+
+
+def b_njnt(b: ModelBuilder) -> int:
+    return len(b.joints)
+
+
+MODELS = {"cartpole": cartpole, "quadruped": quadruped, "hand": hand, "humanoid": humanoid}
 
 
 def model(name: str) -> Model:

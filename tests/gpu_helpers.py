@@ -86,3 +86,48 @@ def rel_err(x, ref, atol=1e-6):
     if np.all(over <= 0):
         return 0.0
     return float(np.max(np.where(over > 0, over / np.maximum(np.abs(ref), 1e-300), 0.0)))
+
+
+class MixedRun:
+    """Several models in one batch (one launch per control step)."""
+
+    def __init__(self, parts, envs_per_cta: int = 0, device="cuda"):
+        self.parts = parts                      # [(workloads.Model, count)]
+        self.cms = {}
+        models = []
+        for m, n in parts:
+            if id(m) not in self.cms:
+                self.cms[id(m)] = core.CompiledModel(m)
+            models.append((self.cms[id(m)], n))
+        self.batch = core.Batch(models, envs_per_cta=envs_per_cta)
+        self.state = core.State(self.batch, device)
+        self.offs = list(np.cumsum([0] + [n for _, n in parts]))
+        self.n = self.offs[-1]
+        self.device = device
+
+    def set_state(self, qs, vs):
+        ld = self.state.ld
+        Q = np.zeros((self.batch.nq_max, ld), np.float32)
+        V = np.zeros((self.batch.nv_max, ld), np.float32)
+        for (m, n), o, q, v in zip(self.parts, self.offs, qs, vs):
+            Q[:m.nq, o:o + n] = q.T
+            V[:m.nv, o:o + n] = v.T
+        self.state.qpos.copy_(torch.from_numpy(Q))
+        self.state.qvel.copy_(torch.from_numpy(V))
+        self.state.qacc_warm.zero_()
+        self.state.status.zero_()
+
+    def ctrl_tensor(self, us):
+        U = np.zeros((max(self.batch.nu_max, 1), self.state.ld), np.float32)
+        for (m, n), o, u in zip(self.parts, self.offs, us):
+            U[:m.nu, o:o + n] = u.T
+        return torch.from_numpy(U).to(self.device)
+
+    def get(self):
+        torch.cuda.synchronize()
+        out = []
+        for (m, n), o in zip(self.parts, self.offs):
+            q = self.state.qpos[:m.nq, o:o + n].cpu().numpy().T.astype(np.float64)
+            v = self.state.qvel[:m.nv, o:o + n].cpu().numpy().T.astype(np.float64)
+            out.append((q, v))
+        return out

@@ -20,6 +20,10 @@ pytestmark = pytest.mark.gpu
 ONE_STEP_RTOL, ONE_STEP_ATOL = 1e-5, 1e-6
 ROLLOUT_RTOL = 1e-3
 FORCE_RTOL = 1e-3
+# Ahat = (J M^-1 J^T)_rr carries M^-1's conditioning and D = d / ((1 - d) Ahat) amplifies the
+# rounding of the impedance d by d / (1 - d) <= 19 (d <= dwidth = 0.95): FP32 intermediates
+# that are 10x looser than the state they produce
+ROW_DERIVED_RTOL = {"D": 1e-4, "Ahat": 1e-4, "force": 1e-4}   # force = D (aref - J a)
 
 
 def scaled_err(x, ref):
@@ -29,8 +33,11 @@ def scaled_err(x, ref):
     return max(d, 0.0) / max(np.abs(ref).max(), 1e-30)
 
 
-def assert_close_scaled(name, x, ref, rtol):
-    e = scaled_err(x, ref)
+def assert_close_scaled(name, x, ref, rtol, scale=None):
+    """max|x - ref| <= rtol * scale + 1e-6, scale = max|ref| unless given"""
+    x = np.asarray(x, np.float64); ref = np.asarray(ref, np.float64)
+    s = np.abs(ref).max() if scale is None else scale
+    e = max(np.abs(x - ref).max() - ONE_STEP_ATOL, 0.0) / max(s, 1e-30)
     assert e <= rtol, "%s: scaled error %.3e > %.1e" % (name, e, rtol)
 
 
@@ -48,7 +55,7 @@ def _contact_states(n_states=6):
     return m, om, out
 
 
-PHASE_FIELDS = ["xpos", "xmat", "xcom", "M", "bias", "passive", "actuator", "a0", "qacc", "qvel_next"]
+PHASE_FIELDS = ["xpos", "xmat", "xcom", "M", "bias", "passive", "actuator", "a0", "qacc"]
 
 
 def _phase_compare(m, om, q, v, u, warm=None, env=5, n=8):
@@ -59,6 +66,9 @@ def _phase_compare(m, om, q, v, u, warm=None, env=5, n=8):
     o = om.forward(q, v, w, u)
     for k in PHASE_FIELDS:
         assert_close_scaled(k, g[k], o[k], ONE_STEP_RTOL)
+    # qvel_next = qvel + h qacc: its rounding scales with the acceleration term as well
+    vscale = max(np.abs(o["qvel_next"]).max(), m.timestep * np.abs(o["qacc"]).max())
+    assert_close_scaled("qvel_next", g["qvel_next"], o["qvel_next"], ONE_STEP_RTOL, vscale)
     assert_close_scaled("qpos_next", canon_qpos(m, g["qpos_next"]), canon_qpos(m, o["qpos_next"]), ONE_STEP_RTOL)
     # contacts: same active set (no slot within 1e-6 of the margin here), same geometry
     if m.npair:
@@ -71,7 +81,7 @@ def _phase_compare(m, om, q, v, u, warm=None, env=5, n=8):
         nv = m.nv
         assert_close_scaled("J", g["rows"][:, :nv], o["rows"][:, :nv], ONE_STEP_RTOL)
         for i, k in enumerate(["r", "v", "aref", "D", "Ahat", "imp", "force"]):
-            assert_close_scaled(k, g["rows"][:, nv + i], o["rows"][:, nv + i], ONE_STEP_RTOL)
+            assert_close_scaled(k, g["rows"][:, nv + i], o["rows"][:, nv + i], ROW_DERIVED_RTOL.get(k, ONE_STEP_RTOL))
     assert g["iterations"] == o["iterations"]
     return g, o
 
@@ -258,3 +268,76 @@ def test_debug_substep_matches_step():
     q2, v2, _ = r2.get()
     assert np.array_equal(d["qpos_next"].astype(np.float32), q2[6].astype(np.float32))
     assert np.array_equal(d["qvel_next"].astype(np.float32), v2[6].astype(np.float32))
+
+
+# --------------------------------------------------------------------------------------
+# hand (dense Hessian; box-box, capsule-box, sphere-box) and humanoid (box-plane,
+# capsule-capsule self contact, nv = 35)
+# --------------------------------------------------------------------------------------
+
+def _rollout_states(m, cfg, times, n_env=4):
+    om = O.OracleModel(m)
+    q0, v0 = W.initial_state(m, cfg, n_env)
+    T = max(times) + 2
+    U = W.actions(m, cfg, n_env, 0, T)
+    _, _, _, _, tq, tv = om.rollout(q0, v0, U, m.n_substeps, trajectory=True, nthreads=4)
+    out = []
+    for t in times:
+        for e in range(n_env):
+            out.append((tq[t, e].astype(np.float32).astype(np.float64), tv[t, e].astype(np.float32).astype(np.float64),
+                        U[t + 1, e].astype(np.float64)))
+    return om, out
+
+
+@pytest.mark.parametrize("mname,cfg", [("hand", 2), ("humanoid", 3)])
+def test_phase_parity_hand_and_humanoid(mname, cfg):
+    m = W.model(mname)
+    om, states = _rollout_states(m, cfg, (0, 6, 30))
+    nrows = []
+    for q, v, u in states:
+        g, o = _phase_compare(m, om, q, v, u, env=1, n=4)
+        nrows.append(g["nrow"])
+    assert max(nrows) >= 16
+
+
+@pytest.mark.parametrize("mname,cfg,n,T,rtol", [("hand", 2, 40, 1, ONE_STEP_RTOL), ("humanoid", 3, 33, 1, ONE_STEP_RTOL),
+                                                 ("hand", 2, 24, 20, ROLLOUT_RTOL), ("humanoid", 3, 24, 50, ROLLOUT_RTOL)])
+def test_trajectories_hand_and_humanoid(mname, cfg, n, T, rtol):
+    m, tqg, tvg, tqo, tvo, stg, sto = _trajectory_parity(mname, cfg, n, T)
+    for e in range(n):
+        assert_close_scaled("qpos env %d" % e, canon_qpos(m, tqg[-1, e]), canon_qpos(m, tqo[-1, e]), rtol)
+        assert_close_scaled("qvel env %d" % e, tvg[-1, e], tvo[-1, e], rtol)
+
+
+# --------------------------------------------------------------------------------------
+# mixed-model batch: one launch, every environment with its own model's timestep and substeps
+# --------------------------------------------------------------------------------------
+
+def _mixed_parity(parts, T, epc=0):
+    from tests.gpu_helpers import MixedRun
+    run = MixedRun([(W.model(nm), n) for nm, cfg, n in parts], envs_per_cta=epc)
+    inits, Us = [], []
+    for nm, cfg, n in parts:
+        m = W.model(nm)
+        q0, v0 = W.initial_state(m, cfg, n)
+        inits.append((q0, v0))
+        Us.append(W.actions(m, cfg, n, 0, T))
+    run.set_state([q for q, _ in inits], [v for _, v in inits])
+    for t in range(T):
+        from paper_2502_08844_b300 import core
+        core.step(run.batch, run.state, run.ctrl_tensor([U[t] for U in Us]), 0)
+    got = run.get()
+    for (nm, cfg, n), (q0, v0), U, (qg, vg) in zip(parts, inits, Us, got):
+        m = W.model(nm)
+        qo, vo, _, _ = O.OracleModel(m).rollout(q0, v0, U, m.n_substeps, nthreads=4)
+        for e in range(n):
+            assert_close_scaled("%s qpos %d" % (nm, e), canon_qpos(m, qg[e]), canon_qpos(m, qo[e]), 1e-4)
+            assert_close_scaled("%s qvel %d" % (nm, e), vg[e], vo[e], 1e-4)
+
+
+def test_mixed_batch_in_order():
+    _mixed_parity([("cartpole", 0, 37), ("quadruped", 1, 45), ("humanoid", 3, 29)], 3)
+
+
+def test_mixed_batch_interleaved_and_forced_tiles():
+    _mixed_parity([("quadruped", 1, 20), ("cartpole", 0, 30), ("humanoid", 3, 15), ("cartpole", 0, 11)], 2, epc=8)
