@@ -282,3 +282,52 @@ def solid_inertia(gtype, size, mass):
 
 def rotor_armature(kg, mr, rr):
     return lib().orc_rotor_armature(float(kg), float(mr), float(rr))
+
+
+def _setup_grad_api():
+    L = lib()
+    if getattr(L, "_grad_ready", False):
+        return L
+    L.orc_rollout_loss.restype = C.c_double
+    L.orc_rollout_loss.argtypes = [C.c_void_p, _dp, _dp, _dp, C.c_int, C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+    L.orc_rollout_grad.argtypes = [C.c_void_p, _dp, _dp, _dp, C.c_int, C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp,
+                                   _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+    L._grad_ready = True
+    return L
+
+
+def tracking_loss_weights(om: "OracleModel", z_target=0.27, v_target=(0.5, 0.0, 0.0)):
+    """Weights/targets of the torso-tracking loss sum_t (z_t - z*)^2 + |v_t - v*|^2 (free-joint
+    height qpos[2] and world linear velocity qvel[0:3])."""
+    wq = np.zeros(om.nq); qs = np.zeros(om.nq); wv = np.zeros(om.nv); vs = np.zeros(om.nv)
+    wq[2] = 1.0; qs[2] = z_target
+    wv[:3] = 1.0; vs[:3] = v_target
+    return wq, qs, wv, vs
+
+
+def _opt(a):
+    return None if a is None else _pd(_d(a))
+
+
+def rollout_loss(om: "OracleModel", q0, v0, ctrl, n_substeps, weights, solver_cap=-1, mass=None, damping=None, kp=None):
+    L = _setup_grad_api()
+    ctrl = _d(ctrl).reshape(-1, om.nu)
+    wq, qs, wv, vs = [_d(x) for x in weights]
+    return L.orc_rollout_loss(om.h, _pd(_d(q0)), _pd(_d(v0)), _pd(ctrl), ctrl.shape[0], int(n_substeps), int(solver_cap),
+                              _opt(mass), _opt(damping), _opt(kp), _pd(wq), _pd(qs), _pd(wv), _pd(vs))
+
+
+def rollout_grad(om: "OracleModel", q0, v0, ctrl, n_substeps, weights, solver_cap=-1, mass=None, damping=None, kp=None):
+    """Reverse-mode gradient of rollout_loss: dict with loss, q0, v0, u [T,nu], mass, damping, kp."""
+    L = _setup_grad_api()
+    ctrl = _d(ctrl).reshape(-1, om.nu)
+    T = ctrl.shape[0]
+    wq, qs, wv, vs = [_d(x) for x in weights]
+    out = {"q0": np.zeros(om.nq), "v0": np.zeros(om.nv), "u": np.zeros((T, om.nu)), "mass": np.zeros(om.nbody),
+           "damping": np.zeros(om.nv), "kp": np.zeros(om.nu)}
+    loss = C.c_double(0)
+    L.orc_rollout_grad(om.h, _pd(_d(q0)), _pd(_d(v0)), _pd(ctrl), T, int(n_substeps), int(solver_cap), _opt(mass),
+                       _opt(damping), _opt(kp), _pd(wq), _pd(qs), _pd(wv), _pd(vs), _pd(out["q0"]), _pd(out["v0"]),
+                       _pd(out["u"]), _pd(out["mass"]), _pd(out["damping"]), _pd(out["kp"]), C.byref(loss))
+    out["loss"] = loss.value
+    return out

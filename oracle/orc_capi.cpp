@@ -9,6 +9,7 @@
 #include <thread>
 #include <vector>
 
+#include "orc_ad.hpp"
 #include "orc_model.hpp"
 #include "orc_step.hpp"
 
@@ -293,6 +294,107 @@ double orc_cost(int nv, const double* M, const double* a0, int nr, const double*
   R.aref.assign(aref, aref + nr);
   R.D.assign(D, D + nr);
   return orc::cost(nv, Mm, aa, R, x);
+}
+
+// ---- rollout loss and its reverse-mode gradient ----------------------------------------
+// Loss over a rollout of T control steps (n_substeps each) from (q0, v0) with controls
+// ctrl[T][nu]:  L = sum_{t=1..T} sum_i wq_i (q_t,i - qs_i)^2 + sum_i wv_i (v_t,i - vs_i)^2.
+// Optional parameters (NULL = the model's): body masses [nbody], dof damping [nv], kp [nu].
+static orc::Params<double> make_params(const Model& m, const double* mass, const double* damp, const double* kp) {
+  orc::Params<double> P;
+  P.mass = mass ? std::vector<double>(mass, mass + m.nbody) : m.mass;
+  P.damping = damp ? std::vector<double>(damp, damp + m.nv) : m.dof_damping;
+  P.kp.resize(m.nu);
+  for (int a = 0; a < m.nu; a++) P.kp[a] = kp ? kp[a] : m.act_kp[a];
+  return P;
+}
+
+static double step_loss(const Model& m, const double* q, const double* v, const double* wq, const double* qs,
+                        const double* wv, const double* vs) {
+  double L = 0;
+  for (int i = 0; i < m.nq; i++) L += wq[i] * (q[i] - qs[i]) * (q[i] - qs[i]);
+  for (int i = 0; i < m.nv; i++) L += wv[i] * (v[i] - vs[i]) * (v[i] - vs[i]);
+  return L;
+}
+
+double orc_rollout_loss(void* h, const double* q0, const double* v0, const double* ctrl, int T, int n_substeps,
+                        int solver_cap, const double* mass, const double* damp, const double* kp, const double* wq,
+                        const double* qs, const double* wv, const double* vs) {
+  const Model& m = *static_cast<Model*>(h);
+  orc::Params<double> P = make_params(m, mass, damp, kp);
+  std::vector<double> q(q0, q0 + m.nq), v(v0, v0 + m.nv), w(m.nv, 0.0);
+  double L = 0;
+  for (int t = 0; t < T; t++) {
+    for (int s = 0; s < n_substeps; s++) orc::substep<double>(m, q.data(), v.data(), w.data(), ctrl + (size_t)t * m.nu, solver_cap, nullptr, &P);
+    L += step_loss(m, q.data(), v.data(), wq, qs, wv, vs);
+  }
+  return L;
+}
+
+// Gradient of orc_rollout_loss by reverse mode: states are kept after every control step and
+// each step is taped from its start state (inputs q, v, u and the parameters; the solver's
+// warm start enters as a constant), then swept backward with the state adjoint of the next step.
+int orc_rollout_grad(void* h, const double* q0, const double* v0, const double* ctrl, int T, int n_substeps,
+                     int solver_cap, const double* mass, const double* damp, const double* kp, const double* wq,
+                     const double* qs, const double* wv, const double* vs, double* gq0, double* gv0, double* gu,
+                     double* gmass, double* gdamp, double* gkp, double* loss) {
+  using orc::adouble;
+  const Model& m = *static_cast<Model*>(h);
+  const int nq = m.nq, nv = m.nv, nu = m.nu, nb = m.nbody;
+  orc::Params<double> P = make_params(m, mass, damp, kp);
+  std::vector<std::vector<double>> Q(T + 1), V(T + 1), Wm(T + 1);
+  Q[0].assign(q0, q0 + nq); V[0].assign(v0, v0 + nv); Wm[0].assign(nv, 0.0);
+  double L = 0;
+  for (int t = 0; t < T; t++) {
+    Q[t + 1] = Q[t]; V[t + 1] = V[t]; Wm[t + 1] = Wm[t];
+    for (int s = 0; s < n_substeps; s++)
+      orc::substep<double>(m, Q[t + 1].data(), V[t + 1].data(), Wm[t + 1].data(), ctrl + (size_t)t * nu, solver_cap, nullptr, &P);
+    L += step_loss(m, Q[t + 1].data(), V[t + 1].data(), wq, qs, wv, vs);
+  }
+  if (loss) *loss = L;
+  std::vector<double> bq(nq), bv(nv);
+  for (int i = 0; i < nq; i++) bq[i] = 2 * wq[i] * (Q[T][i] - qs[i]);
+  for (int i = 0; i < nv; i++) bv[i] = 2 * wv[i] * (V[T][i] - vs[i]);
+  std::fill(gmass, gmass + nb, 0.0);
+  std::fill(gdamp, gdamp + nv, 0.0);
+  std::fill(gkp, gkp + nu, 0.0);
+  orc::Tape tp;
+  orc::tape() = &tp;
+  for (int t = T - 1; t >= 0; t--) {
+    tp.clear();
+    std::vector<adouble> q(nq), v(nv), u(nu), w(nv);
+    for (int i = 0; i < nq; i++) q[i] = adouble::var(Q[t][i]);
+    for (int i = 0; i < nv; i++) v[i] = adouble::var(V[t][i]);
+    for (int i = 0; i < nu; i++) u[i] = adouble::var(ctrl[(size_t)t * nu + i]);
+    for (int i = 0; i < nv; i++) w[i] = adouble(Wm[t][i]);
+    orc::Params<adouble> PA;
+    for (int b = 0; b < nb; b++) PA.mass.push_back(adouble::var(P.mass[b]));
+    for (int i = 0; i < nv; i++) PA.damping.push_back(adouble::var(P.damping[i]));
+    for (int a = 0; a < nu; a++) PA.kp.push_back(adouble::var(P.kp[a]));
+    std::vector<int> iq(nq), iv(nv), iu(nu);
+    for (int i = 0; i < nq; i++) iq[i] = q[i].i;
+    for (int i = 0; i < nv; i++) iv[i] = v[i].i;
+    for (int i = 0; i < nu; i++) iu[i] = u[i].i;
+    for (int s = 0; s < n_substeps; s++) orc::substep<adouble>(m, q.data(), v.data(), w.data(), u.data(), solver_cap, nullptr, &PA);
+    std::vector<std::pair<int, double>> seeds;
+    for (int i = 0; i < nq; i++) seeds.push_back({q[i].i, bq[i]});
+    for (int i = 0; i < nv; i++) seeds.push_back({v[i].i, bv[i]});
+    std::vector<double> adj = tp.backward(seeds);
+    for (int i = 0; i < nq; i++) bq[i] = adj[iq[i]];
+    for (int i = 0; i < nv; i++) bv[i] = adj[iv[i]];
+    for (int i = 0; i < nu; i++) gu[(size_t)t * nu + i] = adj[iu[i]];
+    for (int b = 0; b < nb; b++) gmass[b] += adj[PA.mass[b].i];
+    for (int i = 0; i < nv; i++) gdamp[i] += adj[PA.damping[i].i];
+    for (int a = 0; a < nu; a++) gkp[a] += adj[PA.kp[a].i];
+    if (t >= 1) {
+      for (int i = 0; i < nq; i++) bq[i] += 2 * wq[i] * (Q[t][i] - qs[i]);
+      for (int i = 0; i < nv; i++) bv[i] += 2 * wv[i] * (V[t][i] - vs[i]);
+    }
+  }
+  orc::tape() = nullptr;
+  std::memcpy(gq0, bq.data(), sizeof(double) * nq);
+  std::memcpy(gv0, bv.data(), sizeof(double) * nv);
+  return 0;
 }
 
 double orc_impedance(double r, const double* solimp) { return orc::impedance(r, solimp); }

@@ -29,6 +29,17 @@ namespace orc {
 
 using std::sqrt;
 
+// Optional differentiable model parameters (a tape scalar can take derivatives through them):
+// body masses (a body's inertia scales with its mass, its centre of mass is unchanged), dof
+// damping and actuator kp.  A null pointer means the model's own constants.
+template <class T> struct Params {
+  std::vector<T> mass, damping, kp;
+};
+
+template <class T> inline T body_mass(const Model& m, const Params<T>* P, int b) {
+  return P ? P->mass[b] : T(m.mass[b]);
+}
+
 // ------------------------------------------------------------------------------------
 // kinematics
 // ------------------------------------------------------------------------------------
@@ -51,7 +62,7 @@ template <class T> inline V3<T> cv3(const double* p) { return V3<T>{T(p[0]), T(p
 // World frame of every body: X(b) = X(parent) * X_offset(b) * prod_j X_joint(j, q_j).
 // Hinge: rotation by q about the axis through the anchor; slide: translation q along the axis;
 // free: position qpos[0:3] and the normalised quaternion qpos[3:7] (the parent is the world).
-template <class T> void kinematics(const Model& m, const T* qpos, Kin<T>& k) {
+template <class T> void kinematics(const Model& m, const T* qpos, Kin<T>& k, const Params<T>* P = nullptr) {
   k.xbody.assign(m.nbody, xf_identity<T>());
   k.xcom.assign(m.nbody, V3<T>{T(0), T(0), T(0)});
   k.Iw.assign(m.nbody, M3<T>{});
@@ -83,6 +94,8 @@ template <class T> void kinematics(const Model& m, const T* qpos, Kin<T>& k) {
     k.xcom[b] = xform(X, cv3<T>(&m.ipos[3 * b]));
     const double* I = &m.inertia[6 * b];
     M3<T> Ib{T(I[0]), T(I[3]), T(I[4]), T(I[3]), T(I[1]), T(I[5]), T(I[4]), T(I[5]), T(I[2])};
+    if (P && m.mass[b] > 0)
+      for (int q = 0; q < 9; q++) Ib[q] = Ib[q] * (P->mass[b] / m.mass[b]);
     k.Iw[b] = mm(X.R, mm(Ib, mT(X.R)));
   }
   k.xgeom.resize(m.ngeom);
@@ -130,7 +143,7 @@ template <class T> void point_jacobian(const Model& m, const Kin<T>& k, int b, c
 
 // M = sum_b ( m_b Jv(com_b)^T Jv(com_b) + Jw_b^T Iw_b Jw_b ) + diag(armature):
 // the matrix of the kinetic energy 1/2 qdot^T M qdot (rotor inertia on the diagonal).
-template <class T> void mass_matrix(const Model& m, const Kin<T>& k, std::vector<T>& M) {
+template <class T> void mass_matrix(const Model& m, const Kin<T>& k, std::vector<T>& M, const Params<T>* P = nullptr) {
   const int nv = m.nv;
   M.assign(nv * nv, T(0));
   std::vector<T> Jv, Jw;
@@ -139,7 +152,7 @@ template <class T> void mass_matrix(const Model& m, const Kin<T>& k, std::vector
     for (int i = 0; i < nv; i++)
       for (int j = 0; j < nv; j++) {
         T s = T(0);
-        for (int r = 0; r < 3; r++) s = s + T(m.mass[b]) * Jv[r * nv + i] * Jv[r * nv + j];
+        for (int r = 0; r < 3; r++) s = s + body_mass(m, P, b) * Jv[r * nv + i] * Jv[r * nv + j];
         for (int r = 0; r < 3; r++)
           for (int c = 0; c < 3; c++) s = s + Jw[r * nv + i] * k.Iw[b][3 * r + c] * Jw[c * nv + j];
         M[i * nv + j] = M[i * nv + j] + s;
@@ -199,7 +212,8 @@ template <class T> inline V3<T> point_acc(const Motion<T>& s, const V3<T>& P) {
 // Inverse dynamics tau = M(q) qdd + c(q, qd) by Newton-Euler: per body the force
 // m (a_com - g) and the torque about the COM Iw al + w x Iw w, mapped to generalised forces
 // with the body's Jacobians (virtual work); plus armature * qdd.
-template <class T> void inverse_dynamics(const Model& m, const Kin<T>& k, const T* qvel, const T* qacc, std::vector<T>& tau) {
+template <class T> void inverse_dynamics(const Model& m, const Kin<T>& k, const T* qvel, const T* qacc, std::vector<T>& tau,
+                                         const Params<T>* P = nullptr) {
   const int nv = m.nv;
   std::vector<Motion<T>> mo;
   body_motion(m, k, qvel, qacc, mo);
@@ -208,7 +222,7 @@ template <class T> void inverse_dynamics(const Model& m, const Kin<T>& k, const 
   std::vector<T> Jv, Jw;
   for (int b = 1; b < m.nbody; b++) {
     V3<T> ac = point_acc(mo[b], k.xcom[b]);
-    V3<T> F = scl(sub(ac, g), T(m.mass[b]));
+    V3<T> F = scl(sub(ac, g), body_mass(m, P, b));
     V3<T> Iwv = mv(k.Iw[b], mo[b].w);
     V3<T> N = add(mv(k.Iw[b], mo[b].al), cross(mo[b].w, Iwv));
     point_jacobian(m, k, b, k.xcom[b], Jv, Jw);
@@ -739,7 +753,8 @@ template <class T> struct Forward {
 
 // Actuation: motor tau += gear * u (u clamped to ctrlrange when ctrllimited);
 // position (PD, eq. pd_mapping) tau += kp (u - q) - kd qdot on the actuated joint.
-template <class T> void actuation(const Model& m, const T* qpos, const T* qvel, const T* ctrl, std::vector<T>& tau) {
+template <class T> void actuation(const Model& m, const T* qpos, const T* qvel, const T* ctrl, std::vector<T>& tau,
+                                  const Params<T>* P = nullptr) {
   tau.assign(m.nv, T(0));
   for (int a = 0; a < m.nu; a++) {
     int j = m.act_jnt[a], d = m.jnt_dofadr[j], qa = m.jnt_qposadr[j];
@@ -749,7 +764,7 @@ template <class T> void actuation(const Model& m, const T* qpos, const T* qvel, 
       if (val(u) > m.act_ctrlrange[2 * a + 1]) u = T(m.act_ctrlrange[2 * a + 1]);
     }
     if (m.act_type[a] == MOTOR) tau[d] = tau[d] + T(m.act_gear[a]) * u;
-    else tau[d] = tau[d] + T(m.act_kp[a]) * (u - qpos[qa]) - T(m.act_kd[a]) * qvel[d];
+    else tau[d] = tau[d] + (P ? P->kp[a] : T(m.act_kp[a])) * (u - qpos[qa]) - T(m.act_kd[a]) * qvel[d];
   }
 }
 
@@ -829,15 +844,15 @@ template <class T> void build_rows(const Model& m, const Forward<T>& F, const T*
 
 // solver_cap < 0 selects the converged mode (cap 200, exact termination only)
 template <class T> void forward(const Model& m, const T* qpos, const T* qvel, const T* qacc_warm, const T* ctrl,
-                                int solver_cap, Forward<T>& F) {
+                                int solver_cap, Forward<T>& F, const Params<T>* P = nullptr) {
   const int nv = m.nv;
-  kinematics(m, qpos, F.kin);
-  mass_matrix(m, F.kin, F.M);
+  kinematics(m, qpos, F.kin, P);
+  mass_matrix(m, F.kin, F.M, P);
   std::vector<T> zero(nv, T(0));
-  inverse_dynamics(m, F.kin, qvel, zero.data(), F.bias);
+  inverse_dynamics(m, F.kin, qvel, zero.data(), F.bias, P);
   F.passive.assign(nv, T(0));
-  for (int i = 0; i < nv; i++) F.passive[i] = -T(m.dof_damping[i]) * qvel[i];
-  actuation(m, qpos, qvel, ctrl, F.actuator);
+  for (int i = 0; i < nv; i++) F.passive[i] = -(P ? P->damping[i] : T(m.dof_damping[i])) * qvel[i];
+  actuation(m, qpos, qvel, ctrl, F.actuator, P);
   std::vector<T> Mchol(F.M);
   if (!cholesky(Mchol, nv)) F.status |= ST_NAN;
   F.a0.assign(nv, T(0));
@@ -892,11 +907,11 @@ template <class T> void integrate_pos(const Model& m, T* qpos, const T* qvel, do
 }
 
 template <class T> uint32_t substep(const Model& m, T* qpos, T* qvel, T* qacc_warm, const T* ctrl, int solver_cap,
-                                    Forward<T>* keep = nullptr) {
+                                    Forward<T>* keep = nullptr, const Params<T>* P = nullptr) {
   Forward<T> local;
   Forward<T>& F = keep ? *keep : local;
   F = Forward<T>();
-  forward(m, qpos, qvel, qacc_warm, ctrl, solver_cap, F);
+  forward(m, qpos, qvel, qacc_warm, ctrl, solver_cap, F, P);
   const int nv = m.nv;
   for (int i = 0; i < nv; i++) qvel[i] = qvel[i] + T(m.timestep) * F.sol.qacc[i];
   integrate_pos(m, qpos, qvel, m.timestep);

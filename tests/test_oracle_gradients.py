@@ -1,0 +1,61 @@
+"""Pins of the oracle's reverse-mode rollout gradient against FP64 central differences
+(step 1e-6) with the converged solver.  CPU only."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2502_08844_b300 import workloads as W
+
+EPS = 1e-6
+
+
+def _setup(T=4, env=0):
+    m = W.quadruped()
+    om = O.OracleModel(m)
+    q0, v0 = W.initial_state(m, 4, env + 1)
+    U = W.actions(m, 4, env + 1, 0, T)[:, env]
+    w = O.tracking_loss_weights(om)
+    mass, _, _, _ = om.massprops()
+    return m, om, q0[env].astype(np.float64), v0[env].astype(np.float64), U.astype(np.float64), w, mass
+
+
+def _fd(f, x, idx):
+    out = []
+    for i in idx:
+        xp, xm = x.copy(), x.copy()
+        xp.flat[i] += EPS
+        xm.flat[i] -= EPS
+        out.append((f(xp) - f(xm)) / (2 * EPS))
+    return np.array(out)
+
+
+def _close(a, b, rtol=1e-4, atol=1e-6):
+    a, b = np.asarray(a), np.asarray(b)
+    scale = max(np.abs(b).max(), 1e-12)
+    assert np.abs(a - b).max() <= rtol * scale + atol, (a, b)
+
+
+def test_gradient_matches_central_differences_state_and_controls():
+    m, om, q0, v0, U, w, mass = _setup()
+    g = O.rollout_grad(om, q0, v0, U, 5, w)
+    assert g["loss"] == pytest.approx(O.rollout_loss(om, q0, v0, U, 5, w), rel=1e-12)
+    # qpos: torso position, a quaternion component and the leg joints; qvel all
+    qi = [0, 1, 2, 4, 7, 9, 12, 15, 18]
+    _close(g["q0"][qi], _fd(lambda x: O.rollout_loss(om, x, v0, U, 5, w), q0, qi))
+    vi = list(range(18))
+    _close(g["v0"][vi], _fd(lambda x: O.rollout_loss(om, q0, x, U, 5, w), v0, vi))
+    ui = [0, 5, 11, 12 + 3, 36 + 8]
+    _close(g["u"].flat[ui], _fd(lambda x: O.rollout_loss(om, q0, v0, x.reshape(U.shape), 5, w), U, ui))
+
+
+def test_gradient_matches_central_differences_parameters():
+    m, om, q0, v0, U, w, mass = _setup()
+    damping = np.zeros(18)
+    kp = np.full(12, float(np.float32(35.0)))
+    g = O.rollout_grad(om, q0, v0, U, 5, w, mass=mass, damping=damping, kp=kp)
+    bi = list(range(1, 10))
+    _close(g["mass"][bi], _fd(lambda x: O.rollout_loss(om, q0, v0, U, 5, w, mass=x, damping=damping, kp=kp), mass, bi))
+    di = [0, 3, 6, 8, 14, 17]
+    _close(g["damping"][di], _fd(lambda x: O.rollout_loss(om, q0, v0, U, 5, w, mass=mass, damping=x, kp=kp), damping, di))
+    ki = list(range(12))
+    _close(g["kp"][ki], _fd(lambda x: O.rollout_loss(om, q0, v0, U, 5, w, mass=mass, damping=damping, kp=x), kp, ki))
