@@ -99,17 +99,24 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def kernel_source_hash() -> str:
+    """sha256 (first 16 hex digits) of the step kernel's sources: its device functions, kernels
+    and internal layout header, in that order."""
+    h = hashlib.sha256()
+    for f in ("step_device.cuh", "step.cu", "pg_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_2502_08844_b300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def kernel_traffic(workload: str):
     """DRAM bytes per launch from a committed ncu summary, valid only for the current kernel source."""
     p = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
-    src = os.path.join(ROOT, "paper_2502_08844_b300", "csrc", "step.cu")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     ent = d.get(workload)
-    if not ent or ent.get("step_cu_sha256_16") != h:
+    if not ent or ent.get("kernel_source_sha256_16") != kernel_source_hash():
         return None
     return ent.get("dram_bytes_per_launch")
 

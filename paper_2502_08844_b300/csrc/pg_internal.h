@@ -57,8 +57,9 @@ struct ModelHdr {
 constexpr int kHdrWords = (int)(sizeof(ModelHdr) / 4);
 static_assert(sizeof(ModelHdr) % 4 == 0, "header must be whole words");
 
-// per active contact in the workspace: slot, dist, pos[3], n[3]
-constexpr int kConFloats = 8;
+// per active contact in the workspace: slot, dist, pos[3], n[3], feature (the capsule endpoint or
+// box corner a plane contact comes from; 0 otherwise)
+constexpr int kConFloats = 9;
 
 // one thread block's work: `count` consecutive envs starting at `env0` of model `model`
 struct Tile {

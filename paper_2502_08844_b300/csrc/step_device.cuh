@@ -1,0 +1,1254 @@
+// Device functions of the physics step: vector and quaternion algebra, collision primitives and
+// every phase of one substep for one environment (a thread), over a structure-of-arrays
+// workspace (element i of environment l at w[i * S + l], S the structure-of-arrays width).
+// Included by the step kernels and by the adjoint kernels; everything lives in an anonymous
+// namespace, one copy per translation unit.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "pg.h"
+#include "pg_internal.h"
+
+namespace pg {
+namespace {
+
+
+// ---------------------------------------------------------------------------------------
+// small vector algebra
+// ---------------------------------------------------------------------------------------
+struct Quat {
+  float w, x, y, z;
+};
+
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator*(float3 a, float s) { return make_float3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+  return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float3 ld3(const float* p) { return make_float3(p[0], p[1], p[2]); }
+__device__ __forceinline__ void st3(float* p, float3 v) { p[0] = v.x; p[1] = v.y; p[2] = v.z; }
+__device__ __forceinline__ Quat ldq(const float* p) { return Quat{p[0], p[1], p[2], p[3]}; }
+__device__ __forceinline__ void stq(float* p, Quat q) { p[0] = q.w; p[1] = q.x; p[2] = q.y; p[3] = q.z; }
+
+__device__ __forceinline__ Quat qmul(Quat a, Quat b) {
+  return Quat{a.w * b.w - a.x * b.x - a.y * b.y - a.z * b.z, a.w * b.x + a.x * b.w + a.y * b.z - a.z * b.y,
+              a.w * b.y - a.x * b.z + a.y * b.w + a.z * b.x, a.w * b.z + a.x * b.y - a.y * b.x + a.z * b.w};
+}
+__device__ __forceinline__ Quat qnormalize(Quat q) {
+  float s = rsqrtf(q.w * q.w + q.x * q.x + q.y * q.y + q.z * q.z);
+  return Quat{q.w * s, q.x * s, q.y * s, q.z * s};
+}
+// rotate v by the unit quaternion q: v + 2 w (u x v) + 2 u x (u x v)
+__device__ __forceinline__ float3 qrot(Quat q, float3 v) {
+  float3 u = make_float3(q.x, q.y, q.z);
+  float3 t = cross3(u, v) * 2.0f;
+  return v + t * q.w + cross3(u, t);
+}
+__device__ __forceinline__ void qmat(Quat q, float* R) {
+  float xx = q.x * q.x, yy = q.y * q.y, zz = q.z * q.z, xy = q.x * q.y, xz = q.x * q.z, yz = q.y * q.z;
+  float wx = q.w * q.x, wy = q.w * q.y, wz = q.w * q.z;
+  R[0] = 1 - 2 * (yy + zz); R[1] = 2 * (xy - wz); R[2] = 2 * (xz + wy);
+  R[3] = 2 * (xy + wz); R[4] = 1 - 2 * (xx + zz); R[5] = 2 * (yz - wx);
+  R[6] = 2 * (xz - wy); R[7] = 2 * (yz + wx); R[8] = 1 - 2 * (xx + yy);
+}
+__device__ __forceinline__ float3 mat_col(const float* R, int k) { return make_float3(R[k], R[3 + k], R[6 + k]); }
+__device__ __forceinline__ float3 mat_mul(const float* R, float3 v) {
+  return make_float3(R[0] * v.x + R[1] * v.y + R[2] * v.z, R[3] * v.x + R[4] * v.y + R[5] * v.z,
+                     R[6] * v.x + R[7] * v.y + R[8] * v.z);
+}
+__device__ __forceinline__ float3 mat_tmul(const float* R, float3 v) {   // R^T v
+  return make_float3(R[0] * v.x + R[3] * v.y + R[6] * v.z, R[1] * v.x + R[4] * v.y + R[7] * v.z,
+                     R[2] * v.x + R[5] * v.y + R[8] * v.z);
+}
+
+// ---------------------------------------------------------------------------------------
+// collision primitives (per thread)
+// ---------------------------------------------------------------------------------------
+struct Con {
+  float dist;
+  float3 pos, n;
+  int feat = 0;   // capsule endpoint / box corner index of a plane contact
+};
+
+__device__ Con sphere_sphere(float3 c1, float r1, float3 c2, float r2) {
+  Con k;
+  const float3 d = c2 - c1;
+  const float L = sqrtf(dot3(d, d));
+  k.n = L > 1e-12f ? d * (1.f / L) : make_float3(0.f, 0.f, 1.f);
+  k.dist = L - r1 - r2;
+  k.pos = ((c1 + k.n * r1) + (c2 - k.n * r2)) * 0.5f;
+  return k;
+}
+
+__device__ Con plane_sphere(float3 p0, float3 nz, float3 c, float r) {
+  Con k;
+  const float hgt = dot3(nz, c - p0);
+  k.n = nz;
+  k.dist = hgt - r;
+  k.pos = c - nz * (r + 0.5f * k.dist);
+  return k;
+}
+
+// sphere (geom1) vs box (geom2): clamped closest point outside, least-penetration face inside
+__device__ Con sphere_box(float3 c, float r, float3 bp, const float* bR, float3 hs) {
+  Con k;
+  const float3 p = mat_tmul(bR, c - bp);
+  const float hh[3] = {hs.x, hs.y, hs.z};
+  const float pp[3] = {p.x, p.y, p.z};
+  float q[3];
+  bool inside = true;
+#pragma unroll
+  for (int i = 0; i < 3; i++) {
+    q[i] = fminf(fmaxf(pp[i], -hh[i]), hh[i]);
+    if (pp[i] > hh[i] || pp[i] < -hh[i]) inside = false;
+  }
+  float3 out_dir, surf;
+  if (!inside) {
+    const float3 dl = make_float3(pp[0] - q[0], pp[1] - q[1], pp[2] - q[2]);
+    const float L = sqrtf(dot3(dl, dl));
+    out_dir = mat_mul(bR, dl * (1.f / L));
+    surf = make_float3(q[0], q[1], q[2]);
+    k.dist = L - r;
+  } else {
+    int kb = 0;
+    float best = hh[0] - fabsf(pp[0]);
+#pragma unroll
+    for (int i = 1; i < 3; i++) {
+      const float s = hh[i] - fabsf(pp[i]);
+      if (s < best) { best = s; kb = i; }
+    }
+    const float sg = pp[kb] >= 0.f ? 1.f : -1.f;
+    float ev[3] = {0.f, 0.f, 0.f};
+    ev[kb] = sg;
+    out_dir = mat_mul(bR, make_float3(ev[0], ev[1], ev[2]));
+    float sf[3] = {pp[0], pp[1], pp[2]};
+    sf[kb] = sg * hh[kb];
+    surf = make_float3(sf[0], sf[1], sf[2]);
+    k.dist = -(hh[kb] - sg * pp[kb]) - r;
+  }
+  k.n = out_dir * -1.f;
+  k.pos = ((bp + mat_mul(bR, surf)) + (c + k.n * r)) * 0.5f;
+  return k;
+}
+
+// closest points of c1 + u a1 (|u| <= h1) and c2 + v a2 (|v| <= h2)
+__device__ void seg_seg(float3 c1, float3 a1, float h1, float3 c2, float3 a2, float h2, float& u, float& v) {
+  const float3 r = c1 - c2;
+  const float b = dot3(a1, a2), c = dot3(a1, r), f = dot3(a2, r);
+  const float den = 1.f - b * b;
+  u = den > 1e-10f ? fminf(fmaxf((b * f - c) / den, -h1), h1) : 0.f;
+  v = fminf(fmaxf(b * u + f, -h2), h2);
+  u = fminf(fmaxf(b * v - c, -h1), h1);
+}
+
+// box-box: separating axes (3 + 3 face normals, 9 edge products), face axes preferred within a
+// relative tolerance, face case by clipping the incident face against the reference face's
+// side planes, edge case by the closest points of the supporting edges.  Returns the count.
+__device__ int box_box(float3 pA, const float* RA, float3 hA3, float3 pB, const float* RB, float3 hB3, Con* out) {
+  const float hA[3] = {hA3.x, hA3.y, hA3.z}, hB[3] = {hB3.x, hB3.y, hB3.z};
+  float3 A[3], B[3];
+#pragma unroll
+  for (int k = 0; k < 3; k++) { A[k] = mat_col(RA, k); B[k] = mat_col(RB, k); }
+  const float3 dc = pB - pA;
+  float best_ov[3] = {0.f, 0.f, 0.f};
+  int best_ax[3] = {-1, -1, -1};
+  float3 axes_best[3];
+  for (int k = 0; k < 15; k++) {
+    float3 L;
+    if (k < 3) L = A[k];
+    else if (k < 6) L = B[k - 3];
+    else {
+      L = cross3(A[(k - 6) / 3], B[(k - 6) % 3]);
+      const float n = sqrtf(dot3(L, L));
+      if (!(n > 1e-6f)) continue;
+      L = L * (1.f / n);
+    }
+    float rA = 0.f, rB = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+      rA += hA[i] * fabsf(dot3(L, A[i]));
+      rB += hB[i] * fabsf(dot3(L, B[i]));
+    }
+    const float ov = rA + rB - fabsf(dot3(L, dc));
+    if (ov < 0.f) return 0;
+    const int grp = k < 3 ? 0 : (k < 6 ? 1 : 2);
+    if (best_ax[grp] < 0 || ov < best_ov[grp]) { best_ov[grp] = ov; best_ax[grp] = k; axes_best[grp] = L; }
+  }
+  int g = 0;
+  if (best_ov[1] < best_ov[0] - 1e-5f * (1.f + best_ov[0])) g = 1;
+  if (best_ax[2] >= 0 && best_ov[2] < best_ov[g] - 1e-5f * (1.f + best_ov[g])) g = 2;
+  const float depth = best_ov[g];
+  const int best = best_ax[g];
+  float3 n = axes_best[g];
+  if (dot3(n, dc) < 0.f) n = n * -1.f;
+  if (g == 2) {
+    const int i = (best - 6) / 3, j = (best - 6) % 3;
+    float3 ea = pA, eb = pB;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      if (k != i) ea = ea + A[k] * (dot3(n, A[k]) >= 0.f ? hA[k] : -hA[k]);
+      if (k != j) eb = eb + B[k] * (dot3(n, B[k]) >= 0.f ? -hB[k] : hB[k]);
+    }
+    float u, v;
+    seg_seg(ea, A[i], hA[i], eb, B[j], hB[j], u, v);
+    out[0].n = n;
+    out[0].dist = -depth;
+    out[0].pos = ((ea + A[i] * u) + (eb + B[j] * v)) * 0.5f;
+    return 1;
+  }
+  const bool refA = g == 0;
+  const float3 pR = refA ? pA : pB, pI = refA ? pB : pA;
+  const float3* AR = refA ? A : B;
+  const float3* AI = refA ? B : A;
+  const float* hR = refA ? hA : hB;
+  const float* hI = refA ? hB : hA;
+  const int kr = refA ? best : best - 3;
+  const float3 nref = refA ? n : n * -1.f;
+  int fk = 0;
+  float fs = 1.f, bd = 2.f;
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    const float dd = dot3(AI[k], nref);
+    if (dd < bd) { bd = dd; fk = k; fs = 1.f; }
+    if (-dd < bd) { bd = -dd; fk = k; fs = -1.f; }
+  }
+  const int ku = (fk + 1) % 3, kv = (fk + 2) % 3;
+  float3 poly[8], tmp[8];
+  int np = 4;
+  const float su[4] = {-1.f, 1.f, 1.f, -1.f}, sv[4] = {-1.f, -1.f, 1.f, 1.f};
+#pragma unroll
+  for (int c = 0; c < 4; c++) poly[c] = pI + AI[fk] * (fs * hI[fk]) + AI[ku] * (su[c] * hI[ku]) + AI[kv] * (sv[c] * hI[kv]);
+  const int ru = (kr + 1) % 3, rv = (kr + 2) % 3;
+  for (int pl = 0; pl < 4 && np > 0; pl++) {
+    const float3 pn = (pl < 2 ? AR[ru] : AR[rv]) * ((pl % 2 == 0) ? 1.f : -1.f);
+    const float ph = pl < 2 ? hR[ru] : hR[rv];
+    int no = 0;
+    float3 S = poly[np - 1];
+    float sS = ph - dot3(S - pR, pn);
+    for (int q = 0; q < np; q++) {
+      const float3 E = poly[q];
+      const float sE = ph - dot3(E - pR, pn);
+      if (sE >= 0.f) {
+        if (sS < 0.f && no < 8) tmp[no++] = S + (E - S) * (sS / (sS - sE));
+        if (no < 8) tmp[no++] = E;
+      } else if (sS >= 0.f && no < 8) {
+        tmp[no++] = S + (E - S) * (sS / (sS - sE));
+      }
+      S = E;
+      sS = sE;
+    }
+    np = no;
+    for (int q = 0; q < np; q++) poly[q] = tmp[q];
+  }
+  float dep[8];
+  int idx[8], nk = 0;
+  for (int q = 0; q < np; q++) {
+    dep[q] = hR[kr] - dot3(poly[q] - pR, nref);
+    if (dep[q] >= 0.f) idx[nk++] = q;
+  }
+  if (nk > 4) {
+    int keep[4];
+    int p0 = idx[0];
+    for (int q = 0; q < nk; q++) if (dep[idx[q]] > dep[p0]) p0 = idx[q];
+    int p1 = -1; float b1 = -1.f;
+    for (int q = 0; q < nk; q++) {
+      const int i = idx[q];
+      if (i == p0) continue;
+      const float3 dd = poly[i] - poly[p0];
+      const float dv = sqrtf(dot3(dd, dd));
+      if (dv > b1) { b1 = dv; p1 = i; }
+    }
+    int p2 = -1; float b2 = -1.f;
+    for (int q = 0; q < nk; q++) {
+      const int i = idx[q];
+      if (i == p0 || i == p1) continue;
+      const float3 cr = cross3(poly[p1] - poly[p0], poly[i] - poly[p0]);
+      const float a = sqrtf(dot3(cr, cr));
+      if (a > b2) { b2 = a; p2 = i; }
+    }
+    int p3 = -1; float b3 = -1.f;
+    for (int q = 0; q < nk; q++) {
+      const int i = idx[q];
+      if (i == p0 || i == p1 || i == p2) continue;
+      const float3 c1 = cross3(poly[p1] - poly[p0], poly[i] - poly[p0]);
+      const float3 c2 = cross3(poly[p2] - poly[p1], poly[i] - poly[p1]);
+      const float3 c3 = cross3(poly[p0] - poly[p2], poly[i] - poly[p2]);
+      const float a = sqrtf(dot3(c1, c1)) + sqrtf(dot3(c2, c2)) + sqrtf(dot3(c3, c3));
+      if (a > b3) { b3 = a; p3 = i; }
+    }
+    keep[0] = p0; keep[1] = p1; keep[2] = p2; keep[3] = p3;
+    // polygon order
+    for (int a = 0; a < 4; a++)
+      for (int b = a + 1; b < 4; b++)
+        if (keep[b] < keep[a]) { const int t = keep[a]; keep[a] = keep[b]; keep[b] = t; }
+    for (int a = 0; a < 4; a++) idx[a] = keep[a];
+    nk = 4;
+  }
+  for (int c = 0; c < nk; c++) {
+    const int i = idx[c];
+    out[c].n = n;
+    out[c].dist = -dep[i];
+    out[c].pos = poly[i] + nref * (0.5f * dep[i]);
+  }
+  return nk;
+}
+
+// frame: t1 = normalise(n x e_k) with e_k the world axis of smallest |n_k| (ties: lowest k)
+__device__ __forceinline__ void contact_frame(float3 n, float3& t1, float3& t2) {
+  const float a0 = fabsf(n.x), a1 = fabsf(n.y), a2 = fabsf(n.z);
+  int k = 0;
+  if (a1 < a0) k = 1;
+  if (a2 < (k == 0 ? a0 : a1)) k = 2;
+  const float3 ek = make_float3(k == 0 ? 1.f : 0.f, k == 1 ? 1.f : 0.f, k == 2 ? 1.f : 0.f);
+  float3 t = cross3(n, ek);
+  t1 = t * rsqrtf(dot3(t, t));
+  t2 = cross3(n, t1);
+}
+
+// ---------------------------------------------------------------------------------------
+// per-environment context: model tables in shared memory (broadcast reads), the thread's
+// structure-of-arrays workspace (element i at w[32 i]) and its controls in global memory
+// ---------------------------------------------------------------------------------------
+struct Ctx {
+  const ModelHdr& h;
+  int S;   // element stride of the structure-of-arrays workspace (environments per warp block)
+  const int* __restrict__ I;
+  const float* __restrict__ F;
+  float* __restrict__ w;
+  const float* __restrict__ ctrl;
+  int64_t ld;
+  int64_t env;
+};
+
+#define MI(name, i) (c.I[c.h.o_##name + (i)])
+#define MF(name, i) (c.F[c.h.o_##name + (i)])
+#define W(name, i) (c.w[(c.h.w_##name + (i)) * c.S])
+
+__device__ __forceinline__ float3 W3(const Ctx& c, int off) {
+  return make_float3(c.w[off * c.S], c.w[(off + 1) * c.S], c.w[(off + 2) * c.S]);
+}
+__device__ __forceinline__ void S3(const Ctx& c, int off, float3 v) {
+  c.w[off * c.S] = v.x; c.w[(off + 1) * c.S] = v.y; c.w[(off + 2) * c.S] = v.z;
+}
+__device__ __forceinline__ float3 T3(const float* t) { return make_float3(t[0], t[1], t[2]); }
+
+// reference point of body b's tree: the free root's position, else the root's fixed frame origin
+__device__ __forceinline__ float3 tree_origin(const Ctx& c, int b) {
+  const int r = MI(body_root, b), fa = MI(root_freeadr, r);
+  if (fa >= 0) return W3(c, c.h.w_qpos + fa);
+  return T3(&MF(body_pos, 3 * r));
+}
+
+__device__ __forceinline__ void body_frame(const Ctx& c, int b, float3& x, Quat& q) {
+  if (b == 0) {
+    x = make_float3(0.f, 0.f, 0.f);
+    q = Quat{1.f, 0.f, 0.f, 0.f};
+  } else {
+    x = W3(c, c.h.w_xpos + 3 * b);
+    const int o = c.h.w_xquat + 4 * b;
+    q = Quat{c.w[o * c.S], c.w[(o + 1) * c.S], c.w[(o + 2) * c.S], c.w[(o + 3) * c.S]};
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// kinematics: bodies in level order (parent before child), each from its parent's frame, the
+// body offset and its joints (hinge: rotation about the axis through the anchor; slide:
+// translation; free: qpos position and normalised quaternion).  On the way: the motion
+// subspace of every dof (cdof, angular;linear about the tree's reference point o) and the
+// body's spatial inertia about o (Ixx Iyy Izz Ixy Ixz Iyz, m c, m).
+// ---------------------------------------------------------------------------------------
+__device__ void kinematics(const Ctx& c) {
+  const ModelHdr& h = c.h;
+  for (int b = 1; b < h.nbody; b++) {
+    float3 x;
+    Quat q;
+    body_frame(c, MI(body_parent, b), x, q);
+    x = x + qrot(q, T3(&MF(body_pos, 3 * b)));
+    q = qmul(q, Quat{MF(body_quat, 4 * b), MF(body_quat, 4 * b + 1), MF(body_quat, 4 * b + 2), MF(body_quat, 4 * b + 3)});
+    const float3 o = tree_origin(c, b);
+    const int j0 = MI(body_jntadr, b), nj = MI(body_jntnum, b);
+    for (int j = j0; j < j0 + nj; j++) {
+      const int type = MI(jnt_type, j), qa = MI(jnt_qposadr, j), d0 = MI(jnt_dofadr, j);
+      if (type == PG_JNT_FREE) {
+        x = W3(c, h.w_qpos + qa);
+        q = qnormalize(Quat{W(qpos, qa + 3), W(qpos, qa + 4), W(qpos, qa + 5), W(qpos, qa + 6)});
+        float R[9];
+        qmat(q, R);
+        for (int k = 0; k < 3; k++) {
+          S3(c, h.w_cdof + 6 * (d0 + k), make_float3(0.f, 0.f, 0.f));
+          S3(c, h.w_cdof + 6 * (d0 + k) + 3, make_float3(k == 0 ? 1.f : 0.f, k == 1 ? 1.f : 0.f, k == 2 ? 1.f : 0.f));
+          const float3 ax = mat_col(R, k);
+          S3(c, h.w_cdof + 6 * (d0 + 3 + k), ax);
+          S3(c, h.w_cdof + 6 * (d0 + 3 + k) + 3, cross3(ax, o - x));
+        }
+      } else {
+        const float3 lp = T3(&MF(jnt_pos, 3 * j)), la = T3(&MF(jnt_axis, 3 * j));
+        const float3 anchor = x + qrot(q, lp), axis = qrot(q, la);
+        if (type == PG_JNT_HINGE) {
+          S3(c, h.w_cdof + 6 * d0, axis);
+          S3(c, h.w_cdof + 6 * d0 + 3, cross3(axis, o - anchor));
+          float sn, cs;
+          sincosf(0.5f * W(qpos, qa), &sn, &cs);
+          q = qmul(q, Quat{cs, la.x * sn, la.y * sn, la.z * sn});
+          x = anchor - qrot(q, lp);
+        } else {
+          S3(c, h.w_cdof + 6 * d0, make_float3(0.f, 0.f, 0.f));
+          S3(c, h.w_cdof + 6 * d0 + 3, axis);
+          x = x + axis * W(qpos, qa);
+        }
+      }
+    }
+    q = qnormalize(q);
+    S3(c, h.w_xpos + 3 * b, x);
+    const int qo = h.w_xquat + 4 * b;
+    c.w[qo * c.S] = q.w; c.w[(qo + 1) * c.S] = q.x; c.w[(qo + 2) * c.S] = q.y; c.w[(qo + 3) * c.S] = q.z;
+    // spatial inertia about o: I_com(world) + m (|c|^2 1 - c c^T), h = m c
+    float R[9];
+    qmat(q, R);
+    const float3 com = x + mat_mul(R, T3(&MF(body_ipos, 3 * b)));
+    const float m = MF(body_mass, b);
+    const float* In = &MF(body_inertia, 6 * b);
+    const float Ib[9] = {In[0], In[3], In[4], In[3], In[1], In[5], In[4], In[5], In[2]};
+    float T[9];
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+      for (int k = 0; k < 3; k++) T[3 * r + k] = R[3 * r] * Ib[k] + R[3 * r + 1] * Ib[3 + k] + R[3 * r + 2] * Ib[6 + k];
+    const float3 cc = com - o;
+    const float c2 = dot3(cc, cc);
+    const int ci = h.w_cinert + 10 * b;
+    c.w[(ci + 0) * c.S] = T[0] * R[0] + T[1] * R[1] + T[2] * R[2] + m * (c2 - cc.x * cc.x);
+    c.w[(ci + 1) * c.S] = T[3] * R[3] + T[4] * R[4] + T[5] * R[5] + m * (c2 - cc.y * cc.y);
+    c.w[(ci + 2) * c.S] = T[6] * R[6] + T[7] * R[7] + T[8] * R[8] + m * (c2 - cc.z * cc.z);
+    c.w[(ci + 3) * c.S] = T[0] * R[3] + T[1] * R[4] + T[2] * R[5] - m * cc.x * cc.y;
+    c.w[(ci + 4) * c.S] = T[0] * R[6] + T[1] * R[7] + T[2] * R[8] - m * cc.x * cc.z;
+    c.w[(ci + 5) * c.S] = T[3] * R[6] + T[4] * R[7] + T[5] * R[8] - m * cc.y * cc.z;
+    c.w[(ci + 6) * c.S] = m * cc.x;
+    c.w[(ci + 7) * c.S] = m * cc.y;
+    c.w[(ci + 8) * c.S] = m * cc.z;
+    c.w[(ci + 9) * c.S] = m;
+  }
+}
+
+// spatial inertia (about o) times a motion vector (w; v)
+__device__ __forceinline__ void inert_mul(const Ctx& c, int ci, float3 w, float3 v, float3& fa, float3& fl) {
+  const float* q = c.w + ci * c.S;
+  const int S = c.S;
+  const float i0 = q[0], i1 = q[S], i2 = q[2 * S], i3 = q[3 * S], i4 = q[4 * S], i5 = q[5 * S];
+  const float3 hc = make_float3(q[6 * S], q[7 * S], q[8 * S]);
+  const float m = q[9 * S];
+  fa = make_float3(i0 * w.x + i3 * w.y + i4 * w.z, i3 * w.x + i1 * w.y + i5 * w.z, i4 * w.x + i5 * w.y + i2 * w.z) +
+       cross3(hc, v);
+  fl = v * m - cross3(hc, w);
+}
+
+// ---------------------------------------------------------------------------------------
+// RNEA bias forces c(q, qdot): velocities and bias accelerations outward (the world
+// accelerates by -gravity), body forces I a + v x* I v accumulated inward, projected on cdof.
+// Serial joints of one body act as massless intermediate frames; the free joint's three
+// rotations all take the velocity after its translation (their axes move with the body).
+// ---------------------------------------------------------------------------------------
+__device__ void rnea(const Ctx& c) {
+  const ModelHdr& h = c.h;
+  for (int b = 1; b < h.nbody; b++) {
+    const int p = MI(body_parent, b);
+    float3 w, v, aw, av;
+    if (p == 0) {
+      w = v = aw = make_float3(0.f, 0.f, 0.f);
+      av = make_float3(-h.grav[0], -h.grav[1], -h.grav[2]);
+    } else {
+      w = W3(c, h.w_cvel + 6 * p); v = W3(c, h.w_cvel + 6 * p + 3);
+      aw = W3(c, h.w_cacc + 6 * p); av = W3(c, h.w_cacc + 6 * p + 3);
+    }
+    const int j0 = MI(body_jntadr, b), nj = MI(body_jntnum, b);
+    for (int j = j0; j < j0 + nj; j++) {
+      const int d0 = MI(jnt_dofadr, j);
+      float3 dw, dv;
+      if (MI(jnt_type, j) == PG_JNT_FREE) {
+        v = v + make_float3(W(qvel, d0), W(qvel, d0 + 1), W(qvel, d0 + 2));
+        dw = dv = make_float3(0.f, 0.f, 0.f);
+        for (int k = 3; k < 6; k++) {
+          const float qd = W(qvel, d0 + k);
+          dw = dw + W3(c, h.w_cdof + 6 * (d0 + k)) * qd;
+          dv = dv + W3(c, h.w_cdof + 6 * (d0 + k) + 3) * qd;
+        }
+      } else {
+        const float qd = W(qvel, d0);
+        dw = W3(c, h.w_cdof + 6 * d0) * qd;
+        dv = W3(c, h.w_cdof + 6 * d0 + 3) * qd;
+      }
+      aw = aw + cross3(w, dw);
+      av = av + cross3(w, dv) + cross3(v, dw);
+      w = w + dw;
+      v = v + dv;
+    }
+    S3(c, h.w_cvel + 6 * b, w); S3(c, h.w_cvel + 6 * b + 3, v);
+    S3(c, h.w_cacc + 6 * b, aw); S3(c, h.w_cacc + 6 * b + 3, av);
+    float3 fa, fl, ia, il;
+    inert_mul(c, h.w_cinert + 10 * b, aw, av, fa, fl);
+    inert_mul(c, h.w_cinert + 10 * b, w, v, ia, il);
+    S3(c, h.w_cfrc + 6 * b, fa + cross3(w, ia) + cross3(v, il));
+    S3(c, h.w_cfrc + 6 * b + 3, fl + cross3(w, il));
+  }
+  for (int b = h.nbody - 1; b >= 1; b--) {
+    const int p = MI(body_parent, b);
+    if (p == 0) continue;
+    for (int k = 0; k < 6; k++) W(cfrc, 6 * p + k) += W(cfrc, 6 * b + k);
+  }
+  for (int d = 0; d < h.nv; d++) {
+    const int f = h.w_cfrc + 6 * MI(dof_body, d);
+    W(bias, d) = dot3(W3(c, h.w_cdof + 6 * d), W3(c, f)) + dot3(W3(c, h.w_cdof + 6 * d + 3), W3(c, f + 3));
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// CRBA: composite inertias (inward sum, in place), M_ji = cdof_i . (Ic(body j) cdof_j) for i on
+// j's dof chain, armature on the diagonal, stored packed (row j: j, parent(j), ...)
+// ---------------------------------------------------------------------------------------
+__device__ void crba(const Ctx& c) {
+  const ModelHdr& h = c.h;
+  for (int b = h.nbody - 1; b >= 1; b--) {
+    const int p = MI(body_parent, b);
+    if (p == 0) continue;
+    for (int k = 0; k < 10; k++) W(cinert, 10 * p + k) += W(cinert, 10 * b + k);
+  }
+  for (int j = 0; j < h.nv; j++) {
+    float3 fa, fl;
+    inert_mul(c, h.w_cinert + 10 * MI(dof_body, j), W3(c, h.w_cdof + 6 * j), W3(c, h.w_cdof + 6 * j + 3), fa, fl);
+    const int r0 = MI(dof_rowadr, j), n = MI(dof_depth, j) + 1;
+    for (int t = 0; t < n; t++) {
+      const int i = MI(Lcol, r0 + t);
+      float v = dot3(W3(c, h.w_cdof + 6 * i), fa) + dot3(W3(c, h.w_cdof + 6 * i + 3), fl);
+      if (t == 0) v += MF(dof_armature, j);
+      W(M, r0 + t) = v;
+    }
+  }
+}
+
+// packed tree-sparse factorisation in place: A = L^T D L, L unit lower triangular on the
+// ancestor pattern (no fill-in); row k ends as (D_k, L_k,parent(k), ...)
+__device__ void ldl_factor(const Ctx& c, int A) {
+  const ModelHdr& h = c.h;
+  float* a = c.w + A * c.S;
+  for (int k = h.nv - 1; k >= 0; k--) {
+    const int r0 = MI(dof_rowadr, k), dk = MI(dof_depth, k);
+    const float dinv = 1.f / a[r0 * c.S];
+    for (int t = 1; t <= dk; t++) {
+      const int ri = MI(dof_rowadr, MI(Lcol, r0 + t));
+      const float lt = a[(r0 + t) * c.S] * dinv;
+      for (int s = t; s <= dk; s++) a[(ri + s - t) * c.S] -= lt * a[(r0 + s) * c.S];
+    }
+    for (int t = 1; t <= dk; t++) a[(r0 + t) * c.S] *= dinv;
+  }
+}
+
+// x <- A^-1 x with the packed factor of A (x: element offset of an nv-vector)
+__device__ void ldl_solve(const Ctx& c, int A, int X) {
+  const ModelHdr& h = c.h;
+  const float* a = c.w + A * c.S;
+  float* x = c.w + X * c.S;
+  for (int k = h.nv - 1; k >= 0; k--) {
+    const int r0 = MI(dof_rowadr, k), dk = MI(dof_depth, k);
+    const float xk = x[k * c.S];
+    for (int t = 1; t <= dk; t++) x[MI(Lcol, r0 + t) * c.S] -= a[(r0 + t) * c.S] * xk;
+  }
+  for (int k = 0; k < h.nv; k++) x[k * c.S] /= a[MI(dof_rowadr, k) * c.S];
+  for (int k = 0; k < h.nv; k++) {
+    const int r0 = MI(dof_rowadr, k), dk = MI(dof_depth, k);
+    float s = x[k * c.S];
+    for (int t = 1; t <= dk; t++) s -= a[(r0 + t) * c.S] * x[MI(Lcol, r0 + t) * c.S];
+    x[k * c.S] = s;
+  }
+}
+
+// y = M x with M stored packed symmetric (x, y: element offsets of nv-vectors)
+__device__ void sym_mul(const Ctx& c, int Mo, int X, int Y) {
+  const ModelHdr& h = c.h;
+  const float* m = c.w + Mo * c.S;
+  const float* x = c.w + X * c.S;
+  float* y = c.w + Y * c.S;
+  for (int j = 0; j < h.nv; j++) y[j * c.S] = 0.f;
+  for (int j = 0; j < h.nv; j++) {
+    const int r0 = MI(dof_rowadr, j), dj = MI(dof_depth, j);
+    const float xj = x[j * c.S];
+    float yj = m[r0 * c.S] * xj;
+    for (int t = 1; t <= dj; t++) {
+      const int i = MI(Lcol, r0 + t);
+      const float mji = m[(r0 + t) * c.S];
+      yj = fmaf(mji, x[i * c.S], yj);
+      y[i * c.S] = fmaf(mji, xj, y[i * c.S]);
+    }
+    y[j * c.S] += yj;
+  }
+}
+
+// passive (joint damping) and actuator forces (motor: gear * clamp(u); PD: kp (u - q) - kd qd),
+// then a0 = M^-1 (tau - c)
+template <bool DEBUG>
+__device__ void smooth_acc(const Ctx& c, float* dbg) {
+  const ModelHdr& h = c.h;
+  for (int d = 0; d < h.nv; d++) {
+    const float pas = -MF(dof_damping, d) * W(qvel, d);
+    W(a0, d) = pas - W(bias, d);
+    if (DEBUG) { dbg[h.dbg_passive + d] = pas; dbg[h.dbg_act + d] = 0.f; dbg[h.dbg_bias + d] = W(bias, d); }
+  }
+  for (int a = 0; a < h.nu; a++) {
+    const int d = MI(act_dof, a);
+    float u = c.ctrl[a * c.ld + c.env];
+    if (MI(act_ctrllimited, a)) u = fminf(fmaxf(u, MF(act_range, 2 * a)), MF(act_range, 2 * a + 1));
+    const float tau = MI(act_type, a) == PG_ACT_MOTOR
+                          ? MF(act_gear, a) * u
+                          : MF(act_kp, a) * (u - W(qpos, MI(act_qposadr, a))) - MF(act_kd, a) * W(qvel, d);
+    W(a0, d) += tau;
+    if (DEBUG) dbg[h.dbg_act + d] += tau;
+  }
+  for (int k = 0; k < h.nL; k++) W(L, k) = W(M, k);
+  ldl_factor(c, h.w_L);
+  ldl_solve(c, h.w_L, h.w_a0);
+}
+// ---------------------------------------------------------------------------------------
+// collision over the static pair list; active contacts (dist < margin) are kept in slot order
+// up to max_contacts as (slot, dist, pos, n)
+// ---------------------------------------------------------------------------------------
+template <bool DEBUG>
+__device__ int collide(const Ctx& c, uint32_t& status, float* dbg) {
+  const ModelHdr& h = c.h;
+  int nc = 0;
+  for (int p = 0; p < h.npair; p++) {
+    const int g1 = MI(pair_g1, p), g2 = MI(pair_g2, p);
+    const int t1 = MI(geom_type, g1), t2 = MI(geom_type, g2);
+    float3 x1, x2;
+    float R1[9], R2[9];
+    {
+      float3 bx;
+      Quat bq;
+      body_frame(c, MI(geom_body, g1), bx, bq);
+      x1 = bx + qrot(bq, T3(&MF(geom_pos, 3 * g1)));
+      qmat(qnormalize(qmul(bq, Quat{MF(geom_quat, 4 * g1), MF(geom_quat, 4 * g1 + 1), MF(geom_quat, 4 * g1 + 2),
+                                    MF(geom_quat, 4 * g1 + 3)})), R1);
+      body_frame(c, MI(geom_body, g2), bx, bq);
+      x2 = bx + qrot(bq, T3(&MF(geom_pos, 3 * g2)));
+      qmat(qnormalize(qmul(bq, Quat{MF(geom_quat, 4 * g2), MF(geom_quat, 4 * g2 + 1), MF(geom_quat, 4 * g2 + 2),
+                                    MF(geom_quat, 4 * g2 + 3)})), R2);
+    }
+    const float *s1 = &MF(geom_size, 3 * g1), *s2 = &MF(geom_size, 3 * g2);
+    const int s0 = MI(pair_slotadr, p), ns = MI(pair_nslot, p);
+    Con k[4];
+    int valid = ns;
+    for (int i = 0; i < 4; i++) { k[i].dist = 1.f; k[i].pos = x1; k[i].n = make_float3(0.f, 0.f, 1.f); }
+    if (t1 == PG_GEOM_PLANE) {
+      const float3 nz = mat_col(R1, 2);
+      if (t2 == PG_GEOM_SPHERE) {
+        k[0] = plane_sphere(x1, nz, x2, s2[0]);
+      } else if (t2 == PG_GEOM_CAPSULE) {
+        const float3 a = mat_col(R2, 2);
+        k[0] = plane_sphere(x1, nz, x2 - a * s2[1], s2[0]);
+        k[1] = plane_sphere(x1, nz, x2 + a * s2[1], s2[0]);
+        k[1].feat = 1;
+      } else {
+        float dd[8];
+        float3 cp[8];
+        for (int v = 0; v < 8; v++) {
+          const float3 l = make_float3((v & 1) ? s2[0] : -s2[0], (v & 2) ? s2[1] : -s2[1], (v & 4) ? s2[2] : -s2[2]);
+          cp[v] = x2 + mat_mul(R2, l);
+          dd[v] = dot3(nz, cp[v] - x1);
+        }
+        // the 4 deepest corners (ties: lower index), kept in corner order
+        unsigned chosen = 0;
+        for (int r = 0; r < 4; r++) {
+          int bi = -1;
+          for (int v = 0; v < 8; v++)
+            if (!((chosen >> v) & 1u) && (bi < 0 || dd[v] < dd[bi])) bi = v;
+          chosen |= 1u << bi;
+        }
+        int i = 0;
+        for (int v = 0; v < 8; v++)
+          if ((chosen >> v) & 1u) {
+            k[i].n = nz;
+            k[i].dist = dd[v];
+            k[i].pos = cp[v] - nz * (0.5f * dd[v]);
+            k[i].feat = v;
+            i++;
+          }
+      }
+    } else if (t1 == PG_GEOM_SPHERE) {
+      if (t2 == PG_GEOM_SPHERE) {
+        k[0] = sphere_sphere(x1, s1[0], x2, s2[0]);
+      } else if (t2 == PG_GEOM_CAPSULE) {
+        const float3 a = mat_col(R2, 2);
+        const float t = fminf(fmaxf(dot3(x1 - x2, a), -s2[1]), s2[1]);
+        k[0] = sphere_sphere(x1, s1[0], x2 + a * t, s2[0]);
+      } else {
+        k[0] = sphere_box(x1, s1[0], x2, R2, make_float3(s2[0], s2[1], s2[2]));
+      }
+    } else if (t1 == PG_GEOM_CAPSULE) {
+      const float3 a1 = mat_col(R1, 2);
+      if (t2 == PG_GEOM_CAPSULE) {
+        const float3 a2 = mat_col(R2, 2);
+        float u, v;
+        seg_seg(x1, a1, s1[1], x2, a2, s2[1], u, v);
+        k[0] = sphere_sphere(x1 + a1 * u, s1[0], x2 + a2 * v, s2[0]);
+      } else {
+        const float3 hb = make_float3(s2[0], s2[1], s2[2]);
+        k[0] = sphere_box(x1 - a1 * s1[1], s1[0], x2, R2, hb);
+        k[1] = sphere_box(x1 + a1 * s1[1], s1[0], x2, R2, hb);
+      }
+    } else {
+      valid = box_box(x1, R1, make_float3(s1[0], s1[1], s1[2]), x2, R2, make_float3(s2[0], s2[1], s2[2]), k);
+    }
+    for (int i = 0; i < ns; i++) {
+      const bool act = i < valid && k[i].dist < h.margin;
+      if (DEBUG) {
+        float3 tv1, tv2;
+        contact_frame(k[i].n, tv1, tv2);
+        float* o = dbg + h.dbg_con + 14 * (s0 + i);
+        o[0] = 0.f;
+        o[1] = i < valid ? k[i].dist : 1.f;
+        o[2] = k[i].pos.x; o[3] = k[i].pos.y; o[4] = k[i].pos.z;
+        o[5] = k[i].n.x; o[6] = k[i].n.y; o[7] = k[i].n.z;
+        o[8] = tv1.x; o[9] = tv1.y; o[10] = tv1.z;
+        o[11] = tv2.x; o[12] = tv2.y; o[13] = tv2.z;
+        if (act && nc < h.max_contacts) o[0] = 1.f;
+      }
+      if (!act) continue;
+      if (nc >= h.max_contacts) { status |= PG_STATUS_CAPACITY; continue; }
+      const int o = h.w_con + kConFloats * nc;
+      c.w[o * c.S] = (float)(s0 + i);
+      c.w[(o + 1) * c.S] = k[i].dist;
+      S3(c, o + 2, k[i].pos);
+      S3(c, o + 5, k[i].n);
+      c.w[(o + 8) * c.S] = (float)k[i].feat;
+      nc++;
+    }
+  }
+  return nc;
+}
+
+// ---------------------------------------------------------------------------------------
+// constraint rows, laid out identically in every environment (static shapes):
+//   rows 4k .. 4k+3 belong to the k-th active contact (k < max_contacts): edges n+mu t1,
+//   n-mu t1, n+mu t2, n-mu t2 of the pyramid (a condim-1 contact uses edge 0 = n only);
+//   rows 4 max_contacts + l belong to the l-th limited joint.
+// A row that does not exist in this environment has D = 0 and is never active.  The k-th
+// contact's Jacobian rows (n, t1, t2) are stored over its pair's columns, padded to ncol_max
+// (padding columns are zero and point at the first column).
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ int con_pair(const Ctx& c, int k) {
+  return MI(slot_pair, (int)c.w[(c.h.w_con + kConFloats * k) * c.S]);
+}
+
+__device__ void build_rows(const Ctx& c, int nc) {
+  const ModelHdr& h = c.h;
+  const int NC = h.ncol_max;
+  for (int k = 0; k < h.max_contacts; k++) {
+    float* J = c.w + (h.w_J + 3 * NC * k) * c.S;
+    float* gc = c.w + (h.w_gcol + NC * k) * c.S;
+    if (k >= nc) {
+      for (int a = 0; a < NC; a++) { J[a * c.S] = 0.f; J[(NC + a) * c.S] = 0.f; J[(2 * NC + a) * c.S] = 0.f; gc[a * c.S] = 0.f; }
+      continue;
+    }
+    const int p = con_pair(c, k);
+    const int co = h.w_con + kConFloats * k;
+    const float3 pos = W3(c, co + 2), n = W3(c, co + 5);
+    float3 t1, t2;
+    contact_frame(n, t1, t2);
+    const int b1 = MI(geom_body, MI(pair_g1, p)), b2 = MI(geom_body, MI(pair_g2, p));
+    const float3 o1 = tree_origin(c, b1), o2 = tree_origin(c, b2);
+    const int ca = MI(pair_coladr, p), ncol = MI(pair_ncol, p);
+    for (int a = 0; a < NC; a++) {
+      if (a < ncol) {
+        const int d = MI(col_dof, ca + a), sg = MI(col_sign, ca + a);
+        const float3 cw = W3(c, h.w_cdof + 6 * d), cl = W3(c, h.w_cdof + 6 * d + 3);
+        const float3 jac = (cl + cross3(cw, pos - (sg > 0 ? o2 : o1))) * (float)sg;
+        J[a * c.S] = dot3(n, jac);
+        J[(NC + a) * c.S] = dot3(t1, jac);
+        J[(2 * NC + a) * c.S] = dot3(t2, jac);
+        gc[a * c.S] = __int_as_float(d);
+      } else {
+        J[a * c.S] = 0.f; J[(NC + a) * c.S] = 0.f; J[(2 * NC + a) * c.S] = 0.f;
+        gc[a * c.S] = __int_as_float(ncol > 0 ? MI(col_dof, ca) : 0);
+      }
+    }
+  }
+  for (int li = 0; li < h.nlimited; li++) {
+    const int j = MI(limit_jnt, li);
+    const float q = W(qpos, MI(jnt_qposadr, j));
+    float sgn = 0.f;
+    if (q - MF(jnt_range, 2 * j) < h.margin) sgn = 1.f;
+    else if (MF(jnt_range, 2 * j + 1) - q < h.margin) sgn = -1.f;
+    W(lsgn, li) = sgn;
+  }
+}
+
+__device__ __forceinline__ float edge_value(float mu, int e, float dn, float d1, float d2) {
+  const float dt = e < 2 ? d1 : d2;
+  return (e & 1) ? dn - mu * dt : dn + mu * dt;
+}
+
+// J_r . x for every row into the element buffer OUT (rows of absent contacts give 0)
+__device__ void rows_dot(const Ctx& c, int X, int OUT) {
+  const ModelHdr& h = c.h;
+  const int NC = h.ncol_max, MC = h.max_contacts;
+  const float* x = c.w + X * c.S;
+  for (int k = 0; k < MC; k++) {
+    const float* J = c.w + (h.w_J + 3 * NC * k) * c.S;
+    const float* gc = c.w + (h.w_gcol + NC * k) * c.S;
+    float dn = 0.f, d1 = 0.f, d2 = 0.f;
+    for (int a = 0; a < NC; a++) {
+      const float xa = x[__float_as_int(gc[a * c.S]) * c.S];
+      dn = fmaf(J[a * c.S], xa, dn);
+      d1 = fmaf(J[(NC + a) * c.S], xa, d1);
+      d2 = fmaf(J[(2 * NC + a) * c.S], xa, d2);
+    }
+    const float mu = W(gmu, k);
+    for (int e = 0; e < 4; e++) c.w[(OUT + 4 * k + e) * c.S] = edge_value(mu, e, dn, d1, d2);
+  }
+  for (int li = 0; li < h.nlimited; li++) {
+    const int d = MI(jnt_dofadr, MI(limit_jnt, li));
+    c.w[(OUT + 4 * MC + li) * c.S] = W(lsgn, li) * x[d * c.S];
+  }
+}
+
+// impedance d(r) from solimp = (d0, dwidth, width, mid, power)
+__device__ __forceinline__ float impedance(const ModelHdr& h, float pos) {
+  const float d0 = h.solimp[0], d1 = h.solimp[1], width = h.solimp[2], mid = h.solimp[3], pw = h.solimp[4];
+  const float x = fminf(fabsf(pos) / width, 1.f);
+  float y;
+  if (x >= 1.f) y = 1.f;
+  else if (x <= mid) y = powf(x, pw) / powf(mid, pw - 1.f);
+  else y = 1.f - powf(1.f - x, pw) / powf(1.f - mid, pw - 1.f);
+  return d0 + y * (d1 - d0);
+}
+
+__device__ __forceinline__ void set_row(const Ctx& c, int r, bool valid, float pos, float A) {
+  const ModelHdr& h = c.h;
+  const float d = impedance(h, pos), vel = W(rv, r);
+  W(rr, r) = pos;
+  W(Ahat, r) = A;
+  W(imp, r) = d;
+  W(aref, r) = -h.bref * vel - h.kref * d * pos;
+  W(rD, r) = valid ? d / ((1.f - d) * A) : 0.f;
+}
+
+// z <- L^-T z along the chain that starts at dof c0 (z is zero off that chain), or over all dofs
+// when the model's pairs do not lie on single chains
+__device__ __forceinline__ void ltsolve_chain(const Ctx& c, float* z, int c0) {
+  const ModelHdr& h = c.h;
+  const float* L = c.w + h.w_L * c.S;
+  if (h.tree_hessian) {
+    const int rc = MI(dof_rowadr, c0), n = MI(dof_depth, c0);
+    for (int t = 0; t <= n; t++) {
+      const int k = MI(Lcol, rc + t);
+      const float zk = z[k * c.S];
+      const int r0 = MI(dof_rowadr, k), dk = MI(dof_depth, k);
+      for (int s = 1; s <= dk; s++) z[MI(Lcol, r0 + s) * c.S] -= L[(r0 + s) * c.S] * zk;
+    }
+  } else {
+    for (int k = h.nv - 1; k >= 0; k--) {
+      const float zk = z[k * c.S];
+      const int r0 = MI(dof_rowadr, k), dk = MI(dof_depth, k);
+      for (int s = 1; s <= dk; s++) z[MI(Lcol, r0 + s) * c.S] -= L[(r0 + s) * c.S] * zk;
+    }
+  }
+}
+
+// per row: position, velocity, exact Ahat = (J M^-1 J^T)_rr = sum_k z_k z_k / D_k with
+// z = L^-T J_r^T (for a pyramid from the n / t1 / t2 solves: Ahat = A_nn +- 2 mu A_nk + mu^2 A_kk),
+// impedance, aref = -b v - k d r, D = d / ((1 - d) Ahat) (0 for absent rows)
+__device__ void row_params(const Ctx& c, int nc) {
+  const ModelHdr& h = c.h;
+  const int nv = h.nv, NC = h.ncol_max, MC = h.max_contacts;
+  const float* L = c.w + h.w_L * c.S;
+  for (int k = 0; k < MC; k++) {
+    const bool valid = k < nc;
+    const int p = valid ? con_pair(c, k) : 0;
+    W(gmu, k) = valid ? MF(pair_friction, p) : 0.f;
+    W(gcond, k) = valid ? (float)MI(pair_condim, p) : 0.f;
+  }
+  rows_dot(c, h.w_qvel, h.w_rv);
+  for (int k = 0; k < MC; k++) {
+    const bool valid = k < nc;
+    const float mu = W(gmu, k), dist = valid ? W(con, kConFloats * k + 1) : 0.f;
+    const bool pyr = W(gcond, k) == 3.f;
+    const float* J = c.w + (h.w_J + 3 * NC * k) * c.S;
+    const float* gc = c.w + (h.w_gcol + NC * k) * c.S;
+    float Ann = 1.f, An1 = 0.f, An2 = 0.f, A11 = 1.f, A22 = 1.f;
+    if (valid) {
+      const int c0 = __float_as_int(gc[0]);
+      for (int s = 0; s < 3; s++) {
+        float* z = c.w + (h.w_z + s * nv) * c.S;
+        for (int i = 0; i < nv; i++) z[i * c.S] = 0.f;
+        for (int a = 0; a < NC; a++) z[__float_as_int(gc[a * c.S]) * c.S] += J[(s * NC + a) * c.S];
+        ltsolve_chain(c, z, c0);
+      }
+      Ann = An1 = An2 = A11 = A22 = 0.f;
+      for (int i = 0; i < nv; i++) {
+        const float dinv = 1.f / L[MI(dof_rowadr, i) * c.S];
+        const float zn = W(z, i), z1 = W(z, nv + i), z2 = W(z, 2 * nv + i);
+        Ann = fmaf(zn * zn, dinv, Ann);
+        An1 = fmaf(zn * z1, dinv, An1);
+        An2 = fmaf(zn * z2, dinv, An2);
+        A11 = fmaf(z1 * z1, dinv, A11);
+        A22 = fmaf(z2 * z2, dinv, A22);
+      }
+    }
+    if (pyr) {
+      set_row(c, 4 * k + 0, valid, dist, Ann + 2.f * mu * An1 + mu * mu * A11);
+      set_row(c, 4 * k + 1, valid, dist, Ann - 2.f * mu * An1 + mu * mu * A11);
+      set_row(c, 4 * k + 2, valid, dist, Ann + 2.f * mu * An2 + mu * mu * A22);
+      set_row(c, 4 * k + 3, valid, dist, Ann - 2.f * mu * An2 + mu * mu * A22);
+    } else {
+      set_row(c, 4 * k + 0, valid, dist, Ann);
+      for (int e = 1; e < 4; e++) set_row(c, 4 * k + e, false, dist, 1.f);
+    }
+  }
+  for (int li = 0; li < h.nlimited; li++) {
+    const int j = MI(limit_jnt, li), d = MI(jnt_dofadr, j);
+    const float sgn = W(lsgn, li);
+    const float q = W(qpos, MI(jnt_qposadr, j));
+    const float pos = sgn < 0.f ? MF(jnt_range, 2 * j + 1) - q : q - MF(jnt_range, 2 * j);
+    float A = 1.f;
+    if (sgn != 0.f) {
+      // (M^-1)_dd = sum_k z_k^2 / D_k with z = L^-T e_d, supported on d's chain
+      float* z = c.w + h.w_z * c.S;
+      for (int i = 0; i < nv; i++) z[i * c.S] = 0.f;
+      z[d * c.S] = 1.f;
+      const int rc = MI(dof_rowadr, d), n = MI(dof_depth, d);
+      A = 0.f;
+      for (int t = 0; t <= n; t++) {
+        const int k = MI(Lcol, rc + t);
+        const float zk = z[k * c.S];
+        const int r0 = MI(dof_rowadr, k), dk = MI(dof_depth, k);
+        for (int s = 1; s <= dk; s++) z[MI(Lcol, r0 + s) * c.S] -= L[(r0 + s) * c.S] * zk;
+        A = fmaf(zk * zk, 1.f / L[r0 * c.S], A);
+      }
+    }
+    set_row(c, 4 * MC + li, sgn != 0.f, pos, A);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Newton solve of  min_a f(a) = 1/2 (a-a0)^T M (a-a0) + sum_r 1/2 D_r min(0, J_r a - aref_r)^2
+// ---------------------------------------------------------------------------------------
+__device__ float cost_of(const Ctx& c, int X) {
+  const ModelHdr& h = c.h;
+  for (int k = 0; k < h.nv; k++) W(t, k) = c.w[(X + k) * c.S] - W(a0, k);
+  sym_mul(c, h.w_M, h.w_t, h.w_g);
+  float f = 0.f;
+  for (int k = 0; k < h.nv; k++) f = fmaf(0.5f * W(t, k), W(g, k), f);
+  rows_dot(c, X, h.w_jar);
+  for (int r = 0; r < h.nrow_max; r++) {
+    const float jar = W(jar, r) - W(aref, r);
+    if (jar < 0.f) f = fmaf(0.5f * W(rD, r) * jar, jar, f);
+  }
+  return f;
+}
+
+__device__ __forceinline__ bool bit(const unsigned act[4], int r) { return (act[r >> 5] >> (r & 31)) & 1u; }
+
+// jar = J a - aref for every row; the active set holds the existing rows with jar < 0
+__device__ void residuals(const Ctx& c, unsigned act[4]) {
+  const ModelHdr& h = c.h;
+  rows_dot(c, h.w_a, h.w_jar);
+  act[0] = act[1] = act[2] = act[3] = 0u;
+  for (int r = 0; r < h.nrow_max; r++) {
+    const float jar = W(jar, r) - W(aref, r);
+    W(jar, r) = jar;
+    if (jar < 0.f && W(rD, r) > 0.f) act[r >> 5] |= 1u << (r & 31);
+  }
+}
+
+// g = M (a - a0) + J_A^T D_A jar_A, H = M + J_A^T D_A J_A (packed on the tree pattern in the
+// L buffer, or dense lower triangle), factorised; p = -H^-1 g.  `zero`: g is exactly zero.
+__device__ bool newton_direction(const Ctx& c, const unsigned act[4], bool& zero) {
+  const ModelHdr& h = c.h;
+  const int nv = h.nv, nL = h.nL, NC = h.ncol_max, MC = h.max_contacts;
+  const bool tree = h.tree_hessian != 0;
+  for (int k = 0; k < nv; k++) W(t, k) = W(a, k) - W(a0, k);
+  sym_mul(c, h.w_M, h.w_t, h.w_g);
+  if (tree) {
+    for (int k = 0; k < nL; k++) W(L, k) = W(M, k);
+  } else {
+    for (int i = 0; i < nv * nv; i++) W(H, i) = 0.f;
+    for (int j = 0; j < nv; j++) {
+      const int r0 = MI(dof_rowadr, j), dj = MI(dof_depth, j);
+      for (int t = 0; t <= dj; t++) W(H, j * nv + MI(Lcol, r0 + t)) = W(M, r0 + t);
+    }
+  }
+  for (int k = 0; k < MC; k++) {
+    const float mu = W(gmu, k);
+    // the active edges summed in the (n, t1, t2) basis
+    float Sn = 0.f, c1 = 0.f, c2 = 0.f, s1 = 0.f, s2 = 0.f, gn = 0.f, g1 = 0.f, g2 = 0.f;
+    for (int e = 0; e < 4; e++) {
+      const int r = 4 * k + e;
+      const float D = bit(act, r) ? W(rD, r) : 0.f, DJ = D * W(jar, r);
+      const float sg = (e & 1) ? -mu : mu;
+      Sn += D;
+      gn += DJ;
+      if (e < 2) { c1 += sg * D; s1 += mu * mu * D; g1 += sg * DJ; }
+      else { c2 += sg * D; s2 += mu * mu * D; g2 += sg * DJ; }
+    }
+    if (Sn == 0.f) continue;
+    const float* J = c.w + (h.w_J + 3 * NC * k) * c.S;
+    const float* gc = c.w + (h.w_gcol + NC * k) * c.S;
+    for (int a = 0; a < NC; a++) {
+      const int da = __float_as_int(gc[a * c.S]);
+      const float na = J[a * c.S], ta = J[(NC + a) * c.S], ua = J[(2 * NC + a) * c.S];
+      W(g, da) += gn * na + g1 * ta + g2 * ua;
+      const float hn = Sn * na + c1 * ta + c2 * ua;
+      const float ht = c1 * na + s1 * ta;
+      const float hu = c2 * na + s2 * ua;
+      const int ra = MI(dof_rowadr, da), depa = MI(dof_depth, da);
+      for (int b = a; b < NC; b++) {
+        const int db = __float_as_int(gc[b * c.S]);
+        const float v = hn * J[b * c.S] + ht * J[(NC + b) * c.S] + hu * J[(2 * NC + b) * c.S];
+        if (tree) W(L, ra + depa - MI(dof_depth, db)) += v;
+        else W(H, (da > db ? da * nv + db : db * nv + da)) += v;
+      }
+    }
+  }
+  for (int li = 0; li < h.nlimited; li++) {
+    const int r = 4 * MC + li, d = MI(jnt_dofadr, MI(limit_jnt, li));
+    const float D = bit(act, r) ? W(rD, r) : 0.f;
+    W(g, d) += W(lsgn, li) * D * W(jar, r);
+    if (tree) W(L, MI(dof_rowadr, d)) += D;
+    else W(H, d * nv + d) += D;
+  }
+  bool nz = false;
+  for (int k = 0; k < nv; k++) { W(p, k) = -W(g, k); nz = nz || W(g, k) != 0.f; }
+  zero = !nz;
+  if (zero) return false;
+  if (tree) {
+    ldl_factor(c, h.w_L);
+    for (int k = 0; k < nv; k++)
+      if (!(W(L, MI(dof_rowadr, k)) > 0.f)) return false;
+    ldl_solve(c, h.w_L, h.w_p);
+    return true;
+  }
+  for (int j = 0; j < nv; j++) {
+    float s = W(H, j * nv + j);
+    for (int k = 0; k < j; k++) s -= W(H, j * nv + k) * W(H, j * nv + k);
+    if (!(s > 0.f)) return false;
+    const float djj = sqrtf(s), inv = 1.f / djj;
+    W(H, j * nv + j) = djj;
+    for (int i = j + 1; i < nv; i++) {
+      float t = W(H, i * nv + j);
+      for (int k = 0; k < j; k++) t -= W(H, i * nv + k) * W(H, j * nv + k);
+      W(H, i * nv + j) = t * inv;
+    }
+  }
+  for (int i = 0; i < nv; i++) {
+    float s = W(p, i);
+    for (int k = 0; k < i; k++) s -= W(H, i * nv + k) * W(p, k);
+    W(p, i) = s / W(H, i * nv + i);
+  }
+  for (int i = nv - 1; i >= 0; i--) {
+    float s = W(p, i);
+    for (int k = i + 1; k < nv; k++) s -= W(H, k * nv + i) * W(p, k);
+    W(p, i) = s / W(H, i * nv + i);
+  }
+  return true;
+}
+
+// Exact minimiser of phi(alpha) = f(a + alpha p) (convex, piecewise quadratic): start from the
+// active set just after alpha = 0 and walk the breakpoints alpha_r = -jar_r / Jp_r in increasing
+// order (each next one found by a scan), toggling the rows that cross, until the root of the
+// current linear piece of phi' lies before the next breakpoint.
+__device__ float line_search(const Ctx& c) {
+  const ModelHdr& h = c.h;
+  const int nv = h.nv, R = h.nrow_max;
+  sym_mul(c, h.w_M, h.w_p, h.w_g);   // g <- M p
+  float qt = 0.f, lt = 0.f;
+  for (int k = 0; k < nv; k++) {
+    qt = fmaf(W(p, k), W(g, k), qt);
+    lt = fmaf(W(t, k), W(g, k), lt);   // t = a - a0
+  }
+  rows_dot(c, h.w_p, h.w_Jp);
+  unsigned on[4] = {0u, 0u, 0u, 0u};
+  for (int r = 0; r < R; r++) {
+    const float D = W(rD, r), jp = W(Jp, r), jr = W(jar, r);
+    if (D > 0.f && (jr < 0.f || (jr == 0.f && jp < 0.f))) {
+      on[r >> 5] |= 1u << (r & 31);
+      qt = fmaf(D * jp, jp, qt);
+      lt = fmaf(D * jp, jr, lt);
+    }
+  }
+  float alpha = 0.f;
+  for (int step = 0; step <= R; step++) {
+    const float root = qt > 0.f ? -lt / qt : alpha;
+    float next = INFINITY;
+    for (int r = 0; r < R; r++) {
+      const float jp = W(Jp, r);
+      if (!(W(rD, r) > 0.f) || jp == 0.f) continue;
+      const float br = -W(jar, r) / jp;
+      if (br > alpha && br < next) next = br;
+    }
+    if (root <= next) return root;
+    alpha = next;
+    for (int r = 0; r < R; r++) {
+      const float D = W(rD, r), jp = W(Jp, r);
+      if (!(D > 0.f) || jp == 0.f || -W(jar, r) / jp != next) continue;
+      const float sg = bit(on, r) ? -1.f : 1.f;
+      on[r >> 5] ^= 1u << (r & 31);
+      qt = fmaf(sg * D * jp, jp, qt);
+      lt = fmaf(sg * D * jp, W(jar, r), lt);
+    }
+  }
+  return qt > 0.f ? -lt / qt : alpha;
+}
+
+// Newton's method with exact termination: stop at the cap or when the active set after the
+// step equals the one the Hessian was built from.  Warm start: qacc_warm if f(warm) < f(a0).
+__device__ int newton(const Ctx& c, bool& converged) {
+  const ModelHdr& h = c.h;
+  const int nv = h.nv;
+  converged = false;
+  const float fw = cost_of(c, h.w_warm), f0 = cost_of(c, h.w_a0);
+  const bool use_warm = fw < f0;
+  for (int k = 0; k < nv; k++) W(a, k) = use_warm ? W(warm, k) : W(a0, k);
+  unsigned act[4];
+  residuals(c, act);
+  int it = 0;
+  while (it < h.cap) {
+    bool zero = false;
+    const bool ok = newton_direction(c, act, zero);
+    it++;
+    if (zero) { converged = true; break; }
+    if (!ok) break;
+    const float alpha = line_search(c);
+    for (int k = 0; k < nv; k++) W(a, k) = fmaf(alpha, W(p, k), W(a, k));
+    unsigned act2[4];
+    residuals(c, act2);
+    const bool same = act2[0] == act[0] && act2[1] == act[1] && act2[2] == act[2] && act2[3] == act[3];
+    act[0] = act2[0]; act[1] = act2[1]; act[2] = act2[2]; act[3] = act2[3];
+    if (same) { converged = true; break; }
+  }
+  return it;
+}
+
+// ---------------------------------------------------------------------------------------
+// one substep
+// ---------------------------------------------------------------------------------------
+template <bool DEBUG>
+__device__ void substep(const Ctx& c, uint32_t& status, float* dbg, uint32_t cnt[3]) {
+  const ModelHdr& h = c.h;
+  const int nv = h.nv;
+  kinematics(c);
+  if (DEBUG) {
+    for (int b = 0; b < h.nbody; b++) {
+      float3 x;
+      Quat q;
+      body_frame(c, b, x, q);
+      float R[9];
+      qmat(q, R);
+      const float3 com = b ? x + mat_mul(R, T3(&MF(body_ipos, 3 * b))) : make_float3(0.f, 0.f, 0.f);
+      dbg[h.dbg_xpos + 3 * b] = x.x; dbg[h.dbg_xpos + 3 * b + 1] = x.y; dbg[h.dbg_xpos + 3 * b + 2] = x.z;
+      dbg[h.dbg_xcom + 3 * b] = com.x; dbg[h.dbg_xcom + 3 * b + 1] = com.y; dbg[h.dbg_xcom + 3 * b + 2] = com.z;
+      for (int k = 0; k < 9; k++) dbg[h.dbg_xmat + 9 * b + k] = R[k];
+    }
+  }
+  rnea(c);
+  crba(c);
+  if (DEBUG) {
+    for (int i = 0; i < nv * nv; i++) dbg[h.dbg_M + i] = 0.f;
+    for (int j = 0; j < nv; j++) {
+      const int r0 = MI(dof_rowadr, j), dj = MI(dof_depth, j);
+      for (int t = 0; t <= dj; t++) {
+        const int i = MI(Lcol, r0 + t);
+        dbg[h.dbg_M + j * nv + i] = W(M, r0 + t);
+        dbg[h.dbg_M + i * nv + j] = W(M, r0 + t);
+      }
+    }
+  }
+  smooth_acc<DEBUG>(c, dbg);
+  if (DEBUG)
+    for (int k = 0; k < nv; k++) dbg[h.dbg_a0 + k] = W(a0, k);
+  const int nc = collide<DEBUG>(c, status, dbg);
+  build_rows(c, nc);
+  row_params(c, nc);
+  int nrow = 0;   // rows that exist in this environment
+  for (int r = 0; r < h.nrow_max; r++) nrow += W(rD, r) > 0.f ? 1 : 0;
+  int iters = 0;
+  bool conv = true;
+  if (nrow == 0) {
+    for (int k = 0; k < nv; k++) W(a, k) = W(a0, k);
+  } else {
+    iters = newton(c, conv);
+    if (!conv) status |= PG_STATUS_NOT_CONVERGED;
+  }
+  cnt[0] += (uint32_t)iters;
+  cnt[1] += (uint32_t)nrow;
+  cnt[2] += (uint32_t)(nrow * iters);
+  if (DEBUG) {
+    // rows in the oracle's order: existing contact rows, then existing limit rows
+    rows_dot(c, h.w_a, h.w_jar);
+    int o_r = 0;
+    for (int r = 0; r < h.nrow_max; r++) {
+      if (!(W(rD, r) > 0.f)) continue;
+      float* o = dbg + h.dbg_rows + (o_r++) * (nv + 7);
+      for (int k = 0; k < nv; k++) o[k] = 0.f;
+      if (r < 4 * h.max_contacts) {
+        const int k = r >> 2, e = r & 3;
+        const float mu = W(gmu, k);
+        const float* J = c.w + (h.w_J + 3 * h.ncol_max * k) * c.S;
+        const float* gc = c.w + (h.w_gcol + h.ncol_max * k) * c.S;
+        for (int a = 0; a < h.ncol_max; a++)
+          o[__float_as_int(gc[a * c.S])] += W(gcond, k) == 3.f
+              ? edge_value(mu, e, J[a * c.S], J[(h.ncol_max + a) * c.S], J[(2 * h.ncol_max + a) * c.S])
+              : J[a * c.S];
+      } else {
+        const int li = r - 4 * h.max_contacts, d = MI(jnt_dofadr, MI(limit_jnt, li));
+        o[d] = W(lsgn, li);
+      }
+      o[nv] = W(rr, r); o[nv + 1] = W(rv, r); o[nv + 2] = W(aref, r); o[nv + 3] = W(rD, r);
+      o[nv + 4] = W(Ahat, r); o[nv + 5] = W(imp, r);
+      const float jar = W(jar, r) - W(aref, r);
+      o[nv + 6] = jar < 0.f ? -W(rD, r) * jar : 0.f;
+    }
+    dbg[h.dbg_nrow] = (float)nrow;
+    dbg[h.dbg_iter] = (float)iters;
+  }
+  // semi-implicit Euler
+  bool bad = false;
+  for (int d = 0; d < nv; d++) {
+    const float acc = W(a, d);
+    W(qvel, d) = fmaf(h.h, acc, W(qvel, d));
+    W(warm, d) = acc;
+    bad = bad || !isfinite(acc) || !isfinite(W(qvel, d));
+    if (DEBUG) dbg[h.dbg_qacc + d] = acc;
+  }
+  for (int j = 0; j < h.njnt; j++) {
+    const int qa = MI(jnt_qposadr, j), da = MI(jnt_dofadr, j);
+    if (MI(jnt_type, j) == PG_JNT_FREE) {
+      for (int k = 0; k < 3; k++) W(qpos, qa + k) = fmaf(h.h, W(qvel, da + k), W(qpos, qa + k));
+      const float3 w = make_float3(W(qvel, da + 3), W(qvel, da + 4), W(qvel, da + 5));
+      const float wn = sqrtf(dot3(w, w));
+      Quat q{W(qpos, qa + 3), W(qpos, qa + 4), W(qpos, qa + 5), W(qpos, qa + 6)};
+      if (wn > 0.f) {
+        float sn, cs;
+        sincosf(0.5f * h.h * wn, &sn, &cs);
+        const float s = sn / wn;
+        q = qmul(q, Quat{cs, w.x * s, w.y * s, w.z * s});
+      }
+      q = qnormalize(q);
+      W(qpos, qa + 3) = q.w; W(qpos, qa + 4) = q.x; W(qpos, qa + 5) = q.y; W(qpos, qa + 6) = q.z;
+      for (int k = 0; k < 7; k++) bad = bad || !isfinite(W(qpos, qa + k));
+    } else {
+      W(qpos, qa) = fmaf(h.h, W(qvel, da), W(qpos, qa));
+      bad = bad || !isfinite(W(qpos, qa));
+    }
+  }
+  if (bad) status |= PG_STATUS_NAN;
+  if (DEBUG) {
+    for (int k = 0; k < h.nq; k++) dbg[h.dbg_qpos + k] = W(qpos, k);
+    for (int k = 0; k < nv; k++) dbg[h.dbg_qvel + k] = W(qvel, k);
+    dbg[h.dbg_status] = (float)status;
+  }
+}
+
+}  // namespace
+}  // namespace pg
