@@ -221,6 +221,61 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def measure_adjoint(dev, n: int = 4096, steps: int = 64, segment: int = 8, reps: int = 3):
+    """Full rollout gradient against the forward rollout on the adjoint workload: 4096
+    quadrupeds, 64 control steps, loss sum_t (z_t - 0.27)^2 + |v_t - (0.5, 0, 0)|^2 of the torso
+    height and linear velocity, gradients with respect to the initial state, all 64 x 12
+    controls and the per-environment masses, damping and kp, checkpoints every 8 steps.  The
+    gradient's time covers the checkpointed forward pass, the loss and the backward sweep."""
+    import torch
+    from paper_2502_08844_b300 import adjoint, core
+    m = W.quadruped()
+    cm = core.CompiledModel(m)
+    batch = core.Batch([(cm, n)])
+    st = core.State(batch, dev)
+    ld = st.ld
+    q0, v0 = W.initial_state(m, 4, n)
+    U = W.actions(m, 4, n, 0, steps)
+    Q0 = torch.from_numpy(core.to_soa(q0, ld, batch.nq_max)).to(dev)
+    V0 = torch.from_numpy(core.to_soa(v0, ld, batch.nv_max)).to(dev)
+    Us = np.zeros((steps, batch.nu_max, ld), np.float32)
+    Us[:, :m.nu, :n] = U.transpose(0, 2, 1)
+    ctrl = torch.from_numpy(Us).to(dev)
+    params = adjoint.param_values(batch, ld, dev)
+    zs = torch.zeros((batch.nq_max, 1), device=dev); zs[2] = 0.27
+    vs = torch.zeros((batch.nv_max, 1), device=dev); vs[0] = 0.5
+    wq = torch.zeros((batch.nq_max, 1), device=dev); wq[2] = 1.0
+    wv = torch.zeros((batch.nv_max, 1), device=dev); wv[:3] = 1.0
+
+    def forward():
+        st.qpos.copy_(Q0); st.qvel.copy_(V0); st.qacc_warm.zero_()
+        for t in range(steps):
+            core.step(batch, st, ctrl[t], 0)
+
+    def gradient():
+        q = Q0.clone().requires_grad_(); v = V0.clone().requires_grad_()
+        u = ctrl.clone().requires_grad_(); p = params.clone().requires_grad_()
+        Q, V = adjoint.rollout(batch, q, v, u, p, 0, segment)
+        loss = (wq * (Q[:, :, :n] - zs) ** 2).sum() + (wv * (V[:, :, :n] - vs) ** 2).sum()
+        loss.backward()
+        return loss
+
+    def timed(f):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        f()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    gradient(); forward()   # warm-up (the adjoint's scratch is allocated on its first call)
+    tf = min(timed(forward) for _ in range(reps))
+    tg = min(timed(gradient) for _ in range(reps))
+    return {"ratio": tg / tf, "forward_ms": tf, "gradient_ms": tg, "envs": n, "steps": steps, "segment": segment,
+            "newton_cap": m.iterations, "note": "gradient = checkpointed forward + loss + backward sweep"}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -330,6 +385,10 @@ def run_ours(args):
             "adjoint_forward_ratio": None}
     if not args.no_mixed:
         line["mixed_batch"] = measure_mixed(dev)
+    if not args.no_adjoint:
+        adj = measure_adjoint(dev)
+        line["adjoint_forward_ratio"] = adj["ratio"]
+        line["adjoint"] = adj
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(m, cfg, n)
     print(json.dumps(line))
@@ -346,6 +405,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -108,6 +108,9 @@ typedef struct pg_model_sizes {
   int max_contacts;
   int workspace_bytes;  /* per-env shared-memory workspace of the step kernel            */
   int debug_floats;     /* length of the record written by pg_debug_substep              */
+  int adjoint_workspace_bytes;  /* per-env workspace of pg_step_vjp; 0 when the model is
+                                   outside the adjoint's scope (see pg_step_vjp)          */
+  int nparam;           /* nbody + nv + nu: rows of the per-env parameter gradient        */
 } pg_model_sizes;
 
 /* Caller-owned batch state (device pointers, [coord][ld] float32; status [n] uint32). */
@@ -164,6 +167,51 @@ int pg_debug_substep(const pg_batch* batch, pg_state* state, const float* ctrl_d
  * outputs. */
 int pg_step_host(pg_batch* batch, pg_state* state, const float* ctrl_host, float* qpos_host, float* qvel_host,
                  int n_substeps, void* stream);
+
+/* Reverse-mode sweep (vector-Jacobian product) of n_steps consecutive control steps.
+ *
+ * The paper reports no gradients. This is the library's adjoint of the step above. It is a
+ * hand-written reverse sweep: the smooth dynamics (kinematics, CRBA, RNEA, actuation,
+ * semi-implicit Euler) are differentiated directly, and the convex contact solve implicitly at
+ * the solver's final iterate with the active set held fixed.
+ *
+ * Procedure. The call replays the steps forward from `ckpt`, on library-owned scratch,
+ * recording every substep's start state and acceleration. It then sweeps back from the last
+ * step to the first.
+ *
+ * Arguments (device memory, [coord][ld] float32, ld = ckpt->ld):
+ *   ckpt          state at the start of the first step: qpos, qvel, qacc_warm. Read only;
+ *                 status and stats are ignored.
+ *   ctrl_dev      [n_steps][nu_max][ld] controls of the steps.
+ *   g_qpos_dev    [n_steps][nq_max][ld] cotangent (dLoss/d) of the qpos after each step, or NULL.
+ *   g_qvel_dev    [n_steps][nv_max][ld] the same for qvel, or NULL.
+ *   adj_qpos_dev  [nq_max][ld] in/out. In: the adjoint of the state after the last step,
+ *                 added to that step's cotangent. Out: the adjoint of ckpt's qpos.
+ *   adj_qvel_dev  [nv_max][ld] the same for qvel.
+ *   g_ctrl_dev    [n_steps][nu_max][ld] out: dLoss/dctrl.
+ *   g_param_dev   [nparam_max][ld], ACCUMULATED (+=): per environment, the gradient with
+ *                 respect to its model's body masses [nbody] (a body's rotational inertia
+ *                 scales with its mass), then dof damping [nv], then actuator kp [nu].
+ *
+ * Gradients are not taken with respect to the warm start. The solver's result does not depend
+ * on it at convergence.
+ *
+ * Scope. Every model of the batch needs adjoint_workspace_bytes > 0. That means:
+ *   * any joints and actuators;
+ *   * joint limits;
+ *   * contacts only between a world-fixed plane (geom1) and spheres, capsules or boxes.
+ * Otherwise the call returns PG_EUNSUPPORTED.
+ *
+ * Scratch and errors.
+ *   * Scratch, about (n_steps * substeps * (nq + 3 nv) + adjoint workspace) floats per env, is
+ *     allocated on the first call and grown when a later call needs more. Such a call returns
+ *     only after the allocation, so make it before any stream capture.
+ *   * Calls on the same batch share the scratch: calls that overlap on the GPU race.
+ *   * Errors: PG_EINVAL for NULL or inconsistent arguments, PG_EUNSUPPORTED,
+ *     PG_ENOMEM / PG_ECUDA. */
+int pg_step_vjp(pg_batch* batch, const pg_state* ckpt, const float* ctrl_dev, int n_steps, int n_substeps,
+                const float* g_qpos_dev, const float* g_qvel_dev, float* adj_qpos_dev, float* adj_qvel_dev,
+                float* g_ctrl_dev, float* g_param_dev, void* stream);
 
 const char* pg_last_error(void);
 

@@ -292,6 +292,7 @@ def _setup_grad_api():
     L.orc_rollout_loss.argtypes = [C.c_void_p, _dp, _dp, _dp, C.c_int, C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
     L.orc_rollout_grad.argtypes = [C.c_void_p, _dp, _dp, _dp, C.c_int, C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp,
                                    _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+    L.orc_step_vjp.argtypes = [C.c_void_p, _dp, _dp, _dp, C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
     L._grad_ready = True
     return L
 
@@ -311,16 +312,29 @@ def _opt(a):
 
 def rollout_loss(om: "OracleModel", q0, v0, ctrl, n_substeps, weights, solver_cap=-1, mass=None, damping=None, kp=None):
     L = _setup_grad_api()
-    ctrl = _d(ctrl).reshape(-1, om.nu)
+    ctrl = _d(ctrl).reshape(len(ctrl), om.nu)
     wq, qs, wv, vs = [_d(x) for x in weights]
     return L.orc_rollout_loss(om.h, _pd(_d(q0)), _pd(_d(v0)), _pd(ctrl), ctrl.shape[0], int(n_substeps), int(solver_cap),
                               _opt(mass), _opt(damping), _opt(kp), _pd(wq), _pd(qs), _pd(wv), _pd(vs))
 
 
+def step_vjp(om: "OracleModel", q, v, u, n_substeps, bq, bv, solver_cap=-1, mass=None, damping=None, kp=None):
+    """Reverse mode through one control step from (q, v) with controls u, given the adjoint (bq, bv)
+    of the post-step state: dict with the pre-step adjoints q, v, the control adjoint u and the
+    parameter adjoints mass, damping, kp (the warm start is a constant)."""
+    L = _setup_grad_api()
+    out = {"q": _d(bq).copy(), "v": _d(bv).copy(), "u": np.zeros(om.nu), "mass": np.zeros(om.nbody),
+           "damping": np.zeros(om.nv), "kp": np.zeros(om.nu)}
+    L.orc_step_vjp(om.h, _pd(_d(q)), _pd(_d(v)), _pd(_d(u).reshape(om.nu)), int(n_substeps), int(solver_cap),
+                   _opt(mass), _opt(damping), _opt(kp), _pd(out["q"]), _pd(out["v"]), _pd(out["u"]), _pd(out["mass"]),
+                   _pd(out["damping"]), _pd(out["kp"]))
+    return out
+
+
 def rollout_grad(om: "OracleModel", q0, v0, ctrl, n_substeps, weights, solver_cap=-1, mass=None, damping=None, kp=None):
     """Reverse-mode gradient of rollout_loss: dict with loss, q0, v0, u [T,nu], mass, damping, kp."""
     L = _setup_grad_api()
-    ctrl = _d(ctrl).reshape(-1, om.nu)
+    ctrl = _d(ctrl).reshape(len(ctrl), om.nu)
     T = ctrl.shape[0]
     wq, qs, wv, vs = [_d(x) for x in weights]
     out = {"q0": np.zeros(om.nq), "v0": np.zeros(om.nv), "u": np.zeros((T, om.nu)), "mass": np.zeros(om.nbody),

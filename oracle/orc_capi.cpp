@@ -331,6 +331,56 @@ double orc_rollout_loss(void* h, const double* q0, const double* v0, const doubl
   return L;
 }
 
+// Reverse mode through one control step (n_substeps substeps) from (q, v) with controls u: the
+// adjoint (bq, bv) of the post-step state is replaced by the adjoint of the pre-step state;
+// control adjoints are written to gu and parameter adjoints added to gmass / gdamp / gkp.  The
+// warm start enters as a constant.
+static void control_step_vjp(const Model& m, const orc::Params<double>& P, const double* q0, const double* v0,
+                             const double* w0, const double* u0, int n_substeps, int solver_cap, double* bq, double* bv,
+                             double* gu, double* gmass, double* gdamp, double* gkp) {
+  using orc::adouble;
+  const int nq = m.nq, nv = m.nv, nu = m.nu, nb = m.nbody;
+  orc::Tape tp;
+  orc::Tape* prev = orc::tape();
+  orc::tape() = &tp;
+  std::vector<adouble> q(nq), v(nv), u(nu), w(nv);
+  for (int i = 0; i < nq; i++) q[i] = adouble::var(q0[i]);
+  for (int i = 0; i < nv; i++) v[i] = adouble::var(v0[i]);
+  for (int i = 0; i < nu; i++) u[i] = adouble::var(u0[i]);
+  for (int i = 0; i < nv; i++) w[i] = adouble(w0 ? w0[i] : 0.0);
+  orc::Params<adouble> PA;
+  for (int b = 0; b < nb; b++) PA.mass.push_back(adouble::var(P.mass[b]));
+  for (int i = 0; i < nv; i++) PA.damping.push_back(adouble::var(P.damping[i]));
+  for (int a = 0; a < nu; a++) PA.kp.push_back(adouble::var(P.kp[a]));
+  std::vector<int> iq(nq), iv(nv), iu(nu);
+  for (int i = 0; i < nq; i++) iq[i] = q[i].i;
+  for (int i = 0; i < nv; i++) iv[i] = v[i].i;
+  for (int i = 0; i < nu; i++) iu[i] = u[i].i;
+  for (int s = 0; s < n_substeps; s++) orc::substep<adouble>(m, q.data(), v.data(), w.data(), u.data(), solver_cap, nullptr, &PA);
+  std::vector<std::pair<int, double>> seeds;
+  for (int i = 0; i < nq; i++) seeds.push_back({q[i].i, bq[i]});
+  for (int i = 0; i < nv; i++) seeds.push_back({v[i].i, bv[i]});
+  std::vector<double> adj = tp.backward(seeds);
+  for (int i = 0; i < nq; i++) bq[i] = adj[iq[i]];
+  for (int i = 0; i < nv; i++) bv[i] = adj[iv[i]];
+  for (int i = 0; i < nu; i++) gu[i] = adj[iu[i]];
+  for (int b = 0; b < nb; b++) gmass[b] += adj[PA.mass[b].i];
+  for (int i = 0; i < nv; i++) gdamp[i] += adj[PA.damping[i].i];
+  for (int a = 0; a < nu; a++) gkp[a] += adj[PA.kp[a].i];
+  orc::tape() = prev;
+}
+
+// One control step's vector-Jacobian product at a given state (see control_step_vjp); the
+// parameter adjoints are accumulated (+=) into gmass / gdamp / gkp.
+int orc_step_vjp(void* h, const double* q, const double* v, const double* u, int n_substeps, int solver_cap,
+                 const double* mass, const double* damp, const double* kp, double* bq, double* bv, double* gu,
+                 double* gmass, double* gdamp, double* gkp) {
+  const Model& m = *static_cast<Model*>(h);
+  orc::Params<double> P = make_params(m, mass, damp, kp);
+  control_step_vjp(m, P, q, v, nullptr, u, n_substeps, solver_cap, bq, bv, gu, gmass, gdamp, gkp);
+  return 0;
+}
+
 // Gradient of orc_rollout_loss by reverse mode: states are kept after every control step and
 // each step is taped from its start state (inputs q, v, u and the parameters; the solver's
 // warm start enters as a constant), then swept backward with the state adjoint of the next step.
@@ -338,7 +388,6 @@ int orc_rollout_grad(void* h, const double* q0, const double* v0, const double* 
                      int solver_cap, const double* mass, const double* damp, const double* kp, const double* wq,
                      const double* qs, const double* wv, const double* vs, double* gq0, double* gv0, double* gu,
                      double* gmass, double* gdamp, double* gkp, double* loss) {
-  using orc::adouble;
   const Model& m = *static_cast<Model*>(h);
   const int nq = m.nq, nv = m.nv, nu = m.nu, nb = m.nbody;
   orc::Params<double> P = make_params(m, mass, damp, kp);
@@ -358,40 +407,14 @@ int orc_rollout_grad(void* h, const double* q0, const double* v0, const double* 
   std::fill(gmass, gmass + nb, 0.0);
   std::fill(gdamp, gdamp + nv, 0.0);
   std::fill(gkp, gkp + nu, 0.0);
-  orc::Tape tp;
-  orc::tape() = &tp;
   for (int t = T - 1; t >= 0; t--) {
-    tp.clear();
-    std::vector<adouble> q(nq), v(nv), u(nu), w(nv);
-    for (int i = 0; i < nq; i++) q[i] = adouble::var(Q[t][i]);
-    for (int i = 0; i < nv; i++) v[i] = adouble::var(V[t][i]);
-    for (int i = 0; i < nu; i++) u[i] = adouble::var(ctrl[(size_t)t * nu + i]);
-    for (int i = 0; i < nv; i++) w[i] = adouble(Wm[t][i]);
-    orc::Params<adouble> PA;
-    for (int b = 0; b < nb; b++) PA.mass.push_back(adouble::var(P.mass[b]));
-    for (int i = 0; i < nv; i++) PA.damping.push_back(adouble::var(P.damping[i]));
-    for (int a = 0; a < nu; a++) PA.kp.push_back(adouble::var(P.kp[a]));
-    std::vector<int> iq(nq), iv(nv), iu(nu);
-    for (int i = 0; i < nq; i++) iq[i] = q[i].i;
-    for (int i = 0; i < nv; i++) iv[i] = v[i].i;
-    for (int i = 0; i < nu; i++) iu[i] = u[i].i;
-    for (int s = 0; s < n_substeps; s++) orc::substep<adouble>(m, q.data(), v.data(), w.data(), u.data(), solver_cap, nullptr, &PA);
-    std::vector<std::pair<int, double>> seeds;
-    for (int i = 0; i < nq; i++) seeds.push_back({q[i].i, bq[i]});
-    for (int i = 0; i < nv; i++) seeds.push_back({v[i].i, bv[i]});
-    std::vector<double> adj = tp.backward(seeds);
-    for (int i = 0; i < nq; i++) bq[i] = adj[iq[i]];
-    for (int i = 0; i < nv; i++) bv[i] = adj[iv[i]];
-    for (int i = 0; i < nu; i++) gu[(size_t)t * nu + i] = adj[iu[i]];
-    for (int b = 0; b < nb; b++) gmass[b] += adj[PA.mass[b].i];
-    for (int i = 0; i < nv; i++) gdamp[i] += adj[PA.damping[i].i];
-    for (int a = 0; a < nu; a++) gkp[a] += adj[PA.kp[a].i];
+    control_step_vjp(m, P, Q[t].data(), V[t].data(), Wm[t].data(), ctrl + (size_t)t * nu, n_substeps, solver_cap,
+                     bq.data(), bv.data(), gu + (size_t)t * nu, gmass, gdamp, gkp);
     if (t >= 1) {
       for (int i = 0; i < nq; i++) bq[i] += 2 * wq[i] * (Q[t][i] - qs[i]);
       for (int i = 0; i < nv; i++) bv[i] += 2 * wv[i] * (V[t][i] - vs[i]);
     }
   }
-  orc::tape() = nullptr;
   std::memcpy(gq0, bq.data(), sizeof(double) * nq);
   std::memcpy(gv0, bv.data(), sizeof(double) * nv);
   return 0;

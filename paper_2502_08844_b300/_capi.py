@@ -40,7 +40,8 @@ class pg_model_desc(C.Structure):
 
 class pg_model_sizes(C.Structure):
     _fields_ = [(n, C.c_int) for n in ("nq", "nv", "nu", "nbody", "njnt", "ngeom", "npair", "nslot", "nrow_max",
-                                        "max_contacts", "workspace_bytes", "debug_floats")]
+                                        "max_contacts", "workspace_bytes", "debug_floats",
+                                        "adjoint_workspace_bytes", "nparam")]
 
 
 class pg_state(C.Structure):
@@ -49,7 +50,8 @@ class pg_state(C.Structure):
 
 
 EXPORTS = ["pg_model_compile", "pg_model_info", "pg_model_free", "pg_batch_compile", "pg_batch_info",
-           "pg_batch_free", "pg_reset", "pg_step", "pg_debug_substep", "pg_step_host", "pg_last_error"]
+           "pg_batch_free", "pg_reset", "pg_step", "pg_debug_substep", "pg_step_host", "pg_step_vjp",
+           "pg_last_error"]
 
 if not os.path.exists(LIB_PATH):
     raise ImportError("libpg.so is not built (run `python -m paper_2502_08844_b300.build` or "
@@ -71,6 +73,7 @@ _lib.pg_reset.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_void_
 _lib.pg_step.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_int, C.c_void_p]
 _lib.pg_debug_substep.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
 _lib.pg_step_host.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
+_lib.pg_step_vjp.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_int, C.c_int] + [C.c_void_p] * 7
 for _n in EXPORTS:
     if _n not in ("pg_last_error", "pg_model_free", "pg_batch_free"):
         getattr(_lib, _n).restype = C.c_int
@@ -141,3 +144,9 @@ def pg_debug_substep(batch, state: pg_state, ctrl_ptr, env: int, out_ptr, stream
 def pg_step_host(batch, state: pg_state, ctrl_host_ptr, qpos_host_ptr, qvel_host_ptr, n_substeps: int, stream) -> None:
     _check(_lib.pg_step_host(batch, C.byref(state), ctrl_host_ptr, qpos_host_ptr, qvel_host_ptr, int(n_substeps), stream),
            "pg_step_host")
+
+
+def pg_step_vjp(batch, ckpt: pg_state, ctrl_ptr, n_steps: int, n_substeps: int, g_qpos_ptr, g_qvel_ptr, adj_qpos_ptr,
+                adj_qvel_ptr, g_ctrl_ptr, g_param_ptr, stream) -> None:
+    _check(_lib.pg_step_vjp(batch, C.byref(ckpt), ctrl_ptr, int(n_steps), int(n_substeps), g_qpos_ptr, g_qvel_ptr,
+                            adj_qpos_ptr, adj_qvel_ptr, g_ctrl_ptr, g_param_ptr, stream), "pg_step_vjp")

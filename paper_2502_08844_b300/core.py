@@ -86,6 +86,8 @@ class Batch:
         self.handle = _capi.pg_batch_compile([m.handle for m in self.models], self.counts, envs_per_cta)
         self.n, self.nq_max, self.nv_max, self.nu_max = _capi.pg_batch_info(self.handle)
         self.env_off = list(np.cumsum([0] + self.counts[:-1]))
+        # rows of the per-environment parameter gradient of pg_step_vjp (masses | damping | kp)
+        self.nparam_max = max(m.sizes.nparam for m in self.models)
 
     def __del__(self):
         h = getattr(self, "handle", None)
@@ -132,6 +134,23 @@ def step_host(batch: Batch, state: State, ctrl_host: torch.Tensor, qpos_host: to
               n_substeps: int, stream=None) -> None:
     _capi.pg_step_host(batch.handle, state.c(), _ptr(ctrl_host), _ptr(qpos_host), _ptr(qvel_host), int(n_substeps),
                        _stream_ptr(stream))
+
+
+def step_vjp(batch: Batch, ckpt: State, ctrl: torch.Tensor, n_substeps: int, g_qpos: Optional[torch.Tensor],
+             g_qvel: Optional[torch.Tensor], adj_qpos: torch.Tensor, adj_qvel: torch.Tensor, g_ctrl: torch.Tensor,
+             g_param: torch.Tensor, stream=None) -> None:
+    """pg_step_vjp over the K = ctrl.shape[0] control steps that start from `ckpt` (see include/pg.h):
+    adj_qpos / adj_qvel in: adjoint after the last step, out: adjoint of ckpt; g_ctrl [K, nu_max, ld]
+    written; g_param [nparam_max, ld] accumulated."""
+    K = ctrl.shape[0]
+    for t, shape in ((ctrl, (K, max(batch.nu_max, 1), ckpt.ld)), (adj_qpos, (batch.nq_max, ckpt.ld)),
+                     (adj_qvel, (batch.nv_max, ckpt.ld)), (g_ctrl, (K, max(batch.nu_max, 1), ckpt.ld)),
+                     (g_param, (batch.nparam_max, ckpt.ld))):
+        assert t.dtype == torch.float32 and t.is_contiguous() and tuple(t.shape) == shape, (t.shape, shape)
+    for t, rows in ((g_qpos, batch.nq_max), (g_qvel, batch.nv_max)):
+        assert t is None or (t.dtype == torch.float32 and t.is_contiguous() and tuple(t.shape) == (K, rows, ckpt.ld))
+    _capi.pg_step_vjp(batch.handle, ckpt.c(), _ptr(ctrl), K, int(n_substeps), _ptr(g_qpos), _ptr(g_qvel),
+                      _ptr(adj_qpos), _ptr(adj_qvel), _ptr(g_ctrl), _ptr(g_param), _stream_ptr(stream))
 
 
 DEBUG_FIELDS = ["xpos", "xmat", "xcom", "M", "bias", "passive", "actuator", "a0", "contacts", "nrow", "rows", "qacc",

@@ -57,6 +57,8 @@ int pg_model_info(const pg_model* m, pg_model_sizes* out) {
   out->npair = h.npair; out->nslot = h.nslot; out->nrow_max = h.nrow_max; out->max_contacts = h.max_contacts;
   out->workspace_bytes = 4 * h.ws_floats;
   out->debug_floats = h.debug_floats;
+  out->adjoint_workspace_bytes = h.adj_ok ? 4 * h.ws_adj_floats : 0;
+  out->nparam = h.nbody + h.nv + h.nu;
   return PG_OK;
 }
 
@@ -72,6 +74,7 @@ void pg_batch_free(pg_batch* b) {
   if (b->d_blob_off) cudaFree(b->d_blob_off);
   if (b->d_tiles) cudaFree(b->d_tiles);
   if (b->d_ctrl_stage) cudaFree(b->d_ctrl_stage);
+  if (b->d_vjp) cudaFree(b->d_vjp);
   delete b;
 }
 
@@ -129,6 +132,7 @@ int pg_batch_compile(const pg_model* const* models, const int64_t* counts, int n
   }
   if ((int)all.size() > kMaxParamWords) { delete b; return set_error(PG_ECAPACITY, "the batch's model tables exceed the 28 KB kernel-parameter budget"); }
   b->blob_host = all;
+  for (int k = 0; k < nmodels; k++) b->blob_host_adj.insert(b->blob_host_adj.end(), models[k]->blob_adj.begin(), models[k]->blob_adj.end());
   for (int k = 0; k < nmodels; k++) {
     const int e = b->envs_per_cta[k];
     for (int64_t e0 = 0; e0 < counts[k]; e0 += e)
@@ -228,6 +232,69 @@ int pg_step_host(pg_batch* b, pg_state* s, const float* ctrl_host, float* qpos_h
     return cuda_error(e, "qpos download");
   if ((e = cudaMemcpyAsync(qvel_host, s->qvel, (size_t)b->nv_max * s->ld * sizeof(float), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
     return cuda_error(e, "qvel download");
+  return PG_OK;
+}
+
+int pg_step_vjp(pg_batch* b, const pg_state* ck, const float* ctrl, int n_steps, int n_substeps, const float* g_qpos,
+                const float* g_qvel, float* adj_qpos, float* adj_qvel, float* g_ctrl, float* g_param, void* stream) {
+  if (!b || !ck) return set_error(PG_EINVAL, "NULL batch or checkpoint");
+  if (ck->n != b->n) return set_error(PG_EINVAL, "ckpt.n differs from the batch's environment count");
+  if (ck->ld < ck->n) return set_error(PG_EINVAL, "ckpt.ld must be >= ckpt.n");
+  if (n_steps < 1) return set_error(PG_EINVAL, "n_steps must be >= 1");
+  if (n_substeps < 0) return set_error(PG_EINVAL, "n_substeps must be >= 0 (0: each model's own)");
+  if (b->n == 0) return PG_OK;
+  if (!ck->qpos || !ck->qvel || !ck->qacc_warm) return set_error(PG_EINVAL, "NULL checkpoint array");
+  if ((b->nu_max > 0 && (!ctrl || !g_ctrl)) || !adj_qpos || !adj_qvel || !g_param)
+    return set_error(PG_EINVAL, "NULL argument");
+  int sub_max = 1, ws_max = 1;
+  for (const pg_model* m : b->models) {
+    if (!m->hdr.adj_ok) return set_error(PG_EUNSUPPORTED, "a model of the batch is outside the adjoint's scope");
+    sub_max = std::max(sub_max, n_substeps > 0 ? n_substeps : std::max(m->hdr.substeps, 1));
+    ws_max = std::max(ws_max, m->hdr_adj.ws_adj_floats);
+  }
+  const int64_t ld = ck->ld;
+  const int nq = b->nq_max, nv = b->nv_max, nu = std::max(b->nu_max, 1);
+  const int tape_rows = nq + 3 * nv;
+  const size_t state_f = (size_t)(nq + 2 * nv + 1) * ld;            // qpos | qvel | warm | status
+  const size_t tape_f = (size_t)n_steps * sub_max * tape_rows * ld;
+  const size_t ws_f = (size_t)ws_max * ld;
+  const size_t need = state_f + tape_f + ws_f;
+  if (b->vjp_floats < need) {
+    if (b->d_vjp) cudaFree(b->d_vjp);
+    b->d_vjp = nullptr;
+    b->vjp_floats = 0;
+    cudaError_t e = cudaMalloc(&b->d_vjp, need * sizeof(float));
+    if (e != cudaSuccess) return cuda_error(e, "cudaMalloc (adjoint scratch)");
+    b->vjp_floats = need;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  float* sq = b->d_vjp;
+  float* sv = sq + (size_t)nq * ld;
+  float* sw = sv + (size_t)nv * ld;
+  uint32_t* sstat = reinterpret_cast<uint32_t*>(sw + (size_t)nv * ld);
+  float* tape = b->d_vjp + state_f;
+  float* ws = tape + tape_f;
+  pg_state s{sq, sv, sw, sstat, ck->n, ld, nullptr};
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(sq, ck->qpos, (size_t)nq * ld * 4, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(sv, ck->qvel, (size_t)nv * ld * 4, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(sw, ck->qacc_warm, (size_t)nv * ld * 4, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(sstat, 0, (size_t)ld * 4, st)) != cudaSuccess)
+    return cuda_error(e, "checkpoint copy");
+  const size_t tape_step = (size_t)sub_max * tape_rows * ld;
+  for (int t = 0; t < n_steps; t++) {
+    const float* u = b->nu_max > 0 ? ctrl + (size_t)t * nu * ld : nullptr;
+    if ((e = launch_step_tape(b, &s, u, n_substeps, tape + t * tape_step, tape_rows, st)) != cudaSuccess)
+      return cuda_error(e, "replay launch");
+  }
+  for (int t = n_steps - 1; t >= 0; t--) {
+    const float* u = b->nu_max > 0 ? ctrl + (size_t)t * nu * ld : nullptr;
+    if ((e = launch_vjp_step(b, tape + t * tape_step, tape_rows, u, g_qpos ? g_qpos + (size_t)t * nq * ld : nullptr,
+                             g_qvel ? g_qvel + (size_t)t * nv * ld : nullptr, adj_qpos, adj_qvel,
+                             b->nu_max > 0 ? g_ctrl + (size_t)t * nu * ld : nullptr, g_param, ws, ld, n_substeps, st)) !=
+        cudaSuccess)
+      return cuda_error(e, "adjoint launch");
+  }
   return PG_OK;
 }
 

@@ -370,6 +370,31 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
     ws = std::max(ws, off + b.size);
   }
   h.ws_floats = std::max(ws, 1);
+  // ---- adjoint layout: the same buffers laid end to end, then the reverse sweep's own ----
+  {
+    int a = 0;
+    auto take = [&](int n) { int r = a; a += std::max(n, 1); return r; };
+    ModelHdr& g = out->hdr_adj;
+    g = h;
+    for (Buf& b : bufs) *(int*)((char*)&g + ((char*)b.off - (char*)&h)) = take(b.size);
+    g.w_ci0 = take(10 * nbody);
+    g.w_HL = take(nL);
+    g.b_q = take(nq); g.b_v = take(nv); g.b_a = take(nv); g.b_bias = take(nv); g.b_M = take(nL);
+    g.b_cdof = take(6 * nv); g.b_I = take(10 * nbody); g.b_vel = take(6 * nbody); g.b_acc = take(6 * nbody);
+    g.b_frc = take(6 * nbody); g.b_wr = take(6 * nbody); g.b_w = take(3 * nv);
+    g.ws_adj_floats = a;
+    // scope of the hand-written adjoint: contacts only between a world-fixed plane (geom1) and a
+    // sphere, capsule or box, which keeps the Newton Hessian on the mass matrix's pattern
+    bool ok = true;
+    for (int p = 0; p < npair; p++) {
+      const int g1 = d->pair_geom[2 * p], g2 = d->pair_geom[2 * p + 1];
+      if (d->geom_type[g1] != PG_GEOM_PLANE || d->geom_body[g1] != 0 || d->geom_type[g2] == PG_GEOM_PLANE) ok = false;
+    }
+    if (npair > 0 && !tree_hessian) ok = false;
+    g.adj_ok = ok ? 1 : 0;
+    h.adj_ok = g.adj_ok;
+    h.ws_adj_floats = g.ws_adj_floats;
+  }
   // environments per warp block: the largest power of two <= 32 whose workspaces fit in shared memory
   h.soa = 32;
   while (h.soa > 1 && (size_t)4 * h.soa * h.ws_floats > (size_t)kMaxSmem) h.soa /= 2;
@@ -383,8 +408,11 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
   h.dbg_status = dbg(1); h.dbg_qpos = dbg(nq); h.dbg_qvel = dbg(nv);
   h.debug_floats = q;
 
+  out->hdr_adj.debug_floats = h.debug_floats;
   std::memcpy(B.w.data(), &h, sizeof(h));
   out->hdr = h;
+  out->blob_adj = B.w;
+  std::memcpy(out->blob_adj.data(), &out->hdr_adj, sizeof(h));
   out->blob = std::move(B.w);
   return PG_OK;
 }

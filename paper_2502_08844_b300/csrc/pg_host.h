@@ -11,6 +11,8 @@
 struct pg_model {
   pg::ModelHdr hdr;
   std::vector<uint32_t> blob;
+  pg::ModelHdr hdr_adj;             // the adjoint's header (its workspace layout)
+  std::vector<uint32_t> blob_adj;   // the blob with the adjoint's header
   uint32_t* d_blob = nullptr;   // device copy of the blob
 };
 
@@ -30,9 +32,14 @@ struct pg_batch {
   std::vector<int> blob_off;
   std::vector<uint32_t> blob_host;   // all models' blobs, concatenated (passed as a kernel parameter)
   std::vector<pg::Tile> tiles;
+  std::vector<uint32_t> blob_host_adj;   // the same with the adjoint headers
   // staging buffer of the host-buffer path (allocated on its first use)
   float* d_ctrl_stage = nullptr;
   size_t ctrl_stage_floats = 0;
+  // scratch of pg_step_vjp (allocated on its first use, grown when a call needs more): the
+  // replayed state, the substep tape and the adjoint workspaces
+  float* d_vjp = nullptr;
+  size_t vjp_floats = 0;
 };
 
 namespace pg {
@@ -47,5 +54,11 @@ cudaError_t launch_debug(const pg_batch* b, const pg_state* s, const float* ctrl
 cudaError_t launch_reset(const pg_batch* b, const pg_state* s, const uint8_t* mask, const float* qpos0,
                          const float* qvel0, cudaStream_t st);
 cudaError_t configure_step_kernels(size_t smem_bytes);
+cudaError_t launch_step_tape(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, float* tape,
+                             int tape_rows, cudaStream_t st);
+// adjoint.cu
+cudaError_t launch_vjp_step(const pg_batch* b, const float* tape, int tape_rows, const float* ctrl, const float* gq,
+                            const float* gv, float* adj_q, float* adj_v, float* g_ctrl, float* g_params, float* ws,
+                            int64_t ld, int n_substeps, cudaStream_t st);
 
 }  // namespace pg

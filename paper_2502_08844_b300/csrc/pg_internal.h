@@ -49,6 +49,13 @@ struct ModelHdr {
   int w_M, w_L, w_a0, w_con, w_J, w_z;
   int w_gcol, w_gmu, w_gcond, w_lsgn, w_rr, w_rv, w_Ahat, w_imp, w_aref, w_rD, w_jar, w_Jp;
   int w_a, w_g, w_p, w_t, w_H;
+  // adjoint workspace (the reverse sweep): every forward buffer above gets its own space (no
+  // sharing between phases), plus the own body inertias `ci0` (CRBA overwrites w_cinert with
+  // composites), the Hessian factor `HL` and the adjoint buffers b_*.  Valid only in the adjoint
+  // copy of the header; adj_ok = 0 when the model is outside the adjoint's scope.
+  int adj_ok, ws_adj_floats;
+  int w_ci0, w_HL;
+  int b_q, b_v, b_a, b_bias, b_M, b_cdof, b_I, b_vel, b_acc, b_frc, b_wr, b_w;
   int debug_floats;
   int dbg_xpos, dbg_xmat, dbg_xcom, dbg_M, dbg_bias, dbg_passive, dbg_act, dbg_a0, dbg_con, dbg_nrow, dbg_rows,
       dbg_qacc, dbg_iter, dbg_status, dbg_qpos, dbg_qvel;

@@ -43,12 +43,18 @@ struct StepArgs {
   int n_substeps;
   float* dbg;
   Tile dbg_tile;
+  float* tape;                        // optional record of every substep (see TAPE below)
+  int tape_rows, tape_nq, tape_nv;    // rows per substep entry; the batch's nq_max, nv_max
   int model_off[kMaxModels];          // word offset of each model's blob in `blob`
   uint32_t blob[kMaxParamWords];      // the batch's model blobs (header + tables)
 };
 
 // One thread per environment; a block steps the `count` consecutive environments of its tile.
-template <bool DEBUG>
+// TAPE: also record, for every substep s, the state it starts from and the acceleration the
+// solver returns, at tape[(s * tape_rows + row) * ld + env] with rows qpos [0, nq), qvel from
+// tape_nq, the warm start from tape_nq + tape_nv and the acceleration from tape_nq + 2 tape_nv
+// (the adjoint replays the substeps from this record).
+template <bool DEBUG, bool TAPE>
 __global__ void __launch_bounds__(kMaxEnvsPerCta) step_kernel(const __grid_constant__ StepArgs A) {
   extern __shared__ __align__(16) float smem[];
   const Tile tile = DEBUG ? A.dbg_tile : A.tiles[blockIdx.x];
@@ -76,7 +82,19 @@ __global__ void __launch_bounds__(kMaxEnvsPerCta) step_kernel(const __grid_const
   }
   uint32_t cnt[3] = {0u, 0u, 0u};
   const int nsub = DEBUG ? 1 : (A.n_substeps > 0 ? A.n_substeps : h.substeps);
-  for (int s = 0; s < nsub; s++) substep<DEBUG>(c, status, A.dbg, cnt);
+  for (int s = 0; s < nsub; s++) {
+    float* tp = TAPE ? A.tape + (int64_t)s * A.tape_rows * A.ld + env : nullptr;
+    if (TAPE) {
+      for (int k = 0; k < h.nq; k++) tp[k * A.ld] = W(qpos, k);
+      for (int k = 0; k < h.nv; k++) {
+        tp[(A.tape_nq + k) * A.ld] = W(qvel, k);
+        tp[(A.tape_nq + A.tape_nv + k) * A.ld] = W(warm, k);
+      }
+    }
+    substep<DEBUG>(c, status, A.dbg, cnt);
+    if (TAPE)
+      for (int k = 0; k < h.nv; k++) tp[(A.tape_nq + 2 * A.tape_nv + k) * A.ld] = W(warm, k);
+  }
   for (int k = 0; k < h.nq; k++) A.qpos[k * A.ld + env] = W(qpos, k);
   for (int k = 0; k < h.nv; k++) {
     A.qvel[k * A.ld + env] = W(qvel, k);
@@ -103,9 +121,11 @@ __global__ void reset_kernel(float* qpos, float* qvel, float* warm, uint32_t* st
 }  // namespace
 
 cudaError_t configure_step_kernels(size_t smem_bytes) {
-  cudaError_t e = cudaFuncSetAttribute(step_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+  cudaError_t e = cudaFuncSetAttribute(step_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(step_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+  e = cudaFuncSetAttribute(step_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(step_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
 }
 
 static void make_args(StepArgs& A, const pg_batch* b, const pg_state* s, const float* ctrl) {
@@ -120,6 +140,8 @@ static void make_args(StepArgs& A, const pg_batch* b, const pg_state* s, const f
   A.n_substeps = 1;
   A.dbg = nullptr;
   A.dbg_tile = Tile{0, 0, 0, 0};
+  A.tape = nullptr;
+  A.tape_rows = A.tape_nq = A.tape_nv = 0;
   for (int k = 0; k < kMaxModels; k++) A.model_off[k] = k < (int)b->blob_off.size() ? b->blob_off[k] : 0;
   std::memcpy(A.blob, b->blob_host.data(), b->blob_host.size() * sizeof(uint32_t));
 }
@@ -129,7 +151,21 @@ cudaError_t launch_step(const pg_batch* b, const pg_state* s, const float* ctrl,
   static thread_local StepArgs A;
   make_args(A, b, s, ctrl);
   A.n_substeps = n_substeps;
-  step_kernel<false><<<b->ntiles, b->threads, b->smem_bytes, st>>>(A);
+  step_kernel<false, false><<<b->ntiles, b->threads, b->smem_bytes, st>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_tape(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, float* tape,
+                             int tape_rows, cudaStream_t st) {
+  if (b->ntiles == 0) return cudaSuccess;
+  static thread_local StepArgs A;
+  make_args(A, b, s, ctrl);
+  A.n_substeps = n_substeps;
+  A.tape = tape;
+  A.tape_rows = tape_rows;
+  A.tape_nq = b->nq_max;
+  A.tape_nv = b->nv_max;
+  step_kernel<false, true><<<b->ntiles, b->threads, b->smem_bytes, st>>>(A);
   return cudaGetLastError();
 }
 
@@ -141,7 +177,7 @@ cudaError_t launch_debug(const pg_batch* b, const pg_state* s, const float* ctrl
     if (env >= b->env_off[k] && env < b->env_off[k] + b->counts[k]) model = (int)k;
   A.dbg = out;
   A.dbg_tile = Tile{model, (int)env, 1, 0};
-  step_kernel<true><<<1, 32, b->smem_bytes, st>>>(A);
+  step_kernel<true, false><<<1, 32, b->smem_bytes, st>>>(A);
   return cudaGetLastError();
 }
 

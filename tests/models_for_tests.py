@@ -85,3 +85,33 @@ def quadruped_passive(timestep=0.004, gravity=(0, 0, 0)):
     m.act_kp[:] = 0.0
     m.act_kd[:] = 0.0
     return m
+
+
+def box_and_capsule_on_plane(timestep=0.002, iterations=100, friction=1.0):
+    """A tilted free box and a tilted free capsule resting on the floor plane: box-corner and
+    capsule-end contacts (pyramidal), for the adjoint's plane-contact features."""
+    b = W.ModelBuilder("box_capsule_plane")
+    floor = b.geom(0, W.PLANE, (0, 0, 0))
+    box = b.body(0, (0, 0, 0.2))
+    b.joint(box, W.FREE)
+    g1 = b.geom(box, W.BOX, (0.05, 0.04, 0.03), mass=0.8)
+    cap = b.body(0, (0.5, 0, 0.2))
+    b.joint(cap, W.FREE)
+    g2 = b.geom(cap, W.CAPSULE, (0.02, 0.08), mass=0.3)
+    b.pair(floor, g1, friction=friction, condim=3)
+    b.pair(floor, g2, friction=friction, condim=3)
+    return b.build(timestep=timestep, iterations=iterations, n_substeps=4)
+
+
+def limited_arm(timestep=0.002, iterations=100):
+    """Two-link arm under gravity with PD actuators driving both hinges into their limits."""
+    b = W.ModelBuilder("limited_arm")
+    l1 = b.body(0, (0, 0, 0))
+    j1 = b.joint(l1, W.HINGE, axis=(0, 1, 0), limited=True, range=(-0.4, 0.5), damping=0.05)
+    b.geom(l1, W.CAPSULE, (0.03, 0.15), pos=(0, 0, -0.15), mass=0.6)
+    l2 = b.body(l1, (0, 0, -0.3))
+    j2 = b.joint(l2, W.HINGE, axis=(0.3, 0.9, 0.3), limited=True, range=(-0.6, 0.3), damping=0.02)
+    b.geom(l2, W.CAPSULE, (0.02, 0.1), pos=(0, 0, -0.1), mass=0.3)
+    b.actuator(j1, W.POSITION, kp=8.0, kd=0.2)
+    b.actuator(j2, W.POSITION, kp=3.0, kd=0.1)
+    return b.build(timestep=timestep, iterations=iterations, n_substeps=4)

@@ -69,3 +69,18 @@ def test_null_arguments_are_errors():
     assert lib.pg_step(None, None, None, 1, None) == _capi.PG_EINVAL
     assert lib.pg_model_info(None, None) == _capi.PG_EINVAL
     assert lib.pg_batch_compile(None, None, 0, 0, None) == _capi.PG_EINVAL
+
+
+def test_adjoint_scope_and_parameter_rows():
+    """pg_model_info reports the adjoint workspace only for models inside the adjoint's scope:
+    contacts between a world plane and spheres / capsules / boxes (quadruped, cartpole), not the
+    hand (box-box, capsule-box) nor the humanoid (capsule-capsule self contact)."""
+    from paper_2502_08844_b300 import core
+    from tests import models_for_tests as MT
+    for m, ok in [(W.quadruped(), True), (W.cartpole(), True), (MT.box_and_capsule_on_plane(), True),
+                  (MT.limited_arm(), True), (W.hand(), False), (W.humanoid(), False)]:
+        s = core.CompiledModel(m).sizes
+        assert (s.adjoint_workspace_bytes > 0) == ok, m.name
+        assert s.nparam == m.nbody + m.nv + m.nu
+        if ok:
+            assert s.adjoint_workspace_bytes >= s.workspace_bytes

@@ -59,3 +59,23 @@ def test_gradient_matches_central_differences_parameters():
     _close(g["damping"][di], _fd(lambda x: O.rollout_loss(om, q0, v0, U, 5, w, mass=mass, damping=x, kp=kp), damping, di))
     ki = list(range(12))
     _close(g["kp"][ki], _fd(lambda x: O.rollout_loss(om, q0, v0, U, 5, w, mass=mass, damping=damping, kp=x), kp, ki))
+
+
+def test_step_vjp_chain_equals_rollout_gradient():
+    """The per-control-step reverse sweep, chained along the trajectory with the loss cotangents,
+    reproduces the rollout gradient (same tape, same order)."""
+    m, om, q0, v0, U, w, mass = _setup(T=3, env=1)
+    g = O.rollout_grad(om, q0, v0, U, m.n_substeps, w)
+    wq, qs, wv, vs = w
+    _, _, _, _, tq, tv = om.rollout(q0[None], v0[None], U[:, None], m.n_substeps, solver_cap=-1, trajectory=True)
+    Q = np.concatenate([q0[None], tq[:, 0]]); V = np.concatenate([v0[None], tv[:, 0]])
+    bq = np.zeros(m.nq); bv = np.zeros(m.nv); gm = np.zeros(m.nbody)
+    for t in range(2, -1, -1):
+        bq = bq + 2 * wq * (Q[t + 1] - qs); bv = bv + 2 * wv * (V[t + 1] - vs)
+        o = O.step_vjp(om, Q[t], V[t], U[t], m.n_substeps, bq, bv)
+        bq, bv = o["q"], o["v"]
+        gm += o["mass"]
+        assert np.allclose(o["u"], g["u"][t], rtol=1e-9, atol=1e-12)
+    assert np.allclose(bq, g["q0"], rtol=1e-9, atol=1e-12)
+    assert np.allclose(bv, g["v0"], rtol=1e-9, atol=1e-12)
+    assert np.allclose(gm, g["mass"], rtol=1e-9, atol=1e-12)
