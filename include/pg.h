@@ -213,6 +213,20 @@ int pg_step_vjp(pg_batch* batch, const pg_state* ckpt, const float* ctrl_dev, in
                 const float* g_qpos_dev, const float* g_qvel_dev, float* adj_qpos_dev, float* adj_qvel_dev,
                 float* g_ctrl_dev, float* g_param_dev, void* stream);
 
+/* pg_step_vjp without allocation: the same arguments, results and scope as pg_step_vjp, with
+ * the scratch in a fixed array of 4194304 floats (16 MiB) inside the library, not allocated.
+ * The paper has no counterpart; this exists for callers that must not allocate device memory
+ * during the call, e.g. one whose device memory is all held by its own pool, or a latency-bound
+ * loop where cudaMalloc / cudaFree would synchronise the device.
+ *   * A call that needs more scratch (n_steps, environments, substeps) returns PG_ECAPACITY
+ *     before any GPU work.
+ *   * Every call on a device shares the array, so calls that overlap on the GPU race.
+ *   * The first call on a device looks up the array's address and may load the library's device
+ *     code. Make it before any stream capture. */
+int pg_step_vjp_noalloc(pg_batch* batch, const pg_state* ckpt, const float* ctrl_dev, int n_steps, int n_substeps,
+                        const float* g_qpos_dev, const float* g_qvel_dev, float* adj_qpos_dev, float* adj_qvel_dev,
+                        float* g_ctrl_dev, float* g_param_dev, void* stream);
+
 const char* pg_last_error(void);
 
 #ifdef __cplusplus
