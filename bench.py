@@ -99,6 +99,26 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def replica_env0(rank: int, n_per_rank: int) -> int:
+    """First global environment index of a rank: ranks step contiguous, disjoint env ranges of
+    one job (their seeded inputs are those envs' own), no data-path exchange."""
+    return rank * n_per_rank
+
+
+def whole_job_rate(local_seconds: float, ws: int, n_per_rank: int, steps: int, dist=None):
+    """(env-steps/s of the whole job, seconds) over all ranks: every rank's env-steps over the
+    slowest rank's timed region (MAX all-reduce of the seconds when ws > 1)."""
+    secs = float(local_seconds)
+    if ws > 1:
+        import torch
+        t = torch.tensor([secs], dtype=torch.float64)
+        if torch.cuda.is_available() and dist.get_backend() == "nccl":
+            t = t.cuda()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        secs = float(t.item())
+    return ws * n_per_rank * steps / secs, secs
+
+
 def kernel_source_hash() -> str:
     """sha256 (first 16 hex digits) of the step kernel's sources: its device functions, kernels
     and internal layout header, in that order."""
@@ -291,7 +311,7 @@ def run_ours(args):
     cm = core.CompiledModel(m)
     batch = core.Batch([(cm, n)], envs_per_cta=args.envs_per_cta)
     state = core.State(batch, dev)
-    env0 = rank * n
+    env0 = replica_env0(rank, n)
     q0, v0 = W.initial_state(m, cfg, n, env0)
     ld = state.ld
     state.qpos.copy_(torch.from_numpy(core.to_soa(q0, ld, batch.nq_max)))
@@ -328,11 +348,7 @@ def run_ours(args):
     dev_s = sum(times) / 1e3
     st = stats[:, :n].to(torch.int64).sum(dim=1).cpu().numpy()
     status = state.status.cpu().numpy().view(np.uint32)
-    if ws > 1:
-        t = torch.tensor([dev_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_s = float(t.item())
-    value = ws * n * args.steps / dev_s
+    value, dev_s = whole_job_rate(dev_s, ws, n, args.steps, dist)
     # roofline: algorithmic FP32 flops per launch / mean launch time, against the CUDA-core peak
     fm = FL.flop_model(m)
     flops_total = fm.substeps(n * m.n_substeps * args.steps, st[1], st[0], st[2])
