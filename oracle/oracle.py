@@ -64,9 +64,11 @@ def lib():
         L.orc_point_jacobian.argtypes = [C.c_void_p, _dp, C.c_int, _dp, _dp, _dp]
         L.orc_integrate_pos.argtypes = [C.c_void_p, _dp, _dp, C.c_double]
         L.orc_collide.argtypes = [C.c_int, _dp, _dp, _dp, C.c_int, _dp, _dp, _dp, _dp]
-        L.orc_solve.argtypes = [C.c_int, _dp, _dp, C.c_int, _dp, _dp, _dp, _dp, C.c_int, _dp, _dp, _ip]
+        L.orc_solve.argtypes = [C.c_int, _dp, _dp, C.c_int, _dp, _dp, _dp, _dp, C.c_int, _dp, _dp, _ip, _ip, _dp]
         L.orc_cost.restype = C.c_double
-        L.orc_cost.argtypes = [C.c_int, _dp, _dp, C.c_int, _dp, _dp, _dp, _dp]
+        L.orc_cost.argtypes = [C.c_int, _dp, _dp, C.c_int, _dp, _dp, _dp, _dp, _ip, _dp]
+        L.orc_cone_cost.restype = C.c_double
+        L.orc_cone_cost.argtypes = [_dp, C.c_double, C.c_double, _dp, _dp, _ip]
         L.orc_impedance.restype = C.c_double
         L.orc_impedance.argtypes = [C.c_double, _dp]
         L.orc_solid_inertia.argtypes = [C.c_int, _dp, C.c_double, _dp]
@@ -255,19 +257,40 @@ def collide(t1, R1, p1, s1, t2, R2, p2, s2):
     return out[:n]
 
 
-def solve(M, a0, J, aref, D, warm=None, cap=-1):
-    """Newton solve on raw data; cap < 0 runs to convergence.  Returns (qacc, force, iters, converged)."""
+def _kinds(kind, mu, nr):
+    if kind is None:
+        return None, None, None
+    k = np.ascontiguousarray(np.asarray(kind, np.int32)).reshape(nr)
+    m = _d(mu).reshape(nr)
+    return k, k.ctypes.data_as(_ip), _pd(m)
+
+
+def solve(M, a0, J, aref, D, warm=None, cap=-1, kind=None, mu=None):
+    """Newton solve on raw data; cap < 0 runs to convergence.  Returns (qacc, force, iters, converged).
+    kind / mu (optional, per row): 0 scalar one-sided row, 1 elliptic normal row followed by its
+    two tangent rows (kind 2), with the contact's friction in mu."""
     M = _d(M); a0 = _d(a0); J = _d(J).reshape(-1, M.shape[0]); aref = _d(aref); D = _d(D)
     nv, nr = M.shape[0], J.shape[0]
     qacc = np.zeros(nv); force = np.zeros(max(nr, 1)); it = C.c_int(0)
+    keep, kp, mp = _kinds(kind, mu, nr)
     conv = lib().orc_solve(nv, _pd(M), _pd(a0), nr, _pd(J), _pd(aref), _pd(D),
-                           _pd(_d(warm)) if warm is not None else None, int(cap), _pd(qacc), _pd(force), C.byref(it))
+                           _pd(_d(warm)) if warm is not None else None, int(cap), _pd(qacc), _pd(force), C.byref(it),
+                           kp, mp)
     return qacc, force[:nr], it.value, bool(conv)
 
 
-def cost(M, a0, J, aref, D, a):
+def cost(M, a0, J, aref, D, a, kind=None, mu=None):
     M = _d(M); J = _d(J).reshape(-1, M.shape[0])
-    return lib().orc_cost(M.shape[0], _pd(M), _pd(_d(a0)), J.shape[0], _pd(J), _pd(_d(aref)), _pd(_d(D)), _pd(_d(a)))
+    keep, kp, mp = _kinds(kind, mu, J.shape[0])
+    return lib().orc_cost(M.shape[0], _pd(M), _pd(_d(a0)), J.shape[0], _pd(J), _pd(_d(aref)), _pd(_d(D)), _pd(_d(a)),
+                          kp, mp)
+
+
+def cone_cost(x, D, mu):
+    """Elliptic contact cost s(x) with its gradient, Hessian and zone (0 free, 1 boundary, 2 full)."""
+    g = np.zeros(3); H = np.zeros(9); z = C.c_int(0)
+    f = lib().orc_cone_cost(_pd(_d(x)), float(D), float(mu), _pd(g), _pd(H), C.byref(z))
+    return f, g, H.reshape(3, 3), z.value
 
 
 def impedance(r, solimp):

@@ -270,14 +270,27 @@ int orc_collide(int t1, const double* R1, const double* p1, const double* s1, in
 }
 
 // The Newton solver on raw data (M, a0, rows J/aref/D); cap < 0 selects the converged mode.
-int orc_solve(int nv, const double* M, const double* a0, int nr, const double* J, const double* aref, const double* D,
-              const double* warm, int cap, double* qacc, double* force, int* iters) {
-  std::vector<double> Mm(M, M + nv * nv), a(a0, a0 + nv);
+// Rows from raw arrays; kind / mu NULL: every row a one-sided scalar row
+static orc::Rows<double> raw_rows(int nv, int nr, const double* J, const double* aref, const double* D, const int* kind,
+                                  const double* mu) {
   orc::Rows<double> R;
   R.n = nr;
   R.J.assign(J, J + nr * nv);
   R.aref.assign(aref, aref + nr);
   R.D.assign(D, D + nr);
+  R.kind.assign(nr, 0);
+  R.mu.assign(nr, 0.0);
+  for (int i = 0; i < nr; i++) {
+    if (kind) R.kind[i] = kind[i];
+    if (mu) R.mu[i] = mu[i];
+  }
+  return R;
+}
+
+int orc_solve(int nv, const double* M, const double* a0, int nr, const double* J, const double* aref, const double* D,
+              const double* warm, int cap, double* qacc, double* force, int* iters, const int* kind, const double* mu) {
+  std::vector<double> Mm(M, M + nv * nv), a(a0, a0 + nv);
+  orc::Rows<double> R = raw_rows(nv, nr, J, aref, D, kind, mu);
   orc::SolveResult<double> s = orc::newton_solve(nv, Mm, a, R, warm, cap < 0 ? 200 : cap);
   std::memcpy(qacc, s.qacc.data(), sizeof(double) * nv);
   if (nr > 0) std::memcpy(force, s.force.data(), sizeof(double) * nr);
@@ -286,14 +299,17 @@ int orc_solve(int nv, const double* M, const double* a0, int nr, const double* J
 }
 
 double orc_cost(int nv, const double* M, const double* a0, int nr, const double* J, const double* aref, const double* D,
-                const double* a) {
+                const double* a, const int* kind, const double* mu) {
   std::vector<double> Mm(M, M + nv * nv), aa(a0, a0 + nv), x(a, a + nv);
-  orc::Rows<double> R;
-  R.n = nr;
-  R.J.assign(J, J + nr * nv);
-  R.aref.assign(aref, aref + nr);
-  R.D.assign(D, D + nr);
+  orc::Rows<double> R = raw_rows(nv, nr, J, aref, D, kind, mu);
   return orc::cost(nv, Mm, aa, R, x);
+}
+
+// the elliptic contact cost, its zone, gradient and Hessian at x (3), for pins
+double orc_cone_cost(const double* x, double D, double mu, double* g, double* H, int* zone) {
+  orc::cone_grad_hess(x, D, mu, g, H);
+  *zone = orc::cone_zone(x, mu);
+  return orc::cone_cost(x, D, mu);
 }
 
 // ---- rollout loss and its reverse-mode gradient ----------------------------------------

@@ -175,8 +175,9 @@ std::string compile_model(const Desc& d, Model& m) {
   for (int k = 0; k < 3; k++) m.gravity[k] = d.gravity[k];
   m.iterations = d.iterations;
   m.cone = d.cone;
-  if (m.cone != PYRAMIDAL) return "only the pyramidal cone is implemented";
+  if (m.cone != PYRAMIDAL && m.cone != ELLIPTIC) return "unknown cone";
   m.impratio = d.impratio;
+  if (m.cone == ELLIPTIC && m.impratio != 1.0) return "the elliptic cone is implemented for impratio = 1";
   for (int k = 0; k < 2; k++) m.solref[k] = d.solref[k];
   for (int k = 0; k < 5; k++) m.solimp[k] = d.solimp[k];
   m.margin = d.margin;

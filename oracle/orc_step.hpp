@@ -585,7 +585,52 @@ template <class T> struct Rows {
   std::vector<T> J;                          // n x nv
   std::vector<T> r, v, aref, D, Ahat, imp;   // per row
   std::vector<int> slot;                     // contact slot (or -1 - joint for a limit)
+  // row kind: 0 one-sided scalar row (pyramid edge, frictionless normal, joint limit);
+  // 1 normal row of an elliptic contact, followed by its 2 tangent rows (kind 2)
+  std::vector<int> kind;
+  std::vector<double> mu;                    // friction of an elliptic contact's rows
 };
+
+// Soft cost of an elliptic contact with residual x = (x_n, x_1, x_2) = J a - aref: half D times
+// the squared distance from x to the dual cone K* = {x_n >= mu |x_t|}.  With t = |x_t|:
+//   x_n >= mu t                (inside K*)          s = 0
+//   mu x_n + t <= 0            (inside -K, polar)   s = D |x|^2 / 2
+//   otherwise                  (projection on the boundary)  s = D (x_n - mu t)^2 / (2 (1 + mu^2))
+// zone: 0 / 2 / 1 respectively.  Gradient and Hessian of s in the same zones.
+template <class T> int cone_zone(const T* x, double mu) {
+  double t = std::sqrt(val(x[1]) * val(x[1]) + val(x[2]) * val(x[2]));
+  if (val(x[0]) >= mu * t) return 0;
+  if (mu * val(x[0]) + t <= 0) return 2;
+  return 1;
+}
+template <class T> T cone_cost(const T* x, const T& D, double mu) {
+  int z = cone_zone(x, mu);
+  if (z == 0) return T(0);
+  if (z == 2) return T(0.5) * D * (x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  T t = sqrt(x[1] * x[1] + x[2] * x[2]);
+  T ph = x[0] - T(mu) * t;
+  return T(0.5) * D * ph * ph / T(1 + mu * mu);
+}
+template <class T> void cone_grad_hess(const T* x, const T& D, double mu, T* g, T* H) {
+  for (int i = 0; i < 3; i++) { g[i] = T(0); for (int j = 0; j < 3; j++) H[3 * i + j] = T(0); }
+  int z = cone_zone(x, mu);
+  if (z == 0) return;
+  if (z == 2) {
+    for (int i = 0; i < 3; i++) { g[i] = D * x[i]; H[4 * i] = D; }
+    return;
+  }
+  T t = sqrt(x[1] * x[1] + x[2] * x[2]);
+  T u[2] = {x[1] / t, x[2] / t};
+  T ph = x[0] - T(mu) * t, k = D / T(1 + mu * mu);
+  T dphi[3] = {T(1), -T(mu) * u[0], -T(mu) * u[1]};
+  for (int i = 0; i < 3; i++) {
+    g[i] = k * ph * dphi[i];
+    for (int j = 0; j < 3; j++) H[3 * i + j] = k * dphi[i] * dphi[j];
+  }
+  // phi times the Hessian of phi: -mu (I - u u^T) / t on the tangent block
+  for (int i = 0; i < 2; i++)
+    for (int j = 0; j < 2; j++) H[3 * (i + 1) + (j + 1)] = H[3 * (i + 1) + (j + 1)] - k * ph * T(mu) * (T(i == j ? 1 : 0) - u[i] * u[j]) / t;
+}
 
 // Impedance d(r) from solimp = (d0, dwidth, width, mid, power): x = min(|r| / width, 1),
 // y = x^p / mid^(p-1) for x <= mid, else 1 - (1-x)^p / (1-mid)^(p-1); d = d0 + y (dwidth - d0).
@@ -613,11 +658,87 @@ template <class T> T cost(int nv, const std::vector<T>& M, const std::vector<T>&
     f = f + T(0.5) * (a[i] - a0[i]) * s;
   }
   for (int i = 0; i < R.n; i++) {
+    if (R.kind[i] == 2) continue;
+    if (R.kind[i] == 1) {
+      T x[3];
+      for (int e = 0; e < 3; e++) {
+        x[e] = -R.aref[i + e];
+        for (int j = 0; j < nv; j++) x[e] = x[e] + R.J[(i + e) * nv + j] * a[j];
+      }
+      f = f + cone_cost(x, R.D[i], R.mu[i]);
+      continue;
+    }
     T jar = -R.aref[i];
     for (int j = 0; j < nv; j++) jar = jar + R.J[i * nv + j] * a[j];
     if (val(jar) < 0) f = f + T(0.5) * R.D[i] * jar * jar;
   }
   return f;
+}
+
+// Minimiser over alpha >= 0 of the convex phi(alpha) = f(a + alpha p) when elliptic contacts make
+// it non-quadratic: bracket the root of phi' (phi'(0) < 0; double alpha from 1 until phi' >= 0),
+// then safeguarded Newton steps on phi' (a bisection whenever the Newton point leaves the
+// bracket), until the bracket or |phi'| is at rounding level.
+template <class T> T smooth_line_search(int nv, const std::vector<T>& M, const std::vector<T>& a0, const Rows<T>& R,
+                                        const std::vector<T>& a, const std::vector<T>& p) {
+  std::vector<T> jar(R.n), Jp(R.n);
+  for (int i = 0; i < R.n; i++) {
+    T s = -R.aref[i], t = T(0);
+    for (int j = 0; j < nv; j++) {
+      s = s + R.J[i * nv + j] * a[j];
+      t = t + R.J[i * nv + j] * p[j];
+    }
+    jar[i] = s;
+    Jp[i] = t;
+  }
+  T quad = T(0), lin = T(0);
+  for (int i = 0; i < nv; i++) {
+    T Mp = T(0), Md = T(0);
+    for (int j = 0; j < nv; j++) {
+      Mp = Mp + M[i * nv + j] * p[j];
+      Md = Md + M[i * nv + j] * (a[j] - a0[j]);
+    }
+    quad = quad + p[i] * Mp;
+    lin = lin + p[i] * Md;
+  }
+  // phi'(alpha) and phi''(alpha)
+  auto deriv = [&](const T& al, T& d2) {
+    T d1 = lin + al * quad;
+    d2 = quad;
+    for (int i = 0; i < R.n; i++) {
+      if (R.kind[i] == 2) continue;
+      if (R.kind[i] == 1) {
+        T x[3], y[3], g[3], H[9];
+        for (int e = 0; e < 3; e++) { x[e] = jar[i + e] + al * Jp[i + e]; y[e] = Jp[i + e]; }
+        cone_grad_hess(x, R.D[i], R.mu[i], g, H);
+        for (int e = 0; e < 3; e++) {
+          d1 = d1 + g[e] * y[e];
+          for (int f = 0; f < 3; f++) d2 = d2 + y[e] * H[3 * e + f] * y[f];
+        }
+        continue;
+      }
+      T x = jar[i] + al * Jp[i];
+      if (val(x) < 0) { d1 = d1 + R.D[i] * x * Jp[i]; d2 = d2 + R.D[i] * Jp[i] * Jp[i]; }
+    }
+    return d1;
+  };
+  T d2;
+  T g0 = deriv(T(0), d2);
+  if (!(val(g0) < 0)) return T(0);
+  T lo = T(0), hi = T(1);
+  for (int k = 0; k < 200 && val(deriv(hi, d2)) < 0; k++) { lo = hi; hi = hi * T(2); }
+  T al = lo;
+  T glo = deriv(lo, d2);
+  for (int it = 0; it < 200; it++) {
+    T cand = al - glo / d2;
+    if (!(val(cand) > val(lo) && val(cand) < val(hi))) cand = T(0.5) * (lo + hi);
+    T d2c;
+    T gc = deriv(cand, d2c);
+    if (val(gc) < 0) { lo = cand; al = cand; glo = gc; d2 = d2c; }
+    else { hi = cand; al = cand; glo = gc; d2 = d2c; }
+    if (val(hi) - val(lo) <= 1e-15 * val(hi) || std::fabs(val(gc)) <= 1e-14 * std::fabs(val(g0))) break;
+  }
+  return al;
 }
 
 template <class T> struct SolveResult {
@@ -691,15 +812,29 @@ template <class T> SolveResult<T> newton_solve(int nv, const std::vector<T>& M, 
     std::vector<T> w(warm, warm + nv);
     if (val(cost(nv, M, a0, R, w)) < val(cost(nv, M, a0, R, a0))) { a = w; out.warm_used = true; }
   }
+  bool elliptic = false;
+  for (int i = 0; i < R.n; i++) elliptic = elliptic || R.kind[i] == 1;
+  // active set: per scalar row jar < 0; per elliptic contact its zone (on its normal row)
   auto active_set = [&](const std::vector<T>& x) {
-    std::vector<char> s(R.n);
+    std::vector<char> s(R.n, 0);
     for (int i = 0; i < R.n; i++) {
+      if (R.kind[i] == 2) continue;
+      if (R.kind[i] == 1) {
+        T y[3];
+        for (int e = 0; e < 3; e++) {
+          y[e] = -R.aref[i + e];
+          for (int j = 0; j < nv; j++) y[e] = y[e] + R.J[(i + e) * nv + j] * x[j];
+        }
+        s[i] = (char)cone_zone(y, R.mu[i]);
+        continue;
+      }
       T jar = -R.aref[i];
       for (int j = 0; j < nv; j++) jar = jar + R.J[i * nv + j] * x[j];
       s[i] = val(jar) < 0;
     }
     return s;
   };
+  T f_cur = cost(nv, M, a0, R, a);
   for (int it = 0; it < cap; it++) {
     std::vector<char> A = active_set(a);
     std::vector<T> g(nv), H(M);
@@ -709,7 +844,22 @@ template <class T> SolveResult<T> newton_solve(int nv, const std::vector<T>& M, 
       g[i] = s;
     }
     for (int r = 0; r < R.n; r++) {
-      if (!A[r]) continue;
+      if (!A[r] || R.kind[r] == 2) continue;
+      if (R.kind[r] == 1) {   // J_c^T grad s and J_c^T hess s J_c over the contact's 3 rows
+        T x[3], gc[3], Hc[9];
+        for (int e = 0; e < 3; e++) {
+          x[e] = -R.aref[r + e];
+          for (int j = 0; j < nv; j++) x[e] = x[e] + R.J[(r + e) * nv + j] * a[j];
+        }
+        cone_grad_hess(x, R.D[r], R.mu[r], gc, Hc);
+        for (int i = 0; i < nv; i++)
+          for (int e = 0; e < 3; e++) {
+            g[i] = g[i] + R.J[(r + e) * nv + i] * gc[e];
+            for (int j = 0; j < nv; j++)
+              for (int f = 0; f < 3; f++) H[i * nv + j] = H[i * nv + j] + R.J[(r + e) * nv + i] * Hc[3 * e + f] * R.J[(r + f) * nv + j];
+          }
+        continue;
+      }
       T jar = -R.aref[r];
       for (int j = 0; j < nv; j++) jar = jar + R.J[r * nv + j] * a[j];
       for (int i = 0; i < nv; i++) {
@@ -725,13 +875,35 @@ template <class T> SolveResult<T> newton_solve(int nv, const std::vector<T>& M, 
     std::vector<T> p(g);
     chol_solve(H, nv, p);
     for (int i = 0; i < nv; i++) p[i] = -p[i];
-    T alpha = exact_line_search(nv, M, a0, R, a, p);
+    T alpha = elliptic ? smooth_line_search(nv, M, a0, R, a, p) : exact_line_search(nv, M, a0, R, a, p);
     for (int i = 0; i < nv; i++) a[i] = a[i] + alpha * p[i];
-    if (active_set(a) == A) { out.converged = true; break; }
+    std::vector<char> A2 = active_set(a);
+    if (!elliptic) {
+      if (A2 == A) { out.converged = true; break; }
+      continue;
+    }
+    // elliptic contacts: the Newton step is exact only when no contact sits in the middle zone
+    // (there s is not quadratic); otherwise stop when f no longer decreases
+    bool middle = false;
+    for (int i = 0; i < R.n; i++) middle = middle || (R.kind[i] == 1 && A2[i] == 1);
+    T f_new = cost(nv, M, a0, R, a);
+    if ((A2 == A && !middle) || !(val(f_new) < val(f_cur))) { out.converged = true; break; }
+    f_cur = f_new;
   }
   out.qacc = a;
   out.force.assign(R.n, T(0));
   for (int i = 0; i < R.n; i++) {
+    if (R.kind[i] == 2) continue;
+    if (R.kind[i] == 1) {   // force = -grad s
+      T x[3], gc[3], Hc[9];
+      for (int e = 0; e < 3; e++) {
+        x[e] = -R.aref[i + e];
+        for (int j = 0; j < nv; j++) x[e] = x[e] + R.J[(i + e) * nv + j] * a[j];
+      }
+      cone_grad_hess(x, R.D[i], R.mu[i], gc, Hc);
+      for (int e = 0; e < 3; e++) out.force[i + e] = -gc[e];
+      continue;
+    }
     T jar = -R.aref[i];
     for (int j = 0; j < nv; j++) jar = jar + R.J[i * nv + j] * a[j];
     if (val(jar) < 0) out.force[i] = -R.D[i] * jar;
@@ -773,10 +945,12 @@ template <class T> void build_rows(const Model& m, const Forward<T>& F, const T*
   const int nv = m.nv;
   R = Rows<T>();
   std::vector<T> Jv1, Jw1, Jv2, Jw2;
-  auto push = [&](const std::vector<T>& Jrow, T r, int slot) {
+  auto push = [&](const std::vector<T>& Jrow, T r, int slot, int kind = 0, double mu = 0.0) {
     R.J.insert(R.J.end(), Jrow.begin(), Jrow.end());
     R.r.push_back(r);
     R.slot.push_back(slot);
+    R.kind.push_back(kind);
+    R.mu.push_back(mu);
     R.n++;
   };
   for (int p = 0; p < m.npair; p++) {
@@ -796,6 +970,10 @@ template <class T> void build_rows(const Model& m, const Forward<T>& F, const T*
       }
       if (m.pair_condim[p] == 1) {
         push(Jn, c.dist, s);
+      } else if (m.cone == ELLIPTIC) {
+        push(Jn, c.dist, s, 1, m.pair_friction[p]);
+        push(Jt1, T(0), s, 2, m.pair_friction[p]);
+        push(Jt2, T(0), s, 2, m.pair_friction[p]);
       } else {
         T mu = T(m.pair_friction[p]);
         std::vector<T> e(nv);
@@ -829,12 +1007,20 @@ template <class T> void build_rows(const Model& m, const Forward<T>& F, const T*
   for (int i = 0; i < R.n; i++) {
     T v = T(0);
     for (int j = 0; j < nv; j++) v = v + R.J[i * nv + j] * qvel[j];
+    R.v[i] = v;
+    if (R.kind[i] == 2) {   // elliptic tangent row: the normal row's impedance, Ahat and D
+      const int n0 = R.kind[i - 1] == 1 ? i - 1 : i - 2;
+      R.Ahat[i] = R.Ahat[n0];
+      R.imp[i] = R.imp[n0];
+      R.aref[i] = -T(bb) * v - T(kk) * R.imp[n0] * R.r[i];
+      R.D[i] = R.D[n0] * T(m.impratio);
+      continue;
+    }
     std::vector<T> x(R.J.begin() + i * nv, R.J.begin() + (i + 1) * nv);
     chol_solve(Mchol, nv, x);
     T A = T(0);
     for (int j = 0; j < nv; j++) A = A + R.J[i * nv + j] * x[j];
     T d = impedance(R.r[i], m.solimp);
-    R.v[i] = v;
     R.Ahat[i] = A;
     R.imp[i] = d;
     R.aref[i] = -T(bb) * v - T(kk) * d * R.r[i];
