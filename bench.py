@@ -120,10 +120,10 @@ def whole_job_rate(local_seconds: float, ws: int, n_per_rank: int, steps: int, d
 
 
 def kernel_source_hash() -> str:
-    """sha256 (first 16 hex digits) of the step kernel's sources: its device functions, kernels
-    and internal layout header, in that order."""
+    """sha256 (first 16 hex digits) of the pyramidal step kernel's sources: its device functions,
+    kernels, translation unit and internal layout header, in that order."""
     h = hashlib.sha256()
-    for f in ("step_device.cuh", "step.cu", "pg_internal.h"):
+    for f in ("step_device.cuh", "step_kernels.cuh", "step.cu", "pg_internal.h"):
         h.update(open(os.path.join(ROOT, "paper_2502_08844_b300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

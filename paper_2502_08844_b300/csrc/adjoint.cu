@@ -46,6 +46,7 @@
 
 #include "pg_host.h"
 #include "pg_internal.h"
+#define PG_WITH_ELLIPTIC 0   // the adjoint covers pyramidal and frictionless contacts
 #include "step_device.cuh"
 
 namespace pg {

@@ -98,6 +98,7 @@ int pg_batch_compile(const pg_model* const* models, const int64_t* counts, int n
     b->max_ws_floats = std::max(b->max_ws_floats, h.ws_floats);
     b->max_blob_words = std::max(b->max_blob_words, h.words);
     b->max_debug = std::max(b->max_debug, h.debug_floats);
+    b->has_elliptic = b->has_elliptic || h.cone == PG_CONE_ELLIPTIC;
     b->blob_off.push_back(0);
   }
   if (b->n > (int64_t)1 << 31) { delete b; return set_error(PG_EINVAL, "too many environments"); }

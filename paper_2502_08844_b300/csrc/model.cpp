@@ -282,7 +282,9 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
   // ---- options ----
   if (!(d->timestep > 0)) return set_error(PG_EINVAL, "timestep must be > 0");
   if (d->iterations < 1) return set_error(PG_EINVAL, "iterations must be >= 1");
-  if (d->cone != PG_CONE_PYRAMIDAL) return set_error(PG_EUNSUPPORTED, "only the pyramidal cone is implemented");
+  if (d->cone != PG_CONE_PYRAMIDAL && d->cone != PG_CONE_ELLIPTIC) return set_error(PG_EINVAL, "unknown cone");
+  if (d->cone == PG_CONE_ELLIPTIC && d->impratio != 1.f)
+    return set_error(PG_EUNSUPPORTED, "the elliptic cone is implemented for impratio = 1");
   int max_contacts = d->max_contacts < 0 ? nslot : std::min(d->max_contacts, nslot);
   int nrow_max = 4 * max_contacts + (int)limit_jnt.size();
   if (nrow_max > kMaxRow) return set_error(PG_ECAPACITY, "constraint rows exceed the kernel limit (128)");
@@ -391,6 +393,7 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
       if (d->geom_type[g1] != PG_GEOM_PLANE || d->geom_body[g1] != 0 || d->geom_type[g2] == PG_GEOM_PLANE) ok = false;
     }
     if (npair > 0 && !tree_hessian) ok = false;
+    if (d->cone == PG_CONE_ELLIPTIC) ok = false;
     g.adj_ok = ok ? 1 : 0;
     h.adj_ok = g.adj_ok;
     h.ws_adj_floats = g.ws_adj_floats;

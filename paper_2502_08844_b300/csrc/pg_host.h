@@ -33,6 +33,7 @@ struct pg_batch {
   std::vector<uint32_t> blob_host;   // all models' blobs, concatenated (passed as a kernel parameter)
   std::vector<pg::Tile> tiles;
   std::vector<uint32_t> blob_host_adj;   // the same with the adjoint headers
+  bool has_elliptic = false;             // a model uses the elliptic cone (selects the kernels)
   // staging buffer of the host-buffer path (allocated on its first use)
   float* d_ctrl_stage = nullptr;
   size_t ctrl_stage_floats = 0;
@@ -56,6 +57,20 @@ cudaError_t launch_reset(const pg_batch* b, const pg_state* s, const uint8_t* ma
 cudaError_t configure_step_kernels(size_t smem_bytes);
 cudaError_t launch_step_tape(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, float* tape,
                              int tape_rows, cudaStream_t st);
+// the kernels of step_kernels.cuh, compiled without (step.cu) and with (step_elliptic.cu) the
+// elliptic cone
+#define PG_DECLARE_STEP_KERNELS(NS)                                                                               \
+  namespace NS {                                                                                                 \
+  cudaError_t configure(size_t smem_bytes);                                                                      \
+  cudaError_t step(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st);    \
+  cudaError_t step_tape(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, float* tape,     \
+                        int tape_rows, cudaStream_t st);                                                         \
+  cudaError_t debug(const pg_batch* b, const pg_state* s, const float* ctrl, int64_t env, float* out,            \
+                    cudaStream_t st);                                                                            \
+  }
+PG_DECLARE_STEP_KERNELS(pyramidal)
+PG_DECLARE_STEP_KERNELS(elliptic)
+#undef PG_DECLARE_STEP_KERNELS
 // adjoint.cu
 cudaError_t launch_vjp_step(const pg_batch* b, const float* tape, int tape_rows, const float* ctrl, const float* gq,
                             const float* gv, float* adj_q, float* adj_v, float* g_ctrl, float* g_params, float* ws,

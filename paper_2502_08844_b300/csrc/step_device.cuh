@@ -4,6 +4,11 @@
 // Included by the step kernels and by the adjoint kernels; everything lives in an anonymous
 // namespace, one copy per translation unit.
 #pragma once
+// PG_WITH_ELLIPTIC (0 or 1), set by the including translation unit, says whether its kernels
+// handle the elliptic friction cone; with 0 every elliptic branch is compiled out of the loops.
+#ifndef PG_WITH_ELLIPTIC
+#error "define PG_WITH_ELLIPTIC (0 or 1) before including step_device.cuh"
+#endif
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -789,6 +794,58 @@ __device__ __forceinline__ float edge_value(float mu, int e, float dn, float d1,
   return (e & 1) ? dn - mu * dt : dn + mu * dt;
 }
 
+// the 4 rows of a contact group: pyramid edges, or (n, t1, t2, -) of an elliptic contact
+__device__ __forceinline__ float row_value(bool ell, float mu, int e, float dn, float d1, float d2) {
+  if (ell) return e == 0 ? dn : (e == 1 ? d1 : (e == 2 ? d2 : 0.f));
+  return edge_value(mu, e, dn, d1, d2);
+}
+
+__device__ __forceinline__ bool elliptic_group(const Ctx& c, int k) {
+  return PG_WITH_ELLIPTIC && c.h.cone == PG_CONE_ELLIPTIC && W(gcond, k) == 3.f;
+}
+
+// Elliptic contact with residual x = (xn, x1, x2), friction mu and D: the soft cost is D/2 times
+// the squared distance from x to the dual cone {xn >= mu |xt|}.  Zones: 0 inside (no cost),
+// 2 inside the polar cone (mu xn + |xt| <= 0: the full quadratic), 1 between (distance to the
+// boundary: D (xn - mu |xt|)^2 / (2 (1 + mu^2))).
+__device__ __forceinline__ int cone_zone(float xn, float x1, float x2, float mu) {
+  const float t = sqrtf(x1 * x1 + x2 * x2);
+  if (xn >= mu * t) return 0;
+  if (mu * xn + t <= 0.f) return 2;
+  return 1;
+}
+__device__ __forceinline__ float cone_cost(float xn, float x1, float x2, float mu, float D) {
+  const int z = cone_zone(xn, x1, x2, mu);
+  if (z == 0) return 0.f;
+  if (z == 2) return 0.5f * D * (xn * xn + x1 * x1 + x2 * x2);
+  const float ph = xn - mu * sqrtf(x1 * x1 + x2 * x2);
+  return 0.5f * D * ph * ph / (1.f + mu * mu);
+}
+// gradient g and Hessian B = (B00 B01 B02 B11 B12 B22) of the elliptic cost
+__device__ __forceinline__ void cone_derivs(float xn, float x1, float x2, float mu, float D, float g[3], float B[6]) {
+  const int z = cone_zone(xn, x1, x2, mu);
+  if (z == 0) {
+    g[0] = g[1] = g[2] = 0.f;
+    B[0] = B[1] = B[2] = B[3] = B[4] = B[5] = 0.f;
+    return;
+  }
+  if (z == 2) {
+    g[0] = D * xn; g[1] = D * x1; g[2] = D * x2;
+    B[0] = D; B[1] = 0.f; B[2] = 0.f; B[3] = D; B[4] = 0.f; B[5] = D;
+    return;
+  }
+  const float t = sqrtf(x1 * x1 + x2 * x2), u1 = x1 / t, u2 = x2 / t;
+  const float ph = xn - mu * t, k = D / (1.f + mu * mu);
+  const float d1 = -mu * u1, d2 = -mu * u2, q = k * ph * mu / t;   // q: phi times the curvature term
+  g[0] = k * ph; g[1] = k * ph * d1; g[2] = k * ph * d2;
+  B[0] = k;
+  B[1] = k * d1;
+  B[2] = k * d2;
+  B[3] = k * d1 * d1 - q * (1.f - u1 * u1);
+  B[4] = k * d1 * d2 + q * u1 * u2;
+  B[5] = k * d2 * d2 - q * (1.f - u2 * u2);
+}
+
 // J_r . x for every row into the element buffer OUT (rows of absent contacts give 0)
 __device__ void rows_dot(const Ctx& c, int X, int OUT) {
   const ModelHdr& h = c.h;
@@ -805,7 +862,8 @@ __device__ void rows_dot(const Ctx& c, int X, int OUT) {
       d2 = fmaf(J[(2 * NC + a) * c.S], xa, d2);
     }
     const float mu = W(gmu, k);
-    for (int e = 0; e < 4; e++) c.w[(OUT + 4 * k + e) * c.S] = edge_value(mu, e, dn, d1, d2);
+    const bool ell = elliptic_group(c, k);
+    for (int e = 0; e < 4; e++) c.w[(OUT + 4 * k + e) * c.S] = row_value(ell, mu, e, dn, d1, d2);
   }
   for (int li = 0; li < h.nlimited; li++) {
     const int d = MI(jnt_dofadr, MI(limit_jnt, li));
@@ -866,7 +924,7 @@ __device__ void row_params(const Ctx& c, int nc) {
   for (int k = 0; k < MC; k++) {
     const bool valid = k < nc;
     const int p = valid ? con_pair(c, k) : 0;
-    W(gmu, k) = valid ? MF(pair_friction, p) : 0.f;
+    W(gmu, k) = valid && MI(pair_condim, p) == 3 ? MF(pair_friction, p) : 0.f;
     W(gcond, k) = valid ? (float)MI(pair_condim, p) : 0.f;
   }
   rows_dot(c, h.w_qvel, h.w_rv);
@@ -896,7 +954,20 @@ __device__ void row_params(const Ctx& c, int nc) {
         A22 = fmaf(z2 * z2, dinv, A22);
       }
     }
-    if (pyr) {
+    if (pyr && PG_WITH_ELLIPTIC && c.h.cone == PG_CONE_ELLIPTIC) {
+      // normal row: impedance from the depth; the tangent rows share its impedance, Ahat and D
+      // (impratio 1) at zero position, so their reference acceleration is -b v
+      set_row(c, 4 * k + 0, valid, dist, Ann);
+      for (int e = 1; e < 3; e++) {
+        const int r = 4 * k + e;
+        W(rr, r) = 0.f;
+        W(Ahat, r) = W(Ahat, 4 * k);
+        W(imp, r) = W(imp, 4 * k);
+        W(aref, r) = -h.bref * W(rv, r);
+        W(rD, r) = W(rD, 4 * k);
+      }
+      set_row(c, 4 * k + 3, false, dist, 1.f);
+    } else if (pyr) {
       set_row(c, 4 * k + 0, valid, dist, Ann + 2.f * mu * An1 + mu * mu * A11);
       set_row(c, 4 * k + 1, valid, dist, Ann - 2.f * mu * An1 + mu * mu * A11);
       set_row(c, 4 * k + 2, valid, dist, Ann + 2.f * mu * An2 + mu * mu * A22);
@@ -942,6 +1013,12 @@ __device__ float cost_of(const Ctx& c, int X) {
   for (int k = 0; k < h.nv; k++) f = fmaf(0.5f * W(t, k), W(g, k), f);
   rows_dot(c, X, h.w_jar);
   for (int r = 0; r < h.nrow_max; r++) {
+    if (r < 4 * h.max_contacts && elliptic_group(c, r >> 2)) {
+      if ((r & 3) == 0 && W(rD, r) > 0.f)
+        f += cone_cost(W(jar, r) - W(aref, r), W(jar, r + 1) - W(aref, r + 1), W(jar, r + 2) - W(aref, r + 2),
+                       W(gmu, r >> 2), W(rD, r));
+      continue;
+    }
     const float jar = W(jar, r) - W(aref, r);
     if (jar < 0.f) f = fmaf(0.5f * W(rD, r) * jar, jar, f);
   }
@@ -955,10 +1032,18 @@ __device__ void residuals(const Ctx& c, unsigned act[4]) {
   const ModelHdr& h = c.h;
   rows_dot(c, h.w_a, h.w_jar);
   act[0] = act[1] = act[2] = act[3] = 0u;
+  for (int r = 0; r < h.nrow_max; r++) W(jar, r) = W(jar, r) - W(aref, r);
   for (int r = 0; r < h.nrow_max; r++) {
-    const float jar = W(jar, r) - W(aref, r);
-    W(jar, r) = jar;
-    if (jar < 0.f && W(rD, r) > 0.f) act[r >> 5] |= 1u << (r & 31);
+    if (r < 4 * h.max_contacts && elliptic_group(c, r >> 2)) {
+      // an elliptic contact's zone on its first two bits: not free / full
+      if ((r & 3) == 0 && W(rD, r) > 0.f) {
+        const int z = cone_zone(W(jar, r), W(jar, r + 1), W(jar, r + 2), W(gmu, r >> 2));
+        if (z != 0) act[r >> 5] |= 1u << (r & 31);
+        if (z == 2) act[(r + 1) >> 5] |= 1u << ((r + 1) & 31);
+      }
+      continue;
+    }
+    if (W(jar, r) < 0.f && W(rD, r) > 0.f) act[r >> 5] |= 1u << (r & 31);
   }
 }
 
@@ -981,16 +1066,26 @@ __device__ bool newton_direction(const Ctx& c, const unsigned act[4], bool& zero
   }
   for (int k = 0; k < MC; k++) {
     const float mu = W(gmu, k);
-    // the active edges summed in the (n, t1, t2) basis
-    float Sn = 0.f, c1 = 0.f, c2 = 0.f, s1 = 0.f, s2 = 0.f, gn = 0.f, g1 = 0.f, g2 = 0.f;
-    for (int e = 0; e < 4; e++) {
-      const int r = 4 * k + e;
-      const float D = bit(act, r) ? W(rD, r) : 0.f, DJ = D * W(jar, r);
-      const float sg = (e & 1) ? -mu : mu;
-      Sn += D;
-      gn += DJ;
-      if (e < 2) { c1 += sg * D; s1 += mu * mu * D; g1 += sg * DJ; }
-      else { c2 += sg * D; s2 += mu * mu * D; g2 += sg * DJ; }
+    // gradient (gn, g1, g2) and Hessian block (Sn c1 c2 / s1 c12 / s2) in the (n, t1, t2) basis:
+    // the active pyramid edges summed, or the elliptic cost's derivatives
+    float Sn = 0.f, c1 = 0.f, c2 = 0.f, s1 = 0.f, s2 = 0.f, c12 = 0.f, gn = 0.f, g1 = 0.f, g2 = 0.f;
+    if (elliptic_group(c, k)) {
+      const int r = 4 * k;
+      if (!bit(act, r)) continue;
+      float gg[3], B[6];
+      cone_derivs(W(jar, r), W(jar, r + 1), W(jar, r + 2), mu, W(rD, r), gg, B);
+      gn = gg[0]; g1 = gg[1]; g2 = gg[2];
+      Sn = B[0]; c1 = B[1]; c2 = B[2]; s1 = B[3]; c12 = B[4]; s2 = B[5];
+    } else {
+      for (int e = 0; e < 4; e++) {
+        const int r = 4 * k + e;
+        const float D = bit(act, r) ? W(rD, r) : 0.f, DJ = D * W(jar, r);
+        const float sg = (e & 1) ? -mu : mu;
+        Sn += D;
+        gn += DJ;
+        if (e < 2) { c1 += sg * D; s1 += mu * mu * D; g1 += sg * DJ; }
+        else { c2 += sg * D; s2 += mu * mu * D; g2 += sg * DJ; }
+      }
     }
     if (Sn == 0.f) continue;
     const float* J = c.w + (h.w_J + 3 * NC * k) * c.S;
@@ -1000,8 +1095,8 @@ __device__ bool newton_direction(const Ctx& c, const unsigned act[4], bool& zero
       const float na = J[a * c.S], ta = J[(NC + a) * c.S], ua = J[(2 * NC + a) * c.S];
       W(g, da) += gn * na + g1 * ta + g2 * ua;
       const float hn = Sn * na + c1 * ta + c2 * ua;
-      const float ht = c1 * na + s1 * ta;
-      const float hu = c2 * na + s2 * ua;
+      const float ht = c1 * na + s1 * ta + c12 * ua;
+      const float hu = c2 * na + c12 * ta + s2 * ua;
       const int ra = MI(dof_rowadr, da), depa = MI(dof_depth, da);
       for (int b = a; b < NC; b++) {
         const int db = __float_as_int(gc[b * c.S]);
@@ -1101,15 +1196,86 @@ __device__ float line_search(const Ctx& c) {
   return qt > 0.f ? -lt / qt : alpha;
 }
 
+// Line search when elliptic contacts make phi(alpha) = f(a + alpha p) convex but not piecewise
+// quadratic: bracket the root of phi' (phi'(0) < 0; alpha doubled from 1 until phi' >= 0), then
+// safeguarded Newton steps on phi' (bisection whenever the Newton point leaves the bracket) until
+// the bracket or |phi'| is at FP32 rounding level.
+__device__ float line_search_smooth(const Ctx& c) {
+  const ModelHdr& h = c.h;
+  const int nv = h.nv, R = h.nrow_max, MC = h.max_contacts;
+  sym_mul(c, h.w_M, h.w_p, h.w_g);   // g <- M p
+  float qt = 0.f, lt = 0.f;
+  for (int k = 0; k < nv; k++) {
+    qt = fmaf(W(p, k), W(g, k), qt);
+    lt = fmaf(W(t, k), W(g, k), lt);   // t = a - a0
+  }
+  rows_dot(c, h.w_p, h.w_Jp);
+  auto deriv = [&](float al, float& d2) {
+    float d1 = fmaf(al, qt, lt);
+    d2 = qt;
+    for (int r = 0; r < R; r++) {
+      if (!(W(rD, r) > 0.f)) continue;
+      if (r < 4 * MC && elliptic_group(c, r >> 2)) {
+        if ((r & 3) != 0) continue;
+        const float y0 = W(Jp, r), y1 = W(Jp, r + 1), y2 = W(Jp, r + 2);
+        float gg[3], B[6];
+        cone_derivs(fmaf(al, y0, W(jar, r)), fmaf(al, y1, W(jar, r + 1)), fmaf(al, y2, W(jar, r + 2)), W(gmu, r >> 2),
+                    W(rD, r), gg, B);
+        d1 += gg[0] * y0 + gg[1] * y1 + gg[2] * y2;
+        d2 += B[0] * y0 * y0 + B[3] * y1 * y1 + B[5] * y2 * y2 + 2.f * (B[1] * y0 * y1 + B[2] * y0 * y2 + B[4] * y1 * y2);
+        continue;
+      }
+      const float jp = W(Jp, r), x = fmaf(al, jp, W(jar, r));
+      if (x < 0.f) {
+        d1 = fmaf(W(rD, r) * x, jp, d1);
+        d2 = fmaf(W(rD, r) * jp, jp, d2);
+      }
+    }
+    return d1;
+  };
+  float d2;
+  const float g0 = deriv(0.f, d2);
+  if (!(g0 < 0.f)) return 0.f;
+  float lo = 0.f, hi = 1.f;
+  for (int k = 0; k < 60 && deriv(hi, d2) < 0.f; k++) { lo = hi; hi *= 2.f; }
+  float al = lo;
+  float glo = deriv(lo, d2);
+  for (int it = 0; it < 40; it++) {
+    float cand = al - glo / d2;
+    if (!(cand > lo && cand < hi)) cand = 0.5f * (lo + hi);
+    float d2c;
+    const float gc = deriv(cand, d2c);
+    if (gc < 0.f) lo = cand;
+    else hi = cand;
+    al = cand;
+    glo = gc;
+    d2 = d2c;
+    if (hi - lo <= 1e-6f * hi || fabsf(gc) <= 1e-6f * fabsf(g0)) break;
+  }
+  return al;
+}
+
+// any elliptic contact in this environment's rows
+__device__ __forceinline__ bool has_elliptic(const Ctx& c) {
+  if (!PG_WITH_ELLIPTIC || c.h.cone != PG_CONE_ELLIPTIC) return false;
+  bool any = false;
+  for (int k = 0; k < c.h.max_contacts; k++) any = any || (elliptic_group(c, k) && W(rD, 4 * k) > 0.f);
+  return any;
+}
+
 // Newton's method with exact termination: stop at the cap or when the active set after the
 // step equals the one the Hessian was built from.  Warm start: qacc_warm if f(warm) < f(a0).
+// With elliptic contacts the step is exact only when none is on its cone's boundary zone;
+// otherwise it stops when f no longer decreases.
 __device__ int newton(const Ctx& c, bool& converged) {
   const ModelHdr& h = c.h;
   const int nv = h.nv;
   converged = false;
   const float fw = cost_of(c, h.w_warm), f0 = cost_of(c, h.w_a0);
   const bool use_warm = fw < f0;
+  float f_cur = use_warm ? fw : f0;
   for (int k = 0; k < nv; k++) W(a, k) = use_warm ? W(warm, k) : W(a0, k);
+  const bool ell = has_elliptic(c);
   unsigned act[4];
   residuals(c, act);
   int it = 0;
@@ -1119,13 +1285,22 @@ __device__ int newton(const Ctx& c, bool& converged) {
     it++;
     if (zero) { converged = true; break; }
     if (!ok) break;
-    const float alpha = line_search(c);
+    const float alpha = ell ? line_search_smooth(c) : line_search(c);
     for (int k = 0; k < nv; k++) W(a, k) = fmaf(alpha, W(p, k), W(a, k));
+    const float f_new = ell ? cost_of(c, h.w_a) : 0.f;   // (before the residuals: cost_of reuses jar)
     unsigned act2[4];
     residuals(c, act2);
     const bool same = act2[0] == act[0] && act2[1] == act[1] && act2[2] == act[2] && act2[3] == act[3];
     act[0] = act2[0]; act[1] = act2[1]; act[2] = act2[2]; act[3] = act2[3];
-    if (same) { converged = true; break; }
+    if (!ell) {
+      if (same) { converged = true; break; }
+      continue;
+    }
+    bool middle = false;
+    for (int k = 0; k < h.max_contacts; k++)
+      middle = middle || (elliptic_group(c, k) && W(rD, 4 * k) > 0.f && bit(act, 4 * k) && !bit(act, 4 * k + 1));
+    if ((same && !middle) || !(f_new < f_cur)) { converged = true; break; }
+    f_cur = f_new;
   }
   return it;
 }
@@ -1196,9 +1371,10 @@ __device__ void substep(const Ctx& c, uint32_t& status, float* dbg, uint32_t cnt
         const float mu = W(gmu, k);
         const float* J = c.w + (h.w_J + 3 * h.ncol_max * k) * c.S;
         const float* gc = c.w + (h.w_gcol + h.ncol_max * k) * c.S;
+        const bool ell = elliptic_group(c, k);
         for (int a = 0; a < h.ncol_max; a++)
           o[__float_as_int(gc[a * c.S])] += W(gcond, k) == 3.f
-              ? edge_value(mu, e, J[a * c.S], J[(h.ncol_max + a) * c.S], J[(2 * h.ncol_max + a) * c.S])
+              ? row_value(ell, mu, e, J[a * c.S], J[(h.ncol_max + a) * c.S], J[(2 * h.ncol_max + a) * c.S])
               : J[a * c.S];
       } else {
         const int li = r - 4 * h.max_contacts, d = MI(jnt_dofadr, MI(limit_jnt, li));
@@ -1208,6 +1384,13 @@ __device__ void substep(const Ctx& c, uint32_t& status, float* dbg, uint32_t cnt
       o[nv + 4] = W(Ahat, r); o[nv + 5] = W(imp, r);
       const float jar = W(jar, r) - W(aref, r);
       o[nv + 6] = jar < 0.f ? -W(rD, r) * jar : 0.f;
+      if (r < 4 * h.max_contacts && elliptic_group(c, r >> 2)) {   // force = -grad of the cone cost
+        const int r0 = r & ~3;
+        float gg[3], B[6];
+        cone_derivs(W(jar, r0) - W(aref, r0), W(jar, r0 + 1) - W(aref, r0 + 1), W(jar, r0 + 2) - W(aref, r0 + 2),
+                    W(gmu, r >> 2), W(rD, r0), gg, B);
+        o[nv + 6] = -gg[r & 3];
+      }
     }
     dbg[h.dbg_nrow] = (float)nrow;
     dbg[h.dbg_iter] = (float)iters;

@@ -345,7 +345,7 @@ HAND_CUBE = 0.07
 HAND_CUBE_Y = 0.025   # cube centre towards the finger roots: curled fingers reach its +y face
 
 
-def hand(max_contacts: int = 20) -> Model:
+def hand(max_contacts: int = 20, cone: int = PYRAMIDAL) -> Model:
     """Fixed-base 16-hinge hand with a free 7 cm cube (LEAP-like, App. C.2).  World-fixed palm box
     0.12x0.10x0.02 m with its top face at z = 0; 4 fingers rooted on the palm's +y edge, each a
     chain of 4 capsule phalanges (r 0.01; 0.05/0.04/0.035/0.03 m, 0.05/0.04/0.03/0.02 kg) with
@@ -382,8 +382,15 @@ def hand(max_contacts: int = 20) -> Model:
     for j in range(16):   # targets are drawn within the joint's range
         b.actuator(j, POSITION, kp=3.0, kd=0.1, ctrlrange=(-0.5, 0.5) if j % 4 == 0 else (-0.3, 1.6))
     qpos = [0.0] * 16 + [0.0, HAND_CUBE_Y, HAND_CUBE / 2, 1.0, 0.0, 0.0, 0.0]
-    return b.build(timestep=0.005, iterations=6, cone=PYRAMIDAL, n_substeps=10, max_contacts=max_contacts,
-                   qpos_init=qpos)
+    m = b.build(timestep=0.005, iterations=6, cone=cone, n_substeps=10, max_contacts=max_contacts, qpos_init=qpos)
+    if cone == ELLIPTIC:
+        m.name = "hand_elliptic"
+    return m
+
+
+def hand_elliptic() -> Model:
+    """The hand with the elliptic friction cone (the workload's other cone option)."""
+    return hand(cone=ELLIPTIC)
 
 
 def humanoid() -> Model:
@@ -475,7 +482,7 @@ def b_njnt(b: ModelBuilder) -> int:
     return len(b.joints)
 
 
-MODELS = {"cartpole": cartpole, "quadruped": quadruped, "hand": hand, "humanoid": humanoid}
+MODELS = {"cartpole": cartpole, "quadruped": quadruped, "hand": hand, "hand_elliptic": hand_elliptic, "humanoid": humanoid}
 
 
 def model(name: str) -> Model:

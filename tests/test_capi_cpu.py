@@ -50,7 +50,8 @@ def _broken(mutate):
     (lambda m: m.jnt_axis.__setitem__(slice(3, 4), 0.0), -1),           # zero hinge axis
     (lambda m: m.pair_geom.__setitem__((0, 0), m.pair_geom[0, 1]) or m.pair_geom.__setitem__((0, 1), 0), -4),  # sphere-plane order
     (lambda m: m.pair_condim.__setitem__(0, 6), -4),                     # condim 6
-    (lambda m: setattr(m, "cone", W.ELLIPTIC), -4),
+    (lambda m: setattr(m, "cone", 2), -1),                                # unknown cone
+    (lambda m: setattr(m, "cone", W.ELLIPTIC) or setattr(m, "impratio", 2.0), -4),   # elliptic needs impratio 1
     (lambda m: setattr(m, "timestep", 0.0), -1),
     (lambda m: m.act_jnt.__setitem__(0, 0), -1),                         # actuator on the free joint
 ])

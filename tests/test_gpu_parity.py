@@ -84,7 +84,12 @@ def _phase_compare(m, om, q, v, u, warm=None, env=5, n=8):
         assert_close_scaled("J", g["rows"][:, :nv], o["rows"][:, :nv], ONE_STEP_RTOL)
         for i, k in enumerate(["r", "v", "aref", "D", "Ahat", "imp", "force"]):
             assert_close_scaled(k, g["rows"][:, nv + i], o["rows"][:, nv + i], ROW_DERIVED_RTOL.get(k, ONE_STEP_RTOL))
-    assert g["iterations"] == o["iterations"]
+    if m.cone == W.ELLIPTIC:
+        # with a contact on its cone's boundary zone the solver stops when f no longer decreases,
+        # which FP32 reaches earlier than FP64; the acceleration above agrees all the same
+        assert 1 <= g["iterations"] <= o["iterations"]
+    else:
+        assert g["iterations"] == o["iterations"]
     return g, o
 
 
@@ -178,6 +183,28 @@ def test_contact_forces_match_converged_oracle():
         assert err <= FORCE_RTOL, err
         checked += 1
     assert checked >= 3
+
+
+def test_elliptic_contact_forces_match_converged_oracle():
+    """Hand with the elliptic cone, both solvers run to convergence: the contact forces (n, t1, t2
+    per contact) against the oracle's."""
+    m = W.hand_elliptic()
+    om, states = _rollout_states(m, 2, (0, 6, 30))
+    mc = W.hand_elliptic()
+    mc.iterations = 100
+    checked = 0
+    for q, v, u in states:
+        run = GpuRun(mc, 4)
+        run.set_state(np.repeat(q[None], 4, 0), np.repeat(v[None], 4, 0))
+        g = run.debug(np.repeat(u[None], 4, 0), 2)
+        o = om.forward(q, v, np.zeros(m.nv), u, solver_cap=-1)
+        if g["nrow"] == 0 or g["nrow"] != o["nrow"]:
+            continue
+        fg, fo = g["rows"][:, m.nv + 6], o["rows"][:, m.nv + 6]
+        err = np.abs(fg - fo).max() / max(np.abs(fo).max(), 1e-9)
+        assert err <= FORCE_RTOL, err
+        checked += 1
+    assert checked >= 6
 
 
 def test_full_size_launch_sampled_envs():
@@ -291,7 +318,7 @@ def _rollout_states(m, cfg, times, n_env=4):
     return om, out
 
 
-@pytest.mark.parametrize("mname,cfg", [("hand", 2), ("humanoid", 3)])
+@pytest.mark.parametrize("mname,cfg", [("hand", 2), ("hand_elliptic", 2), ("humanoid", 3)])
 def test_phase_parity_hand_and_humanoid(mname, cfg):
     m = W.model(mname)
     om, states = _rollout_states(m, cfg, (0, 6, 30))
@@ -303,7 +330,9 @@ def test_phase_parity_hand_and_humanoid(mname, cfg):
 
 
 @pytest.mark.parametrize("mname,cfg,n,T,rtol", [("hand", 2, 40, 1, ONE_STEP_RTOL), ("humanoid", 3, 33, 1, ONE_STEP_RTOL),
-                                                 ("hand", 2, 24, 20, ROLLOUT_RTOL), ("humanoid", 3, 24, 50, ROLLOUT_RTOL)])
+                                                 ("hand_elliptic", 2, 40, 1, ONE_STEP_RTOL),
+                                                 ("hand", 2, 24, 20, ROLLOUT_RTOL), ("humanoid", 3, 24, 50, ROLLOUT_RTOL),
+                                                 ("hand_elliptic", 2, 24, 20, ROLLOUT_RTOL)])
 def test_trajectories_hand_and_humanoid(mname, cfg, n, T, rtol):
     m, tqg, tvg, tqo, tvo, stg, sto = _trajectory_parity(mname, cfg, n, T)
     for e in range(n):
