@@ -120,10 +120,11 @@ def whole_job_rate(local_seconds: float, ws: int, n_per_rank: int, steps: int, d
 
 
 def kernel_source_hash() -> str:
-    """sha256 (first 16 hex digits) of the pyramidal step kernel's sources: its device functions,
-    kernels, translation unit and internal layout header, in that order."""
+    """sha256 (first 16 hex digits) of the step kernel's sources (the generic and the run-time
+    specialised builds): device functions, kernel body, kernels, translation unit, specialiser
+    and internal layout header, in that order."""
     h = hashlib.sha256()
-    for f in ("step_device.cuh", "step_kernels.cuh", "step.cu", "pg_internal.h"):
+    for f in ("step_device.cuh", "step_kernel_body.cuh", "step_kernels.cuh", "step.cu", "specialize.cpp", "pg_internal.h"):
         h.update(open(os.path.join(ROOT, "paper_2502_08844_b300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -310,6 +311,13 @@ def run_ours(args):
     m = W.model(args.workload)
     cm = core.CompiledModel(m)
     batch = core.Batch([(cm, n)], envs_per_cta=args.envs_per_cta)
+    kernel = "generic"
+    if not args.generic_kernel:
+        try:
+            batch.specialize()   # NVRTC, cached; seconds on a first compile (outside the timed region)
+            kernel = "model-specialised (run-time compiled)"
+        except Exception as e:   # keeps the generic kernel; reported in the line
+            kernel = "generic (specialisation failed: %s)" % str(e).splitlines()[0][:200]
     state = core.State(batch, dev)
     env0 = replica_env0(rank, n)
     q0, v0 = W.initial_state(m, cfg, n, env0)
@@ -393,7 +401,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "%s-%d" % (args.workload, n), "n_envs_per_gpu": n, "substeps": m.n_substeps,
                        "dt": m.timestep, "newton_cap": m.iterations, "cone": "pyramidal",
-                       "envs_per_cta": args.envs_per_cta or "default",
+                       "envs_per_cta": args.envs_per_cta or "default", "kernel": kernel,
                        "l2": "flushed between timed steps (256 MB write outside the events)",
                        "wall_s_timed_region": wall},
             "roofline": roof, "e2e": e2e, "gpu_launches": args.steps,
@@ -422,6 +430,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--generic-kernel", action="store_true", help="skip pg_batch_specialize")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

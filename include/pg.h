@@ -30,8 +30,18 @@
 #ifndef PG_H_
 #define PG_H_
 
+#ifdef __CUDACC_RTC__   /* the library's runtime kernel compiler: no system headers */
+typedef unsigned long size_t;
+typedef signed char int8_t;
+typedef unsigned char uint8_t;
+typedef int int32_t;
+typedef unsigned int uint32_t;
+typedef long long int64_t;
+typedef unsigned long long uint64_t;
+#else
 #include <stddef.h>
 #include <stdint.h>
+#endif
 
 #ifdef __cplusplus
 extern "C" {
@@ -125,6 +135,8 @@ typedef struct pg_state {
                          += Newton iterations, += constraint rows, += rows * iterations      */
 } pg_state;
 
+#ifndef __CUDACC_RTC__   /* host API (not seen by the run-time kernel compiler) */
+
 /* Validate a description and build the library's model (host tables and a device copy).
  * Errors: PG_EINVAL (malformed tree or arrays), PG_EUNSUPPORTED (pair/cone type),
  * PG_ECAPACITY (beyond the kernel's compiled limits: nv <= 64, nbody <= 64, slots <= 64,
@@ -140,6 +152,25 @@ int pg_batch_compile(const pg_model* const* models, const int64_t* counts, int n
                      pg_batch** out);
 int pg_batch_info(const pg_batch* batch, int64_t* n_envs, int* nq_max, int* nv_max, int* nu_max);
 void pg_batch_free(pg_batch* batch);
+
+/* Compile, at run time, a step kernel specialised to the batch's model and use it for every
+ * following pg_step / pg_step_host of this batch.
+ *
+ * What changes. The specialised kernel takes the model's header, tables and workspace stride as
+ * constants, which the generic kernel reads at run time. The arithmetic is the same source in
+ * the same order, so results are identical.
+ *
+ * How. The kernel is compiled with NVRTC (libnvrtc.so.13, loaded on first use) for sm_103a and
+ * cached per process and on disk ($PG_KERNEL_CACHE, else ~/.cache/paper_2502_08844_b300/kernels).
+ * A first compile takes seconds, so call this before any stream capture and outside timed
+ * regions.
+ *
+ * Scope. Only single-model batches, and only the production step: the tape (pg_step_vjp) and
+ * debug kernels stay generic.
+ *
+ * Errors. PG_EUNSUPPORTED (a mixed batch, NVRTC missing or failing, with its log in
+ * pg_last_error; the batch then keeps the generic kernel), PG_ECUDA. */
+int pg_batch_specialize(pg_batch* batch);
 
 /* Reset the envs whose env_mask_dev[e] != 0 (all envs when env_mask_dev is NULL): copy
  * qpos0/qvel0 ([coord][ld], same layout as the state), zero qacc_warm and status. */
@@ -228,6 +259,8 @@ int pg_step_vjp_noalloc(pg_batch* batch, const pg_state* ckpt, const float* ctrl
                         float* g_ctrl_dev, float* g_param_dev, void* stream);
 
 const char* pg_last_error(void);
+
+#endif  /* __CUDACC_RTC__ */
 
 #ifdef __cplusplus
 }

@@ -51,7 +51,7 @@ class pg_state(C.Structure):
 
 EXPORTS = ["pg_model_compile", "pg_model_info", "pg_model_free", "pg_batch_compile", "pg_batch_info",
            "pg_batch_free", "pg_reset", "pg_step", "pg_debug_substep", "pg_step_host", "pg_step_vjp",
-           "pg_step_vjp_noalloc", "pg_last_error"]
+           "pg_step_vjp_noalloc", "pg_batch_specialize", "pg_last_error"]
 
 if not os.path.exists(LIB_PATH):
     raise ImportError("libpg.so is not built (run `python -m paper_2502_08844_b300.build` or "
@@ -74,6 +74,7 @@ _lib.pg_step.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_int, C
 _lib.pg_debug_substep.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
 _lib.pg_step_host.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
 _lib.pg_step_vjp.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_int, C.c_int] + [C.c_void_p] * 7
+_lib.pg_batch_specialize.argtypes = [C.c_void_p]
 _lib.pg_step_vjp_noalloc.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_int, C.c_int] + [C.c_void_p] * 7
 for _n in EXPORTS:
     if _n not in ("pg_last_error", "pg_model_free", "pg_batch_free"):
@@ -158,3 +159,7 @@ def pg_step_vjp_noalloc(batch, ckpt: pg_state, ctrl_ptr, n_steps: int, n_substep
     _check(_lib.pg_step_vjp_noalloc(batch, C.byref(ckpt), ctrl_ptr, int(n_steps), int(n_substeps), g_qpos_ptr,
                                     g_qvel_ptr, adj_qpos_ptr, adj_qvel_ptr, g_ctrl_ptr, g_param_ptr, stream),
            "pg_step_vjp_noalloc")
+
+
+def pg_batch_specialize(batch) -> None:
+    _check(_lib.pg_batch_specialize(batch), "pg_batch_specialize")

@@ -20,6 +20,33 @@ LIB = os.path.join(HERE, "libpg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
+# headers compiled again at run time by pg_batch_specialize (NVRTC), embedded in the library
+EMBEDDED = [("pg.h", os.path.join(INCLUDE, "pg.h")), ("pg_internal.h", os.path.join(CSRC, "pg_internal.h")),
+            ("step_device.cuh", os.path.join(CSRC, "step_device.cuh")),
+            ("step_kernel_body.cuh", os.path.join(CSRC, "step_kernel_body.cuh"))]
+BUILD_DIR = os.path.join(HERE, "_build")
+EMBED_CPP = os.path.join(BUILD_DIR, "pg_embedded.cpp")
+
+
+def write_embedded() -> str:
+    """C++ source holding the embedded headers as raw string literals (regenerated every build)."""
+    os.makedirs(BUILD_DIR, exist_ok=True)
+    out = ["// generated by build.py from the kernel headers; do not edit", "namespace pg {",
+           "extern const int kEmbeddedCount = %d;" % len(EMBEDDED),
+           "extern const char* const kEmbeddedNames[] = {%s};" % ", ".join('"%s"' % n for n, _ in EMBEDDED),
+           "extern const char* const kEmbeddedTexts[] = {"]
+    for _, path in EMBEDDED:
+        text = open(path).read()
+        assert ")PGSRC\"" not in text
+        out.append('R"PGSRC(' + text + ')PGSRC",')
+    out += ["};", "}  // namespace pg", ""]
+    tmp = EMBED_CPP + ".%d.tmp" % os.getpid()
+    with open(tmp, "w") as f:
+        f.write("\n".join(out))
+    os.replace(tmp, EMBED_CPP)
+    return EMBED_CPP
+
+
 def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
 
@@ -34,7 +61,7 @@ def needs_build() -> bool:
 
 def nvcc_cmd(out: str, verbose: bool = False):
     cmd = ["nvcc", *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
-           "-o", out, *sources(), "-lcudart"]
+           "-o", out, *sources(), EMBED_CPP, "-lcudart", "-ldl"]
     if verbose:
         cmd[1:1] = ["-Xptxas", "-v"]
     return cmd
@@ -43,6 +70,7 @@ def nvcc_cmd(out: str, verbose: bool = False):
 def build(force: bool = False, verbose: bool = False) -> str:
     if force or needs_build():
         tmp = LIB + ".%d.tmp" % os.getpid()
+        write_embedded()
         subprocess.run(nvcc_cmd(tmp, verbose), check=True)
         os.replace(tmp, LIB)
     return LIB

@@ -88,6 +88,12 @@ class Batch:
         self.env_off = list(np.cumsum([0] + self.counts[:-1]))
         # rows of the per-environment parameter gradient of pg_step_vjp (masses | damping | kp)
         self.nparam_max = max(m.sizes.nparam for m in self.models)
+        self.specialized = False
+
+    def specialize(self) -> None:
+        """pg_batch_specialize: compile (NVRTC, cached) a step kernel specialised to the model."""
+        _capi.pg_batch_specialize(self.handle)
+        self.specialized = True
 
     def __del__(self):
         h = getattr(self, "handle", None)

@@ -75,6 +75,7 @@ void pg_batch_free(pg_batch* b) {
   if (b->d_tiles) cudaFree(b->d_tiles);
   if (b->d_ctrl_stage) cudaFree(b->d_ctrl_stage);
   if (b->d_vjp) cudaFree(b->d_vjp);
+  if (b->spec_lib) cudaLibraryUnload(b->spec_lib);
   delete b;
 }
 

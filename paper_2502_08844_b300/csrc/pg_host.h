@@ -34,6 +34,9 @@ struct pg_batch {
   std::vector<pg::Tile> tiles;
   std::vector<uint32_t> blob_host_adj;   // the same with the adjoint headers
   bool has_elliptic = false;             // a model uses the elliptic cone (selects the kernels)
+  // model-specialised step kernel compiled at run time (pg_batch_specialize), else NULL
+  cudaLibrary_t spec_lib = nullptr;
+  cudaKernel_t spec_kernel = nullptr;
   // staging buffer of the host-buffer path (allocated on its first use)
   float* d_ctrl_stage = nullptr;
   size_t ctrl_stage_floats = 0;
@@ -67,6 +70,7 @@ cudaError_t launch_step_tape(const pg_batch* b, const pg_state* s, const float* 
                         int tape_rows, cudaStream_t st);                                                         \
   cudaError_t debug(const pg_batch* b, const pg_state* s, const float* ctrl, int64_t env, float* out,            \
                     cudaStream_t st);                                                                            \
+  cudaError_t step_spec(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st);\
   }
 PG_DECLARE_STEP_KERNELS(pyramidal)
 PG_DECLARE_STEP_KERNELS(elliptic)

@@ -11,7 +11,10 @@
 // element each of them touches.  The host assigns every buffer an interval of the substep's
 // phases and packs buffers whose intervals do not overlap into the same space.
 #pragma once
+#ifndef __CUDACC_RTC__
 #include <stdint.h>
+#endif
+#include "pg.h"
 
 namespace pg {
 

@@ -1,0 +1,221 @@
+// Model-specialised step kernels, compiled at run time.
+//
+// Why: the library's compiled kernel reads the model at run time. That covers the header fields
+// and tables (kernel-parameter loads) and the structure-of-arrays stride of the workspace. About
+// 40 % of its instructions are this addressing arithmetic and table reads. Compiling the same
+// kernel body with the model's blob as a constant array turns all of it into immediates.
+//
+// How: pg_batch_specialize generates a small source that defines the blob (kSpecBlob) and
+// includes the kernel body headers, which are embedded in this library at build time. It
+// compiles that source with NVRTC (loaded with dlopen on first use) for sm_103a, loads the
+// cubin with cudaLibraryLoadData, and from then on pg_step launches that kernel for the batch.
+// The arithmetic is the same source in the same order, so results equal the generic kernel's.
+//
+// Cache: compiled cubins are kept per process and on disk, keyed by a hash of the generated
+// source and the NVRTC version. The disk cache is $PG_KERNEL_CACHE or
+// ~/.cache/paper_2502_08844_b300/kernels.
+#include <cuda_runtime.h>
+#include <dlfcn.h>
+#include <sys/stat.h>
+#include <unistd.h>
+
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "pg.h"
+#include "pg_host.h"
+#include "pg_internal.h"
+
+namespace pg {
+
+// the kernel sources embedded at build time (generated by build.py)
+extern const int kEmbeddedCount;
+extern const char* const kEmbeddedNames[];
+extern const char* const kEmbeddedTexts[];
+
+namespace {
+
+// ---- NVRTC, resolved at run time ----
+typedef int (*nvrtcCreateProgram_t)(void**, const char*, const char*, int, const char* const*, const char* const*);
+typedef int (*nvrtcCompileProgram_t)(void*, int, const char* const*);
+typedef int (*nvrtcGetSize_t)(void*, size_t*);
+typedef int (*nvrtcGetData_t)(void*, char*);
+typedef int (*nvrtcDestroyProgram_t)(void**);
+typedef int (*nvrtcVersion_t)(int*, int*);
+
+struct Nvrtc {
+  bool ok = false;
+  std::string why;
+  nvrtcCreateProgram_t create = nullptr;
+  nvrtcCompileProgram_t compile = nullptr;
+  nvrtcGetSize_t log_size = nullptr, cubin_size = nullptr;
+  nvrtcGetData_t log = nullptr, cubin = nullptr;
+  nvrtcDestroyProgram_t destroy = nullptr;
+  int major = 0, minor = 0;
+};
+
+std::mutex g_mutex;
+std::map<uint64_t, std::vector<char>> g_cubins;
+
+const Nvrtc& nvrtc() {
+  static Nvrtc n;
+  static bool tried = false;
+  if (tried) return n;
+  tried = true;
+  const char* names[] = {"libnvrtc.so.13", "/usr/local/cuda/lib64/libnvrtc.so.13", "libnvrtc.so"};
+  void* h = nullptr;
+  for (const char* nm : names)
+    if ((h = dlopen(nm, RTLD_NOW | RTLD_LOCAL))) break;
+  if (!h) { n.why = "NVRTC (libnvrtc.so.13) not found"; return n; }
+  n.create = (nvrtcCreateProgram_t)dlsym(h, "nvrtcCreateProgram");
+  n.compile = (nvrtcCompileProgram_t)dlsym(h, "nvrtcCompileProgram");
+  n.log_size = (nvrtcGetSize_t)dlsym(h, "nvrtcGetProgramLogSize");
+  n.log = (nvrtcGetData_t)dlsym(h, "nvrtcGetProgramLog");
+  n.cubin_size = (nvrtcGetSize_t)dlsym(h, "nvrtcGetCUBINSize");
+  n.cubin = (nvrtcGetData_t)dlsym(h, "nvrtcGetCUBIN");
+  n.destroy = (nvrtcDestroyProgram_t)dlsym(h, "nvrtcDestroyProgram");
+  nvrtcVersion_t ver = (nvrtcVersion_t)dlsym(h, "nvrtcVersion");
+  if (!n.create || !n.compile || !n.log_size || !n.log || !n.cubin_size || !n.cubin || !n.destroy || !ver) {
+    n.why = "NVRTC lacks an expected entry point";
+    return n;
+  }
+  ver(&n.major, &n.minor);
+  n.ok = true;
+  return n;
+}
+
+uint64_t fnv1a(const std::string& s, uint64_t h = 1469598103934665603ull) {
+  for (unsigned char ch : s) { h ^= ch; h *= 1099511628211ull; }
+  return h;
+}
+
+std::string cache_dir() {
+  if (const char* d = getenv("PG_KERNEL_CACHE")) return d;
+  const char* home = getenv("HOME");
+  return std::string(home ? home : "/tmp") + "/.cache/paper_2502_08844_b300/kernels";
+}
+
+void mkdirs(const std::string& path) {
+  std::string cur;
+  for (size_t i = 0; i < path.size(); i++) {
+    cur += path[i];
+    if (path[i] == '/' && cur.size() > 1) mkdir(cur.c_str(), 0755);
+  }
+  mkdir(path.c_str(), 0755);
+}
+
+bool read_file(const std::string& p, std::vector<char>& out) {
+  FILE* f = fopen(p.c_str(), "rb");
+  if (!f) return false;
+  fseek(f, 0, SEEK_END);
+  long n = ftell(f);
+  fseek(f, 0, SEEK_SET);
+  out.resize(n > 0 ? (size_t)n : 0);
+  bool ok = n > 0 && fread(out.data(), 1, (size_t)n, f) == (size_t)n;
+  fclose(f);
+  return ok;
+}
+
+void write_file(const std::string& p, const std::vector<char>& data) {
+  const std::string tmp = p + ".tmp" + std::to_string((long)getpid());
+  FILE* f = fopen(tmp.c_str(), "wb");
+  if (!f) return;
+  const bool ok = fwrite(data.data(), 1, data.size(), f) == data.size();
+  fclose(f);
+  if (ok) rename(tmp.c_str(), p.c_str());
+  else remove(tmp.c_str());
+}
+
+// the generated translation unit: the model blob as a constant array, then the kernel body
+std::string spec_source(const pg_model* m) {
+  std::string s;
+  s += "#define PG_WITH_ELLIPTIC " + std::to_string(m->hdr.cone == PG_CONE_ELLIPTIC ? 1 : 0) + "\n";
+  s += "#define PG_SPEC 1\n#include \"pg_internal.h\"\nnamespace pg {\n";
+  s += "constexpr int kSpecSoa = " + std::to_string(m->hdr.soa) + ";\n";
+  s += "__device__ const uint32_t kSpecBlob[" + std::to_string(m->blob.size()) + "] __attribute__((aligned(16))) = {";
+  for (size_t i = 0; i < m->blob.size(); i++) {
+    if (i % 16 == 0) s += "\n";
+    s += std::to_string(m->blob[i]) + "u,";
+  }
+  s += "\n};\n}  // namespace pg\n#include \"step_kernel_body.cuh\"\n";
+  s += "extern \"C\" __global__ void __launch_bounds__(" + std::to_string(kMaxEnvsPerCta) +
+       ") pg_step_spec(const __grid_constant__ pg::StepArgs A) { pg::step_body<false, false>(A); }\n";
+  return s;
+}
+
+int compile_cubin(const pg_model* m, std::vector<char>& cubin) {
+  const Nvrtc& n = nvrtc();
+  if (!n.ok) return set_error(PG_EUNSUPPORTED, "pg_batch_specialize: " + n.why);
+  const std::string src = spec_source(m);
+  std::string key_src = src + "|nvrtc " + std::to_string(n.major) + "." + std::to_string(n.minor) + "|sm_103a";
+  for (int i = 0; i < kEmbeddedCount; i++) key_src += kEmbeddedTexts[i];
+  const uint64_t key = fnv1a(key_src);
+  {
+    std::lock_guard<std::mutex> lock(g_mutex);
+    auto it = g_cubins.find(key);
+    if (it != g_cubins.end()) { cubin = it->second; return PG_OK; }
+  }
+  char name[32];
+  snprintf(name, sizeof(name), "%016llx.cubin", (unsigned long long)key);
+  const std::string dir = cache_dir(), path = dir + "/" + name;
+  if (!read_file(path, cubin)) {
+    void* prog = nullptr;
+    if (n.create(&prog, src.c_str(), "pg_step_spec.cu", kEmbeddedCount, kEmbeddedTexts, kEmbeddedNames) != 0)
+      return set_error(PG_EUNSUPPORTED, "pg_batch_specialize: nvrtcCreateProgram failed");
+    const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo"};
+    const int rc = n.compile(prog, 3, opts);
+    if (rc != 0) {
+      size_t ls = 0;
+      n.log_size(prog, &ls);
+      std::string log(ls, '\0');
+      if (ls) n.log(prog, &log[0]);
+      n.destroy(&prog);
+      return set_error(PG_EUNSUPPORTED, "pg_batch_specialize: NVRTC compilation failed: " + log.substr(0, 2000));
+    }
+    size_t cs = 0;
+    n.cubin_size(prog, &cs);
+    cubin.assign(cs, 0);
+    n.cubin(prog, cubin.data());
+    n.destroy(&prog);
+    mkdirs(dir);
+    write_file(path, cubin);
+  }
+  std::lock_guard<std::mutex> lock(g_mutex);
+  g_cubins[key] = cubin;
+  return PG_OK;
+}
+
+}  // namespace
+}  // namespace pg
+
+using namespace pg;
+
+extern "C" int pg_batch_specialize(pg_batch* b) {
+  if (!b) return set_error(PG_EINVAL, "batch is NULL");
+  if (b->models.size() != 1) return set_error(PG_EUNSUPPORTED, "pg_batch_specialize: only single-model batches");
+  if (b->spec_kernel) return PG_OK;
+  std::vector<char> cubin;
+  int rc = compile_cubin(b->models[0], cubin);
+  if (rc != PG_OK) return rc;
+  cudaLibrary_t lib = nullptr;
+  cudaError_t e = cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+  if (e != cudaSuccess) return set_error(PG_ECUDA, std::string("cudaLibraryLoadData: ") + cudaGetErrorString(e));
+  cudaKernel_t k = nullptr;
+  e = cudaLibraryGetKernel(&k, lib, "pg_step_spec");
+  int dev = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess)
+    e = cudaKernelSetAttributeForDevice(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem_bytes, dev);
+  if (e != cudaSuccess) {
+    cudaLibraryUnload(lib);
+    return set_error(PG_ECUDA, std::string("specialised kernel set-up: ") + cudaGetErrorString(e));
+  }
+  b->spec_lib = lib;
+  b->spec_kernel = k;
+  return PG_OK;
+}

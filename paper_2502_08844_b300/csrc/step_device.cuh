@@ -9,9 +9,11 @@
 #ifndef PG_WITH_ELLIPTIC
 #error "define PG_WITH_ELLIPTIC (0 or 1) before including step_device.cuh"
 #endif
+#ifndef __CUDACC_RTC__
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#endif
 
 #include "pg.h"
 #include "pg_internal.h"
@@ -1175,7 +1177,7 @@ __device__ float line_search(const Ctx& c) {
   float alpha = 0.f;
   for (int step = 0; step <= R; step++) {
     const float root = qt > 0.f ? -lt / qt : alpha;
-    float next = INFINITY;
+    float next = __int_as_float(0x7f800000);   // +inf
     for (int r = 0; r < R; r++) {
       const float jp = W(Jp, r);
       if (!(W(rD, r) > 0.f) || jp == 0.f) continue;

@@ -1,0 +1,41 @@
+"""pg_batch_specialize: the step kernel compiled at run time (NVRTC) with the model as constants
+runs the same source as the generic kernel.  With the model known the compiler may fold known
+zeros and forward stored constants, which can regroup an FMA, so trajectories agree to rounding
+(1e-6 of their scale over a few steps; often bitwise).  Mixed batches are refused."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2502_08844_b300 import _capi, core
+from paper_2502_08844_b300 import workloads as W
+from tests.gpu_helpers import GpuRun
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("mname,cfg,n,T", [("quadruped", 1, 300, 6), ("cartpole", 0, 77, 6), ("hand_elliptic", 2, 40, 3),
+                                          ("humanoid", 3, 50, 3)])
+def test_specialised_kernel_matches_generic(mname, cfg, n, T):
+    m = W.model(mname)
+    q0, v0 = W.initial_state(m, cfg, n)
+    U = W.actions(m, cfg, n, 0, T)
+    out = []
+    for spec in (False, True):
+        run = GpuRun(m, n)
+        if spec:
+            run.batch.specialize()
+        run.set_state(q0, v0)
+        tq, tv = run.rollout(U, m.n_substeps, keep=True)
+        out.append((tq, tv, run.status()))
+    for k in (0, 1):
+        a, b = out[0][k], out[1][k]
+        assert np.abs(a - b).max() <= 1e-6 * max(np.abs(a).max(), 1.0), (k, np.abs(a - b).max())
+    assert np.array_equal(out[0][2], out[1][2])
+
+
+def test_specialise_refuses_mixed_batches():
+    parts = [(core.CompiledModel(W.cartpole()), 4), (core.CompiledModel(W.quadruped()), 4)]
+    batch = core.Batch(parts)
+    with pytest.raises(_capi.PgError) as ei:
+        batch.specialize()
+    assert ei.value.code == _capi.PG_EUNSUPPORTED
