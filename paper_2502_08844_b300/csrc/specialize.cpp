@@ -137,7 +137,9 @@ std::string spec_source(const pg_model* m) {
   s += "#define PG_WITH_ELLIPTIC " + std::to_string(m->hdr.cone == PG_CONE_ELLIPTIC ? 1 : 0) + "\n";
   s += "#define PG_SPEC 1\n#include \"pg_internal.h\"\nnamespace pg {\n";
   s += "constexpr int kSpecSoa = " + std::to_string(m->hdr.soa) + ";\n";
-  s += "__device__ const uint32_t kSpecBlob[" + std::to_string(m->blob.size()) + "] __attribute__((aligned(16))) = {";
+  // in the constant bank: reads at compile-time indices fold away, the rest are uniform
+  // constant-cache loads (every thread of the kernel steps the same model)
+  s += "__constant__ const uint32_t kSpecBlob[" + std::to_string(m->blob.size()) + "] __attribute__((aligned(16))) = {";
   for (size_t i = 0; i < m->blob.size(); i++) {
     if (i % 16 == 0) s += "\n";
     s += std::to_string(m->blob[i]) + "u,";

@@ -18,6 +18,15 @@
 #include "pg.h"
 #include "pg_internal.h"
 
+// PG_SPEC_UNROLL: in a model-specialised build (PG_SPEC, trip counts and tables are constants)
+// the tree factorisation, solve and product loops are unrolled completely, so every workspace
+// address is a constant and the compiler schedules the loads freely; elsewhere it is empty.
+#ifdef PG_SPEC
+#define PG_SPEC_UNROLL _Pragma("unroll")
+#else
+#define PG_SPEC_UNROLL
+#endif
+
 namespace pg {
 namespace {
 
@@ -538,18 +547,35 @@ __device__ void crba(const Ctx& c) {
 
 // packed tree-sparse factorisation in place: A = L^T D L, L unit lower triangular on the
 // ancestor pattern (no fill-in); row k ends as (D_k, L_k,parent(k), ...)
+// (The inner loops below move 4 entries at a time: all loads of a chunk first, then the
+// arithmetic, then the stores.  Row segments never overlap, so this is the same arithmetic in the
+// same order per entry; it lets the shared-memory loads of a chunk overlap instead of waiting
+// behind the previous store, which the compiler cannot prove independent.)
 __device__ void ldl_factor(const Ctx& c, int A) {
   const ModelHdr& h = c.h;
-  float* a = c.w + A * c.S;
+  const int S = c.S;
+  float* a = c.w + A * S;
+  PG_SPEC_UNROLL
   for (int k = h.nv - 1; k >= 0; k--) {
     const int r0 = MI(dof_rowadr, k), dk = MI(dof_depth, k);
-    const float dinv = 1.f / a[r0 * c.S];
+    const float dinv = __frcp_rn(a[r0 * S]);   // = 1 / pivot, correctly rounded
+    PG_SPEC_UNROLL
     for (int t = 1; t <= dk; t++) {
       const int ri = MI(dof_rowadr, MI(Lcol, r0 + t));
-      const float lt = a[(r0 + t) * c.S] * dinv;
-      for (int s = t; s <= dk; s++) a[(ri + s - t) * c.S] -= lt * a[(r0 + s) * c.S];
+      const float lt = a[(r0 + t) * S] * dinv;
+      float* dst = a + (ri - t) * S;   // entry s of row k updates entry s - t of row i
+      int s = t;
+      for (; s + 3 <= dk; s += 4) {
+        const float x0 = a[(r0 + s) * S], x1 = a[(r0 + s + 1) * S], x2 = a[(r0 + s + 2) * S], x3 = a[(r0 + s + 3) * S];
+        const float y0 = dst[s * S], y1 = dst[(s + 1) * S], y2 = dst[(s + 2) * S], y3 = dst[(s + 3) * S];
+        dst[s * S] = y0 - lt * x0;
+        dst[(s + 1) * S] = y1 - lt * x1;
+        dst[(s + 2) * S] = y2 - lt * x2;
+        dst[(s + 3) * S] = y3 - lt * x3;
+      }
+      for (; s <= dk; s++) dst[s * S] -= lt * a[(r0 + s) * S];
     }
-    for (int t = 1; t <= dk; t++) a[(r0 + t) * c.S] *= dinv;
+    for (int t = 1; t <= dk; t++) a[(r0 + t) * S] *= dinv;
   }
 }
 
@@ -558,17 +584,40 @@ __device__ void ldl_solve(const Ctx& c, int A, int X) {
   const ModelHdr& h = c.h;
   const float* a = c.w + A * c.S;
   float* x = c.w + X * c.S;
+  const int S = c.S;
+  PG_SPEC_UNROLL
   for (int k = h.nv - 1; k >= 0; k--) {
     const int r0 = MI(dof_rowadr, k), dk = MI(dof_depth, k);
-    const float xk = x[k * c.S];
-    for (int t = 1; t <= dk; t++) x[MI(Lcol, r0 + t) * c.S] -= a[(r0 + t) * c.S] * xk;
+    const float xk = x[k * S];
+    int t = 1;
+    for (; t + 3 <= dk; t += 4) {
+      const int i0 = MI(Lcol, r0 + t), i1 = MI(Lcol, r0 + t + 1), i2 = MI(Lcol, r0 + t + 2), i3 = MI(Lcol, r0 + t + 3);
+      const float a0 = a[(r0 + t) * S], a1 = a[(r0 + t + 1) * S], a2 = a[(r0 + t + 2) * S], a3 = a[(r0 + t + 3) * S];
+      const float y0 = x[i0 * S], y1 = x[i1 * S], y2 = x[i2 * S], y3 = x[i3 * S];
+      x[i0 * S] = y0 - a0 * xk;
+      x[i1 * S] = y1 - a1 * xk;
+      x[i2 * S] = y2 - a2 * xk;
+      x[i3 * S] = y3 - a3 * xk;
+    }
+    for (; t <= dk; t++) x[MI(Lcol, r0 + t) * S] -= a[(r0 + t) * S] * xk;
   }
-  for (int k = 0; k < h.nv; k++) x[k * c.S] /= a[MI(dof_rowadr, k) * c.S];
+  for (int k = 0; k < h.nv; k++) x[k * S] /= a[MI(dof_rowadr, k) * S];
+  PG_SPEC_UNROLL
   for (int k = 0; k < h.nv; k++) {
     const int r0 = MI(dof_rowadr, k), dk = MI(dof_depth, k);
-    float s = x[k * c.S];
-    for (int t = 1; t <= dk; t++) s -= a[(r0 + t) * c.S] * x[MI(Lcol, r0 + t) * c.S];
-    x[k * c.S] = s;
+    float s = x[k * S];
+    int t = 1;
+    for (; t + 3 <= dk; t += 4) {
+      const float a0 = a[(r0 + t) * S], a1 = a[(r0 + t + 1) * S], a2 = a[(r0 + t + 2) * S], a3 = a[(r0 + t + 3) * S];
+      const float y0 = x[MI(Lcol, r0 + t) * S], y1 = x[MI(Lcol, r0 + t + 1) * S], y2 = x[MI(Lcol, r0 + t + 2) * S],
+                  y3 = x[MI(Lcol, r0 + t + 3) * S];
+      s -= a0 * y0;
+      s -= a1 * y1;
+      s -= a2 * y2;
+      s -= a3 * y3;
+    }
+    for (; t <= dk; t++) s -= a[(r0 + t) * S] * x[MI(Lcol, r0 + t) * S];
+    x[k * S] = s;
   }
 }
 
@@ -578,18 +627,35 @@ __device__ void sym_mul(const Ctx& c, int Mo, int X, int Y) {
   const float* m = c.w + Mo * c.S;
   const float* x = c.w + X * c.S;
   float* y = c.w + Y * c.S;
-  for (int j = 0; j < h.nv; j++) y[j * c.S] = 0.f;
+  const int S = c.S;
+  for (int j = 0; j < h.nv; j++) y[j * S] = 0.f;
+  PG_SPEC_UNROLL
   for (int j = 0; j < h.nv; j++) {
     const int r0 = MI(dof_rowadr, j), dj = MI(dof_depth, j);
-    const float xj = x[j * c.S];
-    float yj = m[r0 * c.S] * xj;
-    for (int t = 1; t <= dj; t++) {
-      const int i = MI(Lcol, r0 + t);
-      const float mji = m[(r0 + t) * c.S];
-      yj = fmaf(mji, x[i * c.S], yj);
-      y[i * c.S] = fmaf(mji, xj, y[i * c.S]);
+    const float xj = x[j * S];
+    float yj = m[r0 * S] * xj;
+    int t = 1;
+    for (; t + 3 <= dj; t += 4) {   // chunks of 4: loads first (see ldl_factor)
+      const int i0 = MI(Lcol, r0 + t), i1 = MI(Lcol, r0 + t + 1), i2 = MI(Lcol, r0 + t + 2), i3 = MI(Lcol, r0 + t + 3);
+      const float m0 = m[(r0 + t) * S], m1 = m[(r0 + t + 1) * S], m2 = m[(r0 + t + 2) * S], m3 = m[(r0 + t + 3) * S];
+      const float x0 = x[i0 * S], x1 = x[i1 * S], x2 = x[i2 * S], x3 = x[i3 * S];
+      const float y0 = y[i0 * S], y1 = y[i1 * S], y2 = y[i2 * S], y3 = y[i3 * S];
+      yj = fmaf(m0, x0, yj);
+      yj = fmaf(m1, x1, yj);
+      yj = fmaf(m2, x2, yj);
+      yj = fmaf(m3, x3, yj);
+      y[i0 * S] = fmaf(m0, xj, y0);
+      y[i1 * S] = fmaf(m1, xj, y1);
+      y[i2 * S] = fmaf(m2, xj, y2);
+      y[i3 * S] = fmaf(m3, xj, y3);
     }
-    y[j * c.S] += yj;
+    for (; t <= dj; t++) {
+      const int i = MI(Lcol, r0 + t);
+      const float mji = m[(r0 + t) * S];
+      yj = fmaf(mji, x[i * S], yj);
+      y[i * S] = fmaf(mji, xj, y[i * S]);
+    }
+    y[j * S] += yj;
   }
 }
 
@@ -1092,7 +1158,8 @@ __device__ bool newton_direction(const Ctx& c, const unsigned act[4], bool& zero
     if (Sn == 0.f) continue;
     const float* J = c.w + (h.w_J + 3 * NC * k) * c.S;
     const float* gc = c.w + (h.w_gcol + NC * k) * c.S;
-    for (int a = 0; a < NC; a++) {
+    const int nck = MI(pair_ncol, con_pair(c, k));   // the pair's real columns (the rest is zero padding)
+    for (int a = 0; a < nck; a++) {
       const int da = __float_as_int(gc[a * c.S]);
       const float na = J[a * c.S], ta = J[(NC + a) * c.S], ua = J[(2 * NC + a) * c.S];
       W(g, da) += gn * na + g1 * ta + g2 * ua;
@@ -1100,11 +1167,29 @@ __device__ bool newton_direction(const Ctx& c, const unsigned act[4], bool& zero
       const float ht = c1 * na + s1 * ta + c12 * ua;
       const float hu = c2 * na + c12 * ta + s2 * ua;
       const int ra = MI(dof_rowadr, da), depa = MI(dof_depth, da);
-      for (int b = a; b < NC; b++) {
-        const int db = __float_as_int(gc[b * c.S]);
-        const float v = hn * J[b * c.S] + ht * J[(NC + b) * c.S] + hu * J[(2 * NC + b) * c.S];
-        if (tree) W(L, ra + depa - MI(dof_depth, db)) += v;
-        else W(H, (da > db ? da * nv + db : db * nv + da)) += v;
+      if (tree) {
+        // the real columns are distinct dofs of one chain: distinct entries of row da, updated two
+        // at a time with both loads first
+        int b = a;
+        for (; b + 1 < nck; b += 2) {
+          const int db0 = __float_as_int(gc[b * c.S]), db1 = __float_as_int(gc[(b + 1) * c.S]);
+          const float v0 = hn * J[b * c.S] + ht * J[(NC + b) * c.S] + hu * J[(2 * NC + b) * c.S];
+          const float v1 = hn * J[(b + 1) * c.S] + ht * J[(NC + b + 1) * c.S] + hu * J[(2 * NC + b + 1) * c.S];
+          const int o0 = ra + depa - MI(dof_depth, db0), o1 = ra + depa - MI(dof_depth, db1);
+          const float l0 = W(L, o0), l1 = W(L, o1);
+          W(L, o0) = l0 + v0;
+          W(L, o1) = l1 + v1;
+        }
+        for (; b < nck; b++) {
+          const int db = __float_as_int(gc[b * c.S]);
+          W(L, ra + depa - MI(dof_depth, db)) += hn * J[b * c.S] + ht * J[(NC + b) * c.S] + hu * J[(2 * NC + b) * c.S];
+        }
+      } else {
+        for (int b = a; b < nck; b++) {
+          const int db = __float_as_int(gc[b * c.S]);
+          const float v = hn * J[b * c.S] + ht * J[(NC + b) * c.S] + hu * J[(2 * NC + b) * c.S];
+          W(H, (da > db ? da * nv + db : db * nv + da)) += v;
+        }
       }
     }
   }
