@@ -303,6 +303,8 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
     h.bref = (float)(2.0 / (dmax * tc));
   }
   for (int k = 0; k < 5; k++) h.solimp[k] = d->solimp[k];
+  h.imp_mid_inv = (float)(1.0 / std::pow((double)d->solimp[3], (double)d->solimp[4] - 1.0));
+  h.imp_tail_inv = (float)(1.0 / std::pow(1.0 - (double)d->solimp[3], (double)d->solimp[4] - 1.0));
   h.margin = d->margin;
 
   Blob B;
@@ -347,7 +349,7 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
       {&h.w_xpos, 3 * nbody, 1, 7}, {&h.w_xquat, 4 * nbody, 1, 7}, {&h.w_cdof, 6 * nv, 1, 7},
       {&h.w_cinert, 10 * nbody, 1, 3}, {&h.w_cvel, 6 * nbody, 2, 2}, {&h.w_cacc, 6 * nbody, 2, 2},
       {&h.w_cfrc, 6 * nbody, 2, 2}, {&h.w_bias, nv, 2, 5}, {&h.w_M, nL, 3, 9}, {&h.w_L, nL, 4, 9},
-      {&h.w_a0, nv, 5, 9}, {&h.w_con, kConFloats * C, 6, 10}, {&h.w_J, 3 * ncol_max * C, 7, 10},
+      {&h.w_a0, nv, 5, 9}, {&h.w_Dinv, nv, 5, 8}, {&h.w_con, kConFloats * C, 6, 10}, {&h.w_J, 3 * ncol_max * C, 7, 10},
       {&h.w_gcol, ncol_max * C, 7, 10}, {&h.w_lsgn, std::max((int)limit_jnt.size(), 1), 7, 10},
       {&h.w_gmu, C, 8, 10}, {&h.w_gcond, C, 8, 10},
       {&h.w_z, 3 * nv, 8, 8}, {&h.w_rr, R, 8, 10}, {&h.w_rv, R, 8, 10},

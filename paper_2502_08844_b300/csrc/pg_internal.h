@@ -34,6 +34,7 @@ struct ModelHdr {
   int cap, cone, tree_hessian, ncol_max, soa, substeps;
   // options (float32)
   float h, grav[3], kref, bref, solimp[5], margin;
+  float imp_mid_inv, imp_tail_inv;   // 1 / mid^(p-1) and 1 / (1 - mid)^(p-1) of the impedance
   // table offsets (words from the blob start)
   int o_body_parent, o_body_root, o_body_jntadr, o_body_jntnum, o_body_pos, o_body_quat, o_body_mass,
       o_body_ipos, o_body_inertia, o_root_freeadr;
@@ -51,7 +52,7 @@ struct ModelHdr {
   int w_xpos, w_xquat, w_cdof, w_cinert, w_cvel, w_cacc, w_cfrc, w_bias;
   int w_M, w_L, w_a0, w_con, w_J, w_z;
   int w_gcol, w_gmu, w_gcond, w_lsgn, w_rr, w_rv, w_Ahat, w_imp, w_aref, w_rD, w_jar, w_Jp;
-  int w_a, w_g, w_p, w_t, w_H;
+  int w_a, w_g, w_p, w_t, w_H, w_Dinv;
   // adjoint workspace (the reverse sweep): every forward buffer above gets its own space (no
   // sharing between phases), plus the own body inertias `ci0` (CRBA overwrites w_cinert with
   // composites), the Hessian factor `HL` and the adjoint buffers b_*.  Valid only in the adjoint

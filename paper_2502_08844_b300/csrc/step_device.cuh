@@ -682,6 +682,7 @@ __device__ void smooth_acc(const Ctx& c, float* dbg) {
   for (int k = 0; k < h.nL; k++) W(L, k) = W(M, k);
   ldl_factor(c, h.w_L);
   ldl_solve(c, h.w_L, h.w_a0);
+  for (int k = 0; k < h.nv; k++) W(Dinv, k) = 1.f / W(L, MI(dof_rowadr, k));   // for the row parameters
 }
 // ---------------------------------------------------------------------------------------
 // collision over the static pair list; active contacts (dist < margin) are kept in slot order
@@ -940,24 +941,32 @@ __device__ void rows_dot(const Ctx& c, int X, int OUT) {
 }
 
 // impedance d(r) from solimp = (d0, dwidth, width, mid, power)
+// (x^p by a multiplication for the usual power 2; the mid-point powers come from the header)
+__device__ __forceinline__ float ipow(float x, float p) { return p == 2.f ? x * x : powf(x, p); }
 __device__ __forceinline__ float impedance(const ModelHdr& h, float pos) {
   const float d0 = h.solimp[0], d1 = h.solimp[1], width = h.solimp[2], mid = h.solimp[3], pw = h.solimp[4];
   const float x = fminf(fabsf(pos) / width, 1.f);
   float y;
   if (x >= 1.f) y = 1.f;
-  else if (x <= mid) y = powf(x, pw) / powf(mid, pw - 1.f);
-  else y = 1.f - powf(1.f - x, pw) / powf(1.f - mid, pw - 1.f);
+  else if (x <= mid) y = ipow(x, pw) * h.imp_mid_inv;
+  else y = 1.f - ipow(1.f - x, pw) * h.imp_tail_inv;
   return d0 + y * (d1 - d0);
 }
 
-__device__ __forceinline__ void set_row(const Ctx& c, int r, bool valid, float pos, float A) {
+// row r from its position, impedance d and Ahat; a row that does not exist gets D = 0
+__device__ __forceinline__ void set_row(const Ctx& c, int r, bool valid, float pos, float d, float A) {
   const ModelHdr& h = c.h;
-  const float d = impedance(h, pos), vel = W(rv, r);
   W(rr, r) = pos;
   W(Ahat, r) = A;
+  if (!valid) {
+    W(imp, r) = 0.f;
+    W(aref, r) = 0.f;
+    W(rD, r) = 0.f;
+    return;
+  }
   W(imp, r) = d;
-  W(aref, r) = -h.bref * vel - h.kref * d * pos;
-  W(rD, r) = valid ? d / ((1.f - d) * A) : 0.f;
+  W(aref, r) = -h.bref * W(rv, r) - h.kref * d * pos;
+  W(rD, r) = d / ((1.f - d) * A);
 }
 
 // z <- L^-T z along the chain that starts at dof c0 (z is zero off that chain), or over all dofs
@@ -1002,47 +1011,55 @@ __device__ void row_params(const Ctx& c, int nc) {
     const bool pyr = W(gcond, k) == 3.f;
     const float* J = c.w + (h.w_J + 3 * NC * k) * c.S;
     const float* gc = c.w + (h.w_gcol + NC * k) * c.S;
-    float Ann = 1.f, An1 = 0.f, An2 = 0.f, A11 = 1.f, A22 = 1.f;
+    float Ann = 1.f, An1 = 0.f, An2 = 0.f, A11 = 1.f, A22 = 1.f, d = 0.f;
     if (valid) {
+      d = impedance(h, dist);   // one impedance for all rows of the contact
       const int c0 = __float_as_int(gc[0]);
-      for (int s = 0; s < 3; s++) {
+      const int ns = pyr && !(PG_WITH_ELLIPTIC && c.h.cone == PG_CONE_ELLIPTIC) ? 3 : 1;   // pyramids need t1, t2
+      for (int s = 0; s < ns; s++) {
         float* z = c.w + (h.w_z + s * nv) * c.S;
         for (int i = 0; i < nv; i++) z[i * c.S] = 0.f;
         for (int a = 0; a < NC; a++) z[__float_as_int(gc[a * c.S]) * c.S] += J[(s * NC + a) * c.S];
         ltsolve_chain(c, z, c0);
       }
       Ann = An1 = An2 = A11 = A22 = 0.f;
-      for (int i = 0; i < nv; i++) {
-        const float dinv = 1.f / L[MI(dof_rowadr, i) * c.S];
-        const float zn = W(z, i), z1 = W(z, nv + i), z2 = W(z, 2 * nv + i);
+      // z is supported on the pair's chain (its columns) when pairs lie on single chains
+      const int nsum = h.tree_hessian ? MI(pair_ncol, con_pair(c, k)) : nv;
+      for (int q = 0; q < nsum; q++) {
+        const int i = h.tree_hessian ? __float_as_int(gc[q * c.S]) : q;
+        const float dinv = W(Dinv, i);
+        const float zn = W(z, i);
         Ann = fmaf(zn * zn, dinv, Ann);
-        An1 = fmaf(zn * z1, dinv, An1);
-        An2 = fmaf(zn * z2, dinv, An2);
-        A11 = fmaf(z1 * z1, dinv, A11);
-        A22 = fmaf(z2 * z2, dinv, A22);
+        if (ns == 3) {
+          const float z1 = W(z, nv + i), z2 = W(z, 2 * nv + i);
+          An1 = fmaf(zn * z1, dinv, An1);
+          An2 = fmaf(zn * z2, dinv, An2);
+          A11 = fmaf(z1 * z1, dinv, A11);
+          A22 = fmaf(z2 * z2, dinv, A22);
+        }
       }
     }
     if (pyr && PG_WITH_ELLIPTIC && c.h.cone == PG_CONE_ELLIPTIC) {
       // normal row: impedance from the depth; the tangent rows share its impedance, Ahat and D
       // (impratio 1) at zero position, so their reference acceleration is -b v
-      set_row(c, 4 * k + 0, valid, dist, Ann);
+      set_row(c, 4 * k + 0, valid, dist, d, Ann);
       for (int e = 1; e < 3; e++) {
         const int r = 4 * k + e;
         W(rr, r) = 0.f;
         W(Ahat, r) = W(Ahat, 4 * k);
         W(imp, r) = W(imp, 4 * k);
-        W(aref, r) = -h.bref * W(rv, r);
+        W(aref, r) = valid ? -h.bref * W(rv, r) : 0.f;
         W(rD, r) = W(rD, 4 * k);
       }
-      set_row(c, 4 * k + 3, false, dist, 1.f);
+      set_row(c, 4 * k + 3, false, dist, d, 1.f);
     } else if (pyr) {
-      set_row(c, 4 * k + 0, valid, dist, Ann + 2.f * mu * An1 + mu * mu * A11);
-      set_row(c, 4 * k + 1, valid, dist, Ann - 2.f * mu * An1 + mu * mu * A11);
-      set_row(c, 4 * k + 2, valid, dist, Ann + 2.f * mu * An2 + mu * mu * A22);
-      set_row(c, 4 * k + 3, valid, dist, Ann - 2.f * mu * An2 + mu * mu * A22);
+      set_row(c, 4 * k + 0, valid, dist, d, Ann + 2.f * mu * An1 + mu * mu * A11);
+      set_row(c, 4 * k + 1, valid, dist, d, Ann - 2.f * mu * An1 + mu * mu * A11);
+      set_row(c, 4 * k + 2, valid, dist, d, Ann + 2.f * mu * An2 + mu * mu * A22);
+      set_row(c, 4 * k + 3, valid, dist, d, Ann - 2.f * mu * An2 + mu * mu * A22);
     } else {
-      set_row(c, 4 * k + 0, valid, dist, Ann);
-      for (int e = 1; e < 4; e++) set_row(c, 4 * k + e, false, dist, 1.f);
+      set_row(c, 4 * k + 0, valid, dist, d, Ann);
+      for (int e = 1; e < 4; e++) set_row(c, 4 * k + e, false, dist, d, 1.f);
     }
   }
   for (int li = 0; li < h.nlimited; li++) {
@@ -1063,10 +1080,10 @@ __device__ void row_params(const Ctx& c, int nc) {
         const float zk = z[k * c.S];
         const int r0 = MI(dof_rowadr, k), dk = MI(dof_depth, k);
         for (int s = 1; s <= dk; s++) z[MI(Lcol, r0 + s) * c.S] -= L[(r0 + s) * c.S] * zk;
-        A = fmaf(zk * zk, 1.f / L[r0 * c.S], A);
+        A = fmaf(zk * zk, W(Dinv, k), A);
       }
     }
-    set_row(c, 4 * MC + li, sgn != 0.f, pos, A);
+    set_row(c, 4 * MC + li, sgn != 0.f, pos, sgn != 0.f ? impedance(h, pos) : 0.f, A);
   }
 }
 
