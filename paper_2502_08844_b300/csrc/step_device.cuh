@@ -991,6 +991,32 @@ __device__ __forceinline__ void ltsolve_chain(const Ctx& c, float* z, int c0) {
   }
 }
 
+// z_s <- L^-T z_s for the ns (1 or 3) vectors of one contact along the chain that starts at dof c0,
+// all three in the same pass (three independent update chains; the chain's indices and L entries
+// are loaded once)
+__device__ __forceinline__ void ltsolve_chain3(const Ctx& c, float* z0, float* z1, float* z2, int ns, int c0) {
+  const ModelHdr& h = c.h;
+  const int S = c.S;
+  const float* L = c.w + h.w_L * S;
+  const int rc = MI(dof_rowadr, c0), n = MI(dof_depth, c0);
+  for (int t = 0; t <= n; t++) {
+    const int k = MI(Lcol, rc + t);
+    const float a0 = z0[k * S], a1 = ns == 3 ? z1[k * S] : 0.f, a2 = ns == 3 ? z2[k * S] : 0.f;
+    const int r0 = MI(dof_rowadr, k), dk = MI(dof_depth, k);
+    for (int s = 1; s <= dk; s++) {
+      const int i = MI(Lcol, r0 + s);
+      const float l = L[(r0 + s) * S];
+      const float y0 = z0[i * S];
+      if (ns == 3) {
+        const float y1 = z1[i * S], y2 = z2[i * S];
+        z1[i * S] = y1 - l * a1;
+        z2[i * S] = y2 - l * a2;
+      }
+      z0[i * S] = y0 - l * a0;
+    }
+  }
+}
+
 // per row: position, velocity, exact Ahat = (J M^-1 J^T)_rr = sum_k z_k z_k / D_k with
 // z = L^-T J_r^T (for a pyramid from the n / t1 / t2 solves: Ahat = A_nn +- 2 mu A_nk + mu^2 A_kk),
 // impedance, aref = -b v - k d r, D = d / ((1 - d) Ahat) (0 for absent rows)
@@ -1016,11 +1042,21 @@ __device__ void row_params(const Ctx& c, int nc) {
       d = impedance(h, dist);   // one impedance for all rows of the contact
       const int c0 = __float_as_int(gc[0]);
       const int ns = pyr && !(PG_WITH_ELLIPTIC && c.h.cone == PG_CONE_ELLIPTIC) ? 3 : 1;   // pyramids need t1, t2
-      for (int s = 0; s < ns; s++) {
-        float* z = c.w + (h.w_z + s * nv) * c.S;
-        for (int i = 0; i < nv; i++) z[i * c.S] = 0.f;
-        for (int a = 0; a < NC; a++) z[__float_as_int(gc[a * c.S]) * c.S] += J[(s * NC + a) * c.S];
-        ltsolve_chain(c, z, c0);
+      if (h.tree_hessian) {
+        // the pair's columns are its chain (distinct dofs), the support of z: no other entry is read
+        const int nck = MI(pair_ncol, con_pair(c, k));
+        for (int s = 0; s < ns; s++) {
+          float* z = c.w + (h.w_z + s * nv) * c.S;
+          for (int a = 0; a < nck; a++) z[__float_as_int(gc[a * c.S]) * c.S] = J[(s * NC + a) * c.S];
+        }
+        ltsolve_chain3(c, c.w + h.w_z * c.S, c.w + (h.w_z + nv) * c.S, c.w + (h.w_z + 2 * nv) * c.S, ns, c0);
+      } else {
+        for (int s = 0; s < ns; s++) {
+          float* z = c.w + (h.w_z + s * nv) * c.S;
+          for (int i = 0; i < nv; i++) z[i * c.S] = 0.f;
+          for (int a = 0; a < NC; a++) z[__float_as_int(gc[a * c.S]) * c.S] += J[(s * NC + a) * c.S];
+          ltsolve_chain(c, z, c0);
+        }
       }
       Ann = An1 = An2 = A11 = A22 = 0.f;
       // z is supported on the pair's chain (its columns) when pairs lie on single chains
