@@ -354,7 +354,7 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
       {&h.w_gmu, C, 8, 10}, {&h.w_gcond, C, 8, 10},
       {&h.w_z, 3 * nv, 8, 8}, {&h.w_rr, R, 8, 10}, {&h.w_rv, R, 8, 10},
       {&h.w_Ahat, R, 8, 10}, {&h.w_imp, R, 8, 10}, {&h.w_aref, R, 8, 10}, {&h.w_rD, R, 8, 10},
-      {&h.w_jar, R, 9, 10}, {&h.w_Jp, R, 9, 9}, {&h.w_a, nv, 9, 10}, {&h.w_g, nv, 9, 9}, {&h.w_p, nv, 9, 9},
+      {&h.w_jar, R, 9, 10}, {&h.w_Jp, R, 9, 9}, {&h.w_bp, R, 9, 9}, {&h.w_a, nv, 9, 10}, {&h.w_g, nv, 9, 9}, {&h.w_p, nv, 9, 9},
       {&h.w_t, nv, 9, 9}, {&h.w_H, Hsize, 9, 9}};
   std::vector<std::array<int, 4>> placed;   // offset, size, birth, death
   int ws = 0;

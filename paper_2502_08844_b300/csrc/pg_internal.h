@@ -52,7 +52,7 @@ struct ModelHdr {
   int w_xpos, w_xquat, w_cdof, w_cinert, w_cvel, w_cacc, w_cfrc, w_bias;
   int w_M, w_L, w_a0, w_con, w_J, w_z;
   int w_gcol, w_gmu, w_gcond, w_lsgn, w_rr, w_rv, w_Ahat, w_imp, w_aref, w_rD, w_jar, w_Jp;
-  int w_a, w_g, w_p, w_t, w_H, w_Dinv;
+  int w_a, w_g, w_p, w_t, w_H, w_Dinv, w_bp;
   // adjoint workspace (the reverse sweep): every forward buffer above gets its own space (no
   // sharing between phases), plus the own body inertias `ci0` (CRBA overwrites w_cinert with
   // composites), the Hessian factor `HL` and the adjoint buffers b_*.  Valid only in the adjoint

@@ -1304,6 +1304,7 @@ __device__ float line_search(const Ctx& c) {
   }
   rows_dot(c, h.w_p, h.w_Jp);
   unsigned on[4] = {0u, 0u, 0u, 0u};
+  const float none = -__int_as_float(0x7f800000);   // -inf: no breakpoint
   for (int r = 0; r < R; r++) {
     const float D = W(rD, r), jp = W(Jp, r), jr = W(jar, r);
     if (D > 0.f && (jr < 0.f || (jr == 0.f && jp < 0.f))) {
@@ -1311,22 +1312,21 @@ __device__ float line_search(const Ctx& c) {
       qt = fmaf(D * jp, jp, qt);
       lt = fmaf(D * jp, jr, lt);
     }
+    W(bp, r) = D > 0.f && jp != 0.f ? -jr / jp : none;   // the row's breakpoint, once
   }
   float alpha = 0.f;
   for (int step = 0; step <= R; step++) {
     const float root = qt > 0.f ? -lt / qt : alpha;
     float next = __int_as_float(0x7f800000);   // +inf
     for (int r = 0; r < R; r++) {
-      const float jp = W(Jp, r);
-      if (!(W(rD, r) > 0.f) || jp == 0.f) continue;
-      const float br = -W(jar, r) / jp;
+      const float br = W(bp, r);
       if (br > alpha && br < next) next = br;
     }
     if (root <= next) return root;
     alpha = next;
     for (int r = 0; r < R; r++) {
+      if (W(bp, r) != next) continue;
       const float D = W(rD, r), jp = W(Jp, r);
-      if (!(D > 0.f) || jp == 0.f || -W(jar, r) / jp != next) continue;
       const float sg = bit(on, r) ? -1.f : 1.f;
       on[r >> 5] ^= 1u << (r & 31);
       qt = fmaf(sg * D * jp, jp, qt);
