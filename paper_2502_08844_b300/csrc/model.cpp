@@ -269,10 +269,9 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
     pncol[p] = (int)col_dof.size() - pcoladr[p];
     ncol_max = std::max(ncol_max, pncol[p]);
     for (int a = pcoladr[p] + 1; a < (int)col_dof.size(); a++) {
-      // each column must be an ancestor of the previous one
-      int x = col_dof[a - 1];
-      while (x >= 0 && x != col_dof[a]) x = dof_parent[x];
-      if (x < 0) tree_hessian = 0;
+      // each column must be the parent dof of the previous one (one chain, consecutive depths:
+      // column b of column a's row then sits b - a entries into that packed row)
+      if (dof_parent[col_dof[a - 1]] != col_dof[a]) tree_hessian = 0;
     }
     for (int s = pslotadr[p]; s < pslotadr[p] + pnslot[p]; s++) slot_pair[s] = p;
   }

@@ -1219,24 +1219,23 @@ __device__ bool newton_direction(const Ctx& c, const unsigned act[4], bool& zero
       const float hn = Sn * na + c1 * ta + c2 * ua;
       const float ht = c1 * na + s1 * ta + c12 * ua;
       const float hu = c2 * na + c12 * ta + s2 * ua;
-      const int ra = MI(dof_rowadr, da), depa = MI(dof_depth, da);
+      const int ra = MI(dof_rowadr, da);
       if (tree) {
-        // the real columns are distinct dofs of one chain: distinct entries of row da, updated two
-        // at a time with both loads first
+        // the columns are a chain of consecutive parents (checked by the model compiler): column b
+        // updates entry b - a of row da's packed segment, four at a time with the loads first
+        float* Lr = c.w + (h.w_L + ra) * c.S;
         int b = a;
-        for (; b + 1 < nck; b += 2) {
-          const int db0 = __float_as_int(gc[b * c.S]), db1 = __float_as_int(gc[(b + 1) * c.S]);
-          const float v0 = hn * J[b * c.S] + ht * J[(NC + b) * c.S] + hu * J[(2 * NC + b) * c.S];
-          const float v1 = hn * J[(b + 1) * c.S] + ht * J[(NC + b + 1) * c.S] + hu * J[(2 * NC + b + 1) * c.S];
-          const int o0 = ra + depa - MI(dof_depth, db0), o1 = ra + depa - MI(dof_depth, db1);
-          const float l0 = W(L, o0), l1 = W(L, o1);
-          W(L, o0) = l0 + v0;
-          W(L, o1) = l1 + v1;
+        for (; b + 3 < nck; b += 4) {
+          float v[4], l[4];
+#pragma unroll
+          for (int q = 0; q < 4; q++) {
+            v[q] = hn * J[(b + q) * c.S] + ht * J[(NC + b + q) * c.S] + hu * J[(2 * NC + b + q) * c.S];
+            l[q] = Lr[(b + q - a) * c.S];
+          }
+#pragma unroll
+          for (int q = 0; q < 4; q++) Lr[(b + q - a) * c.S] = l[q] + v[q];
         }
-        for (; b < nck; b++) {
-          const int db = __float_as_int(gc[b * c.S]);
-          W(L, ra + depa - MI(dof_depth, db)) += hn * J[b * c.S] + ht * J[(NC + b) * c.S] + hu * J[(2 * NC + b) * c.S];
-        }
+        for (; b < nck; b++) Lr[(b - a) * c.S] += hn * J[b * c.S] + ht * J[(NC + b) * c.S] + hu * J[(2 * NC + b) * c.S];
       } else {
         for (int b = a; b < nck; b++) {
           const int db = __float_as_int(gc[b * c.S]);
