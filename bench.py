@@ -204,6 +204,7 @@ def measure_mixed(dev, steps: int = 200):
     t_eager = a.elapsed_time(b) / 1e3
     n_tot = sum(n for _, _, n in comp)
     return {"value": n_tot * steps / t_graph, "unit": "env-steps/s", "eager_value": n_tot * steps / t_eager,
+            "kernel": "generic (one body shared by the batch's models)",
             "composition": {nm: n for nm, _, n in comp}, "steps": steps, "cuda_graph": True,
             "envs_per_cta": epc or "default (one wave)", "launches": steps}
 

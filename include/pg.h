@@ -166,9 +166,11 @@ void pg_batch_free(pg_batch* batch);
  * regions.
  *
  * Scope. Only single-model batches, and only the production step: the tape (pg_step_vjp) and
- * debug kernels stay generic.
+ * debug kernels stay generic. A mixed batch keeps the generic kernel, whose one body all its
+ * models share: one specialised body per model was measured slower, as blocks of different
+ * models on one SM evict each other's code from the instruction cache.
  *
- * Errors. PG_EUNSUPPORTED (a mixed batch, NVRTC missing or failing, with its log in
+ * Errors. PG_EUNSUPPORTED (a mixed batch; NVRTC missing or failing, with its log in
  * pg_last_error; the batch then keeps the generic kernel), PG_ECUDA. */
 int pg_batch_specialize(pg_batch* batch);
 

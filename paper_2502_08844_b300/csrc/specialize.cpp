@@ -5,8 +5,8 @@
 // 40 % of its instructions are this addressing arithmetic and table reads. Compiling the same
 // kernel body with the model's blob as a constant array turns all of it into immediates.
 //
-// How: pg_batch_specialize generates a small source that defines the blob (kSpecBlob) and
-// includes the kernel body headers, which are embedded in this library at build time. It
+// How: pg_batch_specialize generates a small source that defines the model's blob and includes
+// the kernel body headers, which are embedded in this library at build time. It
 // compiles that source with NVRTC (loaded with dlopen on first use) for sm_103a, loads the
 // cubin with cudaLibraryLoadData, and from then on pg_step launches that kernel for the batch.
 // The arithmetic is the same source in the same order, so results equal the generic kernel's.
@@ -131,22 +131,24 @@ void write_file(const std::string& p, const std::vector<char>& data) {
   else remove(tmp.c_str());
 }
 
-// the generated translation unit: the model blob as a constant array, then the kernel body
+// The generated translation unit: the model's blob as a constant array with its SoA width
+// (SpecModel<0>), then the kernel body and the kernel.
 std::string spec_source(const pg_model* m) {
   std::string s;
-  s += "#define PG_WITH_ELLIPTIC " + std::to_string(m->hdr.cone == PG_CONE_ELLIPTIC ? 1 : 0) + "\n";
-  s += "#define PG_SPEC 1\n#include \"pg_internal.h\"\nnamespace pg {\n";
-  s += "constexpr int kSpecSoa = " + std::to_string(m->hdr.soa) + ";\n";
+  s += "#define PG_WITH_ELLIPTIC " + std::string(m->hdr.cone == PG_CONE_ELLIPTIC ? "1" : "0") + "\n";
+  s += "#define PG_SPEC 1\n#include \"pg_internal.h\"\nnamespace pg {\ntemplate <int M> struct SpecModel;\n";
   // in the constant bank: reads at compile-time indices fold away, the rest are uniform
-  // constant-cache loads (every thread of the kernel steps the same model)
+  // constant-cache loads (every thread steps the same model)
   s += "__constant__ const uint32_t kSpecBlob[" + std::to_string(m->blob.size()) + "] __attribute__((aligned(16))) = {";
   for (size_t i = 0; i < m->blob.size(); i++) {
     if (i % 16 == 0) s += "\n";
     s += std::to_string(m->blob[i]) + "u,";
   }
-  s += "\n};\n}  // namespace pg\n#include \"step_kernel_body.cuh\"\n";
+  s += "\n};\ntemplate <> struct SpecModel<0> {\n  static constexpr int soa = " + std::to_string(m->hdr.soa) +
+       ";\n  __device__ static const uint32_t* blob() { return kSpecBlob; }\n};\n";
+  s += "}  // namespace pg\n#include \"step_kernel_body.cuh\"\n";
   s += "extern \"C\" __global__ void __launch_bounds__(" + std::to_string(kMaxEnvsPerCta) +
-       ") pg_step_spec(const __grid_constant__ pg::StepArgs A) { pg::step_body<false, false>(A); }\n";
+       ") pg_step_spec(const __grid_constant__ pg::StepArgs A) { pg::step_body<false, false, 0>(A); }\n";
   return s;
 }
 
@@ -199,7 +201,12 @@ using namespace pg;
 
 extern "C" int pg_batch_specialize(pg_batch* b) {
   if (!b) return set_error(PG_EINVAL, "batch is NULL");
-  if (b->models.size() != 1) return set_error(PG_EUNSUPPORTED, "pg_batch_specialize: only single-model batches");
+  // A mixed batch would need one body per model in one kernel. Measured, that is slower than the
+  // generic kernel: blocks of different models share an SM and their large specialised bodies
+  // evict each other from the instruction cache. So mixed batches keep the generic kernel.
+  if (b->models.size() != 1)
+    return set_error(PG_EUNSUPPORTED, "pg_batch_specialize: single-model batches only (a mixed batch keeps the "
+                                      "generic kernel, whose one body all models share)");
   if (b->spec_kernel) return PG_OK;
   std::vector<char> cubin;
   int rc = compile_cubin(b->models[0], cubin);

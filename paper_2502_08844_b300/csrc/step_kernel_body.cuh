@@ -1,8 +1,9 @@
 // The step kernel's body and its argument block, shared by the library's compiled kernels
 // (step_kernels.cuh) and by the model-specialised kernels it compiles at run time (NVRTC, see
 // specialize.cpp).  The including unit sets PG_WITH_ELLIPTIC; PG_SPEC (run-time compilation)
-// takes the model from the constant kSpecBlob / kSpecSoa instead of the kernel argument, so the
-// compiler folds every header field, table entry and workspace offset.
+// takes model SPEC_M of the batch from the constant SpecModel<SPEC_M> (its blob and SoA width,
+// defined by the generated source) instead of the kernel argument, so the compiler folds every
+// header field, table entry and workspace offset.
 #pragma once
 #include "step_device.cuh"
 
@@ -36,14 +37,14 @@ struct StepArgs {
 // tape_nq, the warm start from tape_nq + tape_nv and the acceleration from tape_nq + 2 tape_nv
 // (the adjoint replays the substeps from this record).
 
-template <bool DEBUG, bool TAPE>
+template <bool DEBUG, bool TAPE, int SPEC_M = 0>
 __device__ __forceinline__ void step_body(const StepArgs& A) {
   extern __shared__ __align__(16) float smem[];
   const Tile tile = DEBUG ? A.dbg_tile : A.tiles[blockIdx.x];
 #ifdef PG_SPEC
-  const uint32_t* blob = kSpecBlob;
-  const ModelHdr& h = *reinterpret_cast<const ModelHdr*>(kSpecBlob);
-  constexpr int S = kSpecSoa;
+  const uint32_t* blob = SpecModel<SPEC_M>::blob();
+  const ModelHdr& h = *reinterpret_cast<const ModelHdr*>(blob);
+  constexpr int S = SpecModel<SPEC_M>::soa;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #else
   const uint32_t* blob = A.blob + A.model_off[tile.model];

@@ -1,7 +1,7 @@
 """pg_batch_specialize: the step kernel compiled at run time (NVRTC) with the model as constants
 runs the same source as the generic kernel.  With the model known the compiler may fold known
 zeros and forward stored constants, which can regroup an FMA, so trajectories agree to rounding
-(1e-6 of their scale over a few steps; often bitwise).  Mixed batches are refused."""
+(1e-6 of their scale over a few steps; often bitwise).  Mixed batches keep the generic kernel."""
 import numpy as np
 import pytest
 import torch
@@ -33,7 +33,7 @@ def test_specialised_kernel_matches_generic(mname, cfg, n, T):
     assert np.array_equal(out[0][2], out[1][2])
 
 
-def test_specialise_refuses_mixed_batches():
+def test_specialise_keeps_mixed_batches_generic():
     parts = [(core.CompiledModel(W.cartpole()), 4), (core.CompiledModel(W.quadruped()), 4)]
     batch = core.Batch(parts)
     with pytest.raises(_capi.PgError) as ei:
