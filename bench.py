@@ -243,7 +243,7 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def measure_adjoint(dev, n: int = 4096, steps: int = 64, segment: int = 8, reps: int = 3):
+def measure_adjoint(dev, n: int = 4096, steps: int = 64, segment: int = 8, reps: int = 3, specialize: bool = True):
     """Full rollout gradient against the forward rollout on the adjoint workload: 4096
     quadrupeds, 64 control steps, loss sum_t (z_t - 0.27)^2 + |v_t - (0.5, 0, 0)|^2 of the torso
     height and linear velocity, gradients with respect to the initial state, all 64 x 12
@@ -254,6 +254,8 @@ def measure_adjoint(dev, n: int = 4096, steps: int = 64, segment: int = 8, reps:
     m = W.quadruped()
     cm = core.CompiledModel(m)
     batch = core.Batch([(cm, n)])
+    if specialize:
+        batch.specialize()   # forward, tape replay and reverse sweep compiled for the model
     st = core.State(batch, dev)
     ld = st.ld
     q0, v0 = W.initial_state(m, 4, n)
@@ -295,7 +297,8 @@ def measure_adjoint(dev, n: int = 4096, steps: int = 64, segment: int = 8, reps:
     tf = min(timed(forward) for _ in range(reps))
     tg = min(timed(gradient) for _ in range(reps))
     return {"ratio": tg / tf, "forward_ms": tf, "gradient_ms": tg, "envs": n, "steps": steps, "segment": segment,
-            "newton_cap": m.iterations, "note": "gradient = checkpointed forward + loss + backward sweep"}
+            "newton_cap": m.iterations, "kernels": "model-specialised" if specialize else "generic",
+            "note": "gradient = checkpointed forward + loss + backward sweep"}
 
 
 def run_ours(args):
@@ -411,9 +414,12 @@ def run_ours(args):
     if not args.no_mixed:
         line["mixed_batch"] = measure_mixed(dev)
     if not args.no_adjoint:
-        adj = measure_adjoint(dev)
+        adj = measure_adjoint(dev, specialize=kernel.startswith("model-specialised"))
         line["adjoint_forward_ratio"] = adj["ratio"]
         line["adjoint"] = adj
+        gen = measure_adjoint(dev, specialize=False)
+        line["adjoint"]["generic_kernels"] = {"ratio": gen["ratio"], "forward_ms": gen["forward_ms"],
+                                              "gradient_ms": gen["gradient_ms"]}
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(m, cfg, n)
     print(json.dumps(line))

@@ -373,19 +373,52 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
     ws = std::max(ws, off + b.size);
   }
   h.ws_floats = std::max(ws, 1);
-  // ---- adjoint layout: the same buffers laid end to end, then the reverse sweep's own ----
+  // ---- adjoint layout: the buffers of the reverse sweep's substep, packed by lifetime like the
+  // forward's.  Phases: 0 the running state adjoint (across substeps), 1 forward recompute,
+  // 2 integration reverse and lambda = H^-1 abar, 3 forces and constraint rows, 4 CRBA,
+  // 5 composite-to-own inertias and RNEA, 6 inertia wrenches, 7 inward sweep. ----
   {
-    int a = 0;
-    auto take = [&](int n) { int r = a; a += std::max(n, 1); return r; };
     ModelHdr& g = out->hdr_adj;
     g = h;
-    for (Buf& b : bufs) *(int*)((char*)&g + ((char*)b.off - (char*)&h)) = take(b.size);
-    g.w_ci0 = take(10 * nbody);
-    g.w_HL = take(nL);
-    g.b_q = take(nq); g.b_v = take(nv); g.b_a = take(nv); g.b_bias = take(nv); g.b_M = take(nL);
-    g.b_cdof = take(6 * nv); g.b_I = take(10 * nbody); g.b_vel = take(6 * nbody); g.b_acc = take(6 * nbody);
-    g.b_frc = take(6 * nbody); g.b_wr = take(6 * nbody); g.b_w = take(3 * nv);
-    g.ws_adj_floats = a;
+    const int RA = std::max(nrow_max, 1), CA = std::max(max_contacts, 1);
+    struct ABuf { int* off; int size; int birth, death; };
+    std::vector<ABuf> ab = {
+        {&g.b_q, nq, 0, 7}, {&g.b_v, nv, 0, 7},
+        {&g.w_qpos, nq, 1, 7}, {&g.w_qvel, nv, 1, 5}, {&g.w_a, nv, 1, 3},
+        {&g.w_xpos, 3 * nbody, 1, 7}, {&g.w_xquat, 4 * nbody, 1, 7}, {&g.w_cdof, 6 * nv, 1, 7},
+        {&g.w_cinert, 10 * nbody, 1, 4}, {&g.w_ci0, 10 * nbody, 1, 5},
+        {&g.w_cvel, 6 * nbody, 1, 5}, {&g.w_cacc, 6 * nbody, 1, 5}, {&g.w_cfrc, 6 * nbody, 1, 5},
+        {&g.w_M, nL, 1, 2}, {&g.w_L, nL, 1, 3},
+        {&g.w_con, kConFloats * CA, 1, 3}, {&g.w_J, 3 * ncol_max * CA, 1, 3}, {&g.w_gcol, ncol_max * CA, 1, 3},
+        {&g.w_lsgn, std::max((int)limit_jnt.size(), 1), 1, 3}, {&g.w_gmu, CA, 1, 3}, {&g.w_gcond, CA, 1, 3},
+        {&g.w_rr, RA, 1, 3}, {&g.w_Ahat, RA, 1, 3}, {&g.w_imp, RA, 1, 3}, {&g.w_rD, RA, 1, 3},
+        {&g.w_jar, RA, 1, 3}, {&g.w_Jp, RA, 1, 3},
+        // used by the forward recompute only
+        {&g.w_warm, nv, 1, 1}, {&g.w_bias, nv, 1, 1}, {&g.w_a0, nv, 1, 1}, {&g.w_Dinv, nv, 1, 1},
+        {&g.w_z, 3 * nv, 1, 1}, {&g.w_rv, RA, 1, 1}, {&g.w_aref, RA, 1, 1}, {&g.w_g, nv, 1, 1},
+        {&g.w_p, nv, 1, 1}, {&g.w_t, nv, 1, 1}, {&g.w_H, tree_hessian ? 0 : nv * nv, 1, 1}, {&g.w_bp, RA, 1, 1},
+        // the reverse sweep's own
+        {&g.w_HL, nL, 2, 2}, {&g.b_a, nv, 2, 3}, {&g.b_bias, nv, 3, 5}, {&g.b_M, nL, 3, 4},
+        {&g.b_cdof, 6 * nv, 3, 7}, {&g.b_I, 10 * nbody, 3, 6}, {&g.b_wr, 6 * nbody, 3, 7}, {&g.b_w, 3 * nv, 3, 3},
+        {&g.b_vel, 6 * nbody, 5, 5}, {&g.b_acc, 6 * nbody, 5, 5}, {&g.b_frc, 6 * nbody, 5, 5}};
+    std::vector<std::array<int, 4>> put;
+    int top = 0;
+    for (ABuf& b : ab) {
+      int off = 0;
+      bool moved = true;
+      while (moved) {
+        moved = false;
+        for (auto& q : put) {
+          const bool overlap_t = !(b.death < q[2] || q[3] < b.birth);
+          const bool overlap_s = off < q[0] + q[1] && q[0] < off + b.size;
+          if (overlap_t && overlap_s) { off = q[0] + q[1]; moved = true; }
+        }
+      }
+      *b.off = off;
+      put.push_back({off, b.size, b.birth, b.death});
+      top = std::max(top, off + b.size);
+    }
+    g.ws_adj_floats = std::max(top, 1);
     // scope of the hand-written adjoint: contacts only between a world-fixed plane (geom1) and a
     // sphere, capsule or box, which keeps the Newton Hessian on the mass matrix's pattern
     bool ok = true;

@@ -37,6 +37,8 @@ struct pg_batch {
   // model-specialised step kernel compiled at run time (pg_batch_specialize), else NULL
   cudaLibrary_t spec_lib = nullptr;
   cudaKernel_t spec_kernel = nullptr;
+  cudaKernel_t spec_kernel_tape = nullptr;   // the same with the substep tape (adjoint replay)
+  cudaKernel_t spec_kernel_vjp = nullptr;    // the adjoint's reverse sweep (NULL outside its scope)
   // staging buffer of the host-buffer path (allocated on its first use)
   float* d_ctrl_stage = nullptr;
   size_t ctrl_stage_floats = 0;
@@ -71,6 +73,8 @@ cudaError_t launch_step_tape(const pg_batch* b, const pg_state* s, const float* 
   cudaError_t debug(const pg_batch* b, const pg_state* s, const float* ctrl, int64_t env, float* out,            \
                     cudaStream_t st);                                                                            \
   cudaError_t step_spec(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st);\
+  cudaError_t step_spec_tape(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, float* tape,\
+                             int tape_rows, cudaStream_t st);                                                   \
   }
 PG_DECLARE_STEP_KERNELS(pyramidal)
 PG_DECLARE_STEP_KERNELS(elliptic)

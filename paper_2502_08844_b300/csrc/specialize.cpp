@@ -144,11 +144,26 @@ std::string spec_source(const pg_model* m) {
     if (i % 16 == 0) s += "\n";
     s += std::to_string(m->blob[i]) + "u,";
   }
-  s += "\n};\ntemplate <> struct SpecModel<0> {\n  static constexpr int soa = " + std::to_string(m->hdr.soa) +
-       ";\n  __device__ static const uint32_t* blob() { return kSpecBlob; }\n};\n";
-  s += "}  // namespace pg\n#include \"step_kernel_body.cuh\"\n";
-  s += "extern \"C\" __global__ void __launch_bounds__(" + std::to_string(kMaxEnvsPerCta) +
-       ") pg_step_spec(const __grid_constant__ pg::StepArgs A) { pg::step_body<false, false, 0>(A); }\n";
+  s += "\n};\n";
+  const bool adj = m->hdr.adj_ok && m->hdr.cone != PG_CONE_ELLIPTIC;
+  if (adj) {   // the same tables with the adjoint's header (its workspace layout)
+    s += "__constant__ const uint32_t kSpecBlobAdj[" + std::to_string(m->blob_adj.size()) +
+         "] __attribute__((aligned(16))) = {";
+    for (size_t i = 0; i < m->blob_adj.size(); i++) {
+      if (i % 16 == 0) s += "\n";
+      s += std::to_string(m->blob_adj[i]) + "u,";
+    }
+    s += "\n};\n";
+  }
+  s += "template <> struct SpecModel<0> {\n  static constexpr int soa = " + std::to_string(m->hdr.soa) +
+       ";\n  __device__ static const uint32_t* blob() { return kSpecBlob; }\n";
+  if (adj) s += "  __device__ static const uint32_t* blob_adj() { return kSpecBlobAdj; }\n";
+  s += "};\n}  // namespace pg\n#include \"step_kernel_body.cuh\"\n";
+  const std::string lb = "__launch_bounds__(" + std::to_string(kMaxEnvsPerCta) + ")";
+  s += "extern \"C\" __global__ void " + lb + " pg_step_spec(const __grid_constant__ pg::StepArgs A) { pg::step_body<false, false, 0>(A); }\n";
+  s += "extern \"C\" __global__ void " + lb + " pg_step_spec_tape(const __grid_constant__ pg::StepArgs A) { pg::step_body<false, true, 0>(A); }\n";
+  if (adj)
+    s += "#include \"adjoint_body.cuh\"\nextern \"C\" __global__ void __launch_bounds__(64) pg_vjp_spec(const __grid_constant__ pg::VjpArgs A) { pg::vjp_body<0>(A); }\n";
   return s;
 }
 
@@ -214,17 +229,26 @@ extern "C" int pg_batch_specialize(pg_batch* b) {
   cudaLibrary_t lib = nullptr;
   cudaError_t e = cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
   if (e != cudaSuccess) return set_error(PG_ECUDA, std::string("cudaLibraryLoadData: ") + cudaGetErrorString(e));
-  cudaKernel_t k = nullptr;
+  cudaKernel_t k = nullptr, kt = nullptr, kv = nullptr;
   e = cudaLibraryGetKernel(&k, lib, "pg_step_spec");
+  if (e == cudaSuccess) e = cudaLibraryGetKernel(&kt, lib, "pg_step_spec_tape");
+  if (e == cudaSuccess && b->models[0]->hdr.adj_ok && b->models[0]->hdr.cone != PG_CONE_ELLIPTIC)
+    e = cudaLibraryGetKernel(&kv, lib, "pg_vjp_spec");
   int dev = 0;
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess)
     e = cudaKernelSetAttributeForDevice(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem_bytes, dev);
+  if (e == cudaSuccess)
+    e = cudaKernelSetAttributeForDevice(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem_bytes, dev);
+  if (e == cudaSuccess && kv)   // the reverse sweep uses no shared memory: all of the unified cache to L1
+    e = cudaKernelSetAttributeForDevice(kv, cudaFuncAttributePreferredSharedMemoryCarveout, 0, dev);
   if (e != cudaSuccess) {
     cudaLibraryUnload(lib);
     return set_error(PG_ECUDA, std::string("specialised kernel set-up: ") + cudaGetErrorString(e));
   }
   b->spec_lib = lib;
   b->spec_kernel = k;
+  b->spec_kernel_tape = kt;
+  b->spec_kernel_vjp = kv;
   return PG_OK;
 }

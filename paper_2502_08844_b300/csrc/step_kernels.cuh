@@ -70,6 +70,20 @@ cudaError_t step_spec(const pg_batch* b, const pg_state* s, const float* ctrl, i
   return cudaLaunchKernel((const void*)b->spec_kernel, dim3(b->ntiles), dim3(b->threads), params, b->smem_bytes, st);
 }
 
+cudaError_t step_spec_tape(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, float* tape,
+                           int tape_rows, cudaStream_t st) {
+  if (b->ntiles == 0) return cudaSuccess;
+  static thread_local StepArgs A;
+  make_args(A, b, s, ctrl);
+  A.n_substeps = n_substeps;
+  A.tape = tape;
+  A.tape_rows = tape_rows;
+  A.tape_nq = b->nq_max;
+  A.tape_nv = b->nv_max;
+  void* params[] = {&A};
+  return cudaLaunchKernel((const void*)b->spec_kernel_tape, dim3(b->ntiles), dim3(b->threads), params, b->smem_bytes, st);
+}
+
 cudaError_t step_tape(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, float* tape,
                              int tape_rows, cudaStream_t st) {
   if (b->ntiles == 0) return cudaSuccess;

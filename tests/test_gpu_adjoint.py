@@ -24,11 +24,13 @@ pytestmark = pytest.mark.gpu
 GRAD_RTOL, GRAD_ATOL = 1e-3, 1e-6
 
 
-def gpu_rollout_grad(m: W.Model, q0, v0, U, weights, segment=8):
+def gpu_rollout_grad(m: W.Model, q0, v0, U, weights, segment=8, specialize=False):
     """GPU loss and per-env gradients of sum_t sum_i wq_i (q_t,i - qs_i)^2 + wv_i (v_t,i - vs_i)^2."""
     n, T = q0.shape[0], U.shape[0]
     cm = core.CompiledModel(m)
     batch = core.Batch([(cm, n)])
+    if specialize:
+        batch.specialize()
     ld = max(4, (n + 3) // 4 * 4)
     dev = torch.device("cuda")
     qpos0 = torch.from_numpy(core.to_soa(q0.astype(np.float32), ld, batch.nq_max)).to(dev).requires_grad_()

@@ -39,3 +39,20 @@ def test_specialise_keeps_mixed_batches_generic():
     with pytest.raises(_capi.PgError) as ei:
         batch.specialize()
     assert ei.value.code == _capi.PG_EUNSUPPORTED
+
+
+def test_specialised_adjoint_matches_generic():
+    """pg_step_vjp on a specialised batch (specialised forward, tape replay and reverse sweep)
+    against the generic kernels: the same rollout gradient up to rounding."""
+    import dataclasses
+    from tests.test_gpu_adjoint import gpu_rollout_grad
+    from oracle import oracle as O
+    m = dataclasses.replace(W.quadruped(), iterations=100)
+    q0, v0 = W.initial_state(m, 4, 8)
+    U = W.actions(m, 4, 8, 0, 8)
+    w = O.tracking_loss_weights(O.OracleModel(m))
+    a = gpu_rollout_grad(m, q0, v0, U, w)
+    b = gpu_rollout_grad(m, q0, v0, U, w, specialize=True)
+    for k in ("q0", "v0", "u", "mass", "damping", "kp"):
+        x, y = a[k], b[k]
+        assert np.abs(x - y).max() <= 1e-4 * max(np.abs(x).max(), 1e-6), (k, np.abs(x - y).max())
