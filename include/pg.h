@@ -236,9 +236,10 @@ int pg_step_host(pg_batch* batch, pg_state* state, const float* ctrl_host, float
  * Otherwise the call returns PG_EUNSUPPORTED.
  *
  * Scratch and errors.
- *   * Scratch, about (n_steps * substeps * (nq + 3 nv) + adjoint workspace) floats per env, is
- *     allocated on the first call and grown when a later call needs more. Such a call returns
- *     only after the allocation, so make it before any stream capture.
+ *   * Scratch, about n_steps * substeps * (nq + 3 nv) floats per env (plus the adjoint
+ *     workspace when 8 environments' workspaces do not fit in one block's 227 KB of shared
+ *     memory), is allocated on the first call and grown when a later call needs more. Such a
+ *     call returns only after the allocation, so make it before any stream capture.
  *   * Calls on the same batch share the scratch: calls that overlap on the GPU race.
  *   * Errors: PG_EINVAL for NULL or inconsistent arguments, PG_EUNSUPPORTED,
  *     PG_ENOMEM / PG_ECUDA. */

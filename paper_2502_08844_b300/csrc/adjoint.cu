@@ -3,6 +3,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cstring>
 
 #include "pg_host.h"
@@ -13,7 +14,8 @@
 namespace pg {
 namespace {
 
-__global__ void __launch_bounds__(64) vjp_kernel(const __grid_constant__ VjpArgs A) { vjp_body<0>(A); }
+template <bool SMEM>
+__global__ void __launch_bounds__(64) vjp_kernel(const __grid_constant__ VjpArgs A) { vjp_body<0, SMEM>(A); }
 
 }  // namespace
 
@@ -30,18 +32,28 @@ cudaError_t launch_vjp_step(const pg_batch* b, const float* tape, int tape_rows,
     A.model_off[k] = k < A.nmodels ? b->blob_off[k] : 0;
   }
   std::memcpy(A.blob, b->blob_host_adj.data(), b->blob_host_adj.size() * sizeof(uint32_t));
-  const int threads = 32;   // one warp of consecutive environments: 128-byte aligned workspace accesses
+  // the widest shared-memory block every model's workspace fits in (0: global memory)
+  int ws_max = 1;
+  for (const pg_model* m : b->models) ws_max = std::max(ws_max, m->hdr_adj.ws_adj_floats);
+  A.soa = vjp_smem_soa(ws_max);
+  // a shared-memory block holds soa environments; the global-memory form runs one warp of
+  // consecutive environments (128-byte aligned workspace accesses)
+  const int threads = A.soa > 0 ? A.soa : 32;
   const unsigned blocks = (unsigned)((b->n + threads - 1) / threads);
+  const size_t smem = (size_t)4 * A.soa * ws_max;
   if (b->spec_kernel_vjp) {   // the batch's model-specialised build (pg_batch_specialize)
     void* params[] = {&A};
-    return cudaLaunchKernel((const void*)b->spec_kernel_vjp, dim3(blocks), dim3(threads), params, 0, st);
+    return cudaLaunchKernel((const void*)b->spec_kernel_vjp, dim3(blocks), dim3(threads), params, smem, st);
   }
-  static bool carveout = false;   // no shared memory: give the SM's unified cache to L1
-  if (!carveout) {
-    cudaFuncSetAttribute(vjp_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-    carveout = true;
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(vjp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    // no shared memory in the global-memory form: the SM's unified cache goes to L1
+    cudaFuncSetAttribute(vjp_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    configured = true;
   }
-  vjp_kernel<<<blocks, threads, 0, st>>>(A);
+  if (A.soa > 0) vjp_kernel<true><<<blocks, threads, smem, st>>>(A);
+  else vjp_kernel<false><<<blocks, threads, 0, st>>>(A);
   return cudaGetLastError();
 }
 

@@ -641,8 +641,10 @@ struct VjpArgs {
   float* adj_v;          // [nv_max][ld]
   float* g_ctrl;         // [nu_max][ld] out
   float* g_params;       // [np_max][ld] accumulated: body masses | dof damping | actuator kp
-  float* ws;             // adjoint workspaces, element i of env e at ws[i * ld + e]
+  float* ws;             // global-memory workspaces (soa == 0): element i of env e at ws[i * ld + e]
   int64_t ld;
+  int soa;               // > 0: workspaces in shared memory, blocks of soa environments, element i
+                         // of the block's environment l at [i * soa + l]
   int64_t n;
   int tape_rows, nq_max, nv_max;
   int n_substeps;
@@ -652,8 +654,11 @@ struct VjpArgs {
   uint32_t blob[kMaxParamWords];   // the models' adjoint blobs (adjoint header + tables)
 };
 
-template <int SPEC_M = 0>
+// SMEM: the workspace is in shared memory (blocks of A.soa environments, or of the specialised
+// model's constant width); otherwise in global memory at A.ws with stride ld.
+template <int SPEC_M = 0, bool SMEM = true>
 __device__ __forceinline__ void vjp_body(const VjpArgs& A) {
+  extern __shared__ __align__(16) float vjp_ws[];
   const int64_t env = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (env >= A.n) return;
 #ifdef PG_SPEC
@@ -665,7 +670,13 @@ __device__ __forceinline__ void vjp_body(const VjpArgs& A) {
 #endif
   const ModelHdr& h = *reinterpret_cast<const ModelHdr*>(blob);
   const int64_t ld = A.ld;
-  Ctx c{h, (int)ld, reinterpret_cast<const int*>(blob), reinterpret_cast<const float*>(blob), A.ws + env, A.ctrl, ld, env};
+#ifdef PG_SPEC
+  constexpr int kSoa = SMEM ? SpecModel<SPEC_M>::vjp_soa : 0;
+#else
+  const int kSoa = SMEM ? A.soa : 0;
+#endif
+  float* w = SMEM ? vjp_ws + threadIdx.x : A.ws + env;
+  Ctx c{h, SMEM ? kSoa : (int)ld, reinterpret_cast<const int*>(blob), reinterpret_cast<const float*>(blob), w, A.ctrl, ld, env};
   for (int k = 0; k < h.nq; k++) B(q, k) = A.adj_q[k * ld + env] + (A.gq ? A.gq[k * ld + env] : 0.f);
   for (int k = 0; k < h.nv; k++) B(v, k) = A.adj_v[k * ld + env] + (A.gv ? A.gv[k * ld + env] : 0.f);
   for (int k = 0; k < h.nu; k++) A.g_ctrl[k * ld + env] = 0.f;

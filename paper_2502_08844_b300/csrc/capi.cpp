@@ -259,7 +259,8 @@ int pg_step_vjp(pg_batch* b, const pg_state* ck, const float* ctrl, int n_steps,
   const int tape_rows = nq + 3 * nv;
   const size_t state_f = (size_t)(nq + 2 * nv + 1) * ld;            // qpos | qvel | warm | status
   const size_t tape_f = (size_t)n_steps * sub_max * tape_rows * ld;
-  const size_t ws_f = (size_t)ws_max * ld;
+  // the reverse sweep's workspace: in shared memory when a block of it fits, else here
+  const size_t ws_f = vjp_smem_soa(ws_max) > 0 ? 0 : (size_t)ws_max * ld;
   const size_t need = state_f + tape_f + ws_f;
   if (b->vjp_floats < need) {
     if (b->d_vjp) cudaFree(b->d_vjp);

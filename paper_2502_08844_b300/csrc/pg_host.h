@@ -80,6 +80,16 @@ PG_DECLARE_STEP_KERNELS(pyramidal)
 PG_DECLARE_STEP_KERNELS(elliptic)
 #undef PG_DECLARE_STEP_KERNELS
 // adjoint.cu
+// Environments per block of the reverse sweep with its workspace (ws_adj_floats floats per
+// environment) in shared memory: the widest of kVjpSoa, kVjpSoa/2, ... 8 whose block fits in one
+// SM's opt-in shared memory, or 0 when not even 8 fit (the workspace then lives in global memory).
+constexpr int kVjpSoa = 16;
+inline int vjp_smem_soa(int ws_adj_floats) {
+  for (int s = kVjpSoa; s >= 8; s /= 2)
+    if ((size_t)4 * s * ws_adj_floats <= (size_t)kMaxSmem) return s;
+  return 0;
+}
+
 cudaError_t launch_vjp_step(const pg_batch* b, const float* tape, int tape_rows, const float* ctrl, const float* gq,
                             const float* gv, float* adj_q, float* adj_v, float* g_ctrl, float* g_params, float* ws,
                             int64_t ld, int n_substeps, cudaStream_t st);

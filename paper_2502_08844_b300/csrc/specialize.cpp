@@ -157,13 +157,15 @@ std::string spec_source(const pg_model* m) {
   }
   s += "template <> struct SpecModel<0> {\n  static constexpr int soa = " + std::to_string(m->hdr.soa) +
        ";\n  __device__ static const uint32_t* blob() { return kSpecBlob; }\n";
-  if (adj) s += "  __device__ static const uint32_t* blob_adj() { return kSpecBlobAdj; }\n";
+  if (adj)
+    s += "  static constexpr int vjp_soa = " + std::to_string(vjp_smem_soa(m->hdr_adj.ws_adj_floats)) +
+         ";\n  __device__ static const uint32_t* blob_adj() { return kSpecBlobAdj; }\n";
   s += "};\n}  // namespace pg\n#include \"step_kernel_body.cuh\"\n";
   const std::string lb = "__launch_bounds__(" + std::to_string(kMaxEnvsPerCta) + ")";
   s += "extern \"C\" __global__ void " + lb + " pg_step_spec(const __grid_constant__ pg::StepArgs A) { pg::step_body<false, false, 0>(A); }\n";
   s += "extern \"C\" __global__ void " + lb + " pg_step_spec_tape(const __grid_constant__ pg::StepArgs A) { pg::step_body<false, true, 0>(A); }\n";
   if (adj)
-    s += "#include \"adjoint_body.cuh\"\nextern \"C\" __global__ void __launch_bounds__(64) pg_vjp_spec(const __grid_constant__ pg::VjpArgs A) { pg::vjp_body<0>(A); }\n";
+    s += "#include \"adjoint_body.cuh\"\nextern \"C\" __global__ void __launch_bounds__(64) pg_vjp_spec(const __grid_constant__ pg::VjpArgs A) { pg::vjp_body<0, " + std::string(vjp_smem_soa(m->hdr_adj.ws_adj_floats) > 0 ? "true" : "false") + ">(A); }\n";
   return s;
 }
 
@@ -240,8 +242,12 @@ extern "C" int pg_batch_specialize(pg_batch* b) {
     e = cudaKernelSetAttributeForDevice(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem_bytes, dev);
   if (e == cudaSuccess)
     e = cudaKernelSetAttributeForDevice(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem_bytes, dev);
-  if (e == cudaSuccess && kv)   // the reverse sweep uses no shared memory: all of the unified cache to L1
-    e = cudaKernelSetAttributeForDevice(kv, cudaFuncAttributePreferredSharedMemoryCarveout, 0, dev);
+  if (e == cudaSuccess && kv) {
+    if (vjp_smem_soa(b->models[0]->hdr_adj.ws_adj_floats) > 0)   // workspace in shared memory
+      e = cudaKernelSetAttributeForDevice(kv, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem, dev);
+    else   // workspace in global memory: all of the unified cache to L1
+      e = cudaKernelSetAttributeForDevice(kv, cudaFuncAttributePreferredSharedMemoryCarveout, 0, dev);
+  }
   if (e != cudaSuccess) {
     cudaLibraryUnload(lib);
     return set_error(PG_ECUDA, std::string("specialised kernel set-up: ") + cudaGetErrorString(e));

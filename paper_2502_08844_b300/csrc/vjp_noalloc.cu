@@ -89,7 +89,7 @@ extern "C" int pg_step_vjp_noalloc(pg_batch* b, const pg_state* ck, const float*
   const int tape_rows = nq + 3 * nv;
   const size_t state_f = (size_t)(nq + 2 * nv + 1) * ld;
   const size_t tape_step = (size_t)sub_max * tape_rows * ld;
-  const size_t ws_f = (size_t)ws_max * ld;
+  const size_t ws_f = vjp_smem_soa(ws_max) > 0 ? 0 : (size_t)ws_max * ld;   // 0: in shared memory
   // reject before any size product can overflow: each factor is bounded by the scratch size
   if (state_f > kNoAllocScratchFloats || ws_f > kNoAllocScratchFloats || tape_step > kNoAllocScratchFloats ||
       (size_t)n_steps > kNoAllocScratchFloats / tape_step ||
