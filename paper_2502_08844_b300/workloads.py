@@ -485,6 +485,85 @@ def b_njnt(b: ModelBuilder) -> int:
 MODELS = {"cartpole": cartpole, "quadruped": quadruped, "hand": hand, "hand_elliptic": hand_elliptic, "humanoid": humanoid}
 
 
+# --------------------------------------------------------------------------------------
+# locomotion task around the step (configuration only: which geoms are feet, the weights of
+# the reward table's terms, the action mapping; the arithmetic lives in the kernels and, for
+# tests, in the oracle)
+# --------------------------------------------------------------------------------------
+
+ABSOLUTE, RELATIVE = 0, 1
+# reward terms in the order of the C ABI's PG_R_* list
+TERMS = ("lin_vel", "ang_vel", "air_time", "clearance", "slip", "orientation", "torque", "joint_pos",
+         "action_rate", "energy", "pose", "termination", "stand_still", "lin_z", "ang_xy")
+# joystick command ranges (vx, vy, wz) of the first joystick training stage (App. B, "Finetuning")
+COMMAND_RANGE = (1.5, 0.8, 1.2)
+
+
+@dataclasses.dataclass
+class Task:
+    """A locomotion task: the action mapping, the feet and the reward table's weights."""
+
+    action_mode: int             # ABSOLUTE (q_default + scale a) or RELATIVE (q_des_prev + scale a)
+    action_scale: float
+    q_default: np.ndarray        # [nu] float32
+    foot_geom: np.ndarray        # [nfeet] int32 sphere geoms
+    contact_height: float        # a foot touches the ground below this height of its lowest point
+    clearance_height: float      # desired swing height
+    sigma_lin_vel: float
+    sigma_ang_vel: float
+    air_time_min: float
+    air_time_max: float
+    weight: np.ndarray           # [len(TERMS)] float32
+    episode_length: int
+
+    @property
+    def nfeet(self) -> int:
+        return int(self.foot_geom.shape[0])
+
+
+# Weights of the quadruped joystick task. The paper prints the reward table without its
+# coefficients; these are this workload's own choice (tracking rewards positive, penalties
+# negative), not the paper's.
+QUAD_TASK_WEIGHTS = {"lin_vel": 1.0, "ang_vel": 0.5, "air_time": 0.1, "clearance": -2.0, "slip": -0.1,
+                     "orientation": -5.0, "torque": -2e-4, "joint_pos": -0.05, "action_rate": -0.01,
+                     "energy": -1e-3, "pose": 0.5, "termination": -1.0, "stand_still": -0.5, "lin_z": -0.5,
+                     "ang_xy": -0.05}
+
+
+def quadruped_task(action_mode: int = ABSOLUTE, episode_length: int = 1000, weights=None) -> Task:
+    """Joystick locomotion task of the quadruped: absolute targets around the standing pose
+    (action scale 0.3 rad), the four foot spheres as feet."""
+    m = quadruped()
+    feet = np.array([g for g in range(m.ngeom) if m.geom_type[g] == SPHERE], np.int32)
+    w = dict(QUAD_TASK_WEIGHTS)
+    if weights:
+        w.update(weights)
+    return Task(action_mode=action_mode, action_scale=0.3, q_default=_f32(m.default_ctrl), foot_geom=feet,
+                contact_height=0.002, clearance_height=0.08, sigma_lin_vel=0.25, sigma_ang_vel=0.25,
+                air_time_min=0.1, air_time_max=0.5, weight=_f32([w[k] for k in TERMS]),
+                episode_length=int(episode_length))
+
+
+def commands(config: int, n_envs: int, env0: int = 0, draw: int = 0) -> np.ndarray:
+    """Joystick commands [N, 3] (vx, vy, wz) float32, uniform in +-COMMAND_RANGE; draw index
+    2^32 + 3 draw + k of each env's stream."""
+    seeds = env_seeds(config, n_envs, env0)[:, None]
+    k = np.uint64(1 << 32) + np.uint64(3 * draw) + np.arange(3, dtype=np.uint64)[None, :]
+    u = uniform01(seeds, k)
+    return _f32((2.0 * u - 1.0) * np.array(COMMAND_RANGE)[None, :])
+
+
+def policy_actions(m: Model, config: int, n_envs: int, t0: int, n_steps: int, env0: int = 0) -> np.ndarray:
+    """Policy outputs [n_steps, N, nu] float32, uniform in [-1, 1]; draw index
+    2^33 + t nu + j of each env's stream."""
+    seeds = env_seeds(config, n_envs, env0)[None, :, None]
+    nu = m.nu
+    t = np.arange(t0, t0 + n_steps, dtype=np.uint64)[:, None, None]
+    j = np.arange(nu, dtype=np.uint64)[None, None, :]
+    u = uniform01(seeds, np.uint64(1 << 33) + t * np.uint64(nu) + j)
+    return _f32(2.0 * u - 1.0)
+
+
 def model(name: str) -> Model:
     return MODELS[name]()
 
