@@ -209,6 +209,59 @@ def measure_mixed(dev, steps: int = 200):
             "envs_per_cta": epc or "default (one wave)", "launches": steps}
 
 
+def measure_env_layer(dev, n: int = 8192, steps: int = 200, specialize: bool = True):
+    """The locomotion task around the step (pg_env_step: joint targets, physics, reward table,
+    termination, auto-reset and observation in one launch) against the plain step on the same
+    8192 quadrupeds, same policy actions and commands, both with the model-specialised kernels.
+    Time per control step with CUDA events around `steps` back-to-back launches (inputs are
+    device-resident; the state and task arrays, a few MB, stay in L2)."""
+    import torch
+    from paper_2502_08844_b300 import core
+    m = W.quadruped()
+    cm = core.CompiledModel(m)
+    batch = core.Batch([(cm, n)])
+    if specialize:
+        batch.specialize()
+    task = core.Task(cm, W.quadruped_task(episode_length=1000))
+    st = core.State(batch, dev)
+    ld = st.ld
+    q0, v0 = W.initial_state(m, 1, n)
+    Q0 = torch.from_numpy(core.to_soa(q0, ld, batch.nq_max)).to(dev)
+    V0 = torch.from_numpy(core.to_soa(v0, ld, batch.nv_max)).to(dev)
+    cmd = torch.from_numpy(core.to_soa(W.commands(1, n), ld, 3)).to(dev)
+    A = np.zeros((steps, m.nu, ld), np.float32)
+    A[:, :, :n] = W.policy_actions(m, 1, n, 0, steps).transpose(0, 2, 1)
+    act = torch.from_numpy(A).to(dev)
+    ctrl = torch.from_numpy(task.src.q_default[None, :, None] + task.src.action_scale * A).to(dev).contiguous()
+    ts = torch.zeros((task.state_rows, ld), device=dev)
+    obs = torch.zeros((task.nobs, ld), device=dev)
+    rew, done, trunc = (torch.zeros(ld, device=dev) for _ in range(3))
+
+    def env_run():
+        core.env_reset(batch, task, st, ts, Q0, V0, cmd, obs)
+        for t in range(steps):
+            core.env_step(batch, task, st, ts, act[t], cmd, Q0, V0, 0, obs, rew, done, trunc)
+
+    def plain_run():
+        core.reset(batch, st, Q0, V0)
+        for t in range(steps):
+            core.step(batch, st, ctrl[t], 0)
+
+    def timed(f):
+        f()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(); f(); b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3
+
+    t_env, t_plain = timed(env_run), timed(plain_run)
+    return {"value": n * steps / t_env, "unit": "env-steps/s", "plain_step_value": n * steps / t_plain,
+            "overhead": t_env / t_plain - 1.0, "envs": n, "steps": steps, "episode_length": 1000,
+            "kernel": "model-specialised" if specialize else "generic",
+            "note": "pg_env_step vs pg_step on identical targets (absolute mapping); reset launch included"}
+
+
 def run_reference(args):
     """Reference arm: the FP64 oracle as it stands, timed on the host cores."""
     ws, rank, _ = dist_env()
@@ -413,6 +466,8 @@ def run_ours(args):
             "adjoint_forward_ratio": None}
     if not args.no_mixed:
         line["mixed_batch"] = measure_mixed(dev)
+    if not args.no_env:
+        line["env_layer"] = measure_env_layer(dev, specialize=kernel.startswith("model-specialised"))
     if not args.no_adjoint:
         adj = measure_adjoint(dev, specialize=kernel.startswith("model-specialised"))
         line["adjoint_forward_ratio"] = adj["ratio"]
@@ -437,6 +492,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-env", action="store_true", help="skip the locomotion-task measurement")
     ap.add_argument("--generic-kernel", action="store_true", help="skip pg_batch_specialize")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -135,6 +135,35 @@ typedef struct pg_state {
                          += Newton iterations, += constraint rows, += rows * iterations      */
 } pg_state;
 
+/* ---- locomotion task around the step (pg_env_step) ---------------------------------- */
+enum { PG_ACTION_ABSOLUTE = 0, PG_ACTION_RELATIVE = 1 };
+/* Reward terms of the locomotion reward table (App. B, "Reward and Termination"), in the order
+ * of pg_task_desc.weight and of pg_env_step's optional terms output.  Each is the table's
+ * expression without its coefficient k (the coefficient is the weight):
+ *   LIN_VEL      exp(-|cmd_xy - v_xy|^2 / sigma_lin_vel), v in the base frame
+ *   ANG_VEL      exp(-(cmd_wz - w_z)^2 / sigma_ang_vel), w in the base frame
+ *   AIR_TIME     sum over feet of clip((T_air - air_time_min) * C_touchdown, 0,
+ *                air_time_max - air_time_min), C_touchdown = 1 on the step a foot lands
+ *   CLEARANCE    sum over feet of (p_fz - clearance_height)^2 * |v_f,xy|^0.5
+ *   SLIP         sum over feet of C_f |v_f,xy|^2, C_f = 1 while the foot touches the ground
+ *   ORIENTATION  |g_xy|^2 of the gravity direction in the base frame
+ *   TORQUE       |tau|^2 of the PD actuator torques at the step's final state
+ *   JOINT_POS    |q - q_default|^2 over the actuated joints
+ *   ACTION_RATE  |a_t - a_{t-1}|^2
+ *   ENERGY       sum over actuated joints of |qdot_j tau_j|
+ *   POSE         exp(-|q - q_default|^2)
+ *   TERMINATION  1 when the episode terminated on this step (not when truncated)
+ *   STAND_STILL  |cmd_xy| (as printed in the table)
+ *   LIN_Z        v_z^2, base frame
+ *   ANG_XY       w_x^2 + w_y^2, base frame
+ * The reward is max(sum_i weight_i term_i, 0) (the table's weighted sum, clipped at zero). */
+enum {
+  PG_R_LIN_VEL = 0, PG_R_ANG_VEL, PG_R_AIR_TIME, PG_R_CLEARANCE, PG_R_SLIP, PG_R_ORIENTATION, PG_R_TORQUE,
+  PG_R_JOINT_POS, PG_R_ACTION_RATE, PG_R_ENERGY, PG_R_POSE, PG_R_TERMINATION, PG_R_STAND_STILL, PG_R_LIN_Z,
+  PG_R_ANG_XY, PG_NTERMS
+};
+#define PG_MAX_FEET 8
+
 #ifndef __CUDACC_RTC__   /* host API (not seen by the run-time kernel compiler) */
 
 /* Validate a description and build the library's model (host tables and a device copy).
@@ -165,10 +194,11 @@ void pg_batch_free(pg_batch* batch);
  * A first compile takes seconds, so call this before any stream capture and outside timed
  * regions.
  *
- * Scope. Only single-model batches, and only the production step: the tape (pg_step_vjp) and
- * debug kernels stay generic. A mixed batch keeps the generic kernel, whose one body all its
- * models share: one specialised body per model was measured slower, as blocks of different
- * models on one SM evict each other's code from the instruction cache.
+ * Scope. Only single-model batches. The specialised build covers the step, the environment
+ * step (pg_env_step) and, for models inside the adjoint's scope, the tape replay and reverse
+ * sweep of pg_step_vjp; the debug kernel stays generic. A mixed batch keeps the generic kernel,
+ * whose one body all its models share: one specialised body per model was measured slower, as
+ * blocks of different models on one SM evict each other's code from the instruction cache.
  *
  * Errors. PG_EUNSUPPORTED (a mixed batch; NVRTC missing or failing, with its log in
  * pg_last_error; the batch then keeps the generic kernel), PG_ECUDA. */
@@ -260,6 +290,84 @@ int pg_step_vjp(pg_batch* batch, const pg_state* ckpt, const float* ctrl_dev, in
 int pg_step_vjp_noalloc(pg_batch* batch, const pg_state* ckpt, const float* ctrl_dev, int n_steps, int n_substeps,
                         const float* g_qpos_dev, const float* g_qvel_dev, float* adj_qpos_dev, float* adj_qvel_dev,
                         float* g_ctrl_dev, float* g_param_dev, void* stream);
+
+/* ---- locomotion task (the steps either side of the physics in the training loop) ----
+ *
+ * A task wraps one model's step with the environment logic of the paper's locomotion tasks
+ * (App. B, "Observation and Action" and "Reward and Termination"): the action-to-target
+ * mapping, the observation, the reward table, termination when the robot turns over, and
+ * automatic reset.  pg_env_step runs all of it inside the step kernel's launch, before and
+ * after the physics substeps.
+ *
+ * Task description (host memory, caller-owned, read only during pg_task_compile):
+ *   action_mode      PG_ACTION_ABSOLUTE: q_des = q_default + action_scale * a_t (joystick
+ *                    tasks); PG_ACTION_RELATIVE: q_des = q_des_prev + action_scale * a_t.
+ *                    q_des is clipped to each actuator's ctrlrange when it is limited, and
+ *                    is the PD target of the step (eq. pd_mapping).
+ *   q_default        [nu] default joint targets (also the reset value of q_des).
+ *   nfeet, foot_geom [nfeet] (<= PG_MAX_FEET) sphere geoms at the feet. A foot's height is its
+ *                    sphere's lowest point above the world plane z = 0; it touches the ground
+ *                    while that height is below contact_height.
+ *   clearance_height desired swing height of the feet (p_des_z of the clearance term).
+ *   sigma_lin_vel, sigma_ang_vel, air_time_min, air_time_max: reward parameters.
+ *   weight           [PG_NTERMS] weights of the reward terms (see the PG_R_* list).
+ *   episode_length   control steps after which an episode is truncated (>= 1).
+ * The model must have a free joint on body 1 (the base) and only PD position actuators on
+ * hinge or slide joints.
+ * Errors: PG_EINVAL (malformed description), PG_EUNSUPPORTED (model outside that shape). */
+typedef struct pg_task_desc {
+  int action_mode;
+  float action_scale;
+  const float* q_default;
+  int nfeet;
+  const int* foot_geom;
+  float contact_height, clearance_height;
+  float sigma_lin_vel, sigma_ang_vel, air_time_min, air_time_max;
+  float weight[PG_NTERMS];
+  int episode_length;
+} pg_task_desc;
+
+typedef struct pg_task pg_task;   /* opaque, library-owned */
+
+typedef struct pg_task_sizes {
+  int nobs;         /* observation rows: 3 gravity + 3 linear + 3 angular velocity (base
+                       frame) + nu joint positions (q - q_default) + nu joint velocities +
+                       nu previous action + 3 command = 12 + 3 nu                         */
+  int nterms;       /* PG_NTERMS                                                          */
+  int state_rows;   /* rows of the per-env task state: q_des [nu], previous action [nu],
+                       foot air time [nfeet], foot contact [nfeet], episode step [1]       */
+} pg_task_sizes;
+
+int pg_task_compile(const pg_model* model, const pg_task_desc* desc, pg_task** out);
+int pg_task_info(const pg_task* task, pg_task_sizes* out);
+void pg_task_free(pg_task* task);
+
+/* Start every environment of the batch on its initial state: state <- (qpos0, qvel0), warm
+ * start and status zeroed; task state: q_des <- q_default, previous action, air time, contact
+ * and episode step <- 0; obs <- the observation of the initial state with command cmd.
+ * Arguments (device memory, [rows][ld]): task_state [state_rows], qpos0 [nq], qvel0 [nv],
+ * cmd [3] (vx, vy, wz), obs [nobs].  The batch must hold the task's model only.
+ * Errors: PG_EINVAL, PG_EUNSUPPORTED (another model in the batch), PG_ECUDA. */
+int pg_env_reset(const pg_batch* batch, const pg_task* task, pg_state* state, float* task_state_dev,
+                 const float* qpos0_dev, const float* qvel0_dev, const float* cmd_dev, float* obs_dev, void* stream);
+
+/* One environment step of every env, in one kernel launch:
+ *   1. q_des from the actions a_t ([nu][ld], in [-1, 1] by convention) by action_mode;
+ *   2. n_substeps physics substeps with q_des as the PD targets (as pg_step);
+ *   3. on the final state: the reward terms, the reward, termination (the base's z axis points
+ *      below the horizon, or a non-finite state) and truncation (episode_length reached);
+ *   4. environments that are done start over from (qpos0, qvel0) as in pg_env_reset;
+ *   5. obs of every env's current state (after any reset), with the action just applied as
+ *      the previous action (zero after a reset).
+ * Outputs ([rows][ld] device memory): obs [nobs], reward [1], done [1] (1 when the episode
+ * ended on this step: terminated or truncated), truncated [1] (1 when it ended by
+ * episode_length only), terms [PG_NTERMS] (unweighted reward terms, or NULL).
+ * reward, done, truncated and terms describe the transition; obs describes the state the next
+ * action acts on.  Errors as pg_env_reset. */
+int pg_env_step(const pg_batch* batch, const pg_task* task, pg_state* state, float* task_state_dev,
+                const float* action_dev, const float* cmd_dev, const float* qpos0_dev, const float* qvel0_dev,
+                int n_substeps, float* obs_dev, float* reward_dev, float* done_dev, float* truncated_dev,
+                float* terms_dev, void* stream);
 
 const char* pg_last_error(void);
 

@@ -49,9 +49,26 @@ class pg_state(C.Structure):
                 ("n", C.c_int64), ("ld", C.c_int64), ("stats", C.c_void_p)]
 
 
+PG_NTERMS = 15
+PG_MAX_FEET = 8
+
+
+class pg_task_desc(C.Structure):
+    _fields_ = [("action_mode", C.c_int), ("action_scale", C.c_float), ("q_default", C.c_void_p),
+                ("nfeet", C.c_int), ("foot_geom", C.c_void_p), ("contact_height", C.c_float),
+                ("clearance_height", C.c_float), ("sigma_lin_vel", C.c_float), ("sigma_ang_vel", C.c_float),
+                ("air_time_min", C.c_float), ("air_time_max", C.c_float), ("weight", C.c_float * PG_NTERMS),
+                ("episode_length", C.c_int)]
+
+
+class pg_task_sizes(C.Structure):
+    _fields_ = [("nobs", C.c_int), ("nterms", C.c_int), ("state_rows", C.c_int)]
+
+
 EXPORTS = ["pg_model_compile", "pg_model_info", "pg_model_free", "pg_batch_compile", "pg_batch_info",
            "pg_batch_free", "pg_reset", "pg_step", "pg_debug_substep", "pg_step_host", "pg_step_vjp",
-           "pg_step_vjp_noalloc", "pg_batch_specialize", "pg_last_error"]
+           "pg_step_vjp_noalloc", "pg_batch_specialize", "pg_task_compile", "pg_task_info", "pg_task_free",
+           "pg_env_reset", "pg_env_step", "pg_last_error"]
 
 if not os.path.exists(LIB_PATH):
     raise ImportError("libpg.so is not built (run `python -m paper_2502_08844_b300.build` or "
@@ -76,6 +93,13 @@ _lib.pg_step_host.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_v
 _lib.pg_step_vjp.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_int, C.c_int] + [C.c_void_p] * 7
 _lib.pg_batch_specialize.argtypes = [C.c_void_p]
 _lib.pg_step_vjp_noalloc.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_int, C.c_int] + [C.c_void_p] * 7
+_lib.pg_task_compile.argtypes = [C.c_void_p, C.POINTER(pg_task_desc), C.POINTER(C.c_void_p)]
+_lib.pg_task_info.argtypes = [C.c_void_p, C.POINTER(pg_task_sizes)]
+_lib.pg_task_free.argtypes = [C.c_void_p]
+_lib.pg_task_free.restype = None
+_lib.pg_env_reset.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(pg_state)] + [C.c_void_p] * 6
+_lib.pg_env_step.argtypes = ([C.c_void_p, C.c_void_p, C.POINTER(pg_state)] + [C.c_void_p] * 5 + [C.c_int] +
+                             [C.c_void_p] * 6)
 for _n in EXPORTS:
     if _n not in ("pg_last_error", "pg_model_free", "pg_batch_free"):
         getattr(_lib, _n).restype = C.c_int
@@ -163,3 +187,31 @@ def pg_step_vjp_noalloc(batch, ckpt: pg_state, ctrl_ptr, n_steps: int, n_substep
 
 def pg_batch_specialize(batch) -> None:
     _check(_lib.pg_batch_specialize(batch), "pg_batch_specialize")
+
+
+def pg_task_compile(model, desc: pg_task_desc) -> C.c_void_p:
+    out = C.c_void_p()
+    _check(_lib.pg_task_compile(model, C.byref(desc), C.byref(out)), "pg_task_compile")
+    return out
+
+
+def pg_task_info(task) -> pg_task_sizes:
+    s = pg_task_sizes()
+    _check(_lib.pg_task_info(task, C.byref(s)), "pg_task_info")
+    return s
+
+
+def pg_task_free(task) -> None:
+    _lib.pg_task_free(task)
+
+
+def pg_env_reset(batch, task, state: pg_state, task_state_ptr, qpos0_ptr, qvel0_ptr, cmd_ptr, obs_ptr, stream) -> None:
+    _check(_lib.pg_env_reset(batch, task, C.byref(state), task_state_ptr, qpos0_ptr, qvel0_ptr, cmd_ptr, obs_ptr,
+                             stream), "pg_env_reset")
+
+
+def pg_env_step(batch, task, state: pg_state, task_state_ptr, action_ptr, cmd_ptr, qpos0_ptr, qvel0_ptr,
+                n_substeps: int, obs_ptr, reward_ptr, done_ptr, truncated_ptr, terms_ptr, stream) -> None:
+    _check(_lib.pg_env_step(batch, task, C.byref(state), task_state_ptr, action_ptr, cmd_ptr, qpos0_ptr, qvel0_ptr,
+                            int(n_substeps), obs_ptr, reward_ptr, done_ptr, truncated_ptr, terms_ptr, stream),
+           "pg_env_step")

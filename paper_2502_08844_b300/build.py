@@ -23,6 +23,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # headers compiled again at run time by pg_batch_specialize (NVRTC), embedded in the library
 EMBEDDED = [("pg.h", os.path.join(INCLUDE, "pg.h")), ("pg_internal.h", os.path.join(CSRC, "pg_internal.h")),
             ("step_device.cuh", os.path.join(CSRC, "step_device.cuh")),
+            ("env_device.cuh", os.path.join(CSRC, "env_device.cuh")),
             ("step_kernel_body.cuh", os.path.join(CSRC, "step_kernel_body.cuh")),
             ("adjoint_body.cuh", os.path.join(CSRC, "adjoint_body.cuh"))]
 BUILD_DIR = os.path.join(HERE, "_build")

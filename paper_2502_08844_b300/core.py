@@ -124,6 +124,56 @@ class State:
                               None if self.stats is None else self.stats.data_ptr())
 
 
+class Task:
+    """A locomotion task (pg_task_compile) around a compiled model's step: the action mapping,
+    the feet and the reward table's weights of a workloads.Task."""
+
+    def __init__(self, model: CompiledModel, task: W.Task):
+        self.model, self.src = model, task
+        self._q_default = np.ascontiguousarray(task.q_default, np.float32)
+        self._feet = np.ascontiguousarray(task.foot_geom, np.int32)
+        w = (C.c_float * _capi.PG_NTERMS)(*[float(x) for x in task.weight])
+        d = _capi.pg_task_desc(int(task.action_mode), float(task.action_scale),
+                               self._q_default.ctypes.data_as(C.c_void_p), int(task.nfeet),
+                               self._feet.ctypes.data_as(C.c_void_p), float(task.contact_height),
+                               float(task.clearance_height), float(task.sigma_lin_vel), float(task.sigma_ang_vel),
+                               float(task.air_time_min), float(task.air_time_max), w, int(task.episode_length))
+        self.handle = _capi.pg_task_compile(model.handle, d)
+        s = _capi.pg_task_info(self.handle)
+        self.nobs, self.nterms, self.state_rows = s.nobs, s.nterms, s.state_rows
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            _capi.pg_task_free(h)
+            self.handle = None
+
+
+def env_reset(batch: Batch, task: Task, state: State, task_state: torch.Tensor, qpos0: torch.Tensor,
+              qvel0: torch.Tensor, cmd: torch.Tensor, obs: torch.Tensor, stream=None) -> None:
+    """pg_env_reset: every environment starts an episode at (qpos0, qvel0); obs is written."""
+    ld = state.ld
+    assert task_state.shape == (task.state_rows, ld) and obs.shape == (task.nobs, ld) and cmd.shape == (3, ld)
+    assert qpos0.shape == state.qpos.shape and qvel0.shape == state.qvel.shape
+    _capi.pg_env_reset(batch.handle, task.handle, state.c(), _ptr(task_state), _ptr(qpos0.contiguous()),
+                       _ptr(qvel0.contiguous()), _ptr(cmd.contiguous()), _ptr(obs), _stream_ptr(stream))
+
+
+def env_step(batch: Batch, task: Task, state: State, task_state: torch.Tensor, actions: torch.Tensor,
+             cmd: torch.Tensor, qpos0: torch.Tensor, qvel0: torch.Tensor, n_substeps: int, obs: torch.Tensor,
+             reward: torch.Tensor, done: torch.Tensor, truncated: torch.Tensor, terms: Optional[torch.Tensor] = None,
+             stream=None) -> None:
+    """pg_env_step: targets, physics, reward, termination, reset and observation in one launch."""
+    ld = state.ld
+    assert actions.dtype == torch.float32 and actions.is_contiguous() and actions.shape == (task.model.nu, ld)
+    assert task_state.shape == (task.state_rows, ld) and obs.shape == (task.nobs, ld) and cmd.shape == (3, ld)
+    assert reward.numel() >= ld and done.numel() >= ld and truncated.numel() >= ld
+    assert terms is None or terms.shape == (task.nterms, ld)
+    _capi.pg_env_step(batch.handle, task.handle, state.c(), _ptr(task_state), _ptr(actions), _ptr(cmd.contiguous()),
+                      _ptr(qpos0.contiguous()), _ptr(qvel0.contiguous()), int(n_substeps), _ptr(obs), _ptr(reward),
+                      _ptr(done), _ptr(truncated), _ptr(terms), _stream_ptr(stream))
+
+
 def reset(batch: Batch, state: State, qpos0: torch.Tensor, qvel0: torch.Tensor, mask: Optional[torch.Tensor] = None,
           stream=None) -> None:
     assert qpos0.shape == state.qpos.shape and qvel0.shape == state.qvel.shape

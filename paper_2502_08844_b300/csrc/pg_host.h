@@ -16,6 +16,12 @@ struct pg_model {
   uint32_t* d_blob = nullptr;   // device copy of the blob
 };
 
+struct pg_task {
+  const pg_model* model;
+  pg::EnvTask task;
+  int nobs, state_rows;
+};
+
 struct pg_batch {
   std::vector<const pg_model*> models;
   std::vector<int64_t> counts, env_off;
@@ -39,6 +45,7 @@ struct pg_batch {
   cudaKernel_t spec_kernel = nullptr;
   cudaKernel_t spec_kernel_tape = nullptr;   // the same with the substep tape (adjoint replay)
   cudaKernel_t spec_kernel_vjp = nullptr;    // the adjoint's reverse sweep (NULL outside its scope)
+  cudaKernel_t spec_kernel_env = nullptr;    // the environment step of a locomotion task
   // staging buffer of the host-buffer path (allocated on its first use)
   float* d_ctrl_stage = nullptr;
   size_t ctrl_stage_floats = 0;
@@ -60,6 +67,9 @@ cudaError_t launch_debug(const pg_batch* b, const pg_state* s, const float* ctrl
 cudaError_t launch_reset(const pg_batch* b, const pg_state* s, const uint8_t* mask, const float* qpos0,
                          const float* qvel0, cudaStream_t st);
 cudaError_t configure_step_kernels(size_t smem_bytes);
+// environment step and reset of a locomotion task (step.cu)
+cudaError_t launch_env_step(const pg_batch* b, const pg_state* s, const EnvArgs& E, int n_substeps, cudaStream_t st);
+cudaError_t launch_env_reset(const pg_batch* b, const pg_state* s, const EnvArgs& E, cudaStream_t st);
 cudaError_t launch_step_tape(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, float* tape,
                              int tape_rows, cudaStream_t st);
 // the kernels of step_kernels.cuh, compiled without (step.cu) and with (step_elliptic.cu) the
@@ -75,6 +85,9 @@ cudaError_t launch_step_tape(const pg_batch* b, const pg_state* s, const float* 
   cudaError_t step_spec(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st);\
   cudaError_t step_spec_tape(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, float* tape,\
                              int tape_rows, cudaStream_t st);                                                   \
+  cudaError_t step_env(const pg_batch* b, const pg_state* s, const EnvArgs& E, int n_substeps, cudaStream_t st);  \
+  cudaError_t step_spec_env(const pg_batch* b, const pg_state* s, const EnvArgs& E, int n_substeps,            \
+                            cudaStream_t st);                                                                  \
   }
 PG_DECLARE_STEP_KERNELS(pyramidal)
 PG_DECLARE_STEP_KERNELS(elliptic)

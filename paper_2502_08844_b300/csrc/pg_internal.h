@@ -72,6 +72,35 @@ static_assert(sizeof(ModelHdr) % 4 == 0, "header must be whole words");
 // box corner a plane contact comes from; 0 otherwise)
 constexpr int kConFloats = 9;
 
+// A locomotion task (pg_env_step) as the step kernel reads it: the action mapping, the feet
+// and the reward table's parameters, in kernel-parameter space beside the model blobs.
+struct EnvTask {
+  int mode, nu, nfeet, episode_length;
+  int base_qpos, base_dof;          // the free joint's qpos and dof addresses
+  float scale, contact_height, clearance, sig_v, sig_w, air_min, air_max;
+  float weight[PG_NTERMS];
+  float q_default[kMaxNv];
+  int foot_body[PG_MAX_FEET];
+  int foot_lastdof[PG_MAX_FEET];    // last dof of the chain that moves the foot's body
+  float foot_pos[3 * PG_MAX_FEET];  // sphere centre in its body's frame
+  float foot_r[PG_MAX_FEET];
+};
+
+// the task's per-call arrays ([rows][ld] device memory, see pg_env_step)
+struct EnvArgs {
+  float* state;            // q_des [nu] | previous action [nu] | air time [nfeet] | contact [nfeet] | step [1]
+  const float* actions;    // [nu]
+  const float* cmd;        // [3]
+  const float* qpos0;      // [nq] reset state
+  const float* qvel0;      // [nv]
+  float* obs;              // [12 + 3 nu]
+  float* reward;           // [1]
+  float* done;             // [1]
+  float* truncated;        // [1]
+  float* terms;            // [PG_NTERMS] or NULL
+  EnvTask task;
+};
+
 // one thread block's work: `count` consecutive envs starting at `env0` of model `model`
 struct Tile {
   int model;

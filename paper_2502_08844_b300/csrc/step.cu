@@ -19,6 +19,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cstring>
 
 #include "pg_host.h"
@@ -43,6 +44,27 @@ __global__ void reset_kernel(float* qpos, float* qvel, float* warm, uint32_t* st
   status[env] = 0u;
 }
 
+// a new episode for every environment of a single-model batch, and its first observation
+struct EnvResetArgs {
+  float* qpos;
+  float* qvel;
+  float* warm;
+  uint32_t* status;
+  int64_t ld, n;
+  EnvArgs env;
+  uint32_t blob[kMaxParamWords];   // the model's blob (the actuators' addresses)
+};
+static_assert(sizeof(EnvResetArgs) <= 32764, "the reset's argument block must fit the kernel parameter space");
+
+__global__ void env_reset_kernel(const __grid_constant__ EnvResetArgs A) {
+  const int64_t env = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (env >= A.n) return;
+  const ModelHdr& h = *reinterpret_cast<const ModelHdr*>(A.blob);
+  Ctx c{h, 0, reinterpret_cast<const int*>(A.blob), reinterpret_cast<const float*>(A.blob), nullptr, nullptr, A.ld, env};
+  env_restart(c, A.env, A.qpos, A.qvel, A.warm, A.status);
+  env_observe(c, A.env.task, A.qpos, A.qvel, nullptr, A.env.cmd, A.env.obs);
+}
+
 }  // namespace
 
 // a batch with an elliptic-cone model runs the kernels compiled with the elliptic cone; all
@@ -63,6 +85,22 @@ cudaError_t launch_step_tape(const pg_batch* b, const pg_state* s, const float* 
   if (b->spec_kernel_tape) return pyramidal::step_spec_tape(b, s, ctrl, n_substeps, tape, tape_rows, st);
   return b->has_elliptic ? elliptic::step_tape(b, s, ctrl, n_substeps, tape, tape_rows, st)
                          : pyramidal::step_tape(b, s, ctrl, n_substeps, tape, tape_rows, st);
+}
+
+cudaError_t launch_env_step(const pg_batch* b, const pg_state* s, const EnvArgs& E, int n_substeps, cudaStream_t st) {
+  if (b->spec_kernel_env) return pyramidal::step_spec_env(b, s, E, n_substeps, st);
+  return b->has_elliptic ? elliptic::step_env(b, s, E, n_substeps, st) : pyramidal::step_env(b, s, E, n_substeps, st);
+}
+
+cudaError_t launch_env_reset(const pg_batch* b, const pg_state* s, const EnvArgs& E, cudaStream_t st) {
+  if (s->n == 0) return cudaSuccess;
+  static thread_local EnvResetArgs A;
+  A.qpos = s->qpos; A.qvel = s->qvel; A.warm = s->qacc_warm; A.status = s->status;
+  A.ld = s->ld; A.n = s->n; A.env = E;
+  std::memcpy(A.blob, b->blob_host.data(), std::min(b->blob_host.size(), (size_t)kMaxParamWords) * sizeof(uint32_t));
+  const int threads = 128;
+  env_reset_kernel<<<(unsigned)((s->n + threads - 1) / threads), threads, 0, st>>>(A);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_debug(const pg_batch* b, const pg_state* s, const float* ctrl, int64_t env, float* out, cudaStream_t st) {

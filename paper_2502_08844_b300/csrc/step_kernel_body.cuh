@@ -5,7 +5,7 @@
 // defined by the generated source) instead of the kernel argument, so the compiler folds every
 // header field, table entry and workspace offset.
 #pragma once
-#include "step_device.cuh"
+#include "env_device.cuh"
 
 namespace pg {
 namespace {
@@ -28,16 +28,21 @@ struct StepArgs {
   float* tape;                        // optional record of every substep (see TAPE below)
   int tape_rows, tape_nq, tape_nv;    // rows per substep entry; the batch's nq_max, nv_max
   int model_off[kMaxModels];          // word offset of each model's blob in `blob`
+  EnvArgs env;                        // the locomotion task of an environment step (ENV below)
   uint32_t blob[kMaxParamWords];      // the batch's model blobs (header + tables)
 };
+static_assert(sizeof(StepArgs) <= 32764, "the step's argument block must fit the kernel parameter space");
 
 // One thread per environment; a block steps the `count` consecutive environments of its tile.
 // TAPE: also record, for every substep s, the state it starts from and the acceleration the
 // solver returns, at tape[(s * tape_rows + row) * ld + env] with rows qpos [0, nq), qvel from
 // tape_nq, the warm start from tape_nq + tape_nv and the acceleration from tape_nq + 2 tape_nv
 // (the adjoint replays the substeps from this record).
+// ENV: an environment step of the locomotion task A.env: the joint targets from the actions
+// before the substeps (they are the PD targets), and after them the reward, termination,
+// automatic reset and observation (env_device.cuh).
 
-template <bool DEBUG, bool TAPE, int SPEC_M = 0>
+template <bool DEBUG, bool TAPE, int SPEC_M = 0, bool ENV = false>
 __device__ __forceinline__ void step_body(const StepArgs& A) {
   extern __shared__ __align__(16) float smem[];
   const Tile tile = DEBUG ? A.dbg_tile : A.tiles[blockIdx.x];
@@ -57,7 +62,9 @@ __device__ __forceinline__ void step_body(const StepArgs& A) {
   if (t >= tile.count) return;
   const int64_t env = tile.env0 + t;
   float* w = smem + warp * (S * h.ws_floats) + lane;
-  Ctx c{h, S, reinterpret_cast<const int*>(blob), reinterpret_cast<const float*>(blob), w, A.ctrl, A.ld, env};
+  Ctx c{h, S, reinterpret_cast<const int*>(blob), reinterpret_cast<const float*>(blob), w, ENV ? A.env.state : A.ctrl,
+        A.ld, env};
+  if (ENV) env_targets(c, A.env);
   for (int k = 0; k < h.nq; k++) W(qpos, k) = A.qpos[k * A.ld + env];
   uint32_t status = 0;
   bool warm_bad = false;
@@ -94,6 +101,7 @@ __device__ __forceinline__ void step_body(const StepArgs& A) {
   if (status) A.status[env] |= status;
   if (A.stats)
     for (int k = 0; k < 3; k++) A.stats[k * A.ld + env] += cnt[k];
+  if (ENV) env_finish(c, A.env, (float)nsub * h.h, A.qpos, A.qvel, A.warm, A.status);
 }
 
 }  // namespace

@@ -16,9 +16,9 @@
 namespace pg {
 namespace {
 
-template <bool DEBUG, bool TAPE>
+template <bool DEBUG, bool TAPE, bool ENV = false>
 __global__ void __launch_bounds__(kMaxEnvsPerCta) step_kernel(const __grid_constant__ StepArgs A) {
-  step_body<DEBUG, TAPE>(A);
+  step_body<DEBUG, TAPE, 0, ENV>(A);
 }
 
 }  // namespace
@@ -29,6 +29,8 @@ cudaError_t configure(size_t smem_bytes) {
   cudaError_t e = cudaFuncSetAttribute(step_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(step_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(step_kernel<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(step_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
 }
@@ -47,6 +49,7 @@ static void make_args(StepArgs& A, const pg_batch* b, const pg_state* s, const f
   A.dbg_tile = Tile{0, 0, 0, 0};
   A.tape = nullptr;
   A.tape_rows = A.tape_nq = A.tape_nv = 0;
+  A.env.state = nullptr;
   for (int k = 0; k < kMaxModels; k++) A.model_off[k] = k < (int)b->blob_off.size() ? b->blob_off[k] : 0;
   std::memcpy(A.blob, b->blob_host.data(), b->blob_host.size() * sizeof(uint32_t));
 }
@@ -96,6 +99,27 @@ cudaError_t step_tape(const pg_batch* b, const pg_state* s, const float* ctrl, i
   A.tape_nv = b->nv_max;
   step_kernel<false, true><<<b->ntiles, b->threads, b->smem_bytes, st>>>(A);
   return cudaGetLastError();
+}
+
+// an environment step of the locomotion task E (generic kernel, or the batch's specialised one)
+cudaError_t step_env(const pg_batch* b, const pg_state* s, const EnvArgs& E, int n_substeps, cudaStream_t st) {
+  if (b->ntiles == 0) return cudaSuccess;
+  static thread_local StepArgs A;
+  make_args(A, b, s, nullptr);
+  A.n_substeps = n_substeps;
+  A.env = E;
+  step_kernel<false, false, true><<<b->ntiles, b->threads, b->smem_bytes, st>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t step_spec_env(const pg_batch* b, const pg_state* s, const EnvArgs& E, int n_substeps, cudaStream_t st) {
+  if (b->ntiles == 0) return cudaSuccess;
+  static thread_local StepArgs A;
+  make_args(A, b, s, nullptr);
+  A.n_substeps = n_substeps;
+  A.env = E;
+  void* params[] = {&A};
+  return cudaLaunchKernel((const void*)b->spec_kernel_env, dim3(b->ntiles), dim3(b->threads), params, b->smem_bytes, st);
 }
 
 cudaError_t debug(const pg_batch* b, const pg_state* s, const float* ctrl, int64_t env, float* out, cudaStream_t st) {
