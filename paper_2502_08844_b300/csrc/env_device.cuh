@@ -95,7 +95,7 @@ __device__ void env_finish(const Ctx& c, const EnvArgs& E, float dt, float* qpos
   const int64_t ld = c.ld, env = c.env;
   const int nu = T.nu, nf = T.nfeet;
   float* st = E.state + env;
-  kinematics(c);   // body frames and motion subspaces of the final state
+  kinematics<false>(c);   // body frames and motion subspaces of the final state
   bool finite = true;
   for (int k = 0; k < h.nq; k++) finite = finite && isfinite(W(qpos, k));
   for (int k = 0; k < h.nv; k++) finite = finite && isfinite(W(qvel, k));

@@ -375,8 +375,10 @@ __device__ __forceinline__ void body_frame(const Ctx& c, int b, float3& x, Quat&
 // body offset and its joints (hinge: rotation about the axis through the anchor; slide:
 // translation; free: qpos position and normalised quaternion).  On the way: the motion
 // subspace of every dof (cdof, angular;linear about the tree's reference point o) and the
-// body's spatial inertia about o (Ixx Iyy Izz Ixy Ixz Iyz, m c, m).
+// body's spatial inertia about o (Ixx Iyy Izz Ixy Ixz Iyz, m c, m); INERTIA = false skips the
+// inertias (frames and motion subspaces only).
 // ---------------------------------------------------------------------------------------
+template <bool INERTIA = true>
 __device__ void kinematics(const Ctx& c) {
   const ModelHdr& h = c.h;
   for (int b = 1; b < h.nbody; b++) {
@@ -422,6 +424,7 @@ __device__ void kinematics(const Ctx& c) {
     S3(c, h.w_xpos + 3 * b, x);
     const int qo = h.w_xquat + 4 * b;
     c.w[qo * c.S] = q.w; c.w[(qo + 1) * c.S] = q.x; c.w[(qo + 2) * c.S] = q.y; c.w[(qo + 3) * c.S] = q.z;
+    if (!INERTIA) continue;
     // spatial inertia about o: I_com(world) + m (|c|^2 1 - c c^T), h = m c
     float R[9];
     qmat(q, R);
