@@ -35,6 +35,7 @@ class _Desc(C.Structure):
         ("timestep", C.c_double), ("gravity", _dp), ("iterations", C.c_int), ("cone", C.c_int),
         ("impratio", C.c_double), ("solref", _dp), ("solimp", _dp), ("margin", C.c_double),
         ("max_contacts", C.c_int),
+        ("hfield_nrow", C.c_int), ("hfield_ncol", C.c_int), ("hfield_data", _dp),
     ]
 
 
@@ -64,6 +65,7 @@ def lib():
         L.orc_point_jacobian.argtypes = [C.c_void_p, _dp, C.c_int, _dp, _dp, _dp]
         L.orc_integrate_pos.argtypes = [C.c_void_p, _dp, _dp, C.c_double]
         L.orc_collide.argtypes = [C.c_int, _dp, _dp, _dp, C.c_int, _dp, _dp, _dp, _dp]
+        L.orc_collide_hfield.argtypes = [_dp, _dp, _dp, C.c_int, C.c_int, _dp, C.c_int, _dp, _dp, _dp, _dp]
         L.orc_solve.argtypes = [C.c_int, _dp, _dp, C.c_int, _dp, _dp, _dp, _dp, C.c_int, _dp, _dp, _ip, _ip, _dp]
         L.orc_cost.restype = C.c_double
         L.orc_cost.argtypes = [C.c_int, _dp, _dp, C.c_int, _dp, _dp, _dp, _dp, _ip, _dp]
@@ -127,6 +129,9 @@ class OracleModel:
             I("acl", m.act_ctrllimited), D("acr", m.act_ctrlrange),
             float(m.timestep), D("grav", m.gravity), int(m.iterations), int(m.cone), float(m.impratio),
             D("sref", m.solref), D("simp", m.solimp), float(m.margin), int(m.max_contacts),
+            0 if getattr(m, "hfield", None) is None else int(m.hfield.shape[0]),
+            0 if getattr(m, "hfield", None) is None else int(m.hfield.shape[1]),
+            None if getattr(m, "hfield", None) is None else D("hf", m.hfield),
         )
         err = C.create_string_buffer(256)
         h = L.orc_model_new(C.byref(desc), err, 256)
@@ -252,6 +257,18 @@ def collide(t1, R1, p1, s1, t2, R2, p2, s2):
     out = np.zeros((4, 13))
     n = lib().orc_collide(int(t1), _pd(_d(R1)), _pd(_d(p1)), _pd(_d(list(s1) + [0] * (3 - len(s1)))), int(t2),
                           _pd(_d(R2)), _pd(_d(p2)), _pd(_d(list(s2) + [0] * (3 - len(s2)))), _pd(out))
+    if n < 0:
+        raise ValueError("unsupported pair")
+    return out[:n]
+
+
+def collide_hfield(R1, p1, size, elev, t2, R2, p2, s2):
+    """Model-free heightfield (geom1) against a sphere or capsule; [npts, 13] records as collide()."""
+    elev = _d(elev)
+    out = np.zeros((4, 13))
+    n = lib().orc_collide_hfield(_pd(_d(R1)), _pd(_d(p1)), _pd(_d(size)), int(elev.shape[0]), int(elev.shape[1]),
+                                 _pd(np.ascontiguousarray(elev)), int(t2), _pd(_d(R2)), _pd(_d(p2)),
+                                 _pd(_d(list(s2) + [0] * (3 - len(s2)))), _pd(out))
     if n < 0:
         raise ValueError("unsupported pair")
     return out[:n]

@@ -269,6 +269,25 @@ int orc_collide(int t1, const double* R1, const double* p1, const double* s1, in
   return n;
 }
 
+// Model-free collision of a heightfield (geom1: frame R1/p1, size s1, grid nrow x ncol of
+// elevations) with a sphere or capsule (geom2); the same records as orc_collide.
+int orc_collide_hfield(const double* R1, const double* p1, const double* s1, int nrow, int ncol, const double* elev,
+                       int t2, const double* R2, const double* p2, const double* s2, double* out) {
+  int n = orc::pair_max_points(orc::HFIELD, t2);
+  if (n < 0 || nrow < 2 || ncol < 2 || !elev) return -1;
+  orc::Xf<double> X1, X2;
+  for (int i = 0; i < 9; i++) { X1.R[i] = R1[i]; X2.R[i] = R2[i]; }
+  for (int i = 0; i < 3; i++) { X1.p[i] = p1[i]; X2.p[i] = p2[i]; }
+  orc::Contact<double> c[4];
+  orc::collide_pair(orc::HFIELD, X1, s1, t2, X2, s2, c, orc::HField{nrow, ncol, elev});
+  for (int i = 0; i < n; i++) {
+    double* o = out + 13 * i;
+    o[0] = c[i].dist;
+    for (int k = 0; k < 3; k++) { o[1 + k] = c[i].pos[k]; o[4 + k] = c[i].n[k]; o[7 + k] = c[i].t1[k]; o[10 + k] = c[i].t2[k]; }
+  }
+  return n;
+}
+
 // The Newton solver on raw data (M, a0, rows J/aref/D); cap < 0 selects the converged mode.
 // Rows from raw arrays; kind / mu NULL: every row a one-sided scalar row
 static orc::Rows<double> raw_rows(int nv, int nr, const double* J, const double* aref, const double* D, const int* kind,

@@ -93,12 +93,25 @@ std::string compile_model(const Desc& d, Model& m) {
   m.geom_size.assign(d.geom_size, d.geom_size + 3 * d.ngeom);
   m.geom_mass.assign(d.geom_mass, d.geom_mass + d.ngeom);
   for (int g = 0; g < m.ngeom; g++) {
-    if (m.geom_type[g] < PLANE || m.geom_type[g] > BOX) return "unknown geom type";
+    if (m.geom_type[g] < PLANE || m.geom_type[g] > HFIELD) return "unknown geom type";
     if (m.geom_body[g] < 0 || m.geom_body[g] >= m.nbody) return "geom_body out of range";
+    if (m.geom_type[g] == HFIELD) {
+      if (m.geom_body[g] != 0 || m.geom_mass[g] != 0) return "a heightfield must be a massless geom of the world";
+      if (d.hfield_nrow < 2 || d.hfield_ncol < 2 || !d.hfield_data) return "a heightfield geom needs a grid of at least 2 x 2";
+      if (!(m.geom_size[3 * g] > 0 && m.geom_size[3 * g + 1] > 0 && m.geom_size[3 * g + 2] >= 0))
+        return "heightfield size must be (hx > 0, hy > 0, hz >= 0)";
+    }
     double* q = &m.geom_quat[4 * g];
     double n = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
     if (!(n > 0)) return "geom_quat must be non-zero";
     for (int k = 0; k < 4; k++) q[k] /= n;
+  }
+  if (d.hfield_nrow >= 2 && d.hfield_ncol >= 2 && d.hfield_data) {
+    m.hf_nrow = d.hfield_nrow;
+    m.hf_ncol = d.hfield_ncol;
+    m.hfield.assign(d.hfield_data, d.hfield_data + (size_t)d.hfield_nrow * d.hfield_ncol);
+    for (double e : m.hfield)
+      if (!(e >= 0.0 && e <= 1.0)) return "heightfield elevations must lie in [0, 1]";
   }
   // mass properties: given, or the union of the body's geoms as uniform solids
   m.mass.assign(m.nbody, 0.0);
@@ -146,7 +159,7 @@ std::string compile_model(const Desc& d, Model& m) {
     int g1 = d.pair_geom[2 * p], g2 = d.pair_geom[2 * p + 1];
     if (g1 < 0 || g1 >= m.ngeom || g2 < 0 || g2 >= m.ngeom) return "pair geom out of range";
     int n = pair_max_points(m.geom_type[g1], m.geom_type[g2]);
-    if (n < 0) return "unsupported pair (geom1's type must not exceed geom2's: plane < sphere < capsule < box)";
+    if (n < 0) return "unsupported pair (geom1's type must not exceed geom2's: plane < sphere < capsule < box; a heightfield pairs as geom1 with spheres and capsules)";
     if (d.pair_condim[p] != 1 && d.pair_condim[p] != 3) return "pair_condim must be 1 or 3";
     m.pair_g1.push_back(g1);
     m.pair_g2.push_back(g2);

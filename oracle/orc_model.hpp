@@ -10,7 +10,7 @@
 namespace orc {
 
 enum { FREE = 0, HINGE = 1, SLIDE = 2 };
-enum { PLANE = 0, SPHERE = 1, CAPSULE = 2, BOX = 3 };
+enum { PLANE = 0, SPHERE = 1, CAPSULE = 2, BOX = 3, HFIELD = 4 };
 enum { MOTOR = 0, POSITION = 1 };
 enum { PYRAMIDAL = 0, ELLIPTIC = 1 };
 
@@ -33,6 +33,14 @@ struct Desc {
   const int* act_ctrllimited; const double* act_ctrlrange;
   double timestep; const double* gravity; int iterations; int cone; double impratio;
   const double* solref; const double* solimp; double margin; int max_contacts;
+  int hfield_nrow, hfield_ncol; const double* hfield_data;   // the model's heightfield (elevations)
+};
+
+// A heightfield grid: elevations e in [0, 1], row i at y = -hy + 2 hy i / (nrow - 1), column j at
+// x = -hx + 2 hx j / (ncol - 1) of the geom frame; the surface height is hz e (size = hx, hy, hz).
+struct HField {
+  int nrow = 0, ncol = 0;
+  const double* e = nullptr;
 };
 
 struct Model {
@@ -60,6 +68,9 @@ struct Model {
   int nlimited = 0;   // joints with limits (each contributes at most one active row)
   int rows_per_contact = 4;
   int nrow_max = 0;
+  int hf_nrow = 0, hf_ncol = 0;
+  std::vector<double> hfield;
+  HField hf() const { return HField{hf_nrow, hf_ncol, hfield.empty() ? nullptr : hfield.data()}; }
 };
 
 // Contact points a primitive pair can produce (the static slot count of the pair).
@@ -73,6 +84,8 @@ inline int pair_max_points(int t1, int t2) {
   if (t1 == SPHERE && t2 == BOX) return 1;
   if (t1 == CAPSULE && t2 == BOX) return 2;
   if (t1 == BOX && t2 == BOX) return 4;
+  if (t1 == HFIELD && t2 == SPHERE) return 1;
+  if (t1 == HFIELD && t2 == CAPSULE) return 2;
   return -1;
 }
 

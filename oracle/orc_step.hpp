@@ -512,10 +512,118 @@ template <class T> void box_box(const Xf<T>& XA, const double* hA, const Xf<T>& 
   }
 }
 
+// ---- heightfield ------------------------------------------------------------------
+// The surface is the grid's triangulation: cell (i, j) (i < nrow - 1, j < ncol - 1) with corners
+// v00 = (i, j), v01 = (i, j + 1), v10 = (i + 1, j), v11 = (i + 1, j + 1) is split along its
+// v00-v11 diagonal into (v00, v01, v11) and (v00, v11, v10).
+
+template <class T> V3<T> hf_vertex(const HField& hf, const double* size, int i, int j) {
+  const double dx = 2 * size[0] / (hf.ncol - 1), dy = 2 * size[1] / (hf.nrow - 1);
+  return V3<T>{T(-size[0] + j * dx), T(-size[1] + i * dy), T(size[2] * hf.e[(size_t)i * hf.ncol + j])};
+}
+
+template <class T> void hf_triangle(const HField& hf, const double* size, int i, int j, int t, V3<T> v[3]) {
+  v[0] = hf_vertex<T>(hf, size, i, j);
+  v[1] = t == 0 ? hf_vertex<T>(hf, size, i, j + 1) : hf_vertex<T>(hf, size, i + 1, j + 1);
+  v[2] = t == 0 ? hf_vertex<T>(hf, size, i + 1, j + 1) : hf_vertex<T>(hf, size, i + 1, j);
+}
+
+// closest point to p on the triangle v: the projection onto its plane when that falls inside
+// (all barycentric weights >= 0), else the nearest of the three edges' clamped projections
+template <class T> V3<T> closest_on_triangle(const V3<T>& p, const V3<T> v[3]) {
+  V3<T> n = cross(sub(v[1], v[0]), sub(v[2], v[0]));
+  T nn = dot(n, n);
+  V3<T> q = sub(p, scl(n, dot(n, sub(p, v[0])) / nn));
+  T w0 = dot(cross(sub(v[2], v[1]), sub(q, v[1])), n) / nn;
+  T w1 = dot(cross(sub(v[0], v[2]), sub(q, v[2])), n) / nn;
+  if (val(w0) >= 0 && val(w1) >= 0 && val(w0) + val(w1) <= 1) return q;
+  V3<T> best{};
+  double bd = 1e300;
+  for (int k = 0; k < 3; k++) {
+    const V3<T>& a = v[k];
+    const V3<T>& b = v[(k + 1) % 3];
+    V3<T> ab = sub(b, a);
+    T t = dot(sub(p, a), ab) / dot(ab, ab);
+    if (val(t) < 0) t = T(0);
+    if (val(t) > 1) t = T(1);
+    V3<T> c = add(a, scl(ab, t));
+    double d = val(dot(sub(p, c), sub(p, c)));
+    if (d < bd) { bd = d; best = c; }
+  }
+  return best;
+}
+
+// Heightfield (geom1: frame X, size (hx, hy, hz), grid hf) against a sphere (c, r).
+//   * Centre outside the grid's xy footprint: no contact (dist = 1e30).
+//   * Centre on or below the triangle under it (signed distance s <= 0 to that triangle's plane,
+//     normal pointing up): dist = s - r along that normal.
+//   * Otherwise: the closest point q over the triangles of the cells that meet the square of
+//     half-width r around the centre (ties to the first in cell row, column, triangle order);
+//     normal (c - q) / |c - q|, dist = |c - q| - r.
+// The contact point is midway between the sphere's deepest point and the surface point.
+template <class T> Contact<T> hfield_sphere(const Xf<T>& X, const double* size, const HField& hf, const V3<T>& cw, T r) {
+  Contact<T> out;
+  V3<T> c = mtv(X.R, sub(cw, X.p));
+  const double hx = size[0], hy = size[1];
+  const double dx = 2 * hx / (hf.ncol - 1), dy = 2 * hy / (hf.nrow - 1);
+  if (val(c[0]) < -hx || val(c[0]) > hx || val(c[1]) < -hy || val(c[1]) > hy) {
+    out.dist = T(1e30);
+    out.n = col(X.R, 2);
+    out.pos = cw;
+    return out;
+  }
+  auto cell = [](double u, double d, int n) { int k = (int)std::floor(u / d); return k < 0 ? 0 : (k > n - 2 ? n - 2 : k); };
+  const int i = cell(val(c[1]) + hy, dy, hf.nrow), j = cell(val(c[0]) + hx, dx, hf.ncol);
+  const double fu = (val(c[0]) + hx) / dx - j, fv = (val(c[1]) + hy) / dy - i;
+  V3<T> tri[3];
+  hf_triangle(hf, size, i, j, fu >= fv ? 0 : 1, tri);
+  V3<T> nt = cross(sub(tri[1], tri[0]), sub(tri[2], tri[0]));
+  nt = scl(nt, T(1) / norm(nt));
+  T sd = dot(nt, sub(c, tri[0]));
+  V3<T> nl;
+  T d;
+  if (val(sd) <= 0) {
+    nl = nt;
+    d = sd;
+  } else {
+    const double rr = val(r);
+    const int i0 = cell(val(c[1]) - rr + hy, dy, hf.nrow), i1 = cell(val(c[1]) + rr + hy, dy, hf.nrow);
+    const int j0 = cell(val(c[0]) - rr + hx, dx, hf.ncol), j1 = cell(val(c[0]) + rr + hx, dx, hf.ncol);
+    double best = 1e300;
+    V3<T> q{};
+    for (int a = i0; a <= i1; a++)
+      for (int b = j0; b <= j1; b++)
+        for (int t = 0; t < 2; t++) {
+          hf_triangle(hf, size, a, b, t, tri);
+          V3<T> p = closest_on_triangle(c, tri);
+          double dd = val(dot(sub(c, p), sub(c, p)));
+          if (dd < best) { best = dd; q = p; }
+        }
+    V3<T> e = sub(c, q);
+    d = norm(e);
+    nl = scl(e, T(1) / d);
+  }
+  out.n = mv(X.R, nl);
+  out.dist = d - r;
+  out.pos = sub(cw, scl(out.n, r + out.dist * T(0.5)));
+  return out;
+}
+
 // All candidate contacts of one pair, written to out[0 .. pair_max_points).
 template <class T> void collide_pair(int t1, const Xf<T>& X1, const double* s1, int t2, const Xf<T>& X2, const double* s2,
-                                     Contact<T>* out) {
-  if (t1 == PLANE) {
+                                     Contact<T>* out, const HField& hf = HField()) {
+  if (t1 == HFIELD) {
+    // a sphere; a capsule meets the terrain at its two end spheres
+    if (t2 == SPHERE) {
+      out[0] = hfield_sphere(X1, s1, hf, X2.p, T(s2[0]));
+    } else if (t2 == CAPSULE) {
+      V3<T> a = seg_axis(X2);
+      for (int e = 0; e < 2; e++) {
+        T sgn = e == 0 ? T(-1) : T(1);
+        out[e] = hfield_sphere(X1, s1, hf, add(X2.p, scl(a, sgn * T(s2[1]))), T(s2[0]));
+      }
+    }
+  } else if (t1 == PLANE) {
     V3<T> nz = col(X1.R, 2), p0 = X1.p;
     if (t2 == SPHERE) {
       out[0] = plane_sphere(p0, nz, X2.p, T(s2[0]));
@@ -1049,7 +1157,7 @@ template <class T> void forward(const Model& m, const T* qpos, const T* qvel, co
   for (int p = 0; p < m.npair; p++) {
     int g1 = m.pair_g1[p], g2 = m.pair_g2[p];
     collide_pair(m.geom_type[g1], F.kin.xgeom[g1], &m.geom_size[3 * g1], m.geom_type[g2], F.kin.xgeom[g2],
-                 &m.geom_size[3 * g2], &F.con[m.pair_slotadr[p]]);
+                 &m.geom_size[3 * g2], &F.con[m.pair_slotadr[p]], m.hf());
   }
   int nact = 0;
   for (int s = 0; s < m.nslot; s++) {

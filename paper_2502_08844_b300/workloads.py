@@ -29,7 +29,7 @@ import numpy as np
 
 # joint, geom, actuator and cone type codes (shared numbering of the model format)
 FREE, HINGE, SLIDE = 0, 1, 2
-PLANE, SPHERE, CAPSULE, BOX = 0, 1, 2, 3
+PLANE, SPHERE, CAPSULE, BOX, HFIELD = 0, 1, 2, 3, 4
 MOTOR, POSITION = 0, 1
 PYRAMIDAL, ELLIPTIC = 0, 1
 
@@ -113,6 +113,10 @@ class Model:
     n_substeps: int = 1          # physics substeps per control step for this workload
     default_ctrl: Optional[np.ndarray] = None  # [nu] e.g. the standing pose targets
     qpos_init: Optional[np.ndarray] = None     # [nq] reference initial configuration
+    # the model's heightfield (HFIELD geoms, world-fixed): elevations in [0, 1], row i at
+    # y = -hy + 2 hy i / (nrow - 1), column j at x = -hx + 2 hx j / (ncol - 1) of the geom frame;
+    # the surface height is size[2] * elevation
+    hfield: Optional[np.ndarray] = None        # [nrow, ncol] float32
 
     @property
     def nbody(self) -> int:
@@ -200,7 +204,7 @@ class ModelBuilder:
 
     def build(self, *, timestep, gravity=(0, 0, -9.81), iterations=4, cone=PYRAMIDAL, impratio=1.0,
               solref=(0.02, 1.0), solimp=(0.9, 0.95, 0.001, 0.5, 2.0), margin=0.0,
-              max_contacts=None, n_substeps=1, default_ctrl=None, qpos_init=None) -> Model:
+              max_contacts=None, n_substeps=1, default_ctrl=None, qpos_init=None, hfield=None) -> Model:
         B, J, G = self.bodies, self.joints, self.geoms
         dof = []
         for j in J:
@@ -208,7 +212,7 @@ class ModelBuilder:
             dof += [j] * n
         maxpts = {(PLANE, SPHERE): 1, (PLANE, CAPSULE): 2, (PLANE, BOX): 4, (SPHERE, SPHERE): 1,
                   (SPHERE, CAPSULE): 1, (CAPSULE, CAPSULE): 1, (SPHERE, BOX): 1, (CAPSULE, BOX): 2,
-                  (BOX, BOX): 4}
+                  (BOX, BOX): 4, (HFIELD, SPHERE): 1, (HFIELD, CAPSULE): 2}
         slots = sum(maxpts[(G[p["g"][0]]["type"], G[p["g"][1]]["type"])] for p in self.pairs)
         i32 = lambda x: np.asarray(x, np.int32)
         m = Model(
@@ -257,6 +261,7 @@ class ModelBuilder:
             n_substeps=int(n_substeps),
             default_ctrl=None if default_ctrl is None else _f32(default_ctrl),
             qpos_init=None if qpos_init is None else _f32(qpos_init),
+            hfield=None if hfield is None else _f32(hfield),
         )
         return m
 
@@ -483,6 +488,57 @@ def b_njnt(b: ModelBuilder) -> int:
 
 
 MODELS = {"cartpole": cartpole, "quadruped": quadruped, "hand": hand, "hand_elliptic": hand_elliptic, "humanoid": humanoid}
+
+
+def perlin_terrain(nrow: int, ncol: int, cells: int, seed: int) -> np.ndarray:
+    """Elevations [nrow, ncol] in [0, 1] of 2-D gradient noise (Perlin's construction: unit
+    gradients drawn at the corners of a cells x cells lattice, the smoothstep 6t^5 - 15t^4 + 10t^3
+    blend of the corners' dot products), rescaled to span [0, 1].  Seeded, deterministic."""
+    g = uniform01(np.full((cells + 1) * (cells + 1), np.uint64(seed)), np.arange((cells + 1) ** 2, dtype=np.uint64))
+    ang = (2.0 * np.pi * g).reshape(cells + 1, cells + 1)
+    gx, gy = np.cos(ang), np.sin(ang)
+    y = np.linspace(0.0, cells, nrow, endpoint=False) + 0.5 * cells / nrow
+    x = np.linspace(0.0, cells, ncol, endpoint=False) + 0.5 * cells / ncol
+    Y, X = np.meshgrid(y, x, indexing="ij")
+    i0, j0 = np.floor(Y).astype(int), np.floor(X).astype(int)
+    fy, fx = Y - i0, X - j0
+    fade = lambda t: t * t * t * (t * (6.0 * t - 15.0) + 10.0)
+
+    def corner(di, dj):
+        return gx[i0 + di, j0 + dj] * (fx - dj) + gy[i0 + di, j0 + dj] * (fy - di)
+
+    u, v = fade(fx), fade(fy)
+    top = corner(0, 0) + u * (corner(0, 1) - corner(0, 0))
+    bot = corner(1, 0) + u * (corner(1, 1) - corner(1, 0))
+    n = top + v * (bot - top)
+    return _f32((n - n.min()) / (n.max() - n.min()))
+
+
+ROUGH_HALF = 4.0       # the terrain spans 8 m x 8 m
+ROUGH_SAMPLES = 81     # 0.1 m cells
+ROUGH_HEIGHT = 0.06    # 6 cm between the lowest and the highest point
+
+
+def quadruped_rough() -> Model:
+    """The quadruped on rough terrain: the floor plane replaced by an 8 m x 8 m heightfield of
+    gradient noise (81 x 81 samples, 0.1 m cells, 6 cm relief, 0.5 m noise lattice), the rough-terrain setting of the
+    locomotion fine-tuning (App. B, "Finetuning").  The base starts high enough that no foot
+    starts below the terrain."""
+    m = quadruped()
+    m.name = "quadruped_rough"
+    hf = perlin_terrain(ROUGH_SAMPLES, ROUGH_SAMPLES, 16, seed=7)
+    m.geom_type = m.geom_type.copy(); m.geom_size = m.geom_size.copy()
+    m.geom_type[0] = HFIELD
+    m.geom_size[0] = _f32([ROUGH_HALF, ROUGH_HALF, ROUGH_HEIGHT])
+    m.hfield = hf
+    m.qpos_init = m.qpos_init.copy()
+    m.qpos_init[2] += np.float32(ROUGH_HEIGHT * float(hf.max()))
+    m.body_pos = m.body_pos.copy()
+    m.body_pos[1, 2] = m.qpos_init[2]
+    return m
+
+
+MODELS["quadruped_rough"] = quadruped_rough
 
 
 # --------------------------------------------------------------------------------------
