@@ -262,6 +262,42 @@ def measure_env_layer(dev, n: int = 8192, steps: int = 200, specialize: bool = T
             "note": "pg_env_step vs pg_step on identical targets (absolute mapping); reset launch included"}
 
 
+def measure_rough_terrain(dev, n: int = 8192, steps: int = 200, specialize: bool = True):
+    """The quadruped on rough terrain (an 81 x 81 heightfield of gradient noise instead of the
+    floor plane), 8192 environments, the bench workload's actions: env-steps/s of the step with
+    heightfield contacts, CUDA events around `steps` launches (the 26 KB elevation grid stays in
+    L1/L2; the state is device-resident)."""
+    import torch
+    from paper_2502_08844_b300 import core
+    m = W.quadruped_rough()
+    batch = core.Batch([(core.CompiledModel(m), n)])
+    if specialize:
+        batch.specialize()
+    st = core.State(batch, dev)
+    ld = st.ld
+    q0, v0 = W.initial_state(m, 1, n)
+    Q0 = torch.from_numpy(core.to_soa(q0, ld, batch.nq_max)).to(dev)
+    V0 = torch.from_numpy(core.to_soa(v0, ld, batch.nv_max)).to(dev)
+    U = np.zeros((steps, m.nu, ld), np.float32)
+    U[:, :, :n] = W.actions(m, 1, n, 0, steps).transpose(0, 2, 1)
+    ctrl = torch.from_numpy(U).to(dev)
+
+    def run():
+        core.reset(batch, st, Q0, V0)
+        for t in range(steps):
+            core.step(batch, st, ctrl[t], 0)
+
+    run()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(); run(); b.record()
+    torch.cuda.synchronize()
+    t = a.elapsed_time(b) / 1e3
+    return {"value": n * steps / t, "unit": "env-steps/s", "envs": n, "steps": steps,
+            "terrain": "81 x 81 heightfield, 0.1 m cells, 6 cm relief",
+            "kernel": "model-specialised" if specialize else "generic"}
+
+
 def run_reference(args):
     """Reference arm: the FP64 oracle as it stands, timed on the host cores."""
     ws, rank, _ = dist_env()
@@ -468,6 +504,7 @@ def run_ours(args):
         line["mixed_batch"] = measure_mixed(dev)
     if not args.no_env:
         line["env_layer"] = measure_env_layer(dev, specialize=kernel.startswith("model-specialised"))
+        line["rough_terrain"] = measure_rough_terrain(dev, specialize=kernel.startswith("model-specialised"))
     if not args.no_adjoint:
         adj = measure_adjoint(dev, specialize=kernel.startswith("model-specialised"))
         line["adjoint_forward_ratio"] = adj["ratio"]

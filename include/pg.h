@@ -64,7 +64,7 @@ extern "C" {
 
 /* ---- type codes ------------------------------------------------------------------- */
 enum { PG_JNT_FREE = 0, PG_JNT_HINGE = 1, PG_JNT_SLIDE = 2 };
-enum { PG_GEOM_PLANE = 0, PG_GEOM_SPHERE = 1, PG_GEOM_CAPSULE = 2, PG_GEOM_BOX = 3 };
+enum { PG_GEOM_PLANE = 0, PG_GEOM_SPHERE = 1, PG_GEOM_CAPSULE = 2, PG_GEOM_BOX = 3, PG_GEOM_HFIELD = 4 };
 enum { PG_ACT_MOTOR = 0, PG_ACT_POSITION = 1 };
 enum { PG_CONE_PYRAMIDAL = 0, PG_CONE_ELLIPTIC = 1 };
 
@@ -84,6 +84,9 @@ enum { PG_CONE_PYRAMIDAL = 0, PG_CONE_ELLIPTIC = 1 };
  *   pair_geom[2]                   candidate pair (geom1, geom2), type(geom1) <= type(geom2)
  *                                  in plane < sphere < capsule < box; the normal points from
  *                                  geom1 to geom2.  Static list: no broadphase.
+ *                                  A heightfield (PG_GEOM_HFIELD, a massless geom of the world)
+ *                                  pairs as geom1 with spheres (1 point) and capsules (2: its end
+ *                                  spheres); see hfield_data below.
  *   pair_condim                    1 (frictionless) or 3 (pyramidal cone, 4 edge rows)
  *   act_jnt                        hinge or slide joint driven by the actuator
  *   solref = (timeconst, dampratio); solimp = (d0, dwidth, width, mid, power)
@@ -106,6 +109,16 @@ typedef struct pg_model_desc {
   const float* solref; const float* solimp; float margin; int max_contacts;
   int substeps;   /* the model's own physics substeps per control step (used by pg_step when
                      n_substeps == 0, e.g. in a mixed batch); values < 1 mean 1 */
+  /* The model's heightfield, used by its PG_GEOM_HFIELD geoms (rough terrain, App. B
+   * "Finetuning"): hfield_nrow x hfield_ncol (each >= 2) elevations in [0, 1], row-major; row i
+   * lies at y = -hy + 2 hy i / (nrow - 1) and column j at x = -hx + 2 hx j / (ncol - 1) of the
+   * geom frame, at height hz * elevation, with geom_size = (hx, hy, hz).  Each grid cell is split
+   * along its (i, j)-(i+1, j+1) diagonal into two triangles.  A sphere's contact is the closest
+   * point of the triangles within its radius (in the grid's xy), or, when its centre is below the
+   * triangle under it, the depth along that triangle's normal; off the grid there is no contact.
+   * Unused (0, 0, NULL) without heightfield geoms. */
+  int hfield_nrow, hfield_ncol;
+  const float* hfield_data;
 } pg_model_desc;
 
 typedef struct pg_model pg_model;   /* opaque, library-owned */

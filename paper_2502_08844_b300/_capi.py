@@ -35,6 +35,7 @@ class pg_model_desc(C.Structure):
         ("timestep", C.c_float), ("gravity", _fp), ("iterations", C.c_int), ("cone", C.c_int),
         ("impratio", C.c_float), ("solref", _fp), ("solimp", _fp), ("margin", C.c_float),
         ("max_contacts", C.c_int), ("substeps", C.c_int),
+        ("hfield_nrow", C.c_int), ("hfield_ncol", C.c_int), ("hfield_data", _fp),
     ]
 
 

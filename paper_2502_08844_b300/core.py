@@ -54,7 +54,9 @@ class CompiledModel:
             i(m.pair_condim), i(m.act_type), i(m.act_jnt), f(m.act_gear), f(m.act_kp), f(m.act_kd),
             i(m.act_ctrllimited), f(m.act_ctrlrange), float(m.timestep), f(m.gravity), int(m.iterations),
             int(m.cone), float(m.impratio), f(m.solref), f(m.solimp), float(m.margin), int(m.max_contacts),
-            int(m.n_substeps))
+            int(m.n_substeps),
+            0 if m.hfield is None else int(m.hfield.shape[0]), 0 if m.hfield is None else int(m.hfield.shape[1]),
+            None if m.hfield is None else f(m.hfield))
         self.handle = _capi.pg_model_compile(d)
         self.sizes = _capi.pg_model_info(self.handle)
 

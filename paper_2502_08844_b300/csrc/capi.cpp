@@ -73,6 +73,7 @@ void pg_batch_free(pg_batch* b) {
   if (b->d_blobs) cudaFree(b->d_blobs);
   if (b->d_blob_off) cudaFree(b->d_blob_off);
   if (b->d_tiles) cudaFree(b->d_tiles);
+  if (b->d_hfields) cudaFree(b->d_hfields);
   if (b->d_ctrl_stage) cudaFree(b->d_ctrl_stage);
   if (b->d_vjp) cudaFree(b->d_vjp);
   if (b->spec_lib) cudaLibraryUnload(b->spec_lib);
@@ -155,6 +156,23 @@ int pg_batch_compile(const pg_model* const* models, const int64_t* counts, int n
       (b->ntiles && (e = cudaMemcpy(b->d_tiles, b->tiles.data(), b->tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice)) != cudaSuccess)) {
     pg_batch_free(b);
     return cuda_error(e, "cudaMemcpy");
+  }
+  // the models' heightfields, one device copy per model that has one
+  size_t hf_total = 0;
+  for (int k = 0; k < nmodels; k++) hf_total += models[k]->hfield.size();
+  if (hf_total) {
+    if ((e = cudaMalloc(&b->d_hfields, hf_total * sizeof(float))) != cudaSuccess) { pg_batch_free(b); return cuda_error(e, "cudaMalloc"); }
+    size_t off = 0;
+    for (int k = 0; k < nmodels; k++) {
+      const std::vector<float>& hf = models[k]->hfield;
+      if (hf.empty()) continue;
+      if ((e = cudaMemcpy(b->d_hfields + off, hf.data(), hf.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess) {
+        pg_batch_free(b);
+        return cuda_error(e, "cudaMemcpy");
+      }
+      b->hfield_ptr[k] = b->d_hfields + off;
+      off += hf.size();
+    }
   }
   if ((e = configure_step_kernels(b->smem_bytes)) != cudaSuccess) { pg_batch_free(b); return cuda_error(e, "cudaFuncSetAttribute"); }
   *out = b;

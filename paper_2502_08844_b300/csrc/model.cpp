@@ -36,6 +36,7 @@ struct Blob {
 
 // points a primitive pair type can produce (its static slot count); -1: unsupported
 int slots_for(int t1, int t2) {
+  if (t1 == PG_GEOM_HFIELD) return t2 == PG_GEOM_SPHERE ? 1 : (t2 == PG_GEOM_CAPSULE ? 2 : -1);
   static const int table[4][4] = {
       //            plane sphere capsule box
       /* plane   */ {-1, 1, 2, 4},
@@ -215,13 +216,27 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
   std::vector<int> gtype(d->geom_type, d->geom_type + ngeom), gbody(d->geom_body, d->geom_body + ngeom);
   std::vector<float> gpos(d->geom_pos, d->geom_pos + 3 * ngeom), gquat(4 * ngeom), gsize(d->geom_size, d->geom_size + 3 * ngeom);
   for (int g = 0; g < ngeom; g++) {
-    if (gtype[g] < PG_GEOM_PLANE || gtype[g] > PG_GEOM_BOX) return set_error(PG_EINVAL, "bad geom type");
+    if (gtype[g] < PG_GEOM_PLANE || gtype[g] > PG_GEOM_HFIELD) return set_error(PG_EINVAL, "bad geom type");
     if (gbody[g] < 0 || gbody[g] >= nbody) return set_error(PG_EINVAL, "geom_body out of range");
+    if (gtype[g] == PG_GEOM_HFIELD) {
+      if (gbody[g] != 0 || d->geom_mass[g] != 0.f) return set_error(PG_EINVAL, "a heightfield must be a massless geom of the world");
+      if (d->hfield_nrow < 2 || d->hfield_ncol < 2 || !d->hfield_data)
+        return set_error(PG_EINVAL, "a heightfield geom needs hfield_data of at least 2 x 2 elevations");
+      if (!(gsize[3 * g] > 0.f && gsize[3 * g + 1] > 0.f && gsize[3 * g + 2] >= 0.f))
+        return set_error(PG_EINVAL, "heightfield size must be (hx > 0, hy > 0, hz >= 0)");
+    }
     double q[4], n = 0;
     for (int k = 0; k < 4; k++) { q[k] = d->geom_quat[4 * g + k]; n += q[k] * q[k]; }
     n = std::sqrt(n);
     if (!(n > 0)) return set_error(PG_EINVAL, "zero geom quaternion");
     for (int k = 0; k < 4; k++) gquat[4 * g + k] = (float)(q[k] / n);
+  }
+  std::vector<float> hfield;
+  if (d->hfield_data && d->hfield_nrow >= 2 && d->hfield_ncol >= 2) {
+    if ((int64_t)d->hfield_nrow * d->hfield_ncol > (1 << 24)) return set_error(PG_ECAPACITY, "heightfield larger than 2^24 samples");
+    hfield.assign(d->hfield_data, d->hfield_data + (size_t)d->hfield_nrow * d->hfield_ncol);
+    for (float e : hfield)
+      if (!(e >= 0.f && e <= 1.f)) return set_error(PG_EINVAL, "heightfield elevations must lie in [0, 1]");
   }
   std::vector<int> pg1(npair), pg2(npair), pcondim(npair), pslotadr(npair), pnslot(npair);
   std::vector<float> pfric(npair);
@@ -230,7 +245,7 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
     int a = d->pair_geom[2 * p], b = d->pair_geom[2 * p + 1];
     if (a < 0 || a >= ngeom || b < 0 || b >= ngeom) return set_error(PG_EINVAL, "pair geom out of range");
     int n = slots_for(gtype[a], gtype[b]);
-    if (n < 0) return set_error(PG_EUNSUPPORTED, "unsupported pair: type(geom1) must not exceed type(geom2) (plane<sphere<capsule<box), plane-plane unsupported");
+    if (n < 0) return set_error(PG_EUNSUPPORTED, "unsupported pair: type(geom1) must not exceed type(geom2) (plane<sphere<capsule<box), plane-plane unsupported; a heightfield pairs as geom1 with spheres and capsules");
     if (d->pair_condim[p] != 1 && d->pair_condim[p] != 3) return set_error(PG_EUNSUPPORTED, "pair_condim must be 1 or 3");
     pg1[p] = a; pg2[p] = b; pcondim[p] = d->pair_condim[p]; pfric[p] = d->pair_friction[p];
     pslotadr[p] = nslot; pnslot[p] = n;
@@ -295,6 +310,8 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
   h.nL = nL; h.cap = d->iterations; h.cone = d->cone; h.tree_hessian = tree_hessian; h.ncol_max = ncol_max;
   h.h = d->timestep;
   h.substeps = std::max(d->substeps, 1);
+  h.hf_nrow = hfield.empty() ? 0 : d->hfield_nrow;
+  h.hf_ncol = hfield.empty() ? 0 : d->hfield_ncol;
   for (int k = 0; k < 3; k++) h.grav[k] = d->gravity[k];
   {
     double tc = std::max((double)d->solref[0], 2.0 * (double)d->timestep), zeta = d->solref[1], dmax = d->solimp[1];
@@ -451,6 +468,7 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
   out->blob_adj = B.w;
   std::memcpy(out->blob_adj.data(), &out->hdr_adj, sizeof(h));
   out->blob = std::move(B.w);
+  out->hfield = std::move(hfield);
   return PG_OK;
 }
 

@@ -14,6 +14,8 @@ struct pg_model {
   pg::ModelHdr hdr_adj;             // the adjoint's header (its workspace layout)
   std::vector<uint32_t> blob_adj;   // the blob with the adjoint's header
   uint32_t* d_blob = nullptr;   // device copy of the blob
+  std::vector<float> hfield;    // the heightfield's elevations (empty without one); the batch
+                                // holds the device copy
 };
 
 struct pg_task {
@@ -34,6 +36,8 @@ struct pg_batch {
   uint32_t* d_blobs = nullptr;     // all models' blobs, concatenated
   int* d_blob_off = nullptr;       // word offset of each model's blob
   pg::Tile* d_tiles = nullptr;
+  float* d_hfields = nullptr;                      // the models' heightfields, concatenated
+  const float* hfield_ptr[pg::kMaxModels] = {};    // each model's grid in d_hfields (NULL: none)
   int ntiles = 0;
   std::vector<int> blob_off;
   std::vector<uint32_t> blob_host;   // all models' blobs, concatenated (passed as a kernel parameter)

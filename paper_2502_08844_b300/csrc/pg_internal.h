@@ -32,6 +32,7 @@ struct ModelHdr {
   // counts
   int nbody, njnt, nq, nv, nu, ngeom, npair, nslot, nrow_max, max_contacts, nlimited, nL;
   int cap, cone, tree_hessian, ncol_max, soa, substeps;
+  int hf_nrow, hf_ncol;   // the heightfield grid (its elevations live in device memory, not the blob)
   // options (float32)
   float h, grav[3], kref, bref, solimp[5], margin;
   float imp_mid_inv, imp_tail_inv;   // 1 / mid^(p-1) and 1 / (1 - mid)^(p-1) of the impedance

@@ -338,6 +338,7 @@ struct Ctx {
   const float* __restrict__ ctrl;
   int64_t ld;
   int64_t env;
+  const float* __restrict__ hf;   // the model's heightfield elevations (device memory), or NULL
 };
 
 #define MI(name, i) (c.I[c.h.o_##name + (i)])
@@ -688,6 +689,107 @@ __device__ void smooth_acc(const Ctx& c, float* dbg) {
   for (int k = 0; k < h.nv; k++) W(Dinv, k) = 1.f / W(L, MI(dof_rowadr, k));   // for the row parameters
 }
 // ---------------------------------------------------------------------------------------
+// heightfield: the grid's triangulation, cell (i, j) split along its (i, j)-(i+1, j+1) diagonal
+// into triangle 0 = (v00, v01, v11) and triangle 1 = (v00, v11, v10)
+// ---------------------------------------------------------------------------------------
+struct HGrid {
+  const float* e;
+  int nrow, ncol;
+  float hx, hy, hz, dx, dy;
+};
+
+__device__ __forceinline__ float3 hg_vertex(const HGrid& g, int i, int j) {
+  return make_float3(fmaf((float)j, g.dx, -g.hx), fmaf((float)i, g.dy, -g.hy), g.hz * __ldg(g.e + i * g.ncol + j));
+}
+
+__device__ __forceinline__ void hg_triangle(const HGrid& g, int i, int j, int t, float3 v[3]) {
+  v[0] = hg_vertex(g, i, j);
+  v[1] = t == 0 ? hg_vertex(g, i, j + 1) : hg_vertex(g, i + 1, j + 1);
+  v[2] = t == 0 ? hg_vertex(g, i + 1, j + 1) : hg_vertex(g, i + 1, j);
+}
+
+__device__ __forceinline__ int hg_cell(float u, float d, int n) {
+  return min(max((int)floorf(u / d), 0), n - 2);
+}
+
+// closest point to p on triangle v: its projection onto the plane when the barycentric weights
+// are all >= 0, else the nearest of the edges' clamped projections (first edge on ties)
+__device__ float3 closest_on_triangle(float3 p, const float3 v[3]) {
+  const float3 n = cross3(v[1] - v[0], v[2] - v[0]);
+  const float inn = 1.f / dot3(n, n);
+  const float3 q = p - n * (dot3(n, p - v[0]) * inn);
+  const float w0 = dot3(cross3(v[2] - v[1], q - v[1]), n) * inn;
+  const float w1 = dot3(cross3(v[0] - v[2], q - v[2]), n) * inn;
+  if (w0 >= 0.f && w1 >= 0.f && w0 + w1 <= 1.f) return q;
+  float3 best = v[0];
+  float bd = 3.4e38f;
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    const float3 a = v[k], ab = v[(k + 1) % 3] - a;
+    const float t = fminf(fmaxf(dot3(p - a, ab) / dot3(ab, ab), 0.f), 1.f);
+    const float3 cp = a + ab * t;
+    const float3 dd = p - cp;
+    const float d2 = dot3(dd, dd);
+    if (d2 < bd) { bd = d2; best = cp; }
+  }
+  return best;
+}
+
+// Heightfield (geom1 at x1, R1, size (hx, hy, hz)) against a sphere (cw, r):
+//   * centre off the grid's xy footprint: no contact;
+//   * centre on or below the triangle under it: depth s - r along that triangle's upward normal
+//     (s: the centre's signed distance to its plane);
+//   * otherwise the closest point q of the triangles in the cells meeting the square of
+//     half-width r around the centre (first in row, column, triangle order on ties):
+//     normal (c - q)/|c - q|, dist = |c - q| - r.
+// The point is midway between the sphere's deepest point and the surface.
+__device__ Con hfield_sphere(const HGrid& g, float3 x1, const float* R1, float3 cw, float r) {
+  Con out;
+  out.feat = 0;
+  const float3 c = mat_tmul(R1, cw - x1);
+  if (!(c.x >= -g.hx && c.x <= g.hx && c.y >= -g.hy && c.y <= g.hy)) {
+    out.dist = 1e30f;
+    out.n = mat_col(R1, 2);
+    out.pos = cw;
+    return out;
+  }
+  const int i = hg_cell(c.y + g.hy, g.dy, g.nrow), j = hg_cell(c.x + g.hx, g.dx, g.ncol);
+  const float fu = (c.x + g.hx) / g.dx - (float)j, fv = (c.y + g.hy) / g.dy - (float)i;
+  float3 tri[3];
+  hg_triangle(g, i, j, fu >= fv ? 0 : 1, tri);
+  float3 nt = cross3(tri[1] - tri[0], tri[2] - tri[0]);
+  nt = nt * rsqrtf(dot3(nt, nt));
+  const float sd = dot3(nt, c - tri[0]);
+  float3 nl;
+  float d;
+  if (sd <= 0.f) {
+    nl = nt;
+    d = sd;
+  } else {
+    const int i0 = hg_cell(c.y - r + g.hy, g.dy, g.nrow), i1 = hg_cell(c.y + r + g.hy, g.dy, g.nrow);
+    const int j0 = hg_cell(c.x - r + g.hx, g.dx, g.ncol), j1 = hg_cell(c.x + r + g.hx, g.dx, g.ncol);
+    float best = 3.4e38f;
+    float3 q = c;
+    for (int a = i0; a <= i1; a++)
+      for (int b = j0; b <= j1; b++)
+        for (int t = 0; t < 2; t++) {
+          hg_triangle(g, a, b, t, tri);
+          const float3 p = closest_on_triangle(c, tri);
+          const float3 e = c - p;
+          const float d2 = dot3(e, e);
+          if (d2 < best) { best = d2; q = p; }
+        }
+    const float3 e = c - q;
+    d = sqrtf(dot3(e, e));
+    nl = e * (1.f / d);
+  }
+  out.n = mat_mul(R1, nl);
+  out.dist = d - r;
+  out.pos = cw - out.n * (r + 0.5f * out.dist);
+  return out;
+}
+
+// ---------------------------------------------------------------------------------------
 // collision over the static pair list; active contacts (dist < margin) are kept in slot order
 // up to max_contacts as (slot, dist, pos, n)
 // ---------------------------------------------------------------------------------------
@@ -717,7 +819,19 @@ __device__ int collide(const Ctx& c, uint32_t& status, float* dbg) {
     Con k[4];
     int valid = ns;
     for (int i = 0; i < 4; i++) { k[i].dist = 1.f; k[i].pos = x1; k[i].n = make_float3(0.f, 0.f, 1.f); }
-    if (t1 == PG_GEOM_PLANE) {
+    if (t1 == PG_GEOM_HFIELD) {
+      // a sphere; a capsule meets the terrain at its two end spheres
+      const HGrid g{c.hf, h.hf_nrow, h.hf_ncol, s1[0], s1[1], s1[2], 2.f * s1[0] / (float)(h.hf_ncol - 1),
+                    2.f * s1[1] / (float)(h.hf_nrow - 1)};
+      if (t2 == PG_GEOM_SPHERE) {
+        k[0] = hfield_sphere(g, x1, R1, x2, s2[0]);
+      } else {
+        const float3 a = mat_col(R2, 2);
+        k[0] = hfield_sphere(g, x1, R1, x2 - a * s2[1], s2[0]);
+        k[1] = hfield_sphere(g, x1, R1, x2 + a * s2[1], s2[0]);
+        k[1].feat = 1;
+      }
+    } else if (t1 == PG_GEOM_PLANE) {
       const float3 nz = mat_col(R1, 2);
       if (t2 == PG_GEOM_SPHERE) {
         k[0] = plane_sphere(x1, nz, x2, s2[0]);

@@ -28,6 +28,7 @@ struct StepArgs {
   float* tape;                        // optional record of every substep (see TAPE below)
   int tape_rows, tape_nq, tape_nv;    // rows per substep entry; the batch's nq_max, nv_max
   int model_off[kMaxModels];          // word offset of each model's blob in `blob`
+  const float* hfield[kMaxModels];    // each model's heightfield elevations (device), or NULL
   EnvArgs env;                        // the locomotion task of an environment step (ENV below)
   uint32_t blob[kMaxParamWords];      // the batch's model blobs (header + tables)
 };
@@ -63,7 +64,7 @@ __device__ __forceinline__ void step_body(const StepArgs& A) {
   const int64_t env = tile.env0 + t;
   float* w = smem + warp * (S * h.ws_floats) + lane;
   Ctx c{h, S, reinterpret_cast<const int*>(blob), reinterpret_cast<const float*>(blob), w, ENV ? A.env.state : A.ctrl,
-        A.ld, env};
+        A.ld, env, A.hfield[tile.model]};
   if (ENV) env_targets(c, A.env);
   for (int k = 0; k < h.nq; k++) W(qpos, k) = A.qpos[k * A.ld + env];
   uint32_t status = 0;

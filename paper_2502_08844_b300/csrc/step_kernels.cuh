@@ -51,6 +51,7 @@ static void make_args(StepArgs& A, const pg_batch* b, const pg_state* s, const f
   A.tape_rows = A.tape_nq = A.tape_nv = 0;
   A.env.state = nullptr;
   for (int k = 0; k < kMaxModels; k++) A.model_off[k] = k < (int)b->blob_off.size() ? b->blob_off[k] : 0;
+  for (int k = 0; k < kMaxModels; k++) A.hfield[k] = b->hfield_ptr[k];
   std::memcpy(A.blob, b->blob_host.data(), b->blob_host.size() * sizeof(uint32_t));
 }
 
