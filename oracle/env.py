@@ -17,7 +17,8 @@ Readings where the paper leaves a choice (each also listed in the design notes):
   * "phi_body,xy" of the orientation term is the xy part of the gravity direction in the base
     frame.
   * "joint positions" in the observation are q - q_default of the actuated joints.
-  * tau in the torque and energy terms is the PD torque at the step's final state, and
+  * tau in the torque and energy terms is the PD torque at the step's final state (clipped by
+    the actuator's torque limits), and
     "|qdot . tau|" is the sum of |qdot_j tau_j|.
   * T_air grows by the control step before the touchdown test; it restarts at zero while the
     foot touches the ground.
@@ -63,6 +64,9 @@ class OracleTask:
         self.limited = m.act_ctrllimited.astype(bool)
         self.lo = m.act_ctrlrange[:, 0].astype(np.float64)
         self.hi = m.act_ctrlrange[:, 1].astype(np.float64)
+        if m.act_forcelimited is not None:   # torque limits clip the PD torque
+            self.flo = m.act_forcerange[:, 0].astype(np.float64)
+            self.fhi = m.act_forcerange[:, 1].astype(np.float64)
         self.q_default = task.q_default.astype(np.float64)
         self.scale = float(np.float32(task.action_scale))
         self.foot_geom = task.foot_geom.astype(int)
@@ -140,9 +144,12 @@ class OracleTask:
         v = R.T @ np.asarray(qvel[0:3], np.float64)
         w = np.asarray(qvel[3:6], np.float64)
         cmd = np.asarray(cmd, np.float64)
+        m_lim = None if self.m.act_forcelimited is None else self.m.act_forcelimited.astype(bool)
         q = np.asarray(qpos, np.float64)[self.act_q]
         qd = np.asarray(qvel, np.float64)[self.act_d]
         tau = self.kp * (q_des - q) - self.kd * qd
+        if m_lim is not None:
+            tau = np.where(m_lim, np.clip(tau, self.flo, self.fhi), tau)
         _, height, vel = self.feet(qpos, qvel)
         on = height < self.contact_height
         air_now = air + dt

@@ -36,6 +36,7 @@ class _Desc(C.Structure):
         ("impratio", C.c_double), ("solref", _dp), ("solimp", _dp), ("margin", C.c_double),
         ("max_contacts", C.c_int),
         ("hfield_nrow", C.c_int), ("hfield_ncol", C.c_int), ("hfield_data", _dp),
+        ("act_forcelimited", _ip), ("act_forcerange", _dp),
     ]
 
 
@@ -132,6 +133,8 @@ class OracleModel:
             0 if getattr(m, "hfield", None) is None else int(m.hfield.shape[0]),
             0 if getattr(m, "hfield", None) is None else int(m.hfield.shape[1]),
             None if getattr(m, "hfield", None) is None else D("hf", m.hfield),
+            None if getattr(m, "act_forcelimited", None) is None else I("afl", m.act_forcelimited),
+            None if getattr(m, "act_forcerange", None) is None else D("afr", m.act_forcerange),
         )
         err = C.create_string_buffer(256)
         h = L.orc_model_new(C.byref(desc), err, 256)

@@ -182,6 +182,16 @@ std::string compile_model(const Desc& d, Model& m) {
   m.act_kd.assign(d.act_kd, d.act_kd + d.nu);
   m.act_ctrllimited.assign(d.act_ctrllimited, d.act_ctrllimited + d.nu);
   m.act_ctrlrange.assign(d.act_ctrlrange, d.act_ctrlrange + 2 * d.nu);
+  m.act_forcelimited.assign(d.nu, 0);
+  m.act_forcerange.assign(2 * d.nu, 0.0);
+  for (int a = 0; a < d.nu; a++)
+    if (d.act_forcelimited && d.act_forcelimited[a]) {
+      if (!d.act_forcerange || !(d.act_forcerange[2 * a] <= d.act_forcerange[2 * a + 1]))
+        return "act_forcerange must satisfy lo <= hi";
+      m.act_forcelimited[a] = 1;
+      m.act_forcerange[2 * a] = d.act_forcerange[2 * a];
+      m.act_forcerange[2 * a + 1] = d.act_forcerange[2 * a + 1];
+    }
   // options
   if (!(d.timestep > 0)) return "timestep must be > 0";
   m.timestep = d.timestep;

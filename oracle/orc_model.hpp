@@ -34,6 +34,7 @@ struct Desc {
   double timestep; const double* gravity; int iterations; int cone; double impratio;
   const double* solref; const double* solimp; double margin; int max_contacts;
   int hfield_nrow, hfield_ncol; const double* hfield_data;   // the model's heightfield (elevations)
+  const int* act_forcelimited; const double* act_forcerange;  // actuator torque limits (NULL: none)
 };
 
 // A heightfield grid: elevations e in [0, 1], row i at y = -hy + 2 hy i / (nrow - 1), column j at
@@ -60,6 +61,8 @@ struct Model {
   int nslot = 0;
   std::vector<int> act_type, act_jnt, act_ctrllimited;
   std::vector<double> act_gear, act_kp, act_kd, act_ctrlrange;
+  std::vector<int> act_forcelimited;
+  std::vector<double> act_forcerange;
   double timestep = 0.01, impratio = 1.0, margin = 0.0;
   double gravity[3] = {0, 0, -9.81};
   double solref[2] = {0.02, 1.0};

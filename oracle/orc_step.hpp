@@ -1043,8 +1043,13 @@ template <class T> void actuation(const Model& m, const T* qpos, const T* qvel, 
       if (val(u) < m.act_ctrlrange[2 * a]) u = T(m.act_ctrlrange[2 * a]);
       if (val(u) > m.act_ctrlrange[2 * a + 1]) u = T(m.act_ctrlrange[2 * a + 1]);
     }
-    if (m.act_type[a] == MOTOR) tau[d] = tau[d] + T(m.act_gear[a]) * u;
-    else tau[d] = tau[d] + (P ? P->kp[a] : T(m.act_kp[a])) * (u - qpos[qa]) - T(m.act_kd[a]) * qvel[d];
+    T f = m.act_type[a] == MOTOR ? T(m.act_gear[a]) * u
+                                  : (P ? P->kp[a] : T(m.act_kp[a])) * (u - qpos[qa]) - T(m.act_kd[a]) * qvel[d];
+    if (m.act_forcelimited[a]) {   // torque limits: the force is clipped to its range
+      if (val(f) < m.act_forcerange[2 * a]) f = T(m.act_forcerange[2 * a]);
+      if (val(f) > m.act_forcerange[2 * a + 1]) f = T(m.act_forcerange[2 * a + 1]);
+    }
+    tau[d] = tau[d] + f;
   }
 }
 

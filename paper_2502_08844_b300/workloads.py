@@ -117,6 +117,8 @@ class Model:
     # y = -hy + 2 hy i / (nrow - 1), column j at x = -hx + 2 hx j / (ncol - 1) of the geom frame;
     # the surface height is size[2] * elevation
     hfield: Optional[np.ndarray] = None        # [nrow, ncol] float32
+    act_forcelimited: Optional[np.ndarray] = None   # [nu] int32: clip the actuator's force
+    act_forcerange: Optional[np.ndarray] = None     # [nu, 2] (lo, hi)
 
     @property
     def nbody(self) -> int:
@@ -197,9 +199,10 @@ class ModelBuilder:
         return len(self.pairs) - 1
 
     def actuator(self, jnt: int, atype: int, gear=1.0, kp=0.0, kd=0.0, ctrllimited=False,
-                 ctrlrange=(0.0, 0.0)) -> int:
+                 ctrlrange=(0.0, 0.0), forcelimited=False, forcerange=(0.0, 0.0)) -> int:
         self.acts.append(dict(jnt=jnt, type=atype, gear=gear, kp=kp, kd=kd,
-                              ctrllimited=int(ctrllimited), ctrlrange=ctrlrange))
+                              ctrllimited=int(ctrllimited), ctrlrange=ctrlrange,
+                              forcelimited=int(forcelimited), forcerange=forcerange))
         return len(self.acts) - 1
 
     def build(self, *, timestep, gravity=(0, 0, -9.81), iterations=4, cone=PYRAMIDAL, impratio=1.0,
@@ -263,6 +266,9 @@ class ModelBuilder:
             qpos_init=None if qpos_init is None else _f32(qpos_init),
             hfield=None if hfield is None else _f32(hfield),
         )
+        if any(a["forcelimited"] for a in self.acts):
+            m.act_forcelimited = i32([a["forcelimited"] for a in self.acts])
+            m.act_forcerange = _f32([a["forcerange"] for a in self.acts]).reshape(-1, 2)
         return m
 
 
