@@ -119,6 +119,10 @@ typedef struct pg_model_desc {
    * Unused (0, 0, NULL) without heightfield geoms. */
   int hfield_nrow, hfield_ncol;
   const float* hfield_data;
+  /* Actuator torque limits (the 8 Nm bounds of the hand, App. C): where act_forcelimited[a] is
+   * non-zero the actuator's force is clipped to act_forcerange[2a .. 2a+1].  NULL: no limits. */
+  const int* act_forcelimited;
+  const float* act_forcerange;
 } pg_model_desc;
 
 typedef struct pg_model pg_model;   /* opaque, library-owned */
@@ -134,6 +138,7 @@ typedef struct pg_model_sizes {
   int adjoint_workspace_bytes;  /* per-env workspace of pg_step_vjp; 0 when the model is
                                    outside the adjoint's scope (see pg_step_vjp)          */
   int nparam;           /* nbody + nv + nu: rows of the per-env parameter gradient        */
+  int nrand;            /* 2 + 3 nbody + nv + nu: rows of pg_step_dr's per-env parameters */
 } pg_model_sizes;
 
 /* Caller-owned batch state (device pointers, [coord][ld] float32; status [n] uint32). */
@@ -228,6 +233,24 @@ int pg_reset(const pg_batch* batch, pg_state* state, const uint8_t* env_mask_dev
  * timestep.  Advances qpos, qvel, qacc_warm and ORs status bits in place. */
 int pg_step(const pg_batch* batch, pg_state* state, const float* ctrl_dev, int n_substeps, void* stream);
 
+/* pg_step with per-environment physical parameters (domain randomisation, App. B "Domain
+ * Randomization": ground friction, payload mass, link centres of mass, reflected inertia, joint
+ * calibration offsets).  params_dev is [nrand_max][ld] float32 (caller-owned), per environment:
+ *   row 0                      friction scale: every pair's friction is multiplied by it;
+ *   row 1                      payload: a point mass added at the centre of mass of body 1 (the
+ *                              base of a floating robot), so body 1's mass grows and its
+ *                              inertia about its centre of mass is unchanged;
+ *   rows 2 .. 2 + 3 nbody      centre-of-mass offset (x, y, z, body frame) of each body, its
+ *                              inertia about the centre of mass unchanged;
+ *   next nv rows               armature added to each dof;
+ *   next nu rows               calibration offset of each actuator: a PD actuator acts as if
+ *                              its target were ctrl + offset (a motor ignores it).
+ * An all-zero block except row 0 = 1 is the nominal model.  In a mixed batch each environment
+ * reads the rows of its own model's layout.  The adjoint (pg_step_vjp) differentiates the
+ * nominal model only.  Errors as pg_step, and PG_EINVAL for a NULL params_dev. */
+int pg_step_dr(const pg_batch* batch, pg_state* state, const float* ctrl_dev, const float* params_dev, int n_substeps,
+               void* stream);
+
 /* Diagnostics: one substep of environment `env` only (the others are untouched), writing
  * every intermediate to out_dev (debug_floats floats, device memory) in this order:
  * xpos[nbody][3] xmat[nbody][9] xcom[nbody][3] M[nv][nv] bias[nv] passive[nv] actuator[nv]
@@ -275,7 +298,8 @@ int pg_step_host(pg_batch* batch, pg_state* state, const float* ctrl_host, float
  * Scope. Every model of the batch needs adjoint_workspace_bytes > 0. That means:
  *   * any joints and actuators;
  *   * joint limits;
- *   * contacts only between a world-fixed plane (geom1) and spheres, capsules or boxes.
+ *   * contacts only between a world-fixed plane (geom1) and spheres, capsules or boxes;
+ *   * no actuator torque limits.
  * Otherwise the call returns PG_EUNSUPPORTED.
  *
  * Scratch and errors.

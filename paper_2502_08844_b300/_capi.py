@@ -36,13 +36,14 @@ class pg_model_desc(C.Structure):
         ("impratio", C.c_float), ("solref", _fp), ("solimp", _fp), ("margin", C.c_float),
         ("max_contacts", C.c_int), ("substeps", C.c_int),
         ("hfield_nrow", C.c_int), ("hfield_ncol", C.c_int), ("hfield_data", _fp),
+        ("act_forcelimited", _ip), ("act_forcerange", _fp),
     ]
 
 
 class pg_model_sizes(C.Structure):
     _fields_ = [(n, C.c_int) for n in ("nq", "nv", "nu", "nbody", "njnt", "ngeom", "npair", "nslot", "nrow_max",
                                         "max_contacts", "workspace_bytes", "debug_floats",
-                                        "adjoint_workspace_bytes", "nparam")]
+                                        "adjoint_workspace_bytes", "nparam", "nrand")]
 
 
 class pg_state(C.Structure):
@@ -67,7 +68,7 @@ class pg_task_sizes(C.Structure):
 
 
 EXPORTS = ["pg_model_compile", "pg_model_info", "pg_model_free", "pg_batch_compile", "pg_batch_info",
-           "pg_batch_free", "pg_reset", "pg_step", "pg_debug_substep", "pg_step_host", "pg_step_vjp",
+           "pg_batch_free", "pg_reset", "pg_step", "pg_step_dr", "pg_debug_substep", "pg_step_host", "pg_step_vjp",
            "pg_step_vjp_noalloc", "pg_batch_specialize", "pg_task_compile", "pg_task_info", "pg_task_free",
            "pg_env_reset", "pg_env_step", "pg_last_error"]
 
@@ -89,6 +90,7 @@ _lib.pg_batch_free.argtypes = [C.c_void_p]
 _lib.pg_batch_free.restype = None
 _lib.pg_reset.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
 _lib.pg_step.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_int, C.c_void_p]
+_lib.pg_step_dr.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
 _lib.pg_debug_substep.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
 _lib.pg_step_host.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
 _lib.pg_step_vjp.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_int, C.c_int] + [C.c_void_p] * 7
@@ -162,6 +164,10 @@ def pg_reset(batch, state: pg_state, env_mask_ptr, qpos0_ptr, qvel0_ptr, stream)
 
 def pg_step(batch, state: pg_state, ctrl_ptr, n_substeps: int, stream) -> None:
     _check(_lib.pg_step(batch, C.byref(state), ctrl_ptr, int(n_substeps), stream), "pg_step")
+
+
+def pg_step_dr(batch, state: pg_state, ctrl_ptr, params_ptr, n_substeps: int, stream) -> None:
+    _check(_lib.pg_step_dr(batch, C.byref(state), ctrl_ptr, params_ptr, int(n_substeps), stream), "pg_step_dr")
 
 
 def pg_debug_substep(batch, state: pg_state, ctrl_ptr, env: int, out_ptr, stream) -> None:

@@ -56,7 +56,9 @@ class CompiledModel:
             int(m.cone), float(m.impratio), f(m.solref), f(m.solimp), float(m.margin), int(m.max_contacts),
             int(m.n_substeps),
             0 if m.hfield is None else int(m.hfield.shape[0]), 0 if m.hfield is None else int(m.hfield.shape[1]),
-            None if m.hfield is None else f(m.hfield))
+            None if m.hfield is None else f(m.hfield),
+            None if m.act_forcelimited is None else i(m.act_forcelimited),
+            None if m.act_forcerange is None else f(m.act_forcerange))
         self.handle = _capi.pg_model_compile(d)
         self.sizes = _capi.pg_model_info(self.handle)
 
@@ -186,6 +188,16 @@ def reset(batch: Batch, state: State, qpos0: torch.Tensor, qvel0: torch.Tensor, 
 def step(batch: Batch, state: State, ctrl: torch.Tensor, n_substeps: int, stream=None) -> None:
     assert ctrl.dtype == torch.float32 and ctrl.is_contiguous() and ctrl.shape[-1] == state.ld
     _capi.pg_step(batch.handle, state.c(), _ptr(ctrl), int(n_substeps), _stream_ptr(stream))
+
+
+def step_dr(batch: Batch, state: State, ctrl: torch.Tensor, params: torch.Tensor, n_substeps: int,
+            stream=None) -> None:
+    """pg_step_dr: the step with per-environment parameters params [nrand_max][ld] (friction
+    scale, payload, centre-of-mass offsets, armature, calibration offsets)."""
+    assert ctrl.dtype == torch.float32 and ctrl.is_contiguous() and ctrl.shape[-1] == state.ld
+    nrand = max(m.sizes.nrand for m in batch.models)
+    assert params.dtype == torch.float32 and params.is_contiguous() and params.shape == (nrand, state.ld)
+    _capi.pg_step_dr(batch.handle, state.c(), _ptr(ctrl), _ptr(params), int(n_substeps), _stream_ptr(stream))
 
 
 def step_host(batch: Batch, state: State, ctrl_host: torch.Tensor, qpos_host: torch.Tensor, qvel_host: torch.Tensor,

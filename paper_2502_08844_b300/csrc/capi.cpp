@@ -59,6 +59,7 @@ int pg_model_info(const pg_model* m, pg_model_sizes* out) {
   out->debug_floats = h.debug_floats;
   out->adjoint_workspace_bytes = h.adj_ok ? 4 * h.ws_adj_floats : 0;
   out->nparam = h.nbody + h.nv + h.nu;
+  out->nrand = h.nrand;
   return PG_OK;
 }
 
@@ -212,6 +213,17 @@ int pg_step(const pg_batch* b, pg_state* s, const float* ctrl, int n_substeps, v
   if (n_substeps < 0) return set_error(PG_EINVAL, "n_substeps must be >= 0 (0: each model's own)");
   if (b->n > 0 && b->nu_max > 0 && !ctrl) return set_error(PG_EINVAL, "NULL ctrl");
   cudaError_t e = launch_step(b, s, ctrl, n_substeps, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_error(e, "step launch");
+  return PG_OK;
+}
+
+int pg_step_dr(const pg_batch* b, pg_state* s, const float* ctrl, const float* params, int n_substeps, void* stream) {
+  int rc = check_state(b, s);
+  if (rc) return rc;
+  if (n_substeps < 0) return set_error(PG_EINVAL, "n_substeps must be >= 0 (0: each model's own)");
+  if (b->n > 0 && b->nu_max > 0 && !ctrl) return set_error(PG_EINVAL, "NULL ctrl");
+  if (b->n > 0 && !params) return set_error(PG_EINVAL, "NULL params");
+  cudaError_t e = launch_step(b, s, ctrl, n_substeps, (cudaStream_t)stream, params);
   if (e != cudaSuccess) return cuda_error(e, "step launch");
   return PG_OK;
 }

@@ -156,7 +156,7 @@ __device__ void env_finish(const Ctx& c, const EnvArgs& E, float dt, float* qpos
   float torque = 0.f, energy = 0.f, jpos = 0.f, rate = 0.f;
   for (int a = 0; a < nu; a++) {
     const float q = W(qpos, MI(act_qposadr, a)), qd = W(qvel, MI(act_dof, a));
-    const float tau = MF(act_kp, a) * (st[a * ld] - q) - MF(act_kd, a) * qd;
+    const float tau = actuator_force(c, a, st[a * ld]);
     torque += tau * tau;
     energy += fabsf(qd * tau);
     const float dq = q - T.q_default[a];

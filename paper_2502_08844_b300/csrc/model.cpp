@@ -253,8 +253,8 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
   }
   if (nslot > kMaxSlot) return set_error(PG_ECAPACITY, "candidate contact slots exceed the kernel limit (64)");
   // ---- actuators ----
-  std::vector<int> atype(nu), adof(nu), aqadr(nu), aclim(nu);
-  std::vector<float> agear(nu), akp(nu), akd(nu), arange(2 * nu);
+  std::vector<int> atype(nu), adof(nu), aqadr(nu), aclim(nu), aflim(nu, 0);
+  std::vector<float> agear(nu), akp(nu), akd(nu), arange(2 * nu), afrange(2 * nu, 0.f);
   for (int a = 0; a < nu; a++) {
     int j = d->act_jnt[a];
     if (j < 0 || j >= njnt || jnt_type[j] == PG_JNT_FREE) return set_error(PG_EINVAL, "actuators drive hinge or slide joints");
@@ -262,6 +262,12 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
     atype[a] = d->act_type[a]; adof[a] = dofadr[j]; aqadr[a] = qposadr[j]; aclim[a] = d->act_ctrllimited[a];
     agear[a] = d->act_gear[a]; akp[a] = d->act_kp[a]; akd[a] = d->act_kd[a];
     arange[2 * a] = d->act_ctrlrange[2 * a]; arange[2 * a + 1] = d->act_ctrlrange[2 * a + 1];
+    if (d->act_forcelimited && d->act_forcelimited[a]) {
+      if (!d->act_forcerange) return set_error(PG_EINVAL, "act_forcelimited needs act_forcerange");
+      const float lo = d->act_forcerange[2 * a], hi = d->act_forcerange[2 * a + 1];
+      if (!(lo <= hi)) return set_error(PG_EINVAL, "act_forcerange must satisfy lo <= hi");
+      aflim[a] = 1; afrange[2 * a] = lo; afrange[2 * a + 1] = hi;
+    }
   }
   std::vector<int> limit_jnt;
   for (int j = 0; j < njnt; j++)
@@ -350,6 +356,11 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
   h.o_act_type = B.ints(atype); h.o_act_dof = B.ints(adof); h.o_act_qposadr = B.ints(aqadr);
   h.o_act_gear = B.floats(agear); h.o_act_kp = B.floats(akp); h.o_act_kd = B.floats(akd);
   h.o_act_ctrllimited = B.ints(aclim); h.o_act_range = B.floats(arange);
+  h.o_act_forcelimited = B.ints(aflim); h.o_act_forcerange = B.floats(afrange);
+  h.dr_com = 2;
+  h.dr_arm = 2 + 3 * nbody;
+  h.dr_cal = 2 + 3 * nbody + nv;
+  h.nrand = 2 + 3 * nbody + nv + nu;
   h.o_limit_jnt = B.ints(limit_jnt);
   while (B.w.size() % 4) B.w.push_back(0u);
   h.words = (int)B.w.size();
@@ -445,6 +456,8 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
     }
     if (npair > 0 && !tree_hessian) ok = false;
     if (d->cone == PG_CONE_ELLIPTIC) ok = false;
+    for (int a = 0; a < nu; a++)
+      if (aflim[a]) ok = false;   // the reverse sweep has no clipped-force branch
     g.adj_ok = ok ? 1 : 0;
     h.adj_ok = g.adj_ok;
     h.ws_adj_floats = g.ws_adj_floats;

@@ -65,7 +65,8 @@ int set_error(int code, const std::string& msg);
 int compile_model(const pg_model_desc* d, pg_model* out);
 
 // kernel launchers (step.cu)
-cudaError_t launch_step(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st);
+cudaError_t launch_step(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st,
+                        const float* dr = nullptr);
 cudaError_t launch_debug(const pg_batch* b, const pg_state* s, const float* ctrl, int64_t env, float* out,
                          cudaStream_t st);
 cudaError_t launch_reset(const pg_batch* b, const pg_state* s, const uint8_t* mask, const float* qpos0,
@@ -81,12 +82,14 @@ cudaError_t launch_step_tape(const pg_batch* b, const pg_state* s, const float* 
 #define PG_DECLARE_STEP_KERNELS(NS)                                                                               \
   namespace NS {                                                                                                 \
   cudaError_t configure(size_t smem_bytes);                                                                      \
-  cudaError_t step(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st);    \
+  cudaError_t step(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st,     \
+                   const float* dr = nullptr);                                                                   \
   cudaError_t step_tape(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, float* tape,     \
                         int tape_rows, cudaStream_t st);                                                         \
   cudaError_t debug(const pg_batch* b, const pg_state* s, const float* ctrl, int64_t env, float* out,            \
                     cudaStream_t st);                                                                            \
-  cudaError_t step_spec(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st);\
+  cudaError_t step_spec(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st,\
+                        const float* dr = nullptr);                                                              \
   cudaError_t step_spec_tape(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, float* tape,\
                              int tape_rows, cudaStream_t st);                                                   \
   cudaError_t step_env(const pg_batch* b, const pg_state* s, const EnvArgs& E, int n_substeps, cudaStream_t st);  \

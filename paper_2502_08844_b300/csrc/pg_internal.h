@@ -45,6 +45,9 @@ struct ModelHdr {
   int o_pair_g1, o_pair_g2, o_pair_friction, o_pair_condim, o_pair_slotadr, o_pair_nslot, o_pair_coladr,
       o_pair_ncol, o_col_dof, o_col_sign, o_slot_pair;
   int o_act_type, o_act_dof, o_act_qposadr, o_act_gear, o_act_kp, o_act_kd, o_act_ctrllimited, o_act_range;
+  int o_act_forcelimited, o_act_forcerange;
+  int nrand;          // rows of the per-environment parameters of pg_step_dr
+  int dr_com, dr_arm, dr_cal;   // their first rows: COM offsets, armature, calibration offsets
   int o_limit_jnt;
   int words;   // total blob size
   // per-environment workspace layout (element offsets, see above)

@@ -339,7 +339,9 @@ struct Ctx {
   int64_t ld;
   int64_t env;
   const float* __restrict__ hf;   // the model's heightfield elevations (device memory), or NULL
+  const float* __restrict__ dr;   // per-environment parameters ([nrand][ld], pg_step_dr), or NULL
 };
+
 
 #define MI(name, i) (c.I[c.h.o_##name + (i)])
 #define MF(name, i) (c.F[c.h.o_##name + (i)])
@@ -352,6 +354,35 @@ __device__ __forceinline__ void S3(const Ctx& c, int off, float3 v) {
   c.w[off * c.S] = v.x; c.w[(off + 1) * c.S] = v.y; c.w[(off + 2) * c.S] = v.z;
 }
 __device__ __forceinline__ float3 T3(const float* t) { return make_float3(t[0], t[1], t[2]); }
+
+// row k of this environment's parameters (pg_step_dr)
+__device__ __forceinline__ float dr_row(const Ctx& c, int k) { return __ldg(c.dr + k * c.ld + c.env); }
+
+// body b's mass and centre of mass (body frame), with this environment's payload on body 1 and
+// centre-of-mass offsets
+__device__ __forceinline__ void body_massprops(const Ctx& c, int b, float& m, float3& ipos) {
+  m = MF(body_mass, b);
+  ipos = T3(&MF(body_ipos, 3 * b));
+  if (c.dr) {
+    if (b == 1) m += dr_row(c, 1);
+    ipos = ipos + make_float3(dr_row(c, c.h.dr_com + 3 * b), dr_row(c, c.h.dr_com + 3 * b + 1),
+                              dr_row(c, c.h.dr_com + 3 * b + 2));
+  }
+}
+
+// actuator a's force at control u (motor: gear * u; PD: kp (u + calibration - q) - kd qd), u
+// already clipped to a limited control range, then clipped to a limited force range
+__device__ __forceinline__ float actuator_force(const Ctx& c, int a, float u) {
+  float tau;
+  if (MI(act_type, a) == PG_ACT_MOTOR) {
+    tau = MF(act_gear, a) * u;
+  } else {
+    if (c.dr) u += dr_row(c, c.h.dr_cal + a);
+    tau = MF(act_kp, a) * (u - W(qpos, MI(act_qposadr, a))) - MF(act_kd, a) * W(qvel, MI(act_dof, a));
+  }
+  if (MI(act_forcelimited, a)) tau = fminf(fmaxf(tau, MF(act_forcerange, 2 * a)), MF(act_forcerange, 2 * a + 1));
+  return tau;
+}
 
 // reference point of body b's tree: the free root's position, else the root's fixed frame origin
 __device__ __forceinline__ float3 tree_origin(const Ctx& c, int b) {
@@ -429,8 +460,10 @@ __device__ void kinematics(const Ctx& c) {
     // spatial inertia about o: I_com(world) + m (|c|^2 1 - c c^T), h = m c
     float R[9];
     qmat(q, R);
-    const float3 com = x + mat_mul(R, T3(&MF(body_ipos, 3 * b)));
-    const float m = MF(body_mass, b);
+    float m;
+    float3 ip;
+    body_massprops(c, b, m, ip);
+    const float3 com = x + mat_mul(R, ip);
     const float* In = &MF(body_inertia, 6 * b);
     const float Ib[9] = {In[0], In[3], In[4], In[3], In[1], In[5], In[4], In[5], In[2]};
     float T[9];
@@ -543,7 +576,7 @@ __device__ void crba(const Ctx& c) {
     for (int t = 0; t < n; t++) {
       const int i = MI(Lcol, r0 + t);
       float v = dot3(W3(c, h.w_cdof + 6 * i), fa) + dot3(W3(c, h.w_cdof + 6 * i + 3), fl);
-      if (t == 0) v += MF(dof_armature, j);
+      if (t == 0) v += MF(dof_armature, j) + (c.dr ? dr_row(c, h.dr_arm + j) : 0.f);
       W(M, r0 + t) = v;
     }
   }
@@ -677,9 +710,7 @@ __device__ void smooth_acc(const Ctx& c, float* dbg) {
     const int d = MI(act_dof, a);
     float u = c.ctrl[a * c.ld + c.env];
     if (MI(act_ctrllimited, a)) u = fminf(fmaxf(u, MF(act_range, 2 * a)), MF(act_range, 2 * a + 1));
-    const float tau = MI(act_type, a) == PG_ACT_MOTOR
-                          ? MF(act_gear, a) * u
-                          : MF(act_kp, a) * (u - W(qpos, MI(act_qposadr, a))) - MF(act_kd, a) * W(qvel, d);
+    const float tau = actuator_force(c, a, u);
     W(a0, d) += tau;
     if (DEBUG) dbg[h.dbg_act + d] += tau;
   }
@@ -1144,7 +1175,7 @@ __device__ void row_params(const Ctx& c, int nc) {
   for (int k = 0; k < MC; k++) {
     const bool valid = k < nc;
     const int p = valid ? con_pair(c, k) : 0;
-    W(gmu, k) = valid && MI(pair_condim, p) == 3 ? MF(pair_friction, p) : 0.f;
+    W(gmu, k) = valid && MI(pair_condim, p) == 3 ? MF(pair_friction, p) * (c.dr ? dr_row(c, 0) : 1.f) : 0.f;
     W(gcond, k) = valid ? (float)MI(pair_condim, p) : 0.f;
   }
   rows_dot(c, h.w_qvel, h.w_rv);
@@ -1576,7 +1607,10 @@ __device__ void substep(const Ctx& c, uint32_t& status, float* dbg, uint32_t cnt
       body_frame(c, b, x, q);
       float R[9];
       qmat(q, R);
-      const float3 com = b ? x + mat_mul(R, T3(&MF(body_ipos, 3 * b))) : make_float3(0.f, 0.f, 0.f);
+      float mb;
+      float3 ip;
+      if (b) body_massprops(c, b, mb, ip);
+      const float3 com = b ? x + mat_mul(R, ip) : make_float3(0.f, 0.f, 0.f);
       dbg[h.dbg_xpos + 3 * b] = x.x; dbg[h.dbg_xpos + 3 * b + 1] = x.y; dbg[h.dbg_xpos + 3 * b + 2] = x.z;
       dbg[h.dbg_xcom + 3 * b] = com.x; dbg[h.dbg_xcom + 3 * b + 1] = com.y; dbg[h.dbg_xcom + 3 * b + 2] = com.z;
       for (int k = 0; k < 9; k++) dbg[h.dbg_xmat + 9 * b + k] = R[k];

@@ -29,6 +29,7 @@ struct StepArgs {
   int tape_rows, tape_nq, tape_nv;    // rows per substep entry; the batch's nq_max, nv_max
   int model_off[kMaxModels];          // word offset of each model's blob in `blob`
   const float* hfield[kMaxModels];    // each model's heightfield elevations (device), or NULL
+  const float* dr;                    // per-environment parameters (pg_step_dr), or NULL
   EnvArgs env;                        // the locomotion task of an environment step (ENV below)
   uint32_t blob[kMaxParamWords];      // the batch's model blobs (header + tables)
 };
@@ -64,7 +65,7 @@ __device__ __forceinline__ void step_body(const StepArgs& A) {
   const int64_t env = tile.env0 + t;
   float* w = smem + warp * (S * h.ws_floats) + lane;
   Ctx c{h, S, reinterpret_cast<const int*>(blob), reinterpret_cast<const float*>(blob), w, ENV ? A.env.state : A.ctrl,
-        A.ld, env, A.hfield[tile.model]};
+        A.ld, env, A.hfield[tile.model], A.dr};
   if (ENV) env_targets(c, A.env);
   for (int k = 0; k < h.nq; k++) W(qpos, k) = A.qpos[k * A.ld + env];
   uint32_t status = 0;

@@ -50,26 +50,31 @@ static void make_args(StepArgs& A, const pg_batch* b, const pg_state* s, const f
   A.tape = nullptr;
   A.tape_rows = A.tape_nq = A.tape_nv = 0;
   A.env.state = nullptr;
+  A.dr = nullptr;
   for (int k = 0; k < kMaxModels; k++) A.model_off[k] = k < (int)b->blob_off.size() ? b->blob_off[k] : 0;
   for (int k = 0; k < kMaxModels; k++) A.hfield[k] = b->hfield_ptr[k];
   std::memcpy(A.blob, b->blob_host.data(), b->blob_host.size() * sizeof(uint32_t));
 }
 
-cudaError_t step(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st) {
+cudaError_t step(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st,
+                 const float* dr) {
   if (b->ntiles == 0) return cudaSuccess;
   static thread_local StepArgs A;
   make_args(A, b, s, ctrl);
   A.n_substeps = n_substeps;
+  A.dr = dr;
   step_kernel<false, false><<<b->ntiles, b->threads, b->smem_bytes, st>>>(A);
   return cudaGetLastError();
 }
 
 // the batch's model-specialised kernel (same argument block)
-cudaError_t step_spec(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st) {
+cudaError_t step_spec(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st,
+                      const float* dr) {
   if (b->ntiles == 0) return cudaSuccess;
   static thread_local StepArgs A;
   make_args(A, b, s, ctrl);
   A.n_substeps = n_substeps;
+  A.dr = dr;
   void* params[] = {&A};
   return cudaLaunchKernel((const void*)b->spec_kernel, dim3(b->ntiles), dim3(b->threads), params, b->smem_bytes, st);
 }

@@ -615,6 +615,24 @@ def commands(config: int, n_envs: int, env0: int = 0, draw: int = 0) -> np.ndarr
     return _f32((2.0 * u - 1.0) * np.array(COMMAND_RANGE)[None, :])
 
 
+def randomized_params(m: Model, config: int, n_envs: int, env0: int = 0) -> np.ndarray:
+    """Per-environment physical parameters [N, 2 + 3 nbody + nv + nu] float32 in the layout of
+    pg_step_dr: friction scale U[0.6, 1.4], payload U[0, 2] kg on body 1, centre-of-mass offsets
+    U(+-2 cm), added armature U[0, 0.01] kg m^2, calibration offsets U(+-0.05) rad; draw index
+    2^34 + k of each env's stream."""
+    nb, nv, nu = m.nbody, m.nv, m.nu
+    k = 2 + 3 * nb + nv + nu
+    seeds = env_seeds(config, n_envs, env0)[:, None]
+    u = uniform01(seeds, np.uint64(1 << 34) + np.arange(k, dtype=np.uint64)[None, :])
+    p = np.zeros((n_envs, k))
+    p[:, 0] = 0.6 + 0.8 * u[:, 0]
+    p[:, 1] = 2.0 * u[:, 1]
+    p[:, 2:2 + 3 * nb] = 0.02 * (2.0 * u[:, 2:2 + 3 * nb] - 1.0)
+    p[:, 2 + 3 * nb:2 + 3 * nb + nv] = 0.01 * u[:, 2 + 3 * nb:2 + 3 * nb + nv]
+    p[:, 2 + 3 * nb + nv:] = 0.05 * (2.0 * u[:, 2 + 3 * nb + nv:] - 1.0)
+    return _f32(p)
+
+
 def policy_actions(m: Model, config: int, n_envs: int, t0: int, n_steps: int, env0: int = 0) -> np.ndarray:
     """Policy outputs [n_steps, N, nu] float32, uniform in [-1, 1]; draw index
     2^33 + t nu + j of each env's stream."""

@@ -85,3 +85,22 @@ def test_adjoint_scope_and_parameter_rows():
         assert s.nparam == m.nbody + m.nv + m.nu
         if ok:
             assert s.adjoint_workspace_bytes >= s.workspace_bytes
+    q = W.quadruped()
+    q.act_forcelimited = np.ones(q.nu, np.int32)
+    q.act_forcerange = np.tile(np.array([[-4.0, 4.0]], np.float32), (q.nu, 1))
+    assert core.CompiledModel(q).sizes.adjoint_workspace_bytes == 0      # torque limits: outside
+    assert core.CompiledModel(W.quadruped_rough()).sizes.adjoint_workspace_bytes == 0   # heightfield: outside
+
+
+def test_per_environment_parameter_rows():
+    from paper_2502_08844_b300 import core
+    for f in (W.quadruped, W.cartpole, W.humanoid):
+        m = f()
+        assert core.CompiledModel(m).sizes.nrand == 2 + 3 * m.nbody + m.nv + m.nu
+    q = W.quadruped()
+    q.act_forcelimited = np.ones(q.nu, np.int32)
+    q.act_forcerange = np.tile(np.array([[4.0, -4.0]], np.float32), (q.nu, 1))
+    from paper_2502_08844_b300 import _capi
+    with pytest.raises(_capi.PgError) as ei:
+        core.CompiledModel(q)
+    assert ei.value.code == _capi.PG_EINVAL
