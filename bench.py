@@ -298,6 +298,53 @@ def measure_rough_terrain(dev, n: int = 8192, steps: int = 200, specialize: bool
             "kernel": "model-specialised" if specialize else "generic"}
 
 
+def measure_pixels(dev, n: int = 8192, steps: int = 50):
+    """Pixel observations of the cartpole: 8192 environments, one 64 x 64 RGB (uint8) ray-traced
+    image each per control step (pg_render after pg_step), the paper's CartpoleBalance-from-pixels
+    setting (Sec. 5; App. "Madrona benchmark").  Reports rendered frames/s alone and
+    physics + render env-steps/s, CUDA events around `steps` steps."""
+    import torch
+    from paper_2502_08844_b300 import core
+    m = W.cartpole_pixels()
+    scene = W.cartpole_scene()
+    batch = core.Batch([(core.CompiledModel(m), n)])
+    batch.specialize()
+    st = core.State(batch, dev)
+    ld = st.ld
+    q0, v0 = W.initial_state(m, 0, n)
+    st.qpos.copy_(torch.from_numpy(core.to_soa(q0, ld, batch.nq_max)))
+    st.qvel.copy_(torch.from_numpy(core.to_soa(v0, ld, batch.nv_max)))
+    U = np.zeros((steps, 1, ld), np.float32)
+    U[:, :, :n] = W.actions(m, 0, n, 0, steps).transpose(0, 2, 1)
+    ctrl = torch.from_numpy(U).to(dev)
+    px = torch.zeros((n, scene.height, scene.width, 3), dtype=torch.uint8, device=dev)
+
+    def timed(f):
+        f()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(); f(); b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3
+
+    def render_only():
+        for _ in range(steps):
+            core.render(batch, st, scene, px)
+
+    def step_and_render():
+        for t in range(steps):
+            core.step(batch, st, ctrl[t], 1)
+            core.render(batch, st, scene, px)
+
+    t_r, t_sr = timed(render_only), timed(step_and_render)
+    rays = n * scene.width * scene.height
+    return {"frames_per_s": n * steps / t_r, "env_steps_per_s_with_pixels": n * steps / t_sr,
+            "ms_per_render": 1e3 * t_r / steps, "primary_rays_per_s": rays * steps / t_r,
+            "resolution": [scene.width, scene.height], "envs": n, "steps": steps,
+            "output_bytes_per_frame": 3 * rays,
+            "paper_context": "cartpole with pixels ~403,000 steps/s (Madrona + MJX, Sec. 5; other hardware)"}
+
+
 def run_reference(args):
     """Reference arm: the FP64 oracle as it stands, timed on the host cores."""
     ws, rank, _ = dist_env()
@@ -505,6 +552,7 @@ def run_ours(args):
     if not args.no_env:
         line["env_layer"] = measure_env_layer(dev, specialize=kernel.startswith("model-specialised"))
         line["rough_terrain"] = measure_rough_terrain(dev, specialize=kernel.startswith("model-specialised"))
+        line["pixels"] = measure_pixels(dev)
     if not args.no_adjoint:
         adj = measure_adjoint(dev, specialize=kernel.startswith("model-specialised"))
         line["adjoint_forward_ratio"] = adj["ratio"]

@@ -406,6 +406,42 @@ int pg_env_step(const pg_batch* batch, const pg_task* task, pg_state* state, flo
                 int n_substeps, float* obs_dev, float* reward_dev, float* done_dev, float* truncated_dev,
                 float* terms_dev, void* stream);
 
+/* ---- batch ray-traced pixel observations -------------------------------------------------
+ *
+ * The paper pairs the batched physics with batch rendering for pixel-based policies (Sec. 5,
+ * Madrona batch renderer: 64 x 64 cartpole frames).  pg_render ray-traces one image per
+ * environment from the batch state, on the GPU:
+ *   * a pinhole camera shared by the batch (world position, look-at point, up vector, vertical
+ *     field of view in degrees, width x height pixels); pixel (x, y) has y = 0 at the top and
+ *     its ray passes through the pixel's centre;
+ *   * every drawn geom of the model at the environment's current pose (forward kinematics of
+ *     qpos): planes (infinite, both faces), spheres, capsules and boxes; heightfields are not
+ *     drawn;
+ *   * Lambertian shading under one directional light: colour = albedo * (ambient + diffuse *
+ *     max(0, n . l) * lit), l = -light_dir normalised, lit = 0 when a shadow ray from the hit
+ *     point towards the light meets any drawn geom; rays that hit nothing get the background.
+ * Output (device memory, caller-owned): format PG_PIXELS_U8: uint8 [n][height][width][3],
+ * round(255 * clip(colour, 0, 1)); PG_PIXELS_F32: float32 [n][height][width][3] unclipped.
+ * hits_dev (optional, int32 [n][height][width]): 0 for the background, else (geom + 1) plus
+ * 65536 when the point is in shadow.
+ * Scope: single-model batches; ngeom <= 64; width, height in 1 .. 1024.  Errors: PG_EINVAL,
+ * PG_EUNSUPPORTED (a mixed batch), PG_ECAPACITY, PG_ECUDA. */
+enum { PG_PIXELS_U8 = 0, PG_PIXELS_F32 = 1 };
+
+typedef struct pg_render_desc {
+  float cam_pos[3], cam_lookat[3], cam_up[3];
+  float fovy_deg;
+  int width, height;
+  float light_dir[3];     /* direction the light travels                                  */
+  float ambient, diffuse;
+  float background[3];
+  const float* geom_rgb;  /* [ngeom][3] albedo; a geom whose first component is < 0 is not
+                             drawn (and casts no shadow)                                    */
+} pg_render_desc;
+
+int pg_render(const pg_batch* batch, const pg_state* state, const pg_render_desc* desc, int format, void* pixels_dev,
+              int32_t* hits_dev, void* stream);
+
 const char* pg_last_error(void);
 
 #endif  /* __CUDACC_RTC__ */

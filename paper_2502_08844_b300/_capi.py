@@ -67,10 +67,20 @@ class pg_task_sizes(C.Structure):
     _fields_ = [("nobs", C.c_int), ("nterms", C.c_int), ("state_rows", C.c_int)]
 
 
+PG_PIXELS_U8, PG_PIXELS_F32 = 0, 1
+
+
+class pg_render_desc(C.Structure):
+    _fields_ = [("cam_pos", C.c_float * 3), ("cam_lookat", C.c_float * 3), ("cam_up", C.c_float * 3),
+                ("fovy_deg", C.c_float), ("width", C.c_int), ("height", C.c_int), ("light_dir", C.c_float * 3),
+                ("ambient", C.c_float), ("diffuse", C.c_float), ("background", C.c_float * 3),
+                ("geom_rgb", C.c_void_p)]
+
+
 EXPORTS = ["pg_model_compile", "pg_model_info", "pg_model_free", "pg_batch_compile", "pg_batch_info",
            "pg_batch_free", "pg_reset", "pg_step", "pg_step_dr", "pg_debug_substep", "pg_step_host", "pg_step_vjp",
            "pg_step_vjp_noalloc", "pg_batch_specialize", "pg_task_compile", "pg_task_info", "pg_task_free",
-           "pg_env_reset", "pg_env_step", "pg_last_error"]
+           "pg_env_reset", "pg_env_step", "pg_render", "pg_last_error"]
 
 if not os.path.exists(LIB_PATH):
     raise ImportError("libpg.so is not built (run `python -m paper_2502_08844_b300.build` or "
@@ -103,6 +113,8 @@ _lib.pg_task_free.restype = None
 _lib.pg_env_reset.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(pg_state)] + [C.c_void_p] * 6
 _lib.pg_env_step.argtypes = ([C.c_void_p, C.c_void_p, C.POINTER(pg_state)] + [C.c_void_p] * 5 + [C.c_int] +
                              [C.c_void_p] * 6)
+_lib.pg_render.argtypes = [C.c_void_p, C.POINTER(pg_state), C.POINTER(pg_render_desc), C.c_int, C.c_void_p,
+                           C.c_void_p, C.c_void_p]
 for _n in EXPORTS:
     if _n not in ("pg_last_error", "pg_model_free", "pg_batch_free"):
         getattr(_lib, _n).restype = C.c_int
@@ -222,3 +234,7 @@ def pg_env_step(batch, task, state: pg_state, task_state_ptr, action_ptr, cmd_pt
     _check(_lib.pg_env_step(batch, task, C.byref(state), task_state_ptr, action_ptr, cmd_ptr, qpos0_ptr, qvel0_ptr,
                             int(n_substeps), obs_ptr, reward_ptr, done_ptr, truncated_ptr, terms_ptr, stream),
            "pg_env_step")
+
+
+def pg_render(batch, state: pg_state, desc: pg_render_desc, fmt: int, pixels_ptr, hits_ptr, stream) -> None:
+    _check(_lib.pg_render(batch, C.byref(state), C.byref(desc), int(fmt), pixels_ptr, hits_ptr, stream), "pg_render")

@@ -178,6 +178,22 @@ def env_step(batch: Batch, task: Task, state: State, task_state: torch.Tensor, a
                       _ptr(done), _ptr(truncated), _ptr(terms), _stream_ptr(stream))
 
 
+def render(batch: Batch, state: State, scene: W.Scene, pixels: torch.Tensor, hits: Optional[torch.Tensor] = None,
+           stream=None) -> None:
+    """pg_render: one ray-traced image per environment of the current state into pixels
+    (uint8 [n][H][W][3] or float32 [n][H][W][3]); hits (int32 [n][H][W]) optional."""
+    fmt = _capi.PG_PIXELS_U8 if pixels.dtype == torch.uint8 else _capi.PG_PIXELS_F32
+    assert pixels.dtype in (torch.uint8, torch.float32) and pixels.is_contiguous()
+    assert pixels.shape == (state.n, scene.height, scene.width, 3)
+    assert hits is None or (hits.dtype == torch.int32 and hits.shape == (state.n, scene.height, scene.width))
+    rgb = np.ascontiguousarray(scene.geom_rgb, np.float32)
+    f3 = lambda v: (C.c_float * 3)(*[float(x) for x in v])
+    d = _capi.pg_render_desc(f3(scene.cam_pos), f3(scene.cam_lookat), f3(scene.cam_up), float(scene.fovy_deg),
+                             int(scene.width), int(scene.height), f3(scene.light_dir), float(scene.ambient),
+                             float(scene.diffuse), f3(scene.background), rgb.ctypes.data_as(C.c_void_p))
+    _capi.pg_render(batch.handle, state.c(), d, fmt, _ptr(pixels), _ptr(hits), _stream_ptr(stream))
+
+
 def reset(batch: Batch, state: State, qpos0: torch.Tensor, qvel0: torch.Tensor, mask: Optional[torch.Tensor] = None,
           stream=None) -> None:
     assert qpos0.shape == state.qpos.shape and qvel0.shape == state.qvel.shape

@@ -548,6 +548,66 @@ MODELS["quadruped_rough"] = quadruped_rough
 
 
 # --------------------------------------------------------------------------------------
+# pixel observations: a camera, a light and the geoms' colours (configuration only)
+# --------------------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Scene:
+    """What pg_render draws: a pinhole camera, one directional light and per-geom albedo
+    (a negative first component hides a geom)."""
+
+    cam_pos: tuple
+    cam_lookat: tuple
+    cam_up: tuple
+    fovy_deg: float
+    width: int
+    height: int
+    light_dir: tuple
+    ambient: float
+    diffuse: float
+    background: tuple
+    geom_rgb: np.ndarray      # [ngeom, 3] float32
+
+
+def cartpole_pixels() -> Model:
+    """The cartpole with a floor plane 6 cm under the cart's centre for its pixel
+    observations (the floor pairs with nothing: the physics is the cartpole's)."""
+    m = cartpole()
+    m.name = "cartpole_pixels"
+    m.geom_type = np.concatenate([m.geom_type, np.array([PLANE], np.int32)])
+    m.geom_body = np.concatenate([m.geom_body, np.array([0], np.int32)])
+    m.geom_pos = np.concatenate([m.geom_pos, _f32([[0, 0, -0.06]])])
+    m.geom_quat = np.concatenate([m.geom_quat, _f32([[1, 0, 0, 0]])])
+    m.geom_size = np.concatenate([m.geom_size, _f32([[0, 0, 0]])])
+    m.geom_mass = np.concatenate([m.geom_mass, _f32([0])])
+    return m
+
+
+MODELS["cartpole_pixels"] = cartpole_pixels
+
+
+def cartpole_scene(width: int = 64, height: int = 64) -> Scene:
+    """The 64 x 64 pixel observation of the cartpole (the resolution of the paper's pixel
+    policies): camera 3 m in front, looking at the pole's middle, light from above and behind."""
+    return Scene(cam_pos=(0.0, -3.0, 0.7), cam_lookat=(0.0, 0.0, 0.4), cam_up=(0.0, 0.0, 1.0), fovy_deg=45.0,
+                 width=width, height=height, light_dir=(0.35, 0.45, -1.0), ambient=0.25, diffuse=0.75,
+                 background=(0.45, 0.6, 0.85),
+                 geom_rgb=_f32([[0.2, 0.35, 0.85], [0.9, 0.55, 0.15], [0.6, 0.6, 0.6]]))
+
+
+def quadruped_scene(width: int = 64, height: int = 64) -> Scene:
+    """The quadruped from the front-left, every geom drawn (planes, boxes, capsules, spheres)."""
+    m = quadruped()
+    rgb = np.tile(_f32([[0.75, 0.45, 0.2]]), (m.ngeom, 1))
+    rgb[0] = (0.55, 0.6, 0.55)                     # floor
+    rgb[1] = (0.2, 0.3, 0.8)                       # torso
+    rgb[m.geom_type == SPHERE] = (0.1, 0.1, 0.1)   # feet
+    return Scene(cam_pos=(0.9, -1.1, 0.6), cam_lookat=(0.0, 0.0, 0.2), cam_up=(0.0, 0.0, 1.0), fovy_deg=50.0,
+                 width=width, height=height, light_dir=(-0.3, 0.5, -1.0), ambient=0.3, diffuse=0.7,
+                 background=(0.5, 0.65, 0.9), geom_rgb=_f32(rgb))
+
+
+# --------------------------------------------------------------------------------------
 # locomotion task around the step (configuration only: which geoms are feet, the weights of
 # the reward table's terms, the action mapping; the arithmetic lives in the kernels and, for
 # tests, in the oracle)

@@ -1,0 +1,108 @@
+"""GPU parity of the batch ray tracer (pg_render) against the FP64 oracle (oracle/render.py)
+through the C ABI.
+
+Which geom a ray hits, and whether its hit point is in shadow, are decided by floating-point
+comparisons; along a silhouette or a shadow edge a float32 ray and a float64 ray can go either
+way, and both images are then correct.  So the hit codes must agree on every pixel except
+those on an edge of the oracle's own code map (a 4-neighbour with another code), and at most
+1 % of the pixels may differ at all.  Where the codes agree off an edge, float colours agree to
+1e-4 (the rounding of a dot product of unit vectors and a few products) and uint8 colours to one
+code.  On an edge of a round shape the hit distance is the square root of a vanishing
+discriminant, so the shading normal's error grows like the square root of the rounding (~3e-4
+at float32): there agreeing pixels are held to 2e-2."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from oracle import render as RD
+from paper_2502_08844_b300 import core, workloads as W
+from tests.gpu_helpers import GpuRun
+
+pytestmark = pytest.mark.gpu
+
+
+def _edge(code):
+    e = np.zeros_like(code, bool)
+    e[1:, :] |= code[1:, :] != code[:-1, :]
+    e[:-1, :] |= code[:-1, :] != code[1:, :]
+    e[:, 1:] |= code[:, 1:] != code[:, :-1]
+    e[:, :-1] |= code[:, :-1] != code[:, 1:]
+    return e
+
+
+def _render_gpu(run, scene, fmt):
+    n = run.n
+    px = torch.zeros((n, scene.height, scene.width, 3), dtype=torch.uint8 if fmt == "u8" else torch.float32,
+                     device="cuda")
+    hits = torch.zeros((n, scene.height, scene.width), dtype=torch.int32, device="cuda")
+    core.render(run.batch, run.state, scene, px, hits)
+    torch.cuda.synchronize()
+    return px.cpu().numpy(), hits.cpu().numpy()
+
+
+def _check(m, scene, q, v, n):
+    om = O.OracleModel(m)
+    run = GpuRun(m, n)
+    run.set_state(q, v)
+    colf, hits = _render_gpu(run, scene, "f32")
+    col8, hits8 = _render_gpu(run, scene, "u8")
+    assert np.array_equal(hits, hits8)
+    differ = 0
+    drawn = 0
+    for e in range(n):
+        oc, ocode = RD.render(om, scene, q[e].astype(np.float64))
+        bad = hits[e] != ocode
+        assert not np.any(bad & ~_edge(ocode)), e
+        differ += bad.sum()
+        edge = _edge(ocode)
+        same = ~bad & ~edge
+        assert np.abs(colf[e][same] - oc[same]).max() <= 1e-4, e
+        assert np.abs(col8[e][same].astype(int) - RD.quantise(oc)[same].astype(int)).max() <= 1, e
+        on_edge = ~bad & edge
+        if on_edge.any():
+            assert np.abs(colf[e][on_edge] - oc[on_edge]).max() <= 2e-2, e
+        drawn += (ocode > 0).sum()
+    assert differ <= 0.01 * n * scene.width * scene.height
+    return drawn
+
+
+def test_cartpole_pixels_match_oracle():
+    m = W.cartpole_pixels()
+    n = 48
+    q, v = W.initial_state(m, 0, n)
+    q = q.copy(); q[:, 0] *= 8.0; q[:, 1] *= 12.0          # carts across the view, poles swinging
+    drawn = _check(m, W.cartpole_scene(), q, v, n)
+    assert drawn > n * 1000
+
+
+def test_quadruped_pixels_match_oracle():
+    m = W.quadruped()
+    om = O.OracleModel(m)
+    q0, v0 = W.initial_state(m, 1, 12)
+    U = W.actions(m, 1, 12, 0, 40)
+    q, v, _, _ = om.rollout(q0, v0, U, 5)          # varied poses after 40 control steps
+    drawn = _check(m, W.quadruped_scene(48, 40), q.astype(np.float32), v.astype(np.float32), 12)
+    assert drawn > 12 * 500
+
+
+def test_hidden_geoms_and_argument_errors():
+    from paper_2502_08844_b300 import _capi
+    m = W.cartpole_pixels()
+    sc = W.cartpole_scene(32, 24)
+    sc.geom_rgb = sc.geom_rgb.copy(); sc.geom_rgb[1, 0] = -1.0          # hide the pole
+    run = GpuRun(m, 4)
+    q, v = W.initial_state(m, 0, 4)
+    run.set_state(q, v)
+    _, hits = _render_gpu(run, sc, "f32")
+    assert not np.any((hits & 0xFFFF) == 2)
+    mixed = core.Batch([(core.CompiledModel(W.cartpole()), 2), (core.CompiledModel(W.quadruped()), 2)])
+    st = core.State(mixed, "cuda")
+    px = torch.zeros((4, 24, 32, 3), dtype=torch.uint8, device="cuda")
+    with pytest.raises(_capi.PgError) as ei:
+        core.render(mixed, st, sc, px)
+    assert ei.value.code == _capi.PG_EUNSUPPORTED
+    bad = W.cartpole_scene(0, 24)
+    with pytest.raises(_capi.PgError) as ei:
+        core.render(run.batch, run.state, bad, torch.zeros((4, 24, 0, 3), dtype=torch.uint8, device="cuda"))
+    assert ei.value.code == _capi.PG_EINVAL
