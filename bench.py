@@ -301,8 +301,9 @@ def measure_rough_terrain(dev, n: int = 8192, steps: int = 200, specialize: bool
 def measure_pixels(dev, n: int = 8192, steps: int = 50):
     """Pixel observations of the cartpole: 8192 environments, one 64 x 64 RGB (uint8) ray-traced
     image each per control step (pg_render after pg_step), the paper's CartpoleBalance-from-pixels
-    setting (Sec. 5; App. "Madrona benchmark").  Reports rendered frames/s alone and
-    physics + render env-steps/s, CUDA events around `steps` steps."""
+    setting (Sec. 5; App. "Madrona benchmark").  Reports physics + render env-steps/s, physics
+    alone, and the frames/s the renders add (the difference of the two), CUDA events around
+    `steps` steps from the same initial state."""
     import torch
     from paper_2502_08844_b300 import core
     m = W.cartpole_pixels()
@@ -312,8 +313,8 @@ def measure_pixels(dev, n: int = 8192, steps: int = 50):
     st = core.State(batch, dev)
     ld = st.ld
     q0, v0 = W.initial_state(m, 0, n)
-    st.qpos.copy_(torch.from_numpy(core.to_soa(q0, ld, batch.nq_max)))
-    st.qvel.copy_(torch.from_numpy(core.to_soa(v0, ld, batch.nv_max)))
+    Q0 = torch.from_numpy(core.to_soa(q0, ld, batch.nq_max)).to(dev)
+    V0 = torch.from_numpy(core.to_soa(v0, ld, batch.nv_max)).to(dev)
     U = np.zeros((steps, 1, ld), np.float32)
     U[:, :, :n] = W.actions(m, 0, n, 0, steps).transpose(0, 2, 1)
     ctrl = torch.from_numpy(U).to(dev)
@@ -327,18 +328,23 @@ def measure_pixels(dev, n: int = 8192, steps: int = 50):
         torch.cuda.synchronize()
         return a.elapsed_time(b) / 1e3
 
-    def render_only():
-        for _ in range(steps):
-            core.render(batch, st, scene, px)
+    def step_only():
+        core.reset(batch, st, Q0, V0)
+        for t in range(steps):
+            core.step(batch, st, ctrl[t], 1)
 
     def step_and_render():
+        core.reset(batch, st, Q0, V0)
         for t in range(steps):
             core.step(batch, st, ctrl[t], 1)
             core.render(batch, st, scene, px)
 
-    t_r, t_sr = timed(render_only), timed(step_and_render)
+    # every loop starts from the same state and sees the same sequence of states
+    t_s, t_sr = timed(step_only), timed(step_and_render)
+    t_r = max(t_sr - t_s, 1e-9)
     rays = n * scene.width * scene.height
     return {"frames_per_s": n * steps / t_r, "env_steps_per_s_with_pixels": n * steps / t_sr,
+            "env_steps_per_s_physics_only": n * steps / t_s,
             "ms_per_render": 1e3 * t_r / steps, "primary_rays_per_s": rays * steps / t_r,
             "resolution": [scene.width, scene.height], "envs": n, "steps": steps,
             "output_bytes_per_frame": 3 * rays,
