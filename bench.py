@@ -584,10 +584,16 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-env", action="store_true", help="skip the locomotion-task measurement")
+    ap.add_argument("--pixels-only", type=int, default=0, metavar="N",
+                    help="only the pixel-observation measurement, on N cartpoles (for profiling the renderer)")
     ap.add_argument("--generic-kernel", action="store_true", help="skip pg_batch_specialize")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.pixels_only:
+        import torch
+        print(json.dumps(measure_pixels(torch.device("cuda"), n=args.pixels_only, steps=max(args.steps, 1))))
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -50,6 +50,7 @@ struct pg_batch {
   cudaKernel_t spec_kernel_tape = nullptr;   // the same with the substep tape (adjoint replay)
   cudaKernel_t spec_kernel_vjp = nullptr;    // the adjoint's reverse sweep (NULL outside its scope)
   cudaKernel_t spec_kernel_env = nullptr;    // the environment step of a locomotion task
+  cudaKernel_t spec_kernel_dr = nullptr;     // the step with per-environment parameters
   // staging buffer of the host-buffer path (allocated on its first use)
   float* d_ctrl_stage = nullptr;
   size_t ctrl_stage_floats = 0;

@@ -165,6 +165,7 @@ std::string spec_source(const pg_model* m) {
   s += "extern \"C\" __global__ void " + lb + " pg_step_spec(const __grid_constant__ pg::StepArgs A) { pg::step_body<false, false, 0>(A); }\n";
   s += "extern \"C\" __global__ void " + lb + " pg_step_spec_tape(const __grid_constant__ pg::StepArgs A) { pg::step_body<false, true, 0>(A); }\n";
   s += "extern \"C\" __global__ void " + lb + " pg_env_step_spec(const __grid_constant__ pg::StepArgs A) { pg::step_body<false, false, 0, true>(A); }\n";
+  s += "extern \"C\" __global__ void " + lb + " pg_step_spec_dr(const __grid_constant__ pg::StepArgs A) { pg::step_body<false, false, 0, false, true>(A); }\n";
   if (adj)
     s += "#include \"adjoint_body.cuh\"\nextern \"C\" __global__ void __launch_bounds__(64) pg_vjp_spec(const __grid_constant__ pg::VjpArgs A) { pg::vjp_body<0, " + std::string(vjp_smem_soa(m->hdr_adj.ws_adj_floats) > 0 ? "true" : "false") + ">(A); }\n";
   return s;
@@ -232,10 +233,11 @@ extern "C" int pg_batch_specialize(pg_batch* b) {
   cudaLibrary_t lib = nullptr;
   cudaError_t e = cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
   if (e != cudaSuccess) return set_error(PG_ECUDA, std::string("cudaLibraryLoadData: ") + cudaGetErrorString(e));
-  cudaKernel_t k = nullptr, kt = nullptr, kv = nullptr, ke = nullptr;
+  cudaKernel_t k = nullptr, kt = nullptr, kv = nullptr, ke = nullptr, kd = nullptr;
   e = cudaLibraryGetKernel(&k, lib, "pg_step_spec");
   if (e == cudaSuccess) e = cudaLibraryGetKernel(&kt, lib, "pg_step_spec_tape");
   if (e == cudaSuccess) e = cudaLibraryGetKernel(&ke, lib, "pg_env_step_spec");
+  if (e == cudaSuccess) e = cudaLibraryGetKernel(&kd, lib, "pg_step_spec_dr");
   if (e == cudaSuccess && b->models[0]->hdr.adj_ok && b->models[0]->hdr.cone != PG_CONE_ELLIPTIC)
     e = cudaLibraryGetKernel(&kv, lib, "pg_vjp_spec");
   int dev = 0;
@@ -246,6 +248,8 @@ extern "C" int pg_batch_specialize(pg_batch* b) {
     e = cudaKernelSetAttributeForDevice(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem_bytes, dev);
   if (e == cudaSuccess)
     e = cudaKernelSetAttributeForDevice(ke, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem_bytes, dev);
+  if (e == cudaSuccess)
+    e = cudaKernelSetAttributeForDevice(kd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem_bytes, dev);
   if (e == cudaSuccess && kv) {
     if (vjp_smem_soa(b->models[0]->hdr_adj.ws_adj_floats) > 0)   // workspace in shared memory
       e = cudaKernelSetAttributeForDevice(kv, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem, dev);
@@ -261,5 +265,6 @@ extern "C" int pg_batch_specialize(pg_batch* b) {
   b->spec_kernel_tape = kt;
   b->spec_kernel_vjp = kv;
   b->spec_kernel_env = ke;
+  b->spec_kernel_dr = kd;
   return PG_OK;
 }

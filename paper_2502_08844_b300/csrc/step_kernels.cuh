@@ -16,9 +16,9 @@
 namespace pg {
 namespace {
 
-template <bool DEBUG, bool TAPE, bool ENV = false>
+template <bool DEBUG, bool TAPE, bool ENV = false, bool DR = false>
 __global__ void __launch_bounds__(kMaxEnvsPerCta) step_kernel(const __grid_constant__ StepArgs A) {
-  step_body<DEBUG, TAPE, 0, ENV>(A);
+  step_body<DEBUG, TAPE, 0, ENV, DR>(A);
 }
 
 }  // namespace
@@ -31,6 +31,9 @@ cudaError_t configure(size_t smem_bytes) {
   e = cudaFuncSetAttribute(step_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(step_kernel<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(step_kernel<false, false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem_bytes);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(step_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
 }
@@ -63,7 +66,8 @@ cudaError_t step(const pg_batch* b, const pg_state* s, const float* ctrl, int n_
   make_args(A, b, s, ctrl);
   A.n_substeps = n_substeps;
   A.dr = dr;
-  step_kernel<false, false><<<b->ntiles, b->threads, b->smem_bytes, st>>>(A);
+  if (dr) step_kernel<false, false, false, true><<<b->ntiles, b->threads, b->smem_bytes, st>>>(A);
+  else step_kernel<false, false><<<b->ntiles, b->threads, b->smem_bytes, st>>>(A);
   return cudaGetLastError();
 }
 
@@ -76,7 +80,8 @@ cudaError_t step_spec(const pg_batch* b, const pg_state* s, const float* ctrl, i
   A.n_substeps = n_substeps;
   A.dr = dr;
   void* params[] = {&A};
-  return cudaLaunchKernel((const void*)b->spec_kernel, dim3(b->ntiles), dim3(b->threads), params, b->smem_bytes, st);
+  return cudaLaunchKernel((const void*)(dr ? b->spec_kernel_dr : b->spec_kernel), dim3(b->ntiles), dim3(b->threads),
+                          params, b->smem_bytes, st);
 }
 
 cudaError_t step_spec_tape(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, float* tape,
