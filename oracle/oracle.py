@@ -37,6 +37,7 @@ class _Desc(C.Structure):
         ("max_contacts", C.c_int),
         ("hfield_nrow", C.c_int), ("hfield_ncol", C.c_int), ("hfield_data", _dp),
         ("act_forcelimited", _ip), ("act_forcerange", _dp),
+        ("dof_frictionloss", _dp),
     ]
 
 
@@ -135,6 +136,7 @@ class OracleModel:
             None if getattr(m, "hfield", None) is None else D("hf", m.hfield),
             None if getattr(m, "act_forcelimited", None) is None else I("afl", m.act_forcelimited),
             None if getattr(m, "act_forcerange", None) is None else D("afr", m.act_forcerange),
+            None if getattr(m, "dof_frictionloss", None) is None else D("dfl", m.dof_frictionloss),
         )
         err = C.create_string_buffer(256)
         h = L.orc_model_new(C.byref(desc), err, 256)
@@ -288,7 +290,8 @@ def _kinds(kind, mu, nr):
 def solve(M, a0, J, aref, D, warm=None, cap=-1, kind=None, mu=None):
     """Newton solve on raw data; cap < 0 runs to convergence.  Returns (qacc, force, iters, converged).
     kind / mu (optional, per row): 0 scalar one-sided row, 1 elliptic normal row followed by its
-    two tangent rows (kind 2), with the contact's friction in mu."""
+    two tangent rows (kind 2), with the contact's friction in mu; 3 friction-loss row with its
+    force bound in mu."""
     M = _d(M); a0 = _d(a0); J = _d(J).reshape(-1, M.shape[0]); aref = _d(aref); D = _d(D)
     nv, nr = M.shape[0], J.shape[0]
     qacc = np.zeros(nv); force = np.zeros(max(nr, 1)); it = C.c_int(0)

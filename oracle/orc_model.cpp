@@ -209,7 +209,16 @@ std::string compile_model(const Desc& d, Model& m) {
   for (int j = 0; j < m.njnt; j++)
     if (m.jnt_limited[j] && m.jnt_type[j] != FREE) m.nlimited++;
   m.rows_per_contact = 4;
-  m.nrow_max = m.max_contacts * m.rows_per_contact + m.nlimited;
+  m.dof_frictionloss.assign(m.nv, 0.0);
+  m.nfric = 0;
+  if (d.dof_frictionloss)
+    for (int i = 0; i < m.nv; i++) {
+      if (!(d.dof_frictionloss[i] >= 0.0)) return "dof_frictionloss must be >= 0";
+      m.dof_frictionloss[i] = d.dof_frictionloss[i];
+      if (d.dof_frictionloss[i] > 0) m.nfric++;
+    }
+  if (m.nfric > 0 && m.cone == ELLIPTIC) return "friction loss with the elliptic cone is unsupported";
+  m.nrow_max = m.max_contacts * m.rows_per_contact + m.nlimited + m.nfric;
   return "";
 }
 

@@ -35,6 +35,7 @@ struct Desc {
   const double* solref; const double* solimp; double margin; int max_contacts;
   int hfield_nrow, hfield_ncol; const double* hfield_data;   // the model's heightfield (elevations)
   const int* act_forcelimited; const double* act_forcerange;  // actuator torque limits (NULL: none)
+  const double* dof_frictionloss;                               // [nv] joint friction loss (NULL: none)
 };
 
 // A heightfield grid: elevations e in [0, 1], row i at y = -hy + 2 hy i / (nrow - 1), column j at
@@ -69,6 +70,8 @@ struct Model {
   double solimp[5] = {0.9, 0.95, 0.001, 0.5, 2.0};
   int iterations = 4, cone = PYRAMIDAL, max_contacts = 0;
   int nlimited = 0;   // joints with limits (each contributes at most one active row)
+  std::vector<double> dof_frictionloss;   // per dof; > 0 adds a friction-loss row
+  int nfric = 0;
   int rows_per_contact = 4;
   int nrow_max = 0;
   int hf_nrow = 0, hf_ncol = 0;

@@ -694,10 +694,26 @@ template <class T> struct Rows {
   std::vector<T> r, v, aref, D, Ahat, imp;   // per row
   std::vector<int> slot;                     // contact slot (or -1 - joint for a limit)
   // row kind: 0 one-sided scalar row (pyramid edge, frictionless normal, joint limit);
-  // 1 normal row of an elliptic contact, followed by its 2 tangent rows (kind 2)
+  // 1 normal row of an elliptic contact, followed by its 2 tangent rows (kind 2);
+  // 3 joint friction-loss row (two-sided, its force bounded by mu)
   std::vector<int> kind;
-  std::vector<double> mu;                    // friction of an elliptic contact's rows
+  std::vector<double> mu;                    // friction of an elliptic contact's rows; a friction-loss row's bound
 };
+
+// Friction-loss row with residual x = J a - aref, regulariser R = 1 / D and force bound F: the
+// soft cost is the Huber function of x that keeps the row's force -s'(x) inside [-F, F]:
+//   |x| <= R F   s = D x^2 / 2           (zone 1)
+//   x > R F      s = F x - R F^2 / 2     (zone 2)
+//   x < -R F     s = -F x - R F^2 / 2    (zone 0)
+template <class T> int fric_zone(const T& x, const T& D, double F) {
+  const double rf = F / val(D);
+  return val(x) > rf ? 2 : (val(x) < -rf ? 0 : 1);
+}
+template <class T> T fric_cost(const T& x, const T& D, double F) {
+  const int z = fric_zone(x, D, F);
+  if (z == 1) return T(0.5) * D * x * x;
+  return (z == 2 ? T(F) * x : -T(F) * x) - T(0.5 * F * F) / D;
+}
 
 // Soft cost of an elliptic contact with residual x = (x_n, x_1, x_2) = J a - aref: half D times
 // the squared distance from x to the dual cone K* = {x_n >= mu |x_t|}.  With t = |x_t|:
@@ -778,7 +794,8 @@ template <class T> T cost(int nv, const std::vector<T>& M, const std::vector<T>&
     }
     T jar = -R.aref[i];
     for (int j = 0; j < nv; j++) jar = jar + R.J[i * nv + j] * a[j];
-    if (val(jar) < 0) f = f + T(0.5) * R.D[i] * jar * jar;
+    if (R.kind[i] == 3) f = f + fric_cost(jar, R.D[i], R.mu[i]);
+    else if (val(jar) < 0) f = f + T(0.5) * R.D[i] * jar * jar;
   }
   return f;
 }
@@ -882,21 +899,49 @@ template <class T> T exact_line_search(int nv, const std::vector<T>& M, const st
     quad = quad + p[i] * Mp;
     lin = lin + p[i] * Md;
   }
+  // phi'(alpha) = lin + quad alpha between breakpoints.  A one-sided row is quadratic while
+  // jar + alpha Jp < 0 (one breakpoint); a friction-loss row is quadratic inside its band
+  // |x| <= R F and linear outside it (two breakpoints), contributing +-F Jp there.
   std::vector<char> act(R.n, 0);
-  std::vector<int> bp;
+  struct Event { double alpha; int row; double x; };   // x: the residual value at the crossing
+  std::vector<Event> ev;
   for (int i = 0; i < R.n; i++) {
-    bool on = val(jar[i]) < 0 || (val(jar[i]) == 0 && val(Jp[i]) < 0);
+    const double x0 = val(jar[i]), jp = val(Jp[i]);
+    if (R.kind[i] == 3) {
+      const double rf = R.mu[i] / val(R.D[i]);
+      // zone just after alpha = 0
+      int z = x0 > rf ? 2 : (x0 < -rf ? 0 : 1);
+      if (x0 == rf && jp > 0) z = 2;
+      if (x0 == -rf && jp < 0) z = 0;
+      act[i] = (char)z;
+      if (z == 1) { quad = quad + R.D[i] * Jp[i] * Jp[i]; lin = lin + R.D[i] * Jp[i] * jar[i]; }
+      else lin = lin + (z == 2 ? T(R.mu[i]) : -T(R.mu[i])) * Jp[i];
+      for (double edge : {-rf, rf})
+        if (jp != 0 && (edge - x0) / jp > 0) ev.push_back({(edge - x0) / jp, i, edge});
+      continue;
+    }
+    bool on = x0 < 0 || (x0 == 0 && jp < 0);
     act[i] = on;
     if (on) { quad = quad + R.D[i] * Jp[i] * Jp[i]; lin = lin + R.D[i] * Jp[i] * jar[i]; }
-    if (val(Jp[i]) != 0 && -val(jar[i]) / val(Jp[i]) > 0) bp.push_back(i);
+    if (jp != 0 && -x0 / jp > 0) ev.push_back({-x0 / jp, i, 0.0});
   }
-  std::stable_sort(bp.begin(), bp.end(), [&](int x, int y) {
-    return -val(jar[x]) / val(Jp[x]) < -val(jar[y]) / val(Jp[y]);
-  });
-  for (size_t k = 0; k <= bp.size(); k++) {
+  std::stable_sort(ev.begin(), ev.end(), [](const Event& x, const Event& y) { return x.alpha < y.alpha; });
+  for (size_t k = 0; k <= ev.size(); k++) {
     T root = -lin / quad;
-    if (k == bp.size() || val(root) <= -val(jar[bp[k]]) / val(Jp[bp[k]])) return root;
-    int i = bp[k];   // crossing this breakpoint toggles row i
+    if (k == ev.size() || val(root) <= ev[k].alpha) return root;
+    const int i = ev[k].row;
+    if (R.kind[i] == 3) {   // leave the current zone, enter the one the motion leads to
+      const double jp = val(Jp[i]);
+      const int z = act[i];
+      const int zn = z == 1 ? (jp > 0 ? 2 : 0) : 1;
+      if (z == 1) { quad = quad - R.D[i] * Jp[i] * Jp[i]; lin = lin - R.D[i] * Jp[i] * jar[i]; }
+      else lin = lin - (z == 2 ? T(R.mu[i]) : -T(R.mu[i])) * Jp[i];
+      if (zn == 1) { quad = quad + R.D[i] * Jp[i] * Jp[i]; lin = lin + R.D[i] * Jp[i] * jar[i]; }
+      else lin = lin + (zn == 2 ? T(R.mu[i]) : -T(R.mu[i])) * Jp[i];
+      act[i] = (char)zn;
+      continue;
+    }
+    // crossing this breakpoint toggles row i
     if (act[i]) { quad = quad - R.D[i] * Jp[i] * Jp[i]; lin = lin - R.D[i] * Jp[i] * jar[i]; act[i] = 0; }
     else { quad = quad + R.D[i] * Jp[i] * Jp[i]; lin = lin + R.D[i] * Jp[i] * jar[i]; act[i] = 1; }
   }
@@ -938,7 +983,7 @@ template <class T> SolveResult<T> newton_solve(int nv, const std::vector<T>& M, 
       }
       T jar = -R.aref[i];
       for (int j = 0; j < nv; j++) jar = jar + R.J[i * nv + j] * x[j];
-      s[i] = val(jar) < 0;
+      s[i] = R.kind[i] == 3 ? (char)fric_zone(jar, R.D[i], R.mu[i]) : (char)(val(jar) < 0);
     }
     return s;
   };
@@ -952,6 +997,11 @@ template <class T> SolveResult<T> newton_solve(int nv, const std::vector<T>& M, 
       g[i] = s;
     }
     for (int r = 0; r < R.n; r++) {
+      if (R.kind[r] == 3 && A[r] != 1) {   // friction loss outside its band: the constant force bound
+        const T Fs = A[r] == 2 ? T(R.mu[r]) : -T(R.mu[r]);
+        for (int i = 0; i < nv; i++) g[i] = g[i] + Fs * R.J[r * nv + i];
+        continue;
+      }
       if (!A[r] || R.kind[r] == 2) continue;
       if (R.kind[r] == 1) {   // J_c^T grad s and J_c^T hess s J_c over the contact's 3 rows
         T x[3], gc[3], Hc[9];
@@ -1014,7 +1064,12 @@ template <class T> SolveResult<T> newton_solve(int nv, const std::vector<T>& M, 
     }
     T jar = -R.aref[i];
     for (int j = 0; j < nv; j++) jar = jar + R.J[i * nv + j] * a[j];
-    if (val(jar) < 0) out.force[i] = -R.D[i] * jar;
+    if (R.kind[i] == 3) {
+      const int z = fric_zone(jar, R.D[i], R.mu[i]);
+      out.force[i] = z == 1 ? -R.D[i] * jar : (z == 2 ? -T(R.mu[i]) : T(R.mu[i]));
+    } else if (val(jar) < 0) {
+      out.force[i] = -R.D[i] * jar;
+    }
   }
   return out;
 }
@@ -1111,6 +1166,14 @@ template <class T> void build_rows(const Model& m, const Forward<T>& F, const T*
       e[d] = T(-1);
       push(e, T(m.jnt_range[2 * j + 1]) - q, -1 - j);
     }
+  }
+  // joint friction loss: one two-sided row per dof with a positive loss, at zero position (its
+  // reference acceleration is the damping term alone)
+  for (int d = 0; d < nv; d++) {
+    if (!(m.dof_frictionloss[d] > 0)) continue;
+    std::vector<T> e(nv, T(0));
+    e[d] = T(1);
+    push(e, T(0), -100000 - d, 3, m.dof_frictionloss[d]);
   }
   // reference acceleration and regularisation per row
   double h = m.timestep;

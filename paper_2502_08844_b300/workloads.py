@@ -119,6 +119,7 @@ class Model:
     hfield: Optional[np.ndarray] = None        # [nrow, ncol] float32
     act_forcelimited: Optional[np.ndarray] = None   # [nu] int32: clip the actuator's force
     act_forcerange: Optional[np.ndarray] = None     # [nu, 2] (lo, hi)
+    dof_frictionloss: Optional[np.ndarray] = None   # [nv] joint friction loss (a bound on its friction force)
 
     @property
     def nbody(self) -> int:
@@ -183,10 +184,11 @@ class ModelBuilder:
         return len(self.bodies) - 1
 
     def joint(self, body: int, jtype: int, pos=(0, 0, 0), axis=(0, 0, 1), limited=False,
-              range=(0.0, 0.0), damping=0.0, armature=0.0, rotor=(0.0, 0.0, 0.0)) -> int:
+              range=(0.0, 0.0), damping=0.0, armature=0.0, rotor=(0.0, 0.0, 0.0), frictionloss=0.0) -> int:
         assert not self.joints or self.joints[-1]["body"] <= body, "joints must follow body order"
         self.joints.append(dict(body=body, type=jtype, pos=pos, axis=axis, limited=int(limited),
-                                range=range, damping=damping, armature=armature, rotor=rotor))
+                                range=range, damping=damping, armature=armature, rotor=rotor,
+                                frictionloss=frictionloss))
         return len(self.joints) - 1
 
     def geom(self, body: int, gtype: int, size, pos=(0, 0, 0), quat=(1, 0, 0, 0), mass=0.0) -> int:
@@ -266,6 +268,8 @@ class ModelBuilder:
             qpos_init=None if qpos_init is None else _f32(qpos_init),
             hfield=None if hfield is None else _f32(hfield),
         )
+        if any(j["frictionloss"] > 0 for j in J):
+            m.dof_frictionloss = _f32([j["frictionloss"] for j in dof])
         if any(a["forcelimited"] for a in self.acts):
             m.act_forcelimited = i32([a["forcelimited"] for a in self.acts])
             m.act_forcerange = _f32([a["forcerange"] for a in self.acts]).reshape(-1, 2)
