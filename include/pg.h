@@ -123,6 +123,12 @@ typedef struct pg_model_desc {
    * non-zero the actuator's force is clipped to act_forcerange[2a .. 2a+1].  NULL: no limits. */
   const int* act_forcelimited;
   const float* act_forcerange;
+  /* Joint friction loss (the hand's friction loss, App. C): [nv], NULL for none.  Each dof with
+   * a positive loss F gets a two-sided constraint row (Jacobian e_d, reference acceleration
+   * -b qvel_d) whose soft cost is the Huber function of its residual x with regulariser
+   * R = 1 / D: D x^2 / 2 while |x| <= R F, F |x| - R F^2 / 2 outside, so its force stays in
+   * [-F, F].  Not with the elliptic cone (PG_EUNSUPPORTED). */
+  const float* dof_frictionloss;
 } pg_model_desc;
 
 typedef struct pg_model pg_model;   /* opaque, library-owned */
@@ -299,7 +305,7 @@ int pg_step_host(pg_batch* batch, pg_state* state, const float* ctrl_host, float
  *   * any joints and actuators;
  *   * joint limits;
  *   * contacts only between a world-fixed plane (geom1) and spheres, capsules or boxes;
- *   * no actuator torque limits.
+ *   * no actuator torque limits and no joint friction loss.
  * Otherwise the call returns PG_EUNSUPPORTED.
  *
  * Scratch and errors.

@@ -36,7 +36,7 @@ class pg_model_desc(C.Structure):
         ("impratio", C.c_float), ("solref", _fp), ("solimp", _fp), ("margin", C.c_float),
         ("max_contacts", C.c_int), ("substeps", C.c_int),
         ("hfield_nrow", C.c_int), ("hfield_ncol", C.c_int), ("hfield_data", _fp),
-        ("act_forcelimited", _ip), ("act_forcerange", _fp),
+        ("act_forcelimited", _ip), ("act_forcerange", _fp), ("dof_frictionloss", _fp),
     ]
 
 

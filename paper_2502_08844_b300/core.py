@@ -58,7 +58,8 @@ class CompiledModel:
             0 if m.hfield is None else int(m.hfield.shape[0]), 0 if m.hfield is None else int(m.hfield.shape[1]),
             None if m.hfield is None else f(m.hfield),
             None if m.act_forcelimited is None else i(m.act_forcelimited),
-            None if m.act_forcerange is None else f(m.act_forcerange))
+            None if m.act_forcerange is None else f(m.act_forcerange),
+            None if m.dof_frictionloss is None else f(m.dof_frictionloss))
         self.handle = _capi.pg_model_compile(d)
         self.sizes = _capi.pg_model_info(self.handle)
 

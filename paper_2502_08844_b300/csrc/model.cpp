@@ -306,7 +306,18 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
   if (d->cone == PG_CONE_ELLIPTIC && d->impratio != 1.f)
     return set_error(PG_EUNSUPPORTED, "the elliptic cone is implemented for impratio = 1");
   int max_contacts = d->max_contacts < 0 ? nslot : std::min(d->max_contacts, nslot);
-  int nrow_max = 4 * max_contacts + (int)limit_jnt.size();
+  // joint friction loss: one two-sided row per dof with a positive loss, after the limit rows
+  std::vector<int> fric_dof;
+  std::vector<float> fric_F;
+  if (d->dof_frictionloss)
+    for (int i = 0; i < nv; i++) {
+      const float F = d->dof_frictionloss[i];
+      if (!(F >= 0.f) || !std::isfinite(F)) return set_error(PG_EINVAL, "dof_frictionloss must be finite and >= 0");
+      if (F > 0.f) { fric_dof.push_back(i); fric_F.push_back(F); }
+    }
+  if (!fric_dof.empty() && d->cone == PG_CONE_ELLIPTIC)
+    return set_error(PG_EUNSUPPORTED, "joint friction loss with the elliptic cone is unsupported");
+  int nrow_max = 4 * max_contacts + (int)limit_jnt.size() + (int)fric_dof.size();
   if (nrow_max > kMaxRow) return set_error(PG_ECAPACITY, "constraint rows exceed the kernel limit (128)");
 
   ModelHdr h;
@@ -362,6 +373,8 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
   h.dr_cal = 2 + 3 * nbody + nv;
   h.nrand = 2 + 3 * nbody + nv + nu;
   h.o_limit_jnt = B.ints(limit_jnt);
+  h.nfric = (int)fric_dof.size();
+  h.o_fric_dof = B.ints(fric_dof); h.o_fric_F = B.floats(fric_F);
   while (B.w.size() % 4) B.w.push_back(0u);
   h.words = (int)B.w.size();
 
@@ -458,6 +471,7 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
     if (d->cone == PG_CONE_ELLIPTIC) ok = false;
     for (int a = 0; a < nu; a++)
       if (aflim[a]) ok = false;   // the reverse sweep has no clipped-force branch
+    if (!fric_dof.empty()) ok = false;   // nor friction-loss rows
     g.adj_ok = ok ? 1 : 0;
     h.adj_ok = g.adj_ok;
     h.ws_adj_floats = g.ws_adj_floats;

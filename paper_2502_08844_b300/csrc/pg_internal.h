@@ -49,6 +49,7 @@ struct ModelHdr {
   int nrand;          // rows of the per-environment parameters of pg_step_dr
   int dr_com, dr_arm, dr_cal;   // their first rows: COM offsets, armature, calibration offsets
   int o_limit_jnt;
+  int nfric, o_fric_dof, o_fric_F;   // friction-loss rows: their dofs and force bounds
   int words;   // total blob size
   // per-environment workspace layout (element offsets, see above)
   int ws_floats;

@@ -1086,7 +1086,11 @@ __device__ void rows_dot(const Ctx& c, int X, int OUT) {
     const int d = MI(jnt_dofadr, MI(limit_jnt, li));
     c.w[(OUT + 4 * MC + li) * c.S] = W(lsgn, li) * x[d * c.S];
   }
+  for (int k = 0; k < h.nfric; k++) c.w[(OUT + 4 * MC + h.nlimited + k) * c.S] = x[MI(fric_dof, k) * c.S];
 }
+
+// first friction-loss row (rows 4 max_contacts + nlimited + k, k < nfric: the dof fric_dof[k])
+__device__ __forceinline__ int fric_row0(const ModelHdr& h) { return 4 * h.max_contacts + h.nlimited; }
 
 // impedance d(r) from solimp = (d0, dwidth, width, mid, power)
 // (x^p by a multiplication for the usual power 2; the mid-point powers come from the header)
@@ -1163,6 +1167,25 @@ __device__ __forceinline__ void ltsolve_chain3(const Ctx& c, float* z0, float* z
       z0[i * S] = y0 - l * a0;
     }
   }
+}
+
+// (M^-1)_dd = sum_k z_k^2 / D_k with z = L^-T e_d, supported on d's chain (the factor of M in L)
+__device__ float minv_diag(const Ctx& c, int d) {
+  const ModelHdr& h = c.h;
+  const float* L = c.w + h.w_L * c.S;
+  float* z = c.w + h.w_z * c.S;
+  for (int i = 0; i < h.nv; i++) z[i * c.S] = 0.f;
+  z[d * c.S] = 1.f;
+  const int rc = MI(dof_rowadr, d), n = MI(dof_depth, d);
+  float A = 0.f;
+  for (int t = 0; t <= n; t++) {
+    const int k = MI(Lcol, rc + t);
+    const float zk = z[k * c.S];
+    const int r0 = MI(dof_rowadr, k), dk = MI(dof_depth, k);
+    for (int s = 1; s <= dk; s++) z[MI(Lcol, r0 + s) * c.S] -= L[(r0 + s) * c.S] * zk;
+    A = fmaf(zk * zk, W(Dinv, k), A);
+  }
+  return A;
 }
 
 // per row: position, velocity, exact Ahat = (J M^-1 J^T)_rr = sum_k z_k z_k / D_k with
@@ -1251,24 +1274,11 @@ __device__ void row_params(const Ctx& c, int nc) {
     const float sgn = W(lsgn, li);
     const float q = W(qpos, MI(jnt_qposadr, j));
     const float pos = sgn < 0.f ? MF(jnt_range, 2 * j + 1) - q : q - MF(jnt_range, 2 * j);
-    float A = 1.f;
-    if (sgn != 0.f) {
-      // (M^-1)_dd = sum_k z_k^2 / D_k with z = L^-T e_d, supported on d's chain
-      float* z = c.w + h.w_z * c.S;
-      for (int i = 0; i < nv; i++) z[i * c.S] = 0.f;
-      z[d * c.S] = 1.f;
-      const int rc = MI(dof_rowadr, d), n = MI(dof_depth, d);
-      A = 0.f;
-      for (int t = 0; t <= n; t++) {
-        const int k = MI(Lcol, rc + t);
-        const float zk = z[k * c.S];
-        const int r0 = MI(dof_rowadr, k), dk = MI(dof_depth, k);
-        for (int s = 1; s <= dk; s++) z[MI(Lcol, r0 + s) * c.S] -= L[(r0 + s) * c.S] * zk;
-        A = fmaf(zk * zk, W(Dinv, k), A);
-      }
-    }
+    const float A = sgn != 0.f ? minv_diag(c, d) : 1.f;
     set_row(c, 4 * MC + li, sgn != 0.f, pos, sgn != 0.f ? impedance(h, pos) : 0.f, A);
   }
+  // friction loss: at zero position (reference acceleration -b v), impedance d(0)
+  for (int k = 0; k < h.nfric; k++) set_row(c, fric_row0(h) + k, true, 0.f, impedance(h, 0.f), minv_diag(c, MI(fric_dof, k)));
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1289,6 +1299,11 @@ __device__ float cost_of(const Ctx& c, int X) {
       continue;
     }
     const float jar = W(jar, r) - W(aref, r);
+    if (r >= fric_row0(h)) {   // friction loss: Huber cost with the band |x| <= F / D
+      const float D = W(rD, r), F = MF(fric_F, r - fric_row0(h)), rf = F / D;
+      f += fabsf(jar) <= rf ? 0.5f * D * jar * jar : F * fabsf(jar) - 0.5f * F * rf;
+      continue;
+    }
     if (jar < 0.f) f = fmaf(0.5f * W(rD, r) * jar, jar, f);
   }
   return f;
@@ -1296,13 +1311,22 @@ __device__ float cost_of(const Ctx& c, int X) {
 
 __device__ __forceinline__ bool bit(const unsigned act[4], int r) { return (act[r >> 5] >> (r & 31)) & 1u; }
 
-// jar = J a - aref for every row; the active set holds the existing rows with jar < 0
-__device__ void residuals(const Ctx& c, unsigned act[4]) {
+// jar = J a - aref for every row; the active set holds the existing rows with jar < 0, and the
+// friction-loss rows inside their band; `side` (optional) marks the friction-loss rows beyond it
+// on the positive side
+__device__ void residuals(const Ctx& c, unsigned act[4], unsigned* side = nullptr) {
   const ModelHdr& h = c.h;
   rows_dot(c, h.w_a, h.w_jar);
   act[0] = act[1] = act[2] = act[3] = 0u;
+  if (side) side[0] = side[1] = side[2] = side[3] = 0u;
   for (int r = 0; r < h.nrow_max; r++) W(jar, r) = W(jar, r) - W(aref, r);
   for (int r = 0; r < h.nrow_max; r++) {
+    if (r >= fric_row0(h)) {
+      const float x = W(jar, r), rf = MF(fric_F, r - fric_row0(h)) / W(rD, r);
+      if (fabsf(x) <= rf) act[r >> 5] |= 1u << (r & 31);
+      else if (side && x > 0.f) side[r >> 5] |= 1u << (r & 31);
+      continue;
+    }
     if (r < 4 * h.max_contacts && elliptic_group(c, r >> 2)) {
       // an elliptic contact's zone on its first two bits: not free / full
       if ((r & 3) == 0 && W(rD, r) > 0.f) {
@@ -1400,6 +1424,18 @@ __device__ bool newton_direction(const Ctx& c, const unsigned act[4], bool& zero
     if (tree) W(L, MI(dof_rowadr, d)) += D;
     else W(H, d * nv + d) += D;
   }
+  for (int k = 0; k < h.nfric; k++) {   // friction loss: quadratic in its band, the bound +-F beyond
+    const int r = fric_row0(h) + k, d = MI(fric_dof, k);
+    const float x = W(jar, r);
+    if (bit(act, r)) {
+      const float D = W(rD, r);
+      W(g, d) += D * x;
+      if (tree) W(L, MI(dof_rowadr, d)) += D;
+      else W(H, d * nv + d) += D;
+    } else {
+      W(g, d) += x > 0.f ? MF(fric_F, k) : -MF(fric_F, k);
+    }
+  }
   bool nz = false;
   for (int k = 0; k < nv; k++) { W(p, k) = -W(g, k); nz = nz || W(g, k) != 0.f; }
   zero = !nz;
@@ -1452,7 +1488,8 @@ __device__ float line_search(const Ctx& c) {
   rows_dot(c, h.w_p, h.w_Jp);
   unsigned on[4] = {0u, 0u, 0u, 0u};
   const float none = -__int_as_float(0x7f800000);   // -inf: no breakpoint
-  for (int r = 0; r < R; r++) {
+  const int R0 = fric_row0(h);
+  for (int r = 0; r < R0; r++) {
     const float D = W(rD, r), jp = W(Jp, r), jr = W(jar, r);
     if (D > 0.f && (jr < 0.f || (jr == 0.f && jp < 0.f))) {
       on[r >> 5] |= 1u << (r & 31);
@@ -1460,6 +1497,21 @@ __device__ float line_search(const Ctx& c) {
       lt = fmaf(D * jp, jr, lt);
     }
     W(bp, r) = D > 0.f && jp != 0.f ? -jr / jp : none;   // the row's breakpoint, once
+  }
+  // friction-loss rows: quadratic inside the band |x| <= F / D, slope +-F Jp beyond it; the next
+  // band edge the motion reaches is the row's breakpoint (the far edge once inside)
+  for (int r = R0; r < R; r++) {
+    const float D = W(rD, r), jp = W(Jp, r), jr = W(jar, r), F = MF(fric_F, r - R0), rf = F / D;
+    const bool mid = (jr > -rf && jr < rf) || (jr == rf && jp <= 0.f) || (jr == -rf && jp >= 0.f);
+    if (mid) {
+      on[r >> 5] |= 1u << (r & 31);
+      qt = fmaf(D * jp, jp, qt);
+      lt = fmaf(D * jp, jr, lt);
+      W(bp, r) = jp > 0.f ? (rf - jr) / jp : (jp < 0.f ? (-rf - jr) / jp : none);
+    } else {
+      lt = fmaf(jr > 0.f ? F : -F, jp, lt);
+      W(bp, r) = (jr > 0.f && jp < 0.f) ? (rf - jr) / jp : ((jr < 0.f && jp > 0.f) ? (-rf - jr) / jp : none);
+    }
   }
   float alpha = 0.f;
   for (int step = 0; step <= R; step++) {
@@ -1475,6 +1527,18 @@ __device__ float line_search(const Ctx& c) {
       if (W(bp, r) != next) continue;
       const float D = W(rD, r), jp = W(Jp, r);
       const float sg = bit(on, r) ? -1.f : 1.f;
+      if (r >= R0) {
+        // a friction-loss row at a band edge: entering the band from the side it came from, or
+        // leaving it towards the side the motion leads to
+        const float F = MF(fric_F, r - R0), s = jp > 0.f ? 1.f : -1.f;
+        if (sg > 0.f) {   // entering: drop the slope -s F Jp, add the quadratic, next the far edge
+          lt = fmaf(s * F, jp, lt);
+          W(bp, r) = (s * F / D - W(jar, r)) / jp;
+        } else {          // leaving: drop the quadratic (below), add the slope s F Jp
+          lt = fmaf(s * F, jp, lt);
+          W(bp, r) = none;
+        }
+      }
       on[r >> 5] ^= 1u << (r & 31);
       qt = fmaf(sg * D * jp, jp, qt);
       lt = fmaf(sg * D * jp, W(jar, r), lt);
@@ -1563,8 +1627,8 @@ __device__ int newton(const Ctx& c, bool& converged) {
   float f_cur = use_warm ? fw : f0;
   for (int k = 0; k < nv; k++) W(a, k) = use_warm ? W(warm, k) : W(a0, k);
   const bool ell = has_elliptic(c);
-  unsigned act[4];
-  residuals(c, act);
+  unsigned act[4], side[4];
+  residuals(c, act, side);
   int it = 0;
   while (it < h.cap) {
     bool zero = false;
@@ -1575,10 +1639,11 @@ __device__ int newton(const Ctx& c, bool& converged) {
     const float alpha = ell ? line_search_smooth(c) : line_search(c);
     for (int k = 0; k < nv; k++) W(a, k) = fmaf(alpha, W(p, k), W(a, k));
     const float f_new = ell ? cost_of(c, h.w_a) : 0.f;   // (before the residuals: cost_of reuses jar)
-    unsigned act2[4];
-    residuals(c, act2);
-    const bool same = act2[0] == act[0] && act2[1] == act[1] && act2[2] == act[2] && act2[3] == act[3];
-    act[0] = act2[0]; act[1] = act2[1]; act[2] = act2[2]; act[3] = act2[3];
+    unsigned act2[4], side2[4];
+    residuals(c, act2, side2);
+    const bool same = act2[0] == act[0] && act2[1] == act[1] && act2[2] == act[2] && act2[3] == act[3] &&
+                      side2[0] == side[0] && side2[1] == side[1] && side2[2] == side[2] && side2[3] == side[3];
+    for (int k = 0; k < 4; k++) { act[k] = act2[k]; side[k] = side2[k]; }
     if (!ell) {
       if (same) { converged = true; break; }
       continue;
@@ -1666,14 +1731,20 @@ __device__ void substep(const Ctx& c, uint32_t& status, float* dbg, uint32_t cnt
           o[__float_as_int(gc[a * c.S])] += W(gcond, k) == 3.f
               ? row_value(ell, mu, e, J[a * c.S], J[(h.ncol_max + a) * c.S], J[(2 * h.ncol_max + a) * c.S])
               : J[a * c.S];
-      } else {
+      } else if (r < fric_row0(h)) {
         const int li = r - 4 * h.max_contacts, d = MI(jnt_dofadr, MI(limit_jnt, li));
         o[d] = W(lsgn, li);
+      } else {
+        o[MI(fric_dof, r - fric_row0(h))] = 1.f;
       }
       o[nv] = W(rr, r); o[nv + 1] = W(rv, r); o[nv + 2] = W(aref, r); o[nv + 3] = W(rD, r);
       o[nv + 4] = W(Ahat, r); o[nv + 5] = W(imp, r);
       const float jar = W(jar, r) - W(aref, r);
       o[nv + 6] = jar < 0.f ? -W(rD, r) * jar : 0.f;
+      if (r >= fric_row0(h)) {   // friction loss: -D x inside the band, the bound beyond
+        const float F = MF(fric_F, r - fric_row0(h));
+        o[nv + 6] = fabsf(jar) <= F / W(rD, r) ? -W(rD, r) * jar : (jar > 0.f ? -F : F);
+      }
       if (r < 4 * h.max_contacts && elliptic_group(c, r >> 2)) {   // force = -grad of the cone cost
         const int r0 = r & ~3;
         float gg[3], B[6];

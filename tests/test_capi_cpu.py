@@ -92,6 +92,23 @@ def test_adjoint_scope_and_parameter_rows():
     assert core.CompiledModel(W.quadruped_rough()).sizes.adjoint_workspace_bytes == 0   # heightfield: outside
 
 
+def test_friction_loss_rows_and_scope():
+    from paper_2502_08844_b300 import core, _capi
+    m = W.quadruped()
+    m.dof_frictionloss = np.zeros(m.nv, np.float32); m.dof_frictionloss[6:] = 0.5
+    s = core.CompiledModel(m).sizes
+    assert s.nrow_max == 4 * 4 + 12 + 12 and s.adjoint_workspace_bytes == 0
+    h = W.hand_elliptic()
+    h.dof_frictionloss = np.full(h.nv, 0.1, np.float32)
+    with pytest.raises(_capi.PgError) as ei:
+        core.CompiledModel(h)
+    assert ei.value.code == _capi.PG_EUNSUPPORTED
+    m.dof_frictionloss[7] = -1.0
+    with pytest.raises(_capi.PgError) as ei:
+        core.CompiledModel(m)
+    assert ei.value.code == _capi.PG_EINVAL
+
+
 def test_per_environment_parameter_rows():
     from paper_2502_08844_b300 import core
     for f in (W.quadruped, W.cartpole, W.humanoid):
