@@ -164,7 +164,7 @@ def cpu_baseline(model: W.Model, cfg: int, n_envs: int, budget_s: float = 10.0, 
                 n, steps, model.n_substeps, model.name, cores)}
 
 
-def measure_mixed(dev, steps: int = 200):
+def measure_mixed(dev, steps: int = 200, specialize: bool = True):
     """Mixed-model batch: 4096 cartpoles + 4096 quadrupeds + 2048 humanoids in one launch per
     control step (each env with its own model's timestep and substeps), a 200-step rollout
     captured in a CUDA graph, launch shape from the autotuner."""
@@ -174,6 +174,8 @@ def measure_mixed(dev, steps: int = 200):
     models = [(core.CompiledModel(W.model(nm)), n) for nm, _, n in comp]
     epc = rollout.autotune(models)
     batch = core.Batch(models, envs_per_cta=epc)
+    if specialize:
+        batch.specialize()   # one specialised kernel per model over its own blocks
     st = core.State(batch, dev)
     ld = st.ld
     Q = np.zeros((batch.nq_max, ld), np.float32)
@@ -204,9 +206,10 @@ def measure_mixed(dev, steps: int = 200):
     t_eager = a.elapsed_time(b) / 1e3
     n_tot = sum(n for _, _, n in comp)
     return {"value": n_tot * steps / t_graph, "unit": "env-steps/s", "eager_value": n_tot * steps / t_eager,
-            "kernel": "generic (one body shared by the batch's models)",
+            "kernel": "model-specialised: one kernel per model over its own blocks, back to back" if specialize
+                      else "generic (one body shared by the batch's models)",
             "composition": {nm: n for nm, _, n in comp}, "steps": steps, "cuda_graph": True,
-            "envs_per_cta": epc or "default (one wave)", "launches": steps}
+            "envs_per_cta": epc or "default (one wave)", "launches": steps * (len(comp) if specialize else 1)}
 
 
 def measure_env_layer(dev, n: int = 8192, steps: int = 200, specialize: bool = True):
@@ -554,7 +557,11 @@ def run_ours(args):
             "clocks": ck, "status_bits_seen": int(np.bitwise_or.reduce(status)) if status.size else 0,
             "adjoint_forward_ratio": None}
     if not args.no_mixed:
-        line["mixed_batch"] = measure_mixed(dev)
+        spec = kernel.startswith("model-specialised")
+        line["mixed_batch"] = measure_mixed(dev, specialize=spec)
+        if spec:
+            line["mixed_batch"]["generic_kernel"] = {k: v for k, v in measure_mixed(dev, specialize=False).items()
+                                                     if k in ("value", "eager_value")}
     if not args.no_env:
         line["env_layer"] = measure_env_layer(dev, specialize=kernel.startswith("model-specialised"))
         line["rough_terrain"] = measure_rough_terrain(dev, specialize=kernel.startswith("model-specialised"))

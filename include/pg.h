@@ -218,14 +218,15 @@ void pg_batch_free(pg_batch* batch);
  * A first compile takes seconds, so call this before any stream capture and outside timed
  * regions.
  *
- * Scope. Only single-model batches. The specialised build covers the step, the environment
- * step (pg_env_step) and, for models inside the adjoint's scope, the tape replay and reverse
- * sweep of pg_step_vjp; the debug kernel stays generic. A mixed batch keeps the generic kernel,
- * whose one body all its models share: one specialised body per model was measured slower, as
- * blocks of different models on one SM evict each other's code from the instruction cache.
+ * Scope. For a single-model batch the specialised build covers the step, pg_step_dr, the
+ * environment step (pg_env_step) and, for models inside the adjoint's scope, the tape replay and
+ * reverse sweep of pg_step_vjp; the debug kernel stays generic. For a mixed batch pg_step runs
+ * one specialised kernel per model over that model's blocks, one launch after the other (one
+ * kernel holding every model's body measured slower: blocks of different models on one SM evict
+ * each other's code from the instruction cache); its other kernels stay generic.
  *
- * Errors. PG_EUNSUPPORTED (a mixed batch; NVRTC missing or failing, with its log in
- * pg_last_error; the batch then keeps the generic kernel), PG_ECUDA. */
+ * Errors. PG_EUNSUPPORTED (NVRTC missing or failing, with its log in pg_last_error; the batch
+ * then keeps the generic kernel), PG_ECUDA. */
 int pg_batch_specialize(pg_batch* batch);
 
 /* Reset the envs whose env_mask_dev[e] != 0 (all envs when env_mask_dev is NULL): copy

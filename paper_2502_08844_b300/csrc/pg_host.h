@@ -51,6 +51,14 @@ struct pg_batch {
   cudaKernel_t spec_kernel_vjp = nullptr;    // the adjoint's reverse sweep (NULL outside its scope)
   cudaKernel_t spec_kernel_env = nullptr;    // the environment step of a locomotion task
   cudaKernel_t spec_kernel_dr = nullptr;     // the step with per-environment parameters
+  // a mixed batch's specialised step: one kernel per model over that model's (contiguous) tiles
+  struct SpecPart {
+    cudaLibrary_t lib;
+    cudaKernel_t kernel;
+    int tile0, ntiles, threads;
+    size_t smem;
+  };
+  std::vector<SpecPart> spec_parts;
   // staging buffer of the host-buffer path (allocated on its first use)
   float* d_ctrl_stage = nullptr;
   size_t ctrl_stage_floats = 0;
@@ -96,6 +104,8 @@ cudaError_t launch_step_tape(const pg_batch* b, const pg_state* s, const float* 
   cudaError_t step_env(const pg_batch* b, const pg_state* s, const EnvArgs& E, int n_substeps, cudaStream_t st);  \
   cudaError_t step_spec_env(const pg_batch* b, const pg_state* s, const EnvArgs& E, int n_substeps,            \
                             cudaStream_t st);                                                                  \
+  cudaError_t step_spec_parts(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps,          \
+                              cudaStream_t st);                                                                \
   }
 PG_DECLARE_STEP_KERNELS(pyramidal)
 PG_DECLARE_STEP_KERNELS(elliptic)

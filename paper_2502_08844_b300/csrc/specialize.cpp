@@ -218,14 +218,53 @@ int compile_cubin(const pg_model* m, std::vector<char>& cubin) {
 
 using namespace pg;
 
+// A mixed batch: one specialised step kernel per model, each launched over that model's tiles
+// (the batch's tiles are grouped by model).  One kernel holding every model's body behind a switch
+// measured slower than the generic kernel: blocks of different models share an SM and their large
+// specialised bodies evict each other from the instruction cache.  Launched one model after the
+// other, each kernel runs alone.  The tape, adjoint, environment and debug kernels stay generic.
+static int specialize_parts(pg_batch* b) {
+  std::vector<pg_batch::SpecPart> parts;
+  auto fail = [&](int rc) {
+    for (const pg_batch::SpecPart& p : parts) cudaLibraryUnload(p.lib);
+    return rc;
+  };
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_error(PG_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  for (int k = 0; k < (int)b->models.size(); k++) {
+    const pg_model* m = b->models[k];
+    pg_batch::SpecPart part{};
+    part.tile0 = -1;
+    for (int t = 0; t < b->ntiles; t++)
+      if (b->tiles[t].model == k) {
+        if (part.tile0 < 0) part.tile0 = t;
+        else if (t != part.tile0 + part.ntiles) return fail(set_error(PG_EINVAL, "a model's tiles are not contiguous"));
+        part.ntiles++;
+      }
+    if (part.tile0 < 0) part.tile0 = 0;
+    const int soa = m->hdr.soa, nw = (b->envs_per_cta[k] + soa - 1) / soa;
+    part.threads = 32 * nw;
+    part.smem = (size_t)4 * nw * soa * m->hdr.ws_floats;
+    std::vector<char> cubin;
+    int rc = compile_cubin(m, cubin);
+    if (rc != PG_OK) return fail(rc);
+    e = cudaLibraryLoadData(&part.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    if (e != cudaSuccess) return fail(set_error(PG_ECUDA, std::string("cudaLibraryLoadData: ") + cudaGetErrorString(e)));
+    parts.push_back(part);
+    e = cudaLibraryGetKernel(&parts.back().kernel, part.lib, "pg_step_spec");
+    if (e == cudaSuccess)
+      e = cudaKernelSetAttributeForDevice(parts.back().kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)part.smem, dev);
+    if (e != cudaSuccess) return fail(set_error(PG_ECUDA, std::string("specialised kernel set-up: ") + cudaGetErrorString(e)));
+  }
+  b->spec_parts = parts;
+  return PG_OK;
+}
+
 extern "C" int pg_batch_specialize(pg_batch* b) {
   if (!b) return set_error(PG_EINVAL, "batch is NULL");
-  // A mixed batch would need one body per model in one kernel. Measured, that is slower than the
-  // generic kernel: blocks of different models share an SM and their large specialised bodies
-  // evict each other from the instruction cache. So mixed batches keep the generic kernel.
-  if (b->models.size() != 1)
-    return set_error(PG_EUNSUPPORTED, "pg_batch_specialize: single-model batches only (a mixed batch keeps the "
-                                      "generic kernel, whose one body all models share)");
+  if (b->models.size() != 1) return b->spec_parts.empty() ? specialize_parts(b) : PG_OK;
   if (b->spec_kernel) return PG_OK;
   std::vector<char> cubin;
   int rc = compile_cubin(b->models[0], cubin);

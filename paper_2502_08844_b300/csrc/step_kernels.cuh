@@ -112,6 +112,21 @@ cudaError_t step_tape(const pg_batch* b, const pg_state* s, const float* ctrl, i
   return cudaGetLastError();
 }
 
+// a mixed batch's specialised step: each model's kernel over its own tiles, back to back
+cudaError_t step_spec_parts(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st) {
+  static thread_local StepArgs A;
+  make_args(A, b, s, ctrl);
+  A.n_substeps = n_substeps;
+  for (const pg_batch::SpecPart& part : b->spec_parts) {
+    if (part.ntiles == 0) continue;
+    A.tiles = b->d_tiles + part.tile0;
+    void* params[] = {&A};
+    cudaError_t e = cudaLaunchKernel((const void*)part.kernel, dim3(part.ntiles), dim3(part.threads), params, part.smem, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 // an environment step of the locomotion task E (generic kernel, or the batch's specialised one)
 cudaError_t step_env(const pg_batch* b, const pg_state* s, const EnvArgs& E, int n_substeps, cudaStream_t st) {
   if (b->ntiles == 0) return cudaSuccess;

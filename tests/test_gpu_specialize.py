@@ -33,12 +33,39 @@ def test_specialised_kernel_matches_generic(mname, cfg, n, T):
     assert np.array_equal(out[0][2], out[1][2])
 
 
-def test_specialise_keeps_mixed_batches_generic():
-    parts = [(core.CompiledModel(W.cartpole()), 4), (core.CompiledModel(W.quadruped()), 4)]
-    batch = core.Batch(parts)
-    with pytest.raises(_capi.PgError) as ei:
-        batch.specialize()
-    assert ei.value.code == _capi.PG_EUNSUPPORTED
+@pytest.mark.parametrize("order", ["in_order", "interleaved_sizes"])
+def test_specialised_mixed_batch_matches_generic(order):
+    """A mixed batch specialised per model (one kernel per model over its own blocks) against the
+    generic kernel, every environment with its own model's substeps, 20 control steps."""
+    import torch
+    names = [("cartpole", 0, 70), ("quadruped", 1, 45), ("humanoid", 3, 33)]
+    if order != "in_order":
+        names = [names[1], names[2], names[0]]
+    outs = []
+    for spec in (False, True):
+        parts = [(core.CompiledModel(W.model(nm)), n) for nm, _, n in names]
+        batch = core.Batch(parts)
+        if spec:
+            batch.specialize()
+        st = core.State(batch, "cuda")
+        ld = st.ld
+        Q = np.zeros((batch.nq_max, ld), np.float32); V = np.zeros((batch.nv_max, ld), np.float32)
+        U = np.zeros((20, max(batch.nu_max, 1), ld), np.float32)
+        o = 0
+        for (nm, cfg, n), (cm, _) in zip(names, parts):
+            m = cm.src
+            q0, v0 = W.initial_state(m, cfg, n)
+            Q[:m.nq, o:o + n] = q0.T; V[:m.nv, o:o + n] = v0.T
+            U[:, :m.nu, o:o + n] = W.actions(m, cfg, n, 0, 20).transpose(0, 2, 1)
+            o += n
+        st.qpos.copy_(torch.from_numpy(Q)); st.qvel.copy_(torch.from_numpy(V))
+        ctrl = torch.from_numpy(U).to("cuda")
+        for t in range(20):
+            core.step(batch, st, ctrl[t], 0)
+        torch.cuda.synchronize()
+        outs.append((st.qpos.cpu().numpy(), st.qvel.cpu().numpy()))
+    for a, b in zip(outs[0], outs[1]):
+        assert np.allclose(a, b, rtol=1e-4, atol=1e-5)
 
 
 def test_specialised_adjoint_matches_generic():
