@@ -557,17 +557,19 @@ def run_ours(args):
             "roofline": roof, "e2e": e2e, "gpu_launches": args.steps,
             "clocks": ck, "status_bits_seen": int(np.bitwise_or.reduce(status)) if status.size else 0,
             "adjoint_forward_ratio": None}
-    if not args.no_mixed:
+    # the sub-measurements characterise one GPU: the N = 1 line carries them, scaling runs skip them
+    single = ws == 1
+    if single and not args.no_mixed:
         spec = kernel.startswith("model-specialised")
         line["mixed_batch"] = measure_mixed(dev, specialize=spec)
         if spec:
             line["mixed_batch"]["generic_kernel"] = {k: v for k, v in measure_mixed(dev, specialize=False).items()
                                                      if k in ("value", "eager_value")}
-    if not args.no_env:
+    if single and not args.no_env:
         line["env_layer"] = measure_env_layer(dev, specialize=kernel.startswith("model-specialised"))
         line["rough_terrain"] = measure_rough_terrain(dev, specialize=kernel.startswith("model-specialised"))
         line["pixels"] = measure_pixels(dev)
-    if not args.no_adjoint:
+    if single and not args.no_adjoint:
         adj = measure_adjoint(dev, specialize=kernel.startswith("model-specialised"))
         line["adjoint_forward_ratio"] = adj["ratio"]
         line["adjoint"] = adj
