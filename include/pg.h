@@ -425,12 +425,12 @@ int pg_env_step(const pg_batch* batch, const pg_task* task, pg_state* state, flo
  *     qpos): planes (infinite, both faces), spheres, capsules and boxes; heightfields are not
  *     drawn;
  *   * Lambertian shading under one directional light: colour = albedo * (ambient + diffuse *
- *     max(0, n . l) * lit), l = -light_dir normalised, lit = 0 when a shadow ray from the hit
- *     point towards the light meets any drawn geom; rays that hit nothing get the background.
+ *     (n . l) * lit), l = -light_dir normalised, lit = 1 when n . l > 0 and a shadow ray from the
+ *     hit point towards the light meets no drawn geom; rays that hit nothing get the background.
  * Output (device memory, caller-owned): format PG_PIXELS_U8: uint8 [n][height][width][3],
  * round(255 * clip(colour, 0, 1)); PG_PIXELS_F32: float32 [n][height][width][3] unclipped.
  * hits_dev (optional, int32 [n][height][width]): 0 for the background, else (geom + 1) plus
- * 65536 when the point is in shadow.
+ * 65536 when no direct light reaches the point (lit = 0).
  * Scope: single-model batches; ngeom <= 64; width, height in 1 .. 1024.  Errors: PG_EINVAL,
  * PG_EUNSUPPORTED (a mixed batch), PG_ECAPACITY, PG_ECUDA. */
 enum { PG_PIXELS_U8 = 0, PG_PIXELS_F32 = 1 };

@@ -5,7 +5,8 @@ module.  It draws what the library's pixel observations draw (the paper renders 
 observations with a CUDA batch ray tracer, Sec. 5): a pinhole camera, every drawn geom at the
 pose the oracle's own forward kinematics gives, the nearest hit per ray (first geom on ties),
 Lambertian shading under one directional light with an ambient term, and hard shadows from one
-shadow ray per hit.  Written with numpy over all pixels of one image at a time.
+shadow ray per hit.  A point is lit when its surface faces the light and no drawn geom blocks
+its shadow ray (the shadow ray here tests every drawn geom, the one hit included).  Written with numpy over all pixels of one image at a time.
 
 Readings where the paper leaves the choice: pixel (x, y) has y = 0 at the top and its ray goes
 through the pixel's centre; planes are infinite and seen from both faces; a shadow ray starts
@@ -124,7 +125,7 @@ def intersect(gtype, x, R, size, O, D):
 
 def render(om, scene, qpos):
     """One image of one environment: colours [H, W, 3] (float) and hit codes [H, W] (0
-    background, geom + 1, plus 65536 in shadow)."""
+    background, geom + 1, plus 65536 when no direct light reaches the point)."""
     Rg, Xg = om.geom_frames(np.asarray(qpos, np.float64))
     m = om.src
     rgb = np.asarray(scene.geom_rgb, np.float64)
@@ -148,8 +149,9 @@ def render(om, scene, qpos):
     for g in drawn:
         t, _ = intersect(int(m.geom_type[g]), Xg[g], Rg[g], size[g], Q, Ld)
         blocked |= np.isfinite(t)
-    lit = any_hit & ~blocked
-    shade = float(np.float32(scene.ambient)) + np.where(lit, float(np.float32(scene.diffuse)) * np.maximum(nrm @ light, 0), 0)
+    nl = nrm @ light
+    lit = any_hit & (nl > 0) & ~blocked          # facing the light and not blocked
+    shade = float(np.float32(scene.ambient)) + np.where(lit, float(np.float32(scene.diffuse)) * nl, 0)
     col = np.where(any_hit[:, None], rgb[np.maximum(hit, 0)] * shade[:, None], np.asarray(scene.background, np.float64))
     code = np.where(any_hit, hit + 1 + np.where(lit, 0, 65536), 0)
     return col.reshape(H_, W_, 3), code.reshape(H_, W_)

@@ -45,13 +45,13 @@ cudaError_t launch_vjp_step(const pg_batch* b, const float* tape, int tape_rows,
     void* params[] = {&A};
     return cudaLaunchKernel((const void*)b->spec_kernel_vjp, dim3(blocks), dim3(threads), params, smem, st);
   }
-  static bool configured = false;
-  if (!configured) {
+  static std::mutex mu;
+  static unsigned long long configured = 0;
+  once_per_device(mu, configured, [] {
     cudaFuncSetAttribute(vjp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     // no shared memory in the global-memory form: the SM's unified cache goes to L1
     cudaFuncSetAttribute(vjp_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-    configured = true;
-  }
+  });
   if (A.soa > 0) vjp_kernel<true><<<blocks, threads, smem, st>>>(A);
   else vjp_kernel<false><<<blocks, threads, 0, st>>>(A);
   return cudaGetLastError();

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -71,6 +72,19 @@ struct pg_batch {
 namespace pg {
 
 int set_error(int code, const std::string& msg);
+
+// Run f once per device (the current one), under a lock, before any caller on that device goes
+// on: kernel attributes are set before the first launch that needs them, whatever the threads.
+template <class F>
+void once_per_device(std::mutex& mu, unsigned long long& done, F&& f) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) { f(); return; }
+  const unsigned long long bit = 1ull << dev;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done & bit) return;
+  f();
+  done |= bit;
+}
 int compile_model(const pg_model_desc* d, pg_model* out);
 
 // kernel launchers (step.cu)

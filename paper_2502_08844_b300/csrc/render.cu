@@ -3,8 +3,8 @@
 // is the library's own: one thread block per environment.  Its first thread runs the
 // environment's forward kinematics (the step's device code) into shared memory and writes every
 // geom's world frame there; then the block's threads trace the image's pixels, each a primary
-// ray against every drawn geom (closest hit, first geom on ties) and, on a hit, one shadow ray
-// towards the directional light.  Lambertian shading with an ambient term.  A scene holds a
+// ray against every drawn geom (closest hit, first geom on ties) and, on a hit whose surface faces
+// the light, one shadow ray towards it against the other geoms.  Lambertian shading with an ambient term.  A scene holds a
 // handful of primitives, so every ray tests them all: a bounding-volume hierarchy pays only
 // well above the 64 geoms this kernel takes.
 #include <cuda_runtime.h>
@@ -192,13 +192,17 @@ __global__ void __launch_bounds__(256) render_kernel(const __grid_constant__ Ren
     float col[3] = {A.bg[0], A.bg[1], A.bg[2]};
     int32_t code = 0;
     if (hit >= 0) {
+      // direct light reaches the point when its surface faces the light and no other geom blocks
+      // the shadow ray; every drawn geom is convex or a plane, so the one hit cannot block a ray
+      // that leaves its lit side (the ray stays beyond the surface's tangent plane)
+      const float nl = dot3(n, light);
+      bool lit = nl > 0.f;
       const float3 q = cam + d * best + n * kShadowLift;
-      bool lit = true;
       for (int g = 0; g < ng && lit; g++) {
         float3 dummy;
-        if (ray_geom(frames[g], q, light, dummy) < kMiss) lit = false;
+        if (g != hit && ray_geom(frames[g], q, light, dummy) < kMiss) lit = false;
       }
-      const float shade = A.ambient + (lit ? A.diffuse * fmaxf(dot3(n, light), 0.f) : 0.f);
+      const float shade = A.ambient + (lit ? A.diffuse * nl : 0.f);
       for (int k = 0; k < 3; k++) col[k] = A.rgb[3 * hit + k] * shade;
       code = (hit + 1) + (lit ? 0 : 65536);
     }
@@ -260,11 +264,11 @@ extern "C" int pg_render(const pg_batch* b, const pg_state* s, const pg_render_d
   A.pixels = pixels; A.hits = hits;
   std::memcpy(A.blob, m->blob.data(), std::min(m->blob.size(), (size_t)kMaxParamWords) * sizeof(uint32_t));
   const size_t smem = (size_t)4 * m->hdr.ws_floats;
-  static bool configured = false;
-  if (!configured) {
+  static std::mutex mu;
+  static unsigned long long configured = 0;
+  once_per_device(mu, configured, [] {
     cudaFuncSetAttribute(render_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem - 8192);
-    configured = true;
-  }
+  });
   render_kernel<<<(unsigned)b->n, 256, smem, (cudaStream_t)stream>>>(A);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(PG_ECUDA, std::string("render launch: ") + cudaGetErrorString(e));

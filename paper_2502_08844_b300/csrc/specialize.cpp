@@ -62,11 +62,8 @@ struct Nvrtc {
 std::mutex g_mutex;
 std::map<uint64_t, std::vector<char>> g_cubins;
 
-const Nvrtc& nvrtc() {
-  static Nvrtc n;
-  static bool tried = false;
-  if (tried) return n;
-  tried = true;
+Nvrtc load_nvrtc() {
+  Nvrtc n;
   const char* names[] = {"libnvrtc.so.13", "/usr/local/cuda/lib64/libnvrtc.so.13", "libnvrtc.so"};
   void* h = nullptr;
   for (const char* nm : names)
@@ -86,6 +83,12 @@ const Nvrtc& nvrtc() {
   }
   ver(&n.major, &n.minor);
   n.ok = true;
+  return n;
+}
+
+// NVRTC, loaded on first use (a function-local static: initialised once, thread-safe)
+const Nvrtc& nvrtc() {
+  static const Nvrtc n = load_nvrtc();
   return n;
 }
 
