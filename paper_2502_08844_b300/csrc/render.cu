@@ -4,9 +4,10 @@
 // environment's forward kinematics (the step's device code) into shared memory and writes every
 // geom's world frame there; then the block's threads trace the image's pixels, each a primary
 // ray against every drawn geom (closest hit, first geom on ties) and, on a hit whose surface faces
-// the light, one shadow ray towards it against the other geoms.  Lambertian shading with an ambient term.  A scene holds a
-// handful of primitives, so every ray tests them all: a bounding-volume hierarchy pays only
-// well above the 64 geoms this kernel takes.
+// the light, one shadow ray towards it against the other geoms.  Lambertian shading with an
+// ambient term.  A scene holds a handful of primitives, so every ray tests them all (a
+// bounding-volume hierarchy pays only well above the 64 geoms this kernel takes); capsules and
+// boxes are tested only by rays that meet their bounding spheres.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -47,8 +48,17 @@ static_assert(sizeof(RenderArgs) <= 32764, "the renderer's argument block must f
 // one geom's world frame: origin, rotation (row-major), size, type
 struct GeomFrame {
   float x[3], R[9], s[3];
+  float bound2;   // squared radius of a sphere about x holding the shape (slightly enlarged)
   int type;
 };
+
+// the ray o + t d (t > 0) misses the ball |y - x|^2 <= r2 around a shape; conservative (a ray that
+// starts inside the ball, or meets it, is never pruned), so pruning changes no result
+__device__ __forceinline__ bool misses_bound(float3 o, float3 d, float3 x, float r2) {
+  const float3 oc = o - x;
+  const float b = dot3(oc, d), cc = dot3(oc, oc) - r2;
+  return cc > 0.f && (b > 0.f || b * b < cc);
+}
 
 __device__ __forceinline__ float3 ld3s(const float* p) { return make_float3(p[0], p[1], p[2]); }
 
@@ -141,6 +151,9 @@ __device__ float ray_box(float3 o, float3 d, float3 x, const float* R, float3 hs
 
 __device__ float ray_geom(const GeomFrame& g, float3 o, float3 d, float3& n) {
   const float3 x = ld3s(g.x);
+  if (g.type == PG_GEOM_CAPSULE || g.type == PG_GEOM_BOX) {
+    if (misses_bound(o, d, x, g.bound2)) return kMiss;
+  }
   switch (g.type) {
     case PG_GEOM_PLANE: return ray_plane(o, d, x, mat_col(g.R, 2), n);
     case PG_GEOM_SPHERE: return ray_sphere(o, d, x, g.s[0], n);
@@ -171,6 +184,9 @@ __global__ void __launch_bounds__(256) render_kernel(const __grid_constant__ Ren
                                     MF(geom_quat, 4 * g + 3)})), f.R);
       for (int k = 0; k < 3; k++) f.s[k] = MF(geom_size, 3 * g + k);
       f.type = A.rgb[3 * g] < 0.f ? -1 : MI(geom_type, g);   // hidden geoms and heightfields: not drawn
+      const float br = f.type == PG_GEOM_CAPSULE ? f.s[0] + f.s[1]
+                                                 : sqrtf(f.s[0] * f.s[0] + f.s[1] * f.s[1] + f.s[2] * f.s[2]);
+      f.bound2 = br * br * 1.0002f + 1e-8f;
     }
   }
   __syncthreads();
