@@ -444,6 +444,13 @@ typedef struct pg_render_desc {
   float background[3];
   const float* geom_rgb;  /* [ngeom][3] albedo; a geom whose first component is < 0 is not
                              drawn (and casts no shadow)                                    */
+  /* Per-environment visual randomisation (each NULL for none; device memory, [3][ld] with the
+   * state's ld): env_cam_offset moves the camera's position (its look-at point stays, so the view
+   * direction turns with it); env_light_dir replaces light_dir; env_tint multiplies every colour
+   * of the image, background included (colour and brightness randomisation). */
+  const float* env_cam_offset;
+  const float* env_light_dir;
+  const float* env_tint;
 } pg_render_desc;
 
 int pg_render(const pg_batch* batch, const pg_state* state, const pg_render_desc* desc, int format, void* pixels_dev,

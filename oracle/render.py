@@ -123,6 +123,18 @@ def intersect(gtype, x, R, size, O, D):
     return np.where(ok, t, np.inf), nl @ R.T
 
 
+def randomized_scene(scene, cam_offset=None, light_dir=None):
+    """The scene one environment sees under visual randomisation: the camera moved by cam_offset
+    (its look-at point kept), the light along light_dir."""
+    import dataclasses
+    kw = {}
+    if cam_offset is not None:
+        kw["cam_pos"] = tuple(np.asarray(scene.cam_pos, np.float64) + np.asarray(cam_offset, np.float64))
+    if light_dir is not None:
+        kw["light_dir"] = tuple(np.asarray(light_dir, np.float64))
+    return dataclasses.replace(scene, **kw)
+
+
 def render(om, scene, qpos):
     """One image of one environment: colours [H, W, 3] (float) and hit codes [H, W] (0
     background, geom + 1, plus 65536 when no direct light reaches the point)."""

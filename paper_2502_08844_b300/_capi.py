@@ -74,7 +74,8 @@ class pg_render_desc(C.Structure):
     _fields_ = [("cam_pos", C.c_float * 3), ("cam_lookat", C.c_float * 3), ("cam_up", C.c_float * 3),
                 ("fovy_deg", C.c_float), ("width", C.c_int), ("height", C.c_int), ("light_dir", C.c_float * 3),
                 ("ambient", C.c_float), ("diffuse", C.c_float), ("background", C.c_float * 3),
-                ("geom_rgb", C.c_void_p)]
+                ("geom_rgb", C.c_void_p), ("env_cam_offset", C.c_void_p), ("env_light_dir", C.c_void_p),
+                ("env_tint", C.c_void_p)]
 
 
 EXPORTS = ["pg_model_compile", "pg_model_info", "pg_model_free", "pg_batch_compile", "pg_batch_info",

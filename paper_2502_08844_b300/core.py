@@ -180,9 +180,13 @@ def env_step(batch: Batch, task: Task, state: State, task_state: torch.Tensor, a
 
 
 def render(batch: Batch, state: State, scene: W.Scene, pixels: torch.Tensor, hits: Optional[torch.Tensor] = None,
-           stream=None) -> None:
+           stream=None, cam_offset: Optional[torch.Tensor] = None, light_dir: Optional[torch.Tensor] = None,
+           tint: Optional[torch.Tensor] = None) -> None:
     """pg_render: one ray-traced image per environment of the current state into pixels
-    (uint8 [n][H][W][3] or float32 [n][H][W][3]); hits (int32 [n][H][W]) optional."""
+    (uint8 [n][H][W][3] or float32 [n][H][W][3]); hits (int32 [n][H][W]) optional; per-environment
+    camera offsets, light directions and colour tints ([3][ld] each) optional."""
+    for t in (cam_offset, light_dir, tint):
+        assert t is None or (t.dtype == torch.float32 and t.is_contiguous() and t.shape == (3, state.ld))
     fmt = _capi.PG_PIXELS_U8 if pixels.dtype == torch.uint8 else _capi.PG_PIXELS_F32
     assert pixels.dtype in (torch.uint8, torch.float32) and pixels.is_contiguous()
     assert pixels.shape == (state.n, scene.height, scene.width, 3)
@@ -191,7 +195,8 @@ def render(batch: Batch, state: State, scene: W.Scene, pixels: torch.Tensor, hit
     f3 = lambda v: (C.c_float * 3)(*[float(x) for x in v])
     d = _capi.pg_render_desc(f3(scene.cam_pos), f3(scene.cam_lookat), f3(scene.cam_up), float(scene.fovy_deg),
                              int(scene.width), int(scene.height), f3(scene.light_dir), float(scene.ambient),
-                             float(scene.diffuse), f3(scene.background), rgb.ctypes.data_as(C.c_void_p))
+                             float(scene.diffuse), f3(scene.background), rgb.ctypes.data_as(C.c_void_p),
+                             _ptr(cam_offset), _ptr(light_dir), _ptr(tint))
     _capi.pg_render(batch.handle, state.c(), d, fmt, _ptr(pixels), _ptr(hits), _stream_ptr(stream))
 
 

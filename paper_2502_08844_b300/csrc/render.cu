@@ -39,6 +39,11 @@ struct RenderArgs {
   float light[3];                           // unit vector towards the light
   float ambient, diffuse, bg[3];
   float rgb[3 * kMaxRenderGeoms];
+  float lookat[3], upv[3];                  // for per-environment camera positions
+  float tan_half, aspect;
+  const float* env_cam;                     // [3][ld] per-environment camera offsets, or NULL
+  const float* env_light;                   // [3][ld] per-environment light directions, or NULL
+  const float* env_tint;                    // [3][ld] per-environment colour multipliers, or NULL
   void* pixels;
   int32_t* hits;
   uint32_t blob[kMaxParamWords];
@@ -190,7 +195,23 @@ __global__ void __launch_bounds__(256) render_kernel(const __grid_constant__ Ren
     }
   }
   __syncthreads();
-  const float3 cam = ld3s(A.cam), fwd = ld3s(A.fwd), right = ld3s(A.right), up = ld3s(A.up), light = ld3s(A.light);
+  float3 cam = ld3s(A.cam), fwd = ld3s(A.fwd), right = ld3s(A.right), up = ld3s(A.up), light = ld3s(A.light);
+  float tint[3] = {1.f, 1.f, 1.f};
+  if (A.env_cam) {   // this environment's camera: moved, still looking at the same point
+    cam = cam + make_float3(A.env_cam[env], A.env_cam[A.ld + env], A.env_cam[2 * A.ld + env]);
+    fwd = ld3s(A.lookat) - cam;
+    fwd = fwd * rsqrtf(dot3(fwd, fwd));
+    float3 r = cross3(fwd, ld3s(A.upv));
+    r = r * rsqrtf(dot3(r, r));
+    up = cross3(r, fwd) * A.tan_half;
+    right = r * (A.tan_half * A.aspect);
+  }
+  if (A.env_light) {
+    light = make_float3(A.env_light[env], A.env_light[A.ld + env], A.env_light[2 * A.ld + env]) * -1.f;
+    light = light * rsqrtf(dot3(light, light));
+  }
+  if (A.env_tint)
+    for (int k = 0; k < 3; k++) tint[k] = A.env_tint[k * A.ld + env];
   const int W_ = A.width, H_ = A.height, np = W_ * H_;
   for (int p = threadIdx.x; p < np; p += blockDim.x) {
     const int px = p % W_, py = p / W_;
@@ -222,6 +243,7 @@ __global__ void __launch_bounds__(256) render_kernel(const __grid_constant__ Ren
       for (int k = 0; k < 3; k++) col[k] = A.rgb[3 * hit + k] * shade;
       code = (hit + 1) + (lit ? 0 : 65536);
     }
+    for (int k = 0; k < 3; k++) col[k] *= tint[k];
     const int64_t pix = env * (int64_t)np + p;
     if (A.format == PG_PIXELS_U8) {
       uint8_t* o = static_cast<uint8_t*>(A.pixels) + 3 * pix;
@@ -275,6 +297,10 @@ extern "C" int pg_render(const pg_batch* b, const pg_state* s, const pg_render_d
     A.light[k] = (float)L[k]; A.bg[k] = d->background[k];
   }
   A.ambient = d->ambient; A.diffuse = d->diffuse;
+  for (int k = 0; k < 3; k++) { A.lookat[k] = d->cam_lookat[k]; A.upv[k] = d->cam_up[k]; }
+  A.tan_half = (float)th;
+  A.aspect = (float)asp;
+  A.env_cam = d->env_cam_offset; A.env_light = d->env_light_dir; A.env_tint = d->env_tint;
   for (int g = 0; g < m->hdr.ngeom; g++)
     for (int k = 0; k < 3; k++) A.rgb[3 * g + k] = d->geom_rgb[3 * g + k];
   A.pixels = pixels; A.hits = hits;

@@ -106,3 +106,42 @@ def test_hidden_geoms_and_argument_errors():
     with pytest.raises(_capi.PgError) as ei:
         core.render(run.batch, run.state, bad, torch.zeros((4, 24, 0, 3), dtype=torch.uint8, device="cuda"))
     assert ei.value.code == _capi.PG_EINVAL
+
+
+def test_visual_randomisation_matches_oracle():
+    """Per-environment camera positions (look-at kept), light directions and colour tints: each
+    image equals the oracle's image of that environment's scene, times its tint."""
+    m = W.cartpole_pixels()
+    n = 16
+    sc = W.cartpole_scene(48, 40)
+    q, v = W.initial_state(m, 0, n)
+    q = q.copy(); q[:, 1] *= 8.0
+    rng = np.random.default_rng(11)
+    off = rng.uniform(-0.4, 0.4, (n, 3)).astype(np.float32)
+    ldir = np.stack([rng.uniform(-0.6, 0.6, n), rng.uniform(-0.6, 0.6, n), -np.ones(n)], 1).astype(np.float32)
+    tint = rng.uniform(0.6, 1.2, (n, 3)).astype(np.float32)
+    run = GpuRun(m, n)
+    run.set_state(q, v)
+    ld = run.state.ld
+    dev = lambda a: torch.from_numpy(core.to_soa(a, ld, 3)).to("cuda")
+    px = torch.zeros((n, sc.height, sc.width, 3), dtype=torch.float32, device="cuda")
+    hits = torch.zeros((n, sc.height, sc.width), dtype=torch.int32, device="cuda")
+    core.render(run.batch, run.state, sc, px, hits, cam_offset=dev(off), light_dir=dev(ldir), tint=dev(tint))
+    torch.cuda.synchronize()
+    px, hits = px.cpu().numpy(), hits.cpu().numpy()
+    om = O.OracleModel(m)
+    differ = 0
+    for e in range(n):
+        oc, ocode = RD.render(om, RD.randomized_scene(sc, off[e], ldir[e]), q[e].astype(np.float64))
+        oc = oc * tint[e].astype(np.float64)
+        bad = hits[e] != ocode
+        edge = _edge(ocode)
+        assert not np.any(bad & ~edge), e
+        differ += bad.sum()
+        same = ~bad & ~edge
+        # the camera basis is rebuilt per environment in float32 here (once per launch on the host
+        # in float64 otherwise): ray directions carry a few ulps more, so 2e-4
+        assert np.abs(px[e][same] - oc[same]).max() <= 2e-4, e
+    assert differ <= 0.01 * n * sc.width * sc.height
+    # the randomisation shows: two environments' backgrounds differ by their tints
+    assert not np.allclose(px[0][hits[0] == 0].mean(0), px[1][hits[1] == 0].mean(0))
