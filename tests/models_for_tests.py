@@ -115,3 +115,49 @@ def limited_arm(timestep=0.002, iterations=100):
     b.actuator(j1, W.POSITION, kp=8.0, kd=0.2)
     b.actuator(j2, W.POSITION, kp=3.0, kd=0.1)
     return b.build(timestep=timestep, iterations=iterations, n_substeps=4)
+
+
+def floating_chain(ndof):
+    """A floating base (6 dofs) carrying a chain of ndof - 6 hinged links (alternating x and y
+    axes), with joint damping: 64 dofs is the kernels' limit."""
+    b = W.ModelBuilder("chain%d" % ndof)
+    base = b.body(0, (0.0, 0.0, 2.0))
+    b.joint(base, W.FREE)
+    b.geom(base, W.BOX, (0.05, 0.05, 0.05), mass=1.0)
+    parent = base
+    for i in range(ndof - 6):
+        body = b.body(parent, (0.0, 0.0, -0.05))
+        b.joint(body, W.HINGE, axis=(0, 1, 0) if i % 2 else (1, 0, 0), damping=0.01)
+        b.geom(body, W.CAPSULE, (0.01, 0.02), pos=(0, 0, -0.025), mass=0.05)
+        parent = body
+    return b.build(timestep=0.002, iterations=4)
+
+
+def many_feet(nfeet, max_contacts=None):
+    """A free plate on nfeet sphere feet over a plane, each foot a contact pair (4 pyramid rows
+    per contact: 32 simultaneous contacts is the kernels' 128-row limit)."""
+    b = W.ModelBuilder("feet%d" % nfeet)
+    floor = b.geom(0, W.PLANE, (0, 0, 0))
+    body = b.body(0, (0, 0, 0.0795))
+    b.joint(body, W.FREE)
+    b.geom(body, W.BOX, (1.0, 1.0, 0.05), mass=1.0)
+    for k in range(nfeet):
+        g = b.geom(body, W.SPHERE, (0.02,), pos=(-0.9 + 0.05 * k, 0.02 * (k % 3), -0.06))
+        b.pair(floor, g, friction=1.0, condim=3)
+    return b.build(timestep=0.002, iterations=6, max_contacts=max_contacts, qpos_init=(0, 0, 0.0795, 1, 0, 0, 0))
+
+
+def floating_star(ndof):
+    """A floating plate (6 dofs) with ndof - 6 single hinged legs around its rim, alternating
+    radial and tangential axes: the 64-dof limit on a shallow, well-conditioned tree."""
+    b = W.ModelBuilder("star%d" % ndof)
+    base = b.body(0, (0.0, 0.0, 2.0))
+    b.joint(base, W.FREE)
+    b.geom(base, W.BOX, (0.2, 0.2, 0.05), mass=2.0)
+    for i in range(ndof - 6):
+        ang = 2 * math.pi * i / (ndof - 6)
+        c, s = math.cos(ang), math.sin(ang)
+        body = b.body(base, (0.15 * c, 0.15 * s, 0.0))
+        b.joint(body, W.HINGE, axis=(c, s, 0) if i % 2 else (-s, c, 0), damping=0.01)
+        b.geom(body, W.CAPSULE, (0.01, 0.05), pos=(0, 0, -0.05), mass=0.1)
+    return b.build(timestep=0.002, iterations=4)

@@ -1,6 +1,7 @@
 """CPU-only checks of the C ABI library: it loads, exports every function include/pg.h
 declares, and the host-side model compiler validates descriptions (no GPU work)."""
 import ctypes as C
+import dataclasses
 import os
 import re
 
@@ -8,6 +9,7 @@ import numpy as np
 import pytest
 
 from paper_2502_08844_b300 import workloads as W
+from tests import models_for_tests as MT
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -121,3 +123,28 @@ def test_per_environment_parameter_rows():
     with pytest.raises(_capi.PgError) as ei:
         core.CompiledModel(q)
     assert ei.value.code == _capi.PG_EINVAL
+
+
+@pytest.mark.parametrize("ndof,ok", [(64, True), (65, False)])
+def test_dof_capacity_limit(ndof, ok):
+    """The kernels take at most 64 dofs (and 64 bodies, the world included): a floating base
+    with 58 hinges (64 dofs, 60 bodies) compiles, one more hinge does not."""
+    from paper_2502_08844_b300 import core, _capi
+    if ok:
+        assert core.CompiledModel(MT.floating_chain(ndof)).sizes.nv == ndof
+    else:
+        with pytest.raises(_capi.PgError) as ei:
+            core.CompiledModel(MT.floating_chain(ndof))
+        assert ei.value.code == _capi.PG_ECAPACITY
+
+
+def test_row_capacity_limit():
+    """At most 128 constraint rows: a free body on 33 sphere feet (4 rows per contact) compiles
+    with 32 simultaneous contacts (128 rows), not with 33."""
+    from paper_2502_08844_b300 import core, _capi
+    m33 = MT.many_feet(33)
+    with pytest.raises(_capi.PgError) as ei:
+        core.CompiledModel(m33)
+    assert ei.value.code == _capi.PG_ECAPACITY
+    m32 = MT.many_feet(33, max_contacts=32)
+    assert core.CompiledModel(m32).sizes.nrow_max == 128
