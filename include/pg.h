@@ -407,11 +407,13 @@ int pg_env_reset(const pg_batch* batch, const pg_task* task, pg_state* state, fl
  * ended on this step: terminated or truncated), truncated [1] (1 when it ended by
  * episode_length only), terms [PG_NTERMS] (unweighted reward terms, or NULL).
  * reward, done, truncated and terms describe the transition; obs describes the state the next
- * action acts on.  Errors as pg_env_reset. */
+ * action acts on.  params_dev (optional, NULL for none): per-environment physical parameters in
+ * pg_step_dr's layout, used by the physics and the PD torques of the reward terms.  Errors as
+ * pg_env_reset. */
 int pg_env_step(const pg_batch* batch, const pg_task* task, pg_state* state, float* task_state_dev,
                 const float* action_dev, const float* cmd_dev, const float* qpos0_dev, const float* qvel0_dev,
                 int n_substeps, float* obs_dev, float* reward_dev, float* done_dev, float* truncated_dev,
-                float* terms_dev, void* stream);
+                float* terms_dev, const float* params_dev, void* stream);
 
 /* ---- batch ray-traced pixel observations -------------------------------------------------
  *

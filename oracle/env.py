@@ -80,6 +80,10 @@ class OracleTask:
         self.contact_height, self.clearance = f(task.contact_height), f(task.clearance_height)
         self.sig_v, self.sig_w = f(task.sigma_lin_vel), f(task.sigma_ang_vel)
         self.air_min, self.air_max = f(task.air_time_min), f(task.air_time_max)
+        # per-environment calibration offsets of the PD actuators (randomisation): the actuators act
+        # as if their targets were q_des + calibration (set it on a task built on the substituted
+        # model of oracle.randomize)
+        self.calibration = np.zeros(m.nu)
 
     # ---- task state layout: q_des [nu] | previous action [nu] | air time [nf] | contact [nf] | step
     def split(self, st):
@@ -147,7 +151,7 @@ class OracleTask:
         m_lim = None if self.m.act_forcelimited is None else self.m.act_forcelimited.astype(bool)
         q = np.asarray(qpos, np.float64)[self.act_q]
         qd = np.asarray(qvel, np.float64)[self.act_d]
-        tau = self.kp * (q_des - q) - self.kd * qd
+        tau = self.kp * (q_des + self.calibration - q) - self.kd * qd
         if m_lim is not None:
             tau = np.where(m_lim, np.clip(tau, self.flo, self.fhi), tau)
         _, height, vel = self.feet(qpos, qvel)
@@ -191,8 +195,8 @@ class OracleTask:
         q_des_prev, a_prev, air, contact, step = self.split(np.asarray(task_state, np.float64))
         q_des = self.targets(a, q_des_prev)
         qn, vn, wn, status = self.om.rollout(np.asarray(qpos, np.float64)[None], np.asarray(qvel, np.float64)[None],
-                                             q_des[None, None], n_substeps, qacc_warm=np.asarray(warm, np.float64)[None],
-                                             solver_cap=solver_cap)
+                                             (q_des + self.calibration)[None, None], n_substeps,
+                                             qacc_warm=np.asarray(warm, np.float64)[None], solver_cap=solver_cap)
         qn, vn, wn = qn[0], vn[0], wn[0]
         dt = n_substeps * float(np.float32(self.m.timestep))
         term = self.terminated(qn, vn)

@@ -113,7 +113,7 @@ _lib.pg_task_free.argtypes = [C.c_void_p]
 _lib.pg_task_free.restype = None
 _lib.pg_env_reset.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(pg_state)] + [C.c_void_p] * 6
 _lib.pg_env_step.argtypes = ([C.c_void_p, C.c_void_p, C.POINTER(pg_state)] + [C.c_void_p] * 5 + [C.c_int] +
-                             [C.c_void_p] * 6)
+                             [C.c_void_p] * 7)
 _lib.pg_render.argtypes = [C.c_void_p, C.POINTER(pg_state), C.POINTER(pg_render_desc), C.c_int, C.c_void_p,
                            C.c_void_p, C.c_void_p]
 for _n in EXPORTS:
@@ -231,10 +231,10 @@ def pg_env_reset(batch, task, state: pg_state, task_state_ptr, qpos0_ptr, qvel0_
 
 
 def pg_env_step(batch, task, state: pg_state, task_state_ptr, action_ptr, cmd_ptr, qpos0_ptr, qvel0_ptr,
-                n_substeps: int, obs_ptr, reward_ptr, done_ptr, truncated_ptr, terms_ptr, stream) -> None:
+                n_substeps: int, obs_ptr, reward_ptr, done_ptr, truncated_ptr, terms_ptr, params_ptr, stream) -> None:
     _check(_lib.pg_env_step(batch, task, C.byref(state), task_state_ptr, action_ptr, cmd_ptr, qpos0_ptr, qvel0_ptr,
-                            int(n_substeps), obs_ptr, reward_ptr, done_ptr, truncated_ptr, terms_ptr, stream),
-           "pg_env_step")
+                            int(n_substeps), obs_ptr, reward_ptr, done_ptr, truncated_ptr, terms_ptr, params_ptr,
+                            stream), "pg_env_step")
 
 
 def pg_render(batch, state: pg_state, desc: pg_render_desc, fmt: int, pixels_ptr, hits_ptr, stream) -> None:

@@ -167,16 +167,18 @@ def env_reset(batch: Batch, task: Task, state: State, task_state: torch.Tensor, 
 def env_step(batch: Batch, task: Task, state: State, task_state: torch.Tensor, actions: torch.Tensor,
              cmd: torch.Tensor, qpos0: torch.Tensor, qvel0: torch.Tensor, n_substeps: int, obs: torch.Tensor,
              reward: torch.Tensor, done: torch.Tensor, truncated: torch.Tensor, terms: Optional[torch.Tensor] = None,
-             stream=None) -> None:
-    """pg_env_step: targets, physics, reward, termination, reset and observation in one launch."""
+             stream=None, params: Optional[torch.Tensor] = None) -> None:
+    """pg_env_step: targets, physics, reward, termination, reset and observation in one launch;
+    params ([nrand][ld], optional): per-environment physical parameters as for step_dr."""
     ld = state.ld
     assert actions.dtype == torch.float32 and actions.is_contiguous() and actions.shape == (task.model.nu, ld)
     assert task_state.shape == (task.state_rows, ld) and obs.shape == (task.nobs, ld) and cmd.shape == (3, ld)
     assert reward.numel() >= ld and done.numel() >= ld and truncated.numel() >= ld
     assert terms is None or terms.shape == (task.nterms, ld)
+    assert params is None or (params.dtype == torch.float32 and params.shape == (task.model.sizes.nrand, ld))
     _capi.pg_env_step(batch.handle, task.handle, state.c(), _ptr(task_state), _ptr(actions), _ptr(cmd.contiguous()),
                       _ptr(qpos0.contiguous()), _ptr(qvel0.contiguous()), int(n_substeps), _ptr(obs), _ptr(reward),
-                      _ptr(done), _ptr(truncated), _ptr(terms), _stream_ptr(stream))
+                      _ptr(done), _ptr(truncated), _ptr(terms), _ptr(params), _stream_ptr(stream))
 
 
 def render(batch: Batch, state: State, scene: W.Scene, pixels: torch.Tensor, hits: Optional[torch.Tensor] = None,

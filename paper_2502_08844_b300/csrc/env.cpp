@@ -149,7 +149,7 @@ int pg_env_reset(const pg_batch* b, const pg_task* t, pg_state* s, float* task_s
 
 int pg_env_step(const pg_batch* b, const pg_task* t, pg_state* s, float* task_state, const float* actions,
                 const float* cmd, const float* qpos0, const float* qvel0, int n_substeps, float* obs, float* reward,
-                float* done, float* truncated, float* terms, void* stream) {
+                float* done, float* truncated, float* terms, const float* params, void* stream) {
   int rc = check_env_call(b, t, s, task_state);
   if (rc) return rc;
   if (n_substeps < 0) return set_error(PG_EINVAL, "n_substeps must be >= 0 (0: the model's own)");
@@ -160,7 +160,7 @@ int pg_env_step(const pg_batch* b, const pg_task* t, pg_state* s, float* task_st
   E.state = task_state; E.actions = actions; E.cmd = cmd; E.qpos0 = qpos0; E.qvel0 = qvel0;
   E.obs = obs; E.reward = reward; E.done = done; E.truncated = truncated; E.terms = terms;
   E.task = t->task;
-  cudaError_t e = launch_env_step(b, s, E, n_substeps, (cudaStream_t)stream);
+  cudaError_t e = launch_env_step(b, s, E, n_substeps, (cudaStream_t)stream, params);
   if (e != cudaSuccess) return set_error(PG_ECUDA, std::string("environment step launch: ") + cudaGetErrorString(e));
   return PG_OK;
 }

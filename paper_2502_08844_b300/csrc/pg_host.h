@@ -96,7 +96,8 @@ cudaError_t launch_reset(const pg_batch* b, const pg_state* s, const uint8_t* ma
                          const float* qvel0, cudaStream_t st);
 cudaError_t configure_step_kernels(size_t smem_bytes);
 // environment step and reset of a locomotion task (step.cu)
-cudaError_t launch_env_step(const pg_batch* b, const pg_state* s, const EnvArgs& E, int n_substeps, cudaStream_t st);
+cudaError_t launch_env_step(const pg_batch* b, const pg_state* s, const EnvArgs& E, int n_substeps, cudaStream_t st,
+                            const float* dr = nullptr);
 cudaError_t launch_env_reset(const pg_batch* b, const pg_state* s, const EnvArgs& E, cudaStream_t st);
 cudaError_t launch_step_tape(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, float* tape,
                              int tape_rows, cudaStream_t st);
@@ -115,9 +116,10 @@ cudaError_t launch_step_tape(const pg_batch* b, const pg_state* s, const float* 
                         const float* dr = nullptr);                                                              \
   cudaError_t step_spec_tape(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, float* tape,\
                              int tape_rows, cudaStream_t st);                                                   \
-  cudaError_t step_env(const pg_batch* b, const pg_state* s, const EnvArgs& E, int n_substeps, cudaStream_t st);  \
+  cudaError_t step_env(const pg_batch* b, const pg_state* s, const EnvArgs& E, int n_substeps, cudaStream_t st,   \
+                       const float* dr = nullptr);                                                              \
   cudaError_t step_spec_env(const pg_batch* b, const pg_state* s, const EnvArgs& E, int n_substeps,            \
-                            cudaStream_t st);                                                                  \
+                            cudaStream_t st, const float* dr = nullptr);                                       \
   cudaError_t step_spec_parts(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps,          \
                               cudaStream_t st);                                                                \
   }

@@ -168,6 +168,9 @@ __device__ float ray_geom(const GeomFrame& g, float3 o, float3 d, float3& n) {
   }
 }
 
+// VDR: per-environment visual randomisation (camera offsets, light directions, tints); a separate
+// variant, so that the plain kernel carries none of its registers
+template <bool VDR>
 __global__ void __launch_bounds__(256) render_kernel(const __grid_constant__ RenderArgs A) {
   extern __shared__ __align__(16) float ws[];
   __shared__ GeomFrame frames[kMaxRenderGeoms];
@@ -197,7 +200,7 @@ __global__ void __launch_bounds__(256) render_kernel(const __grid_constant__ Ren
   __syncthreads();
   float3 cam = ld3s(A.cam), fwd = ld3s(A.fwd), right = ld3s(A.right), up = ld3s(A.up), light = ld3s(A.light);
   float tint[3] = {1.f, 1.f, 1.f};
-  if (A.env_cam) {   // this environment's camera: moved, still looking at the same point
+  if (VDR && A.env_cam) {   // this environment's camera: moved, still looking at the same point
     cam = cam + make_float3(A.env_cam[env], A.env_cam[A.ld + env], A.env_cam[2 * A.ld + env]);
     fwd = ld3s(A.lookat) - cam;
     fwd = fwd * rsqrtf(dot3(fwd, fwd));
@@ -206,11 +209,11 @@ __global__ void __launch_bounds__(256) render_kernel(const __grid_constant__ Ren
     up = cross3(r, fwd) * A.tan_half;
     right = r * (A.tan_half * A.aspect);
   }
-  if (A.env_light) {
+  if (VDR && A.env_light) {
     light = make_float3(A.env_light[env], A.env_light[A.ld + env], A.env_light[2 * A.ld + env]) * -1.f;
     light = light * rsqrtf(dot3(light, light));
   }
-  if (A.env_tint)
+  if (VDR && A.env_tint)
     for (int k = 0; k < 3; k++) tint[k] = A.env_tint[k * A.ld + env];
   const int W_ = A.width, H_ = A.height, np = W_ * H_;
   for (int p = threadIdx.x; p < np; p += blockDim.x) {
@@ -243,7 +246,8 @@ __global__ void __launch_bounds__(256) render_kernel(const __grid_constant__ Ren
       for (int k = 0; k < 3; k++) col[k] = A.rgb[3 * hit + k] * shade;
       code = (hit + 1) + (lit ? 0 : 65536);
     }
-    for (int k = 0; k < 3; k++) col[k] *= tint[k];
+    if (VDR)
+      for (int k = 0; k < 3; k++) col[k] *= tint[k];
     const int64_t pix = env * (int64_t)np + p;
     if (A.format == PG_PIXELS_U8) {
       uint8_t* o = static_cast<uint8_t*>(A.pixels) + 3 * pix;
@@ -309,9 +313,13 @@ extern "C" int pg_render(const pg_batch* b, const pg_state* s, const pg_render_d
   static std::mutex mu;
   static unsigned long long configured = 0;
   once_per_device(mu, configured, [] {
-    cudaFuncSetAttribute(render_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem - 8192);
+    cudaFuncSetAttribute(render_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem - 8192);
+    cudaFuncSetAttribute(render_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem - 8192);
   });
-  render_kernel<<<(unsigned)b->n, 256, smem, (cudaStream_t)stream>>>(A);
+  if (A.env_cam || A.env_light || A.env_tint)
+    render_kernel<true><<<(unsigned)b->n, 256, smem, (cudaStream_t)stream>>>(A);
+  else
+    render_kernel<false><<<(unsigned)b->n, 256, smem, (cudaStream_t)stream>>>(A);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(PG_ECUDA, std::string("render launch: ") + cudaGetErrorString(e));
   return PG_OK;

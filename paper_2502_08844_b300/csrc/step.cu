@@ -90,9 +90,11 @@ cudaError_t launch_step_tape(const pg_batch* b, const pg_state* s, const float* 
                          : pyramidal::step_tape(b, s, ctrl, n_substeps, tape, tape_rows, st);
 }
 
-cudaError_t launch_env_step(const pg_batch* b, const pg_state* s, const EnvArgs& E, int n_substeps, cudaStream_t st) {
-  if (b->spec_kernel_env) return pyramidal::step_spec_env(b, s, E, n_substeps, st);
-  return b->has_elliptic ? elliptic::step_env(b, s, E, n_substeps, st) : pyramidal::step_env(b, s, E, n_substeps, st);
+cudaError_t launch_env_step(const pg_batch* b, const pg_state* s, const EnvArgs& E, int n_substeps, cudaStream_t st,
+                            const float* dr) {
+  if (b->spec_kernel_env) return pyramidal::step_spec_env(b, s, E, n_substeps, st, dr);
+  return b->has_elliptic ? elliptic::step_env(b, s, E, n_substeps, st, dr)
+                         : pyramidal::step_env(b, s, E, n_substeps, st, dr);
 }
 
 cudaError_t launch_env_reset(const pg_batch* b, const pg_state* s, const EnvArgs& E, cudaStream_t st) {

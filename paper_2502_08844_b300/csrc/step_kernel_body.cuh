@@ -44,8 +44,9 @@ static_assert(sizeof(StepArgs) <= 32764, "the step's argument block must fit the
 // before the substeps (they are the PD targets), and after them the reward, termination,
 // automatic reset and observation (env_device.cuh).
 
-// DR: per-environment parameters (A.dr, pg_step_dr); without it the context's parameter pointer
-// is a compile-time NULL and every parameter branch folds away.
+// DR: per-environment parameters (A.dr, pg_step_dr); the environment step (ENV) reads them when
+// A.dr is set; otherwise the context's parameter pointer is a compile-time NULL and every
+// parameter branch folds away.
 template <bool DEBUG, bool TAPE, int SPEC_M = 0, bool ENV = false, bool DR = false>
 __device__ __forceinline__ void step_body(const StepArgs& A) {
   extern __shared__ __align__(16) float smem[];
@@ -67,7 +68,7 @@ __device__ __forceinline__ void step_body(const StepArgs& A) {
   const int64_t env = tile.env0 + t;
   float* w = smem + warp * (S * h.ws_floats) + lane;
   Ctx c{h, S, reinterpret_cast<const int*>(blob), reinterpret_cast<const float*>(blob), w, ENV ? A.env.state : A.ctrl,
-        A.ld, env, A.hfield[tile.model], DR ? A.dr : nullptr};
+        A.ld, env, A.hfield[tile.model], (DR || ENV) ? A.dr : nullptr};
   if (ENV) env_targets(c, A.env);
   for (int k = 0; k < h.nq; k++) W(qpos, k) = A.qpos[k * A.ld + env];
   uint32_t status = 0;

@@ -128,22 +128,26 @@ cudaError_t step_spec_parts(const pg_batch* b, const pg_state* s, const float* c
 }
 
 // an environment step of the locomotion task E (generic kernel, or the batch's specialised one)
-cudaError_t step_env(const pg_batch* b, const pg_state* s, const EnvArgs& E, int n_substeps, cudaStream_t st) {
+cudaError_t step_env(const pg_batch* b, const pg_state* s, const EnvArgs& E, int n_substeps, cudaStream_t st,
+                     const float* dr) {
   if (b->ntiles == 0) return cudaSuccess;
   static thread_local StepArgs A;
   make_args(A, b, s, nullptr);
   A.n_substeps = n_substeps;
   A.env = E;
+  A.dr = dr;
   step_kernel<false, false, true><<<b->ntiles, b->threads, b->smem_bytes, st>>>(A);
   return cudaGetLastError();
 }
 
-cudaError_t step_spec_env(const pg_batch* b, const pg_state* s, const EnvArgs& E, int n_substeps, cudaStream_t st) {
+cudaError_t step_spec_env(const pg_batch* b, const pg_state* s, const EnvArgs& E, int n_substeps, cudaStream_t st,
+                          const float* dr) {
   if (b->ntiles == 0) return cudaSuccess;
   static thread_local StepArgs A;
   make_args(A, b, s, nullptr);
   A.n_substeps = n_substeps;
   A.env = E;
+  A.dr = dr;
   void* params[] = {&A};
   return cudaLaunchKernel((const void*)b->spec_kernel_env, dim3(b->ntiles), dim3(b->threads), params, b->smem_bytes, st);
 }

@@ -218,5 +218,29 @@ def test_env_step_argument_errors():
         core.env_reset(other, S.t, core.State(other, DEV), S.d_task_state, S.d_q0, S.d_v0, S.d_cmd, S.obs)
     assert ei.value.code == _capi.PG_EUNSUPPORTED
     rc = _capi._lib.pg_env_step(S.batch.handle, S.t.handle, S.state.c(), None, None, None, None, None, 5,
-                                None, None, None, None, None, None)
+                                None, None, None, None, None, None, None)
     assert rc == _capi.PG_EINVAL
+
+
+def test_env_step_with_per_environment_parameters():
+    """pg_env_step with a per-environment parameter block: each environment against the oracle's
+    task on its substituted model (oracle.randomize), calibration offsets included."""
+    O, E = _oracle()
+    from oracle import randomize as RZ
+    task = W.quadruped_task(episode_length=50)
+    S = Setup(24, task, seed=4)
+    S.task_state[:, -1] = 0
+    S.upload()
+    P = W.randomized_params(S.m, 1, S.n)
+    params = torch.from_numpy(core.to_soa(P, S.ld, P.shape[1])).to(DEV)
+    a = torch.from_numpy(core.to_soa(S.U[0], S.ld, S.m.nu)).to(DEV)
+    core.env_step(S.batch, S.t, S.state, S.d_task_state, a, S.d_cmd, S.d_q0, S.d_v0, 5, S.obs, S.rew, S.done,
+                  S.trunc, S.terms, params=params)
+    torch.cuda.synchronize()
+    g = S.host()
+    pre = dict(qpos=S.q.astype(np.float64), qvel=S.v.astype(np.float64), task_state=S.task_state.astype(np.float64))
+    nb, nv = S.m.nbody, S.m.nv
+    for e in range(S.n):
+        ot = E.OracleTask(O.OracleModel(RZ.substituted_model(S.m, P[e])), task)
+        ot.calibration = P[e, 2 + 3 * nb + nv:].astype(np.float64)
+        _compare_env(ot, g, e, pre, S.U[0][e], S.cmd[e], S.q0[e], S.v0[e], np.zeros(nv))
