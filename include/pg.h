@@ -306,7 +306,8 @@ int pg_step_host(pg_batch* batch, pg_state* state, const float* ctrl_host, float
  *   * any joints and actuators;
  *   * joint limits;
  *   * contacts only between a world-fixed plane (geom1) and spheres, capsules or boxes;
- *   * no actuator torque limits and no joint friction loss.
+ *   * no joint friction loss.
+ * A force clipped at its actuator's torque limit is constant: nothing flows back through it.
  * Otherwise the call returns PG_EUNSUPPORTED.
  *
  * Scratch and errors.

@@ -310,6 +310,12 @@ __device__ void substep_vjp(const Ctx& c, int nc, const unsigned act[4], float* 
       u = fminf(fmaxf(u0, MF(act_range, 2 * k)), MF(act_range, 2 * k + 1));
       pass = u0 > MF(act_range, 2 * k) && u0 < MF(act_range, 2 * k + 1);
     }
+    if (MI(act_forcelimited, k)) {   // a force clipped at its limit is constant: no derivative
+      const float f = MI(act_type, k) == PG_ACT_MOTOR
+                          ? MF(act_gear, k) * u
+                          : MF(act_kp, k) * (u - W(qpos, MI(act_qposadr, k))) - MF(act_kd, k) * W(qvel, d);
+      if (f < MF(act_forcerange, 2 * k) || f > MF(act_forcerange, 2 * k + 1)) continue;
+    }
     if (MI(act_type, k) == PG_ACT_MOTOR) {
       if (pass) gu[k * ld + env] += MF(act_gear, k) * lam;
     } else {

@@ -92,6 +92,20 @@ def test_quadruped_rollout_gradient_matches_oracle():
     check_against_oracle(m, q0, v0, U, w)
 
 
+def test_torque_limited_rollout_gradient_matches_oracle():
+    """The quadruped with 4 Nm torque limits (its PD forces saturate): a clipped force is constant,
+    so nothing flows back through it (kp and control gradients of a saturated actuator vanish);
+    end to end over one segment against the oracle's reverse mode."""
+    m = _converged(W.quadruped())
+    m.act_forcelimited = np.ones(m.nu, np.int32)
+    m.act_forcerange = np.tile(np.array([[-4.0, 4.0]], np.float32), (m.nu, 1))
+    n, T = 8, 8
+    q0, v0 = W.initial_state(m, 4, n)
+    U = W.actions(m, 4, n, 0, T)
+    w = O.tracking_loss_weights(O.OracleModel(m))
+    check_against_oracle(m, q0, v0, U, w)
+
+
 def _contact_states(m, n_states=8, T=60):
     """FP32 quadruped states along an oracle rollout (standing, stepping, sliding contacts)."""
     om = O.OracleModel(m)
