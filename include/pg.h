@@ -305,9 +305,9 @@ int pg_step_host(pg_batch* batch, pg_state* state, const float* ctrl_host, float
  * Scope. Every model of the batch needs adjoint_workspace_bytes > 0. That means:
  *   * any joints and actuators;
  *   * joint limits;
- *   * contacts only between a world-fixed plane (geom1) and spheres, capsules or boxes;
- *   * no joint friction loss.
- * A force clipped at its actuator's torque limit is constant: nothing flows back through it.
+ *   * contacts only between a world-fixed plane (geom1) and spheres, capsules or boxes.
+ * A force clipped at its actuator's torque limit, and a friction-loss row's force at its bound,
+ * are constant: nothing flows back through them.
  * Otherwise the call returns PG_EUNSUPPORTED.
  *
  * Scratch and errors.

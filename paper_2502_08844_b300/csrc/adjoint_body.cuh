@@ -36,7 +36,7 @@
 // Scope (checked by the model compiler, `adj_ok`):
 //  * any joints;
 //  * pyramidal or condim-1 contacts between a world-fixed plane and spheres, capsules or boxes;
-//  * joint limits;
+//  * joint limits and joint friction loss;
 //  * motor and PD actuators.
 //
 // The gradient treats the solver's final iterate as the optimum. It is exact when the solver has
@@ -130,6 +130,11 @@ __device__ void hessian_factor(const Ctx& c, const unsigned act[4], int HL) {
   }
   for (int li = 0; li < h.nlimited; li++) {
     const int r = 4 * MC + li, d = MI(jnt_dofadr, MI(limit_jnt, li));
+    if (bit(act, r)) H[MI(dof_rowadr, d) * c.S] += W(rD, r);
+  }
+  // friction-loss rows inside their band (outside it a row's force is the constant bound)
+  for (int k = 0; k < h.nfric; k++) {
+    const int r = fric_row0(h) + k, d = MI(fric_dof, k);
     if (bit(act, r)) H[MI(dof_rowadr, d) * c.S] += W(rD, r);
   }
   ldl_factor(c, HL);
@@ -439,6 +444,21 @@ __device__ void substep_vjp(const Ctx& c, int nc, const unsigned act[4], float* 
     const float db = -h.kref * pos * arefb + Db / ((1.f - dd) * (1.f - dd) * A);
     B(q, qa) += sgn * (-h.kref * dd * arefb + db * impedance_slope(h, pos));
     // Ahat = (M^-1)_dd
+    const int wo = h.b_w;
+    for (int i = 0; i < nv; i++) c.w[(wo + i) * c.S] = 0.f;
+    c.w[(wo + d) * c.S] = 1.f;
+    ldl_solve(c, h.w_L, wo);
+    mbar_outer(c, wo, wo, -Db * D / A);
+  }
+  // friction-loss rows inside their band: as a limit row at zero position (aref = -b v, constant
+  // impedance); outside the band the row's force is the constant bound and passes nothing back
+  for (int k = 0; k < h.nfric; k++) {
+    const int r = fric_row0(h) + k;
+    if (!bit(act, r)) continue;
+    const int d = MI(fric_dof, k);
+    const float D = W(rD, r), jl = W(Jp, r), jar = W(jar, r), A = W(Ahat, r);
+    const float arefb = D * jl, Db = -jl * jar;
+    B(v, d) += -h.bref * arefb;
     const int wo = h.b_w;
     for (int i = 0; i < nv; i++) c.w[(wo + i) * c.S] = 0.f;
     c.w[(wo + d) * c.S] = 1.f;

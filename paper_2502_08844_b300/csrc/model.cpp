@@ -469,7 +469,6 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
     }
     if (npair > 0 && !tree_hessian) ok = false;
     if (d->cone == PG_CONE_ELLIPTIC) ok = false;
-    if (!fric_dof.empty()) ok = false;   // nor friction-loss rows
     g.adj_ok = ok ? 1 : 0;
     h.adj_ok = g.adj_ok;
     h.ws_adj_floats = g.ws_adj_floats;

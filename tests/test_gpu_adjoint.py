@@ -106,6 +106,20 @@ def test_torque_limited_rollout_gradient_matches_oracle():
     check_against_oracle(m, q0, v0, U, w)
 
 
+def test_friction_loss_rollout_gradient_matches_oracle():
+    """The quadruped with joint friction loss on its hinges: rows inside their band act as soft
+    rows, rows at their bound pass nothing back; end to end over one segment against the oracle's
+    reverse mode."""
+    m = _converged(W.quadruped())
+    m.dof_frictionloss = np.zeros(m.nv, np.float32)
+    m.dof_frictionloss[6:] = 0.8
+    n, T = 8, 8
+    q0, v0 = W.initial_state(m, 4, n)
+    U = W.actions(m, 4, n, 0, T)
+    w = O.tracking_loss_weights(O.OracleModel(m))
+    check_against_oracle(m, q0, v0, U, w)
+
+
 def _contact_states(m, n_states=8, T=60):
     """FP32 quadruped states along an oracle rollout (standing, stepping, sliding contacts)."""
     om = O.OracleModel(m)
