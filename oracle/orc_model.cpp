@@ -93,7 +93,7 @@ std::string compile_model(const Desc& d, Model& m) {
   m.geom_size.assign(d.geom_size, d.geom_size + 3 * d.ngeom);
   m.geom_mass.assign(d.geom_mass, d.geom_mass + d.ngeom);
   for (int g = 0; g < m.ngeom; g++) {
-    if (m.geom_type[g] < PLANE || m.geom_type[g] > HFIELD) return "unknown geom type";
+    if (m.geom_type[g] < PLANE || m.geom_type[g] > CYLINDER) return "unknown geom type";
     if (m.geom_body[g] < 0 || m.geom_body[g] >= m.nbody) return "geom_body out of range";
     if (m.geom_type[g] == HFIELD) {
       if (m.geom_body[g] != 0 || m.geom_mass[g] != 0) return "a heightfield must be a massless geom of the world";
@@ -159,7 +159,7 @@ std::string compile_model(const Desc& d, Model& m) {
     int g1 = d.pair_geom[2 * p], g2 = d.pair_geom[2 * p + 1];
     if (g1 < 0 || g1 >= m.ngeom || g2 < 0 || g2 >= m.ngeom) return "pair geom out of range";
     int n = pair_max_points(m.geom_type[g1], m.geom_type[g2]);
-    if (n < 0) return "unsupported pair (geom1's type must not exceed geom2's: plane < sphere < capsule < box; a heightfield pairs as geom1 with spheres and capsules)";
+    if (n < 0) return "unsupported pair (geom1's type must not exceed geom2's: plane < sphere < capsule < box; a heightfield pairs as geom1 with spheres and capsules; a cylinder pairs with planes)";
     if (d.pair_condim[p] != 1 && d.pair_condim[p] != 3) return "pair_condim must be 1 or 3";
     m.pair_g1.push_back(g1);
     m.pair_g2.push_back(g2);

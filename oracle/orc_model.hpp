@@ -10,7 +10,7 @@
 namespace orc {
 
 enum { FREE = 0, HINGE = 1, SLIDE = 2 };
-enum { PLANE = 0, SPHERE = 1, CAPSULE = 2, BOX = 3, HFIELD = 4 };
+enum { PLANE = 0, SPHERE = 1, CAPSULE = 2, BOX = 3, HFIELD = 4, CYLINDER = 5 };
 enum { MOTOR = 0, POSITION = 1 };
 enum { PYRAMIDAL = 0, ELLIPTIC = 1 };
 
@@ -92,13 +92,14 @@ inline int pair_max_points(int t1, int t2) {
   if (t1 == BOX && t2 == BOX) return 4;
   if (t1 == HFIELD && t2 == SPHERE) return 1;
   if (t1 == HFIELD && t2 == CAPSULE) return 2;
+  if (t1 == PLANE && t2 == CYLINDER) return 4;
   return -1;
 }
 
 // Inertia of a uniform solid about its own centre, in its own axes (diagonal), at mass m.
 // Box: full edge lengths 2h.  Capsule: radius r, cylinder half-length hl along z, mass split
 // between the cylinder and the two hemispheres by volume; a hemisphere's centroid lies 3r/8
-// from its flat face (parallel-axis theorem).
+// from its flat face (parallel-axis theorem).  Cylinder: radius r, half-length hl along z.
 inline void solid_inertia(int type, const double* size, double m, double out[3]) {
   const double PI = 3.14159265358979323846;
   if (type == SPHERE) {
@@ -117,6 +118,10 @@ inline void solid_inertia(int type, const double* size, double m, double out[3])
     double perp = mc * (r * r / 4 + L * L / 12) + ms * (0.4 * r * r + L * L / 4 + 3.0 / 8.0 * L * r);
     out[0] = out[1] = perp;
     out[2] = axial;
+  } else if (type == CYLINDER) {
+    double r = size[0], L = 2 * size[1];
+    out[0] = out[1] = m * (3 * r * r + L * L) / 12.0;
+    out[2] = m * r * r / 2;
   } else {
     out[0] = out[1] = out[2] = 0;
   }

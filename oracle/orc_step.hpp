@@ -609,6 +609,36 @@ template <class T> Contact<T> hfield_sphere(const Xf<T>& X, const double* size, 
   return out;
 }
 
+// Cylinder (frame X, radius r, half-length hl along its z axis a) against a plane (point p0,
+// unit normal n).  The deepest point of a cylinder over a plane lies on a rim circle, on the
+// radius along which the rim falls fastest: e = -(n - (n.a) a) / |n - (n.a) a|.  When the axis
+// lies within 1e-4 of the normal every rim point is equally deep and e is the cylinder's own x
+// axis.  The lower cap is the one at -hl when n.a >= 0, else the one at +hl; with b = a x e the
+// four candidate points are
+//   0: lower cap + r e   (the deepest point)        1: upper cap + r e
+//   2: lower cap + r (-e/2 + (sqrt 3)/2 b)        3: lower cap + r (-e/2 - (sqrt 3)/2 b)
+// so that a cylinder standing on a cap rests on a tripod of rim points 120 degrees apart and one
+// lying on its side on the two rims' lowest points.  Each has normal n, distance n.(p - p0) and
+// its contact point midway between p and the plane.
+template <class T> void plane_cylinder(const V3<T>& p0, const V3<T>& n, const Xf<T>& X, T r, T hl, Contact<T>* out) {
+  const V3<T> a = col(X.R, 2);
+  const T s = dot(n, a);
+  V3<T> perp = sub(n, scl(a, s));
+  const T pl = norm(perp);
+  V3<T> e = val(pl) < 1e-4 ? col(X.R, 0) : scl(perp, T(-1) / pl);
+  const V3<T> b = cross(a, e);
+  const T sg = val(s) >= 0 ? T(-1) : T(1);
+  const V3<T> clo = add(X.p, scl(a, sg * hl)), chi = sub(X.p, scl(a, sg * hl));
+  const T c3 = T(std::sqrt(3.0) / 2);
+  V3<T> p[4] = {add(clo, scl(e, r)), add(chi, scl(e, r)), add(clo, scl(add(scl(e, T(-0.5)), scl(b, c3)), r)),
+                add(clo, scl(sub(scl(e, T(-0.5)), scl(b, c3)), r))};
+  for (int k = 0; k < 4; k++) {
+    out[k].n = n;
+    out[k].dist = dot(n, sub(p[k], p0));
+    out[k].pos = sub(p[k], scl(n, out[k].dist * T(0.5)));
+  }
+}
+
 // All candidate contacts of one pair, written to out[0 .. pair_max_points).
 template <class T> void collide_pair(int t1, const Xf<T>& X1, const double* s1, int t2, const Xf<T>& X2, const double* s2,
                                      Contact<T>* out, const HField& hf = HField()) {
@@ -652,6 +682,8 @@ template <class T> void collide_pair(int t1, const Xf<T>& X1, const double* s1, 
         out[i].dist = d[v];
         out[i].pos = sub(cp[v], scl(nz, d[v] * T(0.5)));
       }
+    } else if (t2 == CYLINDER) {
+      plane_cylinder(p0, nz, X2, T(s2[0]), T(s2[1]), out);
     }
   } else if (t1 == SPHERE) {
     if (t2 == SPHERE) {

@@ -29,7 +29,7 @@ import numpy as np
 
 # joint, geom, actuator and cone type codes (shared numbering of the model format)
 FREE, HINGE, SLIDE = 0, 1, 2
-PLANE, SPHERE, CAPSULE, BOX, HFIELD = 0, 1, 2, 3, 4
+PLANE, SPHERE, CAPSULE, BOX, HFIELD, CYLINDER = 0, 1, 2, 3, 4, 5
 MOTOR, POSITION = 0, 1
 PYRAMIDAL, ELLIPTIC = 0, 1
 
@@ -217,7 +217,7 @@ class ModelBuilder:
             dof += [j] * n
         maxpts = {(PLANE, SPHERE): 1, (PLANE, CAPSULE): 2, (PLANE, BOX): 4, (SPHERE, SPHERE): 1,
                   (SPHERE, CAPSULE): 1, (CAPSULE, CAPSULE): 1, (SPHERE, BOX): 1, (CAPSULE, BOX): 2,
-                  (BOX, BOX): 4, (HFIELD, SPHERE): 1, (HFIELD, CAPSULE): 2}
+                  (BOX, BOX): 4, (HFIELD, SPHERE): 1, (HFIELD, CAPSULE): 2, (PLANE, CYLINDER): 4}
         slots = sum(maxpts[(G[p["g"][0]]["type"], G[p["g"][1]]["type"])] for p in self.pairs)
         i32 = lambda x: np.asarray(x, np.int32)
         m = Model(
