@@ -64,7 +64,8 @@ extern "C" {
 
 /* ---- type codes ------------------------------------------------------------------- */
 enum { PG_JNT_FREE = 0, PG_JNT_HINGE = 1, PG_JNT_SLIDE = 2 };
-enum { PG_GEOM_PLANE = 0, PG_GEOM_SPHERE = 1, PG_GEOM_CAPSULE = 2, PG_GEOM_BOX = 3, PG_GEOM_HFIELD = 4 };
+enum { PG_GEOM_PLANE = 0, PG_GEOM_SPHERE = 1, PG_GEOM_CAPSULE = 2, PG_GEOM_BOX = 3, PG_GEOM_HFIELD = 4,
+       PG_GEOM_CYLINDER = 5 };
 enum { PG_ACT_MOTOR = 0, PG_ACT_POSITION = 1 };
 enum { PG_CONE_PYRAMIDAL = 0, PG_CONE_ELLIPTIC = 1 };
 
@@ -77,7 +78,8 @@ enum { PG_CONE_PYRAMIDAL = 0, PG_CONE_ELLIPTIC = 1 };
  *   body_mass, body_ipos[3], body_inertia[6] (xx,yy,zz,xy,xz,yz about the COM, body axes),
  *   body_geom_inertia              1: derive mass, COM and inertia from the body's geoms as
  *                                  uniform solids of geom_mass (box: 2*size edges; capsule:
- *                                  radius size[0], cylinder half-length size[1] along z)
+ *                                  radius size[0], cylinder half-length size[1] along z;
+ *                                  cylinder: radius size[0], half-length size[1] along z)
  *   jnt_pos[3], jnt_axis[3]        anchor and axis in the body frame; jnt_range[2] (lo < hi)
  *   dof_rotor[3]                   (gear ratio k_g, rotor mass m_r, radius r_r): armature
  *                                  k_g^2 m_r r_r^2 / 2 is added to dof_armature (App. C.2.2)
@@ -87,6 +89,9 @@ enum { PG_CONE_PYRAMIDAL = 0, PG_CONE_ELLIPTIC = 1 };
  *                                  A heightfield (PG_GEOM_HFIELD, a massless geom of the world)
  *                                  pairs as geom1 with spheres (1 point) and capsules (2: its end
  *                                  spheres); see hfield_data below.
+ *                                  A cylinder (PG_GEOM_CYLINDER) pairs as geom2 with a plane (4
+ *                                  points: the deepest rim point of each cap and two more rim
+ *                                  points of the lower cap, 120 degrees either side).
  *   pair_condim                    1 (frictionless) or 3 (pyramidal cone, 4 edge rows)
  *   act_jnt                        hinge or slide joint driven by the actuator
  *   solref = (timeconst, dampratio); solimp = (d0, dwidth, width, mid, power)

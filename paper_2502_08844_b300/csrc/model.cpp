@@ -37,6 +37,7 @@ struct Blob {
 // points a primitive pair type can produce (its static slot count); -1: unsupported
 int slots_for(int t1, int t2) {
   if (t1 == PG_GEOM_HFIELD) return t2 == PG_GEOM_SPHERE ? 1 : (t2 == PG_GEOM_CAPSULE ? 2 : -1);
+  if (t2 == PG_GEOM_CYLINDER) return t1 == PG_GEOM_PLANE ? 4 : -1;
   static const int table[4][4] = {
       //            plane sphere capsule box
       /* plane   */ {-1, 1, 2, 4},
@@ -82,6 +83,10 @@ void principal_moments(int type, const float* size, double m, double I[3]) {
     double cap_trans = m_cap * (83.0 / 320.0) * r * r + m_cap * d * d;
     I[0] = I[1] = cyl_trans + 2.0 * cap_trans;
     I[2] = cyl_axial + 2.0 * cap_axial;
+  } else if (type == PG_GEOM_CYLINDER) {
+    double r = size[0], L = 2.0 * size[1];
+    I[0] = I[1] = m * (3.0 * r * r + L * L) / 12.0;
+    I[2] = 0.5 * m * r * r;
   }
 }
 
@@ -216,7 +221,7 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
   std::vector<int> gtype(d->geom_type, d->geom_type + ngeom), gbody(d->geom_body, d->geom_body + ngeom);
   std::vector<float> gpos(d->geom_pos, d->geom_pos + 3 * ngeom), gquat(4 * ngeom), gsize(d->geom_size, d->geom_size + 3 * ngeom);
   for (int g = 0; g < ngeom; g++) {
-    if (gtype[g] < PG_GEOM_PLANE || gtype[g] > PG_GEOM_HFIELD) return set_error(PG_EINVAL, "bad geom type");
+    if (gtype[g] < PG_GEOM_PLANE || gtype[g] > PG_GEOM_CYLINDER) return set_error(PG_EINVAL, "bad geom type");
     if (gbody[g] < 0 || gbody[g] >= nbody) return set_error(PG_EINVAL, "geom_body out of range");
     if (gtype[g] == PG_GEOM_HFIELD) {
       if (gbody[g] != 0 || d->geom_mass[g] != 0.f) return set_error(PG_EINVAL, "a heightfield must be a massless geom of the world");
@@ -245,7 +250,7 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
     int a = d->pair_geom[2 * p], b = d->pair_geom[2 * p + 1];
     if (a < 0 || a >= ngeom || b < 0 || b >= ngeom) return set_error(PG_EINVAL, "pair geom out of range");
     int n = slots_for(gtype[a], gtype[b]);
-    if (n < 0) return set_error(PG_EUNSUPPORTED, "unsupported pair: type(geom1) must not exceed type(geom2) (plane<sphere<capsule<box), plane-plane unsupported; a heightfield pairs as geom1 with spheres and capsules");
+    if (n < 0) return set_error(PG_EUNSUPPORTED, "unsupported pair: type(geom1) must not exceed type(geom2) (plane<sphere<capsule<box), plane-plane unsupported; a heightfield pairs as geom1 with spheres and capsules; a cylinder pairs as geom2 with a plane");
     if (d->pair_condim[p] != 1 && d->pair_condim[p] != 3) return set_error(PG_EUNSUPPORTED, "pair_condim must be 1 or 3");
     pg1[p] = a; pg2[p] = b; pcondim[p] = d->pair_condim[p]; pfric[p] = d->pair_friction[p];
     pslotadr[p] = nslot; pnslot[p] = n;
@@ -465,7 +470,9 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
     bool ok = true;
     for (int p = 0; p < npair; p++) {
       const int g1 = d->pair_geom[2 * p], g2 = d->pair_geom[2 * p + 1];
-      if (d->geom_type[g1] != PG_GEOM_PLANE || d->geom_body[g1] != 0 || d->geom_type[g2] == PG_GEOM_PLANE) ok = false;
+      if (d->geom_type[g1] != PG_GEOM_PLANE || d->geom_body[g1] != 0 || d->geom_type[g2] == PG_GEOM_PLANE ||
+          d->geom_type[g2] == PG_GEOM_CYLINDER)
+        ok = false;
     }
     if (npair > 0 && !tree_hessian) ok = false;
     if (d->cone == PG_CONE_ELLIPTIC) ok = false;

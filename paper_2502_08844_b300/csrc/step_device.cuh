@@ -871,6 +871,28 @@ __device__ int collide(const Ctx& c, uint32_t& status, float* dbg) {
         k[0] = plane_sphere(x1, nz, x2 - a * s2[1], s2[0]);
         k[1] = plane_sphere(x1, nz, x2 + a * s2[1], s2[0]);
         k[1].feat = 1;
+      } else if (t2 == PG_GEOM_CYLINDER) {
+        // the deepest rim point of each cap (along e, the radius on which the rim falls fastest;
+        // the cylinder's x axis when its axis is within 1e-4 of the normal), then two more rim
+        // points of the lower cap 120 degrees either side of the first
+        const float3 a = mat_col(R2, 2);
+        const float s = dot3(nz, a);
+        const float3 perp = nz - a * s;
+        const float pl = sqrtf(dot3(perp, perp));
+        const float3 e = pl < 1e-4f ? mat_col(R2, 0) : perp * (-1.f / pl);
+        const float3 b = cross3(a, e);
+        const float3 off = a * (s >= 0.f ? -s2[1] : s2[1]);
+        const float3 clo = x2 + off, chi = x2 - off;
+        const float r = s2[0];
+        const float3 p[4] = {clo + e * r, chi + e * r, clo + (e * -0.5f + b * 0.8660254f) * r,
+                             clo + (e * -0.5f - b * 0.8660254f) * r};
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+          k[i].n = nz;
+          k[i].dist = dot3(nz, p[i] - x1);
+          k[i].pos = p[i] - nz * (0.5f * k[i].dist);
+          k[i].feat = i;
+        }
       } else {
         float dd[8];
         float3 cp[8];
@@ -1194,7 +1216,6 @@ __device__ float minv_diag(const Ctx& c, int d) {
 __device__ void row_params(const Ctx& c, int nc) {
   const ModelHdr& h = c.h;
   const int nv = h.nv, NC = h.ncol_max, MC = h.max_contacts;
-  const float* L = c.w + h.w_L * c.S;
   for (int k = 0; k < MC; k++) {
     const bool valid = k < nc;
     const int p = valid ? con_pair(c, k) : 0;

@@ -24,10 +24,10 @@ from . import workloads as W
 
 _PAIR_COST = {(W.PLANE, W.SPHERE): 25, (W.PLANE, W.CAPSULE): 55, (W.PLANE, W.BOX): 150, (W.SPHERE, W.SPHERE): 30,
               (W.SPHERE, W.CAPSULE): 45, (W.CAPSULE, W.CAPSULE): 70, (W.SPHERE, W.BOX): 60, (W.CAPSULE, W.BOX): 120,
-              (W.BOX, W.BOX): 600}
+              (W.BOX, W.BOX): 600, (W.PLANE, W.CYLINDER): 80}
 _PAIR_SLOTS = {(W.PLANE, W.SPHERE): 1, (W.PLANE, W.CAPSULE): 2, (W.PLANE, W.BOX): 4, (W.SPHERE, W.SPHERE): 1,
                (W.SPHERE, W.CAPSULE): 1, (W.CAPSULE, W.CAPSULE): 1, (W.SPHERE, W.BOX): 1, (W.CAPSULE, W.BOX): 2,
-               (W.BOX, W.BOX): 4}
+               (W.BOX, W.BOX): 4, (W.PLANE, W.CYLINDER): 4}
 
 
 @dataclasses.dataclass
