@@ -310,7 +310,9 @@ int pg_step_host(pg_batch* batch, pg_state* state, const float* ctrl_host, float
  * Scope. Every model of the batch needs adjoint_workspace_bytes > 0. That means:
  *   * any joints and actuators;
  *   * joint limits;
- *   * contacts only between a world-fixed plane (geom1) and spheres, capsules or boxes.
+ *   * contacts only between a world-fixed plane or heightfield (geom1) and spheres, capsules or
+ *     boxes.  On a heightfield's edges and vertices the contact normal turns with the state, and
+ *     the reverse sweep follows it.
  * A force clipped at its actuator's torque limit, and a friction-loss row's force at its bound,
  * are constant: nothing flows back through them.
  * Otherwise the call returns PG_EUNSUPPORTED.

@@ -30,6 +30,7 @@ cudaError_t launch_vjp_step(const pg_batch* b, const float* tape, int tape_rows,
   for (int k = 0; k < kMaxModels; k++) {
     A.env_end[k] = k < A.nmodels ? b->env_off[k] + b->counts[k] : b->n;
     A.model_off[k] = k < A.nmodels ? b->blob_off[k] : 0;
+    A.hfield[k] = b->hfield_ptr[k];
   }
   std::memcpy(A.blob, b->blob_host_adj.data(), b->blob_host_adj.size() * sizeof(uint32_t));
   // the widest shared-memory block every model's workspace fits in (0: global memory)

@@ -395,7 +395,11 @@ __device__ void substep_vjp(const Ctx& c, int nc, const unsigned act[4], float* 
     const int g1i = MI(pair_g1, p), g2i = MI(pair_g2, p);
     const int gb1 = MI(geom_body, g1i), gb2 = MI(geom_body, g2i);
     const float3 o1 = tree_origin(c, gb1), o2 = tree_origin(c, gb2);
+    // on a heightfield the contact frame turns with the state (at the terrain's edges and
+    // vertices): the adjoints of n, t1 and t2 through the Jacobian rows J_x[a] = x . P_a
+    const bool turns = MI(geom_type, g1i) == PG_GEOM_HFIELD;
     float3 posb = make_float3(0.f, 0.f, 0.f);
+    float3 nb = make_float3(0.f, 0.f, 0.f), t1b = nb, t2b = nb;
     for (int a = 0; a < ncol; a++) {
       const int d = MI(col_dof, ca + a), sg = MI(col_sign, ca + a);
       const float lam = B(a, d), acc = W(a, d), vel = W(qvel, d);
@@ -412,10 +416,16 @@ __device__ void substep_vjp(const Ctx& c, int nc, const unsigned act[4], float* 
       add3(c, h.b_cdof + 6 * d + 3, jb);
       add3(c, h.b_cdof + 6 * d, cross3(r, jb));
       posb = posb + cross3(jb, cw);
+      if (turns) {
+        const float3 P = (cdof_v(c, d) + cross3(cw, r)) * (float)sg;
+        nb = nb + P * jn;
+        t1b = t1b + P * j1;
+        t2b = t2b + P * j2;
+      }
     }
     // contact point and depth -> the feature point y on geom2's body (geom1 is a world plane):
     // dist = n.(y - p0) - r_s, pos = y - n (r_s + dist / 2)
-    const float3 yb = posb - n * (0.5f * dot3(n, posb)) + n * distb;
+    float3 yb = posb - n * (0.5f * dot3(n, posb)) + n * distb;
     float3 bx;
     Quat bq;
     body_frame(c, gb2, bx, bq);
@@ -430,6 +440,47 @@ __device__ void substep_vjp(const Ctx& c, int nc, const unsigned act[4], float* 
     if (t2y == PG_GEOM_CAPSULE) y = x2 + mat_col(R2, 2) * (feat ? s2[1] : -s2[1]);
     else if (t2y == PG_GEOM_BOX)
       y = x2 + mat_mul(R2, make_float3((feat & 1) ? s2[0] : -s2[0], (feat & 2) ? s2[1] : -s2[1], (feat & 4) ? s2[2] : -s2[2]));
+    if (turns) {
+      // the frame: t2 = n x t1, t1 = t / |t|, t = n x e_k (e_k fixed by n's smallest component)
+      nb = nb + cross3(t1, t2b);
+      t1b = t1b + cross3(t2b, n);
+      {
+        const float a0 = fabsf(n.x), a1 = fabsf(n.y), a2 = fabsf(n.z);
+        int kk = 0;
+        if (a1 < a0) kk = 1;
+        if (a2 < (kk == 0 ? a0 : a1)) kk = 2;
+        const float3 ek = make_float3(kk == 0 ? 1.f : 0.f, kk == 1 ? 1.f : 0.f, kk == 2 ? 1.f : 0.f);
+        const float3 t = cross3(n, ek);
+        const float3 tb = (t1b - t1 * dot3(t1, t1b)) * rsqrtf(dot3(t, t));
+        nb = nb + cross3(ek, tb);
+      }
+      // pos = y - n (r + dist / 2)
+      const float rs = s2[0];
+      nb = nb - posb * (rs + 0.5f * dist);
+      // n = (y - q) / |y - q| with q the closest terrain point: at a face (or below the terrain)
+      // n is the triangle's normal and constant; on an edge of direction u,
+      // dn/dy = (I - n n^T)(I - u u^T) / |y - q|; at a vertex, (I - n n^T) / |y - q|
+      float3 gx;
+      Quat gq;
+      body_frame(c, gb1, gx, gq);
+      const float3 x1 = gx + qrot(gq, T3(&MF(geom_pos, 3 * g1i)));
+      float R1[9];
+      qmat(qnormalize(qmul(gq, Quat{MF(geom_quat, 4 * g1i), MF(geom_quat, 4 * g1i + 1), MF(geom_quat, 4 * g1i + 2),
+                                    MF(geom_quat, 4 * g1i + 3)})), R1);
+      const float* s1 = &MF(geom_size, 3 * g1i);
+      const HGrid g{c.hf, h.hf_nrow, h.hf_ncol, s1[0], s1[1], s1[2], 2.f * s1[0] / (float)(h.hf_ncol - 1),
+                    2.f * s1[1] / (float)(h.hf_nrow - 1)};
+      HFeature f{0, make_float3(0.f, 0.f, 0.f)};
+      hfield_sphere<true>(g, x1, R1, y, rs, &f);
+      if (f.kind != 0) {
+        float3 v = nb - n * dot3(n, nb);
+        if (f.kind == 1) {
+          const float3 U = mat_mul(R1, f.u);
+          v = v - U * dot3(U, v);
+        }
+        yb = yb + v * (1.f / (dist + rs));
+      }
+    }
     add3(c, h.b_wr + 6 * gb2, cross3(y - o2, yb));
     add3(c, h.b_wr + 6 * gb2 + 3, yb);
   }
@@ -677,8 +728,10 @@ struct VjpArgs {
   int nmodels;
   int64_t env_end[kMaxModels];
   int model_off[kMaxModels];
-  uint32_t blob[kMaxParamWords];   // the models' adjoint blobs (adjoint header + tables)
+  const float* hfield[kMaxModels];   // each model's heightfield elevations (device), or NULL
+  uint32_t blob[kMaxParamWords];     // the models' adjoint blobs (adjoint header + tables)
 };
+static_assert(sizeof(VjpArgs) <= 32764, "the reverse sweep's argument block must fit the kernel parameter space");
 
 // SMEM: the workspace is in shared memory (blocks of A.soa environments, or of the specialised
 // model's constant width); otherwise in global memory at A.ws with stride ld.
@@ -689,6 +742,7 @@ __device__ __forceinline__ void vjp_body(const VjpArgs& A) {
   if (env >= A.n) return;
 #ifdef PG_SPEC
   const uint32_t* blob = SpecModel<SPEC_M>::blob_adj();   // the run-time compiled build: one model
+  const int m = 0;
 #else
   int m = 0;
   while (m < A.nmodels - 1 && env >= A.env_end[m]) m++;
@@ -702,7 +756,8 @@ __device__ __forceinline__ void vjp_body(const VjpArgs& A) {
   const int kSoa = SMEM ? A.soa : 0;
 #endif
   float* w = SMEM ? vjp_ws + threadIdx.x : A.ws + env;
-  Ctx c{h, SMEM ? kSoa : (int)ld, reinterpret_cast<const int*>(blob), reinterpret_cast<const float*>(blob), w, A.ctrl, ld, env};
+  Ctx c{h, SMEM ? kSoa : (int)ld, reinterpret_cast<const int*>(blob), reinterpret_cast<const float*>(blob), w, A.ctrl, ld, env,
+        A.hfield[m], nullptr};
   for (int k = 0; k < h.nq; k++) B(q, k) = A.adj_q[k * ld + env] + (A.gq ? A.gq[k * ld + env] : 0.f);
   for (int k = 0; k < h.nv; k++) B(v, k) = A.adj_v[k * ld + env] + (A.gv ? A.gv[k * ld + env] : 0.f);
   for (int k = 0; k < h.nu; k++) A.g_ctrl[k * ld + env] = 0.f;

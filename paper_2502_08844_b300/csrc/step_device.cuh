@@ -743,15 +743,28 @@ __device__ __forceinline__ int hg_cell(float u, float d, int n) {
   return min(max((int)floorf(u / d), 0), n - 2);
 }
 
+// the terrain feature a closest point lies on (reported for the adjoint): 0 a triangle's face
+// (the contact normal is that triangle's, constant in the state), 1 the inside of an edge of
+// unit direction u, 2 a vertex
+struct HFeature {
+  int kind;
+  float3 u;
+};
+
 // closest point to p on triangle v: its projection onto the plane when the barycentric weights
-// are all >= 0, else the nearest of the edges' clamped projections (first edge on ties)
-__device__ float3 closest_on_triangle(float3 p, const float3 v[3]) {
+// are all >= 0, else the nearest of the edges' clamped projections (first edge on ties); FEAT
+// also reports its feature in *f
+template <bool FEAT = false>
+__device__ float3 closest_on_triangle(float3 p, const float3 v[3], HFeature* f = nullptr) {
   const float3 n = cross3(v[1] - v[0], v[2] - v[0]);
   const float inn = 1.f / dot3(n, n);
   const float3 q = p - n * (dot3(n, p - v[0]) * inn);
   const float w0 = dot3(cross3(v[2] - v[1], q - v[1]), n) * inn;
   const float w1 = dot3(cross3(v[0] - v[2], q - v[2]), n) * inn;
-  if (w0 >= 0.f && w1 >= 0.f && w0 + w1 <= 1.f) return q;
+  if (w0 >= 0.f && w1 >= 0.f && w0 + w1 <= 1.f) {
+    if (FEAT) f->kind = 0;
+    return q;
+  }
   float3 best = v[0];
   float bd = 3.4e38f;
 #pragma unroll
@@ -761,7 +774,14 @@ __device__ float3 closest_on_triangle(float3 p, const float3 v[3]) {
     const float3 cp = a + ab * t;
     const float3 dd = p - cp;
     const float d2 = dot3(dd, dd);
-    if (d2 < bd) { bd = d2; best = cp; }
+    if (d2 < bd) {
+      bd = d2;
+      best = cp;
+      if (FEAT) {
+        f->kind = t > 0.f && t < 1.f ? 1 : 2;
+        f->u = ab * rsqrtf(dot3(ab, ab));
+      }
+    }
   }
   return best;
 }
@@ -773,10 +793,13 @@ __device__ float3 closest_on_triangle(float3 p, const float3 v[3]) {
 //   * otherwise the closest point q of the triangles in the cells meeting the square of
 //     half-width r around the centre (first in row, column, triangle order on ties):
 //     normal (c - q)/|c - q|, dist = |c - q| - r.
-// The point is midway between the sphere's deepest point and the surface.
-__device__ Con hfield_sphere(const HGrid& g, float3 x1, const float* R1, float3 cw, float r) {
+// The point is midway between the sphere's deepest point and the surface.  FEAT also reports
+// the terrain feature of the contact in *f (its edge direction in the grid frame).
+template <bool FEAT = false>
+__device__ Con hfield_sphere(const HGrid& g, float3 x1, const float* R1, float3 cw, float r, HFeature* f = nullptr) {
   Con out;
   out.feat = 0;
+  if (FEAT) f->kind = 0;
   const float3 c = mat_tmul(R1, cw - x1);
   if (!(c.x >= -g.hx && c.x <= g.hx && c.y >= -g.hy && c.y <= g.hy)) {
     out.dist = 1e30f;
@@ -805,10 +828,15 @@ __device__ Con hfield_sphere(const HGrid& g, float3 x1, const float* R1, float3 
       for (int b = j0; b <= j1; b++)
         for (int t = 0; t < 2; t++) {
           hg_triangle(g, a, b, t, tri);
-          const float3 p = closest_on_triangle(c, tri);
+          HFeature ft{0, make_float3(0.f, 0.f, 0.f)};
+          const float3 p = closest_on_triangle<FEAT>(c, tri, &ft);
           const float3 e = c - p;
           const float d2 = dot3(e, e);
-          if (d2 < best) { best = d2; q = p; }
+          if (d2 < best) {
+            best = d2;
+            q = p;
+            if (FEAT) *f = ft;
+          }
         }
     const float3 e = c - q;
     d = sqrtf(dot3(e, e));

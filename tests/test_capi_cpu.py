@@ -76,7 +76,8 @@ def test_null_arguments_are_errors():
 
 def test_adjoint_scope_and_parameter_rows():
     """pg_model_info reports the adjoint workspace only for models inside the adjoint's scope:
-    contacts between a world plane and spheres / capsules / boxes (quadruped, cartpole), not the
+    contacts between a world plane or heightfield and spheres / capsules / boxes (quadruped,
+    cartpole, the rough-terrain quadruped), not the
     hand (box-box, capsule-box) nor the humanoid (capsule-capsule self contact)."""
     from paper_2502_08844_b300 import core
     from tests import models_for_tests as MT
@@ -91,7 +92,7 @@ def test_adjoint_scope_and_parameter_rows():
     q.act_forcelimited = np.ones(q.nu, np.int32)
     q.act_forcerange = np.tile(np.array([[-4.0, 4.0]], np.float32), (q.nu, 1))
     assert core.CompiledModel(q).sizes.adjoint_workspace_bytes > 0       # torque limits: inside
-    assert core.CompiledModel(W.quadruped_rough()).sizes.adjoint_workspace_bytes == 0   # heightfield: outside
+    assert core.CompiledModel(W.quadruped_rough()).sizes.adjoint_workspace_bytes > 0    # heightfield: inside
 
 
 def test_cylinder_pairs_and_scope():

@@ -106,6 +106,52 @@ def test_torque_limited_rollout_gradient_matches_oracle():
     check_against_oracle(m, q0, v0, U, w)
 
 
+def test_rough_terrain_rollout_gradient_matches_oracle():
+    """The quadruped on gradient-noise terrain: its feet meet triangle faces, edges and vertices,
+    where the contact normal turns with the state; end to end over one segment against the
+    oracle's reverse mode."""
+    m = _converged(W.quadruped_rough())
+    n, T = 8, 8
+    q0, v0 = W.initial_state(m, 4, n)
+    U = W.actions(m, 4, n, 0, T)
+    w = O.tracking_loss_weights(O.OracleModel(m))
+    check_against_oracle(m, q0, v0, U, w)
+
+
+def _ball_on_terrain(elev):
+    b = W.ModelBuilder("ball_terrain")
+    g0 = b.geom(0, W.HFIELD, (0.2, 0.2, 0.1))
+    ball = b.body(0, (0, 0, 0.2))
+    b.joint(ball, W.FREE)
+    g1 = b.geom(ball, W.SPHERE, (0.05,), mass=1.0)
+    b.pair(g0, g1, friction=0.8, condim=3)
+    return b.build(timestep=0.002, iterations=100, n_substeps=4, hfield=elev)
+
+
+@pytest.mark.parametrize("feature", ["edge", "vertex"])
+def test_terrain_edge_and_vertex_contact_gradients(feature):
+    """A ball resting on a terrain ridge (its contact on a triangle edge) or on a peak (on a
+    vertex): the normal follows the ball's centre, dn/dy = (I - n n^T)(I - u u^T) / |y - q| on the
+    edge and (I - n n^T) / |y - q| at the vertex; against the oracle's reverse mode."""
+    elev = np.zeros((5, 5), np.float32)
+    if feature == "edge":
+        elev[2, :] = 1.0            # a ridge along y = 0, 0.1 m high, 45-degree flanks
+    else:
+        elev[2, 2] = 1.0            # a peak at the origin
+    m = _ball_on_terrain(elev)
+    n, T = 4, 8
+    q0 = np.zeros((n, 7))
+    q0[:, 0] = [-0.02, 0.0, 0.01, 0.015] if feature == "edge" else [0.003, -0.002, 0.0, 0.004]
+    q0[:, 1] = [0.0, 0.002, -0.004, 0.006] if feature == "edge" else [-0.002, 0.003, 0.001, 0.0]
+    q0[:, 2] = 0.1495
+    q0[:, 3] = 1.0
+    v0 = np.zeros((n, 6))
+    v0[:, 0] = [0.2, -0.1, 0.0, 0.3] if feature == "edge" else [0.0, 0.05, -0.05, 0.02]
+    U = np.zeros((T, n, 0))
+    w = O.tracking_loss_weights(O.OracleModel(m))
+    check_against_oracle(m, q0, v0, U, w, keys=("q0", "v0", "mass"))
+
+
 def test_friction_loss_rollout_gradient_matches_oracle():
     """The quadruped with joint friction loss on its hinges: rows inside their band act as soft
     rows, rows at their bound pass nothing back; end to end over one segment against the oracle's
