@@ -311,8 +311,9 @@ int pg_step_host(pg_batch* batch, pg_state* state, const float* ctrl_host, float
  *   * any joints and actuators;
  *   * joint limits;
  *   * contacts only between a world-fixed plane or heightfield (geom1) and spheres, capsules or
- *     boxes.  On a heightfield's edges and vertices the contact normal turns with the state, and
- *     the reverse sweep follows it.
+ *     boxes, and between a world-fixed plane and cylinders.  On a heightfield's edges and
+ *     vertices the contact normal turns with the state, and on a cylinder the rim points turn
+ *     with its axis; the reverse sweep follows both.
  * A force clipped at its actuator's torque limit, and a friction-loss row's force at its bound,
  * are constant: nothing flows back through them.
  * Otherwise the call returns PG_EUNSUPPORTED.

@@ -440,6 +440,28 @@ __device__ void substep_vjp(const Ctx& c, int nc, const unsigned act[4], float* 
     if (t2y == PG_GEOM_CAPSULE) y = x2 + mat_col(R2, 2) * (feat ? s2[1] : -s2[1]);
     else if (t2y == PG_GEOM_BOX)
       y = x2 + mat_mul(R2, make_float3((feat & 1) ? s2[0] : -s2[0], (feat & 2) ? s2[1] : -s2[1], (feat & 4) ? s2[2] : -s2[2]));
+    if (t2y == PG_GEOM_CYLINDER) {
+      // rim point y = cap centre + r E, E = c1 e + c2 (a x e) with e = -perp / |perp|,
+      // perp = n - (n.a) a: E turns with the axis a, so beyond the rigid motion of a body-fixed
+      // point y gains r (dE - dtheta x E); its adjoint is the couple r (a x abar - E x ybar)
+      const float3 a = mat_col(R2, 2);
+      const float s = dot3(n, a);
+      const float3 perp = n - a * s;
+      const float pl = sqrtf(dot3(perp, perp));
+      const bool fixed = pl < 1e-4f;   // e is the cylinder's own x axis: y is a body-fixed point
+      const float3 e = fixed ? mat_col(R2, 0) : perp * (-1.f / pl);
+      const float3 bv = cross3(a, e);
+      const float c1 = feat >= 2 ? -0.5f : 1.f, c2 = feat == 2 ? 0.8660254f : (feat == 3 ? -0.8660254f : 0.f);
+      const float3 E = e * c1 + bv * c2;
+      const float hs = (s >= 0.f ? -s2[1] : s2[1]) * (feat == 1 ? -1.f : 1.f);
+      y = x2 + a * hs + E * s2[0];
+      if (!fixed) {
+        const float3 eb = yb * c1 + cross3(yb, a) * c2;
+        const float3 perpb = (eb - e * dot3(e, eb)) * (-1.f / pl);
+        const float3 ab = cross3(e, yb) * c2 - n * dot3(perpb, a) - perpb * s;
+        add3(c, h.b_wr + 6 * gb2, (cross3(a, ab) - cross3(E, yb)) * s2[0]);
+      }
+    }
     if (turns) {
       // the frame: t2 = n x t1, t1 = t / |t|, t = n x e_k (e_k fixed by n's smallest component)
       nb = nb + cross3(t1, t2b);

@@ -466,13 +466,14 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
     }
     g.ws_adj_floats = std::max(top, 1);
     // scope of the hand-written adjoint: contacts only between a world-fixed plane or heightfield
-    // (geom1) and a sphere, capsule or box, which keeps the Newton Hessian on the mass matrix's
-    // pattern
+    // (geom1) and a sphere, capsule, box or (on a plane) cylinder, which keeps the Newton Hessian
+    // on the mass matrix's pattern
     bool ok = true;
     for (int p = 0; p < npair; p++) {
       const int g1 = d->pair_geom[2 * p], g2 = d->pair_geom[2 * p + 1];
       const bool ground = d->geom_type[g1] == PG_GEOM_PLANE || d->geom_type[g1] == PG_GEOM_HFIELD;
-      if (!ground || d->geom_body[g1] != 0 || d->geom_type[g2] == PG_GEOM_PLANE || d->geom_type[g2] == PG_GEOM_CYLINDER)
+      if (!ground || d->geom_body[g1] != 0 || d->geom_type[g2] == PG_GEOM_PLANE ||
+          (d->geom_type[g1] == PG_GEOM_HFIELD && d->geom_type[g2] == PG_GEOM_CYLINDER))
         ok = false;
     }
     if (npair > 0 && !tree_hessian) ok = false;

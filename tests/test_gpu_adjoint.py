@@ -152,6 +152,47 @@ def test_terrain_edge_and_vertex_contact_gradients(feature):
     check_against_oracle(m, q0, v0, U, w, keys=("q0", "v0", "mass"))
 
 
+def test_cylinder_rollout_gradients_match_oracle():
+    """Cylinders on a plane: one falling tilted and spinning (its deepest rim point slides round
+    the rim as it turns) and one rolling on its side, against the oracle's reverse mode."""
+    from tests.test_gpu_cylinder import _cylinder_scene, _initial_states
+    m = dataclasses.replace(_cylinder_scene(), iterations=100)
+    q0, v0 = _initial_states()
+    q0, v0 = q0[:2], v0[:2]
+    T = 8
+    U = np.zeros((T, 2, 0))
+    w = O.tracking_loss_weights(O.OracleModel(m))
+    check_against_oracle(m, q0, v0, U, w, keys=("q0", "v0", "mass"))
+
+
+def test_upright_cylinder_landing_gradient_matches_central_differences():
+    """A cylinder landing upright on its tripod (its rim points fixed to the body): the gradient
+    with respect to the initial velocity against FP64 central differences of the oracle's loss
+    (step 1e-6).  Here the oracle's taped reverse mode is not the reference: when a symmetric
+    contact set switches on inside a control step, differentiating its Newton iterations gives a
+    derivative that differs from central differences (and breaks the scene's mirror symmetry),
+    while the implicit derivative at the optimum agrees with them."""
+    from tests.test_gpu_cylinder import _cylinder_scene, _initial_states
+    m = dataclasses.replace(_cylinder_scene(), iterations=100)
+    q0, v0 = _initial_states()
+    q0, v0 = q0[2:], v0[2:]
+    T = 8
+    U = np.zeros((T, 1, 0))
+    om = O.OracleModel(m)
+    w = O.tracking_loss_weights(om)
+    g = gpu_rollout_grad(m, q0, v0, U, w)
+    fd = np.zeros(6)
+    for k in range(6):
+        vp, vm = v0[0].copy(), v0[0].copy()
+        vp[k] += 1e-6
+        vm[k] -= 1e-6
+        fd[k] = (O.rollout_loss(om, q0[0], vp, U[:, 0], m.n_substeps, w) -
+                 O.rollout_loss(om, q0[0], vm, U[:, 0], m.n_substeps, w)) / 2e-6
+    err = max(np.abs(g["v0"][0] - fd).max() - GRAD_ATOL, 0.0) / np.abs(fd).max()
+    assert err <= GRAD_RTOL, (g["v0"][0], fd)
+    assert abs(fd[4]) > 0.1          # the tilt the tripod's asymmetry sets up
+
+
 def test_friction_loss_rollout_gradient_matches_oracle():
     """The quadruped with joint friction loss on its hinges: rows inside their band act as soft
     rows, rows at their bound pass nothing back; end to end over one segment against the oracle's
