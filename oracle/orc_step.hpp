@@ -1286,10 +1286,18 @@ template <class T> void integrate_pos(const Model& m, T* qpos, const T* qvel, do
       for (int k = 0; k < 3; k++) q[k] = q[k] + T(h) * v[k];
       T wn = sqrt(v[3] * v[3] + v[4] * v[4] + v[5] * v[5]);
       std::array<T, 4> qq{q[3], q[4], q[5], q[6]};
-      if (val(wn) > 0) {
+      if (val(wn) > 1e-8) {
         using std::cos; using std::sin;
         T ang = T(h) * wn, s = sin(ang * T(0.5)) / wn;
         std::array<T, 4> dq{cos(ang * T(0.5)), v[3] * s, v[4] * s, v[5] * s};
+        qq = qmul(qq, dq);
+      } else {
+        // the same rotation by its series (cos(h|w|/2), (h/2) w (1 - O(h^2 |w|^2))): at w = 0 it is
+        // the identity, and its derivative (h/2 along w) survives in reverse mode, which the
+        // closed form through |w| cannot give there
+        const T hh = T(0.5 * h);
+        std::array<T, 4> dq{T(1) - T(0.5) * hh * hh * (v[3] * v[3] + v[4] * v[4] + v[5] * v[5]), v[3] * hh, v[4] * hh,
+                            v[5] * hh};
         qq = qmul(qq, dq);
       }
       T n = sqrt(qq[0] * qq[0] + qq[1] * qq[1] + qq[2] * qq[2] + qq[3] * qq[3]);

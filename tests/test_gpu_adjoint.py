@@ -154,24 +154,21 @@ def test_terrain_edge_and_vertex_contact_gradients(feature):
 
 def test_cylinder_rollout_gradients_match_oracle():
     """Cylinders on a plane: one falling tilted and spinning (its deepest rim point slides round
-    the rim as it turns) and one rolling on its side, against the oracle's reverse mode."""
+    the rim as it turns), one rolling on its side and one landing upright on its tripod (rim points
+    fixed to the body), against the oracle's reverse mode."""
     from tests.test_gpu_cylinder import _cylinder_scene, _initial_states
     m = dataclasses.replace(_cylinder_scene(), iterations=100)
     q0, v0 = _initial_states()
-    q0, v0 = q0[:2], v0[:2]
     T = 8
-    U = np.zeros((T, 2, 0))
+    U = np.zeros((T, 3, 0))
     w = O.tracking_loss_weights(O.OracleModel(m))
     check_against_oracle(m, q0, v0, U, w, keys=("q0", "v0", "mass"))
 
 
 def test_upright_cylinder_landing_gradient_matches_central_differences():
-    """A cylinder landing upright on its tripod (its rim points fixed to the body): the gradient
+    """A cylinder landing upright on its tripod, starting with zero angular velocity: the gradient
     with respect to the initial velocity against FP64 central differences of the oracle's loss
-    (step 1e-6).  Here the oracle's taped reverse mode is not the reference: when a symmetric
-    contact set switches on inside a control step, differentiating its Newton iterations gives a
-    derivative that differs from central differences (and breaks the scene's mirror symmetry),
-    while the implicit derivative at the optimum agrees with them."""
+    (step 1e-6).  Its tilt derivative comes from the orientation update's derivative at w = 0."""
     from tests.test_gpu_cylinder import _cylinder_scene, _initial_states
     m = dataclasses.replace(_cylinder_scene(), iterations=100)
     q0, v0 = _initial_states()

@@ -61,6 +61,29 @@ def test_gradient_matches_central_differences_parameters():
     _close(g["kp"][ki], _fd(lambda x: O.rollout_loss(om, q0, v0, U, 5, w, mass=mass, damping=damping, kp=x), kp, ki))
 
 
+def test_gradient_at_rest_matches_central_differences():
+    """A free body starting with zero angular velocity (a cylinder dropped upright onto a plane):
+    the orientation update's derivative with respect to w at w = 0 (h / 2) must survive in reverse
+    mode, else the tilt an angular-velocity perturbation causes is lost once contacts make the
+    orientation matter."""
+    b = W.ModelBuilder("upright")
+    g0 = b.geom(0, W.PLANE, (0, 0, 0))
+    body = b.body(0, (0, 0, 0.2))
+    b.joint(body, W.FREE)
+    g1 = b.geom(body, W.CYLINDER, (0.06, 0.1), mass=1.0)
+    b.pair(g0, g1, friction=0.8, condim=3)
+    m = b.build(timestep=0.002, iterations=100, n_substeps=4)
+    om = O.OracleModel(m)
+    w = O.tracking_loss_weights(om)
+    q0 = np.array([-0.2, 0.0, 0.104, 1.0, 0.0, 0.0, 0.0])
+    v0 = np.zeros(6)
+    U = np.zeros((8, 0))
+    g = O.rollout_grad(om, q0, v0, U, 4, w)
+    fd = _fd(lambda x: O.rollout_loss(om, q0, x, U, 4, w), v0, range(6))
+    _close(g["v0"], fd)
+    assert abs(fd[4]) > 0.1
+
+
 def test_step_vjp_chain_equals_rollout_gradient():
     """The per-control-step reverse sweep, chained along the trajectory with the loss cotangents,
     reproduces the rollout gradient (same tape, same order)."""
