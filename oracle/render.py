@@ -19,7 +19,7 @@ import numpy as np
 
 EPS_T = 1e-5
 LIFT = 1e-4
-PLANE, SPHERE, CAPSULE, BOX = 0, 1, 2, 3
+PLANE, SPHERE, CAPSULE, BOX, CYLINDER = 0, 1, 2, 3, 5
 
 
 def _unit(v):
@@ -94,6 +94,32 @@ def intersect(gtype, x, R, size, O, D):
             best = np.where(take, t, best)
             nl = np.where(take[:, None], ns, nl)
         return best, nl @ R.T
+    if gtype == CYLINDER:
+        r, h = size[0], size[1]
+        best = np.full(D.shape[0], np.inf)
+        nl = np.zeros_like(D)
+        a = ld[:, 0] ** 2 + ld[:, 1] ** 2
+        b = lo[:, 0] * ld[:, 0] + lo[:, 1] * ld[:, 1]
+        c = lo[:, 0] ** 2 + lo[:, 1] ** 2 - r * r
+        disc = b * b - a * c
+        good = (a > 1e-12) & (disc >= 0)
+        sq = np.sqrt(np.maximum(disc, 0))
+        for sgn in (-1.0, 1.0):            # the side, within the caps
+            with np.errstate(divide="ignore", invalid="ignore"):
+                t = (-b + sgn * sq) / a
+            z = lo[:, 2] + t * ld[:, 2]
+            take = good & (t > EPS_T) & (t < best) & (np.abs(z) <= h)
+            best = np.where(take, t, best)
+            p = lo + ld * t[:, None]
+            nl = np.where(take[:, None], np.stack([p[:, 0] / r, p[:, 1] / r, np.zeros_like(t)], -1), nl)
+        for zc in (-h, h):                 # the two cap discs
+            with np.errstate(divide="ignore", invalid="ignore"):
+                t = (zc - lo[:, 2]) / ld[:, 2]
+            p = lo + ld * np.where(np.isfinite(t), t, 0.0)[:, None]
+            take = (np.abs(ld[:, 2]) > 1e-12) & (t > EPS_T) & (t < best) & (p[:, 0] ** 2 + p[:, 1] ** 2 <= r * r)
+            best = np.where(take, t, best)
+            nl = np.where(take[:, None], np.array([0.0, 0.0, 1.0 if zc > 0 else -1.0]), nl)
+        return best, nl @ R.T
     # box: slabs in the box frame
     hs = np.asarray(size, np.float64)
     tn = np.full(D.shape[0], -np.inf); tf = np.full(D.shape[0], np.inf)
@@ -141,7 +167,7 @@ def render(om, scene, qpos):
     Rg, Xg = om.geom_frames(np.asarray(qpos, np.float64))
     m = om.src
     rgb = np.asarray(scene.geom_rgb, np.float64)
-    drawn = [g for g in range(m.ngeom) if rgb[g, 0] >= 0 and m.geom_type[g] in (PLANE, SPHERE, CAPSULE, BOX)]
+    drawn = [g for g in range(m.ngeom) if rgb[g, 0] >= 0 and m.geom_type[g] in (PLANE, SPHERE, CAPSULE, BOX, CYLINDER)]
     cam, D = camera_rays(scene)
     H_, W_ = D.shape[:2]
     D = D.reshape(-1, 3)

@@ -122,6 +122,43 @@ __device__ float ray_capsule(float3 o, float3 d, float3 x, const float* R, float
   return best;
 }
 
+// cylinder (frame x, R; radius r, half-length h along z): the side's roots within |z| <= h and the
+// two caps' discs, nearest first; the outward normal
+__device__ float ray_cylinder(float3 o, float3 d, float3 x, const float* R, float r, float h, float3& n) {
+  const float3 lo = mat_tmul(R, o - x), ld = mat_tmul(R, d);
+  float best = kMiss;
+  float3 nl = make_float3(0.f, 0.f, 1.f);
+  const float a = ld.x * ld.x + ld.y * ld.y;
+  if (a > 1e-12f) {
+    const float b = lo.x * ld.x + lo.y * ld.y, c = lo.x * lo.x + lo.y * lo.y - r * r;
+    const float disc = b * b - a * c;
+    if (disc >= 0.f) {
+      const float sq = sqrtf(disc);
+      for (int k = 0; k < 2; k++) {
+        const float t = (-b + (k ? sq : -sq)) / a;
+        const float z = lo.z + t * ld.z;
+        if (t > kRayEps && t < best && fabsf(z) <= h) {
+          best = t;
+          nl = make_float3((lo.x + t * ld.x) / r, (lo.y + t * ld.y) / r, 0.f);
+        }
+      }
+    }
+  }
+  if (fabsf(ld.z) > 1e-12f) {
+    for (int e = 0; e < 2; e++) {
+      const float zc = e ? h : -h;
+      const float t = (zc - lo.z) / ld.z;
+      const float px = lo.x + t * ld.x, py = lo.y + t * ld.y;
+      if (t > kRayEps && t < best && px * px + py * py <= r * r) {
+        best = t;
+        nl = make_float3(0.f, 0.f, e ? 1.f : -1.f);
+      }
+    }
+  }
+  if (best < kMiss) n = mat_mul(R, nl);
+  return best;
+}
+
 // box (frame x, R; half-sizes hs): slabs; the entering face's outward normal
 __device__ float ray_box(float3 o, float3 d, float3 x, const float* R, float3 hs, float3& n) {
   const float3 lo = mat_tmul(R, o - x), ld = mat_tmul(R, d);
@@ -156,7 +193,7 @@ __device__ float ray_box(float3 o, float3 d, float3 x, const float* R, float3 hs
 
 __device__ float ray_geom(const GeomFrame& g, float3 o, float3 d, float3& n) {
   const float3 x = ld3s(g.x);
-  if (g.type == PG_GEOM_CAPSULE || g.type == PG_GEOM_BOX) {
+  if (g.type == PG_GEOM_CAPSULE || g.type == PG_GEOM_BOX || g.type == PG_GEOM_CYLINDER) {
     if (misses_bound(o, d, x, g.bound2)) return kMiss;
   }
   switch (g.type) {
@@ -164,6 +201,7 @@ __device__ float ray_geom(const GeomFrame& g, float3 o, float3 d, float3& n) {
     case PG_GEOM_SPHERE: return ray_sphere(o, d, x, g.s[0], n);
     case PG_GEOM_CAPSULE: return ray_capsule(o, d, x, g.R, g.s[0], g.s[1], n);
     case PG_GEOM_BOX: return ray_box(o, d, x, g.R, ld3s(g.s), n);
+    case PG_GEOM_CYLINDER: return ray_cylinder(o, d, x, g.R, g.s[0], g.s[1], n);
     default: return kMiss;
   }
 }

@@ -86,6 +86,25 @@ def test_quadruped_pixels_match_oracle():
     assert drawn > 12 * 500
 
 
+def test_cylinder_pixels_match_oracle():
+    """Cylinders (side and cap discs) on a plane, in the poses of the contact tests: falling tilted,
+    rolling on the side, standing on a cap."""
+    from tests.test_gpu_cylinder import _cylinder_scene, _initial_states
+    m = _cylinder_scene()
+    om = O.OracleModel(m)
+    q0, v0 = _initial_states()
+    q0 = np.repeat(q0, 4, 0)
+    v0 = np.repeat(v0, 4, 0)
+    q0[:, 0] = np.tile([0.0, 0.02, -0.02, 0.04], 3)          # all in view
+    q0[:, 1] = 0.0
+    q, v, _, _ = om.rollout(q0, v0, np.zeros((30, 12, 0)), 4)
+    scene = W.Scene(cam_pos=(0.3, -0.3, 0.22), cam_lookat=(0.03, 0.0, 0.07), cam_up=(0.0, 0.0, 1.0), fovy_deg=50.0,
+                    width=48, height=40, light_dir=(-0.3, 0.4, -1.0), ambient=0.3, diffuse=0.7,
+                    background=(0.2, 0.3, 0.4), geom_rgb=np.array([[0.6, 0.6, 0.6], [0.9, 0.3, 0.1]], np.float32))
+    drawn = _check(m, scene, q.astype(np.float32), v.astype(np.float32), 12)
+    assert drawn > 12 * 1500
+
+
 def test_hidden_geoms_and_argument_errors():
     from paper_2502_08844_b300 import _capi
     m = W.cartpole_pixels()

@@ -103,18 +103,22 @@ def _march(inside, O_, d, tmax=10.0, step=2e-5):
     return ts[k] if inside(pts[k:k + 1])[0] else np.inf
 
 
-@pytest.mark.parametrize("gtype", [W.BOX, W.CAPSULE])
-def test_box_and_capsule_hits_match_ray_marching(gtype):
+@pytest.mark.parametrize("gtype", [W.BOX, W.CAPSULE, W.CYLINDER])
+def test_box_capsule_and_cylinder_hits_match_ray_marching(gtype):
     rng = np.random.default_rng(7 + gtype)
     q = np.array([0.9, 0.2, -0.3, 0.25]); q /= np.linalg.norm(q)
     x = np.array([2.0, 0.1, -0.2])
-    size = (0.3, 0.2, 0.15) if gtype == W.BOX else (0.15, 0.35)
+    size = (0.3, 0.2, 0.15) if gtype == W.BOX else ((0.15, 0.35) if gtype == W.CAPSULE else (0.2, 0.25))
     m = _one_geom_model(gtype, size, pos=x, quat=q)
     om = O.OracleModel(m)
     Rg, Xg = om.geom_frames(np.zeros(0))
     R, X = Rg[0], Xg[0]
     if gtype == W.BOX:
         inside = lambda P: np.all(np.abs((P - X) @ R) <= np.array(size), axis=1)
+    elif gtype == W.CYLINDER:
+        def inside(P):
+            L = (P - X) @ R
+            return (np.hypot(L[:, 0], L[:, 1]) <= size[0]) & (np.abs(L[:, 2]) <= size[1])
     else:
         def inside(P):
             L = (P - X) @ R
