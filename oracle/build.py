@@ -12,7 +12,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SOURCES = ["orc_model.cpp", "orc_capi.cpp"]
-HEADERS = ["orc_math.hpp", "orc_model.hpp", "orc_step.hpp", "orc_ad.hpp"]
+HEADERS = ["orc_math.hpp", "orc_model.hpp", "orc_step.hpp", "orc_ad.hpp", "orc_count.hpp"]
 LIB = os.path.join(HERE, "liborc.so")
 
 

@@ -60,6 +60,7 @@ def lib():
         L.orc_forward.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp, C.c_int, _dp]
         L.orc_inverse_dynamics.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp]
         L.orc_mass_matrix.argtypes = [C.c_void_p, _dp, _dp]
+        L.orc_mass_matrix_crba.argtypes = [C.c_void_p, _dp, _dp]
         L.orc_body_frames.argtypes = [C.c_void_p, _dp, _dp]
         L.orc_geom_frames.argtypes = [C.c_void_p, _dp, _dp]
         L.orc_energy.argtypes = [C.c_void_p, _dp, _dp, _dp]
@@ -224,6 +225,13 @@ class OracleModel:
     def mass_matrix(self, qpos):
         M = np.zeros((self.nv, self.nv))
         lib().orc_mass_matrix(self.h, _pd(_d(qpos)), _pd(M))
+        return M
+
+    def mass_matrix_crba(self, qpos):
+        """The mass matrix by CRBA (the method the flop count takes), against mass_matrix's
+        kinetic-energy definition."""
+        M = np.zeros((self.nv, self.nv))
+        lib().orc_mass_matrix_crba(self.h, _pd(_d(qpos)), _pd(M))
         return M
 
     def body_frames(self, qpos):
@@ -391,3 +399,39 @@ def rollout_grad(om: "OracleModel", q0, v0, ctrl, n_substeps, weights, solver_ca
                        _pd(out["u"]), _pd(out["mass"]), _pd(out["damping"]), _pd(out["kp"]), C.byref(loss))
     out["loss"] = loss.value
     return out
+
+
+COUNT_PHASES = ("kinematics", "mass_matrix", "bias", "smooth", "collision", "rows", "solve", "integrate", "force_output")
+COUNT_KINDS = ("add", "mul", "div", "sqrt", "trans")
+
+
+def count_selftest(which: int, n: int) -> float:
+    """Counted flops of a textbook kernel on the counting scalar (see orc_count_selftest)."""
+    L = lib()
+    L.orc_count_selftest.argtypes = [C.c_int, C.c_int, _dp]
+    out = np.zeros(1)
+    if L.orc_count_selftest(int(which), int(n), _pd(out)) != 0:
+        raise ValueError("orc_count_selftest failed")
+    return float(out[0])
+
+
+def count_substeps(om: "OracleModel", qpos, qvel, qacc_warm, ctrl, n_substeps: int, solver_cap: Optional[int] = None):
+    """The oracle on its counting scalar (orc_count.hpp) over n_substeps substeps of one
+    environment: (counts [S, phase, kind], rows [S], iters [S], final qpos, qvel, warm).  kind:
+    add, mul, div, sqrt, transcendental; the factorisations counted are the leaves-first L^T D L."""
+    L = lib()
+    if not getattr(L, "_count_ready", False):
+        L.orc_count_substeps.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp, C.c_int, C.c_int, _dp,
+                                         C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L._count_ready = True
+    q, v, w = _d(qpos).copy(), _d(qvel).copy(), _d(qacc_warm).copy()
+    u = _d(ctrl).reshape(-1).copy() if om.nu else np.zeros(1)
+    S = int(n_substeps)
+    counts = np.zeros((S, len(COUNT_PHASES), len(COUNT_KINDS)))
+    rows = np.zeros(S, np.int32)
+    iters = np.zeros(S, np.int32)
+    cap = om.src.iterations if solver_cap is None else solver_cap
+    r = L.orc_count_substeps(om.h, _pd(q), _pd(v), _pd(w), _pd(u), S, int(cap), _pd(counts), _pi(rows), _pi(iters))
+    if r != 0:
+        raise ValueError("orc_count_substeps failed")
+    return counts, rows, iters, q, v, w

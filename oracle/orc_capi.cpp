@@ -12,6 +12,7 @@
 #include "orc_ad.hpp"
 #include "orc_model.hpp"
 #include "orc_step.hpp"
+#include "orc_count.hpp"
 
 using orc::Model;
 
@@ -163,6 +164,17 @@ int orc_mass_matrix(void* h, const double* qpos, double* M) {
 }
 
 // per body: R (9, row-major), x (3), com (3)
+// the mass matrix by CRBA (the counted method), row-major nv x nv
+int orc_mass_matrix_crba(void* h, const double* qpos, double* M) {
+  const Model& m = *static_cast<Model*>(h);
+  orc::Kin<double> k;
+  orc::kinematics(m, qpos, k);
+  std::vector<double> Mv;
+  orc::crba_mass_matrix(m, k, Mv);
+  std::memcpy(M, Mv.data(), sizeof(double) * m.nv * m.nv);
+  return 0;
+}
+
 int orc_body_frames(void* h, const double* qpos, double* out) {
   const Model& m = *static_cast<Model*>(h);
   orc::Kin<double> k;
@@ -460,5 +472,79 @@ double orc_impedance(double r, const double* solimp) { return orc::impedance(r, 
 void orc_solid_inertia(int type, const double* size, double m, double* out) { orc::solid_inertia(type, size, m, out); }
 
 double orc_rotor_armature(double kg, double mr, double rr) { return orc::rotor_armature(kg, mr, rr); }
+
+// Counting-scalar checks on textbook kernels of size n (all entries variable unless stated):
+//   0 dense matrix-vector product y = A x                      (expect 2 n^2 - n)
+//   1 the same with A a constant zero matrix                    (expect 0)
+//   2 dense Cholesky factor and solve of an SPD matrix          (see the test for the formula)
+//   3 leaves-first L^T D L factor and solve of an arrowhead (tree) matrix: dense diagonal,
+//     first row/column, constant zeros elsewhere                 (no fill: 3 (n - 1) + ... )
+// Returns the counted flops (all kinds summed) in *out.
+int orc_count_selftest(int which, int n, double* out) {
+  using orc::cdouble;
+  if (n < 1) return -1;
+  orc::Counts& C = orc::counts();
+  C.clear();
+  std::vector<cdouble> A((size_t)n * n), x(n), y(n);
+  for (int i = 0; i < n; i++) {
+    x[i] = cdouble::var(1.0 + 0.1 * i);
+    for (int j = 0; j < n; j++) {
+      const double v = (i == j ? n + 1.0 : 1.0 / (1.0 + i + j));
+      if (which == 1) A[i * n + j] = cdouble(0.0);
+      else if (which == 3 && i != j && i != 0 && j != 0) A[i * n + j] = cdouble(0.0);
+      else A[i * n + j] = cdouble::var(v);
+    }
+  }
+  if (which == 0 || which == 1) {
+    for (int i = 0; i < n; i++) {
+      cdouble s(0.0);
+      for (int j = 0; j < n; j++) s = s + A[i * n + j] * x[j];
+      y[i] = s;
+    }
+  } else if (which == 2) {
+    if (!orc::cholesky(A, n)) return -2;
+    orc::chol_solve(A, n, x);
+  } else if (which == 3) {
+    if (!orc::ldlt_leaves_first(A, n)) return -2;
+    orc::ldlt_solve(A, n, x);
+  } else {
+    return -1;
+  }
+  double t = 0;
+  for (int k = 0; k < orc::PH_N; k++) t += C.add[k] + C.mul[k] + C.div[k] + C.sqrt[k] + C.trans[k];
+  *out = t;
+  return 0;
+}
+
+// Counted flops of n_substeps substeps of one environment from (qpos, qvel, qacc_warm) with the
+// controls ctrl held: the oracle on the counting scalar (orc_count.hpp).  Per substep s:
+// counts[(s * 9 + phase) * 5 + {add, mul, div, sqrt, transcendental}] (phase 8: the contact-force
+// output, not part of the step), rows[s] (constraint rows
+// assembled) and iters[s] (Newton iterations).  The state is advanced in place.
+int orc_count_substeps(void* h, double* qpos, double* qvel, double* qacc_warm, const double* ctrl, int n_substeps,
+                       int solver_cap, double* counts, int* rows, int* iters) {
+  const Model& m = *static_cast<Model*>(h);
+  if (n_substeps < 1) return -1;
+  using orc::cdouble;
+  std::vector<cdouble> q(m.nq), v(m.nv), w(m.nv), u(std::max(m.nu, 1));
+  for (int i = 0; i < m.nq; i++) q[i] = cdouble::var(qpos[i]);
+  for (int i = 0; i < m.nv; i++) { v[i] = cdouble::var(qvel[i]); w[i] = cdouble::var(qacc_warm[i]); }
+  for (int i = 0; i < m.nu; i++) u[i] = cdouble::var(ctrl[i]);
+  orc::Counts& C = orc::counts();
+  for (int s = 0; s < n_substeps; s++) {
+    C.clear();
+    orc::Forward<cdouble> F;
+    orc::substep(m, q.data(), v.data(), w.data(), u.data(), solver_cap, &F);
+    for (int k = 0; k < orc::PH_N; k++) {
+      double* o = counts + ((size_t)s * orc::PH_N + k) * 5;
+      o[0] = C.add[k]; o[1] = C.mul[k]; o[2] = C.div[k]; o[3] = C.sqrt[k]; o[4] = C.trans[k];
+    }
+    rows[s] = F.rows.n;
+    iters[s] = F.sol.iterations;
+  }
+  for (int i = 0; i < m.nq; i++) qpos[i] = q[i].v;
+  for (int i = 0; i < m.nv; i++) { qvel[i] = v[i].v; qacc_warm[i] = w[i].v; }
+  return 0;
+}
 
 }  // extern "C"

@@ -119,4 +119,48 @@ template <class T> void chol_solve(const Vec<T>& L, int n, Vec<T>& b) {
   }
 }
 
+// L^T D L factorisation of a symmetric positive definite matrix, eliminating from the last index
+// (A = L^T D L, L unit lower triangular).  For a matrix whose pattern is a tree's ancestor
+// pattern with parents before children (a mass matrix in level order) it makes no fill-in.
+// The oracle solves with the Cholesky factor; the flop count (orc_count.hpp) takes this one,
+// the tree-sparse factorisation of the method.  In place: A_kk = D_k, A_ki = L_ki (i < k);
+// returns false if a pivot is not positive.
+template <class T> bool ldlt_leaves_first(Vec<T>& A, int n) {
+  for (int k = n - 1; k >= 0; k--) {
+    if (!(val(A[k * n + k]) > 0.0)) return false;
+    for (int i = k - 1; i >= 0; i--) {
+      T l = A[k * n + i] / A[k * n + k];
+      for (int j = 0; j <= i; j++) A[i * n + j] = A[i * n + j] - l * A[k * n + j];
+      A[k * n + i] = l;
+    }
+  }
+  return true;
+}
+
+// solve (L^T D L) x = b in place with the factor of ldlt_leaves_first
+template <class T> void ldlt_solve(const Vec<T>& A, int n, Vec<T>& b) {
+  for (int k = n - 1; k >= 0; k--)
+    for (int i = 0; i < k; i++) b[i] = b[i] - A[k * n + i] * b[k];
+  for (int k = 0; k < n; k++) b[k] = b[k] / A[k * n + k];
+  for (int k = 0; k < n; k++)
+    for (int i = 0; i < k; i++) b[k] = b[k] - A[k * n + i] * b[i];
+}
+
+// The methods the oracle uses: its plain ones (the mass matrix from the kinetic energy, Cholesky
+// solves), except for a counting scalar (orc_count.hpp), which takes the tree methods whose flops
+// the step's count is of: CRBA and the leaves-first L^T D L (each pinned against the plain one).
+template <class T> struct TreeMethods { static constexpr bool value = false; };
+template <class T> bool spd_factor(Vec<T>& A, int n) {
+  return TreeMethods<T>::value ? ldlt_leaves_first(A, n) : cholesky(A, n);
+}
+template <class T> void spd_solve(const Vec<T>& A, int n, Vec<T>& b) {
+  if (TreeMethods<T>::value) ldlt_solve(A, n, b);
+  else chol_solve(A, n, b);
+}
+
+// Phases of the substep for a counting scalar's tally (orc_count.hpp); nothing for the others.
+template <class T> struct PhaseHook {
+  static void set(int) {}
+};
+
 }  // namespace orc

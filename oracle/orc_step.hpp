@@ -161,6 +161,74 @@ template <class T> void mass_matrix(const Model& m, const Kin<T>& k, std::vector
   for (int i = 0; i < nv; i++) M[i * nv + i] = M[i * nv + i] + T(m.dof_armature[i]);
 }
 
+// The same matrix by the composite-rigid-body algorithm (CRBA).  Spatial vectors about the world
+// origin: a dof's motion subspace s = (w, v) moves a body point P with velocity v + w x P (hinge
+// with axis a through the anchor p: (a, p x a); slide: (0, a); free translation k: (0, e_k); free
+// rotation k about the body origin x: (R e_k, x x R e_k)); a body's spatial inertia about the
+// origin is (I_O = Iw + m (|c|^2 1 - c c^T), h = m c, m) with c its centre of mass.  Composite
+// inertias Ic(b) = own + the children's composites; for dof j on body b the force Ic(b) s_j =
+// (I_O w + h x v, m v - h x w), and M_ij = s_i . (Ic(b) s_j) for every dof i on j's chain.
+template <class T> void crba_mass_matrix(const Model& m, const Kin<T>& k, std::vector<T>& M, const Params<T>* P = nullptr) {
+  const int nv = m.nv;
+  M.assign(nv * nv, T(0));
+  std::vector<std::array<T, 6>> S(nv);
+  std::vector<int> dof_body(nv, 0);
+  for (int b = 1; b < m.nbody; b++)
+    for (int j = m.body_jntadr[b]; j < m.body_jntadr[b] + m.body_jntnum[b]; j++) {
+      const int d = m.jnt_dofadr[j];
+      if (m.jnt_type[j] == FREE) {
+        const Xf<T>& X = k.xbody[b];
+        for (int c = 0; c < 3; c++) {
+          S[d + c] = {T(0), T(0), T(0), T(c == 0 ? 1 : 0), T(c == 1 ? 1 : 0), T(c == 2 ? 1 : 0)};
+          const V3<T> e = col(X.R, c), v = cross(X.p, e);
+          S[d + 3 + c] = {e[0], e[1], e[2], v[0], v[1], v[2]};
+          dof_body[d + c] = dof_body[d + 3 + c] = b;
+        }
+      } else if (m.jnt_type[j] == HINGE) {
+        const V3<T> a = k.jaxis[j], v = cross(k.janchor[j], a);
+        S[d] = {a[0], a[1], a[2], v[0], v[1], v[2]};
+        dof_body[d] = b;
+      } else {
+        const V3<T> a = k.jaxis[j];
+        S[d] = {T(0), T(0), T(0), a[0], a[1], a[2]};
+        dof_body[d] = b;
+      }
+    }
+  // spatial inertias about the origin: I_O (Ixx Iyy Izz Ixy Ixz Iyz), h, m
+  std::vector<std::array<T, 10>> Ic(m.nbody);
+  for (int b = 1; b < m.nbody; b++) {
+    const T mb = body_mass(m, P, b);
+    const V3<T>& c = k.xcom[b];
+    const M3<T>& I = k.Iw[b];
+    const T c2 = dot(c, c);
+    Ic[b] = {I[0] + mb * (c2 - c[0] * c[0]), I[4] + mb * (c2 - c[1] * c[1]), I[8] + mb * (c2 - c[2] * c[2]),
+             I[1] - mb * c[0] * c[1], I[2] - mb * c[0] * c[2], I[5] - mb * c[1] * c[2],
+             mb * c[0], mb * c[1], mb * c[2], mb};
+  }
+  for (int b = m.nbody - 1; b >= 1; b--)
+    if (m.parent[b] > 0)
+      for (int q = 0; q < 10; q++) Ic[m.parent[b]][q] = Ic[m.parent[b]][q] + Ic[b][q];
+  for (int j = 0; j < nv; j++) {
+    const std::array<T, 10>& I = Ic[dof_body[j]];
+    const V3<T> w{S[j][0], S[j][1], S[j][2]}, v{S[j][3], S[j][4], S[j][5]}, h{I[6], I[7], I[8]};
+    const V3<T> fa = add(V3<T>{I[0] * w[0] + I[3] * w[1] + I[4] * w[2], I[3] * w[0] + I[1] * w[1] + I[5] * w[2],
+                               I[4] * w[0] + I[5] * w[1] + I[2] * w[2]},
+                         cross(h, v));
+    const V3<T> fl = sub(scl(v, I[9]), cross(h, w));
+    // dof j's chain: the earlier dofs of its body, then every dof of its ancestors
+    for (int b = dof_body[j]; b > 0; b = m.parent[b])
+      for (int jj = m.body_jntadr[b]; jj < m.body_jntadr[b] + m.body_jntnum[b]; jj++)
+        for (int i = m.jnt_dofadr[jj]; i < m.jnt_dofadr[jj] + (m.jnt_type[jj] == FREE ? 6 : 1); i++) {
+          if (b == dof_body[j] && i > j) continue;
+          const T Mij = S[i][0] * fa[0] + S[i][1] * fa[1] + S[i][2] * fa[2] + S[i][3] * fl[0] + S[i][4] * fl[1] +
+                        S[i][5] * fl[2];
+          M[j * nv + i] = Mij;
+          M[i * nv + j] = Mij;
+        }
+  }
+  for (int i = 0; i < nv; i++) M[i * nv + i] = M[i * nv + i] + T(m.dof_armature[i]);
+}
+
 // Per-body angular velocity w and acceleration al, and a reference point r fixed in the body
 // with its velocity vr and acceleration ar, propagated from the world along each joint:
 //   hinge (axis a through p): move the reference to p (rigid-body formulas), then
@@ -808,10 +876,12 @@ template <class T> T impedance(const T& r, const double* solimp) {
 template <class T> T cost(int nv, const std::vector<T>& M, const std::vector<T>& a0, const Rows<T>& R,
                           const std::vector<T>& a) {
   T f = T(0);
+  std::vector<T> t(nv);
+  for (int j = 0; j < nv; j++) t[j] = a[j] - a0[j];
   for (int i = 0; i < nv; i++) {
     T s = T(0);
-    for (int j = 0; j < nv; j++) s = s + M[i * nv + j] * (a[j] - a0[j]);
-    f = f + T(0.5) * (a[i] - a0[i]) * s;
+    for (int j = 0; j < nv; j++) s = s + M[i * nv + j] * t[j];
+    f = f + T(0.5) * t[i] * s;
   }
   for (int i = 0; i < R.n; i++) {
     if (R.kind[i] == 2) continue;
@@ -1019,13 +1089,16 @@ template <class T> SolveResult<T> newton_solve(int nv, const std::vector<T>& M, 
     }
     return s;
   };
-  T f_cur = cost(nv, M, a0, R, a);
+  T f_cur = elliptic ? cost(nv, M, a0, R, a) : T(0);   // (the stopping rule of elliptic contacts)
   for (int it = 0; it < cap; it++) {
     std::vector<char> A = active_set(a);
-    std::vector<T> g(nv), H(M);
+    // g and the lower triangle of H (the factorisations read only that triangle; it is mirrored
+    // before them)
+    std::vector<T> g(nv), H(M), t(nv);
+    for (int j = 0; j < nv; j++) t[j] = a[j] - a0[j];
     for (int i = 0; i < nv; i++) {
       T s = T(0);
-      for (int j = 0; j < nv; j++) s = s + M[i * nv + j] * (a[j] - a0[j]);
+      for (int j = 0; j < nv; j++) s = s + M[i * nv + j] * t[j];
       g[i] = s;
     }
     for (int r = 0; r < R.n; r++) {
@@ -1045,25 +1118,29 @@ template <class T> SolveResult<T> newton_solve(int nv, const std::vector<T>& M, 
         for (int i = 0; i < nv; i++)
           for (int e = 0; e < 3; e++) {
             g[i] = g[i] + R.J[(r + e) * nv + i] * gc[e];
-            for (int j = 0; j < nv; j++)
+            for (int j = 0; j <= i; j++)
               for (int f = 0; f < 3; f++) H[i * nv + j] = H[i * nv + j] + R.J[(r + e) * nv + i] * Hc[3 * e + f] * R.J[(r + f) * nv + j];
           }
         continue;
       }
       T jar = -R.aref[r];
       for (int j = 0; j < nv; j++) jar = jar + R.J[r * nv + j] * a[j];
+      const T Djar = R.D[r] * jar;
       for (int i = 0; i < nv; i++) {
-        g[i] = g[i] + R.D[r] * jar * R.J[r * nv + i];
-        for (int j = 0; j < nv; j++) H[i * nv + j] = H[i * nv + j] + R.D[r] * R.J[r * nv + i] * R.J[r * nv + j];
+        g[i] = g[i] + Djar * R.J[r * nv + i];
+        const T DJ = R.D[r] * R.J[r * nv + i];
+        for (int j = 0; j <= i; j++) H[i * nv + j] = H[i * nv + j] + DJ * R.J[r * nv + j];
       }
     }
+    for (int i = 0; i < nv; i++)
+      for (int j = i + 1; j < nv; j++) H[i * nv + j] = H[j * nv + i];
     out.iterations = it + 1;
     bool zero = true;
     for (int i = 0; i < nv; i++) zero = zero && val(g[i]) == 0;
     if (zero) { out.converged = true; break; }
-    if (!cholesky(H, nv)) break;
+    if (!spd_factor(H, nv)) break;
     std::vector<T> p(g);
-    chol_solve(H, nv, p);
+    spd_solve(H, nv, p);
     for (int i = 0; i < nv; i++) p[i] = -p[i];
     T alpha = elliptic ? smooth_line_search(nv, M, a0, R, a, p) : exact_line_search(nv, M, a0, R, a, p);
     for (int i = 0; i < nv; i++) a[i] = a[i] + alpha * p[i];
@@ -1081,6 +1158,7 @@ template <class T> SolveResult<T> newton_solve(int nv, const std::vector<T>& M, 
     f_cur = f_new;
   }
   out.qacc = a;
+  PhaseHook<T>::set(8);   // the contact forces: an output, not part of the step's work
   out.force.assign(R.n, T(0));
   for (int i = 0; i < R.n; i++) {
     if (R.kind[i] == 2) continue;
@@ -1225,7 +1303,7 @@ template <class T> void build_rows(const Model& m, const Forward<T>& F, const T*
       continue;
     }
     std::vector<T> x(R.J.begin() + i * nv, R.J.begin() + (i + 1) * nv);
-    chol_solve(Mchol, nv, x);
+    spd_solve(Mchol, nv, x);
     T A = T(0);
     for (int j = 0; j < nv; j++) A = A + R.J[i * nv + j] * x[j];
     T d = impedance(R.r[i], m.solimp);
@@ -1240,18 +1318,24 @@ template <class T> void build_rows(const Model& m, const Forward<T>& F, const T*
 template <class T> void forward(const Model& m, const T* qpos, const T* qvel, const T* qacc_warm, const T* ctrl,
                                 int solver_cap, Forward<T>& F, const Params<T>* P = nullptr) {
   const int nv = m.nv;
+  PhaseHook<T>::set(0);   // kinematics
   kinematics(m, qpos, F.kin, P);
-  mass_matrix(m, F.kin, F.M, P);
+  PhaseHook<T>::set(1);   // mass matrix
+  if (TreeMethods<T>::value) crba_mass_matrix(m, F.kin, F.M, P);
+  else mass_matrix(m, F.kin, F.M, P);
+  PhaseHook<T>::set(2);   // bias forces
   std::vector<T> zero(nv, T(0));
   inverse_dynamics(m, F.kin, qvel, zero.data(), F.bias, P);
+  PhaseHook<T>::set(3);   // passive and actuator forces, the smooth acceleration
   F.passive.assign(nv, T(0));
   for (int i = 0; i < nv; i++) F.passive[i] = -(P ? P->damping[i] : T(m.dof_damping[i])) * qvel[i];
   actuation(m, qpos, qvel, ctrl, F.actuator, P);
   std::vector<T> Mchol(F.M);
-  if (!cholesky(Mchol, nv)) F.status |= ST_NAN;
+  if (!spd_factor(Mchol, nv)) F.status |= ST_NAN;
   F.a0.assign(nv, T(0));
   for (int i = 0; i < nv; i++) F.a0[i] = F.actuator[i] + F.passive[i] - F.bias[i];
-  chol_solve(Mchol, nv, F.a0);
+  spd_solve(Mchol, nv, F.a0);
+  PhaseHook<T>::set(4);   // collision
   // collision over the static pair list; then the active-contact cap in slot order
   F.con.assign(m.nslot, Contact<T>());
   for (int p = 0; p < m.npair; p++) {
@@ -1267,7 +1351,9 @@ template <class T> void forward(const Model& m, const T* qpos, const T* qvel, co
       else nact++;
     }
   }
+  PhaseHook<T>::set(5);   // constraint rows
   build_rows(m, F, qpos, qvel, F.rows, Mchol);
+  PhaseHook<T>::set(6);   // the Newton solve
   bool warm_ok = true;
   for (int i = 0; i < nv; i++) warm_ok = warm_ok && std::isfinite(val(qacc_warm[i]));
   if (!warm_ok) F.status |= ST_WARM_RESET;
@@ -1314,6 +1400,7 @@ template <class T> uint32_t substep(const Model& m, T* qpos, T* qvel, T* qacc_wa
   Forward<T>& F = keep ? *keep : local;
   F = Forward<T>();
   forward(m, qpos, qvel, qacc_warm, ctrl, solver_cap, F, P);
+  PhaseHook<T>::set(7);   // integration
   const int nv = m.nv;
   for (int i = 0; i < nv; i++) qvel[i] = qvel[i] + T(m.timestep) * F.sol.qacc[i];
   integrate_pos(m, qpos, qvel, m.timestep);

@@ -1,33 +1,31 @@
-"""Algorithmic FP32 flop count of the physics step (for the ALU roofline).
+"""Algorithmic FP32 flop count of the physics step (the numerator of the ALU roofline).
 
-Counts what the method needs on the tree-sparse pattern, independent of how the kernel
-schedules it: add = mul = 1, fma = 2, div = sqrt = rsqrt = 1, a sin/cos pair = 2.  Per
-substep the count is
+The count is the FP64 oracle's own, taken on its counting scalar: every floating-point operation
+on a value that depends on the state, the controls or the solver counts one flop (add, sub, mul,
+div, sqrt, a transcendental; a fused multiply-add two), operations a model-specialised program
+folds count nothing (on constants only, products with a constant 0 or +-1, sums with a constant
+0), and the methods counted are the tree methods of the step: CRBA for M and the leaves-first
+L^T D L for every factorisation (no fill on a tree pattern).  The solver's contact-force output
+is not part of the step.
 
-    A + B * nrow + C * iters + E * nrow * iters
+Per substep the count is fitted, per model, as
 
-with nrow the constraint rows assembled and iters the Newton iterations of that substep
-(the kernel's optional solver counters give their sums).  A covers kinematics, CRBA, the
-LDL^T factor, RNEA, the smooth solve, collision and integration; B the per-row Jacobian,
-Ahat and reference acceleration; C the per-iteration dense work on nv (Cholesky, solves,
-M products); E the per-iteration per-row work (residual, gradient, Hessian update,
-line search, active-set check).  Dense Cholesky of H is counted at nv^3/3 because H is
-dense in general; everything on M uses the ancestor pattern only.
+    A + B * rows + C * iters + E * rows * iters
+
+with rows the constraint rows assembled and iters the Newton iterations of the substep; the step
+kernels' optional solver counters give their sums over a launch, so a launch's count is
+A * substeps + B * sum(rows) + C * sum(iters) + E * sum(rows * iters).  The fitted coefficients
+are stored in flop_counts.json beside this file; the oracle's own script (oracle/count_flops.py)
+writes them and a CPU test refits and checks them.
 """
 from __future__ import annotations
 
 import dataclasses
+import json
+import os
 
-import numpy as np
-
-from . import workloads as W
-
-_PAIR_COST = {(W.PLANE, W.SPHERE): 25, (W.PLANE, W.CAPSULE): 55, (W.PLANE, W.BOX): 150, (W.SPHERE, W.SPHERE): 30,
-              (W.SPHERE, W.CAPSULE): 45, (W.CAPSULE, W.CAPSULE): 70, (W.SPHERE, W.BOX): 60, (W.CAPSULE, W.BOX): 120,
-              (W.BOX, W.BOX): 600, (W.PLANE, W.CYLINDER): 80}
-_PAIR_SLOTS = {(W.PLANE, W.SPHERE): 1, (W.PLANE, W.CAPSULE): 2, (W.PLANE, W.BOX): 4, (W.SPHERE, W.SPHERE): 1,
-               (W.SPHERE, W.CAPSULE): 1, (W.CAPSULE, W.CAPSULE): 1, (W.SPHERE, W.BOX): 1, (W.CAPSULE, W.BOX): 2,
-               (W.BOX, W.BOX): 4, (W.PLANE, W.CYLINDER): 4}
+HERE = os.path.dirname(os.path.abspath(__file__))
+COUNTS = os.path.join(HERE, "flop_counts.json")
 
 
 @dataclasses.dataclass
@@ -41,67 +39,18 @@ class FlopModel:
         return self.A * n_substeps + self.B * sum_rows + self.C * sum_iters + self.E * sum_rows_iters
 
 
-def _dof_tree(m: W.Model):
-    nv = m.nv
-    dof_body = np.zeros(nv, int)
-    parent = -np.ones(nv, int)
-    last = {0: -1}
-    adr = m.jnt_dofadr()
-    for b in range(1, m.nbody):
-        prev = last[int(m.body_parent[b])]
-        for j in np.where(m.jnt_body == b)[0]:
-            for k in range(6 if m.jnt_type[j] == W.FREE else 1):
-                d = adr[j] + k
-                dof_body[d] = b
-                parent[d] = prev
-                prev = d
-        last[b] = prev
-    depth = np.zeros(nv, int)
-    for d in range(nv):
-        depth[d] = 0 if parent[d] < 0 else depth[parent[d]] + 1
-    chain = {0: set()}
-    for b in range(1, m.nbody):
-        chain[b] = set(chain[int(m.body_parent[b])]) | set(np.where(dof_body == b)[0].tolist())
-    return depth, chain
+def stored_counts() -> dict:
+    with open(COUNTS) as f:
+        return json.load(f)["models"]
 
 
-def flop_model(m: W.Model) -> FlopModel:
-    nv, nq = m.nv, m.nq
-    nb = m.nbody - 1
-    depth, chain = _dof_tree(m)
-    nnzM = int(np.sum(depth + 1))
-    jt = list(m.jnt_type)
-    n_hinge, n_slide, n_free = jt.count(W.HINGE), jt.count(W.SLIDE), jt.count(W.FREE)
-    # kinematics and derived quantities
-    fk = 98 * nb + 129 * n_hinge + 69 * n_slide + 12 * n_free
-    derived = 116 * nb + 98 * m.ngeom + 12 * nv
-    n_children = sum(1 for b in range(1, m.nbody) if m.body_parent[b] > 0)
-    crba = 10 * n_children + 45 * nv + 11 * nnzM
-    ldl = int(sum(d + d * (d + 1) for d in depth))
-    rnea = 48 * nv + 135 * nb + 11 * nv
-    smooth = 2 * nv + 5 * m.nu + 2 * nv + 4 * int(np.sum(depth)) + nv
-    coll = 0
-    slots = 0
-    for p in range(m.npair):
-        key = (int(m.geom_type[m.pair_geom[p, 0]]), int(m.geom_type[m.pair_geom[p, 1]]))
-        coll += _PAIR_COST[key]
-        slots += _PAIR_SLOTS[key]
-    coll += 25 * slots
-    integ = 2 * nv + sum(1 for t in jt if t != W.FREE) * 2 + n_free * 46
-    warm_cost = 2 * (4 * nnzM + 2 * nv)
-    A = fk + derived + crba + ldl + rnea + smooth + coll + integ + warm_cost
-    # per row: Jacobian share (38 per chain dof per contact, 4 rows), velocity, Ahat, aref, D
-    if m.npair:
-        nnz = np.mean([len(chain[int(m.geom_body[m.pair_geom[p, 0]])] | chain[int(m.geom_body[m.pair_geom[p, 1]])])
-                       for p in range(m.npair)])
-        chain_depth = np.mean([np.sum(depth[list(chain[int(m.geom_body[m.pair_geom[p, 1]])])])
-                               for p in range(m.npair)])
-    else:
-        nnz, chain_depth = 1.0, 0.0
-    B = 38 * nnz / 4 + 2 * nnz + (2 * chain_depth + 2 * nnz + nv) + 15 + 4 + 3 + 2 * (2 * nnz + 4)
-    C = (4 * nnzM + nv) + (nv ** 3 / 3 + nv ** 2 / 2 + nv) + 2 * nv * nv + 4 * nnzM + 4 * nv + 2 * nv
-    E = (2 * nnz + 1) + (2 * nnz + 1) + nnz * (nnz + 1) + 2 * nnz + 8 + (2 * nnz + 1)
-    return FlopModel(float(A), float(B), float(C), float(E))
+def flop_model(m) -> FlopModel:
+    """The counted per-substep flop model of a workload model (by its name)."""
+    c = stored_counts()
+    if m.name not in c:
+        raise KeyError("no counted flops stored for model %r (oracle/count_flops.py --write)" % m.name)
+    e = c[m.name]
+    return FlopModel(e["A"], e["B"], e["C"], e["E"])
 
 
 def fp32_peak_tflops(sm_count: int, sm_mhz: float) -> float:
