@@ -205,18 +205,22 @@ void pg_model_free(pg_model* model);
 
 /* Batch of environments: counts[k] consecutive envs of models[k], in that order.  The
  * models must outlive the batch.  envs_per_cta (>= 1, or 0 for the default) sets how many
- * environments (one warp each) share a thread block. */
+ * environments share a thread block of the thread-per-environment kernels (one thread each;
+ * the default is one wave: about n / SMs per block).  Allocates the batch's device tables and
+ * nothing else; the scratch of pg_step_vjp is allocated by its first call (see there). */
 int pg_batch_compile(const pg_model* const* models, const int64_t* counts, int nmodels, int envs_per_cta,
                      pg_batch** out);
 int pg_batch_info(const pg_batch* batch, int64_t* n_envs, int* nq_max, int* nv_max, int* nu_max);
 void pg_batch_free(pg_batch* batch);
 
-/* Compile, at run time, a step kernel specialised to the batch's model and use it for every
- * following pg_step / pg_step_host of this batch.
+/* Compile, at run time, step kernels specialised to the batch's model and use them for every
+ * following pg_step / pg_step_host of this batch. Same as pg_batch_specialize_ex(batch,
+ * PG_SPEC_BRANCH).
  *
  * What changes. The specialised kernel takes the model's header, tables and workspace stride as
  * constants, which the generic kernel reads at run time. The arithmetic is the same source in
- * the same order, so results are identical.
+ * the same order; the compiler may regroup an FMA where a constant folds, so results agree with
+ * the generic kernel's to rounding (not bit for bit).
  *
  * How. The kernel is compiled with NVRTC (libnvrtc.so.13, loaded on first use) for sm_103a and
  * cached per process and on disk ($PG_KERNEL_CACHE, else ~/.cache/paper_2502_08844_b300/kernels).
@@ -233,6 +237,40 @@ void pg_batch_free(pg_batch* batch);
  * Errors. PG_EUNSUPPORTED (NVRTC missing or failing, with its log in pg_last_error; the batch
  * then keeps the generic kernel), PG_ECUDA. */
 int pg_batch_specialize(pg_batch* batch);
+
+/* pg_batch_specialize with options. flags:
+ *   PG_SPEC_BRANCH  for a single-model batch whose model qualifies, pg_step and pg_step_host run
+ *                   the branch-parallel kernel: one thread per (environment, branch), where the
+ *                   branches are the chains of hinge/slide bodies hanging from the model's trunk
+ *                   (a quadruped's legs, a humanoid's legs and arms) and the trunk's work is shared
+ *                   through warp shuffles. It computes the same step (Sec. 3, "Environment": the
+ *                   physics step of MJX) with the mass matrix and the Newton Hessian factorised as
+ *                   block arrowheads (branches first, the trunk's Schur complement last), so results
+ *                   agree with the other kernels to FP32 rounding. A model qualifies when it has
+ *                   2 to 8 branches, each contact pair touches at most one branch, at most one
+ *                   actuator drives each dof, the cone is pyramidal, it has no heightfield and no
+ *                   joint friction loss, and its candidate contact points fit max_contacts;
+ *                   pg_batch_kernel reports why one does not. pg_step_dr, pg_env_step, the tape and
+ *                   the adjoint keep the thread-per-environment kernels.
+ *   0               the thread-per-environment specialised kernels only.
+ * Errors as pg_batch_specialize; flags other than these: PG_EINVAL. */
+#define PG_SPEC_BRANCH 1u
+int pg_batch_specialize_ex(pg_batch* batch, unsigned flags);
+
+/* Which kernel pg_step runs for the batch. */
+enum { PG_KERNEL_GENERIC = 0, PG_KERNEL_SPECIALISED = 1, PG_KERNEL_SPECIALISED_PARTS = 2, PG_KERNEL_BRANCH = 3 };
+typedef struct {
+  int kernel;          /* PG_KERNEL_*                                                              */
+  int lanes_per_env;   /* threads per environment (1, or the branch kernel's lane group)           */
+  int branches;        /* branches of the model (branch kernel), else 0                            */
+  char reason[160];    /* why the branch kernel is not used (empty when it is or was not asked)    */
+} pg_kernel_info;
+int pg_batch_kernel(const pg_batch* batch, pg_kernel_info* out);
+/* Whether a model qualifies for the branch-parallel kernel (host only, no device work): out->kernel
+ * is PG_KERNEL_BRANCH with its lane group and branch count, else PG_KERNEL_SPECIALISED with the
+ * reason.  With the environment variable PG_BRANCH_SOURCE set to a path, the kernel source
+ * generated for the model is written there (a developer aid). */
+int pg_model_branch_plan(const pg_model* model, pg_kernel_info* out);
 
 /* Reset the envs whose env_mask_dev[e] != 0 (all envs when env_mask_dev is NULL): copy
  * qpos0/qvel0 ([coord][ld], same layout as the state), zero qacc_warm and status. */

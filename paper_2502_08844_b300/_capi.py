@@ -69,6 +69,14 @@ class pg_task_sizes(C.Structure):
 
 PG_PIXELS_U8, PG_PIXELS_F32 = 0, 1
 
+PG_SPEC_BRANCH = 1
+PG_KERNEL_GENERIC, PG_KERNEL_SPECIALISED, PG_KERNEL_SPECIALISED_PARTS, PG_KERNEL_BRANCH = 0, 1, 2, 3
+KERNEL_NAMES = {0: "generic", 1: "specialised", 2: "specialised per model", 3: "branch-parallel"}
+
+
+class pg_kernel_info(C.Structure):
+    _fields_ = [("kernel", C.c_int), ("lanes_per_env", C.c_int), ("branches", C.c_int), ("reason", C.c_char * 160)]
+
 
 class pg_render_desc(C.Structure):
     _fields_ = [("cam_pos", C.c_float * 3), ("cam_lookat", C.c_float * 3), ("cam_up", C.c_float * 3),
@@ -80,7 +88,8 @@ class pg_render_desc(C.Structure):
 
 EXPORTS = ["pg_model_compile", "pg_model_info", "pg_model_free", "pg_batch_compile", "pg_batch_info",
            "pg_batch_free", "pg_reset", "pg_step", "pg_step_dr", "pg_debug_substep", "pg_step_host", "pg_step_vjp",
-           "pg_step_vjp_noalloc", "pg_batch_specialize", "pg_task_compile", "pg_task_info", "pg_task_free",
+           "pg_step_vjp_noalloc", "pg_batch_specialize", "pg_batch_specialize_ex", "pg_batch_kernel",
+           "pg_model_branch_plan", "pg_task_compile", "pg_task_info", "pg_task_free",
            "pg_env_reset", "pg_env_step", "pg_render", "pg_last_error"]
 
 if not os.path.exists(LIB_PATH):
@@ -106,6 +115,9 @@ _lib.pg_debug_substep.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C
 _lib.pg_step_host.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
 _lib.pg_step_vjp.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_int, C.c_int] + [C.c_void_p] * 7
 _lib.pg_batch_specialize.argtypes = [C.c_void_p]
+_lib.pg_batch_specialize_ex.argtypes = [C.c_void_p, C.c_uint]
+_lib.pg_batch_kernel.argtypes = [C.c_void_p, C.POINTER(pg_kernel_info)]
+_lib.pg_model_branch_plan.argtypes = [C.c_void_p, C.POINTER(pg_kernel_info)]
 _lib.pg_step_vjp_noalloc.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_int, C.c_int] + [C.c_void_p] * 7
 _lib.pg_task_compile.argtypes = [C.c_void_p, C.POINTER(pg_task_desc), C.POINTER(C.c_void_p)]
 _lib.pg_task_info.argtypes = [C.c_void_p, C.POINTER(pg_task_sizes)]
@@ -207,6 +219,22 @@ def pg_step_vjp_noalloc(batch, ckpt: pg_state, ctrl_ptr, n_steps: int, n_substep
 
 def pg_batch_specialize(batch) -> None:
     _check(_lib.pg_batch_specialize(batch), "pg_batch_specialize")
+
+
+def pg_batch_specialize_ex(batch, flags: int) -> None:
+    _check(_lib.pg_batch_specialize_ex(batch, flags), "pg_batch_specialize_ex")
+
+
+def pg_batch_kernel(batch) -> pg_kernel_info:
+    out = pg_kernel_info()
+    _check(_lib.pg_batch_kernel(batch, C.byref(out)), "pg_batch_kernel")
+    return out
+
+
+def pg_model_branch_plan(model) -> pg_kernel_info:
+    out = pg_kernel_info()
+    _check(_lib.pg_model_branch_plan(model, C.byref(out)), "pg_model_branch_plan")
+    return out
 
 
 def pg_task_compile(model, desc: pg_task_desc) -> C.c_void_p:

@@ -25,7 +25,8 @@ EMBEDDED = [("pg.h", os.path.join(INCLUDE, "pg.h")), ("pg_internal.h", os.path.j
             ("step_device.cuh", os.path.join(CSRC, "step_device.cuh")),
             ("env_device.cuh", os.path.join(CSRC, "env_device.cuh")),
             ("step_kernel_body.cuh", os.path.join(CSRC, "step_kernel_body.cuh")),
-            ("adjoint_body.cuh", os.path.join(CSRC, "adjoint_body.cuh"))]
+            ("adjoint_body.cuh", os.path.join(CSRC, "adjoint_body.cuh")),
+            ("branch_body.cuh", os.path.join(CSRC, "branch_body.cuh"))]
 BUILD_DIR = os.path.join(HERE, "_build")
 EMBED_CPP = os.path.join(BUILD_DIR, "pg_embedded.cpp")
 
@@ -57,24 +58,63 @@ def needs_build() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
-    return any(os.path.getmtime(f) > t for f in deps)
+    return any(os.path.getmtime(f) > t for f in sources() + _headers())
 
 
-def nvcc_cmd(out: str, verbose: bool = False):
-    cmd = ["nvcc", *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
-           "-o", out, *sources(), EMBED_CPP, "-lcudart", "-ldl"]
+# headers that only the run-time compiler sees (embedded, included by no source compiled here)
+RTC_ONLY = {"branch_body.cuh"}
+
+
+def _headers(compiled_only: bool = False):
+    hs = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+    return [h for h in hs if not (compiled_only and os.path.basename(h) in RTC_ONLY)]
+
+
+def _object(src: str) -> str:
+    return os.path.join(BUILD_DIR, os.path.basename(src) + ".o")
+
+
+def compile_cmd(src: str, out: str, verbose: bool = False):
+    cmd = ["nvcc", *ARCH, "-O3", "-lineinfo", "-std=c++17", "-c", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
+           "-o", out, src]
     if verbose:
         cmd[1:1] = ["-Xptxas", "-v"]
     return cmd
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    if force or needs_build():
-        tmp = LIB + ".%d.tmp" % os.getpid()
-        write_embedded()
-        subprocess.run(nvcc_cmd(tmp, verbose), check=True)
-        os.replace(tmp, LIB)
+    """Compile every source to an object under _build/ (in parallel, each only when it or a
+    header is newer than its object), then link libpg.so."""
+    if not (force or needs_build()):
+        return LIB
+    from concurrent.futures import ThreadPoolExecutor
+    write_embedded()
+    newest_header = max(os.path.getmtime(f) for f in _headers(compiled_only=True))
+    srcs = sources() + [EMBED_CPP]
+    todo = []
+    for src in srcs:
+        obj = _object(src)
+        if force or src == EMBED_CPP or not os.path.exists(obj) or \
+                os.path.getmtime(obj) < max(os.path.getmtime(src), newest_header):
+            todo.append(src)
+
+    def run(src):
+        tmp = _object(src) + ".%d.tmp" % os.getpid()
+        r = subprocess.run(compile_cmd(src, tmp, verbose), capture_output=True, text=True)
+        if r.returncode == 0:
+            os.replace(tmp, _object(src))
+        return src, r
+
+    with ThreadPoolExecutor(max_workers=max(1, min(len(todo), os.cpu_count() or 1))) as ex:
+        results = list(ex.map(run, todo))
+    for src, r in results:
+        if verbose or r.returncode:
+            sys.stderr.write(r.stdout + r.stderr)
+        if r.returncode:
+            raise subprocess.CalledProcessError(r.returncode, r.args)
+    tmp = LIB + ".%d.tmp" % os.getpid()
+    subprocess.run(["nvcc", *ARCH, "-shared", "-o", tmp, *[_object(s) for s in srcs], "-lcudart", "-ldl"], check=True)
+    os.replace(tmp, LIB)
     return LIB
 
 

@@ -69,6 +69,12 @@ class CompiledModel:
             _capi.pg_model_free(h)
             self.handle = None
 
+    def branch_plan(self) -> dict:
+        """pg_model_branch_plan: whether the model qualifies for the branch-parallel kernel."""
+        k = _capi.pg_model_branch_plan(self.handle)
+        return {"branch": k.kernel == _capi.PG_KERNEL_BRANCH, "lanes_per_env": k.lanes_per_env,
+                "branches": k.branches, "reason": k.reason.decode()}
+
     @property
     def nq(self):
         return self.sizes.nq
@@ -95,10 +101,18 @@ class Batch:
         self.nparam_max = max(m.sizes.nparam for m in self.models)
         self.specialized = False
 
-    def specialize(self) -> None:
-        """pg_batch_specialize: compile (NVRTC, cached) a step kernel specialised to the model."""
-        _capi.pg_batch_specialize(self.handle)
+    def specialize(self, branch: bool = True) -> None:
+        """pg_batch_specialize_ex: compile (NVRTC, cached) step kernels specialised to the model;
+        branch: let pg_step run the branch-parallel kernel when the model qualifies."""
+        _capi.pg_batch_specialize_ex(self.handle, _capi.PG_SPEC_BRANCH if branch else 0)
         self.specialized = True
+
+    def kernel(self) -> dict:
+        """pg_batch_kernel: the kernel pg_step runs (name, lanes per environment, branches, and why
+        the branch-parallel kernel is not used)."""
+        k = _capi.pg_batch_kernel(self.handle)
+        return {"kernel": _capi.KERNEL_NAMES[k.kernel], "lanes_per_env": k.lanes_per_env, "branches": k.branches,
+                "reason": k.reason.decode()}
 
     def __del__(self):
         h = getattr(self, "handle", None)

@@ -78,6 +78,7 @@ void pg_batch_free(pg_batch* b) {
   if (b->d_ctrl_stage) cudaFree(b->d_ctrl_stage);
   if (b->d_vjp) cudaFree(b->d_vjp);
   if (b->spec_lib) cudaLibraryUnload(b->spec_lib);
+  if (b->branch_lib) cudaLibraryUnload(b->branch_lib);
   for (const pg_batch::SpecPart& part : b->spec_parts) cudaLibraryUnload(part.lib);
   delete b;
 }

@@ -60,6 +60,11 @@ struct pg_batch {
     size_t smem;
   };
   std::vector<SpecPart> spec_parts;
+  // the branch-parallel step kernel (pg_batch_specialize_ex with PG_SPEC_BRANCH), else NULL
+  cudaLibrary_t branch_lib = nullptr;
+  cudaKernel_t branch_kernel = nullptr;
+  int branch_lanes = 0, branch_count = 0;
+  std::string branch_why;   // why a requested branch kernel is not used
   // staging buffer of the host-buffer path (allocated on its first use)
   float* d_ctrl_stage = nullptr;
   size_t ctrl_stage_floats = 0;
@@ -86,6 +91,10 @@ void once_per_device(std::mutex& mu, unsigned long long& done, F&& f) {
   done |= bit;
 }
 int compile_model(const pg_model_desc* d, pg_model* out);
+// branch.cpp: the branch-parallel kernel's plan and generated source for a model
+int branch_plan(const pg_model* m, std::string& src, std::string& why, int& lanes_per_env, int& threads,
+                int& branches);
+cudaError_t launch_branch(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st);
 
 // kernel launchers (step.cu)
 cudaError_t launch_step(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st,

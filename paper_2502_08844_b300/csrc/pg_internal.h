@@ -106,6 +106,19 @@ struct EnvArgs {
   EnvTask task;
 };
 
+// The branch-parallel step kernel's arguments (a single-model batch; see branch_body.cuh):
+// batch state and controls in the [coord][ld] layout of pg_state, n environments.
+struct BranchArgs {
+  float* qpos;
+  float* qvel;
+  float* warm;
+  uint32_t* status;
+  uint32_t* stats;       // optional solver counters [3][ld], or NULL
+  const float* ctrl;
+  int64_t ld, n;
+  int n_substeps;
+};
+
 // one thread block's work: `count` consecutive envs starting at `env0` of model `model`
 struct Tile {
   int model;

@@ -174,10 +174,10 @@ std::string spec_source(const pg_model* m) {
   return s;
 }
 
-int compile_cubin(const pg_model* m, std::vector<char>& cubin) {
+// compile (or find in the caches) the cubin of a generated source
+int compile_source(const std::string& src, const char* name, std::vector<char>& cubin) {
   const Nvrtc& n = nvrtc();
   if (!n.ok) return set_error(PG_EUNSUPPORTED, "pg_batch_specialize: " + n.why);
-  const std::string src = spec_source(m);
   std::string key_src = src + "|nvrtc " + std::to_string(n.major) + "." + std::to_string(n.minor) + "|sm_103a";
   for (int i = 0; i < kEmbeddedCount; i++) key_src += kEmbeddedTexts[i];
   const uint64_t key = fnv1a(key_src);
@@ -186,12 +186,12 @@ int compile_cubin(const pg_model* m, std::vector<char>& cubin) {
     auto it = g_cubins.find(key);
     if (it != g_cubins.end()) { cubin = it->second; return PG_OK; }
   }
-  char name[32];
-  snprintf(name, sizeof(name), "%016llx.cubin", (unsigned long long)key);
-  const std::string dir = cache_dir(), path = dir + "/" + name;
+  char fname[32];
+  snprintf(fname, sizeof(fname), "%016llx.cubin", (unsigned long long)key);
+  const std::string dir = cache_dir(), path = dir + "/" + fname;
   if (!read_file(path, cubin)) {
     void* prog = nullptr;
-    if (n.create(&prog, src.c_str(), "pg_step_spec.cu", kEmbeddedCount, kEmbeddedTexts, kEmbeddedNames) != 0)
+    if (n.create(&prog, src.c_str(), name, kEmbeddedCount, kEmbeddedTexts, kEmbeddedNames) != 0)
       return set_error(PG_EUNSUPPORTED, "pg_batch_specialize: nvrtcCreateProgram failed");
     const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo"};
     const int rc = n.compile(prog, 3, opts);
@@ -213,6 +213,39 @@ int compile_cubin(const pg_model* m, std::vector<char>& cubin) {
   }
   std::lock_guard<std::mutex> lock(g_mutex);
   g_cubins[key] = cubin;
+  return PG_OK;
+}
+
+int compile_cubin(const pg_model* m, std::vector<char>& cubin) {
+  return compile_source(spec_source(m), "pg_step_spec.cu", cubin);
+}
+
+// the branch-parallel kernel of a single-model batch, when its model qualifies (else the reason
+// goes to b->branch_why and the batch keeps its other kernels)
+int specialize_branch(pg_batch* b) {
+  std::string src, why;
+  int lanes = 0, threads = 0, branches = 0;
+  if (branch_plan(b->models[0], src, why, lanes, threads, branches) != PG_OK) {
+    b->branch_why = why;
+    return PG_OK;
+  }
+  std::vector<char> cubin;
+  int rc = compile_source(src, "pg_step_branch.cu", cubin);
+  if (rc != PG_OK) return rc;
+  cudaLibrary_t lib = nullptr;
+  cudaError_t e = cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+  if (e != cudaSuccess) return set_error(PG_ECUDA, std::string("cudaLibraryLoadData: ") + cudaGetErrorString(e));
+  cudaKernel_t k = nullptr;
+  e = cudaLibraryGetKernel(&k, lib, "pg_step_branch");
+  if (e != cudaSuccess) {
+    cudaLibraryUnload(lib);
+    return set_error(PG_ECUDA, std::string("branch kernel set-up: ") + cudaGetErrorString(e));
+  }
+  b->branch_lib = lib;
+  b->branch_kernel = k;
+  b->branch_lanes = lanes;
+  b->branch_count = branches;
+  b->branch_why.clear();
   return PG_OK;
 }
 
@@ -265,9 +298,54 @@ static int specialize_parts(pg_batch* b) {
   return PG_OK;
 }
 
-extern "C" int pg_batch_specialize(pg_batch* b) {
+extern "C" int pg_batch_specialize(pg_batch* b) { return pg_batch_specialize_ex(b, PG_SPEC_BRANCH); }
+
+extern "C" int pg_batch_kernel(const pg_batch* b, pg_kernel_info* out) {
+  if (!b || !out) return set_error(PG_EINVAL, "batch or out is NULL");
+  std::memset(out, 0, sizeof(*out));
+  out->lanes_per_env = 1;
+  if (b->branch_kernel) {
+    out->kernel = PG_KERNEL_BRANCH;
+    out->lanes_per_env = b->branch_lanes;
+    out->branches = b->branch_count;
+  } else if (b->spec_kernel) {
+    out->kernel = PG_KERNEL_SPECIALISED;
+  } else if (!b->spec_parts.empty()) {
+    out->kernel = PG_KERNEL_SPECIALISED_PARTS;
+  }
+  snprintf(out->reason, sizeof(out->reason), "%s", b->branch_why.c_str());
+  return PG_OK;
+}
+
+extern "C" int pg_model_branch_plan(const pg_model* m, pg_kernel_info* out) {
+  if (!m || !out) return set_error(PG_EINVAL, "model or out is NULL");
+  std::memset(out, 0, sizeof(*out));
+  std::string src, why;
+  int lanes = 0, threads = 0, branches = 0;
+  if (branch_plan(m, src, why, lanes, threads, branches) != PG_OK) {
+    out->kernel = PG_KERNEL_SPECIALISED;
+    out->lanes_per_env = 1;
+    snprintf(out->reason, sizeof(out->reason), "%s", why.c_str());
+    return PG_OK;
+  }
+  out->kernel = PG_KERNEL_BRANCH;
+  out->lanes_per_env = lanes;
+  out->branches = branches;
+  if (const char* dump = getenv("PG_BRANCH_SOURCE")) {
+    FILE* f = fopen(dump, "w");
+    if (f) { fwrite(src.data(), 1, src.size(), f); fclose(f); }
+  }
+  return PG_OK;
+}
+
+extern "C" int pg_batch_specialize_ex(pg_batch* b, unsigned flags) {
   if (!b) return set_error(PG_EINVAL, "batch is NULL");
+  if (flags & ~PG_SPEC_BRANCH) return set_error(PG_EINVAL, "unknown pg_batch_specialize_ex flags");
   if (b->models.size() != 1) return b->spec_parts.empty() ? specialize_parts(b) : PG_OK;
+  if ((flags & PG_SPEC_BRANCH) && !b->branch_kernel) {
+    const int rc = specialize_branch(b);
+    if (rc != PG_OK) return rc;
+  }
   if (b->spec_kernel) return PG_OK;
   std::vector<char> cubin;
   int rc = compile_cubin(b->models[0], cubin);

@@ -9,10 +9,17 @@ from paper_2502_08844_b300 import workloads as W
 
 
 class GpuRun:
-    def __init__(self, model: W.Model, n: int, envs_per_cta: int = 0, device="cuda"):
+    def __init__(self, model: W.Model, n: int, envs_per_cta: int = 0, device="cuda", specialize=False):
+        """specialize: False (the library's generic kernel), True (the model-specialised
+        thread-per-environment kernel) or "branch" (the branch-parallel kernel, which the model
+        must qualify for)."""
         self.model = model
         self.cm = core.CompiledModel(model)
         self.batch = core.Batch([(self.cm, n)], envs_per_cta=envs_per_cta)
+        if specialize:
+            self.batch.specialize(branch=specialize == "branch")
+            if specialize == "branch":
+                assert self.batch.kernel()["kernel"] == "branch-parallel", self.batch.kernel()
         self.state = core.State(self.batch, device)
         self.n = n
         self.device = device
@@ -91,7 +98,7 @@ def rel_err(x, ref, atol=1e-6):
 class MixedRun:
     """Several models in one batch (one launch per control step)."""
 
-    def __init__(self, parts, envs_per_cta: int = 0, device="cuda"):
+    def __init__(self, parts, envs_per_cta: int = 0, device="cuda", specialize: bool = False):
         self.parts = parts                      # [(workloads.Model, count)]
         self.cms = {}
         models = []
@@ -100,6 +107,8 @@ class MixedRun:
                 self.cms[id(m)] = core.CompiledModel(m)
             models.append((self.cms[id(m)], n))
         self.batch = core.Batch(models, envs_per_cta=envs_per_cta)
+        if specialize:
+            self.batch.specialize(branch=False)
         self.state = core.State(self.batch, device)
         self.offs = list(np.cumsum([0] + [n for _, n in parts]))
         self.n = self.offs[-1]

@@ -54,8 +54,9 @@ def gpu_rollout_grad(m: W.Model, q0, v0, U, weights, segment=8, specialize=False
             "damping": gp[:, nb:nb + nv], "kp": gp[:, nb + nv:nb + nv + nu]}
 
 
-def check_against_oracle(m, q0, v0, U, weights, keys=("q0", "v0", "u", "mass", "damping", "kp"), segment=8):
-    g = gpu_rollout_grad(m, q0, v0, U, weights, segment)
+def check_against_oracle(m, q0, v0, U, weights, keys=("q0", "v0", "u", "mass", "damping", "kp"), segment=8,
+                         specialize=False):
+    g = gpu_rollout_grad(m, q0, v0, U, weights, segment, specialize=specialize)
     om = O.OracleModel(m)
     worst = {}
     for e in range(q0.shape[0]):
@@ -82,14 +83,16 @@ def _converged(m: W.Model) -> W.Model:
     return dataclasses.replace(m, iterations=100)
 
 
-def test_quadruped_rollout_gradient_matches_oracle():
-    """End to end over one checkpoint segment (8 control steps = 40 substeps with contacts)."""
+@pytest.mark.parametrize("specialize", [pytest.param(False, id="generic"), pytest.param(True, id="specialised")])
+def test_quadruped_rollout_gradient_matches_oracle(specialize):
+    """End to end over one checkpoint segment (8 control steps = 40 substeps with contacts), with
+    the library's compiled kernels and with the model-specialised ones the benchmark times."""
     m = _converged(W.quadruped())
     n, T = 8, 8
     q0, v0 = W.initial_state(m, 4, n)
     U = W.actions(m, 4, n, 0, T)
     w = O.tracking_loss_weights(O.OracleModel(m))
-    check_against_oracle(m, q0, v0, U, w)
+    check_against_oracle(m, q0, v0, U, w, specialize=specialize)
 
 
 def test_torque_limited_rollout_gradient_matches_oracle():
@@ -236,18 +239,20 @@ def test_single_control_step_vjp_at_contact_states():
             assert err <= 1e-4, (e, k, err)
 
 
-def test_quadruped_16_steps_reanchored_on_gpu_trajectory():
-    """Two checkpoint segments (16 control steps).  The oracle's per-step reverse sweep is chained
-    along the GPU's own FP32 trajectory, so the comparison measures the adjoint, not the
-    divergence of FP32 and FP64 forward rollouts through contact events."""
+@pytest.mark.parametrize("T,specialize", [(16, False), (64, False), (64, True)])
+def test_quadruped_rollout_reanchored_on_gpu_trajectory(T, specialize):
+    """Two and eight checkpoint segments (16 and 64 control steps: the adjoint workload's horizon).
+    The oracle's per-step reverse sweep is chained along the GPU's own FP32 trajectory, so the
+    comparison measures the adjoint, not the divergence of FP32 and FP64 forward rollouts through
+    contact events."""
     m = _converged(W.quadruped())
-    n, T = 8, 16
+    n = 8
     q0, v0 = W.initial_state(m, 4, n)
     q0 = q0.astype(np.float64); v0 = v0.astype(np.float64)
     U = W.actions(m, 4, n, 0, T)
     w = O.tracking_loss_weights(O.OracleModel(m))
     wq, qs, wv, vs = w
-    g = gpu_rollout_grad(m, q0, v0, U, w)
+    g = gpu_rollout_grad(m, q0, v0, U, w, specialize=specialize)
     Q, V = g["traj_q"], g["traj_v"]            # [n, T, nq], the GPU states after each step
     om = O.OracleModel(m)
     for e in range(n):

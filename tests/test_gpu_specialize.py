@@ -23,7 +23,7 @@ def test_specialised_kernel_matches_generic(mname, cfg, n, T):
     for spec in (False, True):
         run = GpuRun(m, n)
         if spec:
-            run.batch.specialize()
+            run.batch.specialize(branch=False)
         run.set_state(q0, v0)
         tq, tv = run.rollout(U, m.n_substeps, keep=True)
         out.append((tq, tv, run.status()))
@@ -46,7 +46,7 @@ def test_specialised_mixed_batch_matches_generic(order):
         parts = [(core.CompiledModel(W.model(nm)), n) for nm, _, n in names]
         batch = core.Batch(parts)
         if spec:
-            batch.specialize()
+            batch.specialize(branch=False)
         st = core.State(batch, "cuda")
         ld = st.ld
         Q = np.zeros((batch.nq_max, ld), np.float32); V = np.zeros((batch.nv_max, ld), np.float32)
