@@ -411,172 +411,236 @@ template <class T> void segment_segment(const V3<T>& c1, const V3<T>& a1, T h1, 
 
 template <class T> inline V3<T> seg_axis(const Xf<T>& X) { return col(X.R, 2); }
 
+// Closest points of the segments c1 + u a1 (|u| <= h1) and c2 + v a2 (|v| <= h2) by exhaustion of
+// the parameter rectangle: the unconstrained stationary point when it lies inside, and the best
+// point of each of the rectangle's four sides (one parameter fixed at a bound, the other clamped
+// to its own optimum); the candidate of least distance wins (ties to the first listed).
+template <class T> void segment_pair_exhaustive(const V3<T>& c1, const V3<T>& a1, double h1, const V3<T>& c2,
+                                                const V3<T>& a2, double h2, T& u_out, T& v_out) {
+  const V3<T> r = sub(c1, c2);
+  const T b = dot(a1, a2), c = dot(a1, r), f = dot(a2, r);
+  auto clampd = [](T x, double lo, double hi) { return val(x) < lo ? T(lo) : (val(x) > hi ? T(hi) : x); };
+  auto dist2 = [&](const T& u, const T& v) {
+    const V3<T> d = sub(add(c1, scl(a1, u)), add(c2, scl(a2, v)));
+    return dot(d, d);
+  };
+  std::vector<std::pair<T, T>> cand;
+  const T den = T(1) - b * b;
+  if (val(den) > 1e-12) {
+    const T u = (b * f - c) / den, v = (f - b * c) / den;
+    if (std::fabs(val(u)) <= h1 && std::fabs(val(v)) <= h2) cand.push_back({u, v});
+  }
+  for (double us : {-h1, h1}) cand.push_back({T(us), clampd(b * T(us) + f, -h2, h2)});
+  for (double vs : {-h2, h2}) cand.push_back({clampd(b * T(vs) - c, -h1, h1), T(vs)});
+  size_t best = 0;
+  for (size_t k = 1; k < cand.size(); k++)
+    if (val(dist2(cand[k].first, cand[k].second)) < val(dist2(cand[best].first, cand[best].second))) best = k;
+  u_out = cand[best].first;
+  v_out = cand[best].second;
+}
+
 // Box-box by the separating-axis test over the 15 candidate axes (3 face normals of each box and
-// the 9 edge-edge cross products).  Overlap along a unit axis L: sum_k hA_k |L.A_k| +
-// sum_k hB_k |L.B_k| - |L.(cB - cA)|.  If any axis separates, every slot stays inactive.
-// Axis choice: the best face axis of box 1, replaced by box 2's best face axis only if that is
-// smaller by more than tol = 1e-5 (1 + overlap), then by the best edge axis only if smaller
-// again by more than tol (ties to the lower index throughout).
-//   Face case: the owning box is the reference; the incident face is the other box's face whose
-//   outward normal is most opposed to the reference normal; it is clipped (Sutherland-Hodgman)
-//   against the four side planes of the reference face; clipped points below the reference face
-//   (depth >= 0) are contacts, at the midpoint between the point and its projection on the
-//   reference face.  More than 4: the deepest, the farthest from it, the one of largest triangle
-//   area with those two, then the one farthest outside that triangle; kept in polygon order.
-//   Edge case: the closest points of the two supporting edges; one contact.
+// the 9 edge-edge cross products; a cross product shorter than 1e-6 is no axis).  Overlap along a
+// unit axis L: sum_k hA_k |L.A_k| + sum_k hB_k |L.B_k| - |L.(cB - cA)|.  If any axis separates,
+// every slot stays inactive.  Axis choice (R15): the best face axis of box 1, replaced by box 2's
+// best face axis only if that is smaller by more than tol = 1e-5 (1 + overlap), then by the best
+// edge axis only if smaller again by more than tol (ties to the lower index throughout).
+//   Face case: the box owning the axis is the reference; its face with outward normal nref along
+//   the axis (towards the other box) is the reference face; the incident face is the other box's
+//   face whose outward normal is most opposed to nref.  The contact polygon is the part of the
+//   incident face inside the reference face's prism (the reference face swept along nref).  Its
+//   vertices are constructed directly: (a) incident-face corners inside the prism, (b) crossings
+//   of the incident face's edges with the prism's side planes that lie inside the prism, (c)
+//   the prism's side edges (through the reference face's corners, along nref) piercing the
+//   incident face inside it; duplicates merged, then ordered by angle about their centroid in
+//   the reference face's plane.  Vertices below the reference face (depth >= 0) are contacts,
+//   at the midpoint between the vertex and its projection on the reference face.  More than 4:
+//   the deepest, the farthest from it, the one of largest triangle area with those two, then the
+//   one farthest outside that triangle (largest sum of the three sub-triangle areas), each with
+//   ties to the first in that order; kept in that order.
+//   Edge case: the closest points of the two edges (one per box, parallel to the axis's two
+//   factors) that are furthest along +n on box 1 and along -n on box 2; one contact.
 // The normal points from box 1 to box 2.
 template <class T> void box_box(const Xf<T>& XA, const double* hA, const Xf<T>& XB, const double* hB, Contact<T>* out) {
   for (int i = 0; i < 4; i++) { out[i].dist = T(1); out[i].n = V3<T>{T(0), T(0), T(1)}; out[i].pos = XA.p; }
-  V3<T> A[3] = {col(XA.R, 0), col(XA.R, 1), col(XA.R, 2)};
-  V3<T> B[3] = {col(XB.R, 0), col(XB.R, 1), col(XB.R, 2)};
-  V3<T> dc = sub(XB.p, XA.p);
-  auto overlap = [&](const V3<T>& L) {
-    T rA = T(0), rB = T(0);
-    for (int k = 0; k < 3; k++) {
-      T a = dot(L, A[k]), b = dot(L, B[k]);
-      rA = rA + T(hA[k]) * (val(a) < 0 ? -a : a);
-      rB = rB + T(hB[k]) * (val(b) < 0 ? -b : b);
-    }
-    T s = dot(L, dc);
-    return rA + rB - (val(s) < 0 ? -s : s);
+  const V3<T> axA[3] = {col(XA.R, 0), col(XA.R, 1), col(XA.R, 2)};
+  const V3<T> axB[3] = {col(XB.R, 0), col(XB.R, 1), col(XB.R, 2)};
+  const V3<T> d = sub(XB.p, XA.p);
+  auto absv = [](const T& x) { return val(x) < 0 ? -x : x; };
+  auto overlap_along = [&](const V3<T>& L) {
+    T reach = T(0);
+    for (int k = 0; k < 3; k++) reach = reach + T(hA[k]) * absv(dot(L, axA[k])) + T(hB[k]) * absv(dot(L, axB[k]));
+    return reach - absv(dot(L, d));
   };
-  V3<T> axes[15];
-  bool valid[15];
-  T ov[15];
-  for (int k = 0; k < 3; k++) { axes[k] = A[k]; axes[3 + k] = B[k]; valid[k] = valid[3 + k] = true; }
+  // candidate axes in the order: box 1 faces, box 2 faces, edge pairs (i of box 1, j of box 2)
+  struct Axis { V3<T> L; T ov; bool ok; };
+  std::vector<Axis> ax;
+  for (int k = 0; k < 3; k++) ax.push_back({axA[k], T(0), true});
+  for (int k = 0; k < 3; k++) ax.push_back({axB[k], T(0), true});
   for (int i = 0; i < 3; i++)
     for (int j = 0; j < 3; j++) {
-      V3<T> c = cross(A[i], B[j]);
-      T n = norm(c);
-      valid[6 + 3 * i + j] = val(n) > 1e-6;
-      axes[6 + 3 * i + j] = valid[6 + 3 * i + j] ? scl(c, T(1) / n) : c;
+      const V3<T> c = cross(axA[i], axB[j]);
+      const T len = norm(c);
+      ax.push_back({val(len) > 1e-6 ? scl(c, T(1) / len) : c, T(0), val(len) > 1e-6});
     }
-  for (int k = 0; k < 15; k++) {
-    if (!valid[k]) continue;
-    ov[k] = overlap(axes[k]);
-    if (val(ov[k]) < 0) return;   // separated
+  for (Axis& a : ax) {
+    if (!a.ok) continue;
+    a.ov = overlap_along(a.L);
+    if (val(a.ov) < 0) return;   // a separating axis
   }
-  auto best_in = [&](int lo, int hi) {
-    int b = -1;
+  auto least = [&](int lo, int hi) {
+    int w = -1;
     for (int k = lo; k < hi; k++)
-      if (valid[k] && (b < 0 || val(ov[k]) < val(ov[b]))) b = k;
-    return b;
+      if (ax[k].ok && (w < 0 || val(ax[k].ov) < val(ax[w].ov))) w = k;
+    return w;
   };
-  int best = best_in(0, 3);
-  int bB = best_in(3, 6);
-  if (val(ov[bB]) < val(ov[best]) - 1e-5 * (1 + val(ov[best]))) best = bB;
-  int bE = best_in(6, 15);
-  if (bE >= 0 && val(ov[bE]) < val(ov[best]) - 1e-5 * (1 + val(ov[best]))) best = bE;
-  V3<T> L = axes[best];
-  T depth = ov[best];
-  V3<T> n = val(dot(L, dc)) < 0 ? scl(L, T(-1)) : L;   // from box 1 to box 2
-  if (best >= 6) {
-    int i = (best - 6) / 3, j = (best - 6) % 3;
-    V3<T> pa = XA.p, pb = XB.p;
-    for (int k = 0; k < 3; k++) {
-      if (k != i) pa = add(pa, scl(A[k], T(val(dot(n, A[k])) >= 0 ? hA[k] : -hA[k])));
-      if (k != j) pb = add(pb, scl(B[k], T(val(dot(n, B[k])) >= 0 ? -hB[k] : hB[k])));
-    }
+  int pick = least(0, 3);
+  const int f2 = least(3, 6), e = least(6, 15);
+  if (val(ax[f2].ov) < val(ax[pick].ov) - 1e-5 * (1 + val(ax[pick].ov))) pick = f2;
+  if (e >= 0 && val(ax[e].ov) < val(ax[pick].ov) - 1e-5 * (1 + val(ax[pick].ov))) pick = e;
+  const T depth = ax[pick].ov;
+  const V3<T> n = val(dot(ax[pick].L, d)) < 0 ? scl(ax[pick].L, T(-1)) : ax[pick].L;   // box 1 -> box 2
+  if (pick >= 6) {
+    const int i = (pick - 6) / 3, j = (pick - 6) % 3;
+    // of the 4 edges of a box parallel to an axis, the one whose midpoint is furthest along s
+    auto support_edge_mid = [](const Xf<T>& X, const V3<T>* axes, const double* h, int along, const V3<T>& s) {
+      V3<T> best_mid = X.p;
+      double best_val = -1e300;
+      for (int corner = 0; corner < 4; corner++) {
+        V3<T> mid = X.p;
+        int bit = 0;
+        for (int k = 0; k < 3; k++) {
+          if (k == along) continue;
+          const double sg = ((corner >> bit) & 1) ? 1.0 : -1.0;
+          mid = add(mid, scl(axes[k], T(sg * h[k])));
+          bit++;
+        }
+        const double v = val(dot(mid, s));
+        if (v > best_val) { best_val = v; best_mid = mid; }
+      }
+      return best_mid;
+    };
+    const V3<T> ma = support_edge_mid(XA, axA, hA, i, n), mb = support_edge_mid(XB, axB, hB, j, scl(n, T(-1)));
     T u, v;
-    segment_segment(pa, A[i], T(hA[i]), pb, B[j], T(hB[j]), u, v);
-    V3<T> qa = add(pa, scl(A[i], u)), qb = add(pb, scl(B[j], v));
+    segment_pair_exhaustive(ma, axA[i], hA[i], mb, axB[j], hB[j], u, v);
     out[0].n = n;
     out[0].dist = -depth;
-    out[0].pos = scl(add(qa, qb), T(0.5));
+    out[0].pos = scl(add(add(ma, scl(axA[i], u)), add(mb, scl(axB[j], v))), T(0.5));
     return;
   }
-  // face case
-  bool refA = best < 3;
+  // ---- face case ----
+  const bool refA = pick < 3;
   const Xf<T>& XR = refA ? XA : XB;
   const Xf<T>& XI = refA ? XB : XA;
   const double* hR = refA ? hA : hB;
   const double* hI = refA ? hB : hA;
-  int kr = refA ? best : best - 3;
-  V3<T> nref = refA ? n : scl(n, T(-1));   // reference normal, towards the incident box
-  // incident face: outward normal most opposed to nref
+  const int kr = refA ? pick : pick - 3;
+  const V3<T> nref = refA ? n : scl(n, T(-1));   // out of the reference face, towards the incident box
+  const int r1 = (kr + 1) % 3, r2 = (kr + 2) % 3;
+  const V3<T> tu = col(XR.R, r1), tv = col(XR.R, r2);
+  // reference-face coordinates of a point: (along tu, along tv) relative to the face centre, and
+  // its depth below the face
+  auto face_uv = [&](const V3<T>& p) {
+    const V3<T> q = sub(p, XR.p);
+    return std::array<T, 2>{dot(q, tu), dot(q, tv)};
+  };
+  auto depth_of = [&](const V3<T>& p) { return T(hR[kr]) - dot(sub(p, XR.p), nref); };
+  const double tol = 1e-12 * (1 + std::max(std::max(hR[r1], hR[r2]), std::max(hI[0], std::max(hI[1], hI[2]))));
+  auto in_prism = [&](const V3<T>& p) {
+    const std::array<T, 2> uv = face_uv(p);
+    return std::fabs(val(uv[0])) <= hR[r1] + tol && std::fabs(val(uv[1])) <= hR[r2] + tol;
+  };
+  // the incident face: outward normal (axis fk, sign fs) most opposed to nref (ties to the lower
+  // axis, + before -)
   int fk = 0;
-  double fs = 1, bestd = 2;
-  for (int k = 0; k < 3; k++) {
-    double d = val(dot(col(XI.R, k), nref));
-    if (d < bestd) { bestd = d; fk = k; fs = 1; }
-    if (-d < bestd) { bestd = -d; fk = k; fs = -1; }
-  }
-  int ku = (fk + 1) % 3, kv = (fk + 2) % 3;
-  static const int su[4] = {-1, 1, 1, -1}, sv[4] = {-1, -1, 1, 1};
-  std::vector<V3<T>> poly;
-  for (int c = 0; c < 4; c++) {
-    V3<T> l{T(0), T(0), T(0)};
-    l[fk] = T(fs * hI[fk]);
-    l[ku] = T(su[c] * hI[ku]);
-    l[kv] = T(sv[c] * hI[kv]);
-    poly.push_back(xform(XI, l));
-  }
-  int ru = (kr + 1) % 3, rv = (kr + 2) % 3;
-  V3<T> planes_n[4] = {col(XR.R, ru), scl(col(XR.R, ru), T(-1)), col(XR.R, rv), scl(col(XR.R, rv), T(-1))};
-  double planes_h[4] = {hR[ru], hR[ru], hR[rv], hR[rv]};
-  for (int pl = 0; pl < 4 && !poly.empty(); pl++) {
-    auto side = [&](const V3<T>& p) { return T(planes_h[pl]) - dot(sub(p, XR.p), planes_n[pl]); };
-    std::vector<V3<T>> outp;
-    V3<T> S = poly.back();
-    for (size_t e = 0; e < poly.size(); e++) {
-      V3<T> E = poly[e];
-      T sS = side(S), sE = side(E);
-      if (val(sE) >= 0) {
-        if (val(sS) < 0) outp.push_back(add(S, scl(sub(E, S), sS / (sS - sE))));
-        outp.push_back(E);
-      } else if (val(sS) >= 0) {
-        outp.push_back(add(S, scl(sub(E, S), sS / (sS - sE))));
+  double fs = 1, most = 2;
+  for (int k = 0; k < 3; k++)
+    for (double sg : {1.0, -1.0}) {
+      const double c = sg * val(dot(col(XI.R, k), nref));
+      if (c < most) { most = c; fk = k; fs = sg; }
+    }
+  const int i1 = (fk + 1) % 3, i2 = (fk + 2) % 3;
+  const V3<T> fc = add(XI.p, scl(col(XI.R, fk), T(fs * hI[fk])));      // incident face centre
+  const V3<T> iu = col(XI.R, i1), iv = col(XI.R, i2), inrm = scl(col(XI.R, fk), T(fs));
+  std::vector<V3<T>> corners;
+  for (double a : {-1.0, 1.0})
+    for (double b : {-1.0, 1.0}) corners.push_back(add(fc, add(scl(iu, T(a * hI[i1])), scl(iv, T(b * hI[i2])))));
+  const int edges[4][2] = {{0, 1}, {1, 3}, {3, 2}, {2, 0}};   // the face's boundary, corner pairs
+  std::vector<V3<T>> pts;
+  auto add_point = [&](const V3<T>& p) {
+    for (const V3<T>& q : pts)
+      if (val(norm(sub(p, q))) <= 1e3 * tol) return;
+    pts.push_back(p);
+  };
+  for (const V3<T>& c : corners)                                          // (a)
+    if (in_prism(c)) add_point(c);
+  for (const auto& ed : edges) {                                          // (b)
+    const V3<T> &P = corners[ed[0]], &Q = corners[ed[1]];
+    const std::array<T, 2> up = face_uv(P), uq = face_uv(Q);
+    for (int coord = 0; coord < 2; coord++)
+      for (double side : {-1.0, 1.0}) {
+        const double lim = side * (coord == 0 ? hR[r1] : hR[r2]);
+        const T a = up[coord] - T(lim), b = uq[coord] - T(lim);
+        if ((val(a) < 0) == (val(b) < 0) || val(a) == val(b)) continue;   // no crossing
+        const T t = a / (a - b);
+        const V3<T> X = add(P, scl(sub(Q, P), t));
+        if (in_prism(X)) add_point(X);
       }
-      S = E;
-    }
-    poly = outp;
   }
-  std::vector<int> idx;
+  const T den = dot(nref, inrm);
+  if (std::fabs(val(den)) > 1e-12)                                        // (c)
+    for (double a : {-1.0, 1.0})
+      for (double b : {-1.0, 1.0}) {
+        const V3<T> base = add(XR.p, add(scl(tu, T(a * hR[r1])), scl(tv, T(b * hR[r2]))));
+        const T s = dot(sub(fc, base), inrm) / den;                    // base + s nref on the face plane
+        const V3<T> X = add(base, scl(nref, s));
+        const V3<T> q = sub(X, fc);
+        if (std::fabs(val(dot(q, iu))) <= hI[i1] + tol && std::fabs(val(dot(q, iv))) <= hI[i2] + tol) add_point(X);
+      }
+  if (pts.empty()) return;
+  // angular order about the centroid, in the reference face's (tu, tv) plane
+  V3<T> cen{T(0), T(0), T(0)};
+  for (const V3<T>& p : pts) cen = add(cen, p);
+  cen = scl(cen, T(1.0 / pts.size()));
+  std::vector<std::pair<double, int>> ang;
+  for (size_t k = 0; k < pts.size(); k++) {
+    const V3<T> q = sub(pts[k], cen);
+    ang.push_back({std::atan2(val(dot(q, tv)), val(dot(q, tu))), (int)k});
+  }
+  std::sort(ang.begin(), ang.end());
+  std::vector<V3<T>> poly;
   std::vector<T> dep;
-  for (size_t i = 0; i < poly.size(); i++) {
-    T d = T(hR[kr]) - dot(sub(poly[i], XR.p), nref);
-    dep.push_back(d);
-    if (val(d) >= 0) idx.push_back((int)i);
+  for (const auto& a : ang) {
+    const T dd = depth_of(pts[a.second]);
+    if (val(dd) >= 0) { poly.push_back(pts[a.second]); dep.push_back(dd); }
   }
-  if (idx.size() > 4) {
-    std::vector<int> keep;
-    int p0 = idx[0];
-    for (int i : idx) if (val(dep[i]) > val(dep[p0])) p0 = i;
-    keep.push_back(p0);
-    int p1 = -1;
-    double bd = -1;
-    for (int i : idx) {
-      if (i == p0) continue;
-      double d = val(norm(sub(poly[i], poly[p0])));
-      if (d > bd) { bd = d; p1 = i; }
-    }
-    keep.push_back(p1);
-    int p2 = -1;
-    bd = -1;
-    for (int i : idx) {
-      if (i == p0 || i == p1) continue;
-      double d = val(norm(cross(sub(poly[p1], poly[p0]), sub(poly[i], poly[p0]))));
-      if (d > bd) { bd = d; p2 = i; }
-    }
-    keep.push_back(p2);
-    int p3 = -1;
-    bd = -1;
-    for (int i : idx) {
-      if (i == p0 || i == p1 || i == p2) continue;
-      double d = val(norm(cross(sub(poly[p1], poly[p0]), sub(poly[i], poly[p0])))) +
-                 val(norm(cross(sub(poly[p2], poly[p1]), sub(poly[i], poly[p1])))) +
-                 val(norm(cross(sub(poly[p0], poly[p2]), sub(poly[i], poly[p2]))));
-      if (d > bd) { bd = d; p3 = i; }
-    }
-    keep.push_back(p3);
-    std::sort(keep.begin(), keep.end());
-    idx = keep;
+  std::vector<int> keep;
+  for (size_t k = 0; k < poly.size(); k++) keep.push_back((int)k);
+  if (poly.size() > 4) {
+    auto area2 = [&](int a, int b, int c) { return val(norm(cross(sub(poly[b], poly[a]), sub(poly[c], poly[a])))); };
+    auto argmax = [&](auto score, const std::vector<int>& taken) {
+      int w = -1;
+      double bv = -1;
+      for (int k = 0; k < (int)poly.size(); k++) {
+        if (std::find(taken.begin(), taken.end(), k) != taken.end()) continue;
+        const double v = score(k);
+        if (w < 0 || v > bv) { bv = v; w = k; }
+      }
+      return w;
+    };
+    std::vector<int> sel;
+    sel.push_back(argmax([&](int k) { return val(dep[k]); }, sel));
+    sel.push_back(argmax([&](int k) { return val(norm(sub(poly[k], poly[sel[0]]))); }, sel));
+    sel.push_back(argmax([&](int k) { return area2(sel[0], sel[1], k); }, sel));
+    sel.push_back(argmax([&](int k) { return area2(sel[0], sel[1], k) + area2(sel[1], sel[2], k) + area2(sel[2], sel[0], k); },
+                         sel));
+    keep = sel;
   }
-  for (size_t c = 0; c < idx.size(); c++) {
-    int i = idx[c];
+  for (size_t c = 0; c < keep.size(); c++) {
+    const int k = keep[c];
     out[c].n = n;
-    out[c].dist = -dep[i];
-    out[c].pos = add(poly[i], scl(nref, dep[i] * T(0.5)));
+    out[c].dist = -dep[k];
+    out[c].pos = add(poly[k], scl(nref, dep[k] * T(0.5)));
   }
 }
 
