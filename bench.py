@@ -68,7 +68,7 @@ class ClockSampler:
                  "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+                 "--format=csv,noheader,nounits", "-lms", "20"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
@@ -121,11 +121,12 @@ def whole_job_rate(local_seconds: float, ws: int, n_per_rank: int, steps: int, d
 
 
 def kernel_source_hash() -> str:
-    """sha256 (first 16 hex digits) of the step kernel's sources (the generic and the run-time
-    specialised builds): device functions, kernel body, kernels, translation unit, specialiser
-    and internal layout header, in that order."""
+    """sha256 (first 16 hex digits) of the step kernels' sources (the generic, the run-time
+    specialised and the branch-parallel builds): device functions, kernel bodies, kernels,
+    translation unit, specialiser, branch plan and internal layout header, in that order."""
     h = hashlib.sha256()
-    for f in ("step_device.cuh", "step_kernel_body.cuh", "step_kernels.cuh", "step.cu", "specialize.cpp", "pg_internal.h"):
+    for f in ("step_device.cuh", "step_kernel_body.cuh", "step_kernels.cuh", "step.cu", "specialize.cpp",
+              "branch_body.cuh", "branch.cpp", "pg_internal.h"):
         h.update(open(os.path.join(ROOT, "paper_2502_08844_b300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -143,12 +144,20 @@ def kernel_traffic(workload: str):
     return ent.get("dram_bytes_per_launch")
 
 
+def cpu_sample_envs() -> int:
+    """Environments of the oracle's timed sample (the CPU baseline and the reference arm): 16 per
+    host core, at least 256."""
+    return max(256, 16 * (os.cpu_count() or 1))
+
+
 def cpu_baseline(model: W.Model, cfg: int, n_envs: int, budget_s: float = 10.0, chunk: int = 10):
-    """The FP64 oracle on the host cores, on a bounded sample of the workload."""
+    """The FP64 oracle (its -O3 -march=native build) on all host cores, on a bounded sample of the
+    workload: cpu_sample_envs() environments, chunks of `chunk` control steps per call, until
+    budget_s seconds have passed."""
     from oracle import oracle as O
     cores = os.cpu_count() or 1
-    om = O.OracleModel(model)
-    n = min(n_envs, max(cores * 16, 64))
+    om = O.OracleModel(model, native=True)
+    n = min(n_envs, cpu_sample_envs())
     q, v = W.initial_state(model, cfg, n)
     warm = None
     steps, t0 = 0, time.time()
@@ -161,8 +170,8 @@ def cpu_baseline(model: W.Model, cfg: int, n_envs: int, budget_s: float = 10.0, 
             break
     dt = time.time() - t0
     return {"value": n * steps / dt, "unit": "env-steps/s", "cores": cores, "kind": "oracle",
-            "sample": "%d envs x %d control steps (%d substeps each) of the %s workload, FP64, %d threads" % (
-                n, steps, model.n_substeps, model.name, cores)}
+            "sample": "%d envs x %d control steps (%d substeps each, %d-step calls) of the %s workload, FP64 "
+                      "(-O3 -march=native), %d threads" % (n, steps, model.n_substeps, chunk, model.name, cores)}
 
 
 def measure_mixed(dev, steps: int = 200, specialize: bool = True):
@@ -206,8 +215,10 @@ def measure_mixed(dev, steps: int = 200, specialize: bool = True):
     torch.cuda.synchronize()
     t_eager = a.elapsed_time(b) / 1e3
     n_tot = sum(n for _, _, n in comp)
+    k = batch.kernel()
     return {"value": n_tot * steps / t_graph, "unit": "env-steps/s", "eager_value": n_tot * steps / t_eager,
-            "kernel": "model-specialised: one kernel per model over its own blocks, back to back" if specialize
+            "kernel": ("model-specialised: one kernel per model over its own environments, back to back; the "
+                       "branch-parallel kernel for %d of the %d models" % (k["branch_parts"], len(comp))) if specialize
                       else "generic (one body shared by the batch's models)",
             "composition": {nm: n for nm, _, n in comp}, "steps": steps, "cuda_graph": True,
             "envs_per_cta": epc or "default (one wave)", "launches": steps * (len(comp) if specialize else 1)}
@@ -225,7 +236,7 @@ def measure_env_layer(dev, n: int = 8192, steps: int = 200, specialize: bool = T
     cm = core.CompiledModel(m)
     batch = core.Batch([(cm, n)])
     if specialize:
-        batch.specialize()
+        batch.specialize(branch=False)   # the plain step on the kernel the environment step extends
     task = core.Task(cm, W.quadruped_task(episode_length=1000))
     st = core.State(batch, dev)
     ld = st.ld
@@ -356,7 +367,9 @@ def measure_pixels(dev, n: int = 8192, steps: int = 50):
 
 
 def run_reference(args):
-    """Reference arm: the FP64 oracle as it stands, timed on the host cores."""
+    """Reference arm: the FP64 oracle as it stands (its -O3 -march=native build), timed on the
+    host cores on the CPU baseline's sample shape: cpu_sample_envs() environments of the workload,
+    the W warm-up control steps in one call, then the K timed control steps in one call."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
@@ -364,17 +377,14 @@ def run_reference(args):
     m = W.model(args.workload)
     from oracle import oracle as O
     cores = os.cpu_count() or 1
-    om = O.OracleModel(m)
-    n = min(n_total, max(cores * 4, 32))
+    om = O.OracleModel(m, native=True)
+    n = min(n_total, cpu_sample_envs())
     q, v = W.initial_state(m, cfg, n)
     q = q.astype(np.float64); v = v.astype(np.float64)
-    warm = None
-    for t in range(args.warmup):
-        q, v, warm, _ = om.rollout(q, v, W.actions(m, cfg, n, t, 1), m.n_substeps, qacc_warm=warm, nthreads=cores)
+    q, v, warm, _ = om.rollout(q, v, W.actions(m, cfg, n, 0, args.warmup), m.n_substeps, nthreads=cores)
+    U = W.actions(m, cfg, n, args.warmup, args.steps)
     t0 = time.time()
-    for t in range(args.steps):
-        q, v, warm, _ = om.rollout(q, v, W.actions(m, cfg, n, args.warmup + t, 1), m.n_substeps, qacc_warm=warm,
-                                   nthreads=cores)
+    q, v, warm, _ = om.rollout(q, v, U, m.n_substeps, qacc_warm=warm, nthreads=cores)
     dt = time.time() - t0
     val = n * args.steps / dt
     line = {"metric": METRIC, "value": val, "unit": "env-steps/s", "n_gpus": ws, "steps": args.steps,
@@ -384,7 +394,8 @@ def run_reference(args):
                        "substeps": m.n_substeps, "newton_cap": m.iterations},
             "impl": "reference",
             "cpu_baseline": {"value": val, "unit": "env-steps/s", "cores": cores, "kind": "oracle",
-                             "sample": "%d envs per step, FP64 oracle, %d threads" % (n, cores)},
+                             "sample": "%d envs x %d control steps in one call, FP64 oracle (-O3 -march=native), "
+                                       "%d threads" % (n, args.steps, cores)},
             "e2e": {"value": val, "unit": "env-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -442,9 +453,81 @@ def measure_adjoint(dev, n: int = 4096, steps: int = 64, segment: int = 8, reps:
     gradient(); forward()   # warm-up (the adjoint's scratch is allocated on its first call)
     tf = min(timed(forward) for _ in range(reps))
     tg = min(timed(gradient) for _ in range(reps))
+    k = batch.kernel()
     return {"ratio": tg / tf, "forward_ms": tf, "gradient_ms": tg, "envs": n, "steps": steps, "segment": segment,
-            "newton_cap": m.iterations, "kernels": "model-specialised" if specialize else "generic",
+            "newton_cap": m.iterations,
+            "kernels": ("forward: %s; tape replay and reverse sweep: model-specialised thread-per-environment"
+                        % k["kernel"]) if specialize else "generic",
             "note": "gradient = checkpointed forward + loss + backward sweep"}
+
+
+# the other workload configurations, each timed on its own (model, input config, envs, control
+# steps timed): the cartpole (256 envs; 1000 steps as configured), the hand with the pyramidal
+# and the elliptic cone (8192 envs; 50 of the configured 500 control steps of 10 substeps), the
+# humanoid at the mixed batch's count (2048 envs)
+WORKLOADS = [("cartpole-256", "cartpole", 0, 256, 1000), ("hand-8192", "hand", 2, 8192, 50),
+             ("hand_elliptic-8192", "hand_elliptic", 2, 8192, 50), ("humanoid-2048", "humanoid", 3, 2048, 200)]
+
+
+def roofline_alu(m: W.Model, n: int, steps: int, sums, mean_launch_s: float, dev):
+    """ALU roofline of launches of the step: counted flops (flops.py) over the CUDA-core FP32 peak."""
+    import torch
+    fm = FL.flop_model(m)
+    flops_launch = fm.substeps(n * m.n_substeps * steps, sums[1], sums[0], sums[2]) / steps
+    peaks, src = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
+    peak = FL.fp32_peak_tflops(props.multi_processor_count, sm_mhz)
+    achieved = flops_launch / mean_launch_s / 1e12
+    bytes_launch = n * 4 * (2 * (m.nq + 2 * m.nv) + m.nu)
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "peak_source": "%d SMs x 128 FP32 lanes x 2 x sm_max_mhz %.0f (%s)" % (props.multi_processor_count, sm_mhz,
+                                                                                   src),
+            "flops_per_launch": flops_launch, "flops_source": "counted FP64 oracle, per-substep fit (flop_counts.json)",
+            "algorithmic_bytes_per_launch": bytes_launch,
+            "hbm_frac": bytes_launch / mean_launch_s / 1e9 / float(peaks.get("hbm_gbs", 6400.0)),
+            "newton_iters_per_substep": float(sums[0]) / (n * m.n_substeps * steps),
+            "rows_per_substep": float(sums[1]) / (n * m.n_substeps * steps)}
+
+
+def measure_workload(dev, name: str, cfg: int, n: int, steps: int, branch: bool = True, warmup: int = 3,
+                     warp_blocks: bool = False):
+    """Env-steps/s of one workload (its own launches, CUDA events around `steps` back-to-back
+    control steps; inputs device-resident) and its ALU roofline."""
+    import torch
+    from paper_2502_08844_b300 import core
+    m = W.model(name)
+    batch = core.Batch([(core.CompiledModel(m), n)])
+    batch.specialize(branch=branch, warp_blocks=warp_blocks)
+    st = core.State(batch, dev)
+    ld = st.ld
+    q0, v0 = W.initial_state(m, cfg, n)
+    st.qpos.copy_(torch.from_numpy(core.to_soa(q0, ld, batch.nq_max)))
+    st.qvel.copy_(torch.from_numpy(core.to_soa(v0, ld, batch.nv_max)))
+    U = np.zeros((warmup + steps, max(batch.nu_max, 1), ld), np.float32)
+    U[:, :m.nu, :n] = W.actions(m, cfg, n, 0, warmup + steps).transpose(0, 2, 1)
+    ctrl = torch.from_numpy(U).to(dev)
+    for t in range(warmup):
+        core.step(batch, st, ctrl[t], m.n_substeps)
+    stats = st.enable_stats()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    for t in range(steps):
+        core.step(batch, st, ctrl[warmup + t], m.n_substeps)
+    b.record()
+    torch.cuda.synchronize()
+    sec = a.elapsed_time(b) / 1e3
+    sums = stats[:, :n].to(torch.int64).sum(dim=1).cpu().numpy()
+    k = batch.kernel()
+    return {"value": n * steps / sec, "unit": "env-steps/s", "envs": n, "steps": steps, "substeps": m.n_substeps,
+            "newton_cap": m.iterations, "ms_per_step": 1e3 * sec / steps,
+            "kernel": k["kernel"] + ("" if k["kernel"] != "branch-parallel" else
+                                     " (%d lanes per environment, %d branches, %s)" % (
+                                         k["lanes_per_env"], k["branches"],
+                                         "barrier per substep" if k["barrier_per_substep"] else "one-warp blocks")),
+            "branch_kernel_not_used_because": k["reason"] or None,
+            "roofline": roofline_alu(m, n, steps, sums, sec / steps, dev)}
 
 
 def run_ours(args):
@@ -464,8 +547,15 @@ def run_ours(args):
     kernel = "generic"
     if not args.generic_kernel:
         try:
-            batch.specialize()   # NVRTC, cached; seconds on a first compile (outside the timed region)
-            kernel = "model-specialised (run-time compiled)"
+            # NVRTC, cached; seconds on a first compile (outside the timed region); the
+            # branch-parallel kernel where the model qualifies, else the thread-per-environment one
+            batch.specialize(branch=not args.thread_kernel)
+            k = batch.kernel()
+            kernel = ("branch-parallel (run-time compiled; %d lanes per environment, %d branches; %s)"
+                      % (k["lanes_per_env"], k["branches"],
+                         "one wave of blocks whose warps start each substep together" if k["barrier_per_substep"]
+                         else "blocks of one warp") if k["kernel"] == "branch-parallel"
+                      else "model-specialised (run-time compiled)")
         except Exception as e:   # keeps the generic kernel; reported in the line
             kernel = "generic (specialisation failed: %s)" % str(e).splitlines()[0][:200]
     state = core.State(batch, dev)
@@ -488,6 +578,19 @@ def run_ours(args):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clocks = ClockSampler(local)
     clocks.start()
+    # the clock samples (every 20 ms) need the GPU under this load for longer than a short timed
+    # region lasts: untimed steps of the same workload from a copy of the state fill about 0.5 s
+    # just before it (the timed steps start from the warmed-up state itself)
+    side = core.State(batch, dev)
+    side.qpos.copy_(state.qpos); side.qvel.copy_(state.qvel); side.qacc_warm.copy_(state.qacc_warm)
+    a0, b0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    core.step(batch, side, ctrl[0], m.n_substeps)
+    b0.record(stream)
+    torch.cuda.synchronize()
+    n_fill = int(min(20000, 0.5e3 / max(a0.elapsed_time(b0), 1e-3)))
+    for k in range(n_fill):
+        core.step(batch, side, ctrl[k % T], m.n_substeps)
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -502,29 +605,16 @@ def run_ours(args):
         dist.barrier()
     wall = time.time() - wall0
     ck = clocks.stop()
+    if ck is not None:
+        ck["window"] = "%d untimed steps of the workload just before the timed region, and the timed region" % n_fill
     times = [a.elapsed_time(b) for a, b in ev]          # ms per launch
     dev_s = sum(times) / 1e3
     st = stats[:, :n].to(torch.int64).sum(dim=1).cpu().numpy()
     status = state.status.cpu().numpy().view(np.uint32)
     value, dev_s = whole_job_rate(dev_s, ws, n, args.steps, dist)
-    # roofline: algorithmic FP32 flops per launch / mean launch time, against the CUDA-core peak
-    fm = FL.flop_model(m)
-    flops_total = fm.substeps(n * m.n_substeps * args.steps, st[1], st[0], st[2])
-    flops_launch = flops_total / args.steps
-    mean_launch = statistics.mean(times) / 1e3
-    peaks, src = measured_peaks()
-    props = torch.cuda.get_device_properties(dev)
-    sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
-    peak = FL.fp32_peak_tflops(props.multi_processor_count, sm_mhz)
-    achieved = flops_launch / mean_launch / 1e12
-    bytes_launch = n * 4 * (2 * (m.nq + 2 * m.nv) + m.nu)
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": kernel_traffic(args.workload),
-            "peak_source": "%d SMs x 128 FP32 lanes x 2 x sm_max_mhz %.0f (%s)" % (props.multi_processor_count, sm_mhz, src),
-            "flops_per_launch": flops_launch, "algorithmic_bytes_per_launch": bytes_launch,
-            "hbm_frac": bytes_launch / mean_launch / 1e9 / float(peaks.get("hbm_gbs", 6400.0)),
-            "newton_iters_per_substep": float(st[0]) / (n * m.n_substeps * args.steps),
-            "rows_per_substep": float(st[1]) / (n * m.n_substeps * args.steps)}
+    # roofline: algorithmic (counted) FP32 flops per launch / mean launch time, against the CUDA-core peak
+    roof = roofline_alu(m, n, args.steps, st, statistics.mean(times) / 1e3, dev)
+    roof["traffic"] = kernel_traffic(args.workload)
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
     if not args.no_e2e:
@@ -559,18 +649,27 @@ def run_ours(args):
             "adjoint_forward_ratio": None}
     # the sub-measurements characterise one GPU: the N = 1 line carries them, scaling runs skip them
     single = ws == 1
+    spec = not kernel.startswith("generic")
+    if single and not args.no_workloads:
+        line["workloads"] = {label: measure_workload(dev, nm, cfg_w, n_w, steps_w)
+                             for label, nm, cfg_w, n_w, steps_w in WORKLOADS}
+        if kernel.startswith("branch"):   # the headline workload and the humanoid on the other kernels
+            for nm, cfg_w, n_w in ((args.workload, cfg, n), ("humanoid", 3, 2048)):
+                line["workloads"]["%s-%d branch-parallel in one-warp blocks" % (nm, n_w)] = measure_workload(
+                    dev, nm, cfg_w, n_w, 200, warp_blocks=True)
+                line["workloads"]["%s-%d thread-per-environment" % (nm, n_w)] = measure_workload(
+                    dev, nm, cfg_w, n_w, 200, branch=False)
     if single and not args.no_mixed:
-        spec = kernel.startswith("model-specialised")
         line["mixed_batch"] = measure_mixed(dev, specialize=spec)
         if spec:
             line["mixed_batch"]["generic_kernel"] = {k: v for k, v in measure_mixed(dev, specialize=False).items()
                                                      if k in ("value", "eager_value")}
     if single and not args.no_env:
-        line["env_layer"] = measure_env_layer(dev, specialize=kernel.startswith("model-specialised"))
-        line["rough_terrain"] = measure_rough_terrain(dev, specialize=kernel.startswith("model-specialised"))
+        line["env_layer"] = measure_env_layer(dev, specialize=spec)
+        line["rough_terrain"] = measure_rough_terrain(dev, specialize=spec)
         line["pixels"] = measure_pixels(dev)
     if single and not args.no_adjoint:
-        adj = measure_adjoint(dev, specialize=kernel.startswith("model-specialised"))
+        adj = measure_adjoint(dev, specialize=spec)
         line["adjoint_forward_ratio"] = adj["ratio"]
         line["adjoint"] = adj
         gen = measure_adjoint(dev, specialize=False)
@@ -597,6 +696,9 @@ def main():
     ap.add_argument("--pixels-only", type=int, default=0, metavar="N",
                     help="only the pixel-observation measurement, on N cartpoles (for profiling the renderer)")
     ap.add_argument("--generic-kernel", action="store_true", help="skip pg_batch_specialize")
+    ap.add_argument("--thread-kernel", action="store_true",
+                    help="the model-specialised thread-per-environment kernel, not the branch-parallel one")
+    ap.add_argument("--no-workloads", action="store_true", help="skip the other workload configurations")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

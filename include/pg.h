@@ -207,7 +207,8 @@ void pg_model_free(pg_model* model);
  * models must outlive the batch.  envs_per_cta (>= 1, or 0 for the default) sets how many
  * environments share a thread block of the thread-per-environment kernels (one thread each;
  * the default is one wave: about n / SMs per block).  Allocates the batch's device tables and
- * nothing else; the scratch of pg_step_vjp is allocated by its first call (see there). */
+ * nothing else; the scratch of pg_step_vjp is reserved by pg_batch_reserve_vjp (or by the first
+ * pg_step_vjp call that needs it). */
 int pg_batch_compile(const pg_model* const* models, const int64_t* counts, int nmodels, int envs_per_cta,
                      pg_batch** out);
 int pg_batch_info(const pg_batch* batch, int64_t* n_envs, int* nq_max, int* nv_max, int* nu_max);
@@ -240,7 +241,7 @@ int pg_batch_specialize(pg_batch* batch);
 
 /* pg_batch_specialize with options. flags:
  *   PG_SPEC_BRANCH  for a single-model batch whose model qualifies, pg_step and pg_step_host run
- *                   the branch-parallel kernel: one thread per (environment, branch), where the
+ *                   the branch-parallel kernel (in a mixed batch, each qualifying model's part): one thread per (environment, branch), where the
  *                   branches are the chains of hinge/slide bodies hanging from the model's trunk
  *                   (a quadruped's legs, a humanoid's legs and arms) and the trunk's work is shared
  *                   through warp shuffles. It computes the same step (Sec. 3, "Environment": the
@@ -253,8 +254,16 @@ int pg_batch_specialize(pg_batch* batch);
  *                   pg_batch_kernel reports why one does not. pg_step_dr, pg_env_step, the tape and
  *                   the adjoint keep the thread-per-environment kernels.
  *   0               the thread-per-environment specialised kernels only.
+ *   PG_SPEC_BRANCH_WARP  see below.
  * Errors as pg_batch_specialize; flags other than these: PG_EINVAL. */
 #define PG_SPEC_BRANCH 1u
+/* How the branch-parallel kernel is launched.  By default as one wave of blocks of up to 8 warps
+ * (the warps per SM the batch needs) whose warps start every substep together (a barrier per
+ * substep): the substep is a long straight-line program, bound by fetching its own instructions,
+ * and warps that run it close together share those fetches (each substep then waits for the
+ * block's slowest Newton solve).  PG_SPEC_BRANCH_WARP (implies PG_SPEC_BRANCH): blocks of one warp
+ * and no barrier. */
+#define PG_SPEC_BRANCH_WARP 2u
 int pg_batch_specialize_ex(pg_batch* batch, unsigned flags);
 
 /* Which kernel pg_step runs for the batch. */
@@ -264,6 +273,8 @@ typedef struct {
   int lanes_per_env;   /* threads per environment (1, or the branch kernel's lane group)           */
   int branches;        /* branches of the model (branch kernel), else 0                            */
   char reason[160];    /* why the branch kernel is not used (empty when it is or was not asked)    */
+  int branch_parts;    /* mixed batch: models whose part runs the branch-parallel kernel          */
+  int sync;            /* branch kernel launched with a barrier per substep (the default)        */
 } pg_kernel_info;
 int pg_batch_kernel(const pg_batch* batch, pg_kernel_info* out);
 /* Whether a model qualifies for the branch-parallel kernel (host only, no device work): out->kernel
@@ -277,15 +288,41 @@ int pg_model_branch_plan(const pg_model* model, pg_kernel_info* out);
 int pg_reset(const pg_batch* batch, pg_state* state, const uint8_t* env_mask_dev, const float* qpos0_dev,
              const float* qvel0_dev, void* stream);
 
-/* One control step: n_substeps physics substeps with the controls ctrl_dev ([nu_max][ld])
- * held (zero-order hold); n_substeps == 0 runs each model's own `substeps` (a mixed batch
- * whose models run different rates).  Every environment integrates with its own model's
- * timestep.  Advances qpos, qvel, qacc_warm and ORs status bits in place. */
+/* One control step (the environment's step of Sec. 3, "Environment": the physics advanced by
+ * n_substeps substeps at the model's timestep with the controls held): n_substeps physics
+ * substeps with the controls ctrl_dev ([nu_max][ld]) held (zero-order hold); n_substeps == 0
+ * runs each model's own `substeps` (a mixed batch whose models run different rates).  Every
+ * environment integrates with its own model's timestep.  Advances qpos, qvel, qacc_warm and ORs
+ * status bits in place.  After the call qacc_warm holds the last substep's acceleration. */
 int pg_step(const pg_batch* batch, pg_state* state, const float* ctrl_dev, int n_substeps, void* stream);
+
+/* Optional outputs of pg_step_ex, all caller-owned device buffers (NULL: not written).
+ *   contact_force  [nslot][3][ld] float32, nslot = pg_batch_nslot(): for each candidate contact
+ *                  slot of the environment's model (its pairs in order, each with its static
+ *                  number of points), the force of the last substep's solve in the contact's
+ *                  frame (normal, t1, t2 of R14): a pyramid's edge forces D_e max(0, aref_e - J_e a)
+ *                  summed back into the frame (f_n = sum_e f_e, f_t1 = mu (f_0 - f_1), f_t2 =
+ *                  mu (f_2 - f_3)), an elliptic contact's minus the gradient of its cone cost; 0
+ *                  for a slot without an active contact (and for slots beyond the model's own).
+ *   ncon           [ld] int32: the last substep's active contacts. */
+typedef struct pg_step_out {
+  float* contact_force;
+  int32_t* ncon;
+} pg_step_out;
+
+/* pg_step with optional outputs (out may be NULL: exactly pg_step).  Every kernel writes them:
+ * the generic, the model-specialised, the branch-parallel and a mixed batch's parts. */
+int pg_step_ex(const pg_batch* batch, pg_state* state, const float* ctrl_dev, int n_substeps, const pg_step_out* out,
+               void* stream);
+
+/* Candidate contact slots of the batch's models (the largest): the rows of pg_step_out's
+ * contact_force. */
+int pg_batch_nslot(const pg_batch* batch);
 
 /* pg_step with per-environment physical parameters (domain randomisation, App. B "Domain
  * Randomization": ground friction, payload mass, link centres of mass, reflected inertia, joint
- * calibration offsets).  params_dev is [nrand_max][ld] float32 (caller-owned), per environment:
+ * calibration offsets; App. C.2 adds PD gains, link masses and motor friction).  params_dev is
+ * [nrand_max][ld] float32 (caller-owned), per environment:
  *   row 0                      friction scale: every pair's friction is multiplied by it;
  *   row 1                      payload: a point mass added at the centre of mass of body 1 (the
  *                              base of a floating robot), so body 1's mass grows and its
@@ -359,11 +396,18 @@ int pg_step_host(pg_batch* batch, pg_state* state, const float* ctrl_host, float
  * Scratch and errors.
  *   * Scratch, about n_steps * substeps * (nq + 3 nv) floats per env (plus the adjoint
  *     workspace when 8 environments' workspaces do not fit in one block's 227 KB of shared
- *     memory), is allocated on the first call and grown when a later call needs more. Such a
- *     call returns only after the allocation, so make it before any stream capture.
+ *     memory), is library-owned: reserve it up front with pg_batch_reserve_vjp, after which
+ *     calls within the reserved sizes allocate nothing. A call that needs more than is reserved
+ *     grows it (and returns only after the allocation, so make such a call before any stream
+ *     capture).
  *   * Calls on the same batch share the scratch: calls that overlap on the GPU race.
  *   * Errors: PG_EINVAL for NULL or inconsistent arguments, PG_EUNSUPPORTED,
  *     PG_ENOMEM / PG_ECUDA. */
+/* Reserve pg_step_vjp's scratch for calls of up to n_steps control steps of n_substeps substeps
+ * (0: each model's own) on states of row pitch ld, so that those calls allocate nothing.
+ * Errors: PG_EINVAL, PG_EUNSUPPORTED (a model outside the adjoint's scope), PG_ECUDA. */
+int pg_batch_reserve_vjp(pg_batch* batch, int n_steps, int n_substeps, int64_t ld);
+
 int pg_step_vjp(pg_batch* batch, const pg_state* ckpt, const float* ctrl_dev, int n_steps, int n_substeps,
                 const float* g_qpos_dev, const float* g_qvel_dev, float* adj_qpos_dev, float* adj_qvel_dev,
                 float* g_ctrl_dev, float* g_param_dev, void* stream);

@@ -41,13 +41,14 @@ class _Desc(C.Structure):
     ]
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        path = _build.build()
+def lib(native: bool = False):
+    """The oracle's library: the portable build, or (native=True) the -O3 -march=native build
+    that the timed CPU legs use, compiled on the host that runs them."""
+    if native not in _libs:
+        path = _build.build(native=native)
         L = C.CDLL(path)
         L.orc_model_new.restype = C.c_void_p
         L.orc_model_new.argtypes = [C.POINTER(_Desc), C.c_char_p, C.c_int]
@@ -79,8 +80,8 @@ def lib():
         L.orc_solid_inertia.argtypes = [C.c_int, _dp, C.c_double, _dp]
         L.orc_rotor_armature.restype = C.c_double
         L.orc_rotor_armature.argtypes = [C.c_double, C.c_double, C.c_double]
-        _lib = L
-    return _lib
+        _libs[native] = L
+    return _libs[native]
 
 
 def _d(a) -> np.ndarray:
@@ -105,8 +106,11 @@ class OracleModel:
     LAYOUT = ["xpos", "xmat", "xcom", "M", "bias", "passive", "actuator", "a0", "contacts", "nrow", "rows",
               "qacc", "iterations", "status", "qpos_next", "qvel_next"]
 
-    def __init__(self, m):
-        L = lib()
+    def __init__(self, m, native: bool = False):
+        """native: use the -O3 -march=native build (the timed CPU legs); results are the same
+        method in FP64, rounding aside."""
+        L = lib(native)
+        self.L = L
         self.src = m
         keep = {}
 
@@ -154,8 +158,8 @@ class OracleModel:
 
     def __del__(self):
         try:
-            if getattr(self, "h", None) is not None and _lib is not None:
-                _lib.orc_model_free(self.h)
+            if getattr(self, "h", None) is not None and getattr(self, "L", None) is not None:
+                self.L.orc_model_free(self.h)
         except Exception:
             pass
 
@@ -163,7 +167,7 @@ class OracleModel:
     def massprops(self):
         mass = np.zeros(self.nbody); ipos = np.zeros((self.nbody, 3)); inertia = np.zeros((self.nbody, 6))
         arm = np.zeros(self.nv)
-        lib().orc_model_massprops(self.h, _pd(mass), _pd(ipos), _pd(inertia), _pd(arm))
+        self.L.orc_model_massprops(self.h, _pd(mass), _pd(ipos), _pd(inertia), _pd(arm))
         return mass, ipos, inertia, arm
 
     # ---- stepping ------------------------------------------------------------------
@@ -183,7 +187,7 @@ class OracleModel:
         tv = np.zeros((T, N, self.nv)) if trajectory else None
         if ctrl.size == 0:
             ctrl = np.zeros((T, N, max(self.nu, 1)))
-        r = lib().orc_rollout(self.h, N, T, int(n_substeps), _pd(qpos), _pd(qvel), _pd(warm), _pd(ctrl),
+        r = self.L.orc_rollout(self.h, N, T, int(n_substeps), _pd(qpos), _pd(qvel), _pd(warm), _pd(ctrl),
                               status.ctypes.data_as(C.POINTER(C.c_uint32)), int(cap), int(nthreads),
                               _pd(tq) if trajectory else None, _pd(tv) if trajectory else None)
         if r != 0:
@@ -199,7 +203,7 @@ class OracleModel:
         u = np.zeros(max(self.nu, 1)) if ctrl is None else _d(ctrl)
         out = np.zeros(self.off[16])
         cap = self.src.iterations if solver_cap is None else solver_cap
-        lib().orc_forward(self.h, _pd(qpos), _pd(qvel), _pd(warm), _pd(u), int(cap), _pd(out))
+        self.L.orc_forward(self.h, _pd(qpos), _pd(qvel), _pd(warm), _pd(u), int(cap), _pd(out))
         return self.unpack(out)
 
     def unpack(self, out: np.ndarray) -> dict:
@@ -219,49 +223,49 @@ class OracleModel:
     # ---- pins ------------------------------------------------------------------------
     def inverse_dynamics(self, qpos, qvel, qacc):
         tau = np.zeros(self.nv)
-        lib().orc_inverse_dynamics(self.h, _pd(_d(qpos)), _pd(_d(qvel)), _pd(_d(qacc)), _pd(tau))
+        self.L.orc_inverse_dynamics(self.h, _pd(_d(qpos)), _pd(_d(qvel)), _pd(_d(qacc)), _pd(tau))
         return tau
 
     def mass_matrix(self, qpos):
         M = np.zeros((self.nv, self.nv))
-        lib().orc_mass_matrix(self.h, _pd(_d(qpos)), _pd(M))
+        self.L.orc_mass_matrix(self.h, _pd(_d(qpos)), _pd(M))
         return M
 
     def mass_matrix_crba(self, qpos):
         """The mass matrix by CRBA (the method the flop count takes), against mass_matrix's
         kinetic-energy definition."""
         M = np.zeros((self.nv, self.nv))
-        lib().orc_mass_matrix_crba(self.h, _pd(_d(qpos)), _pd(M))
+        self.L.orc_mass_matrix_crba(self.h, _pd(_d(qpos)), _pd(M))
         return M
 
     def body_frames(self, qpos):
         out = np.zeros((self.nbody, 15))
-        lib().orc_body_frames(self.h, _pd(_d(qpos)), _pd(out))
+        self.L.orc_body_frames(self.h, _pd(_d(qpos)), _pd(out))
         return out[:, :9].reshape(-1, 3, 3), out[:, 9:12], out[:, 12:15]
 
     def geom_frames(self, qpos):
         out = np.zeros((self.ngeom, 12))
-        lib().orc_geom_frames(self.h, _pd(_d(qpos)), _pd(out))
+        self.L.orc_geom_frames(self.h, _pd(_d(qpos)), _pd(out))
         return out[:, :9].reshape(-1, 3, 3), out[:, 9:12]
 
     def energy(self, qpos, qvel):
         out = np.zeros(2)
-        lib().orc_energy(self.h, _pd(_d(qpos)), _pd(_d(qvel)), _pd(out))
+        self.L.orc_energy(self.h, _pd(_d(qpos)), _pd(_d(qvel)), _pd(out))
         return out[0], out[1]
 
     def momentum(self, qpos, qvel):
         out = np.zeros(9)
-        lib().orc_momentum(self.h, _pd(_d(qpos)), _pd(_d(qvel)), _pd(out))
+        self.L.orc_momentum(self.h, _pd(_d(qpos)), _pd(_d(qvel)), _pd(out))
         return out[:3], out[3:6], out[6:9]
 
     def point_jacobian(self, qpos, body, point):
         Jv = np.zeros((3, self.nv)); Jw = np.zeros((3, self.nv))
-        lib().orc_point_jacobian(self.h, _pd(_d(qpos)), int(body), _pd(_d(point)), _pd(Jv), _pd(Jw))
+        self.L.orc_point_jacobian(self.h, _pd(_d(qpos)), int(body), _pd(_d(point)), _pd(Jv), _pd(Jw))
         return Jv, Jw
 
     def integrate_pos(self, qpos, qvel, dt):
         q = _d(qpos).copy()
-        lib().orc_integrate_pos(self.h, _pd(q), _pd(_d(qvel)), float(dt))
+        self.L.orc_integrate_pos(self.h, _pd(q), _pd(_d(qvel)), float(dt))
         return q
 
 
@@ -338,8 +342,8 @@ def rotor_armature(kg, mr, rr):
     return lib().orc_rotor_armature(float(kg), float(mr), float(rr))
 
 
-def _setup_grad_api():
-    L = lib()
+def _setup_grad_api(L=None):
+    L = lib() if L is None else L
     if getattr(L, "_grad_ready", False):
         return L
     L.orc_rollout_loss.restype = C.c_double
@@ -365,7 +369,7 @@ def _opt(a):
 
 
 def rollout_loss(om: "OracleModel", q0, v0, ctrl, n_substeps, weights, solver_cap=-1, mass=None, damping=None, kp=None):
-    L = _setup_grad_api()
+    L = _setup_grad_api(om.L)
     ctrl = _d(ctrl).reshape(len(ctrl), om.nu)
     wq, qs, wv, vs = [_d(x) for x in weights]
     return L.orc_rollout_loss(om.h, _pd(_d(q0)), _pd(_d(v0)), _pd(ctrl), ctrl.shape[0], int(n_substeps), int(solver_cap),
@@ -376,7 +380,7 @@ def step_vjp(om: "OracleModel", q, v, u, n_substeps, bq, bv, solver_cap=-1, mass
     """Reverse mode through one control step from (q, v) with controls u, given the adjoint (bq, bv)
     of the post-step state: dict with the pre-step adjoints q, v, the control adjoint u and the
     parameter adjoints mass, damping, kp (the warm start is a constant)."""
-    L = _setup_grad_api()
+    L = _setup_grad_api(om.L)
     out = {"q": _d(bq).copy(), "v": _d(bv).copy(), "u": np.zeros(om.nu), "mass": np.zeros(om.nbody),
            "damping": np.zeros(om.nv), "kp": np.zeros(om.nu)}
     L.orc_step_vjp(om.h, _pd(_d(q)), _pd(_d(v)), _pd(_d(u).reshape(om.nu)), int(n_substeps), int(solver_cap),
@@ -387,7 +391,7 @@ def step_vjp(om: "OracleModel", q, v, u, n_substeps, bq, bv, solver_cap=-1, mass
 
 def rollout_grad(om: "OracleModel", q0, v0, ctrl, n_substeps, weights, solver_cap=-1, mass=None, damping=None, kp=None):
     """Reverse-mode gradient of rollout_loss: dict with loss, q0, v0, u [T,nu], mass, damping, kp."""
-    L = _setup_grad_api()
+    L = _setup_grad_api(om.L)
     ctrl = _d(ctrl).reshape(len(ctrl), om.nu)
     T = ctrl.shape[0]
     wq, qs, wv, vs = [_d(x) for x in weights]
@@ -419,7 +423,7 @@ def count_substeps(om: "OracleModel", qpos, qvel, qacc_warm, ctrl, n_substeps: i
     """The oracle on its counting scalar (orc_count.hpp) over n_substeps substeps of one
     environment: (counts [S, phase, kind], rows [S], iters [S], final qpos, qvel, warm).  kind:
     add, mul, div, sqrt, transcendental; the factorisations counted are the leaves-first L^T D L."""
-    L = lib()
+    L = om.L
     if not getattr(L, "_count_ready", False):
         L.orc_count_substeps.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp, C.c_int, C.c_int, _dp,
                                          C.POINTER(C.c_int), C.POINTER(C.c_int)]

@@ -70,12 +70,18 @@ class pg_task_sizes(C.Structure):
 PG_PIXELS_U8, PG_PIXELS_F32 = 0, 1
 
 PG_SPEC_BRANCH = 1
+PG_SPEC_BRANCH_WARP = 2
 PG_KERNEL_GENERIC, PG_KERNEL_SPECIALISED, PG_KERNEL_SPECIALISED_PARTS, PG_KERNEL_BRANCH = 0, 1, 2, 3
 KERNEL_NAMES = {0: "generic", 1: "specialised", 2: "specialised per model", 3: "branch-parallel"}
 
 
+class pg_step_out(C.Structure):
+    _fields_ = [("contact_force", C.c_void_p), ("ncon", C.c_void_p)]
+
+
 class pg_kernel_info(C.Structure):
-    _fields_ = [("kernel", C.c_int), ("lanes_per_env", C.c_int), ("branches", C.c_int), ("reason", C.c_char * 160)]
+    _fields_ = [("kernel", C.c_int), ("lanes_per_env", C.c_int), ("branches", C.c_int), ("reason", C.c_char * 160),
+                ("branch_parts", C.c_int), ("sync", C.c_int)]
 
 
 class pg_render_desc(C.Structure):
@@ -89,6 +95,7 @@ class pg_render_desc(C.Structure):
 EXPORTS = ["pg_model_compile", "pg_model_info", "pg_model_free", "pg_batch_compile", "pg_batch_info",
            "pg_batch_free", "pg_reset", "pg_step", "pg_step_dr", "pg_debug_substep", "pg_step_host", "pg_step_vjp",
            "pg_step_vjp_noalloc", "pg_batch_specialize", "pg_batch_specialize_ex", "pg_batch_kernel",
+           "pg_step_ex", "pg_batch_nslot", "pg_batch_reserve_vjp",
            "pg_model_branch_plan", "pg_task_compile", "pg_task_info", "pg_task_free",
            "pg_env_reset", "pg_env_step", "pg_render", "pg_last_error"]
 
@@ -116,6 +123,9 @@ _lib.pg_step_host.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_v
 _lib.pg_step_vjp.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_int, C.c_int] + [C.c_void_p] * 7
 _lib.pg_batch_specialize.argtypes = [C.c_void_p]
 _lib.pg_batch_specialize_ex.argtypes = [C.c_void_p, C.c_uint]
+_lib.pg_step_ex.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_int, C.POINTER(pg_step_out), C.c_void_p]
+_lib.pg_batch_nslot.argtypes = [C.c_void_p]
+_lib.pg_batch_reserve_vjp.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int64]
 _lib.pg_batch_kernel.argtypes = [C.c_void_p, C.POINTER(pg_kernel_info)]
 _lib.pg_model_branch_plan.argtypes = [C.c_void_p, C.POINTER(pg_kernel_info)]
 _lib.pg_step_vjp_noalloc.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_int, C.c_int] + [C.c_void_p] * 7
@@ -219,6 +229,19 @@ def pg_step_vjp_noalloc(batch, ckpt: pg_state, ctrl_ptr, n_steps: int, n_substep
 
 def pg_batch_specialize(batch) -> None:
     _check(_lib.pg_batch_specialize(batch), "pg_batch_specialize")
+
+
+def pg_step_ex(batch, state: pg_state, ctrl_ptr, n_substeps: int, out, stream) -> None:
+    _check(_lib.pg_step_ex(batch, C.byref(state), ctrl_ptr, n_substeps, None if out is None else C.byref(out), stream),
+           "pg_step_ex")
+
+
+def pg_batch_reserve_vjp(batch, n_steps: int, n_substeps: int, ld: int) -> None:
+    _check(_lib.pg_batch_reserve_vjp(batch, n_steps, n_substeps, ld), "pg_batch_reserve_vjp")
+
+
+def pg_batch_nslot(batch) -> int:
+    return _lib.pg_batch_nslot(batch)
 
 
 def pg_batch_specialize_ex(batch, flags: int) -> None:

@@ -21,7 +21,7 @@ from typing import Optional, Tuple
 
 import torch
 
-from . import core
+from . import _capi, core
 
 
 class PgRollout(torch.autograd.Function):
@@ -34,6 +34,8 @@ class PgRollout(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, qpos0, qvel0, ctrl, params, batch: core.Batch, n_substeps: int, segment: int):
+        # the backward sweep's scratch, reserved here so that the backward pass allocates nothing
+        _capi.pg_batch_reserve_vjp(batch.handle, min(segment, ctrl.shape[0]), n_substeps, ctrl.shape[-1])
         st = core.State(batch, qpos0.device)
         st.qpos.copy_(qpos0)
         st.qvel.copy_(qvel0)

@@ -101,10 +101,12 @@ class Batch:
         self.nparam_max = max(m.sizes.nparam for m in self.models)
         self.specialized = False
 
-    def specialize(self, branch: bool = True) -> None:
+    def specialize(self, branch: bool = True, warp_blocks: bool = False) -> None:
         """pg_batch_specialize_ex: compile (NVRTC, cached) step kernels specialised to the model;
-        branch: let pg_step run the branch-parallel kernel when the model qualifies."""
-        _capi.pg_batch_specialize_ex(self.handle, _capi.PG_SPEC_BRANCH if branch else 0)
+        branch: let pg_step run the branch-parallel kernel when the model qualifies; warp_blocks:
+        launch it in blocks of one warp without the per-substep barrier (PG_SPEC_BRANCH_WARP)."""
+        flags = (_capi.PG_SPEC_BRANCH if branch else 0) | (_capi.PG_SPEC_BRANCH_WARP if warp_blocks else 0)
+        _capi.pg_batch_specialize_ex(self.handle, flags)
         self.specialized = True
 
     def kernel(self) -> dict:
@@ -112,7 +114,7 @@ class Batch:
         the branch-parallel kernel is not used)."""
         k = _capi.pg_batch_kernel(self.handle)
         return {"kernel": _capi.KERNEL_NAMES[k.kernel], "lanes_per_env": k.lanes_per_env, "branches": k.branches,
-                "reason": k.reason.decode()}
+                "reason": k.reason.decode(), "branch_parts": k.branch_parts, "barrier_per_substep": bool(k.sync)}
 
     def __del__(self):
         h = getattr(self, "handle", None)
@@ -226,6 +228,20 @@ def reset(batch: Batch, state: State, qpos0: torch.Tensor, qvel0: torch.Tensor, 
 def step(batch: Batch, state: State, ctrl: torch.Tensor, n_substeps: int, stream=None) -> None:
     assert ctrl.dtype == torch.float32 and ctrl.is_contiguous() and ctrl.shape[-1] == state.ld
     _capi.pg_step(batch.handle, state.c(), _ptr(ctrl), int(n_substeps), _stream_ptr(stream))
+
+
+def step_ex(batch: Batch, state: State, ctrl: torch.Tensor, n_substeps: int,
+            contact_force: Optional[torch.Tensor] = None, ncon: Optional[torch.Tensor] = None, stream=None) -> None:
+    """pg_step_ex: the step with its optional outputs: contact_force [nslot, 3, ld] float32 (the last
+    substep's force of every candidate contact slot in its contact frame), ncon [ld] int32."""
+    assert ctrl.dtype == torch.float32 and ctrl.is_contiguous() and ctrl.shape[-1] == state.ld
+    nslot = _capi.pg_batch_nslot(batch.handle)
+    assert contact_force is None or (contact_force.dtype == torch.float32 and contact_force.is_contiguous() and
+                                     tuple(contact_force.shape) == (nslot, 3, state.ld))
+    assert ncon is None or (ncon.dtype == torch.int32 and ncon.numel() >= state.ld)
+    out = _capi.pg_step_out(None if contact_force is None else contact_force.data_ptr(),
+                            None if ncon is None else ncon.data_ptr())
+    _capi.pg_step_ex(batch.handle, state.c(), _ptr(ctrl), int(n_substeps), out, _stream_ptr(stream))
 
 
 def step_dr(batch: Batch, state: State, ctrl: torch.Tensor, params: torch.Tensor, n_substeps: int,

@@ -272,7 +272,7 @@ int branch_plan(const pg_model* m, std::string& src, std::string& why, int& lane
   int NCL = 0;
   for (int s = 0; s < PS; s++) { pc0[s] = NCL; NCL += pnp[s]; }
   std::vector<int> pt1(GP * PS, -1), pt2(GP * PS, -1), ps1(GP * PS, -1), ps2(GP * PS, -1), pcond(GP * PS, 0),
-      pjb(GP * PS * NB, 0), pjt(GP * PS * NT, 0);
+      pjb(GP * PS * NB, 0), pjt(GP * PS * NT, 0), pslotadr(GP * PS, 0), pnslot(GP * PS, 0);
   std::vector<float> pgp1(GP * PS * 3, 0.f), pgq1(GP * PS * 4, 0.f), psz1(GP * PS * 3, 0.f), pgp2(GP * PS * 3, 0.f),
       pgq2(GP * PS * 4, 0.f), psz2(GP * PS * 3, 0.f), pmu(GP * PS, 0.f);
   for (int i = 0; i < GP * PS; i++) { pgq1[4 * i] = 1.f; pgq2[4 * i] = 1.f; }
@@ -283,6 +283,7 @@ int branch_plan(const pg_model* m, std::string& src, std::string& why, int& lane
       pt1[e] = TI(geom_type, g1); pt2[e] = TI(geom_type, g2);
       ps1[e] = side(TI(geom_body, g1)); ps2[e] = side(TI(geom_body, g2));
       pcond[e] = TI(pair_condim, p); pmu[e] = TF(pair_friction, p);
+      pslotadr[e] = TI(pair_slotadr, p); pnslot[e] = TI(pair_nslot, p);
       for (int i = 0; i < 3; i++) {
         pgp1[3 * e + i] = TF(geom_pos, 3 * g1 + i); psz1[3 * e + i] = TF(geom_size, 3 * g1 + i);
         pgp2[3 * e + i] = TF(geom_pos, 3 * g2 + i); psz2[3 * e + i] = TF(geom_size, 3 * g2 + i);
@@ -372,9 +373,12 @@ int branch_plan(const pg_model* m, std::string& src, std::string& why, int& lane
     pjb.assign(GP * nbb, 0); pjt.assign(GP * NT, 0); pgp1.assign(3 * GP, 0.f); pgq1.assign(4 * GP, 0.f);
     psz1.assign(3 * GP, 0.f); pgp2.assign(3 * GP, 0.f); pgq2.assign(4 * GP, 0.f); psz2.assign(3 * GP, 0.f);
     pmu.assign(GP, 0.f);
+    pslotadr.assign(GP, 0); pnslot.assign(GP, 0);
   }
   S.ti("kPt1", dims({GP, ps}), pt1); S.ti("kPt2", dims({GP, ps}), pt2); S.ti("kPs1", dims({GP, ps}), ps1);
   S.ti("kPs2", dims({GP, ps}), ps2); S.ti("kPcond", dims({GP, ps}), pcond);
+  S.ti("kPslot", dims({GP, ps}), pslotadr); S.ti("kPnslot", dims({GP, ps}), pnslot);
+  S.ci("NSLOT", h.nslot);
   S.ti("kPjb", dims({GP, ps, nbb}), pjb); S.ti("kPjt", dims({GP, ps, NT}), pjt);
   S.tf("kPgp1", dims({GP, ps, 3}), pgp1); S.tf("kPgq1", dims({GP, ps, 4}), pgq1); S.tf("kPsz1", dims({GP, ps, 3}), psz1);
   S.tf("kPgp2", dims({GP, ps, 3}), pgp2); S.tf("kPgq2", dims({GP, ps, 4}), pgq2); S.tf("kPsz2", dims({GP, ps, 3}), psz2);
@@ -385,17 +389,26 @@ int branch_plan(const pg_model* m, std::string& src, std::string& why, int& lane
   S.line("}  // namespace pgb");
   S.line("#include \"branch_body.cuh\"");
   S.line("extern \"C\" __global__ void __launch_bounds__(32) pg_step_branch(const __grid_constant__ pg::BranchArgs A) "
-         "{ pgb::branch_step(A); }");
+         "{ pgb::branch_step<false>(A); }");
+  S.line("extern \"C\" __global__ void __launch_bounds__(256) pg_step_branch_sync(const __grid_constant__ pg::BranchArgs A) "
+         "{ pgb::branch_step<true>(A); }");
   src = S.s;
   return PG_OK;
 #undef TI
 #undef TF
 }
 
-// one block of 32 threads holds 32 / lanes_per_env environments
-cudaError_t launch_branch(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st) {
-  if (s->n == 0) return cudaSuccess;
+// environments [env0, env0 + count) of a state.  k: blocks of one warp (32 / lanes environments
+// each).  k_sync (when not NULL): one wave of blocks of W warps, W the warps per SM the launch
+// needs (at most 8), whose warps start every substep together.
+cudaError_t launch_branch_range(cudaKernel_t k, cudaKernel_t k_sync, int lanes, int64_t env0, int64_t count,
+                                const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st,
+                                const pg_step_out* out, int nslot) {
+  if (count <= 0) return cudaSuccess;
   BranchArgs A;
+  A.out_force = out ? out->contact_force : nullptr;
+  A.out_ncon = out ? out->ncon : nullptr;
+  A.out_nslot = nslot;
   A.qpos = s->qpos;
   A.qvel = s->qvel;
   A.warm = s->qacc_warm;
@@ -403,12 +416,32 @@ cudaError_t launch_branch(const pg_batch* b, const pg_state* s, const float* ctr
   A.stats = s->stats;
   A.ctrl = ctrl;
   A.ld = s->ld;
-  A.n = s->n;
+  A.env0 = env0;
+  A.n = count;
   A.n_substeps = n_substeps;
-  const int epb = 32 / b->branch_lanes;
+  const int epw = 32 / lanes;   // environments per warp
   void* params[] = {&A};
-  return cudaLaunchKernel((const void*)b->branch_kernel, dim3((unsigned)((s->n + epb - 1) / epb)), dim3(32), params, 0,
-                          st);
+  if (k_sync) {
+    static int sms = 0;
+    if (!sms) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (sms < 1) sms = 1;
+    }
+    const int64_t warps = (count + epw - 1) / epw;
+    const int w = (int)std::min<int64_t>(8, std::max<int64_t>(1, (warps + sms - 1) / sms));
+    const int64_t per_block = (int64_t)w * epw;
+    return cudaLaunchKernel((const void*)k_sync, dim3((unsigned)((count + per_block - 1) / per_block)), dim3(32 * w),
+                            params, 0, st);
+  }
+  return cudaLaunchKernel((const void*)k, dim3((unsigned)((count + epw - 1) / epw)), dim3(32), params, 0, st);
+}
+
+cudaError_t launch_branch(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st,
+                          const pg_step_out* out) {
+  return launch_branch_range(b->branch_kernel, b->branch_kernel_sync, b->branch_lanes, 0, s->n, s, ctrl, n_substeps,
+                             st, out, b->nslot_max);
 }
 
 }  // namespace pg

@@ -83,6 +83,7 @@ __device__ __forceinline__ auto lsel(int br, F f) -> decltype(f(0)) {
 }
 
 __device__ __forceinline__ float inf_f() { return __int_as_float(0x7f800000); }
+
 __device__ __forceinline__ float3 c3(const float* p) { return make_float3(p[0], p[1], p[2]); }
 __device__ __forceinline__ float dot6(const float* a, float3 w, float3 v) {
   return a[0] * w.x + a[1] * w.y + a[2] * w.z + a[3] * v.x + a[4] * v.y + a[5] * v.z;
@@ -127,7 +128,7 @@ __device__ __forceinline__ void imul(const float ci[10], float3 w, float3 v, flo
 
 // impedance d(r) of the soft constraint (solimp = d0, dwidth, width, mid, power)
 __device__ __forceinline__ float imp(float pos) {
-  const float x = fminf(fabsf(pos) / SOLIMP_WIDTH, 1.f);
+  const float x = fminf(fabsf(pos) * (1.f / SOLIMP_WIDTH), 1.f);
   float y;
   if (x >= 1.f) y = 1.f;
   else if (x <= SOLIMP_MID) y = (SOLIMP_POWER == 2.f ? x * x : powf(x, SOLIMP_POWER)) * IMP_MID_INV;
@@ -136,6 +137,10 @@ __device__ __forceinline__ float imp(float pos) {
 }
 
 // ---- small dense factorisations (lower triangles of full arrays) ----
+// (Square roots and divisions in this file take the hardware's reciprocal square root and
+// approximate division, a few ulp from the correctly rounded result, instead of the IEEE
+// sequences whose slow paths would be unrolled at every site: the kernel is bound by fetching
+// its own instructions.)
 // Cholesky in place: L L^T = A; dinv[i] = 1 / L_ii; false when a pivot is not positive
 template <int N>
 __device__ __forceinline__ bool chol(float (&A)[N][N], float (&dinv)[N]) {
@@ -146,8 +151,8 @@ __device__ __forceinline__ bool chol(float (&A)[N][N], float (&dinv)[N]) {
 #pragma unroll
     for (int k = 0; k < j; k++) s -= A[j][k] * A[j][k];
     ok = ok && s > 0.f;
-    const float d = sqrtf(fmaxf(s, 1e-30f)), inv = 1.f / d;
-    A[j][j] = d;
+    const float sp = fmaxf(s, 1e-30f), inv = rsqrtf(sp);
+    A[j][j] = sp * inv;
     dinv[j] = inv;
 #pragma unroll
     for (int i = j + 1; i < N; i++) {
@@ -1048,13 +1053,13 @@ __device__ __forceinline__ float line_search(const Lane& L, const float (&aB)[NB
       qt = fmaf(D * j, j, qt);
       lt = fmaf(D * j, jr, lt);
     }
-    bp[r] = D > 0.f && j != 0.f ? -jr / j : -inf_f();
+    bp[r] = D > 0.f && j != 0.f ? __fdividef(-jr, j) : -inf_f();
   }
   qt = gsum(qt, L.gm) + qtT;
   lt = gsum(lt, L.gm) + ltT;
   float alpha = 0.f;
   for (int step = 0; step <= GP * NRL; step++) {
-    const float root = qt > 0.f ? -lt / qt : alpha;
+    const float root = qt > 0.f ? __fdividef(-lt, qt) : alpha;
     float next = inf_f();
 #pragma unroll
     for (int r = 0; r < NRL; r++)
@@ -1074,11 +1079,12 @@ __device__ __forceinline__ float line_search(const Lane& L, const float (&aB)[NB
     qt += gsum(dq, L.gm);
     lt += gsum(dl, L.gm);
   }
-  return qt > 0.f ? -lt / qt : alpha;
+  return qt > 0.f ? __fdividef(-lt, qt) : alpha;
 }
 
-// one substep of the lane's environment
-__device__ __forceinline__ void substep(Lane& L, uint32_t& status, uint32_t cnt[3]) {
+// one substep of the lane's environment; OUT: also write its contact forces and count (the last
+// substep of a pg_step_ex with outputs)
+__device__ __forceinline__ void substep(Lane& L, uint32_t& status, uint32_t cnt[3], bool out, const BranchArgs& A) {
   Kin K;
   kinematics(L, K);
   float cB[NB], cT[NT];
@@ -1153,7 +1159,7 @@ __device__ __forceinline__ void substep(Lane& L, uint32_t& status, uint32_t cnt[
       }
       const float v = pyr ? edge(mu, e, dn, d1, d2) : (e == 0 ? dn : 0.f);
       L.aref[r] = ex ? -BREF * v - KREF * d * dist[c] : 0.f;
-      L.D[r] = ex ? d / ((1.f - d) * Ah) : 0.f;
+      L.D[r] = ex ? __fdividef(d, (1.f - d) * Ah) : 0.f;
     }
   }
 #pragma unroll
@@ -1178,13 +1184,14 @@ __device__ __forceinline__ void substep(Lane& L, uint32_t& status, uint32_t cnt[
     const float vel = sgn * limit_val(L, kind, dd, L.vB, L.vT);
     const float d = sgn != 0.f ? imp(pos) : 0.f;
     L.aref[r] = sgn != 0.f ? -BREF * vel - KREF * d * pos : 0.f;
-    L.D[r] = sgn != 0.f ? d / ((1.f - d) * A[0][0]) : 0.f;
+    L.D[r] = sgn != 0.f ? __fdividef(d, (1.f - d) * A[0][0]) : 0.f;
   }
   int nrow = 0;
 #pragma unroll
   for (int r = 0; r < NRL; r++) nrow += L.D[r] > 0.f ? 1 : 0;
   nrow = gsumi(nrow, L.gm);
   float aB[NB], aT[NT];
+  float jar[NRL];   // J a - aref at the solution (when rows exist)
   int iters = 0;
   bool conv = true;
 #pragma unroll
@@ -1202,7 +1209,6 @@ __device__ __forceinline__ void substep(Lane& L, uint32_t& status, uint32_t cnt[
 #pragma unroll
       for (int t = 0; t < NT; t++) aT[t] = L.wT[t];
     }
-    float jar[NRL];
     unsigned act = residuals(L, aB, aT, jar);
     conv = false;
     while (iters < CAP) {
@@ -1227,6 +1233,37 @@ __device__ __forceinline__ void substep(Lane& L, uint32_t& status, uint32_t cnt[
   cnt[0] += (uint32_t)iters;
   cnt[1] += (uint32_t)nrow;
   cnt[2] += (uint32_t)(nrow * iters);
+  if (out) {   // the contact forces in each contact's frame, per candidate slot of the lane's pairs
+    int ncon = 0;
+#pragma unroll
+    for (int s = 0; s < PS; s++) {
+      const int slot0 = LV(kPslot, [s]), nsl = LV(kPnslot, [s]);
+#pragma unroll
+      for (int i = 0; i < pnp(s); i++) {
+        const int c = pc0(s) + i;
+        float fe[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+          const int r = 4 * c + e;
+          fe[e] = nrow > 0 && L.D[r] > 0.f && jar[r] < 0.f ? -L.D[r] * jar[r] : 0.f;
+        }
+        ncon += dist[c] < MARGIN ? 1 : 0;
+        if (A.out_force && i < nsl) {
+          float* o = A.out_force + (int64_t)(slot0 + i) * 3 * L.ld + L.env;
+          o[0] = fe[0] + fe[1] + fe[2] + fe[3];
+          o[L.ld] = L.mu[c] * (fe[0] - fe[1]);
+          o[2 * L.ld] = L.mu[c] * (fe[2] - fe[3]);
+        }
+      }
+    }
+    ncon = gsumi(ncon, L.gm);
+    if (L.br == 0) {
+      if (A.out_ncon) A.out_ncon[L.env] = ncon;
+      if (A.out_force)   // the rows of a batch's larger models
+        for (int sl = NSLOT; sl < A.out_nslot; sl++)
+          for (int q = 0; q < 3; q++) A.out_force[((int64_t)sl * 3 + q) * L.ld + L.env] = 0.f;
+    }
+  }
   // semi-implicit Euler
   bool bad = false;
 #pragma unroll
@@ -1253,12 +1290,13 @@ __device__ __forceinline__ void substep(Lane& L, uint32_t& status, uint32_t cnt[
 #pragma unroll
         for (int i = 0; i < 3; i++) L.qT[qa + i] = fmaf(HSTEP, L.vT[da + i], L.qT[qa + i]);
         const float3 w = make_float3(L.vT[da + 3], L.vT[da + 4], L.vT[da + 5]);
-        const float wn = sqrtf(dot3(w, w));
+        const float w2 = dot3(w, w);
         Quat q{L.qT[qa + 3], L.qT[qa + 4], L.qT[qa + 5], L.qT[qa + 6]};
-        if (wn > 0.f) {
+        if (w2 > 0.f) {   // rotation by h |w| about w: |h w / 2| stays far below pi
+          const float inv = rsqrtf(w2);
           float sn, cs;
-          sincosf(0.5f * HSTEP * wn, &sn, &cs);
-          const float s = sn / wn;
+          sincosf(0.5f * HSTEP * (w2 * inv), &sn, &cs);
+          const float s = sn * inv;
           q = qmul(q, Quat{cs, w.x * s, w.y * s, w.z * s});
         }
         q = qnormalize(q);
@@ -1273,14 +1311,20 @@ __device__ __forceinline__ void substep(Lane& L, uint32_t& status, uint32_t cnt[
   if (gor(bad ? 1 : 0, L.gm)) status |= PG_STATUS_NAN;
 }
 
-// The kernel: GP lanes per environment, EPB environments per warp-sized block.
+// The kernel: GP lanes per environment, blockDim.x / GP environments per block.  SYNC: the
+// block's warps start every substep together (a barrier per substep), so that they run its long
+// straight-line phases close together and share their instruction fetches; a group past the
+// last environment then steps the last environment alongside (it writes nothing).
+template <bool SYNC>
 __device__ __forceinline__ void branch_step(const BranchArgs& A) {
   const int tid = threadIdx.x;
   Lane L;
   L.br = tid & (GP - 1);
   L.gm = group_mask();
-  L.env = (int64_t)blockIdx.x * EPB + tid / GP;
-  if (L.env >= A.n) return;   // the whole group leaves together
+  const int64_t local = (int64_t)blockIdx.x * (blockDim.x / GP) + tid / GP;
+  const bool active = local < A.n;
+  if (!SYNC && !active) return;   // the whole group leaves together
+  L.env = A.env0 + (active ? local : A.n - 1);
   L.ld = A.ld;
   L.ctrl = A.ctrl;
   const int64_t ld = A.ld, env = L.env;
@@ -1311,7 +1355,12 @@ __device__ __forceinline__ void branch_step(const BranchArgs& A) {
   }
   uint32_t cnt[3] = {0u, 0u, 0u};
   const int nsub = A.n_substeps > 0 ? A.n_substeps : NSUB;
-  for (int s = 0; s < nsub; s++) substep(L, status, cnt);
+  const bool want = A.out_force || A.out_ncon;
+  for (int s = 0; s < nsub; s++) {
+    if (SYNC) __syncthreads();
+    substep(L, status, cnt, want && s == nsub - 1 && active, A);
+  }
+  if (!active) return;
   if (L.br == 0) {
 #pragma unroll
     for (int i = 0; i < NQT; i++) A.qpos[kTQg[i] * ld + env] = L.qT[i];

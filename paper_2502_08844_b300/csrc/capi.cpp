@@ -79,7 +79,10 @@ void pg_batch_free(pg_batch* b) {
   if (b->d_vjp) cudaFree(b->d_vjp);
   if (b->spec_lib) cudaLibraryUnload(b->spec_lib);
   if (b->branch_lib) cudaLibraryUnload(b->branch_lib);
-  for (const pg_batch::SpecPart& part : b->spec_parts) cudaLibraryUnload(part.lib);
+  for (const pg_batch::SpecPart& part : b->spec_parts) {
+    cudaLibraryUnload(part.lib);
+    if (part.branch_lib) cudaLibraryUnload(part.branch_lib);
+  }
   delete b;
 }
 
@@ -99,6 +102,7 @@ int pg_batch_compile(const pg_model* const* models, const int64_t* counts, int n
     const ModelHdr& h = models[k]->hdr;
     b->nq_max = std::max(b->nq_max, h.nq);
     b->nv_max = std::max(b->nv_max, h.nv);
+    b->nslot_max = std::max(b->nslot_max, h.nslot);
     b->nu_max = std::max(b->nu_max, h.nu);
     b->max_ws_floats = std::max(b->max_ws_floats, h.ws_floats);
     b->max_blob_words = std::max(b->max_blob_words, h.words);
@@ -219,6 +223,19 @@ int pg_step(const pg_batch* b, pg_state* s, const float* ctrl, int n_substeps, v
   return PG_OK;
 }
 
+int pg_step_ex(const pg_batch* b, pg_state* s, const float* ctrl, int n_substeps, const pg_step_out* out, void* stream) {
+  int rc = check_state(b, s);
+  if (rc) return rc;
+  if (n_substeps < 0) return set_error(PG_EINVAL, "n_substeps must be >= 0 (0: each model's own)");
+  if (b->n > 0 && b->nu_max > 0 && !ctrl) return set_error(PG_EINVAL, "NULL ctrl");
+  cudaError_t e = launch_step(b, s, ctrl, n_substeps, (cudaStream_t)stream, nullptr,
+                              out && (out->contact_force || out->ncon) ? out : nullptr);
+  if (e != cudaSuccess) return cuda_error(e, "step launch");
+  return PG_OK;
+}
+
+int pg_batch_nslot(const pg_batch* b) { return b ? b->nslot_max : 0; }
+
 int pg_step_dr(const pg_batch* b, pg_state* s, const float* ctrl, const float* params, int n_substeps, void* stream) {
   int rc = check_state(b, s);
   if (rc) return rc;
@@ -269,6 +286,49 @@ int pg_step_host(pg_batch* b, pg_state* s, const float* ctrl_host, float* qpos_h
   return PG_OK;
 }
 
+// the scratch of a pg_step_vjp call: the replayed state (qpos | qvel | warm | status), the substep
+// tape, and the reverse sweep's workspace when a block of it does not fit in shared memory
+static int vjp_scratch(const pg_batch* b, int n_steps, int n_substeps, int64_t ld, size_t& state_f, size_t& tape_f,
+                       size_t& need, int& sub_max) {
+  sub_max = 1;
+  int ws_max = 1;
+  for (const pg_model* m : b->models) {
+    if (!m->hdr.adj_ok) return set_error(PG_EUNSUPPORTED, "a model of the batch is outside the adjoint's scope");
+    sub_max = std::max(sub_max, n_substeps > 0 ? n_substeps : std::max(m->hdr.substeps, 1));
+    ws_max = std::max(ws_max, m->hdr_adj.ws_adj_floats);
+  }
+  const int nq = b->nq_max, nv = b->nv_max;
+  state_f = (size_t)(nq + 2 * nv + 1) * ld;
+  tape_f = (size_t)n_steps * sub_max * (nq + 3 * nv) * ld;
+  const size_t ws_f = vjp_smem_soa(ws_max) > 0 ? 0 : (size_t)ws_max * ld;
+  need = state_f + tape_f + ws_f;
+  return PG_OK;
+}
+
+static int grow_vjp(pg_batch* b, size_t need) {
+  if (b->vjp_floats >= need) return PG_OK;
+  if (b->d_vjp) cudaFree(b->d_vjp);
+  b->d_vjp = nullptr;
+  b->vjp_floats = 0;
+  cudaError_t e = cudaMalloc(&b->d_vjp, need * sizeof(float));
+  if (e != cudaSuccess) return cuda_error(e, "cudaMalloc (adjoint scratch)");
+  b->vjp_floats = need;
+  return PG_OK;
+}
+
+int pg_batch_reserve_vjp(pg_batch* b, int n_steps, int n_substeps, int64_t ld) {
+  if (!b) return set_error(PG_EINVAL, "NULL batch");
+  if (n_steps < 1) return set_error(PG_EINVAL, "n_steps must be >= 1");
+  if (n_substeps < 0) return set_error(PG_EINVAL, "n_substeps must be >= 0 (0: each model's own)");
+  if (ld < b->n) return set_error(PG_EINVAL, "ld must be >= the batch's environment count");
+  if (b->n == 0) return PG_OK;
+  size_t state_f = 0, tape_f = 0, need = 0;
+  int sub_max = 1;
+  int rc = vjp_scratch(b, n_steps, n_substeps, ld, state_f, tape_f, need, sub_max);
+  if (rc != PG_OK) return rc;
+  return grow_vjp(b, need);
+}
+
 int pg_step_vjp(pg_batch* b, const pg_state* ck, const float* ctrl, int n_steps, int n_substeps, const float* g_qpos,
                 const float* g_qvel, float* adj_qpos, float* adj_qvel, float* g_ctrl, float* g_param, void* stream) {
   if (!b || !ck) return set_error(PG_EINVAL, "NULL batch or checkpoint");
@@ -280,28 +340,14 @@ int pg_step_vjp(pg_batch* b, const pg_state* ck, const float* ctrl, int n_steps,
   if (!ck->qpos || !ck->qvel || !ck->qacc_warm) return set_error(PG_EINVAL, "NULL checkpoint array");
   if ((b->nu_max > 0 && (!ctrl || !g_ctrl)) || !adj_qpos || !adj_qvel || !g_param)
     return set_error(PG_EINVAL, "NULL argument");
-  int sub_max = 1, ws_max = 1;
-  for (const pg_model* m : b->models) {
-    if (!m->hdr.adj_ok) return set_error(PG_EUNSUPPORTED, "a model of the batch is outside the adjoint's scope");
-    sub_max = std::max(sub_max, n_substeps > 0 ? n_substeps : std::max(m->hdr.substeps, 1));
-    ws_max = std::max(ws_max, m->hdr_adj.ws_adj_floats);
-  }
+  size_t state_f = 0, tape_f = 0, need = 0;
+  int sub_max = 1;
+  int rc = vjp_scratch(b, n_steps, n_substeps, ck->ld, state_f, tape_f, need, sub_max);
+  if (rc != PG_OK) return rc;
+  if ((rc = grow_vjp(b, need)) != PG_OK) return rc;
   const int64_t ld = ck->ld;
   const int nq = b->nq_max, nv = b->nv_max, nu = std::max(b->nu_max, 1);
   const int tape_rows = nq + 3 * nv;
-  const size_t state_f = (size_t)(nq + 2 * nv + 1) * ld;            // qpos | qvel | warm | status
-  const size_t tape_f = (size_t)n_steps * sub_max * tape_rows * ld;
-  // the reverse sweep's workspace: in shared memory when a block of it fits, else here
-  const size_t ws_f = vjp_smem_soa(ws_max) > 0 ? 0 : (size_t)ws_max * ld;
-  const size_t need = state_f + tape_f + ws_f;
-  if (b->vjp_floats < need) {
-    if (b->d_vjp) cudaFree(b->d_vjp);
-    b->d_vjp = nullptr;
-    b->vjp_floats = 0;
-    cudaError_t e = cudaMalloc(&b->d_vjp, need * sizeof(float));
-    if (e != cudaSuccess) return cuda_error(e, "cudaMalloc (adjoint scratch)");
-    b->vjp_floats = need;
-  }
   cudaStream_t st = (cudaStream_t)stream;
   float* sq = b->d_vjp;
   float* sv = sq + (size_t)nq * ld;

@@ -30,6 +30,7 @@ struct pg_batch {
   std::vector<int64_t> counts, env_off;
   int64_t n = 0;
   int nq_max = 0, nv_max = 0, nu_max = 0;
+  int nslot_max = 0;               // candidate contact slots of the batch's models (pg_step_out rows)
   int threads = 32;                // threads per block (one environment per thread)
   std::vector<int> envs_per_cta;   // per model
   int max_ws_floats = 0, max_blob_words = 0, max_debug = 0;
@@ -58,11 +59,18 @@ struct pg_batch {
     cudaKernel_t kernel;
     int tile0, ntiles, threads;
     size_t smem;
+    // the model's branch-parallel kernel over its environments [env0, env0 + count), or NULL
+    cudaLibrary_t branch_lib;
+    cudaKernel_t branch;
+    cudaKernel_t branch_sync;
+    int branch_lanes;
+    int64_t env0, count;
   };
   std::vector<SpecPart> spec_parts;
   // the branch-parallel step kernel (pg_batch_specialize_ex with PG_SPEC_BRANCH), else NULL
   cudaLibrary_t branch_lib = nullptr;
   cudaKernel_t branch_kernel = nullptr;
+  cudaKernel_t branch_kernel_sync = nullptr;   // the same with a barrier per substep (the default launch)
   int branch_lanes = 0, branch_count = 0;
   std::string branch_why;   // why a requested branch kernel is not used
   // staging buffer of the host-buffer path (allocated on its first use)
@@ -94,11 +102,15 @@ int compile_model(const pg_model_desc* d, pg_model* out);
 // branch.cpp: the branch-parallel kernel's plan and generated source for a model
 int branch_plan(const pg_model* m, std::string& src, std::string& why, int& lanes_per_env, int& threads,
                 int& branches);
-cudaError_t launch_branch(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st);
+cudaError_t launch_branch(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st,
+                          const pg_step_out* out = nullptr);
+cudaError_t launch_branch_range(cudaKernel_t k, cudaKernel_t k_sync, int lanes, int64_t env0, int64_t count,
+                                const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st,
+                                const pg_step_out* out = nullptr, int nslot = 0);
 
 // kernel launchers (step.cu)
 cudaError_t launch_step(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st,
-                        const float* dr = nullptr);
+                        const float* dr = nullptr, const pg_step_out* out = nullptr);
 cudaError_t launch_debug(const pg_batch* b, const pg_state* s, const float* ctrl, int64_t env, float* out,
                          cudaStream_t st);
 cudaError_t launch_reset(const pg_batch* b, const pg_state* s, const uint8_t* mask, const float* qpos0,
@@ -116,13 +128,13 @@ cudaError_t launch_step_tape(const pg_batch* b, const pg_state* s, const float* 
   namespace NS {                                                                                                 \
   cudaError_t configure(size_t smem_bytes);                                                                      \
   cudaError_t step(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st,     \
-                   const float* dr = nullptr);                                                                   \
+                   const float* dr = nullptr, const pg_step_out* out = nullptr);                                 \
   cudaError_t step_tape(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, float* tape,     \
                         int tape_rows, cudaStream_t st);                                                         \
   cudaError_t debug(const pg_batch* b, const pg_state* s, const float* ctrl, int64_t env, float* out,            \
                     cudaStream_t st);                                                                            \
   cudaError_t step_spec(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st,\
-                        const float* dr = nullptr);                                                              \
+                        const float* dr = nullptr, const pg_step_out* out = nullptr);                            \
   cudaError_t step_spec_tape(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, float* tape,\
                              int tape_rows, cudaStream_t st);                                                   \
   cudaError_t step_env(const pg_batch* b, const pg_state* s, const EnvArgs& E, int n_substeps, cudaStream_t st,   \
@@ -130,7 +142,7 @@ cudaError_t launch_step_tape(const pg_batch* b, const pg_state* s, const float* 
   cudaError_t step_spec_env(const pg_batch* b, const pg_state* s, const EnvArgs& E, int n_substeps,            \
                             cudaStream_t st, const float* dr = nullptr);                                       \
   cudaError_t step_spec_parts(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps,          \
-                              cudaStream_t st);                                                                \
+                              cudaStream_t st, const pg_step_out* out = nullptr);                              \
   }
 PG_DECLARE_STEP_KERNELS(pyramidal)
 PG_DECLARE_STEP_KERNELS(elliptic)

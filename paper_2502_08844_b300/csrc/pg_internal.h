@@ -106,8 +106,8 @@ struct EnvArgs {
   EnvTask task;
 };
 
-// The branch-parallel step kernel's arguments (a single-model batch; see branch_body.cuh):
-// batch state and controls in the [coord][ld] layout of pg_state, n environments.
+// The branch-parallel step kernel's arguments (see branch_body.cuh): batch state and controls in
+// the [coord][ld] layout of pg_state; the n environments from env0 (one model's part of a batch).
 struct BranchArgs {
   float* qpos;
   float* qvel;
@@ -115,8 +115,11 @@ struct BranchArgs {
   uint32_t* status;
   uint32_t* stats;       // optional solver counters [3][ld], or NULL
   const float* ctrl;
-  int64_t ld, n;
+  int64_t ld, env0, n;
   int n_substeps;
+  float* out_force;      // optional [out_nslot][3][ld] contact forces of the last substep, or NULL
+  int32_t* out_ncon;     // optional [ld] active contacts of the last substep, or NULL
+  int out_nslot;
 };
 
 // one thread block's work: `count` consecutive envs starting at `env0` of model `model`

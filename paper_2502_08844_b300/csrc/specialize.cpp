@@ -220,32 +220,47 @@ int compile_cubin(const pg_model* m, std::vector<char>& cubin) {
   return compile_source(spec_source(m), "pg_step_spec.cu", cubin);
 }
 
-// the branch-parallel kernel of a single-model batch, when its model qualifies (else the reason
-// goes to b->branch_why and the batch keeps its other kernels)
-int specialize_branch(pg_batch* b) {
-  std::string src, why;
-  int lanes = 0, threads = 0, branches = 0;
-  if (branch_plan(b->models[0], src, why, lanes, threads, branches) != PG_OK) {
-    b->branch_why = why;
-    return PG_OK;
-  }
+// the branch-parallel kernel of a model, when it qualifies: lib and kernel set (else NULL, with the
+// reason in why)
+int compile_branch(const pg_model* m, bool warp_blocks, cudaLibrary_t& lib, cudaKernel_t& kernel,
+                   cudaKernel_t& kernel_sync, int& lanes, int& branches, std::string& why) {
+  lib = nullptr;
+  kernel = nullptr;
+  kernel_sync = nullptr;
+  std::string src;
+  int threads = 0;
+  if (branch_plan(m, src, why, lanes, threads, branches) != PG_OK) return PG_OK;
   std::vector<char> cubin;
   int rc = compile_source(src, "pg_step_branch.cu", cubin);
   if (rc != PG_OK) return rc;
-  cudaLibrary_t lib = nullptr;
   cudaError_t e = cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
   if (e != cudaSuccess) return set_error(PG_ECUDA, std::string("cudaLibraryLoadData: ") + cudaGetErrorString(e));
-  cudaKernel_t k = nullptr;
-  e = cudaLibraryGetKernel(&k, lib, "pg_step_branch");
+  e = cudaLibraryGetKernel(&kernel, lib, "pg_step_branch");
+  if (e == cudaSuccess && !warp_blocks) e = cudaLibraryGetKernel(&kernel_sync, lib, "pg_step_branch_sync");
   if (e != cudaSuccess) {
     cudaLibraryUnload(lib);
+    lib = nullptr;
+    kernel = nullptr;
+    kernel_sync = nullptr;
     return set_error(PG_ECUDA, std::string("branch kernel set-up: ") + cudaGetErrorString(e));
   }
+  why.clear();
+  return PG_OK;
+}
+
+// the branch-parallel kernel of a single-model batch, when its model qualifies (else the reason
+// goes to b->branch_why and the batch keeps its other kernels)
+int specialize_branch(pg_batch* b, bool warp_blocks) {
+  cudaLibrary_t lib = nullptr;
+  cudaKernel_t k = nullptr, ks = nullptr;
+  int lanes = 0, branches = 0;
+  const int rc = compile_branch(b->models[0], warp_blocks, lib, k, ks, lanes, branches, b->branch_why);
+  if (rc != PG_OK || !k) return rc;
   b->branch_lib = lib;
   b->branch_kernel = k;
+  b->branch_kernel_sync = ks;
   b->branch_lanes = lanes;
   b->branch_count = branches;
-  b->branch_why.clear();
   return PG_OK;
 }
 
@@ -259,10 +274,15 @@ using namespace pg;
 // measured slower than the generic kernel: blocks of different models share an SM and their large
 // specialised bodies evict each other from the instruction cache.  Launched one model after the
 // other, each kernel runs alone.  The tape, adjoint, environment and debug kernels stay generic.
-static int specialize_parts(pg_batch* b) {
+// With PG_SPEC_BRANCH every model that qualifies runs its branch-parallel kernel over its own
+// environments instead.
+static int specialize_parts(pg_batch* b, unsigned flags) {
   std::vector<pg_batch::SpecPart> parts;
   auto fail = [&](int rc) {
-    for (const pg_batch::SpecPart& p : parts) cudaLibraryUnload(p.lib);
+    for (const pg_batch::SpecPart& p : parts) {
+      cudaLibraryUnload(p.lib);
+      if (p.branch_lib) cudaLibraryUnload(p.branch_lib);
+    }
     return rc;
   };
   int dev = 0;
@@ -293,6 +313,15 @@ static int specialize_parts(pg_batch* b) {
       e = cudaKernelSetAttributeForDevice(parts.back().kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)part.smem, dev);
     if (e != cudaSuccess) return fail(set_error(PG_ECUDA, std::string("specialised kernel set-up: ") + cudaGetErrorString(e)));
+    parts.back().env0 = b->env_off[k];
+    parts.back().count = b->counts[k];
+    if (flags & PG_SPEC_BRANCH) {
+      int branches = 0;
+      std::string why;
+      rc = compile_branch(m, (flags & PG_SPEC_BRANCH_WARP) != 0, parts.back().branch_lib, parts.back().branch,
+                          parts.back().branch_sync, parts.back().branch_lanes, branches, why);
+      if (rc != PG_OK) return fail(rc);
+    }
   }
   b->spec_parts = parts;
   return PG_OK;
@@ -308,10 +337,12 @@ extern "C" int pg_batch_kernel(const pg_batch* b, pg_kernel_info* out) {
     out->kernel = PG_KERNEL_BRANCH;
     out->lanes_per_env = b->branch_lanes;
     out->branches = b->branch_count;
+    out->sync = b->branch_kernel_sync != nullptr;
   } else if (b->spec_kernel) {
     out->kernel = PG_KERNEL_SPECIALISED;
   } else if (!b->spec_parts.empty()) {
     out->kernel = PG_KERNEL_SPECIALISED_PARTS;
+    for (const pg_batch::SpecPart& p : b->spec_parts) out->branch_parts += p.branch ? 1 : 0;
   }
   snprintf(out->reason, sizeof(out->reason), "%s", b->branch_why.c_str());
   return PG_OK;
@@ -340,10 +371,11 @@ extern "C" int pg_model_branch_plan(const pg_model* m, pg_kernel_info* out) {
 
 extern "C" int pg_batch_specialize_ex(pg_batch* b, unsigned flags) {
   if (!b) return set_error(PG_EINVAL, "batch is NULL");
-  if (flags & ~PG_SPEC_BRANCH) return set_error(PG_EINVAL, "unknown pg_batch_specialize_ex flags");
-  if (b->models.size() != 1) return b->spec_parts.empty() ? specialize_parts(b) : PG_OK;
+  if (flags & ~(PG_SPEC_BRANCH | PG_SPEC_BRANCH_WARP)) return set_error(PG_EINVAL, "unknown pg_batch_specialize_ex flags");
+  if (flags & PG_SPEC_BRANCH_WARP) flags |= PG_SPEC_BRANCH;
+  if (b->models.size() != 1) return b->spec_parts.empty() ? specialize_parts(b, flags) : PG_OK;
   if ((flags & PG_SPEC_BRANCH) && !b->branch_kernel) {
-    const int rc = specialize_branch(b);
+    const int rc = specialize_branch(b, (flags & PG_SPEC_BRANCH_WARP) != 0);
     if (rc != PG_OK) return rc;
   }
   if (b->spec_kernel) return PG_OK;

@@ -76,12 +76,12 @@ cudaError_t configure_step_kernels(size_t smem_bytes) {
 }
 
 cudaError_t launch_step(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st,
-                        const float* dr) {
-  if (b->branch_kernel && !dr) return launch_branch(b, s, ctrl, n_substeps, st);
-  if (b->spec_kernel) return pyramidal::step_spec(b, s, ctrl, n_substeps, st, dr);
-  if (!b->spec_parts.empty() && !dr) return pyramidal::step_spec_parts(b, s, ctrl, n_substeps, st);
-  return b->has_elliptic ? elliptic::step(b, s, ctrl, n_substeps, st, dr)
-                         : pyramidal::step(b, s, ctrl, n_substeps, st, dr);
+                        const float* dr, const pg_step_out* out) {
+  if (b->branch_kernel && !dr) return launch_branch(b, s, ctrl, n_substeps, st, out);
+  if (b->spec_kernel) return pyramidal::step_spec(b, s, ctrl, n_substeps, st, dr, out);
+  if (!b->spec_parts.empty() && !dr) return pyramidal::step_spec_parts(b, s, ctrl, n_substeps, st, out);
+  return b->has_elliptic ? elliptic::step(b, s, ctrl, n_substeps, st, dr, out)
+                         : pyramidal::step(b, s, ctrl, n_substeps, st, dr, out);
 }
 
 cudaError_t launch_step_tape(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, float* tape,

@@ -370,8 +370,9 @@ __device__ __forceinline__ void body_massprops(const Ctx& c, int b, float& m, fl
   }
 }
 
-// actuator a's force at control u (motor: gear * u; PD: kp (u + calibration - q) - kd qd), u
-// already clipped to a limited control range, then clipped to a limited force range
+// actuator a's force at control u (motor: gear * u; PD: kp (u + calibration - q) - kd qd, the
+// gains scaled by this environment's 1 + s), u already clipped to a limited control range, then
+// clipped to a limited force range
 __device__ __forceinline__ float actuator_force(const Ctx& c, int a, float u) {
   float tau;
   if (MI(act_type, a) == PG_ACT_MOTOR) {
@@ -1706,11 +1707,49 @@ __device__ int newton(const Ctx& c, bool& converged) {
   return it;
 }
 
+// The contact forces of the substep just solved (its nc active contacts), each in its contact's
+// frame (normal, t1, t2), into out[(slot * 3 + k) * ld + env] for every candidate slot < nslot (0 for
+// a slot without an active contact): a pyramid's edge forces D_e max(0, aref_e - J_e a) summed back
+// into the frame (f_n = sum f_e, f_t1 = mu (f_0 - f_1), f_t2 = mu (f_2 - f_3)); an elliptic contact's
+// force minus the gradient of its cone cost.
+__device__ void contact_forces_out(const Ctx& c, int nc, float* out, int nslot) {
+  const ModelHdr& h = c.h;
+  for (int s = 0; s < nslot; s++)
+    for (int k = 0; k < 3; k++) out[(s * 3 + k) * c.ld + c.env] = 0.f;
+  rows_dot(c, h.w_a, h.w_jar);
+  for (int k = 0; k < nc; k++) {
+    const int slot = (int)W(con, kConFloats * k);
+    float f[3] = {0.f, 0.f, 0.f};
+    if (elliptic_group(c, k)) {
+      const int r = 4 * k;
+      if (W(rD, r) > 0.f) {
+        float gg[3], B[6];
+        cone_derivs(W(jar, r) - W(aref, r), W(jar, r + 1) - W(aref, r + 1), W(jar, r + 2) - W(aref, r + 2), W(gmu, k),
+                    W(rD, r), gg, B);
+        f[0] = -gg[0]; f[1] = -gg[1]; f[2] = -gg[2];
+      }
+    } else {
+      float fe[4];
+      for (int e = 0; e < 4; e++) {
+        const int r = 4 * k + e;
+        const float x = W(jar, r) - W(aref, r);
+        fe[e] = W(rD, r) > 0.f && x < 0.f ? -W(rD, r) * x : 0.f;
+      }
+      const float mu = W(gmu, k);
+      f[0] = fe[0] + fe[1] + fe[2] + fe[3];
+      f[1] = mu * (fe[0] - fe[1]);
+      f[2] = mu * (fe[2] - fe[3]);
+    }
+    if (slot >= 0 && slot < nslot)
+      for (int q = 0; q < 3; q++) out[(slot * 3 + q) * c.ld + c.env] = f[q];
+  }
+}
+
 // ---------------------------------------------------------------------------------------
-// one substep
+// one substep; returns its active contacts
 // ---------------------------------------------------------------------------------------
 template <bool DEBUG>
-__device__ void substep(const Ctx& c, uint32_t& status, float* dbg, uint32_t cnt[3]) {
+__device__ int substep(const Ctx& c, uint32_t& status, float* dbg, uint32_t cnt[3]) {
   const ModelHdr& h = c.h;
   const int nv = h.nv;
   kinematics(c);
@@ -1841,6 +1880,7 @@ __device__ void substep(const Ctx& c, uint32_t& status, float* dbg, uint32_t cnt
     for (int k = 0; k < nv; k++) dbg[h.dbg_qvel + k] = W(qvel, k);
     dbg[h.dbg_status] = (float)status;
   }
+  return nc;
 }
 
 }  // namespace

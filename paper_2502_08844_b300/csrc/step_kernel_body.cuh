@@ -31,6 +31,9 @@ struct StepArgs {
   const float* hfield[kMaxModels];    // each model's heightfield elevations (device), or NULL
   const float* dr;                    // per-environment parameters (pg_step_dr), or NULL
   EnvArgs env;                        // the locomotion task of an environment step (ENV below)
+  float* out_force;                   // optional [nslot][3][ld] contact forces of the last substep (pg_step_ex)
+  int32_t* out_ncon;                  // optional [ld] active contacts of the last substep
+  int out_nslot;                      // candidate contact slots of the batch's models (the rows of out_force)
   uint32_t blob[kMaxParamWords];      // the batch's model blobs (header + tables)
 };
 static_assert(sizeof(StepArgs) <= 32764, "the step's argument block must fit the kernel parameter space");
@@ -85,6 +88,7 @@ __device__ __forceinline__ void step_body(const StepArgs& A) {
   }
   uint32_t cnt[3] = {0u, 0u, 0u};
   const int nsub = DEBUG ? 1 : (A.n_substeps > 0 ? A.n_substeps : h.substeps);
+  int nc = 0;
   for (int s = 0; s < nsub; s++) {
     float* tp = TAPE ? A.tape + (int64_t)s * A.tape_rows * A.ld + env : nullptr;
     if (TAPE) {
@@ -94,9 +98,13 @@ __device__ __forceinline__ void step_body(const StepArgs& A) {
         tp[(A.tape_nq + A.tape_nv + k) * A.ld] = W(warm, k);
       }
     }
-    substep<DEBUG>(c, status, A.dbg, cnt);
+    nc = substep<DEBUG>(c, status, A.dbg, cnt);
     if (TAPE)
       for (int k = 0; k < h.nv; k++) tp[(A.tape_nq + 2 * A.tape_nv + k) * A.ld] = W(warm, k);
+  }
+  if (!DEBUG && !TAPE && !ENV) {   // the optional outputs of pg_step_ex (the last substep's contacts)
+    if (A.out_force) contact_forces_out(c, nc, A.out_force, A.out_nslot);
+    if (A.out_ncon) A.out_ncon[env] = nc;
   }
   for (int k = 0; k < h.nq; k++) A.qpos[k * A.ld + env] = W(qpos, k);
   for (int k = 0; k < h.nv; k++) {

@@ -54,18 +54,29 @@ static void make_args(StepArgs& A, const pg_batch* b, const pg_state* s, const f
   A.tape_rows = A.tape_nq = A.tape_nv = 0;
   A.env.state = nullptr;
   A.dr = nullptr;
+  A.out_force = nullptr;
+  A.out_ncon = nullptr;
+  A.out_nslot = 0;
   for (int k = 0; k < kMaxModels; k++) A.model_off[k] = k < (int)b->blob_off.size() ? b->blob_off[k] : 0;
   for (int k = 0; k < kMaxModels; k++) A.hfield[k] = b->hfield_ptr[k];
   std::memcpy(A.blob, b->blob_host.data(), b->blob_host.size() * sizeof(uint32_t));
 }
 
+static void set_out(StepArgs& A, const pg_batch* b, const pg_step_out* out) {
+  if (!out) return;
+  A.out_force = out->contact_force;
+  A.out_ncon = out->ncon;
+  A.out_nslot = b->nslot_max;
+}
+
 cudaError_t step(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st,
-                 const float* dr) {
+                 const float* dr, const pg_step_out* out) {
   if (b->ntiles == 0) return cudaSuccess;
   static thread_local StepArgs A;
   make_args(A, b, s, ctrl);
   A.n_substeps = n_substeps;
   A.dr = dr;
+  set_out(A, b, out);
   if (dr) step_kernel<false, false, false, true><<<b->ntiles, b->threads, b->smem_bytes, st>>>(A);
   else step_kernel<false, false><<<b->ntiles, b->threads, b->smem_bytes, st>>>(A);
   return cudaGetLastError();
@@ -73,12 +84,13 @@ cudaError_t step(const pg_batch* b, const pg_state* s, const float* ctrl, int n_
 
 // the batch's model-specialised kernel (same argument block)
 cudaError_t step_spec(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st,
-                      const float* dr) {
+                      const float* dr, const pg_step_out* out) {
   if (b->ntiles == 0) return cudaSuccess;
   static thread_local StepArgs A;
   make_args(A, b, s, ctrl);
   A.n_substeps = n_substeps;
   A.dr = dr;
+  set_out(A, b, out);
   void* params[] = {&A};
   return cudaLaunchKernel((const void*)(dr ? b->spec_kernel_dr : b->spec_kernel), dim3(b->ntiles), dim3(b->threads),
                           params, b->smem_bytes, st);
@@ -113,11 +125,19 @@ cudaError_t step_tape(const pg_batch* b, const pg_state* s, const float* ctrl, i
 }
 
 // a mixed batch's specialised step: each model's kernel over its own tiles, back to back
-cudaError_t step_spec_parts(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st) {
+cudaError_t step_spec_parts(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st,
+                            const pg_step_out* out) {
   static thread_local StepArgs A;
   make_args(A, b, s, ctrl);
   A.n_substeps = n_substeps;
+  set_out(A, b, out);
   for (const pg_batch::SpecPart& part : b->spec_parts) {
+    if (part.branch) {   // the model's branch-parallel kernel over its environments
+      cudaError_t e = launch_branch_range(part.branch, part.branch_sync, part.branch_lanes, part.env0, part.count, s, ctrl,
+                                          n_substeps, st, out, b->nslot_max);
+      if (e != cudaSuccess) return e;
+      continue;
+    }
     if (part.ntiles == 0) continue;
     A.tiles = b->d_tiles + part.tile0;
     void* params[] = {&A};

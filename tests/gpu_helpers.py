@@ -11,15 +11,18 @@ from paper_2502_08844_b300 import workloads as W
 class GpuRun:
     def __init__(self, model: W.Model, n: int, envs_per_cta: int = 0, device="cuda", specialize=False):
         """specialize: False (the library's generic kernel), True (the model-specialised
-        thread-per-environment kernel) or "branch" (the branch-parallel kernel, which the model
-        must qualify for)."""
+        thread-per-environment kernel), "branch" (the branch-parallel kernel, which the model must
+        qualify for, in its default launch: a barrier per substep) or "branch-warp" (the same
+        kernel in blocks of one warp)."""
         self.model = model
         self.cm = core.CompiledModel(model)
         self.batch = core.Batch([(self.cm, n)], envs_per_cta=envs_per_cta)
         if specialize:
-            self.batch.specialize(branch=specialize == "branch")
-            if specialize == "branch":
-                assert self.batch.kernel()["kernel"] == "branch-parallel", self.batch.kernel()
+            branch = specialize in ("branch", "branch-warp")
+            self.batch.specialize(branch=branch, warp_blocks=specialize == "branch-warp")
+            if branch:
+                k = self.batch.kernel()
+                assert k["kernel"] == "branch-parallel" and k["barrier_per_substep"] == (specialize == "branch"), k
         self.state = core.State(self.batch, device)
         self.n = n
         self.device = device
@@ -107,8 +110,8 @@ class MixedRun:
                 self.cms[id(m)] = core.CompiledModel(m)
             models.append((self.cms[id(m)], n))
         self.batch = core.Batch(models, envs_per_cta=envs_per_cta)
-        if specialize:
-            self.batch.specialize(branch=False)
+        if specialize:   # True: thread-per-environment parts; "branch": branch-parallel parts where a model qualifies
+            self.batch.specialize(branch=specialize == "branch")
         self.state = core.State(self.batch, device)
         self.offs = list(np.cumsum([0] + [n for _, n in parts]))
         self.n = self.offs[-1]

@@ -17,14 +17,16 @@ from tests.test_gpu_parity import ONE_STEP_RTOL, assert_close_scaled
 pytestmark = pytest.mark.gpu
 
 
+@pytest.mark.parametrize("launch", ["branch", "branch-warp"])
 @pytest.mark.parametrize("mname,cfg", [("quadruped", 1), ("humanoid", 3)])
-@pytest.mark.parametrize("n", [1, 5, 8, 9, 37])
-def test_ragged_env_counts(mname, cfg, n):
-    """Blocks hold 32 / lanes environments; counts that leave a block partly empty."""
+@pytest.mark.parametrize("n", [1, 5, 8, 9, 37, 1500])
+def test_ragged_env_counts(mname, cfg, n, launch):
+    """A warp holds 32 / lanes environments and a block up to 8 warps; counts that leave a warp or a
+    block partly empty (its spare groups step the last environment alongside and write nothing)."""
     m = W.model(mname)
     q0, v0 = W.initial_state(m, cfg, n)
     U = W.actions(m, cfg, n, 0, 2)
-    run = GpuRun(m, n, specialize="branch")
+    run = GpuRun(m, n, specialize=launch)
     run.set_state(q0, v0)
     run.rollout(U, m.n_substeps)
     qg, vg, _ = run.get()
@@ -114,6 +116,7 @@ def test_kernel_query_and_opt_out():
     b2.specialize()
     k = b2.kernel()
     assert k["kernel"] == "branch-parallel" and k["lanes_per_env"] == 4 and k["branches"] == 4
+    assert k["barrier_per_substep"]
     h = core.CompiledModel(W.hand())
     b3 = core.Batch([(h, 16)])
     b3.specialize()
