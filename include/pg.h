@@ -132,7 +132,7 @@ typedef struct pg_model_desc {
    * a positive loss F gets a two-sided constraint row (Jacobian e_d, reference acceleration
    * -b qvel_d) whose soft cost is the Huber function of its residual x with regulariser
    * R = 1 / D: D x^2 / 2 while |x| <= R F, F |x| - R F^2 / 2 outside, so its force stays in
-   * [-F, F].  Not with the elliptic cone (PG_EUNSUPPORTED). */
+   * [-F, F].  With either cone. */
   const float* dof_frictionloss;
 } pg_model_desc;
 
@@ -149,7 +149,7 @@ typedef struct pg_model_sizes {
   int adjoint_workspace_bytes;  /* per-env workspace of pg_step_vjp; 0 when the model is
                                    outside the adjoint's scope (see pg_step_vjp)          */
   int nparam;           /* nbody + nv + nu: rows of the per-env parameter gradient        */
-  int nrand;            /* 2 + 3 nbody + nv + nu: rows of pg_step_dr's per-env parameters */
+  int nrand;            /* 2 + 4 nbody + 2 nv + 3 nu: rows of pg_step_dr's per-env parameters */
 } pg_model_sizes;
 
 /* Caller-owned batch state (device pointers, [coord][ld] float32; status [n] uint32). */
@@ -331,10 +331,17 @@ int pg_batch_nslot(const pg_batch* batch);
  *                              inertia about the centre of mass unchanged;
  *   next nv rows               armature added to each dof;
  *   next nu rows               calibration offset of each actuator: a PD actuator acts as if
- *                              its target were ctrl + offset (a motor ignores it).
- * An all-zero block except row 0 = 1 is the nominal model.  In a mixed batch each environment
- * reads the rows of its own model's layout.  The adjoint (pg_step_vjp) differentiates the
- * nominal model only.  Errors as pg_step, and PG_EINVAL for a NULL params_dev. */
+ *                              its target were ctrl + offset (a motor ignores it);
+ *   next nu rows               kp scale s: a PD actuator's kp becomes kp (1 + s);
+ *   next nu rows               kd scale s: its kd becomes kd (1 + s);
+ *   next nbody rows            link mass scale s: body b's mass and its inertia about its centre
+ *                              of mass become (1 + s) times theirs (before body 1's payload);
+ *   next nv rows               friction-loss scale s: a dof's friction loss F becomes F (1 + s)
+ *                              (a dof compiled without friction loss keeps none).
+ * nrand = 2 + 4 nbody + 2 nv + 3 nu.  An all-zero block except row 0 = 1 is the nominal model.
+ * In a mixed batch each environment reads the rows of its own model's layout.  The adjoint
+ * (pg_step_vjp) differentiates the nominal model only.  Errors as pg_step, and PG_EINVAL for a
+ * NULL params_dev. */
 int pg_step_dr(const pg_batch* batch, pg_state* state, const float* ctrl_dev, const float* params_dev, int n_substeps,
                void* stream);
 

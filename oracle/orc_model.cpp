@@ -217,7 +217,6 @@ std::string compile_model(const Desc& d, Model& m) {
       m.dof_frictionloss[i] = d.dof_frictionloss[i];
       if (d.dof_frictionloss[i] > 0) m.nfric++;
     }
-  if (m.nfric > 0 && m.cone == ELLIPTIC) return "friction loss with the elliptic cone is unsupported";
   m.nrow_max = m.max_contacts * m.rows_per_contact + m.nlimited + m.nfric;
   return "";
 }

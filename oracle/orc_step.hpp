@@ -1009,6 +1009,12 @@ template <class T> T smooth_line_search(int nv, const std::vector<T>& M, const s
         continue;
       }
       T x = jar[i] + al * Jp[i];
+      if (R.kind[i] == 3) {   // friction loss: D x inside the band |x| <= F / D, the bound +-F beyond
+        const int z = fric_zone(x, R.D[i], R.mu[i]);
+        if (z == 1) { d1 = d1 + R.D[i] * x * Jp[i]; d2 = d2 + R.D[i] * Jp[i] * Jp[i]; }
+        else d1 = d1 + (z == 2 ? T(R.mu[i]) : -T(R.mu[i])) * Jp[i];
+        continue;
+      }
       if (val(x) < 0) { d1 = d1 + R.D[i] * x * Jp[i]; d2 = d2 + R.D[i] * Jp[i] * Jp[i]; }
     }
     return d1;

@@ -247,7 +247,8 @@ def step_ex(batch: Batch, state: State, ctrl: torch.Tensor, n_substeps: int,
 def step_dr(batch: Batch, state: State, ctrl: torch.Tensor, params: torch.Tensor, n_substeps: int,
             stream=None) -> None:
     """pg_step_dr: the step with per-environment parameters params [nrand_max][ld] (friction
-    scale, payload, centre-of-mass offsets, armature, calibration offsets)."""
+    scale, payload, centre-of-mass offsets, armature, calibration offsets, PD gain scales, link
+    mass scales, friction-loss scales)."""
     assert ctrl.dtype == torch.float32 and ctrl.is_contiguous() and ctrl.shape[-1] == state.ld
     nrand = max(m.sizes.nrand for m in batch.models)
     assert params.dtype == torch.float32 and params.is_contiguous() and params.shape == (nrand, state.ld)

@@ -320,8 +320,6 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
       if (!(F >= 0.f) || !std::isfinite(F)) return set_error(PG_EINVAL, "dof_frictionloss must be finite and >= 0");
       if (F > 0.f) { fric_dof.push_back(i); fric_F.push_back(F); }
     }
-  if (!fric_dof.empty() && d->cone == PG_CONE_ELLIPTIC)
-    return set_error(PG_EUNSUPPORTED, "joint friction loss with the elliptic cone is unsupported");
   int nrow_max = 4 * max_contacts + (int)limit_jnt.size() + (int)fric_dof.size();
   if (nrow_max > kMaxRow) return set_error(PG_ECAPACITY, "constraint rows exceed the kernel limit (128)");
 
@@ -376,7 +374,11 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
   h.dr_com = 2;
   h.dr_arm = 2 + 3 * nbody;
   h.dr_cal = 2 + 3 * nbody + nv;
-  h.nrand = 2 + 3 * nbody + nv + nu;
+  h.dr_kp = h.dr_cal + nu;
+  h.dr_kd = h.dr_kp + nu;
+  h.dr_mass = h.dr_kd + nu;
+  h.dr_fric = h.dr_mass + nbody;
+  h.nrand = h.dr_fric + nv;
   h.o_limit_jnt = B.ints(limit_jnt);
   h.nfric = (int)fric_dof.size();
   h.o_fric_dof = B.ints(fric_dof); h.o_fric_F = B.floats(fric_F);

@@ -47,7 +47,8 @@ struct ModelHdr {
   int o_act_type, o_act_dof, o_act_qposadr, o_act_gear, o_act_kp, o_act_kd, o_act_ctrllimited, o_act_range;
   int o_act_forcelimited, o_act_forcerange;
   int nrand;          // rows of the per-environment parameters of pg_step_dr
-  int dr_com, dr_arm, dr_cal;   // their first rows: COM offsets, armature, calibration offsets
+  int dr_com, dr_arm, dr_cal;   // their first rows: COM offsets, armature, calibration offsets,
+  int dr_kp, dr_kd, dr_mass, dr_fric;   // PD gain scales, link mass scales, friction-loss scales
   int o_limit_jnt;
   int nfric, o_fric_dof, o_fric_F;   // friction-loss rows: their dofs and force bounds
   int words;   // total blob size

@@ -358,12 +358,19 @@ __device__ __forceinline__ float3 T3(const float* t) { return make_float3(t[0], 
 // row k of this environment's parameters (pg_step_dr)
 __device__ __forceinline__ float dr_row(const Ctx& c, int k) { return __ldg(c.dr + k * c.ld + c.env); }
 
-// body b's mass and centre of mass (body frame), with this environment's payload on body 1 and
-// centre-of-mass offsets
+// body b's link mass scale 1 + s_b (mass and inertia about the centre of mass), 1 without
+// per-environment parameters
+__device__ __forceinline__ float mass_scale(const Ctx& c, int b) {
+  return c.dr ? 1.f + dr_row(c, c.h.dr_mass + b) : 1.f;
+}
+
+// body b's mass and centre of mass (body frame), with this environment's link mass scale, its
+// payload on body 1 and its centre-of-mass offsets
 __device__ __forceinline__ void body_massprops(const Ctx& c, int b, float& m, float3& ipos) {
   m = MF(body_mass, b);
   ipos = T3(&MF(body_ipos, 3 * b));
   if (c.dr) {
+    m *= mass_scale(c, b);
     if (b == 1) m += dr_row(c, 1);
     ipos = ipos + make_float3(dr_row(c, c.h.dr_com + 3 * b), dr_row(c, c.h.dr_com + 3 * b + 1),
                               dr_row(c, c.h.dr_com + 3 * b + 2));
@@ -378,8 +385,13 @@ __device__ __forceinline__ float actuator_force(const Ctx& c, int a, float u) {
   if (MI(act_type, a) == PG_ACT_MOTOR) {
     tau = MF(act_gear, a) * u;
   } else {
-    if (c.dr) u += dr_row(c, c.h.dr_cal + a);
-    tau = MF(act_kp, a) * (u - W(qpos, MI(act_qposadr, a))) - MF(act_kd, a) * W(qvel, MI(act_dof, a));
+    float kp = MF(act_kp, a), kd = MF(act_kd, a);
+    if (c.dr) {
+      u += dr_row(c, c.h.dr_cal + a);
+      kp *= 1.f + dr_row(c, c.h.dr_kp + a);
+      kd *= 1.f + dr_row(c, c.h.dr_kd + a);
+    }
+    tau = kp * (u - W(qpos, MI(act_qposadr, a))) - kd * W(qvel, MI(act_dof, a));
   }
   if (MI(act_forcelimited, a)) tau = fminf(fmaxf(tau, MF(act_forcerange, 2 * a)), MF(act_forcerange, 2 * a + 1));
   return tau;
@@ -466,7 +478,9 @@ __device__ void kinematics(const Ctx& c) {
     body_massprops(c, b, m, ip);
     const float3 com = x + mat_mul(R, ip);
     const float* In = &MF(body_inertia, 6 * b);
-    const float Ib[9] = {In[0], In[3], In[4], In[3], In[1], In[5], In[4], In[5], In[2]};
+    const float ms = mass_scale(c, b);
+    const float Ib[9] = {ms * In[0], ms * In[3], ms * In[4], ms * In[3], ms * In[1],
+                         ms * In[5], ms * In[4], ms * In[5], ms * In[2]};
     float T[9];
 #pragma unroll
     for (int r = 0; r < 3; r++)
@@ -1142,6 +1156,11 @@ __device__ void rows_dot(const Ctx& c, int X, int OUT) {
 
 // first friction-loss row (rows 4 max_contacts + nlimited + k, k < nfric: the dof fric_dof[k])
 __device__ __forceinline__ int fric_row0(const ModelHdr& h) { return 4 * h.max_contacts + h.nlimited; }
+// friction-loss row k's force bound F, scaled by this environment's 1 + s of its dof
+__device__ __forceinline__ float fric_bound(const Ctx& c, int k) {
+  const float F = MF(fric_F, k);
+  return c.dr ? F * (1.f + dr_row(c, c.h.dr_fric + MI(fric_dof, k))) : F;
+}
 
 // impedance d(r) from solimp = (d0, dwidth, width, mid, power)
 // (x^p by a multiplication for the usual power 2; the mid-point powers come from the header)
@@ -1350,7 +1369,7 @@ __device__ float cost_of(const Ctx& c, int X) {
     }
     const float jar = W(jar, r) - W(aref, r);
     if (r >= fric_row0(h)) {   // friction loss: Huber cost with the band |x| <= F / D
-      const float D = W(rD, r), F = MF(fric_F, r - fric_row0(h)), rf = F / D;
+      const float D = W(rD, r), F = fric_bound(c, r - fric_row0(h)), rf = F / D;
       f += fabsf(jar) <= rf ? 0.5f * D * jar * jar : F * fabsf(jar) - 0.5f * F * rf;
       continue;
     }
@@ -1372,7 +1391,7 @@ __device__ void residuals(const Ctx& c, unsigned act[4], unsigned* side = nullpt
   for (int r = 0; r < h.nrow_max; r++) W(jar, r) = W(jar, r) - W(aref, r);
   for (int r = 0; r < h.nrow_max; r++) {
     if (r >= fric_row0(h)) {
-      const float x = W(jar, r), rf = MF(fric_F, r - fric_row0(h)) / W(rD, r);
+      const float x = W(jar, r), rf = fric_bound(c, r - fric_row0(h)) / W(rD, r);
       if (fabsf(x) <= rf) act[r >> 5] |= 1u << (r & 31);
       else if (side && x > 0.f) side[r >> 5] |= 1u << (r & 31);
       continue;
@@ -1483,7 +1502,7 @@ __device__ bool newton_direction(const Ctx& c, const unsigned act[4], bool& zero
       if (tree) W(L, MI(dof_rowadr, d)) += D;
       else W(H, d * nv + d) += D;
     } else {
-      W(g, d) += x > 0.f ? MF(fric_F, k) : -MF(fric_F, k);
+      W(g, d) += x > 0.f ? fric_bound(c, k) : -fric_bound(c, k);
     }
   }
   bool nz = false;
@@ -1551,7 +1570,7 @@ __device__ float line_search(const Ctx& c) {
   // friction-loss rows: quadratic inside the band |x| <= F / D, slope +-F Jp beyond it; the next
   // band edge the motion reaches is the row's breakpoint (the far edge once inside)
   for (int r = R0; r < R; r++) {
-    const float D = W(rD, r), jp = W(Jp, r), jr = W(jar, r), F = MF(fric_F, r - R0), rf = F / D;
+    const float D = W(rD, r), jp = W(Jp, r), jr = W(jar, r), F = fric_bound(c, r - R0), rf = F / D;
     const bool mid = (jr > -rf && jr < rf) || (jr == rf && jp <= 0.f) || (jr == -rf && jp >= 0.f);
     if (mid) {
       on[r >> 5] |= 1u << (r & 31);
@@ -1580,7 +1599,7 @@ __device__ float line_search(const Ctx& c) {
       if (r >= R0) {
         // a friction-loss row at a band edge: entering the band from the side it came from, or
         // leaving it towards the side the motion leads to
-        const float F = MF(fric_F, r - R0), s = jp > 0.f ? 1.f : -1.f;
+        const float F = fric_bound(c, r - R0), s = jp > 0.f ? 1.f : -1.f;
         if (sg > 0.f) {   // entering: drop the slope -s F Jp, add the quadratic, next the far edge
           lt = fmaf(s * F, jp, lt);
           W(bp, r) = (s * F / D - W(jar, r)) / jp;
@@ -1598,9 +1617,9 @@ __device__ float line_search(const Ctx& c) {
 }
 
 // Line search when elliptic contacts make phi(alpha) = f(a + alpha p) convex but not piecewise
-// quadratic: bracket the root of phi' (phi'(0) < 0; alpha doubled from 1 until phi' >= 0), then
-// safeguarded Newton steps on phi' (bisection whenever the Newton point leaves the bracket) until
-// the bracket or |phi'| is at FP32 rounding level.
+// quadratic (friction-loss rows add their Huber terms): bracket the root of phi' (phi'(0) < 0;
+// alpha doubled from 1 until phi' >= 0), then safeguarded Newton steps on phi' (bisection whenever
+// the Newton point leaves the bracket) until the bracket or |phi'| is at FP32 rounding level.
 __device__ float line_search_smooth(const Ctx& c) {
   const ModelHdr& h = c.h;
   const int nv = h.nv, R = h.nrow_max, MC = h.max_contacts;
@@ -1627,6 +1646,16 @@ __device__ float line_search_smooth(const Ctx& c) {
         continue;
       }
       const float jp = W(Jp, r), x = fmaf(al, jp, W(jar, r));
+      if (r >= fric_row0(h)) {   // friction loss: D x inside the band |x| <= F / D, the bound +-F beyond
+        const float F = fric_bound(c, r - fric_row0(h));
+        if (fabsf(x) <= F / W(rD, r)) {
+          d1 = fmaf(W(rD, r) * x, jp, d1);
+          d2 = fmaf(W(rD, r) * jp, jp, d2);
+        } else {
+          d1 = fmaf(x > 0.f ? F : -F, jp, d1);
+        }
+        continue;
+      }
       if (x < 0.f) {
         d1 = fmaf(W(rD, r) * x, jp, d1);
         d2 = fmaf(W(rD, r) * jp, jp, d2);
@@ -1830,7 +1859,7 @@ __device__ int substep(const Ctx& c, uint32_t& status, float* dbg, uint32_t cnt[
       const float jar = W(jar, r) - W(aref, r);
       o[nv + 6] = jar < 0.f ? -W(rD, r) * jar : 0.f;
       if (r >= fric_row0(h)) {   // friction loss: -D x inside the band, the bound beyond
-        const float F = MF(fric_F, r - fric_row0(h));
+        const float F = fric_bound(c, r - fric_row0(h));
         o[nv + 6] = fabsf(jar) <= F / W(rD, r) ? -W(rD, r) * jar : (jar > 0.f ? -F : F);
       }
       if (r < 4 * h.max_contacts && elliptic_group(c, r >> 2)) {   // force = -grad of the cone cost

@@ -360,7 +360,7 @@ HAND_CUBE = 0.07
 HAND_CUBE_Y = 0.025   # cube centre towards the finger roots: curled fingers reach its +y face
 
 
-def hand(max_contacts: int = 20, cone: int = PYRAMIDAL) -> Model:
+def hand(max_contacts: int = 20, cone: int = PYRAMIDAL, frictionloss: float = 0.0) -> Model:
     """Fixed-base 16-hinge hand with a free 7 cm cube (LEAP-like, App. C.2).  World-fixed palm box
     0.12x0.10x0.02 m with its top face at z = 0; 4 fingers rooted on the palm's +y edge, each a
     chain of 4 capsule phalanges (r 0.01; 0.05/0.04/0.035/0.03 m, 0.05/0.04/0.03/0.02 kg) with
@@ -368,7 +368,9 @@ def hand(max_contacts: int = 20, cone: int = PYRAMIDAL) -> Model:
     inertia on every dof from the paper's servo numbers.  The cube rests on the palm near the
     finger roots (centre y = 0.025).  Contacts: fingertip spheres and the
     capsules of the last three phalanges against the cube, cube against palm; at most 20 active,
-    friction 1, pyramidal cone.  PD kp 3 kd 0.1; dt 5 ms, 10 substeps, Newton cap 6."""
+    friction 1, pyramidal cone.  PD kp 3 kd 0.1; dt 5 ms, 10 substeps, Newton cap 6.
+    `frictionloss` > 0 gives every hinge that joint friction loss (App. C.2.2 sets it to a tenth of
+    the servo's maximum torque)."""
     b = ModelBuilder("hand")
     palm = b.geom(0, BOX, (0.06, 0.05, 0.01), pos=(0, 0, -0.01))
     tips, caps = [], []
@@ -377,9 +379,11 @@ def hand(max_contacts: int = 20, cone: int = PYRAMIDAL) -> Model:
         for s, (L, m) in enumerate(HAND_PHALANX):
             link = b.body(parent, pos)
             if s == 0:
-                b.joint(link, HINGE, axis=(0, 0, 1), limited=True, range=(-0.5, 0.5), rotor=HAND_ROTOR)
+                b.joint(link, HINGE, axis=(0, 0, 1), limited=True, range=(-0.5, 0.5), rotor=HAND_ROTOR,
+                        frictionloss=frictionloss)
             else:
-                b.joint(link, HINGE, axis=(1, 0, 0), limited=True, range=(-0.3, 1.6), rotor=HAND_ROTOR)
+                b.joint(link, HINGE, axis=(1, 0, 0), limited=True, range=(-0.3, 1.6), rotor=HAND_ROTOR,
+                        frictionloss=frictionloss)
             g = b.geom(link, CAPSULE, (0.01, L / 2), pos=(0, L / 2, 0), quat=_ROT_Z_TO_Y, mass=m)
             if s > 0:
                 caps.append(g)
@@ -680,20 +684,27 @@ def commands(config: int, n_envs: int, env0: int = 0, draw: int = 0) -> np.ndarr
 
 
 def randomized_params(m: Model, config: int, n_envs: int, env0: int = 0) -> np.ndarray:
-    """Per-environment physical parameters [N, 2 + 3 nbody + nv + nu] float32 in the layout of
-    pg_step_dr: friction scale U[0.6, 1.4], payload U[0, 2] kg on body 1, centre-of-mass offsets
-    U(+-2 cm), added armature U[0, 0.01] kg m^2, calibration offsets U(+-0.05) rad; draw index
+    """Per-environment physical parameters [N, 2 + 4 nbody + 2 nv + 3 nu] float32 in the layout
+    of pg_step_dr: friction scale U[0.6, 1.4], payload U[0, 2] kg on body 1, centre-of-mass
+    offsets U(+-2 cm), added armature U[0, 0.01] kg m^2, calibration offsets U(+-0.05) rad, kp and
+    kd scales U(+-20 %), link mass scales U(+-10 %), friction-loss scales U(+-50 %); draw index
     2^34 + k of each env's stream."""
     nb, nv, nu = m.nbody, m.nv, m.nu
-    k = 2 + 3 * nb + nv + nu
+    k = 2 + 4 * nb + 2 * nv + 3 * nu
     seeds = env_seeds(config, n_envs, env0)[:, None]
     u = uniform01(seeds, np.uint64(1 << 34) + np.arange(k, dtype=np.uint64)[None, :])
+    sym = 2.0 * u - 1.0
     p = np.zeros((n_envs, k))
+    arm, cal = 2 + 3 * nb, 2 + 3 * nb + nv
+    kp, kd, ms, fl = cal + nu, cal + 2 * nu, cal + 3 * nu, cal + 3 * nu + nb
     p[:, 0] = 0.6 + 0.8 * u[:, 0]
     p[:, 1] = 2.0 * u[:, 1]
-    p[:, 2:2 + 3 * nb] = 0.02 * (2.0 * u[:, 2:2 + 3 * nb] - 1.0)
-    p[:, 2 + 3 * nb:2 + 3 * nb + nv] = 0.01 * u[:, 2 + 3 * nb:2 + 3 * nb + nv]
-    p[:, 2 + 3 * nb + nv:] = 0.05 * (2.0 * u[:, 2 + 3 * nb + nv:] - 1.0)
+    p[:, 2:arm] = 0.02 * sym[:, 2:arm]
+    p[:, arm:cal] = 0.01 * u[:, arm:cal]
+    p[:, cal:kp] = 0.05 * sym[:, cal:kp]
+    p[:, kp:ms] = 0.2 * sym[:, kp:ms]
+    p[:, ms:fl] = 0.1 * sym[:, ms:fl]
+    p[:, fl:] = 0.5 * sym[:, fl:]
     return _f32(p)
 
 

@@ -121,11 +121,9 @@ def test_friction_loss_rows_and_scope():
     m.dof_frictionloss = np.zeros(m.nv, np.float32); m.dof_frictionloss[6:] = 0.5
     s = core.CompiledModel(m).sizes
     assert s.nrow_max == 4 * 4 + 12 + 12 and s.adjoint_workspace_bytes > 0
-    h = W.hand_elliptic()
-    h.dof_frictionloss = np.full(h.nv, 0.1, np.float32)
-    with pytest.raises(_capi.PgError) as ei:
-        core.CompiledModel(h)
-    assert ei.value.code == _capi.PG_EUNSUPPORTED
+    h = W.hand(cone=W.ELLIPTIC, frictionloss=0.05)   # friction loss beside the elliptic cone
+    hs = core.CompiledModel(h).sizes
+    assert hs.nrow_max == core.CompiledModel(W.hand_elliptic()).sizes.nrow_max + 16
     m.dof_frictionloss[7] = -1.0
     with pytest.raises(_capi.PgError) as ei:
         core.CompiledModel(m)
@@ -136,7 +134,7 @@ def test_per_environment_parameter_rows():
     from paper_2502_08844_b300 import core
     for f in (W.quadruped, W.cartpole, W.humanoid):
         m = f()
-        assert core.CompiledModel(m).sizes.nrand == 2 + 3 * m.nbody + m.nv + m.nu
+        assert core.CompiledModel(m).sizes.nrand == 2 + 4 * m.nbody + 2 * m.nv + 3 * m.nu
     q = W.quadruped()
     q.act_forcelimited = np.ones(q.nu, np.int32)
     q.act_forcerange = np.tile(np.array([[4.0, -4.0]], np.float32), (q.nu, 1))

@@ -53,7 +53,7 @@ def test_nominal_parameters_equal_the_plain_step():
     n = 64
     q0, v0 = W.initial_state(m, 1, n)
     U = W.actions(m, 1, n, 0, 5)
-    P = np.zeros((n, m.nbody * 3 + 2 + m.nv + m.nu), np.float32); P[:, 0] = 1.0
+    P = np.zeros((n, RZ.nrand(m)), np.float32); P[:, 0] = 1.0
     qd, vd, _ = _run_dr(m, q0, v0, U, P, 5)
     run = GpuRun(m, n)
     run.set_state(q0, v0)
@@ -108,3 +108,26 @@ def test_step_dr_argument_errors():
     rc = _capi._lib.pg_step_dr(run.batch.handle, run.state.c(), run.ctrl_tensor(np.zeros((8, 12))).data_ptr(),
                                None, 5, None)
     assert rc == _capi.PG_EINVAL
+
+
+@pytest.mark.parametrize("specialize", [False, True])
+def test_step_dr_elliptic_hand_with_friction_loss(specialize):
+    """The hand's randomisation (App. C.2): PD gains, link masses and motor friction (friction-loss
+    scales) beside the locomotion set, on the elliptic hand with friction loss on its sixteen
+    hinges, one control step against each environment's substituted oracle model."""
+    m = W.hand(cone=W.ELLIPTIC, frictionloss=0.05)
+    n = 24
+    q0, v0 = W.initial_state(m, 2, n)
+    U = W.actions(m, 2, n, 0, 1)
+    P = W.randomized_params(m, 2, n)
+    R = RZ.rows(m)
+    qg, vg, _ = _run_dr(m, q0, v0, U, P, 1, specialize=specialize)
+    for e in range(n):
+        qo, vo = _oracle_env(m, q0[e], v0[e], U[:, e:e + 1], P[e], 1)
+        assert_close_scaled("qpos env %d" % e, canon_qpos(m, qg[e]), canon_qpos(m, qo), ONE_STEP_RTOL)
+        assert_close_scaled("qvel env %d" % e, vg[e], vo, ONE_STEP_RTOL)
+    # the new groups matter: with them zeroed the oracle ends elsewhere
+    P0 = P.copy(); P0[:, R["kp"]:] = 0.0
+    moved = max(np.abs(_oracle_env(m, q0[e], v0[e], U[:, e:e + 1], P0[e], 1)[0]
+                       - _oracle_env(m, q0[e], v0[e], U[:, e:e + 1], P[e], 1)[0]).max() for e in range(4))
+    assert moved > 1e-5

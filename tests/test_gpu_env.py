@@ -224,7 +224,8 @@ def test_env_step_argument_errors():
 
 def test_env_step_with_per_environment_parameters():
     """pg_env_step with a per-environment parameter block: each environment against the oracle's
-    task on its substituted model (oracle.randomize), calibration offsets included."""
+    task on its substituted model (oracle.randomize), calibration offsets and PD gain scales (in
+    the physics and in the reward's PD torques) included."""
     O, E = _oracle()
     from oracle import randomize as RZ
     task = W.quadruped_task(episode_length=50)
@@ -242,5 +243,6 @@ def test_env_step_with_per_environment_parameters():
     nb, nv = S.m.nbody, S.m.nv
     for e in range(S.n):
         ot = E.OracleTask(O.OracleModel(RZ.substituted_model(S.m, P[e])), task)
-        ot.calibration = P[e, 2 + 3 * nb + nv:].astype(np.float64)
+        r = RZ.rows(S.m)["calibration"]
+        ot.calibration = P[e, r:r + S.m.nu].astype(np.float64)
         _compare_env(ot, g, e, pre, S.U[0][e], S.cmd[e], S.q0[e], S.v0[e], np.zeros(nv))

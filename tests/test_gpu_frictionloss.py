@@ -1,14 +1,15 @@
 """GPU parity of joint friction loss (friction-loss rows) against the FP64 oracle through the C
 ABI: every phase of a substep, including the rows' Jacobian, reference acceleration, D, Ahat
-and force, on a one-joint arm and on the quadruped with friction loss on its twelve hinges; one
-control step and 50-step rollouts at the step tolerances; specialised against generic."""
+and force, on a one-joint arm, on the quadruped with friction loss on its twelve hinges and on
+the elliptic-cone hand with friction loss on its sixteen (App. C.2.2); one control step and
+rollouts at the step tolerances; specialised against generic."""
 import numpy as np
 import pytest
 
 from oracle import oracle as O
 from paper_2502_08844_b300 import core, workloads as W
 from tests.gpu_helpers import GpuRun, canon_qpos
-from tests.test_gpu_parity import ONE_STEP_RTOL, ROLLOUT_RTOL, _phase_compare, assert_close_scaled
+from tests.test_gpu_parity import ONE_STEP_RTOL, ROLLOUT_RTOL, _phase_compare, _rollout_states, assert_close_scaled
 
 pytestmark = pytest.mark.gpu
 
@@ -84,3 +85,55 @@ def test_specialised_friction_loss_matches_generic():
         outs.append(run.get())
     for a, b in zip(outs[0], outs[1]):
         assert np.allclose(a, b, rtol=1e-4, atol=1e-5)
+
+
+# The elliptic hand with friction loss on every hinge: a tenth of the servo's maximum torque
+# (App. C.2.2), taken as 0.05 N m for the hand's 3 N m/rad PD servos
+HAND_FRICTIONLOSS = 0.05
+
+
+def _elliptic_hand_with_friction():
+    return W.hand(cone=W.ELLIPTIC, frictionloss=HAND_FRICTIONLOSS)
+
+
+def test_phase_parity_elliptic_hand_with_friction_loss():
+    """Elliptic contacts and friction-loss rows in one solve: every phase, the rows and their
+    forces, on states along a grasp."""
+    m = _elliptic_hand_with_friction()
+    om, states = _rollout_states(m, 2, (0, 6, 30))
+    nrows = []
+    for q, v, u in states:
+        g, o = _phase_compare(m, om, q, v, u, env=1, n=4)
+        nrows.append(g["nrow"])
+    assert min(nrows) >= 16                          # the sixteen friction-loss rows at least
+    assert max(nrows) >= 16 + 6                      # and elliptic contacts
+
+
+@pytest.mark.parametrize("specialize", [pytest.param(False, id="generic"), pytest.param(True, id="specialised")])
+def test_elliptic_hand_with_friction_loss_one_step_and_reanchored(specialize):
+    """One control step on 40 environments at the one-step tolerance, then 20 more steps on 16 of
+    them, each compared with the oracle's step from the GPU's own state (re-anchored, as the
+    elliptic hand's long rollouts are).  qvel's scale is the larger of |qvel| and the step's
+    velocity change: friction loss holds joints nearly still (|qvel| small) while the substeps'
+    h qacc terms, whose FP32 rounding reaches qvel, stay as large as without it."""
+    m = _elliptic_hand_with_friction()
+    om = O.OracleModel(m)
+    n = 40
+    q0, v0 = W.initial_state(m, 2, n)
+    U = W.actions(m, 2, n, 0, 21)
+    run = GpuRun(m, n, specialize=specialize)
+    run.set_state(q0, v0)
+    q, v, w = q0.astype(np.float64), v0.astype(np.float64), np.zeros((n, m.nv))
+    for t in range(21):
+        run.step(U[t], m.n_substeps)
+        qg, vg, wg = run.get()
+        qo, vo, _, _ = om.rollout(q, v, U[t:t + 1], m.n_substeps, qacc_warm=w, nthreads=8)
+        for e in range(n if t == 0 else 16):
+            assert_close_scaled("step %d qpos env %d" % (t, e), canon_qpos(m, qg[e]), canon_qpos(m, qo[e]), ONE_STEP_RTOL)
+            vscale = max(np.abs(vo[e]).max(), np.abs(vo[e] - v[e]).max())
+            assert_close_scaled("step %d qvel env %d" % (t, e), vg[e], vo[e], ONE_STEP_RTOL, scale=vscale)
+        q, v, w = qg, vg, wg
+    # the loss matters: without it the first step already ends elsewhere
+    qf, _, _, _ = O.OracleModel(W.hand_elliptic()).rollout(q0, v0, U[:1], m.n_substeps, nthreads=8)
+    qo1, _, _, _ = om.rollout(q0, v0, U[:1], m.n_substeps, nthreads=8)
+    assert np.abs(qf - qo1).max() > 1e-5

@@ -78,3 +78,31 @@ def test_newton_matches_a_general_minimiser():
         assert _cost(M, a0, J, aref, D, kind, mu, a) <= res.fun + 1e-10
         assert np.allclose(a, res.x, atol=1e-5)
         assert np.all(np.abs(force[kind == 3]) <= mu[kind == 3] + 1e-12)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_newton_with_elliptic_contacts_and_friction_loss_matches_a_general_minimiser(seed):
+    """Friction-loss rows beside elliptic contacts (the elliptic hand with joint friction loss):
+    the line search then walks the smooth convex phi(alpha), whose derivative takes each
+    friction-loss row's D x inside its band and its bound +-F beyond.  The converged Newton solve
+    equals BFGS on the same cost.  A line search that treats those rows as one-sided (a force only
+    for x < 0) stops at the wrong alpha and fails here."""
+    rng = np.random.default_rng(40 + seed)
+    nv = 6
+    Q = rng.normal(size=(nv, nv))
+    M = Q @ Q.T + nv * np.eye(nv)
+    a0 = rng.normal(size=nv) * 2
+    kind = np.array([1, 2, 2, 3, 3, 1, 2, 2, 3], np.int32)
+    nr = kind.size
+    J = rng.normal(size=(nr, nv))
+    aref = rng.normal(size=nr) * 3
+    D = np.r_[[1.3] * 3, rng.uniform(0.5, 4.0, 2), [0.7] * 3, rng.uniform(0.5, 4.0, 1)]
+    mu = np.r_[[0.9] * 3, rng.uniform(0.1, 1.5, 2), [0.4] * 3, rng.uniform(0.1, 1.5, 1)]
+    a, force, it, conv = O.solve(M, a0, J, aref, D, cap=-1, kind=kind, mu=mu)
+    assert conv
+    f = lambda x: _cost(M, a0, J, aref, D, kind, mu, x)
+    res = minimize(f, a0, method="BFGS", options={"gtol": 1e-12, "maxiter": 10000})
+    assert f(a) <= res.fun + 1e-10 * (1 + abs(res.fun))
+    np.testing.assert_allclose(a, res.x, rtol=1e-5, atol=1e-6)
+    fr = kind == 3
+    assert np.all(np.abs(force[fr]) <= mu[fr] + 1e-12)

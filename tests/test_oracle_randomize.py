@@ -112,7 +112,7 @@ def _pd_arm(forcelimited=False):
 
 def test_calibration_offset_shifts_the_pd_equilibrium():
     m = _pd_arm()
-    p = RZ.nominal(m); p[-1] = 0.07
+    p = RZ.nominal(m); p[RZ.rows(m)["calibration"]] = 0.07
     om = O.OracleModel(RZ.substituted_model(m, p))
     u = RZ.controls(m, p, np.full((3000, 1, 1), 0.3))
     q, v, _, _ = om.rollout(np.zeros((1, 1)), np.zeros((1, 1)), u, 1)
@@ -125,3 +125,66 @@ def test_torque_limits_clip_the_pd_force(err, expect):
     m = _pd_arm(forcelimited=True)
     f = O.OracleModel(m).forward(np.zeros(1), np.zeros(1), None, np.array([err]))
     assert f["actuator"][0] == pytest.approx(expect)
+
+
+def test_pd_gain_scales_multiply_kp_and_kd():
+    """tau = kp (1 + s_p) (u - q) - kd (1 + s_d) qd at a state with both terms non-zero (a swapped
+    pair of rows or an additive reading fails)."""
+    m = _pd_arm()
+    R = RZ.rows(m)
+    p = RZ.nominal(m); p[R["kp"]] = 0.3; p[R["kd"]] = -0.4
+    q, qd, u = 0.1, 0.7, 0.35
+    f = O.OracleModel(RZ.substituted_model(m, p)).forward(np.array([q]), np.array([qd]), None, np.array([u]))
+    assert f["actuator"][0] == pytest.approx(20.0 * 1.3 * (u - q) - 1.0 * 0.6 * qd, rel=1e-12)
+
+
+def test_link_mass_scale_scales_mass_and_inertia():
+    """A single free body: every entry of its mass matrix scales by 1 + s (mass and the inertia
+    about the centre of mass both), and resting on a plane the contacts carry (1 + s) m g."""
+    m = _box_on_plane()
+    R = RZ.rows(m)
+    p = RZ.nominal(m); p[R["mass"] + 1] = 0.25
+    q = np.array([0.1, -0.2, 0.3, np.cos(0.4), np.sin(0.4) * 0.6, 0.0, np.sin(0.4) * 0.8])
+    M0 = O.OracleModel(m).mass_matrix(q)
+    M1 = O.OracleModel(RZ.substituted_model(m, p)).mass_matrix(q)
+    np.testing.assert_allclose(M1, 1.25 * M0, rtol=1e-12, atol=1e-15)
+    om, qs, vs = _settle(m, p)
+    assert _normal_force(om, qs, vs) == pytest.approx(1.25 * 2.0 * 9.81, rel=1e-6)
+
+
+def test_link_mass_scale_comes_before_the_payload():
+    """body 1's mass is (1 + s) m + payload: the payload is not scaled."""
+    m = _box_on_plane()
+    R = RZ.rows(m)
+    p = RZ.nominal(m); p[R["mass"] + 1] = -0.5; p[1] = 1.0
+    om, qs, vs = _settle(m, p)
+    assert _normal_force(om, qs, vs) == pytest.approx((0.5 * 2.0 + 1.0) * 9.81, rel=1e-6)
+
+
+def test_friction_loss_scale_sets_the_sliding_deceleration():
+    """A spinning joint with friction loss F and scale s decelerates at F (1 + s) / I."""
+    b = W.ModelBuilder("fric_arm")
+    link = b.body(0, (0, 0, 0))
+    b.joint(link, W.HINGE, axis=(0, 0, 1), frictionloss=0.3)
+    b.geom(link, W.BOX, (0.2, 0.05, 0.05), pos=(0.2, 0, 0), mass=2.0)
+    b.actuator(0, W.MOTOR, gear=1.0)
+    m = b.build(timestep=0.002, gravity=(0, 0, 0), iterations=50)
+    R = RZ.rows(m)
+    p = RZ.nominal(m); p[R["frictionloss"]] = 0.6
+    om = O.OracleModel(RZ.substituted_model(m, p))
+    I = om.mass_matrix(np.zeros(1))[0, 0]
+    f = om.forward(np.zeros(1), np.array([2.0]), None, np.array([0.0]), solver_cap=-1)
+    assert f["qacc"][0] == pytest.approx(-float(np.float32(0.3)) * 1.6 / I, rel=1e-9)
+
+
+def test_parameter_rows_partition_the_block():
+    """the groups' first rows tile [0, nrand) in the documented order"""
+    m = W.quadruped()
+    R = RZ.rows(m)
+    sizes = {"friction": 1, "payload": 1, "com": 3 * m.nbody, "armature": m.nv, "calibration": m.nu,
+             "kp": m.nu, "kd": m.nu, "mass": m.nbody, "frictionloss": m.nv}
+    at = 0
+    for k in ("friction", "payload", "com", "armature", "calibration", "kp", "kd", "mass", "frictionloss"):
+        assert R[k] == at
+        at += sizes[k]
+    assert at == RZ.nrand(m)
