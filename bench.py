@@ -175,17 +175,19 @@ def cpu_baseline(model: W.Model, cfg: int, n_envs: int, budget_s: float = 10.0, 
 
 
 def measure_mixed(dev, steps: int = 200, specialize: bool = True):
-    """Mixed-model batch: 4096 cartpoles + 4096 quadrupeds + 2048 humanoids in one launch per
-    control step (each env with its own model's timestep and substeps), a 200-step rollout
-    captured in a CUDA graph, launch shape from the autotuner."""
+    """Mixed-model batch: 4096 cartpoles + 4096 quadrupeds + 2048 humanoids (each env with its
+    own model's timestep and substeps), a 200-step rollout captured in a CUDA graph.  Specialised:
+    the kernel and launch shape the autotuner picks among the branch-parallel, specialised
+    thread-per-environment and generic kernels; generic: the one launch of the library's kernel
+    over every model, at the autotuner's shape for that kernel."""
     import torch
     from paper_2502_08844_b300 import core, rollout
     comp = [("cartpole", 0, 4096), ("quadruped", 1, 4096), ("humanoid", 3, 2048)]
     models = [(core.CompiledModel(W.model(nm)), n) for nm, _, n in comp]
-    epc = rollout.autotune(models)
-    batch = core.Batch(models, envs_per_cta=epc)
-    if specialize:
-        batch.specialize()   # one specialised kernel per model over its own blocks
+    choice = rollout.autotune(models, kernels=rollout.KERNELS if specialize else ("generic",))
+    batch = rollout.make_batch(models, choice)
+    epc = choice[1]
+    specialize = choice[0] != "generic"
     st = core.State(batch, dev)
     ld = st.ld
     Q = np.zeros((batch.nq_max, ld), np.float32)
@@ -221,7 +223,8 @@ def measure_mixed(dev, steps: int = 200, specialize: bool = True):
                        "branch-parallel kernel for %d of the %d models" % (k["branch_parts"], len(comp))) if specialize
                       else "generic (one body shared by the batch's models)",
             "composition": {nm: n for nm, _, n in comp}, "steps": steps, "cuda_graph": True,
-            "envs_per_cta": epc or "default (one wave)", "launches": steps * (len(comp) if specialize else 1)}
+            "autotuned": {"kernel": choice[0], "envs_per_cta": epc or "default (one wave)"},
+            "launches": steps * (len(comp) if specialize else 1)}
 
 
 def measure_env_layer(dev, n: int = 8192, steps: int = 200, specialize: bool = True):

@@ -1,13 +1,21 @@
-"""Rollouts captured in CUDA graphs, and the launch-shape autotuner.
+"""Rollouts captured in CUDA graphs, and the launch autotuner.
 
 A rollout of T control steps is T launches of the fused step kernel (one per control step,
 each running its model's substeps on chip).  Capturing them in a CUDA graph removes the
 per-launch host cost, which matters for small batches and short steps.
 
-The autotuner picks the environments-per-block of a batch (the kernel runs one environment
-per thread; a block holds up to 8 warps of `soa` environments each, `soa` fixed per model by its
-shared-memory workspace).  It times a few candidate shapes on the device and caches the
-fastest per (model tables, counts, GPU name) in a JSON file.
+The autotuner picks, per batch composition, the kernel and the launch shape:
+
+* the kernel: the branch-parallel one (a thread per environment and branch) in blocks that meet
+  at a barrier every substep or in one-warp blocks, where some model of the batch qualifies;
+  the model-specialised thread-per-environment kernel; or the library's generic kernel;
+* the environments per block of the thread-per-environment kernels (one environment per
+  thread; a block holds up to 8 warps of `soa` environments each, `soa` fixed per model by its
+  shared-memory workspace): one wave over all SMs, or multiples of 16 around one and two waves
+  whose workspace fits shared memory.
+
+It times every candidate on the device, on the kernels that will run, and caches the fastest
+per (model tables, counts, GPU name) in a JSON file.
 """
 from __future__ import annotations
 
@@ -60,7 +68,7 @@ def _key(models: Sequence[core.CompiledModel], counts: Sequence[int]) -> str:
     return h.hexdigest()[:24] + "@" + torch.cuda.get_device_name()
 
 
-def _load() -> Dict[str, int]:
+def _load() -> dict:
     try:
         with open(_CACHE) as f:
             return json.load(f)
@@ -68,7 +76,7 @@ def _load() -> Dict[str, int]:
         return {}
 
 
-def _save(d: Dict[str, int]) -> None:
+def _save(d: dict) -> None:
     try:
         os.makedirs(os.path.dirname(_CACHE), exist_ok=True)
         with open(_CACHE, "w") as f:
@@ -77,30 +85,64 @@ def _save(d: Dict[str, int]) -> None:
         pass
 
 
+KERNELS = ("branch", "branch-warp", "thread", "generic")
+SMEM_PER_BLOCK = 227 * 1024
+
+
+def _up16(x: int) -> int:
+    return max(16, (x + 15) // 16 * 16)
+
+
 def candidate_shapes(models: Sequence[core.CompiledModel], counts: Sequence[int], sms: int) -> List[int]:
-    """envs-per-block candidates: 0 (one wave over all SMs, the library default) and multiples of
-    the smallest SoA width, up to what shared memory admits."""
-    out = [0]
-    for e in (16, 32, 48, 64, 96, 128):
-        if e not in out:
-            out.append(e)
+    """envs-per-block candidates of the thread-per-environment kernels: 0 (one wave over all SMs,
+    the library default), 16, 32, 64, 128 and the multiples of 16 nearest one and two waves, each
+    no more than 256 (8 warps) and with the largest model's workspace fitting shared memory."""
+    ws = max(max(m.sizes.workspace_bytes for m in models), 1)
+    fit = min(256, SMEM_PER_BLOCK // ws // 16 * 16)
+    total = max(sum(counts), 1)
+    wave = -(-total // sms)
+    cands = {16, 32, 64, 128, _up16(wave), _up16(-(-wave // 2))}
+    return [0] + sorted(e for e in cands if 16 <= e <= fit)
+
+
+def candidates(models: Sequence[core.CompiledModel], counts: Sequence[int], sms: int,
+               kernels: Sequence[str] = KERNELS) -> List[Tuple[str, int]]:
+    """(kernel, envs per block) pairs to time; the branch-parallel kernels only where some model
+    qualifies (they launch their own parts with their own shapes; the shape applies to the rest)."""
+    shapes = candidate_shapes(models, counts, sms)
+    branch = any(m.branch_plan()["branch"] for m in models)
+    out = []
+    for k in kernels:
+        if k.startswith("branch") and not branch:
+            continue
+        out += [(k, e) for e in shapes]
     return out
 
 
+def make_batch(parts: Sequence[Tuple[core.CompiledModel, int]], choice: Tuple[str, int]) -> core.Batch:
+    """The batch of `parts` compiled for an autotuner choice (kernel, envs per block)."""
+    kernel, e = choice
+    batch = core.Batch(parts, envs_per_cta=e)
+    if kernel != "generic":
+        batch.specialize(branch=kernel.startswith("branch"), warp_blocks=kernel == "branch-warp")
+    return batch
+
+
 def autotune(parts: Sequence[Tuple[core.CompiledModel, int]], n_substeps: int = 0, steps: int = 4,
-             use_cache: bool = True) -> int:
-    """Return the fastest envs_per_cta for this batch composition (0 = library default)."""
+             use_cache: bool = True, kernels: Sequence[str] = KERNELS) -> Tuple[str, int]:
+    """The fastest (kernel, envs per block) for this batch composition (make_batch builds it).
+    Run-time compilations happen here, once per model and kernel (cached on disk)."""
     models = [m for m, _ in parts]
     counts = [n for _, n in parts]
-    key = _key(models, counts)
+    key = _key(models, counts) + "/" + ",".join(kernels)
     cache = _load() if use_cache else {}
-    if key in cache:
-        return int(cache[key])
+    if isinstance(cache.get(key), list):
+        return (str(cache[key][0]), int(cache[key][1]))
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    best, best_t = 0, float("inf")
-    for e in candidate_shapes(models, counts, sms):
+    best, best_t = ("generic", 0), float("inf")
+    for choice in candidates(models, counts, sms, kernels):
         try:
-            batch = core.Batch(parts, envs_per_cta=e)
+            batch = make_batch(parts, choice)
         except Exception:
             continue
         st = core.State(batch)
@@ -119,8 +161,8 @@ def autotune(parts: Sequence[Tuple[core.CompiledModel, int]], n_substeps: int = 
         torch.cuda.synchronize()
         t = a.elapsed_time(b)
         if t < best_t:
-            best, best_t = e, t
-    cache[key] = best
+            best, best_t = choice, t
+    cache[key] = list(best)
     if use_cache:
         _save(cache)
     return best

@@ -38,16 +38,20 @@ def test_graph_replay_equals_eager_rollout():
         assert np.array_equal(qa, qb) and np.array_equal(va, vb)
 
 
-def test_autotune_returns_a_working_shape(tmp_path, monkeypatch):
+def test_autotune_returns_a_working_choice(tmp_path, monkeypatch):
+    """The autotuner's (kernel, envs per block) is one of its candidates, is cached, and its batch
+    steps as the generic kernel's does (to rounding: the kernels order their arithmetic
+    differently; bitwise where it picked the generic kernel)."""
     monkeypatch.setattr(rollout, "_CACHE", str(tmp_path / "autotune.json"))
     parts = [(core.CompiledModel(W.quadruped()), 300), (core.CompiledModel(W.cartpole()), 200)]
-    e = rollout.autotune(parts)
-    assert e in rollout.candidate_shapes([m for m, _ in parts], [n for _, n in parts], 148)
-    assert rollout.autotune(parts) == e           # cached
-    # the tuned shape gives the same results as the default shape
+    choice = rollout.autotune(parts)
+    models, counts = [m for m, _ in parts], [n for _, n in parts]
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert choice in rollout.candidates(models, counts, sms)
+    assert rollout.autotune(parts) == choice           # cached
+    assert ("branch", 0) in rollout.candidates(models, counts, sms)   # the quadruped qualifies
     outs = []
-    for epc in (0, e):
-        b = core.Batch(parts, envs_per_cta=epc)
+    for b in (core.Batch(parts), rollout.make_batch(parts, choice)):
         st = core.State(b)
         q0, v0 = W.initial_state(W.quadruped(), 1, 300)
         st.qpos[:19, :300] = torch.from_numpy(q0.T).cuda()
@@ -55,4 +59,17 @@ def test_autotune_returns_a_working_shape(tmp_path, monkeypatch):
         ctrl[:, :300] = torch.from_numpy(W.actions(W.quadruped(), 1, 300, 0, 1)[0].T).cuda()
         core.step(b, st, ctrl, 0)
         outs.append(st.qpos[:, :300].cpu().numpy())
-    assert np.array_equal(outs[0], outs[1])
+    if choice[0] == "generic":
+        assert np.array_equal(outs[0], outs[1])
+    else:
+        np.testing.assert_allclose(outs[1], outs[0], rtol=1e-5, atol=1e-6)
+
+
+def test_autotune_generic_only_and_shapes():
+    """The kernel list restricts the search; the shapes fit shared memory and 8 warps."""
+    parts = [(core.CompiledModel(W.humanoid()), 100)]
+    models = [m for m, _ in parts]
+    shapes = rollout.candidate_shapes(models, [100], 148)
+    ws = models[0].sizes.workspace_bytes
+    assert shapes[0] == 0 and all(16 <= e <= 256 and e * ws <= rollout.SMEM_PER_BLOCK for e in shapes[1:])
+    assert all(k == "generic" for k, _ in rollout.candidates(models, [100], 148, ("generic",)))
