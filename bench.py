@@ -403,7 +403,8 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def measure_adjoint(dev, n: int = 4096, steps: int = 64, segment: int = 8, reps: int = 3, specialize: bool = True):
+def measure_adjoint(dev, n: int = 4096, steps: int = 64, segment: int = 8, reps: int = 3, specialize: bool = True,
+                    branch: bool = True):
     """Full rollout gradient against the forward rollout on the adjoint workload: 4096
     quadrupeds, 64 control steps, loss sum_t (z_t - 0.27)^2 + |v_t - (0.5, 0, 0)|^2 of the torso
     height and linear velocity, gradients with respect to the initial state, all 64 x 12
@@ -414,8 +415,8 @@ def measure_adjoint(dev, n: int = 4096, steps: int = 64, segment: int = 8, reps:
     m = W.quadruped()
     cm = core.CompiledModel(m)
     batch = core.Batch([(cm, n)])
-    if specialize:
-        batch.specialize()   # forward, tape replay and reverse sweep compiled for the model
+    if specialize:   # forward, tape replay and reverse sweep compiled for the model
+        batch.specialize(branch=branch)
     st = core.State(batch, dev)
     ld = st.ld
     q0, v0 = W.initial_state(m, 4, n)
@@ -459,7 +460,7 @@ def measure_adjoint(dev, n: int = 4096, steps: int = 64, segment: int = 8, reps:
     k = batch.kernel()
     return {"ratio": tg / tf, "forward_ms": tf, "gradient_ms": tg, "envs": n, "steps": steps, "segment": segment,
             "newton_cap": m.iterations,
-            "kernels": ("forward: %s; tape replay and reverse sweep: model-specialised thread-per-environment"
+            "kernels": ("forward and tape replay: %s; reverse sweep: model-specialised thread-per-environment"
                         % k["kernel"]) if specialize else "generic",
             "note": "gradient = checkpointed forward + loss + backward sweep"}
 
@@ -678,6 +679,9 @@ def run_ours(args):
         gen = measure_adjoint(dev, specialize=False)
         line["adjoint"]["generic_kernels"] = {"ratio": gen["ratio"], "forward_ms": gen["forward_ms"],
                                               "gradient_ms": gen["gradient_ms"]}
+        thr = measure_adjoint(dev, specialize=True, branch=False)
+        line["adjoint"]["thread_per_environment_kernels"] = {"ratio": thr["ratio"], "forward_ms": thr["forward_ms"],
+                                                             "gradient_ms": thr["gradient_ms"]}
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(m, cfg, n)
     print(json.dumps(line))

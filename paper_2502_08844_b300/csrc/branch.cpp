@@ -392,6 +392,9 @@ int branch_plan(const pg_model* m, std::string& src, std::string& why, int& lane
          "{ pgb::branch_step<false>(A); }");
   S.line("extern \"C\" __global__ void __launch_bounds__(256) pg_step_branch_sync(const __grid_constant__ pg::BranchArgs A) "
          "{ pgb::branch_step<true>(A); }");
+  if (m->hdr.adj_ok)   // the adjoint's tape replay (only for models inside its scope)
+    S.line("extern \"C\" __global__ void __launch_bounds__(256) pg_step_branch_tape(const __grid_constant__ pg::BranchArgs A) "
+           "{ pgb::branch_step<true, true>(A); }");
   src = S.s;
   return PG_OK;
 #undef TI
@@ -403,12 +406,17 @@ int branch_plan(const pg_model* m, std::string& src, std::string& why, int& lane
 // needs (at most 8), whose warps start every substep together.
 cudaError_t launch_branch_range(cudaKernel_t k, cudaKernel_t k_sync, int lanes, int64_t env0, int64_t count,
                                 const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st,
-                                const pg_step_out* out, int nslot) {
+                                const pg_step_out* out, int nslot, float* tape, int tape_rows, int tape_nq,
+                                int tape_nv) {
   if (count <= 0) return cudaSuccess;
   BranchArgs A;
   A.out_force = out ? out->contact_force : nullptr;
   A.out_ncon = out ? out->ncon : nullptr;
   A.out_nslot = nslot;
+  A.tape = tape;
+  A.tape_rows = tape_rows;
+  A.tape_nq = tape_nq;
+  A.tape_nv = tape_nv;
   A.qpos = s->qpos;
   A.qvel = s->qvel;
   A.warm = s->qacc_warm;
@@ -442,6 +450,12 @@ cudaError_t launch_branch(const pg_batch* b, const pg_state* s, const float* ctr
                           const pg_step_out* out) {
   return launch_branch_range(b->branch_kernel, b->branch_kernel_sync, b->branch_lanes, 0, s->n, s, ctrl, n_substeps,
                              st, out, b->nslot_max);
+}
+
+cudaError_t launch_branch_tape(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, float* tape,
+                               int tape_rows, cudaStream_t st) {
+  return launch_branch_range(nullptr, b->branch_kernel_tape, b->branch_lanes, 0, s->n, s, ctrl, n_substeps, st,
+                             nullptr, b->nslot_max, tape, tape_rows, b->nq_max, b->nv_max);
 }
 
 }  // namespace pg

@@ -1315,7 +1315,9 @@ __device__ __forceinline__ void substep(Lane& L, uint32_t& status, uint32_t cnt[
 // block's warps start every substep together (a barrier per substep), so that they run its long
 // straight-line phases close together and share their instruction fetches; a group past the
 // last environment then steps the last environment alongside (it writes nothing).
-template <bool SYNC>
+// SYNC: the block's warps meet at a barrier before every substep.  TAPE: also record the adjoint's
+// substep tape (A.tape); a separate instantiation, so the plain step's code is untouched by it.
+template <bool SYNC, bool TAPE = false>
 __device__ __forceinline__ void branch_step(const BranchArgs& A) {
   const int tid = threadIdx.x;
   Lane L;
@@ -1358,7 +1360,38 @@ __device__ __forceinline__ void branch_step(const BranchArgs& A) {
   const bool want = A.out_force || A.out_ncon;
   for (int s = 0; s < nsub; s++) {
     if (SYNC) __syncthreads();
+    float* tp = TAPE && active ? A.tape + (int64_t)s * A.tape_rows * ld + env : nullptr;
+    if (TAPE && tp) {   // the state the substep starts from (each lane its branch's dofs, lane 0 the trunk's)
+      if (L.br == 0) {
+#pragma unroll
+        for (int i = 0; i < NQT; i++) tp[kTQg[i] * ld] = L.qT[i];
+#pragma unroll
+        for (int t = 0; t < NT; t++) {
+          tp[(A.tape_nq + kTDg[t]) * ld] = L.vT[t];
+          tp[(A.tape_nq + A.tape_nv + kTDg[t]) * ld] = L.wT[t];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < NB; i++) {
+        const int gd = LV(kLDg, [i]), gq = LV(kLDq, [i]);
+        if (gd >= 0) {
+          tp[gq * ld] = L.qB[i];
+          tp[(A.tape_nq + gd) * ld] = L.vB[i];
+          tp[(A.tape_nq + A.tape_nv + gd) * ld] = L.wB[i];
+        }
+      }
+    }
     substep(L, status, cnt, want && s == nsub - 1 && active, A);
+    if (TAPE && tp) {   // the solver's acceleration (the next warm start)
+      if (L.br == 0)
+#pragma unroll
+        for (int t = 0; t < NT; t++) tp[(A.tape_nq + 2 * A.tape_nv + kTDg[t]) * ld] = L.wT[t];
+#pragma unroll
+      for (int i = 0; i < NB; i++) {
+        const int gd = LV(kLDg, [i]);
+        if (gd >= 0) tp[(A.tape_nq + 2 * A.tape_nv + gd) * ld] = L.wB[i];
+      }
+    }
   }
   if (!active) return;
   if (L.br == 0) {

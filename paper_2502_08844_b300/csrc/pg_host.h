@@ -71,6 +71,7 @@ struct pg_batch {
   cudaLibrary_t branch_lib = nullptr;
   cudaKernel_t branch_kernel = nullptr;
   cudaKernel_t branch_kernel_sync = nullptr;   // the same with a barrier per substep (the default launch)
+  cudaKernel_t branch_kernel_tape = nullptr;   // the barrier launch recording the adjoint's substep tape
   int branch_lanes = 0, branch_count = 0;
   std::string branch_why;   // why a requested branch kernel is not used
   // staging buffer of the host-buffer path (allocated on its first use)
@@ -106,7 +107,11 @@ cudaError_t launch_branch(const pg_batch* b, const pg_state* s, const float* ctr
                           const pg_step_out* out = nullptr);
 cudaError_t launch_branch_range(cudaKernel_t k, cudaKernel_t k_sync, int lanes, int64_t env0, int64_t count,
                                 const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st,
-                                const pg_step_out* out = nullptr, int nslot = 0);
+                                const pg_step_out* out = nullptr, int nslot = 0, float* tape = nullptr,
+                                int tape_rows = 0, int tape_nq = 0, int tape_nv = 0);
+// the branch-parallel step recording the adjoint's substep tape (layout of launch_step_tape)
+cudaError_t launch_branch_tape(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, float* tape,
+                               int tape_rows, cudaStream_t st);
 
 // kernel launchers (step.cu)
 cudaError_t launch_step(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st,

@@ -223,10 +223,12 @@ int compile_cubin(const pg_model* m, std::vector<char>& cubin) {
 // the branch-parallel kernel of a model, when it qualifies: lib and kernel set (else NULL, with the
 // reason in why)
 int compile_branch(const pg_model* m, bool warp_blocks, cudaLibrary_t& lib, cudaKernel_t& kernel,
-                   cudaKernel_t& kernel_sync, int& lanes, int& branches, std::string& why) {
+                   cudaKernel_t& kernel_sync, int& lanes, int& branches, std::string& why,
+                   cudaKernel_t* kernel_tape = nullptr) {
   lib = nullptr;
   kernel = nullptr;
   kernel_sync = nullptr;
+  if (kernel_tape) *kernel_tape = nullptr;
   std::string src;
   int threads = 0;
   if (branch_plan(m, src, why, lanes, threads, branches) != PG_OK) return PG_OK;
@@ -237,11 +239,13 @@ int compile_branch(const pg_model* m, bool warp_blocks, cudaLibrary_t& lib, cuda
   if (e != cudaSuccess) return set_error(PG_ECUDA, std::string("cudaLibraryLoadData: ") + cudaGetErrorString(e));
   e = cudaLibraryGetKernel(&kernel, lib, "pg_step_branch");
   if (e == cudaSuccess && !warp_blocks) e = cudaLibraryGetKernel(&kernel_sync, lib, "pg_step_branch_sync");
+  if (e == cudaSuccess && kernel_tape) e = cudaLibraryGetKernel(kernel_tape, lib, "pg_step_branch_tape");
   if (e != cudaSuccess) {
     cudaLibraryUnload(lib);
     lib = nullptr;
     kernel = nullptr;
     kernel_sync = nullptr;
+    if (kernel_tape) *kernel_tape = nullptr;
     return set_error(PG_ECUDA, std::string("branch kernel set-up: ") + cudaGetErrorString(e));
   }
   why.clear();
@@ -252,13 +256,15 @@ int compile_branch(const pg_model* m, bool warp_blocks, cudaLibrary_t& lib, cuda
 // goes to b->branch_why and the batch keeps its other kernels)
 int specialize_branch(pg_batch* b, bool warp_blocks) {
   cudaLibrary_t lib = nullptr;
-  cudaKernel_t k = nullptr, ks = nullptr;
+  cudaKernel_t k = nullptr, ks = nullptr, kt = nullptr;
   int lanes = 0, branches = 0;
-  const int rc = compile_branch(b->models[0], warp_blocks, lib, k, ks, lanes, branches, b->branch_why);
+  const int rc = compile_branch(b->models[0], warp_blocks, lib, k, ks, lanes, branches, b->branch_why,
+                                b->models[0]->hdr.adj_ok ? &kt : nullptr);
   if (rc != PG_OK || !k) return rc;
   b->branch_lib = lib;
   b->branch_kernel = k;
   b->branch_kernel_sync = ks;
+  b->branch_kernel_tape = kt;
   b->branch_lanes = lanes;
   b->branch_count = branches;
   return PG_OK;

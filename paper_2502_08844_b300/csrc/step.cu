@@ -86,6 +86,7 @@ cudaError_t launch_step(const pg_batch* b, const pg_state* s, const float* ctrl,
 
 cudaError_t launch_step_tape(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, float* tape,
                              int tape_rows, cudaStream_t st) {
+  if (b->branch_kernel_tape) return launch_branch_tape(b, s, ctrl, n_substeps, tape, tape_rows, st);
   if (b->spec_kernel_tape) return pyramidal::step_spec_tape(b, s, ctrl, n_substeps, tape, tape_rows, st);
   return b->has_elliptic ? elliptic::step_tape(b, s, ctrl, n_substeps, tape, tape_rows, st)
                          : pyramidal::step_tape(b, s, ctrl, n_substeps, tape, tape_rows, st);

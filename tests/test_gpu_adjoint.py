@@ -29,8 +29,10 @@ def gpu_rollout_grad(m: W.Model, q0, v0, U, weights, segment=8, specialize=False
     n, T = q0.shape[0], U.shape[0]
     cm = core.CompiledModel(m)
     batch = core.Batch([(cm, n)])
-    if specialize:
-        batch.specialize()
+    if specialize:   # True: the branch-parallel step and tape where the model qualifies; "thread": not
+        batch.specialize(branch=specialize != "thread")
+        if specialize is True and cm.branch_plan()["branch"]:
+            assert batch.kernel()["kernel"] == "branch-parallel"
     ld = max(4, (n + 3) // 4 * 4)
     dev = torch.device("cuda")
     qpos0 = torch.from_numpy(core.to_soa(q0.astype(np.float32), ld, batch.nq_max)).to(dev).requires_grad_()
@@ -83,10 +85,13 @@ def _converged(m: W.Model) -> W.Model:
     return dataclasses.replace(m, iterations=100)
 
 
-@pytest.mark.parametrize("specialize", [pytest.param(False, id="generic"), pytest.param(True, id="specialised")])
+@pytest.mark.parametrize("specialize", [pytest.param(False, id="generic"), pytest.param("thread", id="specialised"),
+                                        pytest.param(True, id="branch")])
 def test_quadruped_rollout_gradient_matches_oracle(specialize):
     """End to end over one checkpoint segment (8 control steps = 40 substeps with contacts), with
-    the library's compiled kernels and with the model-specialised ones the benchmark times."""
+    the library's compiled kernels, the model-specialised thread-per-environment ones, and the
+    branch-parallel step and tape replay the benchmark times (the reverse sweep is the
+    specialised one in both specialised cases)."""
     m = _converged(W.quadruped())
     n, T = 8, 8
     q0, v0 = W.initial_state(m, 4, n)
@@ -239,7 +244,7 @@ def test_single_control_step_vjp_at_contact_states():
             assert err <= 1e-4, (e, k, err)
 
 
-@pytest.mark.parametrize("T,specialize", [(16, False), (64, False), (64, True)])
+@pytest.mark.parametrize("T,specialize", [(16, False), (64, False), (64, "thread"), (64, True)])
 def test_quadruped_rollout_reanchored_on_gpu_trajectory(T, specialize):
     """Two and eight checkpoint segments (16 and 64 control steps: the adjoint workload's horizon).
     The oracle's per-step reverse sweep is chained along the GPU's own FP32 trajectory, so the

@@ -15,10 +15,12 @@ from paper_2502_08844_b300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def _setup(n=8, K=3):
+def _setup(n=8, K=3, specialize=False):
     m = dataclasses.replace(W.quadruped(), iterations=100)
     cm = core.CompiledModel(m)
     batch = core.Batch([(cm, n)])
+    if specialize:   # True: the branch-parallel tape replay; "thread": the specialised thread kernels
+        batch.specialize(branch=specialize is True)
     st = core.State(batch)
     ld = st.ld
     q0, v0 = W.initial_state(m, 4, n)
@@ -47,8 +49,10 @@ def _run(entry, batch, st, ctrl, gq, gv, aq, av):
     return [x.cpu().numpy() for x in (adj_q, adj_v, g_ctrl, g_par)]
 
 
-def test_noalloc_vjp_matches_vjp_on_two_calls_in_a_row():
-    batch, st, ctrl, gq, gv, aq, av = _setup()
+@pytest.mark.parametrize("specialize", [pytest.param(False, id="generic"), pytest.param("thread", id="specialised"),
+                                        pytest.param(True, id="branch")])
+def test_noalloc_vjp_matches_vjp_on_two_calls_in_a_row(specialize):
+    batch, st, ctrl, gq, gv, aq, av = _setup(specialize=specialize)
     q_before = st.qpos.clone()
     ref = _run(_capi.pg_step_vjp, batch, st, ctrl, gq, gv, aq, av)
     first = _run(_capi.pg_step_vjp_noalloc, batch, st, ctrl, gq, gv, aq, av)
@@ -58,6 +62,27 @@ def test_noalloc_vjp_matches_vjp_on_two_calls_in_a_row():
         assert np.array_equal(a, b)
         assert np.array_equal(a, c)
     assert torch.equal(st.qpos, q_before)   # the checkpoint is read only
+
+
+def test_noalloc_vjp_leaves_device_memory_unchanged():
+    """Free device memory is the same before and after two calls (after one warm-up call, which
+    may load the kernels' code), with every buffer allocated beforehand."""
+    batch, st, ctrl, gq, gv, aq, av = _setup()
+    K, ld = ctrl.shape[0], st.ld
+    g_ctrl = torch.zeros_like(ctrl)
+    g_par = torch.zeros((batch.nparam_max, ld), device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+
+    def call():
+        _capi.pg_step_vjp_noalloc(batch.handle, st.c(), ctrl.data_ptr(), K, 0, gq.data_ptr(), gv.data_ptr(),
+                                  aq.data_ptr(), av.data_ptr(), g_ctrl.data_ptr(), g_par.data_ptr(), s)
+    call()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    call()
+    call()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
 
 
 def test_noalloc_vjp_rejects_calls_beyond_its_scratch():
