@@ -65,7 +65,7 @@ extern "C" {
 /* ---- type codes ------------------------------------------------------------------- */
 enum { PG_JNT_FREE = 0, PG_JNT_HINGE = 1, PG_JNT_SLIDE = 2 };
 enum { PG_GEOM_PLANE = 0, PG_GEOM_SPHERE = 1, PG_GEOM_CAPSULE = 2, PG_GEOM_BOX = 3, PG_GEOM_HFIELD = 4,
-       PG_GEOM_CYLINDER = 5 };
+       PG_GEOM_CYLINDER = 5, PG_GEOM_MESH = 6 };
 enum { PG_ACT_MOTOR = 0, PG_ACT_POSITION = 1 };
 enum { PG_CONE_PYRAMIDAL = 0, PG_CONE_ELLIPTIC = 1 };
 
@@ -92,6 +92,9 @@ enum { PG_CONE_PYRAMIDAL = 0, PG_CONE_ELLIPTIC = 1 };
  *                                  A cylinder (PG_GEOM_CYLINDER) pairs as geom2 with a plane (4
  *                                  points: the deepest rim point of each cap and two more rim
  *                                  points of the lower cap, 120 degrees either side).
+ *                                  A heightfield also pairs as geom1 with boxes and convex meshes,
+ *                                  and a convex mesh (PG_GEOM_MESH) as geom2 with a plane (4 points
+ *                                  each; see the mesh fields below).
  *   pair_condim                    1 (frictionless) or 3 (pyramidal cone, 4 edge rows)
  *   act_jnt                        hinge or slide joint driven by the actuator
  *   solref = (timeconst, dampratio); solimp = (d0, dwidth, width, mid, power)
@@ -134,6 +137,27 @@ typedef struct pg_model_desc {
    * R = 1 / D: D x^2 / 2 while |x| <= R F, F |x| - R F^2 / 2 outside, so its force stays in
    * [-F, F].  With either cone. */
   const float* dof_frictionloss;
+  /* Convex meshes (PG_GEOM_MESH: rigid shapes beyond the primitives, as convex hulls; the
+   * heightfield's box pairs serve box feet on App. B.2.5's rough terrain): mesh k has mesh_vertnum[k] vertices, mesh_vert[3 (mesh_vertadr[k] + i) + 0..2] in the
+   * geom frame, and mesh_facenum[k] triangles, mesh_face[3 (mesh_faceadr[k] + f) + 0..2] (indices
+   * into the mesh's own vertices, counter-clockwise seen from outside), that bound the convex
+   * hull of those vertices.  geom_meshid[g] is the mesh of a mesh geom (ignored for other types).
+   * A mesh geom's mass properties (body_geom_inertia) are those of a uniform solid hull of mass
+   * geom_mass.  Contacts (4 slots a pair):
+   *   plane against mesh: the 4 deepest vertices (ties: lower index), kept in vertex order, each
+   *     at its distance to the plane along the plane's normal;
+   *   heightfield against box or mesh: the candidates are the solid's vertices over the grid, at
+   *     their signed distance to the plane of the triangle under them (that triangle's upward
+   *     normal), then the grid vertices inside the solid, at the depth of the nearest face
+   *     (normal: minus that face's outward normal; ties: lower face index), in row-major order;
+   *     the 4 deepest candidates (ties: candidate order) are kept in candidate order.
+   * Each contact point lies midway between the two surfaces.  At most 32 vertices and 64 faces
+   * a mesh.  PG_EINVAL when a face is not outward or a vertex lies outside a face's plane.
+   * Unused (0, NULL) without mesh geoms. */
+  int nmesh;
+  const int* mesh_vertadr; const int* mesh_vertnum; const float* mesh_vert;
+  const int* mesh_faceadr; const int* mesh_facenum; const int* mesh_face;
+  const int* geom_meshid;
 } pg_model_desc;
 
 typedef struct pg_model pg_model;   /* opaque, library-owned */

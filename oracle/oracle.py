@@ -38,6 +38,8 @@ class _Desc(C.Structure):
         ("hfield_nrow", C.c_int), ("hfield_ncol", C.c_int), ("hfield_data", _dp),
         ("act_forcelimited", _ip), ("act_forcerange", _dp),
         ("dof_frictionloss", _dp),
+        ("nmesh", C.c_int), ("mesh_vertadr", _ip), ("mesh_vertnum", _ip), ("mesh_vert", _dp),
+        ("mesh_faceadr", _ip), ("mesh_facenum", _ip), ("mesh_face", _ip), ("geom_meshid", _ip),
     ]
 
 
@@ -70,6 +72,8 @@ def lib(native: bool = False):
         L.orc_integrate_pos.argtypes = [C.c_void_p, _dp, _dp, C.c_double]
         L.orc_collide.argtypes = [C.c_int, _dp, _dp, _dp, C.c_int, _dp, _dp, _dp, _dp]
         L.orc_collide_hfield.argtypes = [_dp, _dp, _dp, C.c_int, C.c_int, _dp, C.c_int, _dp, _dp, _dp, _dp]
+        L.orc_collide_mesh.argtypes = [C.c_int, _dp, _dp, _dp, C.c_int, C.c_int, _dp, C.c_int, _dp, C.c_int, _ip,
+                                       _dp, _dp, _dp]
         L.orc_solve.argtypes = [C.c_int, _dp, _dp, C.c_int, _dp, _dp, _dp, _dp, C.c_int, _dp, _dp, _ip, _ip, _dp]
         L.orc_cost.restype = C.c_double
         L.orc_cost.argtypes = [C.c_int, _dp, _dp, C.c_int, _dp, _dp, _dp, _dp, _ip, _dp]
@@ -142,6 +146,10 @@ class OracleModel:
             None if getattr(m, "act_forcelimited", None) is None else I("afl", m.act_forcelimited),
             None if getattr(m, "act_forcerange", None) is None else D("afr", m.act_forcerange),
             None if getattr(m, "dof_frictionloss", None) is None else D("dfl", m.dof_frictionloss),
+            getattr(m, "nmesh", 0),
+            *((I("mva", m.mesh_vertadr), I("mvn", m.mesh_vertnum), D("mv", m.mesh_vert), I("mfa", m.mesh_faceadr),
+               I("mfn", m.mesh_facenum), I("mf", m.mesh_face), I("gmi", m.geom_meshid))
+              if getattr(m, "nmesh", 0) else (None,) * 7),
         )
         err = C.create_string_buffer(256)
         h = L.orc_model_new(C.byref(desc), err, 256)
@@ -289,6 +297,23 @@ def collide_hfield(R1, p1, size, elev, t2, R2, p2, s2):
     if n < 0:
         raise ValueError("unsupported pair")
     return out[:n]
+
+
+def collide_mesh(R1, p1, R2, p2, vert, face, size=None, elev=None):
+    """Model-free plane (elev None) or heightfield (size, elev) as geom1 against a convex mesh
+    (vertices [n, 3], outward triangles [f, 3]) as geom2; [4, 13] records as collide()."""
+    vert = np.ascontiguousarray(_d(vert))
+    face = np.ascontiguousarray(np.asarray(face, np.int32))
+    out = np.zeros((4, 13))
+    hf = elev is not None
+    e = np.ascontiguousarray(_d(elev)) if hf else None
+    n = lib().orc_collide_mesh(4 if hf else 0, _pd(_d(R1)), _pd(_d(p1)), _pd(_d(size)) if hf else None,
+                               int(e.shape[0]) if hf else 0, int(e.shape[1]) if hf else 0, _pd(e) if hf else None,
+                               int(vert.shape[0]), _pd(vert), int(face.shape[0]), _pi(face), _pd(_d(R2)), _pd(_d(p2)),
+                               _pd(out))
+    if n < 0:
+        raise ValueError("unsupported pair or mesh")
+    return out
 
 
 def _kinds(kind, mu, nr):

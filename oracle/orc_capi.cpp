@@ -267,7 +267,7 @@ int orc_integrate_pos(void* h, double* qpos, const double* qvel, double dt) {
 int orc_collide(int t1, const double* R1, const double* p1, const double* s1, int t2, const double* R2,
                 const double* p2, const double* s2, double* out) {
   int n = orc::pair_max_points(t1, t2);
-  if (n < 0) return -1;
+  if (n < 0 || t2 == orc::MESH) return -1;
   orc::Xf<double> X1, X2;
   for (int i = 0; i < 9; i++) { X1.R[i] = R1[i]; X2.R[i] = R2[i]; }
   for (int i = 0; i < 3; i++) { X1.p[i] = p1[i]; X2.p[i] = p2[i]; }
@@ -286,7 +286,7 @@ int orc_collide(int t1, const double* R1, const double* p1, const double* s1, in
 int orc_collide_hfield(const double* R1, const double* p1, const double* s1, int nrow, int ncol, const double* elev,
                        int t2, const double* R2, const double* p2, const double* s2, double* out) {
   int n = orc::pair_max_points(orc::HFIELD, t2);
-  if (n < 0 || nrow < 2 || ncol < 2 || !elev) return -1;
+  if (n < 0 || nrow < 2 || ncol < 2 || !elev || t2 == orc::MESH) return -1;
   orc::Xf<double> X1, X2;
   for (int i = 0; i < 9; i++) { X1.R[i] = R1[i]; X2.R[i] = R2[i]; }
   for (int i = 0; i < 3; i++) { X1.p[i] = p1[i]; X2.p[i] = p2[i]; }
@@ -298,6 +298,29 @@ int orc_collide_hfield(const double* R1, const double* p1, const double* s1, int
     for (int k = 0; k < 3; k++) { o[1 + k] = c[i].pos[k]; o[4 + k] = c[i].n[k]; o[7 + k] = c[i].t1[k]; o[10 + k] = c[i].t2[k]; }
   }
   return n;
+}
+
+// Model-free collision of a plane (t1 = PLANE; frame R1/p1) or a heightfield (t1 = HFIELD; size s1,
+// grid nrow x ncol) with a convex mesh (vertices nvert x 3, outward triangles nface x 3, in the
+// frame R2/p2); the same records as orc_collide, 4 of them.  -1 on a bad pair or mesh.
+int orc_collide_mesh(int t1, const double* R1, const double* p1, const double* s1, int nrow, int ncol, const double* elev,
+                     int nvert, const double* vert, int nface, const int* face, const double* R2, const double* p2,
+                     double* out) {
+  if (t1 != orc::PLANE && !(t1 == orc::HFIELD && nrow >= 2 && ncol >= 2 && elev)) return -1;
+  orc::Solid sd;
+  if (!orc::mesh_solid(vert, nvert, face, nface, sd).empty()) return -1;
+  orc::Xf<double> X1, X2;
+  for (int i = 0; i < 9; i++) { X1.R[i] = R1[i]; X2.R[i] = R2[i]; }
+  for (int i = 0; i < 3; i++) { X1.p[i] = p1[i]; X2.p[i] = p2[i]; }
+  orc::Contact<double> c[4];
+  const double zero[3] = {0, 0, 0};
+  orc::collide_pair(t1, X1, s1 ? s1 : zero, orc::MESH, X2, zero, c, orc::HField{nrow, ncol, elev}, &sd);
+  for (int i = 0; i < 4; i++) {
+    double* o = out + 13 * i;
+    o[0] = c[i].dist;
+    for (int k = 0; k < 3; k++) { o[1 + k] = c[i].pos[k]; o[4 + k] = c[i].n[k]; o[7 + k] = c[i].t1[k]; o[10 + k] = c[i].t2[k]; }
+  }
+  return 4;
 }
 
 // The Newton solver on raw data (M, a0, rows J/aref/D); cap < 0 selects the converged mode.

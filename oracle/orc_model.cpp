@@ -12,6 +12,65 @@ static M3<double> quat_rot(const double* q) {
   return quat2mat(u);
 }
 
+std::string mesh_solid(const double* vert, int nv, const int* face, int nf, Solid& sd) {
+  if (nv < 4 || nf < 4) return "a mesh needs at least 4 vertices and 4 faces";
+  sd.vert.assign(vert, vert + 3 * (size_t)nv);
+  sd.plane.clear();
+  for (int t = 0; t < nf; t++) {
+    V3<double> v[3];
+    for (int j = 0; j < 3; j++) {
+      const int i = face[3 * t + j];
+      if (i < 0 || i >= nv) return "mesh face index out of range";
+      v[j] = V3<double>{sd.vert[3 * i], sd.vert[3 * i + 1], sd.vert[3 * i + 2]};
+    }
+    V3<double> n = cross(sub(v[1], v[0]), sub(v[2], v[0]));
+    n = scl(n, 1.0 / norm(n));
+    const double off = dot(n, v[0]);
+    for (int i = 0; i < nv; i++)
+      if (n[0] * sd.vert[3 * i] + n[1] * sd.vert[3 * i + 1] + n[2] * sd.vert[3 * i + 2] > off + 1e-6)
+        return "mesh is not convex or a face is not outward";
+    sd.plane.insert(sd.plane.end(), {n[0], n[1], n[2], off});
+  }
+  return "";
+}
+
+// Volume, centroid and inertia about the centroid (unit density, the mesh's own axes) of the solid
+// bounded by outward triangles: the sum over triangles of the tetrahedra they span with the
+// vertices' mean o (an interior point of a convex hull), each by the exact integrals of a
+// tetrahedron with one vertex at o -- volume det(a, b, c) / 6 and second moment
+// V / 20 (a a^T + b b^T + c c^T + s s^T), s = a + b + c (positions relative to o).
+static void mesh_mass(const Solid& sd, const int* face, int nface, double& vol, double com[3], double I[9]) {
+  double o[3] = {0, 0, 0};
+  const int nv = sd.nv();
+  for (int i = 0; i < nv; i++)
+    for (int k = 0; k < 3; k++) o[k] += sd.vert[3 * i + k] / nv;
+  double first[3] = {0, 0, 0}, S[9] = {0};
+  vol = 0;
+  for (int t = 0; t < nface; t++) {
+    double p[3][3];
+    for (int j = 0; j < 3; j++)
+      for (int k = 0; k < 3; k++) p[j][k] = sd.vert[3 * face[3 * t + j] + k] - o[k];
+    const double V = (p[0][0] * (p[1][1] * p[2][2] - p[1][2] * p[2][1]) - p[0][1] * (p[1][0] * p[2][2] - p[1][2] * p[2][0]) +
+                      p[0][2] * (p[1][0] * p[2][1] - p[1][1] * p[2][0])) / 6.0;
+    double sum[3];
+    for (int k = 0; k < 3; k++) sum[k] = p[0][k] + p[1][k] + p[2][k];
+    vol += V;
+    for (int k = 0; k < 3; k++) first[k] += V * sum[k] / 4.0;   // centroid of the tetrahedron: (0 + a + b + c) / 4
+    for (int r = 0; r < 3; r++)
+      for (int c = 0; c < 3; c++)
+        S[3 * r + c] += V / 20.0 * (p[0][r] * p[0][c] + p[1][r] * p[1][c] + p[2][r] * p[2][c] + sum[r] * sum[c]);
+  }
+  double g[3];   // the centroid relative to o
+  for (int k = 0; k < 3; k++) { g[k] = first[k] / vol; com[k] = o[k] + g[k]; }
+  // second moment about the centroid, then inertia = tr(S) 1 - S
+  double Sc[9];
+  for (int r = 0; r < 3; r++)
+    for (int c = 0; c < 3; c++) Sc[3 * r + c] = S[3 * r + c] - vol * g[r] * g[c];
+  const double tr = Sc[0] + Sc[4] + Sc[8];
+  for (int r = 0; r < 3; r++)
+    for (int c = 0; c < 3; c++) I[3 * r + c] = (r == c ? tr : 0.0) - Sc[3 * r + c];
+}
+
 std::string compile_model(const Desc& d, Model& m) {
   if (d.nbody < 1) return "nbody must be >= 1 (body 0 is the world)";
   m.nbody = d.nbody; m.njnt = d.njnt; m.ngeom = d.ngeom; m.npair = d.npair; m.nu = d.nu;
@@ -93,7 +152,7 @@ std::string compile_model(const Desc& d, Model& m) {
   m.geom_size.assign(d.geom_size, d.geom_size + 3 * d.ngeom);
   m.geom_mass.assign(d.geom_mass, d.geom_mass + d.ngeom);
   for (int g = 0; g < m.ngeom; g++) {
-    if (m.geom_type[g] < PLANE || m.geom_type[g] > CYLINDER) return "unknown geom type";
+    if (m.geom_type[g] < PLANE || m.geom_type[g] > MESH) return "unknown geom type";
     if (m.geom_body[g] < 0 || m.geom_body[g] >= m.nbody) return "geom_body out of range";
     if (m.geom_type[g] == HFIELD) {
       if (m.geom_body[g] != 0 || m.geom_mass[g] != 0) return "a heightfield must be a massless geom of the world";
@@ -113,6 +172,49 @@ std::string compile_model(const Desc& d, Model& m) {
     for (double e : m.hfield)
       if (!(e >= 0.0 && e <= 1.0)) return "heightfield elevations must lie in [0, 1]";
   }
+  // convex meshes: vertices as given, face planes from the outward triangles, mass properties
+  std::vector<double> mvol(d.nmesh), mcom(3 * (size_t)d.nmesh), mI(9 * (size_t)d.nmesh);
+  for (int k = 0; k < d.nmesh; k++) {
+    Solid sd;
+    const int nv = d.mesh_vertnum[k], nf = d.mesh_facenum[k];
+    const int* face = d.mesh_face + 3 * (size_t)d.mesh_faceadr[k];
+    const std::string err = mesh_solid(d.mesh_vert + 3 * (size_t)d.mesh_vertadr[k], nv, face, nf, sd);
+    if (!err.empty()) return err;
+    mesh_mass(sd, face, nf, mvol[k], &mcom[3 * k], &mI[9 * k]);
+    if (!(mvol[k] > 0)) return "mesh encloses no volume";
+    m.meshes.push_back(sd);
+  }
+  m.geom_meshid.assign(m.ngeom, -1);
+  for (int g = 0; g < m.ngeom; g++)
+    if (m.geom_type[g] == MESH) {
+      if (!d.geom_meshid || d.geom_meshid[g] < 0 || d.geom_meshid[g] >= d.nmesh) return "a mesh geom needs a mesh";
+      m.geom_meshid[g] = d.geom_meshid[g];
+    }
+  // a geom's solid: centre of mass in the body frame and inertia about it in the body axes
+  auto geom_solid = [&](int g, double c[3], double Ib[9]) {
+    M3<double> R = quat_rot(&m.geom_quat[4 * g]);
+    double Il[9] = {0}, off[3] = {0, 0, 0};
+    const int mk = m.geom_meshid[g];
+    if (mk >= 0) {
+      for (int k = 0; k < 3; k++) off[k] = mcom[3 * mk + k];
+      for (int k = 0; k < 9; k++) Il[k] = m.geom_mass[g] / mvol[mk] * mI[9 * mk + k];
+    } else {
+      double Id[3];
+      solid_inertia(m.geom_type[g], &m.geom_size[3 * g], m.geom_mass[g], Id);
+      for (int k = 0; k < 3; k++) Il[4 * k] = Id[k];
+    }
+    for (int r = 0; r < 3; r++) {
+      c[r] = m.geom_pos[3 * g + r];
+      for (int k = 0; k < 3; k++) c[r] += R[3 * r + k] * off[k];
+    }
+    for (int r = 0; r < 3; r++)
+      for (int s2 = 0; s2 < 3; s2++) {
+        double v = 0;
+        for (int a = 0; a < 3; a++)
+          for (int b = 0; b < 3; b++) v += R[3 * r + a] * Il[3 * a + b] * R[3 * s2 + b];
+        Ib[3 * r + s2] = v;
+      }
+  };
   // mass properties: given, or the union of the body's geoms as uniform solids
   m.mass.assign(m.nbody, 0.0);
   m.ipos.assign(3 * m.nbody, 0.0);
@@ -127,8 +229,10 @@ std::string compile_model(const Desc& d, Model& m) {
     double M = 0, c[3] = {0, 0, 0};
     for (int g = 0; g < m.ngeom; g++) {
       if (m.geom_body[g] != b || m.geom_mass[g] <= 0) continue;
+      double gc[3], Ib[9];
+      geom_solid(g, gc, Ib);
       M += m.geom_mass[g];
-      for (int k = 0; k < 3; k++) c[k] += m.geom_mass[g] * m.geom_pos[3 * g + k];
+      for (int k = 0; k < 3; k++) c[k] += m.geom_mass[g] * gc[k];
     }
     if (M <= 0) continue;
     for (int k = 0; k < 3; k++) c[k] /= M;
@@ -136,17 +240,12 @@ std::string compile_model(const Desc& d, Model& m) {
     for (int g = 0; g < m.ngeom; g++) {
       if (m.geom_body[g] != b || m.geom_mass[g] <= 0) continue;
       if (m.geom_type[g] == PLANE) return "a plane cannot carry mass";
-      double Id[3];
-      solid_inertia(m.geom_type[g], &m.geom_size[3 * g], m.geom_mass[g], Id);
-      M3<double> R = quat_rot(&m.geom_quat[4 * g]);
-      double dv[3] = {m.geom_pos[3 * g] - c[0], m.geom_pos[3 * g + 1] - c[1], m.geom_pos[3 * g + 2] - c[2]};
+      double gc[3], Ib[9];
+      geom_solid(g, gc, Ib);
+      double dv[3] = {gc[0] - c[0], gc[1] - c[1], gc[2] - c[2]};
       double dd = dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2];
       for (int r = 0; r < 3; r++)
-        for (int s = 0; s < 3; s++) {
-          double rot = 0;
-          for (int k = 0; k < 3; k++) rot += R[3 * r + k] * Id[k] * R[3 * s + k];
-          I[3 * r + s] += rot + m.geom_mass[g] * ((r == s ? dd : 0.0) - dv[r] * dv[s]);
-        }
+        for (int s = 0; s < 3; s++) I[3 * r + s] += Ib[3 * r + s] + m.geom_mass[g] * ((r == s ? dd : 0.0) - dv[r] * dv[s]);
     }
     m.mass[b] = M;
     for (int k = 0; k < 3; k++) m.ipos[3 * b + k] = c[k];
@@ -159,7 +258,7 @@ std::string compile_model(const Desc& d, Model& m) {
     int g1 = d.pair_geom[2 * p], g2 = d.pair_geom[2 * p + 1];
     if (g1 < 0 || g1 >= m.ngeom || g2 < 0 || g2 >= m.ngeom) return "pair geom out of range";
     int n = pair_max_points(m.geom_type[g1], m.geom_type[g2]);
-    if (n < 0) return "unsupported pair (geom1's type must not exceed geom2's: plane < sphere < capsule < box; a heightfield pairs as geom1 with spheres and capsules; a cylinder pairs with planes)";
+    if (n < 0) return "unsupported pair (geom1's type must not exceed geom2's: plane < sphere < capsule < box; a heightfield pairs as geom1 with spheres, capsules, boxes and meshes; a cylinder pairs with planes; a mesh with planes and heightfields)";
     if (d.pair_condim[p] != 1 && d.pair_condim[p] != 3) return "pair_condim must be 1 or 3";
     m.pair_g1.push_back(g1);
     m.pair_g2.push_back(g2);

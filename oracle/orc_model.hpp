@@ -10,7 +10,7 @@
 namespace orc {
 
 enum { FREE = 0, HINGE = 1, SLIDE = 2 };
-enum { PLANE = 0, SPHERE = 1, CAPSULE = 2, BOX = 3, HFIELD = 4, CYLINDER = 5 };
+enum { PLANE = 0, SPHERE = 1, CAPSULE = 2, BOX = 3, HFIELD = 4, CYLINDER = 5, MESH = 6 };
 enum { MOTOR = 0, POSITION = 1 };
 enum { PYRAMIDAL = 0, ELLIPTIC = 1 };
 
@@ -36,6 +36,20 @@ struct Desc {
   int hfield_nrow, hfield_ncol; const double* hfield_data;   // the model's heightfield (elevations)
   const int* act_forcelimited; const double* act_forcerange;  // actuator torque limits (NULL: none)
   const double* dof_frictionloss;                               // [nv] joint friction loss (NULL: none)
+  int nmesh;                                                    // convex meshes (MESH geoms)
+  const int* mesh_vertadr; const int* mesh_vertnum; const double* mesh_vert;
+  const int* mesh_faceadr; const int* mesh_facenum; const int* mesh_face;
+  const int* geom_meshid;
+};
+
+// A convex solid for the collision routines: its vertices and outward face planes
+// (n . x <= offset inside) in its own frame.  A box is 8 corners (corner i has +h on axis k when
+// bit k of i is set) and 6 faces in the order -x, +x, -y, +y, -z, +z.
+struct Solid {
+  std::vector<double> vert;    // 3 per vertex
+  std::vector<double> plane;   // 4 per face: outward unit normal, offset
+  int nv() const { return (int)vert.size() / 3; }
+  int nf() const { return (int)plane.size() / 4; }
 };
 
 // A heightfield grid: elevations e in [0, 1], row i at y = -hy + 2 hy i / (nrow - 1), column j at
@@ -44,6 +58,10 @@ struct HField {
   int nrow = 0, ncol = 0;
   const double* e = nullptr;
 };
+
+// The solid of a convex mesh: its vertices and the outward planes of its triangles (counter-
+// clockwise seen from outside); an error message when a vertex lies outside a face's plane.
+std::string mesh_solid(const double* vert, int nv, const int* face, int nf, Solid& sd);
 
 struct Model {
   int nbody = 0, njnt = 0, nq = 0, nv = 0, ngeom = 0, npair = 0, nu = 0;
@@ -77,6 +95,8 @@ struct Model {
   int hf_nrow = 0, hf_ncol = 0;
   std::vector<double> hfield;
   HField hf() const { return HField{hf_nrow, hf_ncol, hfield.empty() ? nullptr : hfield.data()}; }
+  std::vector<Solid> meshes;        // each mesh's vertices and the face planes of its triangles
+  std::vector<int> geom_meshid;     // a MESH geom's mesh, else -1
 };
 
 // Contact points a primitive pair can produce (the static slot count of the pair).
@@ -93,6 +113,8 @@ inline int pair_max_points(int t1, int t2) {
   if (t1 == HFIELD && t2 == SPHERE) return 1;
   if (t1 == HFIELD && t2 == CAPSULE) return 2;
   if (t1 == PLANE && t2 == CYLINDER) return 4;
+  if (t1 == PLANE && t2 == MESH) return 4;
+  if (t1 == HFIELD && (t2 == BOX || t2 == MESH)) return 4;
   return -1;
 }
 

@@ -771,10 +771,126 @@ template <class T> void plane_cylinder(const V3<T>& p0, const V3<T>& n, const Xf
   }
 }
 
-// All candidate contacts of one pair, written to out[0 .. pair_max_points).
+// ---- convex solids (boxes and meshes) --------------------------------------------
+// A box of half sizes h as a Solid: corner i at (+-h0, +-h1, +-h2), + on axis k when bit k of i is
+// set; faces -x, +x, -y, +y, -z, +z.
+inline Solid box_solid(const double* h) {
+  Solid sd;
+  for (int i = 0; i < 8; i++)
+    for (int k = 0; k < 3; k++) sd.vert.push_back(((i >> k) & 1) ? h[k] : -h[k]);
+  for (int f = 0; f < 6; f++) {
+    double pl[4] = {0, 0, 0, h[f / 2]};
+    pl[f / 2] = (f % 2) ? 1.0 : -1.0;
+    sd.plane.insert(sd.plane.end(), pl, pl + 4);
+  }
+  return sd;
+}
+
+template <class T> struct Candidate {
+  Contact<T> c;
+  int order;
+};
+
+// the 4 deepest candidates (ties: the earlier in the list), written to out in list order
+template <class T> void keep_deepest4(std::vector<Candidate<T>> cand, Contact<T>* out) {
+  std::stable_sort(cand.begin(), cand.end(), [](const Candidate<T>& a, const Candidate<T>& b) {
+    return val(a.c.dist) < val(b.c.dist);
+  });
+  if (cand.size() > 4) cand.resize(4);
+  std::sort(cand.begin(), cand.end(), [](const Candidate<T>& a, const Candidate<T>& b) { return a.order < b.order; });
+  for (size_t i = 0; i < cand.size(); i++) out[i] = cand[i].c;
+}
+
+// Plane (point p0, unit normal n) against a convex solid in frame X: each vertex at its distance
+// n.(v - p0); the 4 deepest (ties: lower vertex index) in vertex order, each midway between the
+// vertex and the plane.
+template <class T> void plane_solid(const V3<T>& p0, const V3<T>& n, const Xf<T>& X, const Solid& sd, Contact<T>* out) {
+  std::vector<Candidate<T>> cand;
+  for (int i = 0; i < sd.nv(); i++) {
+    V3<T> w = xform(X, V3<T>{T(sd.vert[3 * i]), T(sd.vert[3 * i + 1]), T(sd.vert[3 * i + 2])});
+    Candidate<T> k;
+    k.c.n = n;
+    k.c.dist = dot(n, sub(w, p0));
+    k.c.pos = sub(w, scl(n, k.c.dist * T(0.5)));
+    k.order = i;
+    cand.push_back(k);
+  }
+  keep_deepest4(cand, out);
+}
+
+// The triangle of the grid under the grid-frame point (x, y) inside the footprint: its cell by
+// floor (clamped to the last cell), then triangle 0 when the point's offset in the cell has
+// fu >= fv, else triangle 1; returned as its upward unit normal and its first vertex.
+template <class T> void hf_under(const HField& hf, const double* size, double x, double y, V3<T>& nt, V3<T>& v0) {
+  const double hx = size[0], hy = size[1];
+  const double dx = 2 * hx / (hf.ncol - 1), dy = 2 * hy / (hf.nrow - 1);
+  auto cell = [](double u, double d, int n) { int k = (int)std::floor(u / d); return k < 0 ? 0 : (k > n - 2 ? n - 2 : k); };
+  const int i = cell(y + hy, dy, hf.nrow), j = cell(x + hx, dx, hf.ncol);
+  const double fu = (x + hx) / dx - j, fv = (y + hy) / dy - i;
+  V3<T> tri[3];
+  hf_triangle(hf, size, i, j, fu >= fv ? 0 : 1, tri);
+  nt = cross(sub(tri[1], tri[0]), sub(tri[2], tri[0]));
+  nt = scl(nt, T(1) / norm(nt));
+  v0 = tri[0];
+}
+
+// Heightfield (geom1: frame X1, size, grid hf) against a convex solid (frame X2).  Candidates:
+//   first every vertex over the grid's footprint, at its signed distance to the plane of the
+//   triangle under it, along that triangle's upward normal;
+//   then every grid vertex (row-major) strictly inside the solid, at the depth of its nearest
+//   face (the largest of its negative distances to the face planes; ties: lower face index),
+//   normal minus that face's outward normal.
+// The 4 deepest (ties: candidate order) in candidate order, each midway between the surfaces.
+template <class T> void hfield_solid(const Xf<T>& X1, const double* size, const HField& hf, const Xf<T>& X2,
+                                     const Solid& sd, Contact<T>* out) {
+  std::vector<Candidate<T>> cand;
+  for (int i = 0; i < sd.nv(); i++) {
+    V3<T> w = xform(X2, V3<T>{T(sd.vert[3 * i]), T(sd.vert[3 * i + 1]), T(sd.vert[3 * i + 2])});
+    V3<T> p = mtv(X1.R, sub(w, X1.p));
+    if (val(p[0]) < -size[0] || val(p[0]) > size[0] || val(p[1]) < -size[1] || val(p[1]) > size[1]) continue;
+    V3<T> nt, v0;
+    hf_under(hf, size, val(p[0]), val(p[1]), nt, v0);
+    Candidate<T> k;
+    k.c.dist = dot(nt, sub(p, v0));
+    k.c.n = mv(X1.R, nt);
+    k.c.pos = add(X1.p, mv(X1.R, sub(p, scl(nt, k.c.dist * T(0.5)))));
+    k.order = i;
+    cand.push_back(k);
+  }
+  for (int a = 0; a < hf.nrow; a++)
+    for (int b = 0; b < hf.ncol; b++) {
+      V3<T> q = add(X1.p, mv(X1.R, hf_vertex<T>(hf, size, a, b)));
+      V3<T> ql = mtv(X2.R, sub(q, X2.p));
+      int best = -1;
+      T bd = T(0);
+      for (int f = 0; f < sd.nf(); f++) {
+        T s = T(sd.plane[4 * f]) * ql[0] + T(sd.plane[4 * f + 1]) * ql[1] + T(sd.plane[4 * f + 2]) * ql[2] -
+              T(sd.plane[4 * f + 3]);
+        if (best < 0 || val(s) > val(bd)) { best = f; bd = s; }
+      }
+      if (!(val(bd) < 0)) continue;
+      V3<T> nf = mv(X2.R, V3<T>{T(sd.plane[4 * best]), T(sd.plane[4 * best + 1]), T(sd.plane[4 * best + 2])});
+      Candidate<T> k;
+      k.c.dist = bd;
+      k.c.n = scl(nf, T(-1));
+      k.c.pos = sub(q, scl(nf, bd * T(0.5)));
+      k.order = sd.nv() + a * hf.ncol + b;
+      cand.push_back(k);
+    }
+  keep_deepest4(cand, out);
+}
+
+// All candidate contacts of one pair, written to out[0 .. pair_max_points); slots without a
+// candidate keep dist = 1 (inactive).  mesh2: geom2's solid when it is a mesh.
 template <class T> void collide_pair(int t1, const Xf<T>& X1, const double* s1, int t2, const Xf<T>& X2, const double* s2,
-                                     Contact<T>* out, const HField& hf = HField()) {
-  if (t1 == HFIELD) {
+                                     Contact<T>* out, const HField& hf = HField(), const Solid* mesh2 = nullptr) {
+  if ((t1 == HFIELD && (t2 == BOX || t2 == MESH)) || (t1 == PLANE && t2 == MESH))   // 4 slots, maybe not all filled
+    for (int i = 0; i < 4; i++) { out[i].dist = T(1); out[i].n = V3<T>{T(0), T(0), T(1)}; out[i].pos = X1.p; }
+  if (t1 == HFIELD && (t2 == BOX || t2 == MESH)) {
+    hfield_solid(X1, s1, hf, X2, t2 == BOX ? box_solid(s2) : *mesh2, out);
+  } else if (t1 == PLANE && t2 == MESH) {
+    plane_solid(X1.p, col(X1.R, 2), X2, *mesh2, out);
+  } else if (t1 == HFIELD) {
     // a sphere; a capsule meets the terrain at its two end spheres
     if (t2 == SPHERE) {
       out[0] = hfield_sphere(X1, s1, hf, X2.p, T(s2[0]));
@@ -1411,7 +1527,8 @@ template <class T> void forward(const Model& m, const T* qpos, const T* qvel, co
   for (int p = 0; p < m.npair; p++) {
     int g1 = m.pair_g1[p], g2 = m.pair_g2[p];
     collide_pair(m.geom_type[g1], F.kin.xgeom[g1], &m.geom_size[3 * g1], m.geom_type[g2], F.kin.xgeom[g2],
-                 &m.geom_size[3 * g2], &F.con[m.pair_slotadr[p]], m.hf());
+                 &m.geom_size[3 * g2], &F.con[m.pair_slotadr[p]], m.hf(),
+                 m.geom_meshid[g2] >= 0 ? &m.meshes[m.geom_meshid[g2]] : nullptr);
   }
   int nact = 0;
   for (int s = 0; s < m.nslot; s++) {

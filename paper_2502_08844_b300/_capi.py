@@ -37,6 +37,8 @@ class pg_model_desc(C.Structure):
         ("max_contacts", C.c_int), ("substeps", C.c_int),
         ("hfield_nrow", C.c_int), ("hfield_ncol", C.c_int), ("hfield_data", _fp),
         ("act_forcelimited", _ip), ("act_forcerange", _fp), ("dof_frictionloss", _fp),
+        ("nmesh", C.c_int), ("mesh_vertadr", _ip), ("mesh_vertnum", _ip), ("mesh_vert", _fp),
+        ("mesh_faceadr", _ip), ("mesh_facenum", _ip), ("mesh_face", _ip), ("geom_meshid", _ip),
     ]
 
 

@@ -59,7 +59,9 @@ class CompiledModel:
             None if m.hfield is None else f(m.hfield),
             None if m.act_forcelimited is None else i(m.act_forcelimited),
             None if m.act_forcerange is None else f(m.act_forcerange),
-            None if m.dof_frictionloss is None else f(m.dof_frictionloss))
+            None if m.dof_frictionloss is None else f(m.dof_frictionloss),
+            m.nmesh, *((i(m.mesh_vertadr), i(m.mesh_vertnum), f(m.mesh_vert), i(m.mesh_faceadr), i(m.mesh_facenum),
+                        i(m.mesh_face), i(m.geom_meshid)) if m.nmesh else (None,) * 7))
         self.handle = _capi.pg_model_compile(d)
         self.sizes = _capi.pg_model_info(self.handle)
 

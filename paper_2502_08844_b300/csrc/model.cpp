@@ -36,8 +36,9 @@ struct Blob {
 
 // points a primitive pair type can produce (its static slot count); -1: unsupported
 int slots_for(int t1, int t2) {
-  if (t1 == PG_GEOM_HFIELD) return t2 == PG_GEOM_SPHERE ? 1 : (t2 == PG_GEOM_CAPSULE ? 2 : -1);
-  if (t2 == PG_GEOM_CYLINDER) return t1 == PG_GEOM_PLANE ? 4 : -1;
+  if (t1 == PG_GEOM_HFIELD)
+    return t2 == PG_GEOM_SPHERE ? 1 : (t2 == PG_GEOM_CAPSULE ? 2 : (t2 == PG_GEOM_BOX || t2 == PG_GEOM_MESH ? 4 : -1));
+  if (t2 == PG_GEOM_CYLINDER || t2 == PG_GEOM_MESH) return t1 == PG_GEOM_PLANE ? 4 : -1;
   static const int table[4][4] = {
       //            plane sphere capsule box
       /* plane   */ {-1, 1, 2, 4},
@@ -91,6 +92,70 @@ void principal_moments(int type, const float* size, double m, double I[3]) {
 }
 
 int align4(int x) { return (x + 3) & ~3; }
+
+// a convex mesh, checked: its outward face planes (n, offset: n . x <= offset inside) and the mass
+// properties of the uniform solid hull of unit density (volume, centroid, inertia about the
+// centroid in the geom axes), from signed tetrahedra on the origin and each outward triangle
+struct MeshProps {
+  std::vector<float> plane;   // 4 per face
+  double vol = 0, com[3] = {0, 0, 0}, I[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+};
+
+int mesh_props(const float* v, int nvert, const int* f, int nface, MeshProps& out) {
+  if (nvert < 4 || nface < 4) return set_error(PG_EINVAL, "a mesh needs at least 4 vertices and 4 faces");
+  if (nvert > kMaxMeshVert || nface > kMaxMeshFace) return set_error(PG_ECAPACITY, "a mesh exceeds 32 vertices or 64 faces");
+  double ext = 0, mid[3] = {0, 0, 0};
+  for (int i = 0; i < nvert; i++)
+    for (int k = 0; k < 3; k++) {
+      if (!std::isfinite(v[3 * i + k])) return set_error(PG_EINVAL, "non-finite mesh vertex");
+      ext = std::max(ext, std::fabs((double)v[3 * i + k]));
+      mid[k] += v[3 * i + k] / (double)nvert;
+    }
+  double first[3] = {0, 0, 0}, C[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  out.plane.assign(4 * (size_t)nface, 0.f);
+  for (int t = 0; t < nface; t++) {
+    double a[3], b[3], c[3];
+    for (int k = 0; k < 3; k++) {
+      const int ia = f[3 * t], ib = f[3 * t + 1], ic = f[3 * t + 2];
+      if (ia < 0 || ia >= nvert || ib < 0 || ib >= nvert || ic < 0 || ic >= nvert)
+        return set_error(PG_EINVAL, "mesh face index out of range");
+      a[k] = v[3 * ia + k]; b[k] = v[3 * ib + k]; c[k] = v[3 * ic + k];
+    }
+    const double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+    double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    const double nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    if (!(nn > 1e-12 * (ext * ext + 1e-30))) return set_error(PG_EINVAL, "degenerate mesh face");
+    for (int k = 0; k < 3; k++) n[k] /= nn;
+    const double off = n[0] * a[0] + n[1] * a[1] + n[2] * a[2];
+    // outward: the vertices' mean lies inside, and no vertex lies outside the face's plane
+    if (!(n[0] * mid[0] + n[1] * mid[1] + n[2] * mid[2] < off)) return set_error(PG_EINVAL, "mesh face not outward");
+    for (int i = 0; i < nvert; i++)
+      if (n[0] * v[3 * i] + n[1] * v[3 * i + 1] + n[2] * v[3 * i + 2] - off > 1e-5 * (ext + 1e-30))
+        return set_error(PG_EINVAL, "mesh is not convex: a vertex lies outside a face's plane");
+    for (int k = 0; k < 3; k++) out.plane[4 * t + k] = (float)n[k];
+    out.plane[4 * t + 3] = (float)off;
+    // signed tetrahedron (origin, a, b, c): volume, first moment, second moment about the origin
+    const double V = (a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0]) +
+                      a[2] * (b[0] * c[1] - b[1] * c[0])) / 6.0;
+    out.vol += V;
+    const double sum[3] = {a[0] + b[0] + c[0], a[1] + b[1] + c[1], a[2] + b[2] + c[2]};
+    for (int k = 0; k < 3; k++) first[k] += V * sum[k] / 4.0;
+    for (int r = 0; r < 3; r++)
+      for (int q = 0; q < 3; q++)
+        C[r][q] += V / 20.0 * (a[r] * a[q] + b[r] * b[q] + c[r] * c[q] + sum[r] * sum[q]);
+  }
+  if (!(out.vol > 0)) return set_error(PG_EINVAL, "mesh encloses no volume");
+  for (int k = 0; k < 3; k++) out.com[k] = first[k] / out.vol;
+  const double tr = C[0][0] + C[1][1] + C[2][2];
+  for (int r = 0; r < 3; r++)
+    for (int q = 0; q < 3; q++) {
+      // inertia about the origin, then moved to the centroid (parallel axes)
+      const double Io = (r == q ? tr : 0.0) - C[r][q];
+      const double c2 = out.com[0] * out.com[0] + out.com[1] * out.com[1] + out.com[2] * out.com[2];
+      out.I[r][q] = Io - out.vol * ((r == q ? c2 : 0.0) - out.com[r] * out.com[q]);
+    }
+  return PG_OK;
+}
 
 }  // namespace
 
@@ -166,6 +231,52 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
     for (int a = i; a >= 0; a = dof_parent[a]) Lcol.push_back(a);
   }
   const int nL = (int)Lcol.size();
+  // ---- convex meshes ----
+  const int nmesh = d->nmesh;
+  if (nmesh < 0) return set_error(PG_EINVAL, "negative nmesh");
+  if (nmesh > 0 && (!d->mesh_vertadr || !d->mesh_vertnum || !d->mesh_vert || !d->mesh_faceadr || !d->mesh_facenum ||
+                    !d->mesh_face))
+    return set_error(PG_EINVAL, "mesh arrays missing");
+  std::vector<MeshProps> mprops(nmesh);
+  std::vector<int> mvadr(nmesh), mvnum(nmesh), mfadr(nmesh), mfnum(nmesh);
+  std::vector<float> mvert, mplane;
+  for (int k = 0; k < nmesh; k++) {
+    const int va = d->mesh_vertadr[k], vn = d->mesh_vertnum[k], fa = d->mesh_faceadr[k], fn = d->mesh_facenum[k];
+    if (va < 0 || fa < 0) return set_error(PG_EINVAL, "negative mesh address");
+    const int rc = mesh_props(d->mesh_vert + 3 * (size_t)va, vn, d->mesh_face + 3 * (size_t)fa, fn, mprops[k]);
+    if (rc != PG_OK) return rc;
+    mvadr[k] = (int)(mvert.size() / 3); mvnum[k] = vn;
+    mfadr[k] = (int)(mplane.size() / 4); mfnum[k] = fn;
+    mvert.insert(mvert.end(), d->mesh_vert + 3 * (size_t)va, d->mesh_vert + 3 * ((size_t)va + vn));
+    mplane.insert(mplane.end(), mprops[k].plane.begin(), mprops[k].plane.end());
+  }
+  std::vector<int> gmesh(ngeom, -1);
+  for (int g = 0; g < ngeom; g++)
+    if (d->geom_type[g] == PG_GEOM_MESH) {
+      if (!d->geom_meshid || d->geom_meshid[g] < 0 || d->geom_meshid[g] >= nmesh)
+        return set_error(PG_EINVAL, "a mesh geom needs a valid geom_meshid");
+      gmesh[g] = d->geom_meshid[g];
+    }
+  // a geom's solid: its centre of mass in the body frame and its inertia about it in the geom axes
+  auto geom_solid = [&](int g, double com[3], double Il[3][3]) {
+    for (int a = 0; a < 3; a++)
+      for (int c = 0; c < 3; c++) Il[a][c] = 0.0;
+    double R[9];
+    quat_matrix(d->geom_quat + 4 * g, R);
+    const double m = d->geom_mass[g];
+    double off[3] = {0, 0, 0};
+    if (gmesh[g] >= 0) {
+      const MeshProps& mp = mprops[gmesh[g]];
+      for (int k = 0; k < 3; k++) off[k] = mp.com[k];
+      for (int a = 0; a < 3; a++)
+        for (int c = 0; c < 3; c++) Il[a][c] = m / mp.vol * mp.I[a][c];
+    } else {
+      double Ip[3];
+      principal_moments(d->geom_type[g], d->geom_size + 3 * g, m, Ip);
+      for (int a = 0; a < 3; a++) Il[a][a] = Ip[a];
+    }
+    for (int k = 0; k < 3; k++) com[k] = d->geom_pos[3 * g + k] + R[3 * k] * off[0] + R[3 * k + 1] * off[1] + R[3 * k + 2] * off[2];
+  };
   // ---- mass properties ----
   std::vector<float> mass(nbody, 0.f), ipos(3 * nbody, 0.f), inertia(6 * nbody, 0.f);
   for (int b = 1; b < nbody; b++) {
@@ -178,8 +289,10 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
     double M = 0, com[3] = {0, 0, 0};
     for (int g = 0; g < ngeom; g++)
       if (d->geom_body[g] == b && d->geom_mass[g] > 0) {
+        double gc[3], Il[3][3];
+        geom_solid(g, gc, Il);
         M += d->geom_mass[g];
-        for (int k = 0; k < 3; k++) com[k] += d->geom_mass[g] * (double)d->geom_pos[3 * g + k];
+        for (int k = 0; k < 3; k++) com[k] += d->geom_mass[g] * gc[k];
       }
     if (!(M > 0)) continue;
     for (int k = 0; k < 3; k++) com[k] /= M;
@@ -187,15 +300,17 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
     for (int g = 0; g < ngeom; g++) {
       if (d->geom_body[g] != b || !(d->geom_mass[g] > 0)) continue;
       if (d->geom_type[g] == PG_GEOM_PLANE) return set_error(PG_EINVAL, "a plane geom cannot carry mass");
-      double Ip[3], R[9];
-      principal_moments(d->geom_type[g], d->geom_size + 3 * g, d->geom_mass[g], Ip);
+      double R[9], gc[3], Il[3][3];
       quat_matrix(d->geom_quat + 4 * g, R);
+      geom_solid(g, gc, Il);
       double r[3];
-      for (int k = 0; k < 3; k++) r[k] = d->geom_pos[3 * g + k] - com[k];
+      for (int k = 0; k < 3; k++) r[k] = gc[k] - com[k];
       double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
       for (int a = 0; a < 3; a++)
         for (int c = 0; c < 3; c++) {
-          double rot = R[3 * a] * Ip[0] * R[3 * c] + R[3 * a + 1] * Ip[1] * R[3 * c + 1] + R[3 * a + 2] * Ip[2] * R[3 * c + 2];
+          double rot = 0.0;   // R Il R^T
+          for (int u = 0; u < 3; u++)
+            for (int w = 0; w < 3; w++) rot += R[3 * a + u] * Il[u][w] * R[3 * c + w];
           double shift = d->geom_mass[g] * ((a == c ? r2 : 0.0) - r[a] * r[c]);
           I[a][c] += rot + shift;
         }
@@ -221,7 +336,7 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
   std::vector<int> gtype(d->geom_type, d->geom_type + ngeom), gbody(d->geom_body, d->geom_body + ngeom);
   std::vector<float> gpos(d->geom_pos, d->geom_pos + 3 * ngeom), gquat(4 * ngeom), gsize(d->geom_size, d->geom_size + 3 * ngeom);
   for (int g = 0; g < ngeom; g++) {
-    if (gtype[g] < PG_GEOM_PLANE || gtype[g] > PG_GEOM_CYLINDER) return set_error(PG_EINVAL, "bad geom type");
+    if (gtype[g] < PG_GEOM_PLANE || gtype[g] > PG_GEOM_MESH) return set_error(PG_EINVAL, "bad geom type");
     if (gbody[g] < 0 || gbody[g] >= nbody) return set_error(PG_EINVAL, "geom_body out of range");
     if (gtype[g] == PG_GEOM_HFIELD) {
       if (gbody[g] != 0 || d->geom_mass[g] != 0.f) return set_error(PG_EINVAL, "a heightfield must be a massless geom of the world");
@@ -250,7 +365,7 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
     int a = d->pair_geom[2 * p], b = d->pair_geom[2 * p + 1];
     if (a < 0 || a >= ngeom || b < 0 || b >= ngeom) return set_error(PG_EINVAL, "pair geom out of range");
     int n = slots_for(gtype[a], gtype[b]);
-    if (n < 0) return set_error(PG_EUNSUPPORTED, "unsupported pair: type(geom1) must not exceed type(geom2) (plane<sphere<capsule<box), plane-plane unsupported; a heightfield pairs as geom1 with spheres and capsules; a cylinder pairs as geom2 with a plane");
+    if (n < 0) return set_error(PG_EUNSUPPORTED, "unsupported pair: type(geom1) must not exceed type(geom2) (plane<sphere<capsule<box), plane-plane unsupported; a heightfield pairs as geom1 with spheres, capsules, boxes and meshes; a cylinder pairs as geom2 with a plane; a mesh as geom2 with a plane or a heightfield");
     if (d->pair_condim[p] != 1 && d->pair_condim[p] != 3) return set_error(PG_EUNSUPPORTED, "pair_condim must be 1 or 3");
     pg1[p] = a; pg2[p] = b; pcondim[p] = d->pair_condim[p]; pfric[p] = d->pair_friction[p];
     pslotadr[p] = nslot; pnslot[p] = n;
@@ -382,6 +497,10 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
   h.o_limit_jnt = B.ints(limit_jnt);
   h.nfric = (int)fric_dof.size();
   h.o_fric_dof = B.ints(fric_dof); h.o_fric_F = B.floats(fric_F);
+  h.nmesh = nmesh;
+  h.o_mesh_vertadr = B.ints(mvadr); h.o_mesh_vertnum = B.ints(mvnum); h.o_mesh_vert = B.floats(mvert);
+  h.o_mesh_faceadr = B.ints(mfadr); h.o_mesh_facenum = B.ints(mfnum); h.o_mesh_plane = B.floats(mplane);
+  h.o_geom_meshid = B.ints(gmesh);
   while (B.w.size() % 4) B.w.push_back(0u);
   h.words = (int)B.w.size();
 
@@ -474,8 +593,8 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
     for (int p = 0; p < npair; p++) {
       const int g1 = d->pair_geom[2 * p], g2 = d->pair_geom[2 * p + 1];
       const bool ground = d->geom_type[g1] == PG_GEOM_PLANE || d->geom_type[g1] == PG_GEOM_HFIELD;
-      if (!ground || d->geom_body[g1] != 0 || d->geom_type[g2] == PG_GEOM_PLANE ||
-          (d->geom_type[g1] == PG_GEOM_HFIELD && d->geom_type[g2] == PG_GEOM_CYLINDER))
+      if (!ground || d->geom_body[g1] != 0 || d->geom_type[g2] == PG_GEOM_PLANE || d->geom_type[g2] == PG_GEOM_MESH ||
+          (d->geom_type[g1] == PG_GEOM_HFIELD && (d->geom_type[g2] == PG_GEOM_CYLINDER || d->geom_type[g2] == PG_GEOM_BOX)))
         ok = false;
     }
     if (npair > 0 && !tree_hessian) ok = false;

@@ -27,6 +27,8 @@ constexpr int kMaxEnvsPerCta = 256;
 constexpr int kMaxSmem = 232448;       // 227 KB opt-in shared memory per block
 constexpr int kMaxModels = 8;          // models per batch (their blobs travel as a kernel parameter)
 constexpr int kMaxParamWords = 7168;   // 28 KB of blob words in the kernel's parameter space
+constexpr int kMaxMeshVert = 32;       // vertices of a convex mesh
+constexpr int kMaxMeshFace = 64;       // faces (triangles) of a convex mesh
 
 struct ModelHdr {
   // counts
@@ -51,6 +53,9 @@ struct ModelHdr {
   int dr_kp, dr_kd, dr_mass, dr_fric;   // PD gain scales, link mass scales, friction-loss scales
   int o_limit_jnt;
   int nfric, o_fric_dof, o_fric_F;   // friction-loss rows: their dofs and force bounds
+  int nmesh, o_mesh_vertadr, o_mesh_vertnum, o_mesh_vert, o_mesh_faceadr, o_mesh_facenum, o_mesh_plane,
+      o_geom_meshid;                 // convex meshes: vertices (3 floats) and outward face planes
+                                     // (n, offset: 4 floats) per mesh; each geom's mesh or -1
   int words;   // total blob size
   // per-environment workspace layout (element offsets, see above)
   int ws_floats;

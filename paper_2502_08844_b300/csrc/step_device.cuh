@@ -864,6 +864,152 @@ __device__ Con hfield_sphere(const HGrid& g, float3 x1, const float* R1, float3 
 }
 
 // ---------------------------------------------------------------------------------------
+// convex solids (a box or a convex mesh) against a plane or the heightfield
+// ---------------------------------------------------------------------------------------
+// A convex solid in its geom frame: a box (8 corners, corner i at (+-hs.x, +-hs.y, +-hs.z) with
+// bit 0, 1, 2 of i choosing +; 6 faces -x, +x, -y, +y, -z, +z) or a mesh of the model (its
+// vertices and outward face planes n . p <= offset).
+struct Solid {
+  int nv, nf;
+  float3 hs;
+  const float* vert;    // mesh vertices, 3 per vertex (NULL: a box)
+  const float* plane;   // mesh face planes, 4 per face
+};
+
+__device__ __forceinline__ float3 solid_vertex(const Solid& sd, int i) {
+  if (!sd.vert)
+    return make_float3((i & 1) ? sd.hs.x : -sd.hs.x, (i & 2) ? sd.hs.y : -sd.hs.y, (i & 4) ? sd.hs.z : -sd.hs.z);
+  return make_float3(sd.vert[3 * i], sd.vert[3 * i + 1], sd.vert[3 * i + 2]);
+}
+
+// signed distance of the local point p to face f's plane (positive outside); n: its outward normal
+__device__ __forceinline__ float solid_face(const Solid& sd, int f, float3 p, float3& n) {
+  if (!sd.vert) {
+    const float sg = (f & 1) ? 1.f : -1.f;
+    const int ax = f >> 1;
+    n = make_float3(ax == 0 ? sg : 0.f, ax == 1 ? sg : 0.f, ax == 2 ? sg : 0.f);
+    const float pc = ax == 0 ? p.x : (ax == 1 ? p.y : p.z), hc = ax == 0 ? sd.hs.x : (ax == 1 ? sd.hs.y : sd.hs.z);
+    return sg * pc - hc;
+  }
+  n = make_float3(sd.plane[4 * f], sd.plane[4 * f + 1], sd.plane[4 * f + 2]);
+  return dot3(n, p) - sd.plane[4 * f + 3];
+}
+
+// the 4 deepest of candidates offered in order (ties: the earlier offered), kept in offer order
+struct Deepest4 {
+  Con k[4];
+  int ord[4];
+  int n = 0;
+  __device__ __forceinline__ void offer(const Con& c, int o) {
+    if (n < 4) {
+      k[n] = c;
+      ord[n] = o;
+      n++;
+      return;
+    }
+    int w = 0;   // the shallowest kept (ties: the later offered)
+#pragma unroll
+    for (int i = 1; i < 4; i++)
+      if (k[i].dist > k[w].dist || (k[i].dist == k[w].dist && ord[i] > ord[w])) w = i;
+    if (c.dist < k[w].dist) {
+      k[w] = c;
+      ord[w] = o;
+    }
+  }
+  // into out[0 .. n) in offer order; returns n
+  __device__ __forceinline__ int take(Con out[4]) {
+    for (int i = 0; i < n; i++) {
+      int b = -1;
+      for (int j = 0; j < n; j++)
+        if (ord[j] >= 0 && (b < 0 || ord[j] < ord[b])) b = j;
+      out[i] = k[b];
+      out[i].feat = ord[b];
+      ord[b] = -1;
+    }
+    return n;
+  }
+};
+
+// plane (x1, normal nz) against a convex solid at (x2, R2): every vertex at its distance to the
+// plane; the 4 deepest (ties: lower index) in vertex order, each midway between vertex and plane
+__device__ int plane_solid(float3 x1, float3 nz, float3 x2, const float* R2, const Solid& sd, Con out[4]) {
+  Deepest4 top;
+  for (int i = 0; i < sd.nv; i++) {
+    const float3 w = x2 + mat_mul(R2, solid_vertex(sd, i));
+    Con c;
+    c.n = nz;
+    c.dist = dot3(nz, w - x1);
+    c.pos = w - nz * (0.5f * c.dist);
+    top.offer(c, i);
+  }
+  return top.take(out);
+}
+
+// the upward unit normal of the grid triangle under the grid-frame point p (inside the grid's
+// footprint) and one of its vertices
+__device__ __forceinline__ void hg_under(const HGrid& g, float3 p, float3& nt, float3& v0) {
+  const int i = hg_cell(p.y + g.hy, g.dy, g.nrow), j = hg_cell(p.x + g.hx, g.dx, g.ncol);
+  const float fu = (p.x + g.hx) / g.dx - (float)j, fv = (p.y + g.hy) / g.dy - (float)i;
+  float3 tri[3];
+  hg_triangle(g, i, j, fu >= fv ? 0 : 1, tri);
+  nt = cross3(tri[1] - tri[0], tri[2] - tri[0]);
+  nt = nt * rsqrtf(dot3(nt, nt));
+  v0 = tri[0];
+}
+
+// Heightfield (geom1 at x1, R1) against a convex solid (geom2 at x2, R2).  Candidates, in order:
+//   * each vertex over the grid's footprint, at its signed distance to the plane of the triangle
+//     under it along that triangle's upward normal;
+//   * each grid vertex strictly inside the solid (row-major), at the depth of the nearest face
+//     (ties: lower face index), its normal minus that face's outward normal.
+// The 4 deepest (ties: candidate order) are kept in candidate order, each midway between the two
+// surfaces.  Returns how many there are.
+__device__ int hfield_solid(const HGrid& g, float3 x1, const float* R1, float3 x2, const float* R2, const Solid& sd,
+                            Con out[4]) {
+  Deepest4 top;
+  float xlo = 3.4e38f, xhi = -3.4e38f, ylo = 3.4e38f, yhi = -3.4e38f;
+  for (int i = 0; i < sd.nv; i++) {
+    const float3 w = x2 + mat_mul(R2, solid_vertex(sd, i));
+    const float3 p = mat_tmul(R1, w - x1);
+    xlo = fminf(xlo, p.x); xhi = fmaxf(xhi, p.x); ylo = fminf(ylo, p.y); yhi = fmaxf(yhi, p.y);
+    if (!(p.x >= -g.hx && p.x <= g.hx && p.y >= -g.hy && p.y <= g.hy)) continue;
+    float3 nt, v0;
+    hg_under(g, p, nt, v0);
+    Con c;
+    c.dist = dot3(nt, p - v0);
+    c.n = mat_mul(R1, nt);
+    c.pos = x1 + mat_mul(R1, p - nt * (0.5f * c.dist));
+    top.offer(c, i);
+  }
+  // the grid vertices under the solid's bounding rectangle (clamped to the grid)
+  const int i0 = max(0, (int)ceilf((ylo + g.hy) / g.dy)), i1 = min(g.nrow - 1, (int)floorf((yhi + g.hy) / g.dy));
+  const int j0 = max(0, (int)ceilf((xlo + g.hx) / g.dx)), j1 = min(g.ncol - 1, (int)floorf((xhi + g.hx) / g.dx));
+  for (int a = i0; a <= i1; a++)
+    for (int b = j0; b <= j1; b++) {
+      const float3 qw = x1 + mat_mul(R1, hg_vertex(g, a, b));
+      const float3 ql = mat_tmul(R2, qw - x2);
+      float best = -3.4e38f;
+      float3 bn = make_float3(0.f, 0.f, 1.f);
+      for (int f = 0; f < sd.nf; f++) {
+        float3 n;
+        const float sdist = solid_face(sd, f, ql, n);
+        if (sdist > best) {
+          best = sdist;
+          bn = n;
+        }
+      }
+      if (!(best < 0.f)) continue;
+      const float3 nw = mat_mul(R2, bn);
+      Con c;
+      c.dist = best;
+      c.n = nw * -1.f;
+      c.pos = qw - nw * (0.5f * best);
+      top.offer(c, sd.nv + a * g.ncol + b);
+    }
+  return top.take(out);
+}
+
+// ---------------------------------------------------------------------------------------
 // collision over the static pair list; active contacts (dist < margin) are kept in slot order
 // up to max_contacts as (slot, dist, pos, n)
 // ---------------------------------------------------------------------------------------
@@ -893,11 +1039,22 @@ __device__ int collide(const Ctx& c, uint32_t& status, float* dbg) {
     Con k[4];
     int valid = ns;
     for (int i = 0; i < 4; i++) { k[i].dist = 1.f; k[i].pos = x1; k[i].n = make_float3(0.f, 0.f, 1.f); }
+    // a box or a convex mesh as a solid (vertices and face planes)
+    Solid sd{8, 6, make_float3(s2[0], s2[1], s2[2]), nullptr, nullptr};
+    if (t2 == PG_GEOM_MESH) {
+      const int mk = MI(geom_meshid, g2);
+      sd.nv = MI(mesh_vertnum, mk);
+      sd.nf = MI(mesh_facenum, mk);
+      sd.vert = &MF(mesh_vert, 3 * MI(mesh_vertadr, mk));
+      sd.plane = &MF(mesh_plane, 4 * MI(mesh_faceadr, mk));
+    }
     if (t1 == PG_GEOM_HFIELD) {
-      // a sphere; a capsule meets the terrain at its two end spheres
+      // a sphere; a capsule meets the terrain at its two end spheres; a box or mesh as a solid
       const HGrid g{c.hf, h.hf_nrow, h.hf_ncol, s1[0], s1[1], s1[2], 2.f * s1[0] / (float)(h.hf_ncol - 1),
                     2.f * s1[1] / (float)(h.hf_nrow - 1)};
-      if (t2 == PG_GEOM_SPHERE) {
+      if (t2 == PG_GEOM_BOX || t2 == PG_GEOM_MESH) {
+        valid = hfield_solid(g, x1, R1, x2, R2, sd, k);
+      } else if (t2 == PG_GEOM_SPHERE) {
         k[0] = hfield_sphere(g, x1, R1, x2, s2[0]);
       } else {
         const float3 a = mat_col(R2, 2);
@@ -914,6 +1071,8 @@ __device__ int collide(const Ctx& c, uint32_t& status, float* dbg) {
         k[0] = plane_sphere(x1, nz, x2 - a * s2[1], s2[0]);
         k[1] = plane_sphere(x1, nz, x2 + a * s2[1], s2[0]);
         k[1].feat = 1;
+      } else if (t2 == PG_GEOM_MESH) {
+        valid = plane_solid(x1, nz, x2, R2, sd, k);
       } else if (t2 == PG_GEOM_CYLINDER) {
         // the deepest rim point of each cap (along e, the radius on which the rim falls fastest;
         // the cylinder's x axis when its axis is within 1e-4 of the normal), then two more rim

@@ -29,7 +29,7 @@ import numpy as np
 
 # joint, geom, actuator and cone type codes (shared numbering of the model format)
 FREE, HINGE, SLIDE = 0, 1, 2
-PLANE, SPHERE, CAPSULE, BOX, HFIELD, CYLINDER = 0, 1, 2, 3, 4, 5
+PLANE, SPHERE, CAPSULE, BOX, HFIELD, CYLINDER, MESH = 0, 1, 2, 3, 4, 5, 6
 MOTOR, POSITION = 0, 1
 PYRAMIDAL, ELLIPTIC = 0, 1
 
@@ -120,6 +120,20 @@ class Model:
     act_forcelimited: Optional[np.ndarray] = None   # [nu] int32: clip the actuator's force
     act_forcerange: Optional[np.ndarray] = None     # [nu, 2] (lo, hi)
     dof_frictionloss: Optional[np.ndarray] = None   # [nv] joint friction loss (a bound on its friction force)
+    # convex meshes (MESH geoms): mesh k's vertices mesh_vert[mesh_vertadr[k] + i] (geom frame) and
+    # outward counter-clockwise triangles mesh_face[mesh_faceadr[k] + f] (indices into its own
+    # vertices) bounding their convex hull; geom_meshid[g] the mesh of a MESH geom, else -1
+    mesh_vert: Optional[np.ndarray] = None          # [total vertices, 3] float32
+    mesh_vertadr: Optional[np.ndarray] = None       # [nmesh] int32
+    mesh_vertnum: Optional[np.ndarray] = None       # [nmesh] int32
+    mesh_face: Optional[np.ndarray] = None          # [total faces, 3] int32
+    mesh_faceadr: Optional[np.ndarray] = None       # [nmesh] int32
+    mesh_facenum: Optional[np.ndarray] = None       # [nmesh] int32
+    geom_meshid: Optional[np.ndarray] = None        # [ngeom] int32
+
+    @property
+    def nmesh(self) -> int:
+        return 0 if self.mesh_vertadr is None else int(self.mesh_vertadr.shape[0])
 
     @property
     def nbody(self) -> int:
@@ -175,6 +189,7 @@ class ModelBuilder:
         self.geoms: List[dict] = []
         self.pairs: List[dict] = []
         self.acts: List[dict] = []
+        self.meshes: List[tuple] = []
 
     def body(self, parent: int, pos, quat=(1, 0, 0, 0), mass: float = 0.0, ipos=(0, 0, 0),
              inertia=(0,) * 6, geom_inertia: bool = True) -> int:
@@ -191,10 +206,16 @@ class ModelBuilder:
                                 frictionloss=frictionloss))
         return len(self.joints) - 1
 
-    def geom(self, body: int, gtype: int, size, pos=(0, 0, 0), quat=(1, 0, 0, 0), mass=0.0) -> int:
+    def geom(self, body: int, gtype: int, size, pos=(0, 0, 0), quat=(1, 0, 0, 0), mass=0.0, mesh: int = -1) -> int:
         s = list(size) + [0.0] * (3 - len(size))
-        self.geoms.append(dict(body=body, type=gtype, size=s, pos=pos, quat=quat, mass=mass))
+        assert (gtype == MESH) == (mesh >= 0), "a MESH geom names its mesh (ModelBuilder.mesh)"
+        self.geoms.append(dict(body=body, type=gtype, size=s, pos=pos, quat=quat, mass=mass, mesh=mesh))
         return len(self.geoms) - 1
+
+    def mesh(self, vertices, faces) -> int:
+        """a convex mesh: vertices [n, 3] and outward counter-clockwise triangles [f, 3] of their hull"""
+        self.meshes.append((np.asarray(vertices, np.float64).reshape(-1, 3), np.asarray(faces, np.int64).reshape(-1, 3)))
+        return len(self.meshes) - 1
 
     def pair(self, g1: int, g2: int, friction=1.0, condim=3) -> int:
         self.pairs.append(dict(g=(g1, g2), friction=friction, condim=condim))
@@ -217,7 +238,8 @@ class ModelBuilder:
             dof += [j] * n
         maxpts = {(PLANE, SPHERE): 1, (PLANE, CAPSULE): 2, (PLANE, BOX): 4, (SPHERE, SPHERE): 1,
                   (SPHERE, CAPSULE): 1, (CAPSULE, CAPSULE): 1, (SPHERE, BOX): 1, (CAPSULE, BOX): 2,
-                  (BOX, BOX): 4, (HFIELD, SPHERE): 1, (HFIELD, CAPSULE): 2, (PLANE, CYLINDER): 4}
+                  (BOX, BOX): 4, (HFIELD, SPHERE): 1, (HFIELD, CAPSULE): 2, (PLANE, CYLINDER): 4,
+                  (PLANE, MESH): 4, (HFIELD, BOX): 4, (HFIELD, MESH): 4}
         slots = sum(maxpts[(G[p["g"][0]]["type"], G[p["g"][1]]["type"])] for p in self.pairs)
         i32 = lambda x: np.asarray(x, np.int32)
         m = Model(
@@ -270,6 +292,16 @@ class ModelBuilder:
         )
         if any(j["frictionloss"] > 0 for j in J):
             m.dof_frictionloss = _f32([j["frictionloss"] for j in dof])
+        if self.meshes:
+            nv_ = [v.shape[0] for v, _ in self.meshes]
+            nf_ = [f.shape[0] for _, f in self.meshes]
+            m.mesh_vert = _f32(np.concatenate([v for v, _ in self.meshes]))
+            m.mesh_vertadr = i32(np.concatenate([[0], np.cumsum(nv_)[:-1]]))
+            m.mesh_vertnum = i32(nv_)
+            m.mesh_face = i32(np.concatenate([f for _, f in self.meshes]))
+            m.mesh_faceadr = i32(np.concatenate([[0], np.cumsum(nf_)[:-1]]))
+            m.mesh_facenum = i32(nf_)
+            m.geom_meshid = i32([g["mesh"] for g in G])
         if any(a["forcelimited"] for a in self.acts):
             m.act_forcelimited = i32([a["forcelimited"] for a in self.acts])
             m.act_forcerange = _f32([a["forcerange"] for a in self.acts]).reshape(-1, 2)
@@ -553,6 +585,82 @@ def quadruped_rough() -> Model:
 
 
 MODELS["quadruped_rough"] = quadruped_rough
+
+
+def humanoid_rough() -> Model:
+    """The humanoid on the rough terrain of quadruped_rough (the humanoids' training follows the
+    quadruped's fine-tuning, Sec. 4.2.2): its floor plane replaced by the 8 m x 8 m heightfield, so
+    each box foot meets the terrain as a solid (heightfield-box pairs).  The pelvis starts raised
+    by the terrain's highest point."""
+    m = humanoid()
+    m.name = "humanoid_rough"
+    hf = perlin_terrain(ROUGH_SAMPLES, ROUGH_SAMPLES, 16, seed=7)
+    m.geom_type = m.geom_type.copy(); m.geom_size = m.geom_size.copy()
+    assert m.geom_type[0] == PLANE
+    m.geom_type[0] = HFIELD
+    m.geom_size[0] = _f32([ROUGH_HALF, ROUGH_HALF, ROUGH_HEIGHT])
+    m.hfield = hf
+    m.qpos_init = m.qpos_init.copy()
+    m.qpos_init[2] += np.float32(ROUGH_HEIGHT * float(hf.max()))
+    m.body_pos = m.body_pos.copy()
+    m.body_pos[1, 2] = m.qpos_init[2]
+    return m
+
+
+MODELS["humanoid_rough"] = humanoid_rough
+
+
+def convex_hull(seed: int, n_points: int, radii) -> tuple:
+    """A seeded convex polytope: n_points drawn uniformly on the ellipsoid of semi-axes `radii`
+    (directions from normalised Gaussian pairs of draws, Box-Muller), their convex hull
+    (scipy.spatial.ConvexHull) with only its vertices kept and every triangle turned outward
+    (counter-clockwise seen from outside).  Returns (vertices [n, 3], faces [f, 3])."""
+    from scipy.spatial import ConvexHull
+    k = np.arange(4 * n_points, dtype=np.uint64)
+    u = uniform01(np.full(k.shape, np.uint64(seed)), k).reshape(n_points, 4)
+    r = np.sqrt(-2.0 * np.log(1.0 - u[:, :2]))
+    g = np.stack([r[:, 0] * np.cos(2 * np.pi * u[:, 2]), r[:, 0] * np.sin(2 * np.pi * u[:, 2]),
+                  r[:, 1] * np.cos(2 * np.pi * u[:, 3])], axis=1)
+    pts = g / np.linalg.norm(g, axis=1, keepdims=True) * np.asarray(radii, np.float64)
+    pts = _f32(pts).astype(np.float64)            # the float32 vertices the library receives
+    hull = ConvexHull(pts)
+    keep = np.sort(hull.vertices)
+    remap = -np.ones(n_points, np.int64)
+    remap[keep] = np.arange(keep.size)
+    faces = []
+    for tri, eq in zip(hull.simplices, hull.equations):
+        a, b, c = pts[tri]
+        if np.dot(np.cross(b - a, c - a), eq[:3]) < 0:
+            tri = tri[[0, 2, 1]]
+        faces.append(remap[tri])
+    return pts[keep], np.asarray(faces, np.int64)
+
+
+def hulls() -> Model:
+    """Convex rocks: three seeded convex hulls (12, 16 and 20 points on ellipsoids of 4-8 cm
+    semi-axes, 0.2-0.4 kg, uniform density) as free bodies, the first two 14 cm above a plane and
+    the third 20 cm above a 2 m x 2 m heightfield of gradient noise (41 x 41 samples, 5 cm cells, 4 cm
+    relief) beside it; plane-mesh and heightfield-mesh pairs (4 points each), friction 0.8,
+    pyramidal; dt 2 ms, 4 substeps, Newton cap 6."""
+    b = ModelBuilder("hulls")
+    floor = b.geom(0, PLANE, (0, 0, 0))
+    terrain = b.geom(0, HFIELD, (1.0, 1.0, 0.04), pos=(3.0, 0, 0))
+    shapes = [(101, 12, (0.08, 0.06, 0.05), 0.3, (0.0, 0.0, 0.14)), (102, 16, (0.05, 0.07, 0.04), 0.2, (0.4, 0.1, 0.14)),
+              (103, 20, (0.06, 0.06, 0.08), 0.4, (3.1, -0.2, 0.2))]
+    qpos = []
+    for seed, npts, radii, mass, pos in shapes:
+        v, f = convex_hull(seed, npts, radii)
+        mk = b.mesh(v, f)
+        body = b.body(0, pos)
+        b.joint(body, FREE)
+        g = b.geom(body, MESH, (0, 0, 0), mass=mass, mesh=mk)
+        b.pair(terrain if pos[0] > 2.0 else floor, g, friction=0.8, condim=3)
+        qpos += list(pos) + [1.0, 0.0, 0.0, 0.0]
+    hf = perlin_terrain(41, 41, 8, seed=11)
+    return b.build(timestep=0.002, iterations=6, n_substeps=4, qpos_init=qpos, hfield=hf)
+
+
+MODELS["hulls"] = hulls
 
 
 # --------------------------------------------------------------------------------------

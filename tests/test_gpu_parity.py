@@ -62,7 +62,8 @@ PHASE_FIELDS = ["xpos", "xmat", "xcom", "M", "bias", "passive", "actuator", "a0"
 
 _PAIR_SLOTS = {(W.PLANE, W.SPHERE): 1, (W.PLANE, W.CAPSULE): 2, (W.PLANE, W.BOX): 4, (W.SPHERE, W.SPHERE): 1,
                (W.SPHERE, W.CAPSULE): 1, (W.CAPSULE, W.CAPSULE): 1, (W.SPHERE, W.BOX): 1, (W.CAPSULE, W.BOX): 2,
-               (W.BOX, W.BOX): 4, (W.PLANE, W.CYLINDER): 4}
+               (W.BOX, W.BOX): 4, (W.PLANE, W.CYLINDER): 4, (W.HFIELD, W.SPHERE): 1, (W.HFIELD, W.CAPSULE): 2,
+               (W.PLANE, W.MESH): 4, (W.HFIELD, W.BOX): 4, (W.HFIELD, W.MESH): 4}
 
 
 def _pair_slot_adr(m):
