@@ -230,7 +230,9 @@ void pg_model_free(pg_model* model);
 /* Batch of environments: counts[k] consecutive envs of models[k], in that order.  The
  * models must outlive the batch.  envs_per_cta (>= 1, or 0 for the default) sets how many
  * environments share a thread block of the thread-per-environment kernels (one thread each;
- * the default is one wave: about n / SMs per block).  Allocates the batch's device tables and
+ * the default is one wave: about n / SMs per block) and, when not 0, of the branch-parallel
+ * kernel's barrier launch (envs_per_cta / (32 / lanes per environment) warps a block, 1 to 8;
+ * its default is one wave).  Allocates the batch's device tables and
  * nothing else; the scratch of pg_step_vjp is reserved by pg_batch_reserve_vjp (or by the first
  * pg_step_vjp call that needs it). */
 int pg_batch_compile(const pg_model* const* models, const int64_t* counts, int nmodels, int envs_per_cta,

@@ -402,12 +402,13 @@ int branch_plan(const pg_model* m, std::string& src, std::string& why, int& lane
 }
 
 // environments [env0, env0 + count) of a state.  k: blocks of one warp (32 / lanes environments
-// each).  k_sync (when not NULL): one wave of blocks of W warps, W the warps per SM the launch
-// needs (at most 8), whose warps start every substep together.
+// each).  k_sync (when not NULL): blocks of W warps whose warps start every substep together; W is
+// envs_per_block / (32 / lanes) when envs_per_block > 0 (1 to 8), else the warps per SM the launch
+// needs for one wave (at most 8).
 cudaError_t launch_branch_range(cudaKernel_t k, cudaKernel_t k_sync, int lanes, int64_t env0, int64_t count,
                                 const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st,
                                 const pg_step_out* out, int nslot, float* tape, int tape_rows, int tape_nq,
-                                int tape_nv) {
+                                int tape_nv, int envs_per_block) {
   if (count <= 0) return cudaSuccess;
   BranchArgs A;
   A.out_force = out ? out->contact_force : nullptr;
@@ -438,7 +439,8 @@ cudaError_t launch_branch_range(cudaKernel_t k, cudaKernel_t k_sync, int lanes, 
       if (sms < 1) sms = 1;
     }
     const int64_t warps = (count + epw - 1) / epw;
-    const int w = (int)std::min<int64_t>(8, std::max<int64_t>(1, (warps + sms - 1) / sms));
+    const int w = envs_per_block > 0 ? std::min(8, std::max(1, envs_per_block / epw))
+                                     : (int)std::min<int64_t>(8, std::max<int64_t>(1, (warps + sms - 1) / sms));
     const int64_t per_block = (int64_t)w * epw;
     return cudaLaunchKernel((const void*)k_sync, dim3((unsigned)((count + per_block - 1) / per_block)), dim3(32 * w),
                             params, 0, st);
@@ -449,13 +451,13 @@ cudaError_t launch_branch_range(cudaKernel_t k, cudaKernel_t k_sync, int lanes, 
 cudaError_t launch_branch(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st,
                           const pg_step_out* out) {
   return launch_branch_range(b->branch_kernel, b->branch_kernel_sync, b->branch_lanes, 0, s->n, s, ctrl, n_substeps,
-                             st, out, b->nslot_max);
+                             st, out, b->nslot_max, nullptr, 0, 0, 0, b->envs_per_cta_req);
 }
 
 cudaError_t launch_branch_tape(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, float* tape,
                                int tape_rows, cudaStream_t st) {
   return launch_branch_range(nullptr, b->branch_kernel_tape, b->branch_lanes, 0, s->n, s, ctrl, n_substeps, st,
-                             nullptr, b->nslot_max, tape, tape_rows, b->nq_max, b->nv_max);
+                             nullptr, b->nslot_max, tape, tape_rows, b->nq_max, b->nv_max, b->envs_per_cta_req);
 }
 
 }  // namespace pg

@@ -112,6 +112,7 @@ int pg_batch_compile(const pg_model* const* models, const int64_t* counts, int n
   }
   if (b->n > (int64_t)1 << 31) { delete b; return set_error(PG_EINVAL, "too many environments"); }
   if (envs_per_cta < 0 || envs_per_cta > kMaxEnvsPerCta) { delete b; return set_error(PG_EINVAL, "envs_per_cta must be 0 (auto) or 1..256"); }
+  b->envs_per_cta_req = envs_per_cta;
   // environments per block: enough blocks to give every SM work in one wave, as many envs per
   // block as shared memory allows.  Each warp holds `soa` environments of its model.
   int sms = 148, dev = 0;

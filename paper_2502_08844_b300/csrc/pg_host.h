@@ -33,6 +33,8 @@ struct pg_batch {
   int nslot_max = 0;               // candidate contact slots of the batch's models (pg_step_out rows)
   int threads = 32;                // threads per block (one environment per thread)
   std::vector<int> envs_per_cta;   // per model
+  int envs_per_cta_req = 0;        // as requested (0: the default one-wave shapes); the branch-
+                                   // parallel launch takes it as environments per block
   int max_ws_floats = 0, max_blob_words = 0, max_debug = 0;
   size_t smem_bytes = 0;
   uint32_t* d_blobs = nullptr;     // all models' blobs, concatenated
@@ -108,7 +110,7 @@ cudaError_t launch_branch(const pg_batch* b, const pg_state* s, const float* ctr
 cudaError_t launch_branch_range(cudaKernel_t k, cudaKernel_t k_sync, int lanes, int64_t env0, int64_t count,
                                 const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st,
                                 const pg_step_out* out = nullptr, int nslot = 0, float* tape = nullptr,
-                                int tape_rows = 0, int tape_nq = 0, int tape_nv = 0);
+                                int tape_rows = 0, int tape_nq = 0, int tape_nv = 0, int envs_per_block = 0);
 // the branch-parallel step recording the adjoint's substep tape (layout of launch_step_tape)
 cudaError_t launch_branch_tape(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, float* tape,
                                int tape_rows, cudaStream_t st);

@@ -134,7 +134,7 @@ cudaError_t step_spec_parts(const pg_batch* b, const pg_state* s, const float* c
   for (const pg_batch::SpecPart& part : b->spec_parts) {
     if (part.branch) {   // the model's branch-parallel kernel over its environments
       cudaError_t e = launch_branch_range(part.branch, part.branch_sync, part.branch_lanes, part.env0, part.count, s, ctrl,
-                                          n_substeps, st, out, b->nslot_max);
+                                          n_substeps, st, out, b->nslot_max, nullptr, 0, 0, 0, b->envs_per_cta_req);
       if (e != cudaSuccess) return e;
       continue;
     }

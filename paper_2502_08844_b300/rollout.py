@@ -108,14 +108,16 @@ def candidate_shapes(models: Sequence[core.CompiledModel], counts: Sequence[int]
 def candidates(models: Sequence[core.CompiledModel], counts: Sequence[int], sms: int,
                kernels: Sequence[str] = KERNELS) -> List[Tuple[str, int]]:
     """(kernel, envs per block) pairs to time; the branch-parallel kernels only where some model
-    qualifies (they launch their own parts with their own shapes; the shape applies to the rest)."""
+    qualifies.  The shape sets the thread kernels' environments per block and the barrier-launch
+    branch kernel's (its warps a block: envs / environments per warp)."""
     shapes = candidate_shapes(models, counts, sms)
     branch = any(m.branch_plan()["branch"] for m in models)
     out = []
     for k in kernels:
         if k.startswith("branch") and not branch:
             continue
-        out += [(k, e) for e in shapes]
+        # one-warp blocks take no shape of their own (the shape then applies to thread parts only)
+        out += [(k, e) for e in (shapes if k != "branch-warp" or len(models) > 1 else [0])]
     return out
 
 
