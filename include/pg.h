@@ -387,6 +387,19 @@ int pg_debug_substep(const pg_batch* batch, pg_state* state, const float* ctrl_d
 int pg_step_host(pg_batch* batch, pg_state* state, const float* ctrl_host, float* qpos_host, float* qvel_host,
                  int n_substeps, void* stream);
 
+/* n_steps control steps with host inputs and outputs, the transfers overlapped with the
+ * computation: step t reads ctrl_host + t [nu_max][ld] and leaves its resulting state in
+ * qpos_host + t [nq_max][ld] and qvel_host + t [nv_max][ld] (all pinned host memory for the
+ * overlap).  Step t + 1's controls upload while step t computes, and step t's state (snapshotted
+ * on the device) downloads while step t + 1 computes, on two library-owned streams ordered by
+ * events against `stream`.  The state advances as by n_steps pg_step calls with the same kernels.
+ * Returns after queuing; the host outputs are complete when `stream` is synchronised.  Allocates
+ * its double buffers (two control rows, two state snapshots) on first use or when the batch's
+ * sizes outgrow them.  n_steps = 0 does nothing (the buffers may then be NULL).  Errors as
+ * pg_step_host, and PG_EINVAL for n_steps < 0. */
+int pg_rollout_host(pg_batch* batch, pg_state* state, const float* ctrl_host, float* qpos_host, float* qvel_host,
+                    int n_steps, int n_substeps, void* stream);
+
 /* Reverse-mode sweep (vector-Jacobian product) of n_steps consecutive control steps.
  *
  * The paper reports no gradients. This is the library's adjoint of the step above. It is a

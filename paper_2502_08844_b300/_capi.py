@@ -95,7 +95,7 @@ class pg_render_desc(C.Structure):
 
 
 EXPORTS = ["pg_model_compile", "pg_model_info", "pg_model_free", "pg_batch_compile", "pg_batch_info",
-           "pg_batch_free", "pg_reset", "pg_step", "pg_step_dr", "pg_debug_substep", "pg_step_host", "pg_step_vjp",
+           "pg_batch_free", "pg_reset", "pg_step", "pg_step_dr", "pg_debug_substep", "pg_step_host", "pg_rollout_host", "pg_step_vjp",
            "pg_step_vjp_noalloc", "pg_batch_specialize", "pg_batch_specialize_ex", "pg_batch_kernel",
            "pg_step_ex", "pg_batch_nslot", "pg_batch_reserve_vjp",
            "pg_model_branch_plan", "pg_task_compile", "pg_task_info", "pg_task_free",
@@ -122,6 +122,8 @@ _lib.pg_step.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_int, C
 _lib.pg_step_dr.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
 _lib.pg_debug_substep.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
 _lib.pg_step_host.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
+_lib.pg_rollout_host.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
+                                 C.c_void_p]
 _lib.pg_step_vjp.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_int, C.c_int] + [C.c_void_p] * 7
 _lib.pg_batch_specialize.argtypes = [C.c_void_p]
 _lib.pg_batch_specialize_ex.argtypes = [C.c_void_p, C.c_uint]
@@ -209,6 +211,12 @@ def pg_step_dr(batch, state: pg_state, ctrl_ptr, params_ptr, n_substeps: int, st
 
 def pg_debug_substep(batch, state: pg_state, ctrl_ptr, env: int, out_ptr, stream) -> None:
     _check(_lib.pg_debug_substep(batch, C.byref(state), ctrl_ptr, int(env), out_ptr, stream), "pg_debug_substep")
+
+
+def pg_rollout_host(batch, state: pg_state, ctrl_host_ptr, qpos_host_ptr, qvel_host_ptr, n_steps: int, n_substeps: int,
+                    stream) -> None:
+    _check(_lib.pg_rollout_host(batch, C.byref(state), ctrl_host_ptr, qpos_host_ptr, qvel_host_ptr, int(n_steps),
+                                int(n_substeps), stream), "pg_rollout_host")
 
 
 def pg_step_host(batch, state: pg_state, ctrl_host_ptr, qpos_host_ptr, qvel_host_ptr, n_substeps: int, stream) -> None:

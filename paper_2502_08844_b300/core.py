@@ -263,6 +263,18 @@ def step_host(batch: Batch, state: State, ctrl_host: torch.Tensor, qpos_host: to
                        _stream_ptr(stream))
 
 
+def rollout_host(batch: Batch, state: State, ctrl_host: torch.Tensor, qpos_host: torch.Tensor, qvel_host: torch.Tensor,
+                 n_substeps: int, stream=None) -> None:
+    """pg_rollout_host: T = ctrl_host.shape[0] control steps from host buffers (pinned, CPU tensors
+    [T][nu_max][ld], [T][nq_max][ld], [T][nv_max][ld]), transfers overlapped with the steps."""
+    T = ctrl_host.shape[0]
+    for t, rows in ((ctrl_host, max(batch.nu_max, 1)), (qpos_host, batch.nq_max), (qvel_host, batch.nv_max)):
+        assert t.device.type == "cpu" and t.dtype == torch.float32 and t.is_contiguous()
+        assert t.shape[0] == T and t.shape[-1] == state.ld and t.shape[1] >= (rows if t is not ctrl_host else batch.nu_max)
+    _capi.pg_rollout_host(batch.handle, state.c(), _ptr(ctrl_host), _ptr(qpos_host), _ptr(qvel_host), int(T),
+                          int(n_substeps), _stream_ptr(stream))
+
+
 def step_vjp(batch: Batch, ckpt: State, ctrl: torch.Tensor, n_substeps: int, g_qpos: Optional[torch.Tensor],
              g_qvel: Optional[torch.Tensor], adj_qpos: torch.Tensor, adj_qvel: torch.Tensor, g_ctrl: torch.Tensor,
              g_param: torch.Tensor, stream=None) -> None:

@@ -69,6 +69,19 @@ void pg_model_free(pg_model* m) {
   delete m;
 }
 
+static void free_host_stage(pg_batch::HostStage& h) {
+  for (int k = 0; k < 2; k++) {
+    if (h.ctrl[k]) cudaFree(h.ctrl[k]);
+    if (h.snap[k]) cudaFree(h.snap[k]);
+    for (cudaEvent_t ev : {h.in_done[k], h.ctrl_free[k], h.snap_done[k], h.snap_free[k]})
+      if (ev) cudaEventDestroy(ev);
+  }
+  if (h.start) cudaEventDestroy(h.start);
+  if (h.in) cudaStreamDestroy(h.in);
+  if (h.out) cudaStreamDestroy(h.out);
+  h = pg_batch::HostStage();
+}
+
 void pg_batch_free(pg_batch* b) {
   if (!b) return;
   if (b->d_blobs) cudaFree(b->d_blobs);
@@ -76,6 +89,7 @@ void pg_batch_free(pg_batch* b) {
   if (b->d_tiles) cudaFree(b->d_tiles);
   if (b->d_hfields) cudaFree(b->d_hfields);
   if (b->d_ctrl_stage) cudaFree(b->d_ctrl_stage);
+  free_host_stage(b->host_stage);
   if (b->d_vjp) cudaFree(b->d_vjp);
   if (b->spec_lib) cudaLibraryUnload(b->spec_lib);
   if (b->branch_lib) cudaLibraryUnload(b->branch_lib);
@@ -284,6 +298,73 @@ int pg_step_host(pg_batch* b, pg_state* s, const float* ctrl_host, float* qpos_h
     return cuda_error(e, "qpos download");
   if ((e = cudaMemcpyAsync(qvel_host, s->qvel, (size_t)b->nv_max * s->ld * sizeof(float), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
     return cuda_error(e, "qvel download");
+  return PG_OK;
+}
+
+// pg_rollout_host's staging for control buffers of ctrl_f floats and snapshots of snap_f floats
+static int host_stage(pg_batch* b, size_t ctrl_f, size_t snap_f) {
+  pg_batch::HostStage& h = b->host_stage;
+  if (h.in && h.ctrl_floats >= ctrl_f && h.snap_floats >= snap_f) return PG_OK;
+  free_host_stage(h);
+  cudaError_t e = cudaStreamCreateWithFlags(&h.in, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h.out, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h.start, cudaEventDisableTiming);
+  for (int k = 0; k < 2 && e == cudaSuccess; k++) {
+    for (cudaEvent_t* ev : {&h.in_done[k], &h.ctrl_free[k], &h.snap_done[k], &h.snap_free[k]})
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&h.ctrl[k], ctrl_f * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h.snap[k], snap_f * sizeof(float));
+  }
+  if (e != cudaSuccess) {
+    free_host_stage(h);
+    return cuda_error(e, "rollout staging");
+  }
+  h.ctrl_floats = ctrl_f;
+  h.snap_floats = snap_f;
+  return PG_OK;
+}
+
+int pg_rollout_host(pg_batch* b, pg_state* s, const float* ctrl_host, float* qpos_host, float* qvel_host, int n_steps,
+                    int n_substeps, void* stream) {
+  int rc = check_state(b, s);
+  if (rc) return rc;
+  if (n_substeps < 0) return set_error(PG_EINVAL, "n_substeps must be >= 0 (0: each model's own)");
+  if (n_steps < 0) return set_error(PG_EINVAL, "n_steps must be >= 0");
+  if (n_steps == 0) return PG_OK;   // nothing to read or write: the buffers may be NULL
+  if ((b->nu_max > 0 && !ctrl_host) || !qpos_host || !qvel_host) return set_error(PG_EINVAL, "NULL host buffer");
+  const size_t cf = (size_t)b->nu_max * s->ld, qf = (size_t)b->nq_max * s->ld, vf = (size_t)b->nv_max * s->ld;
+  if ((rc = host_stage(b, std::max<size_t>(cf, 1), qf + vf)) != PG_OK) return rc;
+  pg_batch::HostStage& h = b->host_stage;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaEventRecord(h.start, st);   // the staging streams start after the caller's queued work
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h.in, h.start, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h.out, h.start, 0);
+  for (int t = 0; t < n_steps && e == cudaSuccess; t++) {
+    const int k = t & 1;
+    // upload step t's controls once the launch of step t - 2 (which read this buffer) has run
+    if (t >= 2) e = cudaStreamWaitEvent(h.in, h.ctrl_free[k], 0);
+    if (e == cudaSuccess && cf)
+      e = cudaMemcpyAsync(h.ctrl[k], ctrl_host + (size_t)t * cf, cf * sizeof(float), cudaMemcpyHostToDevice, h.in);
+    if (e == cudaSuccess) e = cudaEventRecord(h.in_done[k], h.in);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h.in_done[k], 0);
+    if (e == cudaSuccess) e = launch_step(b, s, h.ctrl[k], n_substeps, st);
+    if (e == cudaSuccess) e = cudaEventRecord(h.ctrl_free[k], st);
+    // snapshot the state once the download of step t - 2 has left this buffer, then download
+    // it on the other stream while the next step computes
+    if (e == cudaSuccess && t >= 2) e = cudaStreamWaitEvent(st, h.snap_free[k], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.snap[k], s->qpos, qf * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.snap[k] + qf, s->qvel, vf * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(h.snap_done[k], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h.out, h.snap_done[k], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(qpos_host + (size_t)t * qf, h.snap[k], qf * sizeof(float), cudaMemcpyDeviceToHost, h.out);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(qvel_host + (size_t)t * vf, h.snap[k] + qf, vf * sizeof(float), cudaMemcpyDeviceToHost, h.out);
+    if (e == cudaSuccess) e = cudaEventRecord(h.snap_free[k], h.out);
+  }
+  // the caller's stream completes only after the last downloads
+  for (int k = 0; k < std::min(n_steps, 2) && e == cudaSuccess; k++) e = cudaStreamWaitEvent(st, h.snap_free[k], 0);
+  if (e != cudaSuccess) return cuda_error(e, "rollout");
   return PG_OK;
 }
 

@@ -79,6 +79,16 @@ struct pg_batch {
   // staging buffer of the host-buffer path (allocated on its first use)
   float* d_ctrl_stage = nullptr;
   size_t ctrl_stage_floats = 0;
+  // pg_rollout_host's double-buffered staging: two control buffers and two state snapshots, an
+  // upload and a download stream, and the events that order them against the step launches
+  struct HostStage {
+    cudaStream_t in = nullptr, out = nullptr;
+    cudaEvent_t start = nullptr, in_done[2] = {nullptr, nullptr}, ctrl_free[2] = {nullptr, nullptr},
+                snap_done[2] = {nullptr, nullptr}, snap_free[2] = {nullptr, nullptr};
+    float* ctrl[2] = {nullptr, nullptr};
+    float* snap[2] = {nullptr, nullptr};
+    size_t ctrl_floats = 0, snap_floats = 0;
+  } host_stage;
   // scratch of pg_step_vjp (allocated on its first use, grown when a call needs more): the
   // replayed state, the substep tape and the adjoint workspaces
   float* d_vjp = nullptr;

@@ -73,3 +73,68 @@ def test_autotune_generic_only_and_shapes():
     ws = models[0].sizes.workspace_bytes
     assert shapes[0] == 0 and all(16 <= e <= 256 and e * ws <= rollout.SMEM_PER_BLOCK for e in shapes[1:])
     assert all(k == "generic" for k, _ in rollout.candidates(models, [100], 148, ("generic",)))
+
+
+def _host_case(specialize, n=300, T=7):
+    m = W.quadruped()
+    outs = []
+    for pipelined in (False, True):
+        b = core.Batch([(core.CompiledModel(m), n)])
+        if specialize:
+            b.specialize()
+        st = core.State(b)
+        q0, v0 = W.initial_state(m, 1, n)
+        st.qpos.copy_(torch.from_numpy(core.to_soa(q0, st.ld, b.nq_max)))
+        st.qvel.copy_(torch.from_numpy(core.to_soa(v0, st.ld, b.nv_max)))
+        U = np.stack([core.to_soa(u, st.ld, b.nu_max) for u in W.actions(m, 1, n, 0, T)])
+        ctrl_h = torch.from_numpy(U).pin_memory()
+        qh = torch.zeros((T, b.nq_max, st.ld)).pin_memory()
+        vh = torch.zeros((T, b.nv_max, st.ld)).pin_memory()
+        if pipelined:
+            core.rollout_host(b, st, ctrl_h, qh, vh, m.n_substeps)
+        else:
+            for t in range(T):
+                core.step_host(b, st, ctrl_h[t], qh[t], vh[t], m.n_substeps)
+        torch.cuda.synchronize()
+        outs.append((qh.numpy().copy(), vh.numpy().copy(), st.qpos.cpu().numpy(), st.qvel.cpu().numpy()))
+    return outs
+
+
+@pytest.mark.parametrize("specialize", [pytest.param(False, id="generic"), pytest.param(True, id="branch")])
+def test_rollout_host_equals_step_host_per_step(specialize):
+    """pg_rollout_host (uploads, steps and downloads overlapped on three streams) returns every
+    step's state bitwise equal to pg_step_host called once per step, and leaves the same state"""
+    (qa, va, qda, vda), (qb, vb, qdb, vdb) = _host_case(specialize)
+    assert np.array_equal(qa, qb) and np.array_equal(va, vb)
+    assert np.array_equal(qda, qdb) and np.array_equal(vda, vdb)
+    assert np.isfinite(qb).all() and not np.array_equal(qb[0], qb[-1])
+
+
+def test_rollout_host_twice_and_zero_steps():
+    """two rollouts back to back reuse the staging buffers in order; 0 steps does nothing; NULL
+    host buffers are refused"""
+    from paper_2502_08844_b300 import _capi
+    m = W.quadruped()
+    n, T = 64, 5
+    b = core.Batch([(core.CompiledModel(m), n)])
+    st = core.State(b)
+    q0, v0 = W.initial_state(m, 1, n)
+    st.qpos.copy_(torch.from_numpy(core.to_soa(q0, st.ld, b.nq_max)))
+    st.qvel.copy_(torch.from_numpy(core.to_soa(v0, st.ld, b.nv_max)))
+    U = np.stack([core.to_soa(u, st.ld, b.nu_max) for u in W.actions(m, 1, n, 0, 2 * T)])
+    ctrl_h = torch.from_numpy(U).pin_memory()
+    qh = torch.zeros((2 * T, b.nq_max, st.ld)).pin_memory()
+    vh = torch.zeros((2 * T, b.nv_max, st.ld)).pin_memory()
+    core.rollout_host(b, st, ctrl_h[:T], qh[:T], vh[:T], m.n_substeps)
+    core.rollout_host(b, st, ctrl_h[T:], qh[T:], vh[T:], m.n_substeps)
+    core.rollout_host(b, st, ctrl_h[:0], qh[:0], vh[:0], m.n_substeps)
+    torch.cuda.synchronize()
+    ref = core.State(b)
+    ref.qpos.copy_(torch.from_numpy(core.to_soa(q0, st.ld, b.nq_max)))
+    ref.qvel.copy_(torch.from_numpy(core.to_soa(v0, st.ld, b.nv_max)))
+    for t in range(2 * T):
+        core.step(b, ref, ctrl_h[t].cuda(), m.n_substeps)
+        torch.cuda.synchronize()
+        assert np.array_equal(ref.qpos.cpu().numpy(), qh[t].numpy())
+    with pytest.raises(_capi.PgError):
+        _capi.pg_rollout_host(b.handle, st.c(), ctrl_h.data_ptr(), None, vh.data_ptr(), 1, 0, None)
