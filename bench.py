@@ -229,8 +229,9 @@ def measure_mixed(dev, steps: int = 200, specialize: bool = True):
 
 def measure_env_layer(dev, n: int = 8192, steps: int = 200, specialize: bool = True):
     """The locomotion task around the step (pg_env_step: joint targets, physics, reward table,
-    termination, auto-reset and observation in one launch) against the plain step on the same
-    8192 quadrupeds, same policy actions and commands, both with the model-specialised kernels.
+    termination, auto-reset and observation) against the plain step on the same 8192 quadrupeds,
+    same policy actions and commands.  Specialised: the substeps on the branch-parallel kernel
+    between a targets launch and an end-of-step launch, against the plain branch-parallel step.
     Time per control step with CUDA events around `steps` back-to-back launches (inputs are
     device-resident; the state and task arrays, a few MB, stay in L2)."""
     import torch
@@ -239,7 +240,7 @@ def measure_env_layer(dev, n: int = 8192, steps: int = 200, specialize: bool = T
     cm = core.CompiledModel(m)
     batch = core.Batch([(cm, n)])
     if specialize:
-        batch.specialize(branch=False)   # the plain step on the kernel the environment step extends
+        batch.specialize()
     task = core.Task(cm, W.quadruped_task(episode_length=1000))
     st = core.State(batch, dev)
     ld = st.ld
@@ -276,7 +277,8 @@ def measure_env_layer(dev, n: int = 8192, steps: int = 200, specialize: bool = T
     t_env, t_plain = timed(env_run), timed(plain_run)
     return {"value": n * steps / t_env, "unit": "env-steps/s", "plain_step_value": n * steps / t_plain,
             "overhead": t_env / t_plain - 1.0, "envs": n, "steps": steps, "episode_length": 1000,
-            "kernel": "model-specialised" if specialize else "generic",
+            "kernel": batch.kernel()["kernel"] if specialize else "generic",
+            "launches_per_env_step": 3 if specialize and batch.kernel()["kernel"] == "branch-parallel" else 1,
             "note": "pg_env_step vs pg_step on identical targets (absolute mapping); reset launch included"}
 
 

@@ -275,10 +275,12 @@ int pg_batch_specialize(pg_batch* batch);
  *                   block arrowheads (branches first, the trunk's Schur complement last), so results
  *                   agree with the other kernels to FP32 rounding. A model qualifies when it has
  *                   2 to 8 branches, each contact pair touches at most one branch, at most one
- *                   actuator drives each dof, the cone is pyramidal, it has no heightfield and no
- *                   joint friction loss, and its candidate contact points fit max_contacts;
- *                   pg_batch_kernel reports why one does not. pg_step_dr, pg_env_step, the tape and
- *                   the adjoint keep the thread-per-environment kernels.
+ *                   actuator drives each dof, the cone is pyramidal, its pairs are primitives up to
+ *                   boxes (a heightfield as geom1 included), it has no joint friction loss, and its
+ *                   candidate contact points fit max_contacts; pg_batch_kernel reports why one does
+ *                   not. The adjoint's tape replay runs on it too (a model inside the adjoint's
+ *                   scope); pg_step_dr, pg_env_step and the adjoint's reverse sweep keep the
+ *                   thread-per-environment kernels.
  *   0               the thread-per-environment specialised kernels only.
  *   PG_SPEC_BRANCH_WARP  see below.
  * Errors as pg_batch_specialize; flags other than these: PG_EINVAL. */

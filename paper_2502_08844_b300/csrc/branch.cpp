@@ -5,9 +5,10 @@
 // climbs through bodies with exactly one child and no free joint, and stops below the world, a
 // free body or a body with several children.  Every other body is trunk.  A model qualifies for
 // the kernel when it has 2 to 8 branches, every contact pair touches at most one branch, at
-// most one actuator drives each dof, the friction cone is pyramidal, and it has no heightfield,
-// no joint friction loss and no more candidate contact points than max_contacts (so no contact
-// is ever dropped); the sizes must also fit the kernel's register budget.  Otherwise
+// most one actuator drives each dof, the friction cone is pyramidal, its pairs are primitives up
+// to boxes (geom1 may be a heightfield), and it has no joint friction loss and no more candidate
+// contact points than max_contacts (so no contact is ever dropped); the sizes must also fit the
+// kernel's register budget.  Otherwise
 // pg_batch_specialize keeps the thread-per-environment kernel.
 #include <algorithm>
 #include <cmath>
@@ -77,7 +78,6 @@ int branch_plan(const pg_model* m, std::string& src, std::string& why, int& lane
     return PG_EUNSUPPORTED;
   };
   if (h.cone != PG_CONE_PYRAMIDAL) return no("the elliptic cone");
-  if (h.hf_nrow > 0) return no("a heightfield");
   if (h.nfric > 0) return no("joint friction loss");
   if (h.nslot > h.max_contacts) return no("more candidate contact points than max_contacts");
   const int nb = h.nbody;
@@ -252,7 +252,8 @@ int branch_plan(const pg_model* m, std::string& src, std::string& why, int& lane
   for (int p = 0; p < h.npair; p++) {
     const int g1 = TI(pair_g1, p), g2 = TI(pair_g2, p);
     const int t1 = TI(geom_type, g1), t2 = TI(geom_type, g2);
-    if (t1 > PG_GEOM_BOX || t2 > PG_GEOM_BOX) return no("a pair type outside the branch kernel");
+    if ((t1 > PG_GEOM_BOX && t1 != PG_GEOM_HFIELD) || t2 > PG_GEOM_BOX)
+      return no("a pair type outside the branch kernel");
     const int b1 = TI(geom_body, g1), b2 = TI(geom_body, g2);
     const int l1 = lane_of[b1], l2 = lane_of[b2];
     if (l1 >= 0 && l2 >= 0) return no("a contact pair between branch bodies");
@@ -333,6 +334,7 @@ int branch_plan(const pg_model* m, std::string& src, std::string& why, int& lane
   S.ci("GP", GP); S.ci("G", G); S.ci("NT", NT); S.ci("NQT", NQT); S.ci("BT", BT); S.ci("NJT", std::max(NJT, 1));
   S.ci("NB", std::max(NB, 1)); S.ci("BB", BB); S.ci("PS", PS); S.ci("NCL", NCL); S.ci("LS", LS);
   S.ci("NTH", threads); S.ci("EPB", envs_per_block); S.ci("CAP", h.cap); S.ci("NSUB", h.substeps);
+  S.ci("HF_NROW", std::max(h.hf_nrow, 2)); S.ci("HF_NCOL", std::max(h.hf_ncol, 2));
   S.cf("HSTEP", h.h); S.cf("GRAV_X", h.grav[0]); S.cf("GRAV_Y", h.grav[1]); S.cf("GRAV_Z", h.grav[2]);
   S.cf("KREF", h.kref); S.cf("BREF", h.bref); S.cf("MARGIN", h.margin);
   S.cf("SOLIMP_D0", h.solimp[0]); S.cf("SOLIMP_DW", h.solimp[1]); S.cf("SOLIMP_WIDTH", h.solimp[2]);
@@ -408,9 +410,10 @@ int branch_plan(const pg_model* m, std::string& src, std::string& why, int& lane
 cudaError_t launch_branch_range(cudaKernel_t k, cudaKernel_t k_sync, int lanes, int64_t env0, int64_t count,
                                 const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st,
                                 const pg_step_out* out, int nslot, float* tape, int tape_rows, int tape_nq,
-                                int tape_nv, int envs_per_block) {
+                                int tape_nv, int envs_per_block, const float* hfield) {
   if (count <= 0) return cudaSuccess;
   BranchArgs A;
+  A.hfield = hfield;
   A.out_force = out ? out->contact_force : nullptr;
   A.out_ncon = out ? out->ncon : nullptr;
   A.out_nslot = nslot;
@@ -451,13 +454,14 @@ cudaError_t launch_branch_range(cudaKernel_t k, cudaKernel_t k_sync, int lanes, 
 cudaError_t launch_branch(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st,
                           const pg_step_out* out) {
   return launch_branch_range(b->branch_kernel, b->branch_kernel_sync, b->branch_lanes, 0, s->n, s, ctrl, n_substeps,
-                             st, out, b->nslot_max, nullptr, 0, 0, 0, b->envs_per_cta_req);
+                             st, out, b->nslot_max, nullptr, 0, 0, 0, b->envs_per_cta_req, b->hfield_ptr[0]);
 }
 
 cudaError_t launch_branch_tape(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, float* tape,
                                int tape_rows, cudaStream_t st) {
   return launch_branch_range(nullptr, b->branch_kernel_tape, b->branch_lanes, 0, s->n, s, ctrl, n_substeps, st,
-                             nullptr, b->nslot_max, tape, tape_rows, b->nq_max, b->nv_max, b->envs_per_cta_req);
+                             nullptr, b->nslot_max, tape, tape_rows, b->nq_max, b->nv_max, b->envs_per_cta_req,
+                             b->hfield_ptr[0]);
 }
 
 }  // namespace pg

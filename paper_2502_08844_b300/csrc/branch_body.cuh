@@ -299,6 +299,7 @@ struct Lane {
   unsigned gm;   // its group's shuffle mask
   int64_t env, ld;
   const float* ctrl;
+  const float* hf;   // the heightfield's elevations (device), or NULL
   __device__ __forceinline__ float ctrl_row(int a) const { return __ldg(ctrl + a * ld + env); }
   // state: trunk (identical on the group's lanes) and branch
   float qT[NQT], vT[NT], wT[NT];
@@ -651,6 +652,22 @@ __device__ __forceinline__ int collide_slot(const Lane& L, const Kin& K, int s, 
 #pragma unroll
   for (int i = 0; i < 4; i++) { k[i].dist = 1.f; k[i].pos = x1; k[i].n = make_float3(0.f, 0.f, 1.f); }
   if (t1 < 0) return 0;
+  if (t1 == PG_GEOM_HFIELD) {   // the terrain: a sphere, a capsule's two end spheres, or a box as a solid
+    const HGrid g{L.hf, HF_NROW, HF_NCOL, s1[0], s1[1], s1[2], 2.f * s1[0] / (float)(HF_NCOL - 1),
+                  2.f * s1[1] / (float)(HF_NROW - 1)};
+    if (t2 == PG_GEOM_SPHERE) {
+      k[0] = hfield_sphere(g, x1, R1, x2, s2[0]);
+      return 1;
+    }
+    if (t2 == PG_GEOM_CAPSULE) {
+      const float3 a = mat_col(R2, 2);
+      k[0] = hfield_sphere(g, x1, R1, x2 - a * s2[1], s2[0]);
+      k[1] = hfield_sphere(g, x1, R1, x2 + a * s2[1], s2[0]);
+      return 2;
+    }
+    const Solid sd{8, 6, make_float3(s2[0], s2[1], s2[2]), nullptr, nullptr};
+    return hfield_solid(g, x1, R1, x2, R2, sd, k);
+  }
   if (t1 == PG_GEOM_PLANE) {
     const float3 nz = mat_col(R1, 2);
     if (t2 == PG_GEOM_SPHERE) {
@@ -1329,6 +1346,7 @@ __device__ __forceinline__ void branch_step(const BranchArgs& A) {
   L.env = A.env0 + (active ? local : A.n - 1);
   L.ld = A.ld;
   L.ctrl = A.ctrl;
+  L.hf = A.hfield;
   const int64_t ld = A.ld, env = L.env;
 #pragma unroll
   for (int i = 0; i < NQT; i++) L.qT[i] = A.qpos[kTQg[i] * ld + env];

@@ -67,6 +67,7 @@ struct pg_batch {
     cudaKernel_t branch_sync;
     int branch_lanes;
     int64_t env0, count;
+    int model;   // the part's model in the batch
   };
   std::vector<SpecPart> spec_parts;
   // the branch-parallel step kernel (pg_batch_specialize_ex with PG_SPEC_BRANCH), else NULL
@@ -120,7 +121,8 @@ cudaError_t launch_branch(const pg_batch* b, const pg_state* s, const float* ctr
 cudaError_t launch_branch_range(cudaKernel_t k, cudaKernel_t k_sync, int lanes, int64_t env0, int64_t count,
                                 const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st,
                                 const pg_step_out* out = nullptr, int nslot = 0, float* tape = nullptr,
-                                int tape_rows = 0, int tape_nq = 0, int tape_nv = 0, int envs_per_block = 0);
+                                int tape_rows = 0, int tape_nq = 0, int tape_nv = 0, int envs_per_block = 0,
+                                const float* hfield = nullptr);
 // the branch-parallel step recording the adjoint's substep tape (layout of launch_step_tape)
 cudaError_t launch_branch_tape(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, float* tape,
                                int tape_rows, cudaStream_t st);
@@ -155,9 +157,9 @@ cudaError_t launch_step_tape(const pg_batch* b, const pg_state* s, const float* 
   cudaError_t step_spec_tape(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, float* tape,\
                              int tape_rows, cudaStream_t st);                                                   \
   cudaError_t step_env(const pg_batch* b, const pg_state* s, const EnvArgs& E, int n_substeps, cudaStream_t st,   \
-                       const float* dr = nullptr);                                                              \
+                       const float* dr = nullptr, int phase = 0);                                               \
   cudaError_t step_spec_env(const pg_batch* b, const pg_state* s, const EnvArgs& E, int n_substeps,            \
-                            cudaStream_t st, const float* dr = nullptr);                                       \
+                            cudaStream_t st, const float* dr = nullptr, int phase = 0);                        \
   cudaError_t step_spec_parts(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps,          \
                               cudaStream_t st, const pg_step_out* out = nullptr);                              \
   }

@@ -321,6 +321,7 @@ static int specialize_parts(pg_batch* b, unsigned flags) {
     if (e != cudaSuccess) return fail(set_error(PG_ECUDA, std::string("specialised kernel set-up: ") + cudaGetErrorString(e)));
     parts.back().env0 = b->env_off[k];
     parts.back().count = b->counts[k];
+    parts.back().model = k;
     if (flags & PG_SPEC_BRANCH) {
       int branches = 0;
       std::string why;

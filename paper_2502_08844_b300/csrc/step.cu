@@ -94,6 +94,14 @@ cudaError_t launch_step_tape(const pg_batch* b, const pg_state* s, const float* 
 
 cudaError_t launch_env_step(const pg_batch* b, const pg_state* s, const EnvArgs& E, int n_substeps, cudaStream_t st,
                             const float* dr) {
+  if (b->branch_kernel && b->spec_kernel_env && !dr) {
+    // the joint targets, the substeps on the branch-parallel kernel (its controls are the task
+    // state's target rows), then the step's end: three launches
+    cudaError_t e = pyramidal::step_spec_env(b, s, E, n_substeps, st, nullptr, 1);
+    if (e == cudaSuccess) e = launch_branch(b, s, E.state, n_substeps, st);
+    if (e == cudaSuccess) e = pyramidal::step_spec_env(b, s, E, n_substeps, st, nullptr, 2);
+    return e;
+  }
   if (b->spec_kernel_env) return pyramidal::step_spec_env(b, s, E, n_substeps, st, dr);
   return b->has_elliptic ? elliptic::step_env(b, s, E, n_substeps, st, dr)
                          : pyramidal::step_env(b, s, E, n_substeps, st, dr);

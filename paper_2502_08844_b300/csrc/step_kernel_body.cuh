@@ -34,6 +34,9 @@ struct StepArgs {
   float* out_force;                   // optional [nslot][3][ld] contact forces of the last substep (pg_step_ex)
   int32_t* out_ncon;                  // optional [ld] active contacts of the last substep
   int out_nslot;                      // candidate contact slots of the batch's models (the rows of out_force)
+  int env_phase;                      // ENV: 0 the whole environment step, 1 the joint targets only,
+                                      // 2 the step's end only (reward to observation; the substeps
+                                      // ran in another kernel)
   uint32_t blob[kMaxParamWords];      // the batch's model blobs (header + tables)
 };
 static_assert(sizeof(StepArgs) <= 32764, "the step's argument block must fit the kernel parameter space");
@@ -72,7 +75,8 @@ __device__ __forceinline__ void step_body(const StepArgs& A) {
   float* w = smem + warp * (S * h.ws_floats) + lane;
   Ctx c{h, S, reinterpret_cast<const int*>(blob), reinterpret_cast<const float*>(blob), w, ENV ? A.env.state : A.ctrl,
         A.ld, env, A.hfield[tile.model], (DR || ENV) ? A.dr : nullptr};
-  if (ENV) env_targets(c, A.env);
+  if (ENV && A.env_phase != 2) env_targets(c, A.env);
+  if (ENV && A.env_phase == 1) return;
   for (int k = 0; k < h.nq; k++) W(qpos, k) = A.qpos[k * A.ld + env];
   uint32_t status = 0;
   bool warm_bad = false;
@@ -87,7 +91,8 @@ __device__ __forceinline__ void step_body(const StepArgs& A) {
     for (int k = 0; k < h.nv; k++) W(warm, k) = 0.f;
   }
   uint32_t cnt[3] = {0u, 0u, 0u};
-  const int nsub = DEBUG ? 1 : (A.n_substeps > 0 ? A.n_substeps : h.substeps);
+  const int nsub_model = A.n_substeps > 0 ? A.n_substeps : h.substeps;
+  const int nsub = DEBUG ? 1 : (ENV && A.env_phase == 2 ? 0 : nsub_model);
   int nc = 0;
   for (int s = 0; s < nsub; s++) {
     float* tp = TAPE ? A.tape + (int64_t)s * A.tape_rows * A.ld + env : nullptr;
@@ -114,7 +119,7 @@ __device__ __forceinline__ void step_body(const StepArgs& A) {
   if (status) A.status[env] |= status;
   if (A.stats)
     for (int k = 0; k < 3; k++) A.stats[k * A.ld + env] += cnt[k];
-  if (ENV) env_finish(c, A.env, (float)nsub * h.h, A.qpos, A.qvel, A.warm, A.status);
+  if (ENV) env_finish(c, A.env, (float)nsub_model * h.h, A.qpos, A.qvel, A.warm, A.status);
 }
 
 }  // namespace

@@ -57,6 +57,7 @@ static void make_args(StepArgs& A, const pg_batch* b, const pg_state* s, const f
   A.out_force = nullptr;
   A.out_ncon = nullptr;
   A.out_nslot = 0;
+  A.env_phase = 0;
   for (int k = 0; k < kMaxModels; k++) A.model_off[k] = k < (int)b->blob_off.size() ? b->blob_off[k] : 0;
   for (int k = 0; k < kMaxModels; k++) A.hfield[k] = b->hfield_ptr[k];
   std::memcpy(A.blob, b->blob_host.data(), b->blob_host.size() * sizeof(uint32_t));
@@ -134,7 +135,8 @@ cudaError_t step_spec_parts(const pg_batch* b, const pg_state* s, const float* c
   for (const pg_batch::SpecPart& part : b->spec_parts) {
     if (part.branch) {   // the model's branch-parallel kernel over its environments
       cudaError_t e = launch_branch_range(part.branch, part.branch_sync, part.branch_lanes, part.env0, part.count, s, ctrl,
-                                          n_substeps, st, out, b->nslot_max, nullptr, 0, 0, 0, b->envs_per_cta_req);
+                                          n_substeps, st, out, b->nslot_max, nullptr, 0, 0, 0, b->envs_per_cta_req,
+                                          b->hfield_ptr[part.model]);
       if (e != cudaSuccess) return e;
       continue;
     }
@@ -149,25 +151,27 @@ cudaError_t step_spec_parts(const pg_batch* b, const pg_state* s, const float* c
 
 // an environment step of the locomotion task E (generic kernel, or the batch's specialised one)
 cudaError_t step_env(const pg_batch* b, const pg_state* s, const EnvArgs& E, int n_substeps, cudaStream_t st,
-                     const float* dr) {
+                     const float* dr, int phase) {
   if (b->ntiles == 0) return cudaSuccess;
   static thread_local StepArgs A;
   make_args(A, b, s, nullptr);
   A.n_substeps = n_substeps;
   A.env = E;
   A.dr = dr;
+  A.env_phase = phase;
   step_kernel<false, false, true><<<b->ntiles, b->threads, b->smem_bytes, st>>>(A);
   return cudaGetLastError();
 }
 
 cudaError_t step_spec_env(const pg_batch* b, const pg_state* s, const EnvArgs& E, int n_substeps, cudaStream_t st,
-                          const float* dr) {
+                          const float* dr, int phase) {
   if (b->ntiles == 0) return cudaSuccess;
   static thread_local StepArgs A;
   make_args(A, b, s, nullptr);
   A.n_substeps = n_substeps;
   A.env = E;
   A.dr = dr;
+  A.env_phase = phase;
   void* params[] = {&A};
   return cudaLaunchKernel((const void*)b->spec_kernel_env, dim3(b->ntiles), dim3(b->threads), params, b->smem_bytes, st);
 }

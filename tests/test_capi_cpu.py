@@ -171,16 +171,17 @@ def test_row_capacity_limit():
 
 def test_branch_plan_of_the_workload_models():
     """pg_model_branch_plan (host only): the quadruped (4 legs under the torso) and the humanoid
-    (2 legs, 2 arms under pelvis and waist) qualify for the branch-parallel kernel with 4 lanes;
-    the cartpole (one chain) and the hand (more candidate contact points than max_contacts) do not,
-    and the plan says why."""
+    (2 legs, 2 arms under pelvis and waist) qualify for the branch-parallel kernel with 4 lanes, on
+    the plane and on the rough terrain; the cartpole (one chain), the hand (more candidate contact
+    points than max_contacts) and the hulls (free bodies, no branch) do not, and the plan says
+    why."""
     from paper_2502_08844_b300 import core
-    for name in ("quadruped", "humanoid"):
+    for name in ("quadruped", "humanoid", "quadruped_rough", "humanoid_rough"):
         p = core.CompiledModel(W.model(name)).branch_plan()
         assert p["branch"] and p["lanes_per_env"] == 4 and p["branches"] == 4, (name, p)
     p = core.CompiledModel(W.cartpole()).branch_plan()
     assert not p["branch"] and "fewer than 2 branches" in p["reason"]
     p = core.CompiledModel(W.hand()).branch_plan()
     assert not p["branch"] and "max_contacts" in p["reason"]
-    rough = core.CompiledModel(W.quadruped_rough()).branch_plan()
-    assert not rough["branch"] and "heightfield" in rough["reason"]
+    p = core.CompiledModel(W.hulls()).branch_plan()
+    assert not p["branch"] and "fewer than 2 branches" in p["reason"]

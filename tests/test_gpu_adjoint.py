@@ -114,16 +114,17 @@ def test_torque_limited_rollout_gradient_matches_oracle():
     check_against_oracle(m, q0, v0, U, w)
 
 
-def test_rough_terrain_rollout_gradient_matches_oracle():
+@pytest.mark.parametrize("specialize", [pytest.param(False, id="generic"), pytest.param(True, id="branch")])
+def test_rough_terrain_rollout_gradient_matches_oracle(specialize):
     """The quadruped on gradient-noise terrain: its feet meet triangle faces, edges and vertices,
     where the contact normal turns with the state; end to end over one segment against the
-    oracle's reverse mode."""
+    oracle's reverse mode, with the generic kernels and with the branch-parallel step and tape."""
     m = _converged(W.quadruped_rough())
     n, T = 8, 8
     q0, v0 = W.initial_state(m, 4, n)
     U = W.actions(m, 4, n, 0, T)
     w = O.tracking_loss_weights(O.OracleModel(m))
-    check_against_oracle(m, q0, v0, U, w)
+    check_against_oracle(m, q0, v0, U, w, specialize=specialize)
 
 
 def _ball_on_terrain(elev):

@@ -122,3 +122,23 @@ def test_kernel_query_and_opt_out():
     b3.specialize()
     k = b3.kernel()
     assert k["kernel"] == "specialised" and "max_contacts" in k["reason"]
+
+
+@pytest.mark.parametrize("mname,cfg,n,T,rtol", [("quadruped_rough", 1, 37, 1, ONE_STEP_RTOL),
+                                                ("quadruped_rough", 1, 33, 50, 1e-3),
+                                                ("humanoid_rough", 3, 33, 1, ONE_STEP_RTOL)])
+def test_terrain_contacts_on_the_branch_kernel(mname, cfg, n, T, rtol):
+    """The rough terrain in the branch kernel: the quadruped's sphere feet (heightfield-sphere) and
+    the humanoid's box feet (heightfield against the box as a solid), against the oracle; one
+    control step at the one-step tolerance, 50 steps of the quadruped at the rollout tolerance."""
+    m = W.model(mname)
+    q0, v0 = W.initial_state(m, cfg, n)
+    U = W.actions(m, cfg, n, 0, T)
+    run = GpuRun(m, n, specialize="branch")   # (asserts the branch-parallel kernel runs)
+    run.set_state(q0, v0)
+    run.rollout(U, m.n_substeps)
+    qg, vg, _ = run.get()
+    qo, vo, _, _ = O.OracleModel(m).rollout(q0, v0, U, m.n_substeps, nthreads=8)
+    for e in range(n):
+        assert_close_scaled("qpos %d" % e, canon_qpos(m, qg[e]), canon_qpos(m, qo[e]), rtol)
+        assert_close_scaled("qvel %d" % e, vg[e], vo[e], rtol)

@@ -132,13 +132,18 @@ def _compare_env(ot, g, e, pre, a, cmd, q0, v0, warm, tol_terms=1e-3):
     return near
 
 
+@pytest.mark.parametrize("specialize", [pytest.param(False, id="generic"), pytest.param(True, id="branch")])
 @pytest.mark.parametrize("mode", [W.ABSOLUTE, W.RELATIVE])
-def test_env_step_matches_oracle(mode):
+def test_env_step_matches_oracle(mode, specialize):
     """One environment step of 200 quadrupeds (a ragged last warp): some upright, some turned
-    over (terminated), some at the end of their episode (truncated)."""
+    over (terminated), some at the end of their episode (truncated).  With specialisation the
+    step runs as three launches: the joint targets, the substeps on the branch-parallel kernel
+    and the step's end (reward to observation)."""
     O, E = _oracle()
     task = dataclasses.replace(W.quadruped_task(action_mode=mode), episode_length=8)
-    S = Setup(200, task)
+    S = Setup(200, task, specialize=specialize)
+    if specialize:
+        assert S.batch.kernel()["kernel"] == "branch-parallel"
     S.q[::17, 2] += 0.3
     S.q[::17, 3:7] = _quat_axis((1, 0, 0), math.pi * 0.95).astype(np.float32)   # turned over
     S.task_state[5::23, -1] = 7                                                    # last step of the episode
@@ -156,12 +161,13 @@ def test_env_step_matches_oracle(mode):
     assert skipped < S.n // 4
 
 
-def test_env_rollout_with_resets_matches_oracle_step_by_step():
+@pytest.mark.parametrize("specialize", [pytest.param(False, id="generic"), pytest.param(True, id="branch")])
+def test_env_rollout_with_resets_matches_oracle_step_by_step(specialize):
     """12 environment steps with 5-step episodes: every environment restarts twice.  Each step
     is checked against the oracle's step from the GPU's own pre-step state and warm start."""
     O, E = _oracle()
     task = W.quadruped_task(episode_length=5)
-    S = Setup(64, task, seed=1)
+    S = Setup(64, task, specialize=specialize, seed=1)
     S.task_state[:, -1] = 0
     S.upload()
     ot = E.OracleTask(O.OracleModel(S.m), task)

@@ -107,6 +107,9 @@ def test_capsule_on_terrain_phases_and_rollout():
 
 
 def test_specialised_rough_terrain_matches_generic():
+    """the specialised thread-per-environment kernel against the generic one (the same code, to
+    rounding; the branch-parallel kernel on the terrain is checked against the oracle in
+    test_gpu_branch.py)"""
     import torch
     m = W.quadruped_rough()
     outs = []
@@ -114,7 +117,7 @@ def test_specialised_rough_terrain_matches_generic():
         cm = core.CompiledModel(m)
         batch = core.Batch([(cm, 300)])
         if spec:
-            batch.specialize()
+            batch.specialize(branch=False)
         st = core.State(batch, "cuda:0")
         q0, v0 = W.initial_state(m, 1, 300)
         st.qpos.copy_(torch.from_numpy(core.to_soa(q0, st.ld, batch.nq_max)))

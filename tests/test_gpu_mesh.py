@@ -206,9 +206,11 @@ def test_hulls_50_steps_reanchored(specialize):
         q, v, w = qg, vg, wg
 
 
-def test_mesh_and_heightfield_box_are_outside_the_adjoint_and_branch_kernels():
+def test_solid_pairs_are_outside_the_adjoint():
+    """mesh and heightfield-box pairs are outside the adjoint's scope; the humanoid's box feet on
+    the terrain run the branch-parallel kernel, the free hulls (no branch) do not"""
     from paper_2502_08844_b300 import core
     for mname in MODELS:
-        cm = core.CompiledModel(W.model(mname))
-        assert cm.sizes.adjoint_workspace_bytes == 0
-        assert not cm.branch_plan()["branch"]
+        assert core.CompiledModel(W.model(mname)).sizes.adjoint_workspace_bytes == 0
+    assert core.CompiledModel(W.humanoid_rough()).branch_plan()["branch"]
+    assert not core.CompiledModel(W.hulls()).branch_plan()["branch"]
