@@ -303,6 +303,8 @@ typedef struct {
   char reason[160];    /* why the branch kernel is not used (empty when it is or was not asked)    */
   int branch_parts;    /* mixed batch: models whose part runs the branch-parallel kernel          */
   int sync;            /* branch kernel launched with a barrier per substep (the default)        */
+  int branch_dr;       /* pg_step_dr runs the branch kernel's per-environment-parameter variant   */
+  int branch_tape;     /* the adjoint's forward recording runs the branch kernel's tape variant    */
 } pg_kernel_info;
 int pg_batch_kernel(const pg_batch* batch, pg_kernel_info* out);
 /* Whether a model qualifies for the branch-parallel kernel (host only, no device work): out->kernel

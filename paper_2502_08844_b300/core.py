@@ -116,7 +116,8 @@ class Batch:
         the branch-parallel kernel is not used)."""
         k = _capi.pg_batch_kernel(self.handle)
         return {"kernel": _capi.KERNEL_NAMES[k.kernel], "lanes_per_env": k.lanes_per_env, "branches": k.branches,
-                "reason": k.reason.decode(), "branch_parts": k.branch_parts, "barrier_per_substep": bool(k.sync)}
+                "reason": k.reason.decode(), "branch_parts": k.branch_parts, "barrier_per_substep": bool(k.sync),
+                "branch_dr": bool(k.branch_dr), "branch_tape": bool(k.branch_tape)}
 
     def __del__(self):
         h = getattr(self, "handle", None)

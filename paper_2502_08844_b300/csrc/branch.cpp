@@ -168,7 +168,8 @@ int branch_plan(const pg_model* m, std::string& src, std::string& why, int& lane
   }
   Src S;
   // ---- trunk tables ----
-  std::vector<int> tbpar(BT), tborg(BT), tjtype(BT * NJT, -1), tjq(BT * NJT, 0), tjd(BT * NJT, 0);
+  std::vector<int> tbpar(BT), tborg(BT), tjtype(BT * NJT, -1), tjq(BT * NJT, 0), tjd(BT * NJT, 0), tbg(BT, 0),
+      lbg(GP * BB, 0);
   std::vector<float> tbpos(3 * BT), tbquat(4 * BT), tbmass(BT), tbipos(3 * BT), tbinert(6 * BT), tborgp(3 * BT),
       tjpos(3 * BT * NJT, 0.f), tjaxis(3 * BT * NJT, 0.f);
   for (int k = 0; k < BT; k++) {
@@ -179,6 +180,7 @@ int branch_plan(const pg_model* m, std::string& src, std::string& why, int& lane
     for (int i = 0; i < 4; i++) tbquat[4 * k + i] = TF(body_quat, 4 * b + i);
     for (int i = 0; i < 6; i++) tbinert[6 * k + i] = TF(body_inertia, 6 * b + i);
     tbmass[k] = TF(body_mass, b);
+    tbg[k] = b;
     origin(b, tborg[k], &tborgp[3 * k]);
     for (int jj = 0; jj < TI(body_jntnum, b); jj++) {
       const int j = TI(body_jntadr, b) + jj, e = k * NJT + jj;
@@ -230,6 +232,7 @@ int branch_plan(const pg_model* m, std::string& src, std::string& why, int& lane
       for (int i = 0; i < 4; i++) lbquat[4 * e + i] = TF(body_quat, 4 * b + i);
       for (int i = 0; i < 6; i++) lbinert[6 * e + i] = TF(body_inertia, 6 * b + i);
       lbmass[e] = TF(body_mass, b);
+      lbg[e] = b;
       for (int jj = 0; jj < TI(body_jntnum, b); jj++) {
         const int j = TI(body_jntadr, b) + jj, d = bdof0[s] + jj, e2 = l * NB + d, gd = TI(jnt_dofadr, j);
         ljtype[e2] = TI(jnt_type, j);
@@ -335,6 +338,9 @@ int branch_plan(const pg_model* m, std::string& src, std::string& why, int& lane
   S.ci("NB", std::max(NB, 1)); S.ci("BB", BB); S.ci("PS", PS); S.ci("NCL", NCL); S.ci("LS", LS);
   S.ci("NTH", threads); S.ci("EPB", envs_per_block); S.ci("CAP", h.cap); S.ci("NSUB", h.substeps);
   S.ci("HF_NROW", std::max(h.hf_nrow, 2)); S.ci("HF_NCOL", std::max(h.hf_ncol, 2));
+  // rows of pg_step_dr's per-environment parameters
+  S.ci("DR_COM", h.dr_com); S.ci("DR_ARM", h.dr_arm); S.ci("DR_CAL", h.dr_cal); S.ci("DR_KP", h.dr_kp);
+  S.ci("DR_KD", h.dr_kd); S.ci("DR_MASS", h.dr_mass);
   S.cf("HSTEP", h.h); S.cf("GRAV_X", h.grav[0]); S.cf("GRAV_Y", h.grav[1]); S.cf("GRAV_Z", h.grav[2]);
   S.cf("KREF", h.kref); S.cf("BREF", h.bref); S.cf("MARGIN", h.margin);
   S.cf("SOLIMP_D0", h.solimp[0]); S.cf("SOLIMP_DW", h.solimp[1]); S.cf("SOLIMP_WIDTH", h.solimp[2]);
@@ -348,6 +354,7 @@ int branch_plan(const pg_model* m, std::string& src, std::string& why, int& lane
   S.ti("kTBpar", dims({BT}), tbpar); S.ti("kTBorg", dims({BT}), tborg);
   S.tf("kTBpos", dims({BT, 3}), tbpos); S.tf("kTBquat", dims({BT, 4}), tbquat); S.tf("kTBmass", dims({BT}), tbmass);
   S.tf("kTBipos", dims({BT, 3}), tbipos); S.tf("kTBinert", dims({BT, 6}), tbinert); S.tf("kTBorgp", dims({BT, 3}), tborgp);
+  S.ti("kTBg", dims({BT}), tbg); S.ti("kLBg", dims({GP, BB}), lbg);
   const int njt = std::max(NJT, 1);
   if (NJT == 0) { tjtype.assign(BT, -1); tjq.assign(BT, 0); tjd.assign(BT, 0); tjpos.assign(3 * BT, 0.f); tjaxis.assign(3 * BT, 0.f); }
   S.ti("kTJtype", dims({BT, njt}), tjtype); S.ti("kTJq", dims({BT, njt}), tjq); S.ti("kTJd", dims({BT, njt}), tjd);
@@ -394,6 +401,8 @@ int branch_plan(const pg_model* m, std::string& src, std::string& why, int& lane
          "{ pgb::branch_step<false>(A); }");
   S.line("extern \"C\" __global__ void __launch_bounds__(256) pg_step_branch_sync(const __grid_constant__ pg::BranchArgs A) "
          "{ pgb::branch_step<true>(A); }");
+  S.line("extern \"C\" __global__ void __launch_bounds__(256) pg_step_branch_dr(const __grid_constant__ pg::BranchArgs A) "
+         "{ pgb::branch_step<true, false, true>(A); }");
   if (m->hdr.adj_ok)   // the adjoint's tape replay (only for models inside its scope)
     S.line("extern \"C\" __global__ void __launch_bounds__(256) pg_step_branch_tape(const __grid_constant__ pg::BranchArgs A) "
            "{ pgb::branch_step<true, true>(A); }");
@@ -410,10 +419,11 @@ int branch_plan(const pg_model* m, std::string& src, std::string& why, int& lane
 cudaError_t launch_branch_range(cudaKernel_t k, cudaKernel_t k_sync, int lanes, int64_t env0, int64_t count,
                                 const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st,
                                 const pg_step_out* out, int nslot, float* tape, int tape_rows, int tape_nq,
-                                int tape_nv, int envs_per_block, const float* hfield) {
+                                int tape_nv, int envs_per_block, const float* hfield, const float* dr) {
   if (count <= 0) return cudaSuccess;
   BranchArgs A;
   A.hfield = hfield;
+  A.dr = dr;
   A.out_force = out ? out->contact_force : nullptr;
   A.out_ncon = out ? out->ncon : nullptr;
   A.out_nslot = nslot;
@@ -455,6 +465,12 @@ cudaError_t launch_branch(const pg_batch* b, const pg_state* s, const float* ctr
                           const pg_step_out* out) {
   return launch_branch_range(b->branch_kernel, b->branch_kernel_sync, b->branch_lanes, 0, s->n, s, ctrl, n_substeps,
                              st, out, b->nslot_max, nullptr, 0, 0, 0, b->envs_per_cta_req, b->hfield_ptr[0]);
+}
+
+cudaError_t launch_branch_dr(const pg_batch* b, const pg_state* s, const float* ctrl, const float* dr, int n_substeps,
+                             cudaStream_t st) {
+  return launch_branch_range(nullptr, b->branch_kernel_dr, b->branch_lanes, 0, s->n, s, ctrl, n_substeps, st, nullptr,
+                             b->nslot_max, nullptr, 0, 0, 0, b->envs_per_cta_req, b->hfield_ptr[0], dr);
 }
 
 cudaError_t launch_branch_tape(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, float* tape,

@@ -300,6 +300,8 @@ struct Lane {
   int64_t env, ld;
   const float* ctrl;
   const float* hf;   // the heightfield's elevations (device), or NULL
+  const float* dr;   // per-environment parameters [nrand][ld] (the DR variant), or NULL
+  __device__ __forceinline__ float dr_row(int k) const { return __ldg(dr + k * ld + env); }
   __device__ __forceinline__ float ctrl_row(int a) const { return __ldg(ctrl + a * ld + env); }
   // state: trunk (identical on the group's lanes) and branch
   float qT[NQT], vT[NT], wT[NT];
@@ -354,6 +356,19 @@ __device__ __forceinline__ void joint_1dof(int type, float3 lp, float3 la, float
   }
 }
 
+// a body's mass, centre of mass and inertia scale with the environment's parameters (DR): the mass
+// scale (mass and inertia), the payload on body 1, the centre-of-mass offset
+template <bool DR>
+__device__ __forceinline__ void body_params(const Lane& L, int g, float& m, float3& ip, float& iscale) {
+  iscale = 1.f;
+  if (!DR) return;
+  iscale = 1.f + L.dr_row(DR_MASS + g);
+  m *= iscale;
+  if (g == 1) m += L.dr_row(1);
+  ip = ip + make_float3(L.dr_row(DR_COM + 3 * g), L.dr_row(DR_COM + 3 * g + 1), L.dr_row(DR_COM + 3 * g + 2));
+}
+
+template <bool DR = false>
 __device__ __forceinline__ void kinematics(const Lane& L, Kin& K) {
   // trunk bodies in level order
 #pragma unroll
@@ -393,10 +408,20 @@ __device__ __forceinline__ void kinematics(const Lane& L, Kin& K) {
     K.xT[k] = x;
     K.qT[k] = q;
     K.oT[k] = o;
-    if (kTBmass[k] > 0.f) spatial_inertia(x, q, o, kTBmass[k], c3(kTBipos[k]), kTBinert[k], K.ciT[k]);
-    else
+    if (DR) {
+      float m = kTBmass[k], sc;
+      float3 ip = c3(kTBipos[k]);
+      body_params<DR>(L, kTBg[k], m, ip, sc);
+      float In[6];
+#pragma unroll
+      for (int i = 0; i < 6; i++) In[i] = sc * kTBinert[k][i];
+      spatial_inertia(x, q, o, m, ip, In, K.ciT[k]);
+    } else if (kTBmass[k] > 0.f) {
+      spatial_inertia(x, q, o, kTBmass[k], c3(kTBipos[k]), kTBinert[k], K.ciT[k]);
+    } else {
 #pragma unroll
       for (int i = 0; i < 10; i++) K.ciT[k][i] = 0.f;
+    }
   }
   // the lane's branch, from its attachment (a trunk body or the world)
   {
@@ -435,11 +460,12 @@ __device__ __forceinline__ void kinematics(const Lane& L, Kin& K) {
     q = qnormalize(q);
     K.xB[b] = x;
     K.qB[b] = q;
-    const float m = LV(kLBmass, [b]);
-    const float In[6] = {LV(kLBinert, [b][0]), LV(kLBinert, [b][1]), LV(kLBinert, [b][2]),
-                         LV(kLBinert, [b][3]), LV(kLBinert, [b][4]), LV(kLBinert, [b][5])};
-    spatial_inertia(x, q, K.oB, m, make_float3(LV(kLBipos, [b][0]), LV(kLBipos, [b][1]), LV(kLBipos, [b][2])), In,
-                    K.ciB[b]);
+    float m = LV(kLBmass, [b]), sc;
+    float3 ip = make_float3(LV(kLBipos, [b][0]), LV(kLBipos, [b][1]), LV(kLBipos, [b][2]));
+    body_params<DR>(L, LV(kLBg, [b]), m, ip, sc);
+    const float In[6] = {sc * LV(kLBinert, [b][0]), sc * LV(kLBinert, [b][1]), sc * LV(kLBinert, [b][2]),
+                         sc * LV(kLBinert, [b][3]), sc * LV(kLBinert, [b][4]), sc * LV(kLBinert, [b][5])};
+    spatial_inertia(x, q, K.oB, m, ip, In, K.ciB[b]);
   }
 }
 
@@ -554,6 +580,7 @@ __device__ __forceinline__ void rnea(const Lane& L, const Kin& K, float (&cB)[NB
 }
 
 // ---- composite-rigid-body mass matrix (in place on the inertias) ----
+template <bool DR = false>
 __device__ __forceinline__ void crba(Lane& L, Kin& K) {
 #pragma unroll
   for (int b = BB - 1; b >= 1; b--)
@@ -594,6 +621,7 @@ __device__ __forceinline__ void crba(Lane& L, Kin& K) {
 #pragma unroll
       for (int i = 0; i <= j; i++) L.MB[j][i] = dot6(K.cdB[i], fa, fl);
       L.MB[j][j] += LV(kLDarm, [j]);
+      if (DR && LV(kLDg, [j]) >= 0) L.MB[j][j] += L.dr_row(DR_ARM + LV(kLDg, [j]));
 #pragma unroll
       for (int t = 0; t < NT; t++) L.MBT[j][t] = ((anc >> t) & 1) ? dot6(K.cdT[t], fa, fl) : 0.f;
     }
@@ -604,6 +632,7 @@ __device__ __forceinline__ void crba(Lane& L, Kin& K) {
 #pragma unroll
     for (int s = 0; s <= t; s++) L.MT[t][s] = ((kTDanc[t] >> s) & 1) ? dot6(K.cdT[s], fa, fl) : 0.f;
     L.MT[t][t] += kTDarm[t];
+    if (DR) L.MT[t][t] += L.dr_row(DR_ARM + kTDg[t]);
   }
 }
 
@@ -1101,12 +1130,29 @@ __device__ __forceinline__ float line_search(const Lane& L, const float (&aB)[NB
 
 // one substep of the lane's environment; OUT: also write its contact forces and count (the last
 // substep of a pg_step_ex with outputs)
+// actuator a's force: act_force, with the environment's parameters in the DR variant (the
+// control clipped first, then a PD target's calibration offset and its gain scales)
+template <bool DR>
+__device__ __forceinline__ float act_force_env(const Lane& L, int a, int atype, float gear, float kp, float kd, int clim,
+                                               float lo, float hi, int flim, float flo, float fhi, float u, float q,
+                                               float qd) {
+  if (!DR) return act_force(atype, gear, kp, kd, clim, lo, hi, flim, flo, fhi, u, q, qd);
+  if (clim) u = fminf(fmaxf(u, lo), hi);
+  if (atype != PG_ACT_MOTOR) {
+    u += L.dr_row(DR_CAL + a);
+    kp *= 1.f + L.dr_row(DR_KP + a);
+    kd *= 1.f + L.dr_row(DR_KD + a);
+  }
+  return act_force(atype, gear, kp, kd, 0, lo, hi, flim, flo, fhi, u, q, qd);
+}
+
+template <bool DR = false>
 __device__ __forceinline__ void substep(Lane& L, uint32_t& status, uint32_t cnt[3], bool out, const BranchArgs& A) {
   Kin K;
-  kinematics(L, K);
+  kinematics<DR>(L, K);
   float cB[NB], cT[NT];
   rnea(L, K, cB, cT);
-  crba(L, K);
+  crba<DR>(L, K);
   // smooth forces tau = passive - bias + actuation, then a0 = M^-1 tau
   float tauB[NB], tauT[NT];
 #pragma unroll
@@ -1115,9 +1161,9 @@ __device__ __forceinline__ void substep(Lane& L, uint32_t& status, uint32_t cnt[
     const int a = LV(kLDact, [i]);
     if (a >= 0) {
       const float u = L.ctrl_row(a);
-      tau += act_force(LV(kLDatype, [i]), LV(kLDgear, [i]), LV(kLDkp, [i]), LV(kLDkd, [i]), LV(kLDclim, [i]),
-                       LV(kLDcr, [i][0]), LV(kLDcr, [i][1]), LV(kLDflim, [i]), LV(kLDfr, [i][0]), LV(kLDfr, [i][1]), u,
-                       L.qB[i], L.vB[i]);
+      tau += act_force_env<DR>(L, a, LV(kLDatype, [i]), LV(kLDgear, [i]), LV(kLDkp, [i]), LV(kLDkd, [i]),
+                               LV(kLDclim, [i]), LV(kLDcr, [i][0]), LV(kLDcr, [i][1]), LV(kLDflim, [i]),
+                               LV(kLDfr, [i][0]), LV(kLDfr, [i][1]), u, L.qB[i], L.vB[i]);
     }
     tauB[i] = tau;
   }
@@ -1126,8 +1172,9 @@ __device__ __forceinline__ void substep(Lane& L, uint32_t& status, uint32_t cnt[
     float tau = -kTDdamp[t] * L.vT[t] - cT[t];
     const int a = kTDact[t];
     if (a >= 0)
-      tau += act_force(kTDatype[t], kTDgear[t], kTDkp[t], kTDkd[t], kTDclim[t], kTDcr[t][0], kTDcr[t][1], kTDflim[t],
-                       kTDfr[t][0], kTDfr[t][1], L.ctrl_row(a), L.qT[kTDqa[t]], L.vT[t]);
+      tau += act_force_env<DR>(L, a, kTDatype[t], kTDgear[t], kTDkp[t], kTDkd[t], kTDclim[t], kTDcr[t][0],
+                               kTDcr[t][1], kTDflim[t], kTDfr[t][0], kTDfr[t][1], L.ctrl_row(a), L.qT[kTDqa[t]],
+                               L.vT[t]);
     tauT[t] = tau;
   }
   Factor FM;
@@ -1151,7 +1198,7 @@ __device__ __forceinline__ void substep(Lane& L, uint32_t& status, uint32_t cnt[
       const int c = pc0(s) + i;
       const bool valid = i < np && k[i].dist < MARGIN;
       dist[c] = valid ? k[i].dist : 1.f;
-      L.mu[c] = valid && LV(kPcond, [s]) == 3 ? LV(kPmu, [s]) : 0.f;
+      L.mu[c] = valid && LV(kPcond, [s]) == 3 ? LV(kPmu, [s]) * (DR ? L.dr_row(0) : 1.f) : 0.f;
       contact_rows(L, K, s, c, k[i].pos, k[i].n);   // (a contact that is not active gets D = 0)
     }
   }
@@ -1334,7 +1381,8 @@ __device__ __forceinline__ void substep(Lane& L, uint32_t& status, uint32_t cnt[
 // last environment then steps the last environment alongside (it writes nothing).
 // SYNC: the block's warps meet at a barrier before every substep.  TAPE: also record the adjoint's
 // substep tape (A.tape); a separate instantiation, so the plain step's code is untouched by it.
-template <bool SYNC, bool TAPE = false>
+// DR: per-environment parameters (A.dr, pg_step_dr's layout), another instantiation.
+template <bool SYNC, bool TAPE = false, bool DR = false>
 __device__ __forceinline__ void branch_step(const BranchArgs& A) {
   const int tid = threadIdx.x;
   Lane L;
@@ -1347,6 +1395,7 @@ __device__ __forceinline__ void branch_step(const BranchArgs& A) {
   L.ld = A.ld;
   L.ctrl = A.ctrl;
   L.hf = A.hfield;
+  L.dr = DR ? A.dr : nullptr;
   const int64_t ld = A.ld, env = L.env;
 #pragma unroll
   for (int i = 0; i < NQT; i++) L.qT[i] = A.qpos[kTQg[i] * ld + env];
@@ -1399,7 +1448,7 @@ __device__ __forceinline__ void branch_step(const BranchArgs& A) {
         }
       }
     }
-    substep(L, status, cnt, want && s == nsub - 1 && active, A);
+    substep<DR>(L, status, cnt, want && s == nsub - 1 && active, A);
     if (TAPE && tp) {   // the solver's acceleration (the next warm start)
       if (L.br == 0)
 #pragma unroll

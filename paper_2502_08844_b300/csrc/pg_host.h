@@ -75,6 +75,7 @@ struct pg_batch {
   cudaKernel_t branch_kernel = nullptr;
   cudaKernel_t branch_kernel_sync = nullptr;   // the same with a barrier per substep (the default launch)
   cudaKernel_t branch_kernel_tape = nullptr;   // the barrier launch recording the adjoint's substep tape
+  cudaKernel_t branch_kernel_dr = nullptr;     // the barrier launch with per-environment parameters
   int branch_lanes = 0, branch_count = 0;
   std::string branch_why;   // why a requested branch kernel is not used
   // staging buffer of the host-buffer path (allocated on its first use)
@@ -122,7 +123,10 @@ cudaError_t launch_branch_range(cudaKernel_t k, cudaKernel_t k_sync, int lanes, 
                                 const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st,
                                 const pg_step_out* out = nullptr, int nslot = 0, float* tape = nullptr,
                                 int tape_rows = 0, int tape_nq = 0, int tape_nv = 0, int envs_per_block = 0,
-                                const float* hfield = nullptr);
+                                const float* hfield = nullptr, const float* dr = nullptr);
+// the branch-parallel step with per-environment parameters (pg_step_dr's layout)
+cudaError_t launch_branch_dr(const pg_batch* b, const pg_state* s, const float* ctrl, const float* dr, int n_substeps,
+                             cudaStream_t st);
 // the branch-parallel step recording the adjoint's substep tape (layout of launch_step_tape)
 cudaError_t launch_branch_tape(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, float* tape,
                                int tape_rows, cudaStream_t st);

@@ -127,6 +127,7 @@ struct BranchArgs {
   int32_t* out_ncon;     // optional [ld] active contacts of the last substep, or NULL
   int out_nslot;
   const float* hfield;   // the model's heightfield elevations (device), or NULL
+  const float* dr;       // per-environment parameters [nrand][ld] (pg_step_dr), in the DR variant
   float* tape;           // optional substep record for the adjoint, or NULL: for substep s, rows
   int tape_rows, tape_nq, tape_nv;   // qpos [0, nq), qvel at tape_nq, warm start at tape_nq +
                                      // tape_nv, the solver's acceleration at tape_nq + 2 tape_nv

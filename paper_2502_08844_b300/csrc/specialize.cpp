@@ -224,11 +224,12 @@ int compile_cubin(const pg_model* m, std::vector<char>& cubin) {
 // reason in why)
 int compile_branch(const pg_model* m, bool warp_blocks, cudaLibrary_t& lib, cudaKernel_t& kernel,
                    cudaKernel_t& kernel_sync, int& lanes, int& branches, std::string& why,
-                   cudaKernel_t* kernel_tape = nullptr) {
+                   cudaKernel_t* kernel_tape = nullptr, cudaKernel_t* kernel_dr = nullptr) {
   lib = nullptr;
   kernel = nullptr;
   kernel_sync = nullptr;
   if (kernel_tape) *kernel_tape = nullptr;
+  if (kernel_dr) *kernel_dr = nullptr;
   std::string src;
   int threads = 0;
   if (branch_plan(m, src, why, lanes, threads, branches) != PG_OK) return PG_OK;
@@ -238,14 +239,29 @@ int compile_branch(const pg_model* m, bool warp_blocks, cudaLibrary_t& lib, cuda
   cudaError_t e = cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
   if (e != cudaSuccess) return set_error(PG_ECUDA, std::string("cudaLibraryLoadData: ") + cudaGetErrorString(e));
   e = cudaLibraryGetKernel(&kernel, lib, "pg_step_branch");
-  if (e == cudaSuccess && !warp_blocks) e = cudaLibraryGetKernel(&kernel_sync, lib, "pg_step_branch_sync");
+  if (e == cudaSuccess) e = cudaLibraryGetKernel(&kernel_sync, lib, "pg_step_branch_sync");
   if (e == cudaSuccess && kernel_tape) e = cudaLibraryGetKernel(kernel_tape, lib, "pg_step_branch_tape");
+  if (e == cudaSuccess && kernel_dr) e = cudaLibraryGetKernel(kernel_dr, lib, "pg_step_branch_dr");
+  // a variant that the compiler fitted far worse than the plain barrier kernel (ptxas has fallen
+  // back to 32 registers and a large stack frame for some of the humanoid's variants) is not used:
+  // its callers keep the thread-per-environment kernels
+  if (e == cudaSuccess && kernel_sync) {
+    cudaFuncAttributes base{}, var{};
+    if (cudaFuncGetAttributes(&base, (const void*)kernel_sync) == cudaSuccess)
+      for (cudaKernel_t* v : {kernel_tape, kernel_dr})
+        if (v && *v && cudaFuncGetAttributes(&var, (const void*)*v) == cudaSuccess &&
+            (var.numRegs < base.numRegs / 2 || var.localSizeBytes > 2 * base.localSizeBytes + 1024))
+          *v = nullptr;
+    cudaGetLastError();
+  }
+  if (warp_blocks) kernel_sync = nullptr;   // pg_step launches blocks of one warp, no barrier
   if (e != cudaSuccess) {
     cudaLibraryUnload(lib);
     lib = nullptr;
     kernel = nullptr;
     kernel_sync = nullptr;
     if (kernel_tape) *kernel_tape = nullptr;
+    if (kernel_dr) *kernel_dr = nullptr;
     return set_error(PG_ECUDA, std::string("branch kernel set-up: ") + cudaGetErrorString(e));
   }
   why.clear();
@@ -256,15 +272,16 @@ int compile_branch(const pg_model* m, bool warp_blocks, cudaLibrary_t& lib, cuda
 // goes to b->branch_why and the batch keeps its other kernels)
 int specialize_branch(pg_batch* b, bool warp_blocks) {
   cudaLibrary_t lib = nullptr;
-  cudaKernel_t k = nullptr, ks = nullptr, kt = nullptr;
+  cudaKernel_t k = nullptr, ks = nullptr, kt = nullptr, kd = nullptr;
   int lanes = 0, branches = 0;
   const int rc = compile_branch(b->models[0], warp_blocks, lib, k, ks, lanes, branches, b->branch_why,
-                                b->models[0]->hdr.adj_ok ? &kt : nullptr);
+                                b->models[0]->hdr.adj_ok ? &kt : nullptr, &kd);
   if (rc != PG_OK || !k) return rc;
   b->branch_lib = lib;
   b->branch_kernel = k;
   b->branch_kernel_sync = ks;
   b->branch_kernel_tape = kt;
+  b->branch_kernel_dr = kd;
   b->branch_lanes = lanes;
   b->branch_count = branches;
   return PG_OK;
@@ -345,6 +362,8 @@ extern "C" int pg_batch_kernel(const pg_batch* b, pg_kernel_info* out) {
     out->lanes_per_env = b->branch_lanes;
     out->branches = b->branch_count;
     out->sync = b->branch_kernel_sync != nullptr;
+    out->branch_dr = b->branch_kernel_dr != nullptr;
+    out->branch_tape = b->branch_kernel_tape != nullptr;
   } else if (b->spec_kernel) {
     out->kernel = PG_KERNEL_SPECIALISED;
   } else if (!b->spec_parts.empty()) {

@@ -78,6 +78,7 @@ cudaError_t configure_step_kernels(size_t smem_bytes) {
 cudaError_t launch_step(const pg_batch* b, const pg_state* s, const float* ctrl, int n_substeps, cudaStream_t st,
                         const float* dr, const pg_step_out* out) {
   if (b->branch_kernel && !dr) return launch_branch(b, s, ctrl, n_substeps, st, out);
+  if (b->branch_kernel_dr && dr && !out) return launch_branch_dr(b, s, ctrl, dr, n_substeps, st);
   if (b->spec_kernel) return pyramidal::step_spec(b, s, ctrl, n_substeps, st, dr, out);
   if (!b->spec_parts.empty() && !dr) return pyramidal::step_spec_parts(b, s, ctrl, n_substeps, st, out);
   return b->has_elliptic ? elliptic::step(b, s, ctrl, n_substeps, st, dr, out)

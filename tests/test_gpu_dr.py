@@ -18,9 +18,14 @@ pytestmark = pytest.mark.gpu
 
 
 def _run_dr(m, q0, v0, U, P, T, specialize=False):
+    """specialize: False (generic), True (the specialised thread-per-environment kernel) or
+    "branch" (the branch-parallel kernel's per-environment-parameter variant)"""
     run = GpuRun(m, q0.shape[0])
     if specialize:
-        run.batch.specialize()
+        run.batch.specialize(branch=specialize == "branch")
+        if specialize == "branch":
+            k = run.batch.kernel()
+            assert k["kernel"] == "branch-parallel" and k["branch_dr"]
     run.set_state(q0, v0)
     params = torch.from_numpy(core.to_soa(P, run.state.ld, P.shape[1])).to("cuda")
     for t in range(T):
@@ -34,14 +39,18 @@ def _oracle_env(m, q0, v0, U, p, T):
     return q[0], v[0]
 
 
+@pytest.mark.parametrize("specialize", [pytest.param(False, id="generic"), pytest.param("branch", id="branch")])
 @pytest.mark.parametrize("T,rtol", [(1, ONE_STEP_RTOL), (20, ROLLOUT_RTOL)])
-def test_step_dr_matches_the_substituted_oracle(T, rtol):
+def test_step_dr_matches_the_substituted_oracle(T, rtol, specialize):
+    """each environment against the oracle's substituted model: the generic kernel, and the
+    branch-parallel kernel's variant (masses, inertias, centres of mass, payload, armature,
+    calibration, gain scales and friction scale read per environment)"""
     m = W.quadruped()
     n = 24
     q0, v0 = W.initial_state(m, 1, n)
     U = W.actions(m, 1, n, 0, T)
     P = W.randomized_params(m, 1, n)
-    qg, vg, _ = _run_dr(m, q0, v0, U, P, T)
+    qg, vg, _ = _run_dr(m, q0, v0, U, P, T, specialize=specialize)
     for e in range(n):
         qo, vo = _oracle_env(m, q0[e], v0[e], U[:, e:e + 1], P[e], T)
         assert_close_scaled("qpos env %d" % e, canon_qpos(m, qg[e]), canon_qpos(m, qo), rtol)
@@ -63,6 +72,7 @@ def test_nominal_parameters_equal_the_plain_step():
 
 
 def test_specialised_step_dr_matches_generic():
+    """the specialised thread-per-environment kernel against the generic one (the same code)"""
     m = W.quadruped()
     n = 96
     q0, v0 = W.initial_state(m, 1, n)
@@ -131,3 +141,20 @@ def test_step_dr_elliptic_hand_with_friction_loss(specialize):
     moved = max(np.abs(_oracle_env(m, q0[e], v0[e], U[:, e:e + 1], P0[e], 1)[0]
                        - _oracle_env(m, q0[e], v0[e], U[:, e:e + 1], P[e], 1)[0]).max() for e in range(4))
     assert moved > 1e-5
+
+
+def test_branch_dr_with_nominal_parameters_follows_the_branch_step():
+    """the branch kernel's per-environment-parameter variant with nominal parameters (unit scales,
+    zero offsets) against the plain branch step: the same arithmetic up to contraction order"""
+    m = W.quadruped_rough()
+    n = 96
+    q0, v0 = W.initial_state(m, 1, n)
+    U = W.actions(m, 1, n, 0, 2)
+    P = np.zeros((n, RZ.nrand(m)), np.float32); P[:, 0] = 1.0
+    qd, vd, _ = _run_dr(m, q0, v0, U, P, 2, specialize="branch")
+    run = GpuRun(m, n)
+    run.batch.specialize()
+    run.set_state(q0, v0)
+    run.rollout(U, m.n_substeps)
+    qp, vp, _ = run.get()
+    assert np.allclose(qd, qp, rtol=1e-4, atol=1e-5) and np.allclose(vd, vp, rtol=1e-4, atol=1e-4)
