@@ -314,8 +314,54 @@ def measure_rough_terrain(dev, n: int = 8192, steps: int = 200, specialize: bool
     torch.cuda.synchronize()
     t = a.elapsed_time(b) / 1e3
     return {"value": n * steps / t, "unit": "env-steps/s", "envs": n, "steps": steps,
-            "terrain": "81 x 81 heightfield, 0.1 m cells, 6 cm relief",
-            "kernel": "model-specialised" if specialize else "generic"}
+            "terrain": "81 x 81 heightfield, 0.1 m cells, 6 cm relief", "kernel": batch.kernel()["kernel"]}
+
+
+def measure_dr(dev, n: int = 8192, steps: int = 200, specialize: bool = True):
+    """pg_step_dr on the bench workload (8192 quadrupeds) with every environment's parameters drawn
+    as in workloads.randomized_params (friction, payload, centres of mass, armature, calibration,
+    gains and link masses), against pg_step on the same batch: CUDA events around `steps` launches
+    each, the state device-resident."""
+    import torch
+    from paper_2502_08844_b300 import core
+    m = W.quadruped()
+    batch = core.Batch([(core.CompiledModel(m), n)])
+    if specialize:
+        batch.specialize()
+    st = core.State(batch, dev)
+    ld = st.ld
+    q0, v0 = W.initial_state(m, 1, n)
+    Q0 = torch.from_numpy(core.to_soa(q0, ld, batch.nq_max)).to(dev)
+    V0 = torch.from_numpy(core.to_soa(v0, ld, batch.nv_max)).to(dev)
+    U = np.zeros((steps, m.nu, ld), np.float32)
+    U[:, :, :n] = W.actions(m, 1, n, 0, steps).transpose(0, 2, 1)
+    ctrl = torch.from_numpy(U).to(dev)
+    P = W.randomized_params(m, 1, n)
+    params = torch.from_numpy(core.to_soa(P, ld, P.shape[1])).to(dev)
+
+    def run(dr):
+        core.reset(batch, st, Q0, V0)
+        for t in range(steps):
+            if dr:
+                core.step_dr(batch, st, ctrl[t], params, 0)
+            else:
+                core.step(batch, st, ctrl[t], 0)
+
+    def timed(dr):
+        run(dr)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(); run(dr); b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3
+
+    t_dr, t_plain = timed(True), timed(False)
+    k = batch.kernel()
+    return {"value": n * steps / t_dr, "unit": "env-steps/s", "envs": n, "steps": steps,
+            "plain_step_value": n * steps / t_plain, "overhead": t_dr / t_plain - 1.0,
+            "nrand": int(P.shape[1]),
+            "kernel": ("branch-parallel (pg_step_branch_dr)" if k["branch_dr"]
+                       else "thread-per-environment (%s)" % k["kernel"])}
 
 
 def measure_pixels(dev, n: int = 8192, steps: int = 50):
@@ -683,6 +729,7 @@ def run_ours(args):
     if single and not args.no_env:
         line["env_layer"] = measure_env_layer(dev, specialize=spec)
         line["rough_terrain"] = measure_rough_terrain(dev, specialize=spec)
+        line["domain_randomisation"] = measure_dr(dev, specialize=spec)
         line["pixels"] = measure_pixels(dev)
     if single and not args.no_adjoint:
         adj = measure_adjoint(dev, specialize=spec)

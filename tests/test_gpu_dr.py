@@ -158,3 +158,20 @@ def test_branch_dr_with_nominal_parameters_follows_the_branch_step():
     run.rollout(U, m.n_substeps)
     qp, vp, _ = run.get()
     assert np.allclose(qd, qp, rtol=1e-4, atol=1e-5) and np.allclose(vd, vp, rtol=1e-4, atol=1e-4)
+
+
+def test_branch_dr_on_rough_terrain_matches_the_substituted_oracle():
+    """The branch kernel's parameter variant on the rough terrain (heightfield-sphere feet): one
+    control step of each environment against the oracle's substituted model at the one-step
+    tolerance.  The friction scale enters the terrain contacts' pyramid edges, the mass
+    properties the kinematics and CRBA, and the calibration and gains the PD forces."""
+    m = W.quadruped_rough()
+    n = 24
+    q0, v0 = W.initial_state(m, 1, n)
+    U = W.actions(m, 1, n, 0, 1)
+    P = W.randomized_params(m, 1, n)
+    qg, vg, _ = _run_dr(m, q0, v0, U, P, 1, specialize="branch")
+    for e in range(n):
+        qo, vo = _oracle_env(m, q0[e], v0[e], U[:, e:e + 1], P[e], 1)
+        assert_close_scaled("qpos env %d" % e, canon_qpos(m, qg[e]), canon_qpos(m, qo), ONE_STEP_RTOL)
+        assert_close_scaled("qvel env %d" % e, vg[e], vo, ONE_STEP_RTOL)
