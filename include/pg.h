@@ -387,7 +387,8 @@ int pg_debug_substep(const pg_batch* batch, pg_state* state, const float* ctrl_d
 /* Host-buffer convenience path: copy ctrl_host ([nu_max][ld] floats, pinned recommended)
  * to a library-owned device buffer, run pg_step, copy qpos/qvel back to qpos_host/qvel_host
  * ([coord][ld]).  Returns after queuing; synchronise the stream before reading the host
- * outputs. */
+ * outputs.  The device buffer is allocated on the first call and grown (after synchronising the
+ * device) when a later call needs more. */
 int pg_step_host(pg_batch* batch, pg_state* state, const float* ctrl_host, float* qpos_host, float* qvel_host,
                  int n_substeps, void* stream);
 
@@ -399,7 +400,9 @@ int pg_step_host(pg_batch* batch, pg_state* state, const float* ctrl_host, float
  * events against `stream`.  The state advances as by n_steps pg_step calls with the same kernels.
  * Returns after queuing; the host outputs are complete when `stream` is synchronised.  Allocates
  * its double buffers (two control rows, two state snapshots) on first use or when the batch's
- * sizes outgrow them.  n_steps = 0 does nothing (the buffers may then be NULL).  Errors as
+ * sizes outgrow them (after synchronising the device, so that no earlier call still uses the old
+ * ones).  Calls on one batch share these buffers: issue them on one stream, or synchronise between
+ * calls on different streams.  n_steps = 0 does nothing (the buffers may then be NULL).  Errors as
  * pg_step_host, and PG_EINVAL for n_steps < 0. */
 int pg_rollout_host(pg_batch* batch, pg_state* state, const float* ctrl_host, float* qpos_host, float* qvel_host,
                     int n_steps, int n_substeps, void* stream);
@@ -448,8 +451,9 @@ int pg_rollout_host(pg_batch* batch, pg_state* state, const float* ctrl_host, fl
  *     workspace when 8 environments' workspaces do not fit in one block's 227 KB of shared
  *     memory), is library-owned: reserve it up front with pg_batch_reserve_vjp, after which
  *     calls within the reserved sizes allocate nothing. A call that needs more than is reserved
- *     grows it (and returns only after the allocation, so make such a call before any stream
- *     capture).
+ *     grows it: it synchronises the device (earlier calls' queued work may still use the old
+ *     scratch), frees the old and allocates the new, so make such a call before any stream
+ *     capture.
  *   * Calls on the same batch share the scratch: calls that overlap on the GPU race.
  *   * Errors: PG_EINVAL for NULL or inconsistent arguments, PG_EUNSUPPORTED,
  *     PG_ENOMEM / PG_ECUDA. */

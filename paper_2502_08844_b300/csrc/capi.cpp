@@ -282,7 +282,10 @@ int pg_step_host(pg_batch* b, pg_state* s, const float* ctrl_host, float* qpos_h
   cudaStream_t st = (cudaStream_t)stream;
   const size_t need = (size_t)std::max(b->nu_max, 1) * (size_t)s->ld;
   if (b->ctrl_stage_floats < need) {
-    if (b->d_ctrl_stage) cudaFree(b->d_ctrl_stage);
+    if (b->d_ctrl_stage) {   // an earlier call's queued upload and launch may still use it
+      cudaDeviceSynchronize();
+      cudaFree(b->d_ctrl_stage);
+    }
     b->d_ctrl_stage = nullptr;
     b->ctrl_stage_floats = 0;
     cudaError_t e = cudaMalloc(&b->d_ctrl_stage, need * sizeof(float));
@@ -305,6 +308,9 @@ int pg_step_host(pg_batch* b, pg_state* s, const float* ctrl_host, float* qpos_h
 static int host_stage(pg_batch* b, size_t ctrl_f, size_t snap_f) {
   pg_batch::HostStage& h = b->host_stage;
   if (h.in && h.ctrl_floats >= ctrl_f && h.snap_floats >= snap_f) return PG_OK;
+  // larger buffers: an earlier rollout's copies and launches (on its caller's stream too) may still
+  // read the old ones, so they finish before the old buffers are freed
+  if (h.in) cudaDeviceSynchronize();
   free_host_stage(h);
   cudaError_t e = cudaStreamCreateWithFlags(&h.in, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h.out, cudaStreamNonBlocking);
@@ -389,7 +395,10 @@ static int vjp_scratch(const pg_batch* b, int n_steps, int n_substeps, int64_t l
 
 static int grow_vjp(pg_batch* b, size_t need) {
   if (b->vjp_floats >= need) return PG_OK;
-  if (b->d_vjp) cudaFree(b->d_vjp);
+  if (b->d_vjp) {   // an earlier call's queued replay and sweep may still use it
+    cudaDeviceSynchronize();
+    cudaFree(b->d_vjp);
+  }
   b->d_vjp = nullptr;
   b->vjp_floats = 0;
   cudaError_t e = cudaMalloc(&b->d_vjp, need * sizeof(float));
