@@ -278,9 +278,14 @@ int pg_batch_specialize(pg_batch* batch);
  *                   actuator drives each dof, the cone is pyramidal, its pairs are primitives up to
  *                   boxes (a heightfield as geom1 included), it has no joint friction loss, and its
  *                   candidate contact points fit max_contacts; pg_batch_kernel reports why one does
- *                   not. The adjoint's tape replay runs on it too (a model inside the adjoint's
- *                   scope); pg_step_dr, pg_env_step and the adjoint's reverse sweep keep the
- *                   thread-per-environment kernels.
+ *                   not. Variants of it also run pg_step_dr (per-environment parameters), the
+ *                   physics of pg_env_step (without parameters; the task's targets and its reward
+ *                   to observation run as launches of the specialised kernel either side), and the
+ *                   adjoint's tape replay (a model inside the adjoint's scope); a variant that
+ *                   the compiler fits far worse than the plain kernel (pg_batch_kernel's branch_dr,
+ *                   branch_tape report which run) is left out, and its caller keeps the
+ *                   thread-per-environment kernel.  The adjoint's reverse sweep keeps the
+ *                   thread-per-environment kernel.
  *   0               the thread-per-environment specialised kernels only.
  *   PG_SPEC_BRANCH_WARP  see below.
  * Errors as pg_batch_specialize; flags other than these: PG_EINVAL. */
