@@ -23,6 +23,8 @@
  *   - Ownership: the caller owns every state, control, output and gradient buffer (for
  *     example torch tensors); the library owns models, batches and their device copies,
  *     all allocated at compile time.  pg_step allocates nothing.
+ *   - A batch holds per-batch staging buffers and scratch: issue the calls that use one batch
+ *     from one host thread at a time.
  *   - Batch state is structure-of-arrays: coordinate-major [coord][ld] float32 device
  *     arrays, env e of coordinate c at c*ld + e, with n <= ld (ld is the row pitch in
  *     elements).  In a mixed batch every array has max-over-models rows.
@@ -257,9 +259,10 @@ void pg_batch_free(pg_batch* batch);
  * Scope. For a single-model batch the specialised build covers the step, pg_step_dr, the
  * environment step (pg_env_step) and, for models inside the adjoint's scope, the tape replay and
  * reverse sweep of pg_step_vjp; the debug kernel stays generic. For a mixed batch pg_step runs
- * one specialised kernel per model over that model's blocks, one launch after the other (one
- * kernel holding every model's body measured slower: blocks of different models on one SM evict
- * each other's code from the instruction cache); its other kernels stay generic.
+ * one specialised kernel per model over that model's environments (one kernel holding every
+ * model's body measured slower: blocks of different models on one SM evict each other's code from
+ * the instruction cache), one launch after the other on the caller's stream (launched
+ * concurrently on forked streams they measured slower).  The batch's other kernels stay generic.
  *
  * Errors. PG_EUNSUPPORTED (NVRTC missing or failing, with its log in pg_last_error; the batch
  * then keeps the generic kernel), PG_ECUDA. */
