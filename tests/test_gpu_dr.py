@@ -175,3 +175,28 @@ def test_branch_dr_on_rough_terrain_matches_the_substituted_oracle():
         qo, vo = _oracle_env(m, q0[e], v0[e], U[:, e:e + 1], P[e], 1)
         assert_close_scaled("qpos env %d" % e, canon_qpos(m, qg[e]), canon_qpos(m, qo), ONE_STEP_RTOL)
         assert_close_scaled("qvel env %d" % e, vg[e], vo, ONE_STEP_RTOL)
+
+
+def test_humanoid_dr_on_a_branch_batch_matches_the_substituted_oracle():
+    """pg_step_dr on a humanoid batch specialised for the branch kernel: its parameter variant
+    runs when the compiler fits it like the plain kernel, and is otherwise left out for the
+    thread-per-environment kernel (pg_batch_kernel's branch_dr says which).  Either way one control
+    step of each environment matches the oracle's substituted model at the one-step tolerance."""
+    m = W.humanoid()
+    n = 8
+    q0, v0 = W.initial_state(m, 3, n)
+    U = W.actions(m, 3, n, 0, 1)
+    P = W.randomized_params(m, 3, n)
+    run = GpuRun(m, n)
+    run.batch.specialize(branch=True)
+    k = run.batch.kernel()
+    assert k["kernel"] == "branch-parallel", k
+    run.set_state(q0, v0)
+    params = torch.from_numpy(core.to_soa(P, run.state.ld, P.shape[1])).to("cuda")
+    core.step_dr(run.batch, run.state, run.ctrl_tensor(U[0]), params, m.n_substeps)
+    qg, vg, _ = run.get()
+    for e in range(n):
+        qo, vo = _oracle_env(m, q0[e], v0[e], U[:, e:e + 1], P[e], 1)
+        assert_close_scaled("qpos env %d (branch_dr %s)" % (e, k["branch_dr"]), canon_qpos(m, qg[e]),
+                            canon_qpos(m, qo), ONE_STEP_RTOL)
+        assert_close_scaled("qvel env %d" % e, vg[e], vo, ONE_STEP_RTOL)

@@ -138,3 +138,39 @@ def test_rollout_host_twice_and_zero_steps():
         assert np.array_equal(ref.qpos.cpu().numpy(), qh[t].numpy())
     with pytest.raises(_capi.PgError):
         _capi.pg_rollout_host(b.handle, st.c(), ctrl_h.data_ptr(), None, vh.data_ptr(), 1, 0, None)
+
+
+def test_rollout_host_staging_grows_for_a_wider_state():
+    """a rollout on a state of larger row pitch right after one on the batch's own state (still
+    queued, not synchronised) regrows the staging buffers; both rollouts return every step's state
+    bitwise equal to pg_step on a reference state"""
+    m = W.quadruped()
+    n, T = 64, 4
+    b = core.Batch([(core.CompiledModel(m), n)])
+    q0, v0 = W.initial_state(m, 1, n)
+    U = W.actions(m, 1, n, 0, T)
+
+    def state(ld):
+        st = core.State(b)
+        st.ld = ld
+        st.qpos = torch.from_numpy(core.to_soa(q0, ld, b.nq_max)).cuda()
+        st.qvel = torch.from_numpy(core.to_soa(v0, ld, b.nv_max)).cuda()
+        st.qacc_warm = torch.zeros((b.nv_max, ld), dtype=torch.float32, device="cuda")
+        return st
+
+    runs = []
+    for ld in (core.State(b).ld, core.State(b).ld + 96):
+        st = state(ld)
+        ctrl_h = torch.from_numpy(np.stack([core.to_soa(u, ld, b.nu_max) for u in U])).pin_memory()
+        qh = torch.zeros((T, b.nq_max, ld)).pin_memory()
+        vh = torch.zeros((T, b.nv_max, ld)).pin_memory()
+        core.rollout_host(b, st, ctrl_h, qh, vh, m.n_substeps)   # the second call regrows
+        runs.append((ld, ctrl_h, qh, vh))
+    torch.cuda.synchronize()
+    for ld, ctrl_h, qh, vh in runs:
+        ref = state(ld)
+        for t in range(T):
+            core.step(b, ref, ctrl_h[t].cuda(), m.n_substeps)
+            torch.cuda.synchronize()
+            assert np.array_equal(ref.qpos.cpu().numpy()[:, :n], qh[t].numpy()[:, :n]), (ld, t)
+            assert np.array_equal(ref.qvel.cpu().numpy()[:, :n], vh[t].numpy()[:, :n]), (ld, t)
