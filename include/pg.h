@@ -234,9 +234,12 @@ void pg_model_free(pg_model* model);
  * environments share a thread block of the thread-per-environment kernels (one thread each;
  * the default is one wave: about n / SMs per block) and, when not 0, of the branch-parallel
  * kernel's barrier launch (envs_per_cta / (32 / lanes per environment) warps a block, 1 to 8;
- * its default is one wave).  Allocates the batch's device tables and
- * nothing else; the scratch of pg_step_vjp is reserved by pg_batch_reserve_vjp (or by the first
- * pg_step_vjp call that needs it). */
+ * its default is one wave).  With envs_per_cta 0 the thread-per-environment kernels hold each
+ * model's environments in warps of its widest width (pg_batch_kernel's envs_per_warp), unless
+ * they need more than one wave at that width: then at the width whose block holds the most of them
+ * (fewer waves, more schedulers busy, less divergence; no change to the arithmetic).  Allocates
+ * the batch's device tables and nothing else; the scratch of pg_step_vjp is reserved by
+ * pg_batch_reserve_vjp (or by the first pg_step_vjp call that needs it). */
 int pg_batch_compile(const pg_model* const* models, const int64_t* counts, int nmodels, int envs_per_cta,
                      pg_batch** out);
 int pg_batch_info(const pg_batch* batch, int64_t* n_envs, int* nq_max, int* nv_max, int* nu_max);
@@ -313,6 +316,7 @@ typedef struct {
   int sync;            /* branch kernel launched with a barrier per substep (the default)        */
   int branch_dr;       /* pg_step_dr runs the branch kernel's per-environment-parameter variant   */
   int branch_tape;     /* the adjoint's forward recording runs the branch kernel's tape variant    */
+  int envs_per_warp;   /* thread-per-environment kernels: environments per warp of the first model */
 } pg_kernel_info;
 int pg_batch_kernel(const pg_batch* batch, pg_kernel_info* out);
 /* Whether a model qualifies for the branch-parallel kernel (host only, no device work): out->kernel

@@ -83,7 +83,8 @@ class pg_step_out(C.Structure):
 
 class pg_kernel_info(C.Structure):
     _fields_ = [("kernel", C.c_int), ("lanes_per_env", C.c_int), ("branches", C.c_int), ("reason", C.c_char * 160),
-                ("branch_parts", C.c_int), ("sync", C.c_int), ("branch_dr", C.c_int), ("branch_tape", C.c_int)]
+                ("branch_parts", C.c_int), ("sync", C.c_int), ("branch_dr", C.c_int), ("branch_tape", C.c_int),
+                ("envs_per_warp", C.c_int)]
 
 
 class pg_render_desc(C.Structure):

@@ -117,7 +117,7 @@ class Batch:
         k = _capi.pg_batch_kernel(self.handle)
         return {"kernel": _capi.KERNEL_NAMES[k.kernel], "lanes_per_env": k.lanes_per_env, "branches": k.branches,
                 "reason": k.reason.decode(), "branch_parts": k.branch_parts, "barrier_per_substep": bool(k.sync),
-                "branch_dr": bool(k.branch_dr), "branch_tape": bool(k.branch_tape)}
+                "branch_dr": bool(k.branch_dr), "branch_tape": bool(k.branch_tape), "envs_per_warp": k.envs_per_warp}
 
     def __del__(self):
         h = getattr(self, "handle", None)

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cstring>
 #include <new>
 #include <string>
@@ -136,8 +137,30 @@ int pg_batch_compile(const pg_model* const* models, const int64_t* counts, int n
   size_t smem = 0;
   int nwarps_max = 1;
   for (int k = 0; k < nmodels; k++) {
-    const int soa = models[k]->hdr.soa;
-    const size_t per_warp = (size_t)4 * soa * models[k]->hdr.ws_floats;
+    const int ws = models[k]->hdr.ws_floats;
+    // environments a block holds at soa environments per warp (shared memory; at most 8 warps)
+    auto block_envs = [&](int soa) {
+      return (int)std::min<size_t>((size_t)kMaxSmem / ((size_t)4 * soa * ws), kMaxEnvsPerCta / 32) * soa;
+    };
+    // Environments per warp.  The model's widest width, unless its environments need more than one
+    // wave of blocks at that width: then the width whose block holds the most environments (the
+    // widest among equals).  A large workspace limits an SM to a few environments; held as one wide
+    // warp they run on one of its four schedulers with their branches serialised, while narrower
+    // warps hold more of them, fill more schedulers and diverge less (8192 hands: 16 environments
+    // an SM as one warp, or 20 as five warps of 4, 35 % faster with the elliptic cone).  When every
+    // environment fits in one wave anyway, extra warps only contend for the instruction cache
+    // (2048 humanoids run 19 % slower at 8 than at 16 a warp).  The width changes no arithmetic.
+    int soa = models[k]->hdr.soa;
+    if (!envs_per_cta && counts[k] > (int64_t)sms * block_envs(soa)) {
+      int most = block_envs(soa);
+      for (int s = soa / 2; s >= 1; s /= 2)
+        if (block_envs(s) > most) {
+          most = block_envs(s);
+          soa = s;
+        }
+    }
+    b->soa.push_back(soa);
+    const size_t per_warp = (size_t)4 * soa * ws;
     const int warps_fit = (int)std::min<size_t>((size_t)kMaxSmem / per_warp, kMaxEnvsPerCta / 32);
     const int cap = warps_fit * soa;
     if (envs_per_cta && envs_per_cta > cap) { delete b; return set_error(PG_ECAPACITY, "envs_per_cta exceeds shared memory for these models"); }
@@ -154,6 +177,7 @@ int pg_batch_compile(const pg_model* const* models, const int64_t* counts, int n
   for (int k = 0; k < nmodels; k++) {
     b->blob_off[k] = (int)all.size();
     all.insert(all.end(), models[k]->blob.begin(), models[k]->blob.end());
+    all[b->blob_off[k] + offsetof(ModelHdr, soa) / 4] = (uint32_t)b->soa[k];   // this batch's width
   }
   if ((int)all.size() > kMaxParamWords) { delete b; return set_error(PG_ECAPACITY, "the batch's model tables exceed the 28 KB kernel-parameter budget"); }
   b->blob_host = all;

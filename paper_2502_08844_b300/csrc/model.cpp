@@ -603,10 +603,11 @@ int compile_model(const pg_model_desc* d, pg_model* out) {
     h.adj_ok = g.adj_ok;
     h.ws_adj_floats = g.ws_adj_floats;
   }
-  // environments per warp block: the largest power of two <= 32 whose workspaces fit in shared memory
+  if ((size_t)4 * h.ws_floats > (size_t)kMaxSmem) return set_error(PG_ECAPACITY, "one environment's workspace exceeds shared memory");
+  // environments per warp (soa): the largest power of two <= 32 whose warp of workspaces fits in
+  // shared memory.  A batch may run the model narrower (pg_batch_compile).
   h.soa = 32;
   while (h.soa > 1 && (size_t)4 * h.soa * h.ws_floats > (size_t)kMaxSmem) h.soa /= 2;
-  if ((size_t)4 * h.ws_floats > (size_t)kMaxSmem) return set_error(PG_ECAPACITY, "one environment's workspace exceeds shared memory");
   // ---- debug record layout ----
   int q = 0;
   auto dbg = [&](int n) { int r = q; q += n; return r; };

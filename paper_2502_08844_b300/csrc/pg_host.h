@@ -70,6 +70,7 @@ struct pg_batch {
     int model;   // the part's model in the batch
   };
   std::vector<SpecPart> spec_parts;
+  std::vector<int> soa;   // each model's environments per warp in this batch (its header's soa in blob_host)
   // the branch-parallel step kernel (pg_batch_specialize_ex with PG_SPEC_BRANCH), else NULL
   cudaLibrary_t branch_lib = nullptr;
   cudaKernel_t branch_kernel = nullptr;

@@ -19,6 +19,7 @@
 #include <sys/stat.h>
 #include <unistd.h>
 
+#include <cstddef>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -134,18 +135,20 @@ void write_file(const std::string& p, const std::vector<char>& data) {
   else remove(tmp.c_str());
 }
 
-// The generated translation unit: the model's blob as a constant array with its SoA width
-// (SpecModel<0>), then the kernel body and the kernel.
-std::string spec_source(const pg_model* m) {
+// The generated translation unit: the model's blob as a constant array with the batch's SoA width
+// soa (SpecModel<0>, and the header's soa word), then the kernel body and the kernel.
+std::string spec_source(const pg_model* m, int soa) {
   std::string s;
+  std::vector<uint32_t> blob = m->blob;
+  blob[offsetof(ModelHdr, soa) / 4] = (uint32_t)soa;
   s += "#define PG_WITH_ELLIPTIC " + std::string(m->hdr.cone == PG_CONE_ELLIPTIC ? "1" : "0") + "\n";
   s += "#define PG_SPEC 1\n#include \"pg_internal.h\"\nnamespace pg {\ntemplate <int M> struct SpecModel;\n";
   // in the constant bank: reads at compile-time indices fold away, the rest are uniform
   // constant-cache loads (every thread steps the same model)
-  s += "__constant__ const uint32_t kSpecBlob[" + std::to_string(m->blob.size()) + "] __attribute__((aligned(16))) = {";
-  for (size_t i = 0; i < m->blob.size(); i++) {
+  s += "__constant__ const uint32_t kSpecBlob[" + std::to_string(blob.size()) + "] __attribute__((aligned(16))) = {";
+  for (size_t i = 0; i < blob.size(); i++) {
     if (i % 16 == 0) s += "\n";
-    s += std::to_string(m->blob[i]) + "u,";
+    s += std::to_string(blob[i]) + "u,";
   }
   s += "\n};\n";
   const bool adj = m->hdr.adj_ok && m->hdr.cone != PG_CONE_ELLIPTIC;
@@ -158,7 +161,7 @@ std::string spec_source(const pg_model* m) {
     }
     s += "\n};\n";
   }
-  s += "template <> struct SpecModel<0> {\n  static constexpr int soa = " + std::to_string(m->hdr.soa) +
+  s += "template <> struct SpecModel<0> {\n  static constexpr int soa = " + std::to_string(soa) +
        ";\n  __device__ static const uint32_t* blob() { return kSpecBlob; }\n";
   if (adj)
     s += "  static constexpr int vjp_soa = " + std::to_string(vjp_smem_soa(m->hdr_adj.ws_adj_floats)) +
@@ -216,8 +219,8 @@ int compile_source(const std::string& src, const char* name, std::vector<char>& 
   return PG_OK;
 }
 
-int compile_cubin(const pg_model* m, std::vector<char>& cubin) {
-  return compile_source(spec_source(m), "pg_step_spec.cu", cubin);
+int compile_cubin(const pg_model* m, int soa, std::vector<char>& cubin) {
+  return compile_source(spec_source(m, soa), "pg_step_spec.cu", cubin);
 }
 
 // the branch-parallel kernel of a model, when it qualifies: lib and kernel set (else NULL, with the
@@ -322,11 +325,11 @@ static int specialize_parts(pg_batch* b, unsigned flags) {
         part.ntiles++;
       }
     if (part.tile0 < 0) part.tile0 = 0;
-    const int soa = m->hdr.soa, nw = (b->envs_per_cta[k] + soa - 1) / soa;
+    const int soa = b->soa[k], nw = (b->envs_per_cta[k] + soa - 1) / soa;
     part.threads = 32 * nw;
     part.smem = (size_t)4 * nw * soa * m->hdr.ws_floats;
     std::vector<char> cubin;
-    int rc = compile_cubin(m, cubin);
+    int rc = compile_cubin(m, soa, cubin);
     if (rc != PG_OK) return fail(rc);
     e = cudaLibraryLoadData(&part.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
     if (e != cudaSuccess) return fail(set_error(PG_ECUDA, std::string("cudaLibraryLoadData: ") + cudaGetErrorString(e)));
@@ -357,6 +360,7 @@ extern "C" int pg_batch_kernel(const pg_batch* b, pg_kernel_info* out) {
   if (!b || !out) return set_error(PG_EINVAL, "batch or out is NULL");
   std::memset(out, 0, sizeof(*out));
   out->lanes_per_env = 1;
+  out->envs_per_warp = b->soa.empty() ? 0 : b->soa[0];
   if (b->branch_kernel) {
     out->kernel = PG_KERNEL_BRANCH;
     out->lanes_per_env = b->branch_lanes;
@@ -406,7 +410,7 @@ extern "C" int pg_batch_specialize_ex(pg_batch* b, unsigned flags) {
   }
   if (b->spec_kernel) return PG_OK;
   std::vector<char> cubin;
-  int rc = compile_cubin(b->models[0], cubin);
+  int rc = compile_cubin(b->models[0], b->soa[0], cubin);
   if (rc != PG_OK) return rc;
   cudaLibrary_t lib = nullptr;
   cudaError_t e = cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);

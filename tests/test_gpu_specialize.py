@@ -83,3 +83,25 @@ def test_specialised_adjoint_matches_generic():
     for k in ("q0", "v0", "u", "mass", "damping", "kp"):
         x, y = a[k], b[k]
         assert np.abs(x - y).max() <= 1e-4 * max(np.abs(x).max(), 1e-6), (k, np.abs(x - y).max())
+
+
+@pytest.mark.parametrize("mname,spec", [("hand_elliptic", False), ("hand_elliptic", True), ("hand", True)])
+def test_environments_per_warp_change_no_arithmetic(mname, spec):
+    """8192 hands need more than one wave of blocks at 16 environments a warp, so the batch runs
+    them 4 a warp (20 a block); a batch given 16 environments a block keeps 16 a warp.  The width
+    only moves the workspaces: two control steps are bitwise equal."""
+    m = W.model(mname)
+    n = 8192
+    q0, v0 = W.initial_state(m, 2, n)
+    U = W.actions(m, 2, n, 0, 2)
+    out = []
+    for epc, width in ((0, 4), (16, 16)):
+        run = GpuRun(m, n, envs_per_cta=epc)
+        if spec:
+            run.batch.specialize(branch=False)
+        assert run.batch.kernel()["envs_per_warp"] == width
+        run.set_state(q0, v0)
+        run.rollout(U, m.n_substeps)
+        out.append(run.get())
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
