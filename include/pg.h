@@ -255,7 +255,8 @@ void pg_batch_free(pg_batch* batch);
  * the generic kernel's to rounding (not bit for bit).
  *
  * How. The kernel is compiled with NVRTC (libnvrtc.so.13, loaded on first use) for sm_103a and
- * cached per process and on disk ($PG_KERNEL_CACHE, else ~/.cache/paper_2502_08844_b300/kernels).
+ * cached per process and on disk ($PG_KERNEL_CACHE, else ~/.cache/paper_2502_08844_b300/kernels);
+ * cubins that pg_model_precompile wrote into kernel_cache/ beside the library file are used too.
  * A first compile takes seconds, so call this before any stream capture and outside timed
  * regions.
  *
@@ -324,6 +325,26 @@ int pg_batch_kernel(const pg_batch* batch, pg_kernel_info* out);
  * reason.  With the environment variable PG_BRANCH_SOURCE set to a path, the kernel source
  * generated for the model is written there (a developer aid). */
 int pg_model_branch_plan(const pg_model* model, pg_kernel_info* out);
+
+/* Compile ahead of time, with NVRTC and without any device work, the cubins that
+ * pg_batch_specialize_ex(batch, flags) needs for `count` environments of `model` in a batch
+ * compiled with envs_per_cta: the specialised thread-per-environment kernels at the width
+ * pg_batch_compile takes on `sms` multiprocessors (0: 148, a B300's), and with PG_SPEC_BRANCH or
+ * PG_SPEC_BRANCH_WARP the branch-parallel kernel when the model qualifies.  They go to the
+ * directory `dir` (NULL or "": the disk cache that pg_batch_specialize writes), named by the same
+ * key pg_batch_specialize looks them up by (the generated source, the NVRTC version and the
+ * library's embedded kernel headers); a cubin already there is not compiled again.
+ * pg_batch_specialize also reads kernel_cache/ beside the library file, so cubins compiled there
+ * when the library is built spare its first calls the compile (seconds to a minute per model);
+ * the kernels are the same either way.  Host only; may be called from several threads at once.
+ * envs_per_warp, when not NULL, receives the thread-per-environment kernels' width; with
+ * PG_PRECOMPILE_WIDTH_ONLY in flags nothing is compiled.  The paper has no counterpart: this is a
+ * build step of the run-time specialisation.
+ * Errors: PG_EINVAL (NULL model, negative count or sms, envs_per_cta outside 0..256, unknown
+ * flags), PG_EUNSUPPORTED (NVRTC missing or failing, with its log in pg_last_error). */
+#define PG_PRECOMPILE_WIDTH_ONLY 4u
+int pg_model_precompile(const pg_model* model, int64_t count, int envs_per_cta, int sms, unsigned flags,
+                        const char* dir, int* envs_per_warp);
 
 /* Reset the envs whose env_mask_dev[e] != 0 (all envs when env_mask_dev is NULL): copy
  * qpos0/qvel0 ([coord][ld], same layout as the state), zero qacc_warm and status. */

@@ -73,6 +73,7 @@ PG_PIXELS_U8, PG_PIXELS_F32 = 0, 1
 
 PG_SPEC_BRANCH = 1
 PG_SPEC_BRANCH_WARP = 2
+PG_PRECOMPILE_WIDTH_ONLY = 4
 PG_KERNEL_GENERIC, PG_KERNEL_SPECIALISED, PG_KERNEL_SPECIALISED_PARTS, PG_KERNEL_BRANCH = 0, 1, 2, 3
 KERNEL_NAMES = {0: "generic", 1: "specialised", 2: "specialised per model", 3: "branch-parallel"}
 
@@ -99,7 +100,7 @@ EXPORTS = ["pg_model_compile", "pg_model_info", "pg_model_free", "pg_batch_compi
            "pg_batch_free", "pg_reset", "pg_step", "pg_step_dr", "pg_debug_substep", "pg_step_host", "pg_rollout_host", "pg_step_vjp",
            "pg_step_vjp_noalloc", "pg_batch_specialize", "pg_batch_specialize_ex", "pg_batch_kernel",
            "pg_step_ex", "pg_batch_nslot", "pg_batch_reserve_vjp",
-           "pg_model_branch_plan", "pg_task_compile", "pg_task_info", "pg_task_free",
+           "pg_model_branch_plan", "pg_model_precompile", "pg_task_compile", "pg_task_info", "pg_task_free",
            "pg_env_reset", "pg_env_step", "pg_render", "pg_last_error"]
 
 if not os.path.exists(LIB_PATH):
@@ -133,6 +134,7 @@ _lib.pg_batch_nslot.argtypes = [C.c_void_p]
 _lib.pg_batch_reserve_vjp.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int64]
 _lib.pg_batch_kernel.argtypes = [C.c_void_p, C.POINTER(pg_kernel_info)]
 _lib.pg_model_branch_plan.argtypes = [C.c_void_p, C.POINTER(pg_kernel_info)]
+_lib.pg_model_precompile.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_uint, C.c_char_p, _ip]
 _lib.pg_step_vjp_noalloc.argtypes = [C.c_void_p, C.POINTER(pg_state), C.c_void_p, C.c_int, C.c_int] + [C.c_void_p] * 7
 _lib.pg_task_compile.argtypes = [C.c_void_p, C.POINTER(pg_task_desc), C.POINTER(C.c_void_p)]
 _lib.pg_task_info.argtypes = [C.c_void_p, C.POINTER(pg_task_sizes)]
@@ -269,6 +271,15 @@ def pg_model_branch_plan(model) -> pg_kernel_info:
     out = pg_kernel_info()
     _check(_lib.pg_model_branch_plan(model, C.byref(out)), "pg_model_branch_plan")
     return out
+
+
+def pg_model_precompile(model, count: int, envs_per_cta: int, sms: int, flags: int, dir_) -> int:
+    """dir_: a directory or None (the disk cache).  Returns the thread-per-environment kernels'
+    width (environments per warp)."""
+    w = C.c_int(0)
+    _check(_lib.pg_model_precompile(model, int(count), int(envs_per_cta), int(sms), flags,
+                                    None if dir_ is None else dir_.encode(), C.byref(w)), "pg_model_precompile")
+    return w.value
 
 
 def pg_task_compile(model, desc: pg_task_desc) -> C.c_void_p:

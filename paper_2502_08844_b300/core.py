@@ -77,6 +77,20 @@ class CompiledModel:
         return {"branch": k.kernel == _capi.PG_KERNEL_BRANCH, "lanes_per_env": k.lanes_per_env,
                 "branches": k.branches, "reason": k.reason.decode()}
 
+    def precompile(self, count: int, envs_per_cta: int = 0, branch: bool = True, cache_dir: str = None,
+                   sms: int = 0) -> int:
+        """pg_model_precompile: compile with NVRTC, without device work, the kernels that
+        Batch.specialize(branch) needs for `count` environments of this model (a batch with
+        envs_per_cta), into cache_dir (None: the disk cache).  Returns the thread-per-environment
+        kernels' width."""
+        return _capi.pg_model_precompile(self.handle, count, envs_per_cta, sms,
+                                         _capi.PG_SPEC_BRANCH if branch else 0, cache_dir)
+
+    def envs_per_warp(self, count: int, envs_per_cta: int = 0, sms: int = 0) -> int:
+        """The thread-per-environment kernels' width (environments per warp) for `count`
+        environments of this model, as pg_batch_compile chooses it (host only)."""
+        return _capi.pg_model_precompile(self.handle, count, envs_per_cta, sms, _capi.PG_PRECOMPILE_WIDTH_ONLY, None)
+
     @property
     def nq(self):
         return self.sizes.nq

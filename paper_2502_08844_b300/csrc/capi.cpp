@@ -27,7 +27,33 @@ static int cuda_error(cudaError_t e, const char* what) {
                    std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-
+// Environments per warp of the thread-per-environment kernels for `count` environments of model m
+// (envs_per_cta as pg_batch_compile takes it; sms multiprocessors).  The model's widest width,
+// unless its environments need more than one wave of blocks at that width: then the width whose
+// block holds the most environments (the widest among equals).  A large workspace limits an SM to
+// a few environments; held as one wide warp they run on one of its four schedulers with their
+// branches serialised, while narrower warps hold more of them, fill more schedulers and diverge
+// less (8192 hands: 16 environments an SM as one warp, or 20 as five warps of 4, 35 % faster with
+// the elliptic cone).  When every environment fits in one wave anyway, extra warps only contend
+// for the instruction cache (2048 humanoids run 19 % slower at 8 than at 16 a warp).  The width
+// changes no arithmetic.
+int thread_soa(const pg_model* m, int64_t count, int envs_per_cta, int sms) {
+  const int ws = m->hdr.ws_floats;
+  // environments a block holds at soa environments per warp (shared memory; at most 8 warps)
+  auto block_envs = [&](int soa) {
+    return (int)std::min<size_t>((size_t)kMaxSmem / ((size_t)4 * soa * ws), kMaxEnvsPerCta / 32) * soa;
+  };
+  int soa = m->hdr.soa;
+  if (!envs_per_cta && count > (int64_t)sms * block_envs(soa)) {
+    int most = block_envs(soa);
+    for (int s = soa / 2; s >= 1; s /= 2)
+      if (block_envs(s) > most) {
+        most = block_envs(s);
+        soa = s;
+      }
+  }
+  return soa;
+}
 }  // namespace pg
 
 using namespace pg;
@@ -138,27 +164,7 @@ int pg_batch_compile(const pg_model* const* models, const int64_t* counts, int n
   int nwarps_max = 1;
   for (int k = 0; k < nmodels; k++) {
     const int ws = models[k]->hdr.ws_floats;
-    // environments a block holds at soa environments per warp (shared memory; at most 8 warps)
-    auto block_envs = [&](int soa) {
-      return (int)std::min<size_t>((size_t)kMaxSmem / ((size_t)4 * soa * ws), kMaxEnvsPerCta / 32) * soa;
-    };
-    // Environments per warp.  The model's widest width, unless its environments need more than one
-    // wave of blocks at that width: then the width whose block holds the most environments (the
-    // widest among equals).  A large workspace limits an SM to a few environments; held as one wide
-    // warp they run on one of its four schedulers with their branches serialised, while narrower
-    // warps hold more of them, fill more schedulers and diverge less (8192 hands: 16 environments
-    // an SM as one warp, or 20 as five warps of 4, 35 % faster with the elliptic cone).  When every
-    // environment fits in one wave anyway, extra warps only contend for the instruction cache
-    // (2048 humanoids run 19 % slower at 8 than at 16 a warp).  The width changes no arithmetic.
-    int soa = models[k]->hdr.soa;
-    if (!envs_per_cta && counts[k] > (int64_t)sms * block_envs(soa)) {
-      int most = block_envs(soa);
-      for (int s = soa / 2; s >= 1; s /= 2)
-        if (block_envs(s) > most) {
-          most = block_envs(s);
-          soa = s;
-        }
-    }
+    const int soa = thread_soa(models[k], counts[k], envs_per_cta, sms);
     b->soa.push_back(soa);
     const size_t per_warp = (size_t)4 * soa * ws;
     const int warps_fit = (int)std::min<size_t>((size_t)kMaxSmem / per_warp, kMaxEnvsPerCta / 32);

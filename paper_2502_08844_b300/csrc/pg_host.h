@@ -115,6 +115,8 @@ void once_per_device(std::mutex& mu, unsigned long long& done, F&& f) {
   done |= bit;
 }
 int compile_model(const pg_model_desc* d, pg_model* out);
+// capi.cpp: environments per warp of the thread-per-environment kernels (pg_batch_compile's rule)
+int thread_soa(const pg_model* m, int64_t count, int envs_per_cta, int sms);
 // branch.cpp: the branch-parallel kernel's plan and generated source for a model
 int branch_plan(const pg_model* m, std::string& src, std::string& why, int& lanes_per_env, int& threads,
                 int& branches);

@@ -23,6 +23,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <string>
@@ -104,6 +105,19 @@ std::string cache_dir() {
   return std::string(home ? home : "/tmp") + "/.cache/paper_2502_08844_b300/kernels";
 }
 
+// Cubins compiled ahead of time (pg_model_precompile) into kernel_cache/ beside the library file,
+// read only; empty when the library's path is unknown.
+const std::string& shipped_cache_dir() {
+  static const std::string dir = [] {
+    Dl_info info{};
+    if (!dladdr((const void*)&shipped_cache_dir, &info) || !info.dli_fname) return std::string();
+    const std::string lib = info.dli_fname;
+    const size_t slash = lib.rfind('/');
+    return (slash == std::string::npos ? std::string(".") : lib.substr(0, slash)) + "/kernel_cache";
+  }();
+  return dir;
+}
+
 void mkdirs(const std::string& path) {
   std::string cur;
   for (size_t i = 0; i < path.size(); i++) {
@@ -126,7 +140,10 @@ bool read_file(const std::string& p, std::vector<char>& out) {
 }
 
 void write_file(const std::string& p, const std::vector<char>& data) {
-  const std::string tmp = p + ".tmp" + std::to_string((long)getpid());
+  // a temporary name of this process and call, renamed into place: concurrent writers of one
+  // cubin (threads or processes) never see each other's partial file
+  static std::atomic<unsigned> serial{0};
+  const std::string tmp = p + ".tmp" + std::to_string((long)getpid()) + "." + std::to_string(serial++);
   FILE* f = fopen(tmp.c_str(), "wb");
   if (!f) return;
   const bool ok = fwrite(data.data(), 1, data.size(), f) == data.size();
@@ -177,40 +194,64 @@ std::string spec_source(const pg_model* m, int soa) {
   return s;
 }
 
-// compile (or find in the caches) the cubin of a generated source
-int compile_source(const std::string& src, const char* name, std::vector<char>& cubin) {
+// NVRTC: the cubin of a generated source for sm_103a
+int nvrtc_compile(const std::string& src, const char* name, std::vector<char>& cubin) {
+  const Nvrtc& n = nvrtc();
+  void* prog = nullptr;
+  if (n.create(&prog, src.c_str(), name, kEmbeddedCount, kEmbeddedTexts, kEmbeddedNames) != 0)
+    return set_error(PG_EUNSUPPORTED, "pg_batch_specialize: nvrtcCreateProgram failed");
+  const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo"};
+  const int rc = n.compile(prog, 3, opts);
+  if (rc != 0) {
+    size_t ls = 0;
+    n.log_size(prog, &ls);
+    std::string log(ls, '\0');
+    if (ls) n.log(prog, &log[0]);
+    n.destroy(&prog);
+    return set_error(PG_EUNSUPPORTED, "pg_batch_specialize: NVRTC compilation failed: " + log.substr(0, 2000));
+  }
+  size_t cs = 0;
+  n.cubin_size(prog, &cs);
+  cubin.assign(cs, 0);
+  n.cubin(prog, cubin.data());
+  n.destroy(&prog);
+  return PG_OK;
+}
+
+// Compile (or find in the caches) the cubin of a generated source.  The caches, in order: this
+// process's, the writable disk cache, the cubins shipped beside the library; a miss compiles and
+// writes the disk cache.  With out_dir (pg_model_precompile): compile into out_dir unless the
+// cubin is there already, and leave `cubin` empty.
+int compile_source(const std::string& src, const char* name, std::vector<char>& cubin,
+                   const std::string* out_dir = nullptr) {
   const Nvrtc& n = nvrtc();
   if (!n.ok) return set_error(PG_EUNSUPPORTED, "pg_batch_specialize: " + n.why);
   std::string key_src = src + "|nvrtc " + std::to_string(n.major) + "." + std::to_string(n.minor) + "|sm_103a";
   for (int i = 0; i < kEmbeddedCount; i++) key_src += kEmbeddedTexts[i];
   const uint64_t key = fnv1a(key_src);
+  char fname[32];
+  snprintf(fname, sizeof(fname), "%016llx.cubin", (unsigned long long)key);
+  if (out_dir) {
+    const std::string path = *out_dir + "/" + fname;
+    struct stat st{};
+    if (stat(path.c_str(), &st) == 0 && st.st_size > 0) return PG_OK;
+    std::vector<char> bin;
+    const int rc = nvrtc_compile(src, name, bin);
+    if (rc != PG_OK) return rc;
+    mkdirs(*out_dir);
+    write_file(path, bin);
+    return PG_OK;
+  }
   {
     std::lock_guard<std::mutex> lock(g_mutex);
     auto it = g_cubins.find(key);
     if (it != g_cubins.end()) { cubin = it->second; return PG_OK; }
   }
-  char fname[32];
-  snprintf(fname, sizeof(fname), "%016llx.cubin", (unsigned long long)key);
   const std::string dir = cache_dir(), path = dir + "/" + fname;
-  if (!read_file(path, cubin)) {
-    void* prog = nullptr;
-    if (n.create(&prog, src.c_str(), name, kEmbeddedCount, kEmbeddedTexts, kEmbeddedNames) != 0)
-      return set_error(PG_EUNSUPPORTED, "pg_batch_specialize: nvrtcCreateProgram failed");
-    const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo"};
-    const int rc = n.compile(prog, 3, opts);
-    if (rc != 0) {
-      size_t ls = 0;
-      n.log_size(prog, &ls);
-      std::string log(ls, '\0');
-      if (ls) n.log(prog, &log[0]);
-      n.destroy(&prog);
-      return set_error(PG_EUNSUPPORTED, "pg_batch_specialize: NVRTC compilation failed: " + log.substr(0, 2000));
-    }
-    size_t cs = 0;
-    n.cubin_size(prog, &cs);
-    cubin.assign(cs, 0);
-    n.cubin(prog, cubin.data());
-    n.destroy(&prog);
+  const std::string& shipped = shipped_cache_dir();
+  if (!read_file(path, cubin) && (shipped.empty() || !read_file(shipped + "/" + fname, cubin))) {
+    const int rc = nvrtc_compile(src, name, cubin);
+    if (rc != PG_OK) return rc;
     mkdirs(dir);
     write_file(path, cubin);
   }
@@ -397,6 +438,26 @@ extern "C" int pg_model_branch_plan(const pg_model* m, pg_kernel_info* out) {
     if (f) { fwrite(src.data(), 1, src.size(), f); fclose(f); }
   }
   return PG_OK;
+}
+
+extern "C" int pg_model_precompile(const pg_model* m, int64_t count, int envs_per_cta, int sms, unsigned flags,
+                                   const char* dir, int* envs_per_warp) {
+  if (!m) return set_error(PG_EINVAL, "model is NULL");
+  if (count < 0 || sms < 0) return set_error(PG_EINVAL, "negative env count or SM count");
+  if (envs_per_cta < 0 || envs_per_cta > kMaxEnvsPerCta) return set_error(PG_EINVAL, "envs_per_cta must be 0 (auto) or 1..256");
+  if (flags & ~(PG_SPEC_BRANCH | PG_SPEC_BRANCH_WARP | PG_PRECOMPILE_WIDTH_ONLY))
+    return set_error(PG_EINVAL, "unknown pg_model_precompile flags");
+  const int soa = thread_soa(m, count, envs_per_cta, sms ? sms : 148);
+  if (envs_per_warp) *envs_per_warp = soa;
+  if (flags & PG_PRECOMPILE_WIDTH_ONLY) return PG_OK;
+  const std::string out = dir && *dir ? std::string(dir) : cache_dir();
+  std::vector<char> unused;
+  int rc = compile_source(spec_source(m, soa), "pg_step_spec.cu", unused, &out);
+  if (rc != PG_OK || !(flags & (PG_SPEC_BRANCH | PG_SPEC_BRANCH_WARP))) return rc;
+  std::string src, why;
+  int lanes = 0, threads = 0, branches = 0;
+  if (branch_plan(m, src, why, lanes, threads, branches) != PG_OK) return PG_OK;   // does not qualify
+  return compile_source(src, "pg_step_branch.cu", unused, &out);
 }
 
 extern "C" int pg_batch_specialize_ex(pg_batch* b, unsigned flags) {

@@ -1,0 +1,76 @@
+"""Which models the GPU tests specialise, found without a GPU, so that their kernels can be
+compiled in parallel before the first test (paper_2502_08844_b300.kernel_cache).
+
+`collect()` runs the GPU tests once in a child pytest, on the CPU and with no device visible,
+with this module as a plugin.  The plugin replaces core.Batch by a recorder: each batch a test
+builds is recorded (its models, environment counts and envs_per_cta) and ends the test at its
+first use, so no test computes anything.  A test that builds a second batch after using its
+first is recorded up to the first; the rest of its kernels compile at run time as before.
+"""
+from __future__ import annotations
+
+import os
+import pickle
+import subprocess
+import sys
+import tempfile
+from typing import List
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CHILD_ENV = "PG_KERNEL_REQUESTS_OUT"
+
+_records = []
+
+
+class _Recorded(Exception):
+    pass
+
+
+def pytest_configure(config):
+    if not os.environ.get(CHILD_ENV):
+        return
+    import torch
+    from paper_2502_08844_b300 import core
+
+    class RecordingBatch:
+        def __init__(self, parts, envs_per_cta: int = 0):
+            parts = list(parts)
+            self.rec = {"parts": [(cm.src, int(n)) for cm, n in parts], "epc": int(envs_per_cta), "branch": None}
+            _records.append(self.rec)
+
+        def specialize(self, branch: bool = True, warp_blocks: bool = False):
+            self.rec["branch"] = bool(branch or warp_blocks)
+            raise _Recorded()
+
+        def __getattr__(self, name):
+            raise _Recorded()
+
+    core.Batch = RecordingBatch
+    # the GPU tests' fixture asks torch for a device; the recorder stops each test before it
+    # touches one
+    torch.cuda.is_available = lambda: True
+
+
+def pytest_sessionfinish(session, exitstatus):
+    out = os.environ.get(CHILD_ENV)
+    if out:
+        with open(out, "wb") as f:
+            pickle.dump(_records, f)
+
+
+def collect(test_paths: List[str], timeout_s: float = 300.0) -> list:
+    """kernel_cache requests (model, count, envs_per_cta, branch) of the GPU tests under
+    test_paths: the batches that the recording saw specialised (a batch that runs the library's
+    generic kernel needs no compile)."""
+    with tempfile.TemporaryDirectory() as tmp:
+        out = os.path.join(tmp, "requests.pkl")
+        env = dict(os.environ, CUDA_VISIBLE_DEVICES="", **{CHILD_ENV: out})
+        env["PYTHONPATH"] = ROOT + os.pathsep + env.get("PYTHONPATH", "")
+        subprocess.run([sys.executable, "-m", "pytest", *test_paths, "-m", "gpu", "-q", "-p", "tests.kernel_requests",
+                        "-p", "no:cacheprovider", "--no-header", "-o", "addopts="],
+                       cwd=ROOT, env=env, stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL, timeout=timeout_s)
+        with open(out, "rb") as f:
+            records = pickle.load(f)
+    return [(m, n, r["epc"], r["branch"]) for r in records if r["branch"] is not None for m, n in r["parts"]]
