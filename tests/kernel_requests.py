@@ -4,7 +4,7 @@ compiled in parallel before the first test (paper_2502_08844_b300.kernel_cache).
 `collect()` runs the GPU tests once in a child pytest, on the CPU and with no device visible,
 with this module as a plugin.  The plugin replaces core.Batch by a recorder: each batch a test
 builds is recorded (its models, environment counts and envs_per_cta) and ends the test at its
-first use, so no test computes anything.  A test that builds a second batch after using its
+first use (or at the first use of a state made for it), so no test computes anything.  A test that builds a second batch after using its
 first is recorded up to the first; the rest of its kernels compile at run time as before.
 """
 from __future__ import annotations
@@ -47,7 +47,18 @@ def pytest_configure(config):
         def __getattr__(self, name):
             raise _Recorded()
 
+    class InertState:
+        """A state that can be made but not used: tests that build their state before they
+        specialise the batch (GpuRun) still reach the specialisation."""
+
+        def __init__(self, *args, **kwargs):
+            pass
+
+        def __getattr__(self, name):
+            raise _Recorded()
+
     core.Batch = RecordingBatch
+    core.State = InertState
     # the GPU tests' fixture asks torch for a device; the recorder stops each test before it
     # touches one
     torch.cuda.is_available = lambda: True
