@@ -9,6 +9,7 @@ first is recorded up to the first; the rest of its kernels compile at run time a
 """
 from __future__ import annotations
 
+import inspect
 import os
 import pickle
 import subprocess
@@ -22,6 +23,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CHILD_ENV = "PG_KERNEL_REQUESTS_OUT"
 
 _records = []
+_current = {"mentions_specialize": False}
 
 
 class _Recorded(Exception):
@@ -37,7 +39,8 @@ def pytest_configure(config):
     class RecordingBatch:
         def __init__(self, parts, envs_per_cta: int = 0):
             parts = list(parts)
-            self.rec = {"parts": [(cm.src, int(n)) for cm, n in parts], "epc": int(envs_per_cta), "branch": None}
+            self.rec = {"parts": [(cm.src, int(n)) for cm, n in parts], "epc": int(envs_per_cta), "branch": None,
+                        "mentions_specialize": _current["mentions_specialize"]}
             _records.append(self.rec)
 
         def specialize(self, branch: bool = True, warp_blocks: bool = False):
@@ -64,6 +67,16 @@ def pytest_configure(config):
     torch.cuda.is_available = lambda: True
 
 
+def pytest_runtest_setup(item):
+    """Whether the test's own source mentions specialisation: a test that compares the generic
+    kernel with a specialised one often builds the generic batch first, and the recording stops
+    there."""
+    try:
+        _current["mentions_specialize"] = "specialize" in inspect.getsource(item.function)
+    except (AttributeError, OSError, TypeError):
+        _current["mentions_specialize"] = False
+
+
 def pytest_sessionfinish(session, exitstatus):
     out = os.environ.get(CHILD_ENV)
     if out:
@@ -73,8 +86,10 @@ def pytest_sessionfinish(session, exitstatus):
 
 def collect(test_paths: List[str], timeout_s: float = 300.0) -> list:
     """kernel_cache requests (model, count, envs_per_cta, branch) of the GPU tests under
-    test_paths: the batches that the recording saw specialised (a batch that runs the library's
-    generic kernel needs no compile)."""
+    test_paths: the batches that the recording saw specialised, and the batches of tests whose
+    source mentions specialisation where the recording stopped first (with the branch-parallel
+    kernel, which compiles only for a model that qualifies).  Batches of other tests run the
+    library's generic kernel and need no compile."""
     with tempfile.TemporaryDirectory() as tmp:
         out = os.path.join(tmp, "requests.pkl")
         env = dict(os.environ, CUDA_VISIBLE_DEVICES="", **{CHILD_ENV: out})
@@ -84,4 +99,10 @@ def collect(test_paths: List[str], timeout_s: float = 300.0) -> list:
                        cwd=ROOT, env=env, stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL, timeout=timeout_s)
         with open(out, "rb") as f:
             records = pickle.load(f)
-    return [(m, n, r["epc"], r["branch"]) for r in records if r["branch"] is not None for m, n in r["parts"]]
+    reqs = []
+    for r in records:
+        if r["branch"] is not None:
+            reqs += [(m, n, r["epc"], r["branch"]) for m, n in r["parts"]]
+        elif r["mentions_specialize"]:
+            reqs += [(m, n, r["epc"], True) for m, n in r["parts"]]
+    return reqs
