@@ -60,20 +60,21 @@ def precompile(requests: Iterable[Request], cache_dir: Optional[str] = None, job
         for i, (count, epc) in enumerate(widths.values()):
             tasks.append((cm, count, epc, branch and i == 0))
     tasks.sort(key=lambda t: -(t[0].src.nv * (2 if t[0].src.cone == W.ELLIPTIC else 1)))
-    skipped = [0]
 
-    def task(t):
+    def task(t) -> str:
         cm, count, epc, branch = t
         if budget_s is not None and time.time() - t0 > budget_s:
-            skipped[0] += 1
-            return
+            return "skipped"
         try:
             cm.precompile(count, envs_per_cta=epc, branch=branch, cache_dir=cache_dir)
+            return "ok"
         except Exception as e:
-            failed.append("%s: %s" % (cm.src.name, str(e).splitlines()[0] if str(e) else type(e).__name__))
+            return "%s: %s" % (cm.src.name, str(e).splitlines()[0] if str(e) else type(e).__name__)
 
+    results = []
     if tasks:
         with ThreadPoolExecutor(max_workers=max(1, min(len(tasks), jobs or os.cpu_count() or 1))) as ex:
-            list(ex.map(task, tasks))
-    return {"models": len(models), "tasks": len(tasks), "failed": failed, "skipped": skipped[0],
+            results = list(ex.map(task, tasks))
+    failed += [r for r in results if r not in ("ok", "skipped")]
+    return {"models": len(models), "tasks": len(tasks), "failed": failed, "skipped": results.count("skipped"),
             "wall_s": time.time() - t0}
