@@ -303,7 +303,10 @@ def test_contact_forces_match_converged_oracle():
         run.set_state(np.repeat(q[None], 4, 0), np.repeat(v[None], 4, 0))
         g = run.debug(np.repeat(u[None], 4, 0), 2)
         o = om.forward(q, v, np.zeros(18), u, solver_cap=-1)
-        if g["nrow"] == 0 or g["nrow"] != o["nrow"]:
+        # the rows are built before the solve, so they are the phase parity test's rows for these
+        # states, which it holds equal to the oracle's
+        assert g["nrow"] == o["nrow"]
+        if o["nrow"] == 0:   # airborne: no contact force to compare
             continue
         fg = _frame_forces(g["rows"], 18, g["contacts"], m)
         fo = _frame_forces(o["rows"], 18, o["contacts"], m)
@@ -311,7 +314,7 @@ def test_contact_forces_match_converged_oracle():
         for a, b in zip(fg, fo):   # per contact and component, against its normal force
             assert np.abs(a - b).max() <= FORCE_RTOL * abs(b[0]) + 1e-6, (a, b)
         checked += 1
-    assert checked >= 3
+    assert checked >= 5   # every state of the set but the airborne one
 
 
 def test_elliptic_contact_forces_match_converged_oracle():
@@ -327,7 +330,8 @@ def test_elliptic_contact_forces_match_converged_oracle():
         run.set_state(np.repeat(q[None], 4, 0), np.repeat(v[None], 4, 0))
         g = run.debug(np.repeat(u[None], 4, 0), 2)
         o = om.forward(q, v, np.zeros(m.nv), u, solver_cap=-1)
-        if g["nrow"] == 0 or g["nrow"] != o["nrow"]:
+        assert g["nrow"] == o["nrow"]   # as the phase parity test holds for these states
+        if o["nrow"] == 0:
             continue
         g = match_box_box_slots(m, g, o)
         nact = int((o["contacts"][:, 0] > 0).sum())   # contact rows first: (n, t1, t2) per contact
