@@ -26,7 +26,8 @@ def pytest_sessionstart(session):
     try:
         from tests.kernel_requests import collect
         from paper_2502_08844_b300 import kernel_cache
-        paths = [str(a) for a in session.config.args] or [os.path.join(ROOT, "tests")]
+        here = str(session.config.invocation_params.dir)   # the child runs from the repository root
+        paths = [os.path.join(here, str(a)) for a in session.config.args] or [os.path.join(ROOT, "tests")]
         r = kernel_cache.precompile(collect(paths), cache_dir=None)
         print("\nkernel cache: %d models compiled or found in %.0f s%s" % (
             r["models"], r["wall_s"], ("; failed: " + "; ".join(r["failed"])) if r["failed"] else ""))
