@@ -8,6 +8,8 @@
 #include <cmath>
 #include <vector>
 
+#include "orc_math.hpp"
+
 namespace orc {
 
 struct Tape {
@@ -53,6 +55,7 @@ struct adouble {
 };
 
 inline double val(const adouble& a) { return a.v; }
+template <> struct Taped<adouble> { static constexpr bool value = true; };
 
 inline adouble node(double v, const adouble& a, double da, const adouble& b, double db) {
   adouble r(v);

@@ -150,6 +150,8 @@ template <class T> void ldlt_solve(const Vec<T>& A, int n, Vec<T>& b) {
 // solves), except for a counting scalar (orc_count.hpp), which takes the tree methods whose flops
 // the step's count is of: CRBA and the leaves-first L^T D L (each pinned against the plain one).
 template <class T> struct TreeMethods { static constexpr bool value = false; };
+// Whether a scalar records a reverse-mode tape (orc_ad.hpp specialises it for adouble).
+template <class T> struct Taped { static constexpr bool value = false; };
 template <class T> bool spd_factor(Vec<T>& A, int n) {
   return TreeMethods<T>::value ? ldlt_leaves_first(A, n) : cholesky(A, n);
 }

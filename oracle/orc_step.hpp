@@ -1276,12 +1276,13 @@ template <class T> SolveResult<T> newton_solve(int nv, const std::vector<T>& M, 
     return s;
   };
   T f_cur = elliptic ? cost(nv, M, a0, R, a) : T(0);   // (the stopping rule of elliptic contacts)
-  for (int it = 0; it < cap; it++) {
-    std::vector<char> A = active_set(a);
-    // g and the lower triangle of H (the factorisations read only that triangle; it is mirrored
-    // before them)
-    std::vector<T> g(nv), H(M), t(nv);
-    for (int j = 0; j < nv; j++) t[j] = a[j] - a0[j];
+  // g and the lower triangle of H at `at` with the active set A (the factorisations read only that
+  // triangle; it is mirrored before them)
+  auto grad_hess = [&](const std::vector<T>& at, const std::vector<char>& A, std::vector<T>& g, std::vector<T>& H) {
+    g.assign(nv, T(0));
+    H = M;
+    std::vector<T> t(nv);
+    for (int j = 0; j < nv; j++) t[j] = at[j] - a0[j];
     for (int i = 0; i < nv; i++) {
       T s = T(0);
       for (int j = 0; j < nv; j++) s = s + M[i * nv + j] * t[j];
@@ -1298,7 +1299,7 @@ template <class T> SolveResult<T> newton_solve(int nv, const std::vector<T>& M, 
         T x[3], gc[3], Hc[9];
         for (int e = 0; e < 3; e++) {
           x[e] = -R.aref[r + e];
-          for (int j = 0; j < nv; j++) x[e] = x[e] + R.J[(r + e) * nv + j] * a[j];
+          for (int j = 0; j < nv; j++) x[e] = x[e] + R.J[(r + e) * nv + j] * at[j];
         }
         cone_grad_hess(x, R.D[r], R.mu[r], gc, Hc);
         for (int i = 0; i < nv; i++)
@@ -1310,7 +1311,7 @@ template <class T> SolveResult<T> newton_solve(int nv, const std::vector<T>& M, 
         continue;
       }
       T jar = -R.aref[r];
-      for (int j = 0; j < nv; j++) jar = jar + R.J[r * nv + j] * a[j];
+      for (int j = 0; j < nv; j++) jar = jar + R.J[r * nv + j] * at[j];
       const T Djar = R.D[r] * jar;
       for (int i = 0; i < nv; i++) {
         g[i] = g[i] + Djar * R.J[r * nv + i];
@@ -1320,6 +1321,11 @@ template <class T> SolveResult<T> newton_solve(int nv, const std::vector<T>& M, 
     }
     for (int i = 0; i < nv; i++)
       for (int j = i + 1; j < nv; j++) H[i * nv + j] = H[j * nv + i];
+  };
+  for (int it = 0; it < cap; it++) {
+    std::vector<char> A = active_set(a);
+    std::vector<T> g, H;
+    grad_hess(a, A, g, H);
     out.iterations = it + 1;
     bool zero = true;
     for (int i = 0; i < nv; i++) zero = zero && val(g[i]) == 0;
@@ -1342,6 +1348,23 @@ template <class T> SolveResult<T> newton_solve(int nv, const std::vector<T>& M, 
     T f_new = cost(nv, M, a0, R, a);
     if ((A2 == A && !middle) || !(val(f_new) < val(f_cur))) { out.converged = true; break; }
     f_cur = f_new;
+  }
+  // Reverse mode differentiates the solve through its iterations.  At the minimiser, one Newton
+  // step with the final active set held, a - H^-1 g(a), leaves the value where it is (g(a) = 0 to
+  // rounding) and carries exactly the implicit derivative of the minimiser, -H^-1 dg/dtheta,
+  // whatever the iterates before it (g is affine in a for a fixed active set, so
+  // a - H^-1 g(a) = a* identically).  Without it, a solve that starts at the minimiser (warm-started
+  // from the previous substep) ends on a step of rounding size, whose line-search factor, and with
+  // it the derivative that factor scales, is rounding noise.  Taped instantiations only: the
+  // values of the plain and counting ones are untouched.
+  if (Taped<T>::value && out.converged && !elliptic) {
+    std::vector<char> A = active_set(a);
+    std::vector<T> g, H;
+    grad_hess(a, A, g, H);
+    if (spd_factor(H, nv)) {
+      spd_solve(H, nv, g);
+      for (int i = 0; i < nv; i++) a[i] = a[i] - g[i];
+    }
   }
   out.qacc = a;
   PhaseHook<T>::set(8);   // the contact forces: an output, not part of the step's work

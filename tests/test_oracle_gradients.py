@@ -102,3 +102,34 @@ def test_step_vjp_chain_equals_rollout_gradient():
     assert np.allclose(bq, g["q0"], rtol=1e-9, atol=1e-12)
     assert np.allclose(bv, g["v0"], rtol=1e-9, atol=1e-12)
     assert np.allclose(gm, g["mass"], rtol=1e-9, atol=1e-12)
+
+
+def test_warm_started_resting_box_gradient_matches_central_differences():
+    """A box dropped flat onto a plane comes to rest, and each substep's solve starts at the
+    previous substep's minimiser (the warm start), so it converges on a step of rounding size.
+    The taped gradient must still be the implicit derivative of the minimiser: against FP64
+    central differences, with the lateral and spin components exactly zero by symmetry.  A tape
+    that differentiates that last rounding-size step's line search instead was off by 1 % in
+    v_x and gave the symmetric components 1e-3."""
+    b = W.ModelBuilder("flat_box")
+    g0 = b.geom(0, W.PLANE, (0, 0, 0))
+    body = b.body(0, (0, 0, 0.2))
+    b.joint(body, W.FREE)
+    g1 = b.geom(body, W.BOX, (0.05, 0.05, 0.05), mass=1.0)
+    b.pair(g0, g1, friction=0.8, condim=3)
+    m = b.build(timestep=0.002, iterations=100, n_substeps=1)
+    om = O.OracleModel(m)
+    w = O.tracking_loss_weights(om)
+    q0 = np.array([0.0, 0.0, 0.052, 1.0, 0.0, 0.0, 0.0])
+    v0 = np.zeros(6)
+    U = np.zeros((16, 0))
+    g = O.rollout_grad(om, q0, v0, U, 1, w)
+    fd = _fd(lambda x: O.rollout_loss(om, q0, x, U, 1, w), v0, range(6))
+    _close(g["v0"], fd, rtol=1e-6)
+    assert np.all(np.abs(g["v0"][[1, 3, 5]]) <= 1e-9)
+    # the same horizon as 16 substeps inside one control step (warm starts taped)
+    m16 = b.build(timestep=0.002, iterations=100, n_substeps=16)
+    om16 = O.OracleModel(m16)
+    g16 = O.rollout_grad(om16, q0, v0, np.zeros((1, 0)), 16, w)
+    fd16 = _fd(lambda x: O.rollout_loss(om16, q0, x, np.zeros((1, 0)), 16, w), v0, range(6))
+    _close(g16["v0"], fd16, rtol=1e-6)
